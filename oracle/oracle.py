@@ -1,0 +1,234 @@
+"""ctypes front end of the serial FP64 CPU oracle (``oracle/sif_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  Nothing here is
+shared with the CUDA library or its Python binding.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sif_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+
+BC = {"reflect": 0, "zerograd": 1, "periodic": 2}
+ERR_NONPHYS, ERR_NOCONV, ERR_INVAL = 1, 2, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle as a shared library (gcc, no FMA contraction)."""
+    hdr = os.path.join(_HERE, "sif_oracle.h")
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(hdr))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("bc", ctypes.c_int * 4),
+                ("gamma", ctypes.c_double * 2), ("pinf", ctypes.c_double * 2),
+                ("cfl", ctypes.c_double), ("rk_order", ctypes.c_int),
+                ("weno_eps", ctypes.c_double), ("mix_alpha", ctypes.c_double),
+                ("ratio_threshold", ctypes.c_double),
+                ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
+                ("band", ctypes.c_double),
+                ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt1", ctypes.c_double), ("dt2", ctypes.c_double),
+                ("n_raw", ctypes.c_double), ("n_used", ctypes.c_double),
+                ("role_fluid1", ctypes.c_int), ("substeps", ctypes.c_int),
+                ("err", ctypes.c_int)]
+
+
+_lib_handle = None
+
+
+def lib():
+    global _lib_handle
+    if _lib_handle is None:
+        L = ctypes.CDLL(build())
+        P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_create.restype = P
+        L.orc_create.argtypes = [ctypes.POINTER(_Config)]
+        L.orc_destroy.argtypes = [P]
+        L.orc_init.argtypes = [P, dp, dp, dp]
+        L.orc_step_single_dt.argtypes = [P, I, D, ctypes.POINTER(_Info)]
+        L.orc_step_multi_dt.argtypes = [P, I, D, ctypes.POINTER(_Info)]
+        L.orc_get_state.argtypes = [P, dp, dp, dp]
+        L.orc_set_state.argtypes = [P, dp, dp, dp]
+        L.orc_integrals.argtypes = [P, dp]
+        L.orc_time.restype = D
+        L.orc_time.argtypes = [P]
+        L.orc_status.argtypes = [P]
+        L.orc_geometry.argtypes = [P, dp, dp, dp, dp, dp]
+        L.orc_rhs.argtypes = [P, I, dp]
+        L.orc_stencil_states.argtypes = [P, I, dp]
+        L.orc_reinit_only.argtypes = [P]
+        L.orc_mix_only.argtypes = [P, I]
+        L.orc_weno5.restype = D
+        L.orc_weno5.argtypes = [dp, D]
+        L.orc_edge_fraction.restype = D
+        L.orc_edge_fraction.argtypes = [D, D]
+        L.orc_cell_alpha.restype = D
+        L.orc_cell_alpha.argtypes = [D, D, D, D]
+        L.orc_riemann.argtypes = [dp, dp, dp]
+        _lib_handle = L
+    return _lib_handle
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_config(cfg: dict) -> _Config:
+    c = _Config()
+    c.dim = int(cfg["dim"])
+    c.nx, c.ny = int(cfg["nx"]), int(cfg["ny"])
+    c.x0, c.y0 = float(cfg.get("x0", 0.0)), float(cfg.get("y0", 0.0))
+    c.dx, c.dy = float(cfg["dx"]), float(cfg["dy"])
+    for i, b in enumerate(cfg["bc"]):
+        c.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    for k in range(2):
+        c.gamma[k] = float(cfg["gamma"][k])
+        c.pinf[k] = float(cfg["pinf"][k])
+    c.cfl = float(cfg.get("cfl", 0.6))
+    c.rk_order = int(cfg.get("rk_order", 2))
+    c.weno_eps = float(cfg.get("weno_eps", 1e-6))
+    c.mix_alpha = float(cfg.get("mix_alpha", 0.5))
+    c.ratio_threshold = float(cfg.get("ratio_threshold", 0.7))
+    c.ext_iters = int(cfg.get("ext_iters", 10))
+    c.reinit_iters = int(cfg.get("reinit_iters", 2))
+    c.band = float(cfg.get("band", 6.0))
+    c.flux_correction = int(cfg.get("flux_correction", 1))
+    c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
+    return c
+
+
+class Oracle:
+    """One two-fluid problem advanced by the serial oracle."""
+
+    def __init__(self, cfg: dict):
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg)
+        self._h = lib().orc_create(ctypes.byref(self._c))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration")
+        self.nx, self.ny = self._c.nx, self._c.ny
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    def init(self, phi, prim_N, prim_P):
+        phi, pN, pP = _f64(phi), _f64(prim_N), _f64(prim_P)
+        lib().orc_init(self._h, _ptr(phi), _ptr(pN), _ptr(pP))
+        return self
+
+    def _info(self, info):
+        return {"t": info.t, "dt1": info.dt1, "dt2": info.dt2, "n_raw": info.n_raw,
+                "n_used": info.n_used, "role_fluid1": info.role_fluid1,
+                "substeps": info.substeps, "err": info.err}
+
+    def step_single_dt(self, nsteps=1, t_end=0.0):
+        info = _Info()
+        lib().orc_step_single_dt(self._h, int(nsteps), float(t_end), ctypes.byref(info))
+        return self._info(info)
+
+    def step_multi_dt(self, ncycles=1, t_end=0.0):
+        info = _Info()
+        lib().orc_step_multi_dt(self._h, int(ncycles), float(t_end), ctypes.byref(info))
+        return self._info(info)
+
+    def state(self):
+        n = self.nx * self.ny
+        qN, qP, phi = np.empty(4 * n), np.empty(4 * n), np.empty(n)
+        lib().orc_get_state(self._h, _ptr(qN), _ptr(qP), _ptr(phi))
+        sh = (4, self.ny, self.nx)
+        return qN.reshape(sh), qP.reshape(sh), phi.reshape(self.ny, self.nx)
+
+    def set_state(self, qN, qP, phi):
+        qN, qP, phi = _f64(qN), _f64(qP), _f64(phi)
+        lib().orc_set_state(self._h, _ptr(qN), _ptr(qP), _ptr(phi))
+
+    def integrals(self):
+        out = np.empty(8)
+        lib().orc_integrals(self._h, _ptr(out))
+        return out.reshape(2, 4)
+
+    @property
+    def t(self):
+        return lib().orc_time(self._h)
+
+    @property
+    def status(self):
+        return lib().orc_status(self._h)
+
+    def geometry(self):
+        nx, ny = self.nx, self.ny
+        al, sx, sy = np.empty(nx * ny), np.empty(nx * ny), np.empty(nx * ny)
+        ax, ay = np.empty((nx + 1) * ny), np.empty(nx * (ny + 1))
+        lib().orc_geometry(self._h, _ptr(al), _ptr(ax), _ptr(ay), _ptr(sx), _ptr(sy))
+        return {"alpha": al.reshape(ny, nx), "ax": ax.reshape(ny, nx + 1),
+                "ay": ay.reshape(ny + 1, nx), "sx": sx.reshape(ny, nx),
+                "sy": sy.reshape(ny, nx)}
+
+    def rhs(self, k):
+        out = np.empty(4 * self.nx * self.ny)
+        lib().orc_rhs(self._h, int(k), _ptr(out))
+        return out.reshape(4, self.ny, self.nx)
+
+    def stencil_states(self, k):
+        out = np.empty(4 * self.nx * self.ny)
+        lib().orc_stencil_states(self._h, int(k), _ptr(out))
+        return out.reshape(4, self.ny, self.nx)
+
+    def reinit_only(self):
+        lib().orc_reinit_only(self._h)
+
+    def mix_only(self, k):
+        lib().orc_mix_only(self._h, int(k))
+
+
+def weno5(v, eps=1e-6):
+    a = _f64(v)
+    return lib().orc_weno5(_ptr(a), float(eps))
+
+
+def edge_fraction(a, b):
+    return lib().orc_edge_fraction(float(a), float(b))
+
+
+def cell_alpha(c00, c10, c11, c01):
+    return lib().orc_cell_alpha(float(c00), float(c10), float(c11), float(c01))
+
+
+def riemann(left, right):
+    """left/right = (rho, u, p, gamma, pinf); returns dict of the star state."""
+    L, R, out = _f64(left), _f64(right), np.empty(7)
+    rc = lib().orc_riemann(_ptr(L), _ptr(R), _ptr(out))
+    return {"p": out[0], "u": out[1], "rho_L": out[2], "rho_R": out[3],
+            "c_L": out[4], "c_R": out[5], "iters": int(out[6]), "rc": rc}

@@ -1,0 +1,1207 @@
+/*
+ * sif_oracle.c -- plain, slow, serial FP64 oracle of the accelerated
+ * conservative sharp-interface method (Long, Cai & Pan, arXiv 1905.03917).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the package smoke check and
+ * the CPU-baseline leg of bench.py, never by the product path.  It shares
+ * no code with the CUDA library.  Compile with -O2 -ffp-contract=off and no
+ * fast-math so that every operation is rounded as written.
+ *
+ * What each part follows and what pins it (tests/test_oracle_*.py):
+ *   edge fraction, cell volume fraction, apertures, interface vector
+ *       -- Sec. 2.1 / Fig. 1 (cut cell with apertures and interface
+ *          segment); pinned by exact half-plane areas and segment lengths
+ *          and by circle areas.
+ *   WENO5-JS reconstruction, Lax-Friedrichs splitting, TVD-RK2 / SSP-RK3
+ *       -- Sec. 4 (WENO-LF, RK2, CFL 0.6); pinned by fifth-order
+ *          convergence of the single-fluid operator and by the
+ *          single-fluid reduction of Eq. 2.
+ *   exact stiffened-gas Riemann problem (interface interaction)
+ *       -- Sec. 2.1 (interface exchange flux X); pinned by textbook
+ *          ideal-gas star states and by Rankine-Hugoniot / isentrope
+ *          checks of the stiffened-gas solution.
+ *   cut-cell update with X, mixing, extension -- Eq. 2, Sec. 2.1-2.3;
+ *          pinned by the static-interface test, exact conservation and
+ *          the 1D exact-solution convergence test.
+ *   level-set advection (Eq. 6) and reinitialisation (Sec. 2.3) -- pinned
+ *          by rigid translation of a circle and invariance of a planar
+ *          signed distance under reinitialisation.
+ *   multi-time-step cycle: time-step ratio and its truncation, fluid-1
+ *          previous/future states, Eq. 7 interpolation, Eq. 8-9 correction
+ *          quantities and the final correction -- Sec. 3.1 steps 1-5;
+ *          pinned by exact conservation with the correction on (and its
+ *          visible loss with it off) and by the bitwise ratio-one
+ *          reduction to the single-step method.
+ * Parity unpinned (checked only against the GPU): the number of extension
+ * and reinitialisation sweeps and the band width (the paper gives none).
+ */
+#include "sif_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define GH 3 /* ghost layers: the WENO5 stencil reaches three cells */
+/* A cell counts as holding fluid k (its stencil state is (alpha U)/alpha
+ * and it enters the CFL bound) only if alpha_k exceeds this; thinner
+ * slivers, which round-off in the corner values creates, take extended
+ * states like empty cells while their (alpha U) is still carried and
+ * mixed. */
+#define ALPHA_REAL 1e-6
+
+struct orc_ctx {
+  orc_config c;
+  int PX, PY, NP;
+  double h; /* min(dx, dy) */
+  double *q[2][4];  /* (alpha U)_k: mass, x-mom, y-mom, energy */
+  double *w[2][4];  /* stencil states W_k: rho, u, v, p */
+  double *phi;
+  double *alpha, *ax, *ay, *sx, *sy; /* alpha_P, P-apertures, S (N to P) */
+  double *xn[3];    /* interface exchange X as applied to fluid N */
+  double *ul[2];    /* level-set velocity */
+  double smax[2];   /* CFL maxima per fluid (cells and star states) */
+  double lf[2][2];  /* Lax-Friedrichs alpha per fluid and direction */
+  double t;
+  int err;
+  /* scratch */
+  double *q0[2][4], *L[2][4], *old[4], *fx[4], *fy[4];
+  double *prev[4], *fut[4], *qi[4], *xc[3];
+  double *phi0, *lphi, *p0;
+  unsigned char *band, *rext;
+};
+
+#define ID(o, i, j) ((i) + GH + ((j) + GH) * (o)->PX)
+
+static double sq(double a) { return a * a; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+
+/* ------------------------------------------------------------------ */
+/* ghost layers                                                        */
+
+/* vel: 0 scalar, 1 x-velocity (odd at x walls), 2 y-velocity (odd at y
+ * walls).  x ghosts are filled for interior rows, then y ghosts for every
+ * column including the x ghosts. */
+static void fill_ghost(orc_ctx *o, double *a, int vel) {
+  int nx = o->c.nx, ny = o->c.ny;
+  for (int j = 0; j < ny; j++) {
+    for (int m = 0; m < GH; m++) {
+      double sl = (vel == 1 && o->c.bc[0] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      double sr = (vel == 1 && o->c.bc[1] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      double vl, vr;
+      switch (o->c.bc[0]) {
+        case ORC_BC_REFLECT: vl = a[ID(o, m, j)]; break;
+        case ORC_BC_PERIODIC: vl = a[ID(o, nx - 1 - m, j)]; break;
+        default: vl = a[ID(o, 0, j)];
+      }
+      switch (o->c.bc[1]) {
+        case ORC_BC_REFLECT: vr = a[ID(o, nx - 1 - m, j)]; break;
+        case ORC_BC_PERIODIC: vr = a[ID(o, m, j)]; break;
+        default: vr = a[ID(o, nx - 1, j)];
+      }
+      a[ID(o, -1 - m, j)] = sl < 0 ? -vl : vl;
+      a[ID(o, nx + m, j)] = sr < 0 ? -vr : vr;
+    }
+  }
+  for (int i = -GH; i < nx + GH; i++) {
+    for (int m = 0; m < GH; m++) {
+      double sb = (vel == 2 && o->c.bc[2] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      double st = (vel == 2 && o->c.bc[3] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      double vb, vt;
+      switch (o->c.bc[2]) {
+        case ORC_BC_REFLECT: vb = a[ID(o, i, m)]; break;
+        case ORC_BC_PERIODIC: vb = a[ID(o, i, ny - 1 - m)]; break;
+        default: vb = a[ID(o, i, 0)];
+      }
+      switch (o->c.bc[3]) {
+        case ORC_BC_REFLECT: vt = a[ID(o, i, ny - 1 - m)]; break;
+        case ORC_BC_PERIODIC: vt = a[ID(o, i, m)]; break;
+        default: vt = a[ID(o, i, ny - 1)];
+      }
+      a[ID(o, i, -1 - m)] = sb < 0 ? -vb : vb;
+      a[ID(o, i, ny + m)] = st < 0 ? -vt : vt;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry from the level set (Sec. 2.1, Fig. 1)                      */
+
+double orc_edge_fraction(double a, double b) {
+  /* fraction of the straight edge from value a to value b with phi >= 0,
+   * phi varying linearly along the edge */
+  if (a >= 0.0 && b >= 0.0) return 1.0;
+  if (a < 0.0 && b < 0.0) return 0.0;
+  if (a >= 0.0) return a / (a - b);
+  return b / (b - a);
+}
+
+double orc_cell_alpha(double c00, double c10, double c11, double c01) {
+  /* area of {phi >= 0} in the unit cell, phi bilinear through the corner
+   * values (counter-clockwise from the lower-left corner), approximated by
+   * the polygon through the P corners and the edge crossings.  In the
+   * saddle case the P corners are taken as disconnected triangles. */
+  const double v[4] = {c00, c10, c11, c01};
+  const double px[4] = {0.0, 1.0, 1.0, 0.0};
+  const double py[4] = {0.0, 0.0, 1.0, 1.0};
+  int npos = 0, changes = 0;
+  for (int e = 0; e < 4; e++) {
+    if (v[e] >= 0.0) npos++;
+    if ((v[e] >= 0.0) != (v[(e + 1) & 3] >= 0.0)) changes++;
+  }
+  if (npos == 4) return 1.0;
+  if (npos == 0) return 0.0;
+  if (changes == 4) {
+    double area = 0.0;
+    for (int e = 0; e < 4; e++) {
+      if (v[e] < 0.0) continue;
+      int n = (e + 1) & 3, p = (e + 3) & 3;
+      double l1 = v[e] / (v[e] - v[n]);
+      double l2 = v[e] / (v[e] - v[p]);
+      area += 0.5 * l1 * l2;
+    }
+    return area;
+  }
+  double X[8], Y[8];
+  int m = 0;
+  for (int e = 0; e < 4; e++) {
+    int n = (e + 1) & 3;
+    if (v[e] >= 0.0) {
+      X[m] = px[e];
+      Y[m] = py[e];
+      m++;
+    }
+    if ((v[e] >= 0.0) != (v[n] >= 0.0)) {
+      double s = v[e] / (v[e] - v[n]);
+      X[m] = px[e] + s * (px[n] - px[e]);
+      Y[m] = py[e] + s * (py[n] - py[e]);
+      m++;
+    }
+  }
+  double a2 = 0.0;
+  for (int k = 0; k < m; k++) {
+    int k1 = (k + 1) % m;
+    a2 += X[k] * Y[k1] - X[k1] * Y[k];
+  }
+  return 0.5 * a2;
+}
+
+/* level set at the lower-left corner of cell (i, j): mean of the four
+ * cells sharing that corner */
+static double corner(const orc_ctx *o, const double *p, int i, int j) {
+  return 0.25 * ((p[ID(o, i - 1, j - 1)] + p[ID(o, i, j - 1)]) +
+                 (p[ID(o, i - 1, j)] + p[ID(o, i, j)]));
+}
+
+static void geometry(orc_ctx *o, double *p) {
+  int nx = o->c.nx, ny = o->c.ny;
+  fill_ghost(o, p, 0);
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i <= nx; i++)
+      o->ax[ID(o, i, j)] =
+          orc_edge_fraction(corner(o, p, i, j), corner(o, p, i, j + 1));
+  for (int j = 0; j <= ny; j++)
+    for (int i = 0; i < nx; i++)
+      o->ay[ID(o, i, j)] =
+          orc_edge_fraction(corner(o, p, i, j), corner(o, p, i + 1, j));
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      int c = ID(o, i, j);
+      o->alpha[c] = orc_cell_alpha(corner(o, p, i, j), corner(o, p, i + 1, j),
+                                   corner(o, p, i + 1, j + 1),
+                                   corner(o, p, i, j + 1));
+      /* the faces of the P region and its interface segment close:
+       * S = sum over faces of A_P times the outward face normal length */
+      o->sx[c] = (o->ax[ID(o, i + 1, j)] - o->ax[c]) * o->c.dy;
+      o->sy[c] = (o->ay[ID(o, i, j + 1)] - o->ay[c]) * o->c.dx;
+    }
+}
+
+static double vol(const orc_ctx *o, int k, int c) {
+  return k == 1 ? o->alpha[c] : 1.0 - o->alpha[c];
+}
+
+/* unit normal grad(phi)/|grad(phi)| by central differences (points into P) */
+static void normal(const orc_ctx *o, const double *p, int i, int j,
+                   double *nxo, double *nyo) {
+  double gx = (p[ID(o, i + 1, j)] - p[ID(o, i - 1, j)]) / (2.0 * o->c.dx);
+  double gy = o->c.dim == 2
+                  ? (p[ID(o, i, j + 1)] - p[ID(o, i, j - 1)]) / (2.0 * o->c.dy)
+                  : 0.0;
+  double m = sqrt(gx * gx + gy * gy);
+  if (m > 0.0) {
+    *nxo = gx / m;
+    *nyo = gy / m;
+  } else {
+    *nxo = 0.0;
+    *nyo = 0.0;
+  }
+}
+
+static int inside(const orc_ctx *o, int i, int j) {
+  return i >= 0 && i < o->c.nx && j >= 0 && j < o->c.ny;
+}
+
+/* ------------------------------------------------------------------ */
+/* small-cell mixing (Sec. 2.2, last paragraph)                        */
+
+static void mix(orc_ctx *o, int k, double *const q[4]) {
+  int nx = o->c.nx, ny = o->c.ny;
+  for (int m = 0; m < 4; m++) memcpy(o->old[m], q[m], sizeof(double) * o->NP);
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      int c = ID(o, i, j);
+      double as = vol(o, k, c);
+      if (as >= o->c.mix_alpha) continue;
+      if (as == 0.0 && o->old[0][c] == 0.0 && o->old[1][c] == 0.0 &&
+          o->old[2][c] == 0.0 && o->old[3][c] == 0.0)
+        continue;
+      double nxv, nyv;
+      normal(o, o->phi, i, j, &nxv, &nyv);
+      if (k == 0) {
+        nxv = -nxv;
+        nyv = -nyv;
+      }
+      int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+      int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
+      double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
+      int nt = o->c.dim == 2 ? 3 : 1;
+      /* targets: normal-direction neighbours of larger volume fraction;
+       * neighbours that are not small cells themselves are preferred, and
+       * only when there is none do smaller (but still larger than the
+       * source) neighbours take part */
+      int keep[3] = {0, 0, 0};
+      double sum = 0.0;
+      for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
+        for (int t = 0; t < nt; t++) {
+          if (!inside(o, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
+          double at = vol(o, k, ID(o, ti[t], tj[t]));
+          if (pass == 0 ? !(at >= o->c.mix_alpha) : !(at > as)) continue;
+          keep[t] = 1;
+          sum += wt[t];
+        }
+      if (!(sum > 0.0)) continue;
+      for (int t = 0; t < nt; t++) {
+        if (!keep[t]) continue;
+        int tc = ID(o, ti[t], tj[t]);
+        double beta = wt[t] / sum;
+        double at = vol(o, k, tc);
+        double den = as * beta + at;
+        for (int m = 0; m < 4; m++) {
+          double M = beta * (o->old[m][tc] * as - o->old[m][c] * at) / den;
+          q[m][c] += M;
+          q[m][tc] -= M;
+        }
+      }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* stencil states: real cells and extension (Sec. 2.3, last paragraph) */
+
+static void prim(orc_ctx *o, int k, double *const q[4]) {
+  double g = o->c.gamma[k], pi = o->c.pinf[k];
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      double a = vol(o, k, c);
+      if (!(a > ALPHA_REAL)) continue;
+      double rho = q[0][c] / a;
+      double u = q[1][c] / q[0][c];
+      double v = q[2][c] / q[0][c];
+      double E = q[3][c] / a;
+      double p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - g * pi;
+      if (!(rho > 0.0) || !(p + pi > 0.0)) o->err |= ORC_ERR_NONPHYS;
+      o->w[k][0][c] = rho;
+      o->w[k][1][c] = u;
+      o->w[k][2][c] = v;
+      o->w[k][3][c] = p;
+    }
+}
+
+/* Jacobi sweeps of the steady upwind discretisation of n_k . grad(q) = 0
+ * (n_k the unit normal pointing into fluid k) for band cells that hold no
+ * fluid k: each sweep sets a target to the upwind-weighted mean of its
+ * upwind x and y neighbours (neighbours outside the domain drop out). */
+static void extend(orc_ctx *o, int k, const double *p) {
+  double bw = o->c.band * o->h;
+  for (int it = 0; it < o->c.ext_iters; it++) {
+    for (int m = 0; m < 4; m++) memcpy(o->old[m], o->w[k][m], sizeof(double) * o->NP);
+    for (int j = 0; j < o->c.ny; j++)
+      for (int i = 0; i < o->c.nx; i++) {
+        int c = ID(o, i, j);
+        if (!(fabs(p[c]) < bw) || vol(o, k, c) > ALPHA_REAL) continue;
+        double nxv, nyv;
+        normal(o, p, i, j, &nxv, &nyv);
+        if (k == 0) {
+          nxv = -nxv;
+          nyv = -nyv;
+        }
+        int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+        double wx = fabs(nxv) / o->c.dx;
+        double wy = o->c.dim == 2 ? fabs(nyv) / o->c.dy : 0.0;
+        if (!inside(o, i + sx, j)) wx = 0.0;
+        if (!inside(o, i, j + sy)) wy = 0.0;
+        double den = wx + wy;
+        if (!(den > 0.0)) continue;
+        for (int m = 0; m < 4; m++) {
+          double num = 0.0;
+          if (wx > 0.0) num += wx * o->old[m][ID(o, i + sx, j)];
+          if (wy > 0.0) num += wy * o->old[m][ID(o, i, j + sy)];
+          o->w[k][m][c] = num / den;
+        }
+      }
+  }
+}
+
+/* Lax-Friedrichs alpha over every cell whose state can enter a stencil
+ * (real or extended), and the CFL sum over real cells. */
+static void wave_maxima(orc_ctx *o, int k, const double *p) {
+  double g = o->c.gamma[k], pi = o->c.pinf[k];
+  double bw = o->c.band * o->h;
+  double lx = 0.0, ly = 0.0, sm = 0.0;
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      int real = vol(o, k, c) > ALPHA_REAL;
+      if (!real && !(fabs(p[c]) < bw)) continue;
+      double rho = o->w[k][0][c], u = o->w[k][1][c], v = o->w[k][2][c];
+      double pr = o->w[k][3][c];
+      double cs = sqrt(dmax(g * (pr + pi) / rho, 0.0));
+      lx = dmax(lx, fabs(u) + cs);
+      ly = dmax(ly, fabs(v) + cs);
+      if (real) {
+        double s = (fabs(u) + cs) / o->c.dx;
+        if (o->c.dim == 2) s += (fabs(v) + cs) / o->c.dy;
+        sm = dmax(sm, s);
+      }
+    }
+  o->lf[k][0] = lx;
+  o->lf[k][1] = ly;
+  o->smax[k] = sm;
+}
+
+/* ------------------------------------------------------------------ */
+/* interface interaction: exact two-material Riemann problem           */
+
+static void side_f(double p, double rho, double pk, double g, double pi,
+                   double ck, double *f, double *df) {
+  double P = pk + pi, Pp = p + pi;
+  if (p > pk) {
+    double A = 2.0 / ((g + 1.0) * rho);
+    double B = (g - 1.0) / (g + 1.0) * P;
+    double qr = sqrt(A / (Pp + B));
+    *f = (p - pk) * qr;
+    *df = qr * (1.0 - 0.5 * (p - pk) / (Pp + B));
+  } else {
+    double r = Pp / P;
+    *f = 2.0 * ck / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
+    *df = 1.0 / (rho * ck) * pow(r, -(g + 1.0) / (2.0 * g));
+  }
+}
+
+static double star_density(double p, double rho, double pk, double g, double pi) {
+  double r = (p + pi) / (pk + pi);
+  if (p > pk) {
+    double qq = (g - 1.0) / (g + 1.0);
+    return rho * (r + qq) / (qq * r + 1.0);
+  }
+  return rho * pow(r, 1.0 / g);
+}
+
+int orc_riemann(const double *L, const double *R, double *out) {
+  double rl = L[0], ul = L[1], pl = L[2], gl = L[3], pil = L[4];
+  double rr = R[0], ur = R[1], pr = R[2], gr = R[3], pir = R[4];
+  double cl = sqrt(gl * (pl + pil) / rl), cr = sqrt(gr * (pr + pir) / rr);
+  double pscale = dmin(pl + pil, pr + pir);
+  double pfloor = -dmin(pil, pir) + 1e-12 * pscale;
+  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  if (p < pfloor) p = pfloor;
+  int it = 0, conv = 0, done = 0;
+  double fl, dfl, fr, dfr;
+  while (it < 50) {
+    it++;
+    side_f(p, rl, pl, gl, pil, cl, &fl, &dfl);
+    side_f(p, rr, pr, gr, pir, cr, &fr, &dfr);
+    double F = fl + fr + (ur - ul);
+    double pn = p - F / (dfl + dfr);
+    if (pn < pfloor) pn = pfloor;
+    double dp = fabs(pn - p);
+    p = pn;
+    if (conv) {
+      done = 1;
+      break;
+    }
+    if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
+  }
+  side_f(p, rl, pl, gl, pil, cl, &fl, &dfl);
+  side_f(p, rr, pr, gr, pir, cr, &fr, &dfr);
+  double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  double rsl = star_density(p, rl, pl, gl, pil);
+  double rsr = star_density(p, rr, pr, gr, pir);
+  out[0] = p;
+  out[1] = us;
+  out[2] = rsl;
+  out[3] = rsr;
+  out[4] = sqrt(gl * (p + pil) / rsl);
+  out[5] = sqrt(gr * (p + pir) / rsr);
+  out[6] = (double)it;
+  return (done || conv) ? 0 : ORC_ERR_NOCONV;
+}
+
+/* X for every cut cell (|S| > 0): fluid N receives momentum -p_I S and
+ * energy -p_I u_I |S|, fluid P the opposite; no mass crosses. */
+static void interface(orc_ctx *o, const double *p) {
+  for (int m = 0; m < 3; m++) memset(o->xn[m], 0, sizeof(double) * o->NP);
+  for (int m = 0; m < 2; m++) memset(o->ul[m], 0, sizeof(double) * o->NP);
+  double fac = 1.0 / o->c.dx + (o->c.dim == 2 ? 1.0 / o->c.dy : 0.0);
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      double Sx = o->sx[c], Sy = o->sy[c];
+      if (Sx == 0.0 && Sy == 0.0) continue;
+      double Sm = sqrt(Sx * Sx + Sy * Sy);
+      double nxv, nyv;
+      normal(o, p, i, j, &nxv, &nyv);
+      if (nxv == 0.0 && nyv == 0.0) {
+        nxv = Sx / Sm;
+        nyv = Sy / Sm;
+      }
+      double L[5] = {o->w[0][0][c], o->w[0][1][c] * nxv + o->w[0][2][c] * nyv,
+                     o->w[0][3][c], o->c.gamma[0], o->c.pinf[0]};
+      double R[5] = {o->w[1][0][c], o->w[1][1][c] * nxv + o->w[1][2][c] * nyv,
+                     o->w[1][3][c], o->c.gamma[1], o->c.pinf[1]};
+      double out[7];
+      if (orc_riemann(L, R, out)) o->err |= ORC_ERR_NOCONV;
+      double ps = out[0], us = out[1];
+      o->xn[0][c] = -ps * Sx;
+      o->xn[1][c] = -ps * Sy;
+      o->xn[2][c] = -ps * us * Sm;
+      o->ul[0][c] = us * nxv;
+      o->ul[1][c] = us * nyv;
+      o->smax[0] = dmax(o->smax[0], (fabs(us) + out[4]) * fac);
+      o->smax[1] = dmax(o->smax[1], (fabs(us) + out[5]) * fac);
+    }
+}
+
+/* level-set velocity: cut-cell values u_I n carried outward through the
+ * band by the same upwind Jacobi sweeps, upwind meaning toward the
+ * interface on either side */
+static void extend_ls_velocity(orc_ctx *o, const double *p) {
+  double bw = o->c.band * o->h;
+  for (int it = 0; it < o->c.ext_iters; it++) {
+    for (int m = 0; m < 2; m++) memcpy(o->old[m], o->ul[m], sizeof(double) * o->NP);
+    for (int j = 0; j < o->c.ny; j++)
+      for (int i = 0; i < o->c.nx; i++) {
+        int c = ID(o, i, j);
+        if (!(fabs(p[c]) < bw)) continue;
+        if (o->sx[c] != 0.0 || o->sy[c] != 0.0) continue;
+        double nxv, nyv;
+        normal(o, p, i, j, &nxv, &nyv);
+        if (p[c] >= 0.0) {
+          nxv = -nxv;
+          nyv = -nyv;
+        }
+        int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+        double wx = fabs(nxv) / o->c.dx;
+        double wy = o->c.dim == 2 ? fabs(nyv) / o->c.dy : 0.0;
+        if (!inside(o, i + sx, j)) wx = 0.0;
+        if (!inside(o, i, j + sy)) wy = 0.0;
+        double den = wx + wy;
+        if (!(den > 0.0)) continue;
+        for (int m = 0; m < 2; m++) {
+          double num = 0.0;
+          if (wx > 0.0) num += wx * o->old[m][ID(o, i + sx, j)];
+          if (wy > 0.0) num += wy * o->old[m][ID(o, i, j + sy)];
+          o->ul[m][c] = num / den;
+        }
+      }
+  }
+}
+
+/* interaction step for the stage states qs and level set p */
+static void eval(orc_ctx *o, double *const qs[2][4], double *p) {
+  geometry(o, p);
+  for (int k = 0; k < 2; k++) {
+    prim(o, k, qs[k]);
+    extend(o, k, p);
+    wave_maxima(o, k, p);
+  }
+  interface(o, p);
+  extend_ls_velocity(o, p);
+}
+
+/* ------------------------------------------------------------------ */
+/* WENO5-LF fluxes and the cut-cell right-hand side (Eq. 2)            */
+
+double orc_weno5(const double *v, double eps) {
+  double v1 = v[0], v2 = v[1], v3 = v[2], v4 = v[3], v5 = v[4];
+  double q0 = (2.0 * v1 - 7.0 * v2 + 11.0 * v3) / 6.0;
+  double q1 = (-v2 + 5.0 * v3 + 2.0 * v4) / 6.0;
+  double q2 = (2.0 * v3 + 5.0 * v4 - v5) / 6.0;
+  double b0 = 13.0 / 12.0 * sq(v1 - 2.0 * v2 + v3) + 0.25 * sq(v1 - 4.0 * v2 + 3.0 * v3);
+  double b1 = 13.0 / 12.0 * sq(v2 - 2.0 * v3 + v4) + 0.25 * sq(v2 - v4);
+  double b2 = 13.0 / 12.0 * sq(v3 - 2.0 * v4 + v5) + 0.25 * sq(3.0 * v3 - 4.0 * v4 + v5);
+  double a0 = 0.1 / sq(eps + b0);
+  double a1 = 0.6 / sq(eps + b1);
+  double a2 = 0.3 / sq(eps + b2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+/* Lax-Friedrichs split fluxes of the stencil state of fluid k at cell c in
+ * direction d (0 = x, 1 = y): fp = (F + a U)/2, fm = (F - a U)/2 */
+static void split(const orc_ctx *o, int k, int c, int d, double a, double *fp,
+                  double *fm) {
+  double g = o->c.gamma[k], pi = o->c.pinf[k];
+  double rho = o->w[k][0][c], u = o->w[k][1][c], v = o->w[k][2][c];
+  double p = o->w[k][3][c];
+  double E = (p + g * pi) / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+  double U[4] = {rho, rho * u, rho * v, E};
+  double F[4];
+  if (d == 0) {
+    F[0] = rho * u;
+    F[1] = rho * u * u + p;
+    F[2] = rho * u * v;
+    F[3] = u * (E + p);
+  } else {
+    F[0] = rho * v;
+    F[1] = rho * u * v;
+    F[2] = rho * v * v + p;
+    F[3] = v * (E + p);
+  }
+  for (int m = 0; m < 4; m++) {
+    fp[m] = 0.5 * (F[m] + a * U[m]);
+    fm[m] = 0.5 * (F[m] - a * U[m]);
+  }
+}
+
+/* numerical flux through the face between cells c - s and c, where s is
+ * the index stride of direction d */
+static void face_flux(const orc_ctx *o, int k, int c, int s, int d, double *Fh) {
+  double a = o->lf[k][d];
+  double fp[6][4], fm[6][4];
+  for (int r = 0; r < 6; r++) split(o, k, c + (r - 3) * s, d, a, fp[r], fm[r]);
+  for (int m = 0; m < 4; m++) {
+    double vp[5] = {fp[0][m], fp[1][m], fp[2][m], fp[3][m], fp[4][m]};
+    double vm[5] = {fm[5][m], fm[4][m], fm[3][m], fm[2][m], fm[1][m]};
+    Fh[m] = orc_weno5(vp, o->c.weno_eps) + orc_weno5(vm, o->c.weno_eps);
+  }
+}
+
+static void fv_rhs(orc_ctx *o, int k, double *const L[4]) {
+  int nx = o->c.nx, ny = o->c.ny;
+  fill_ghost(o, o->w[k][0], 0);
+  fill_ghost(o, o->w[k][1], 1);
+  fill_ghost(o, o->w[k][2], 2);
+  fill_ghost(o, o->w[k][3], 0);
+  for (int m = 0; m < 4; m++) {
+    memset(o->fx[m], 0, sizeof(double) * o->NP);
+    memset(o->fy[m], 0, sizeof(double) * o->NP);
+  }
+  double Fh[4];
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i <= nx; i++) {
+      int c = ID(o, i, j);
+      double A = k == 1 ? o->ax[c] : 1.0 - o->ax[c];
+      if (A == 0.0) continue;
+      face_flux(o, k, c, 1, 0, Fh);
+      for (int m = 0; m < 4; m++) o->fx[m][c] = A * Fh[m];
+    }
+  if (o->c.dim == 2)
+    for (int j = 0; j <= ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int c = ID(o, i, j);
+        double A = k == 1 ? o->ay[c] : 1.0 - o->ay[c];
+        if (A == 0.0) continue;
+        face_flux(o, k, c, o->PX, 1, Fh);
+        for (int m = 0; m < 4; m++) o->fy[m][c] = A * Fh[m];
+      }
+  double sgn = k == 0 ? 1.0 : -1.0, dxdy = o->c.dx * o->c.dy;
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      int c = ID(o, i, j);
+      for (int m = 0; m < 4; m++) {
+        double r = (o->fx[m][c] - o->fx[m][ID(o, i + 1, j)]) / o->c.dx;
+        if (o->c.dim == 2) r += (o->fy[m][c] - o->fy[m][ID(o, i, j + 1)]) / o->c.dy;
+        if (m > 0) r += sgn * o->xn[m - 1][c] / dxdy;
+        L[m][c] = r;
+      }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* level set: advection (Eq. 6) and reinitialisation                   */
+
+static void make_band(orc_ctx *o, const double *p) {
+  double bw = o->c.band * o->h;
+  memset(o->band, 0, o->NP);
+  memset(o->rext, 0, o->NP);
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++)
+      o->band[ID(o, i, j)] = fabs(p[ID(o, i, j)]) < bw;
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j), r = o->band[c];
+      if (i > 0) r |= o->band[ID(o, i - 1, j)];
+      if (i < o->c.nx - 1) r |= o->band[ID(o, i + 1, j)];
+      if (o->c.dim == 2) {
+        if (j > 0) r |= o->band[ID(o, i, j - 1)];
+        if (j < o->c.ny - 1) r |= o->band[ID(o, i, j + 1)];
+      }
+      o->rext[c] = (unsigned char)r;
+    }
+}
+
+/* upwind HJ-WENO5 derivative along stride s: backward-biased if up > 0 */
+static double hj_deriv(const orc_ctx *o, const double *p, int c, int s, double h,
+                       int backward) {
+  double v[5];
+  if (backward) {
+    for (int r = 0; r < 5; r++) {
+      int m = c + (r - 2) * s;
+      v[r] = (p[m] - p[m - s]) / h;
+    }
+  } else {
+    for (int r = 0; r < 5; r++) {
+      int m = c + (2 - r) * s;
+      v[r] = (p[m + s] - p[m]) / h;
+    }
+  }
+  return orc_weno5(v, o->c.weno_eps);
+}
+
+static void ls_rhs(orc_ctx *o, double *p, double *L) {
+  fill_ghost(o, p, 0);
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      if (!o->band[c]) {
+        L[c] = 0.0;
+        continue;
+      }
+      double u = o->ul[0][c], v = o->ul[1][c];
+      double px = 0.0, py = 0.0;
+      if (u != 0.0) px = hj_deriv(o, p, c, 1, o->c.dx, u > 0.0);
+      if (o->c.dim == 2 && v != 0.0) py = hj_deriv(o, p, c, o->PX, o->c.dy, v > 0.0);
+      L[c] = -(u * px + v * py);
+    }
+}
+
+static double grad_est(const double *p, int c, int s, double h) {
+  double dm = fabs(p[c] - p[c - s]), dp = fabs(p[c + s] - p[c]);
+  double dc = 0.5 * fabs(p[c + s] - p[c - s]);
+  return dmax(dmax(dc, dp), dm) / h;
+}
+
+/* sweeps of phi_tau + S(phi0)(|grad phi| - 1) = 0 (Godunov upwind with
+ * WENO5 one-sided derivatives) with the subcell fix in cells where phi0
+ * changes sign across a face, over the band and its face neighbours;
+ * cells farther out keep their last values */
+static void reinit(orc_ctx *o, double *p) {
+  int nx = o->c.nx, ny = o->c.ny, d2 = o->c.dim == 2;
+  double h = o->h;
+  fill_ghost(o, p, 0);
+  memcpy(o->p0, p, sizeof(double) * o->NP);
+  for (int it = 0; it < o->c.reinit_iters; it++) {
+    fill_ghost(o, p, 0);
+    memcpy(o->old[0], p, sizeof(double) * o->NP);
+    const double *q = o->old[0], *z = o->p0;
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int c = ID(o, i, j);
+        if (!o->rext[c]) continue;
+        double s0 = z[c];
+        int pos = s0 >= 0.0;
+        int cut = (z[c - 1] >= 0.0) != pos || (z[c + 1] >= 0.0) != pos;
+        if (d2) cut = cut || (z[c - o->PX] >= 0.0) != pos || (z[c + o->PX] >= 0.0) != pos;
+        if (cut) {
+          /* subcell distance from phi0 and its central-difference gradient
+           * (one-sided maxima where the central difference vanishes) */
+          double gx = (z[c + 1] - z[c - 1]) / (2.0 * o->c.dx);
+          double gy = d2 ? (z[c + o->PX] - z[c - o->PX]) / (2.0 * o->c.dy) : 0.0;
+          double gm = sqrt(gx * gx + gy * gy);
+          if (!(gm > 1e-8)) {
+            gx = grad_est(z, c, 1, o->c.dx);
+            gy = d2 ? grad_est(z, c, o->PX, o->c.dy) : 0.0;
+            gm = sqrt(gx * gx + gy * gy);
+          }
+          /* the interface lies no farther than the linear crossing toward
+           * any face neighbour of opposite sign */
+          double dmin = INFINITY;
+          const int nbs[4] = {-1, 1, -o->PX, o->PX};
+          for (int e = 0; e < (d2 ? 4 : 2); e++) {
+            double zn = z[c + nbs[e]];
+            if ((zn >= 0.0) == pos) continue;
+            double hh = e < 2 ? o->c.dx : o->c.dy;
+            double dd = fabs(s0) / (fabs(s0) + fabs(zn)) * hh;
+            if (dd < dmin) dmin = dd;
+          }
+          double D = fabs(s0) / gm;
+          if (D > dmin) D = dmin;
+          D = pos ? D : -D;
+          double sg = pos ? 1.0 : -1.0;
+          p[c] = q[c] - 0.5 * (sg * fabs(q[c]) - D);
+        } else {
+          double S = s0 / sqrt(s0 * s0 + h * h);
+          /* one-sided HJ-WENO5 derivatives in the Godunov Hamiltonian */
+          double a = hj_deriv(o, q, c, 1, o->c.dx, 1), b = hj_deriv(o, q, c, 1, o->c.dx, 0);
+          double cc = 0.0, d = 0.0;
+          if (d2) {
+            cc = hj_deriv(o, q, c, o->PX, o->c.dy, 1);
+            d = hj_deriv(o, q, c, o->PX, o->c.dy, 0);
+          }
+          double G;
+          if (s0 > 0.0)
+            G = dmax(sq(dmax(a, 0.0)), sq(dmin(b, 0.0))) +
+                dmax(sq(dmax(cc, 0.0)), sq(dmin(d, 0.0)));
+          else if (s0 < 0.0)
+            G = dmax(sq(dmin(a, 0.0)), sq(dmax(b, 0.0))) +
+                dmax(sq(dmin(cc, 0.0)), sq(dmax(d, 0.0)));
+          else
+            continue;
+          p[c] = q[c] - 0.5 * h * S * (sqrt(G) - 1.0);
+        }
+      }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* time integration                                                    */
+
+static const double RK2A[3] = {0.0, 0.0, 0.5}, RK2B[3] = {0.0, 1.0, 0.5};
+static const double RK3A[4] = {0.0, 0.0, 0.75, 1.0 / 3.0};
+static const double RK3B[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
+
+/* dst = cur + dt L (stage 1), else dst = a base + b (cur + dt L) */
+static void rk_plane(orc_ctx *o, int s, double *dst, const double *base,
+                     const double *cur, const double *L, double dt,
+                     const unsigned char *mask) {
+  double a = o->c.rk_order == 3 ? RK3A[s] : RK2A[s];
+  double b = o->c.rk_order == 3 ? RK3B[s] : RK2B[s];
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      if (mask && !mask[c]) continue;
+      if (s == 1)
+        dst[c] = cur[c] + dt * L[c];
+      else
+        dst[c] = a * base[c] + b * (cur[c] + dt * L[c]);
+    }
+}
+
+static double dt_of(const orc_ctx *o, int k) {
+  return o->smax[k] > 0.0 ? o->c.cfl / o->smax[k] : INFINITY;
+}
+
+static void copy_planes(orc_ctx *o, double *const dst[4], double *const src[4], int n) {
+  for (int m = 0; m < n; m++) memcpy(dst[m], src[m], sizeof(double) * o->NP);
+}
+
+/* one RK step of both fluids and the level set with a common dt, the
+ * first interaction step having been evaluated already */
+static void single_step_after_eval(orc_ctx *o, double dt) {
+  int S = o->c.rk_order;
+  for (int k = 0; k < 2; k++) copy_planes(o, o->q0[k], o->q[k], 4);
+  memcpy(o->phi0, o->phi, sizeof(double) * o->NP);
+  make_band(o, o->phi0);
+  for (int s = 1; s <= S; s++) {
+    if (s > 1) eval(o, o->q, o->phi);
+    for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
+    ls_rhs(o, o->phi, o->lphi);
+    for (int k = 0; k < 2; k++)
+      for (int m = 0; m < 4; m++)
+        rk_plane(o, s, o->q[k][m], o->q0[k][m], o->q[k][m], o->L[k][m], dt, NULL);
+    rk_plane(o, s, o->phi, o->phi0, o->phi, o->lphi, dt, o->band);
+    if (s == S) reinit(o, o->phi);
+    geometry(o, o->phi);
+    mix(o, 0, o->q[0]);
+    mix(o, 1, o->q[1]);
+  }
+  o->t += dt;
+}
+
+int orc_step_single_dt(orc_ctx *o, int nsteps, double t_end, orc_info *info) {
+  for (int n = 0; n < nsteps; n++) {
+    if (t_end > 0.0 && o->t >= t_end) break;
+    eval(o, o->q, o->phi);
+    double dt = dmin(dt_of(o, 0), dt_of(o, 1));
+    if (t_end > 0.0 && o->t + dt > t_end) dt = t_end - o->t;
+    single_step_after_eval(o, dt);
+    if (info) {
+      info->t = o->t;
+      info->dt1 = dt;
+      info->dt2 = dt;
+      info->n_raw = 1.0;
+      info->n_used = 1.0;
+      info->role_fluid1 = -1;
+      info->substeps = 1;
+    }
+  }
+  if (info) info->err = o->err;
+  return o->err;
+}
+
+/* Eq. 8 (shared evaluation) or Eq. 9 (fluid-2-only evaluation): update of
+ * the correction quantities with the exchange flux as applied to fluid 1 */
+static void record(orc_ctx *o, int f1, int shared, double dt1, double dt2) {
+  double sgn = f1 == 0 ? 1.0 : -1.0;
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      for (int m = 0; m < 3; m++) {
+        double x1 = sgn * o->xn[m][c];
+        if (shared) o->xc[m][c] = o->xc[m][c] + (-0.5 * x1) * dt1;
+        o->xc[m][c] = o->xc[m][c] + (0.5 * x1) * dt2;
+      }
+    }
+}
+
+/* Eq. 7: fluid-1 state at fluid-2 time t2 inside the cycle */
+static void interpolate(orc_ctx *o, double th) {
+  for (int m = 0; m < 4; m++)
+    for (int j = 0; j < o->c.ny; j++)
+      for (int i = 0; i < o->c.nx; i++) {
+        int c = ID(o, i, j);
+        o->qi[m][c] = (1.0 - th) * o->prev[m][c] + th * o->fut[m][c];
+      }
+}
+
+/* one cycle of the accelerated method (Sec. 3.1, steps 1-5) */
+static void cycle(orc_ctx *o, double t_end, orc_info *info) {
+  eval(o, o->q, o->phi);
+  double dtk[2] = {dt_of(o, 0), dt_of(o, 1)};
+  for (int k = 0; k < 2; k++)
+    if (t_end > 0.0 && o->t + dtk[k] > t_end) dtk[k] = t_end - o->t;
+  int f1 = dtk[1] > dtk[0] ? 1 : 0, f2 = 1 - f1;
+  double dt1 = dtk[f1], dt2 = dtk[f2];
+  double nraw = dt1 / dt2;
+  if (info) {
+    info->n_raw = nraw;
+    info->role_fluid1 = f1;
+    info->dt2 = dt2;
+  }
+  if (o->c.force_ratio_one) {
+    dt1 = dt2;
+  } else {
+    if (isfinite(dt1)) {
+      double fl = floor(nraw);
+      if (nraw - fl < o->c.ratio_threshold) dt1 = fl * dt2;
+    }
+    if (!isfinite(dt1) || dt1 <= dt2) {
+      single_step_after_eval(o, dt2);
+      if (info) {
+        info->dt1 = dt2;
+        info->n_used = 1.0;
+        info->substeps = 1;
+        info->t = o->t;
+      }
+      return;
+    }
+  }
+  if (info) {
+    info->dt1 = dt1;
+    info->n_used = dt1 / dt2;
+  }
+  for (int m = 0; m < 3; m++) memset(o->xc[m], 0, sizeof(double) * o->NP);
+  /* step 2: fluid-1 first RK stage with dt1; keep previous and future */
+  fv_rhs(o, f1, o->L[f1]);
+  copy_planes(o, o->prev, o->q[f1], 4);
+  for (int m = 0; m < 4; m++)
+    rk_plane(o, 1, o->fut[m], o->prev[m], o->prev[m], o->L[f1][m], dt1, NULL);
+  double t2 = 0.0;
+  int sub = 0;
+  double *qs[2][4];
+  for (;;) {
+    sub++;
+    if (sub > 1) {
+      interpolate(o, t2 / dt1);
+      geometry(o, o->phi);
+      mix(o, f1, o->qi);
+      for (int m = 0; m < 4; m++) {
+        qs[f1][m] = o->qi[m];
+        qs[f2][m] = o->q[f2][m];
+      }
+      eval(o, qs, o->phi);
+      dt2 = dt_of(o, f2);
+    }
+    int last = (dt1 - t2) <= dt2 * (1.0 + 1e-12);
+    if (last) dt2 = dt1 - t2;
+    record(o, f1, sub == 1, dt1, dt2);
+    /* step 3: fluid-2 and level-set first RK stage with dt2 */
+    copy_planes(o, o->q0[f2], o->q[f2], 4);
+    memcpy(o->phi0, o->phi, sizeof(double) * o->NP);
+    make_band(o, o->phi0);
+    fv_rhs(o, f2, o->L[f2]);
+    ls_rhs(o, o->phi, o->lphi);
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 1, o->q[f2][m], o->q0[f2][m], o->q[f2][m], o->L[f2][m], dt2, NULL);
+    rk_plane(o, 1, o->phi, o->phi0, o->phi, o->lphi, dt2, o->band);
+    geometry(o, o->phi);
+    mix(o, f2, o->q[f2]);
+    if (last) {
+      mix(o, f1, o->fut);
+      for (int m = 0; m < 4; m++) qs[f1][m] = o->fut[m];
+    } else {
+      interpolate(o, (t2 + dt2) / dt1);
+      mix(o, f1, o->qi);
+      for (int m = 0; m < 4; m++) qs[f1][m] = o->qi[m];
+    }
+    for (int m = 0; m < 4; m++) qs[f2][m] = o->q[f2][m];
+    eval(o, qs, o->phi);
+    record(o, f1, last, dt1, dt2);
+    /* step 4 (and 5 on the last sub-step): second RK stage */
+    fv_rhs(o, f2, o->L[f2]);
+    ls_rhs(o, o->phi, o->lphi);
+    if (last) fv_rhs(o, f1, o->L[f1]);
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 2, o->q[f2][m], o->q0[f2][m], o->q[f2][m], o->L[f2][m], dt2, NULL);
+    rk_plane(o, 2, o->phi, o->phi0, o->phi, o->lphi, dt2, o->band);
+    if (last)
+      for (int m = 0; m < 4; m++)
+        rk_plane(o, 2, o->q[f1][m], o->prev[m], o->fut[m], o->L[f1][m], dt1, NULL);
+    reinit(o, o->phi);
+    if (last) {
+      if (o->c.flux_correction) {
+        double dxdy = o->c.dx * o->c.dy;
+        for (int j = 0; j < o->c.ny; j++)
+          for (int i = 0; i < o->c.nx; i++) {
+            int c = ID(o, i, j);
+            for (int m = 0; m < 3; m++) o->q[f1][m + 1][c] += o->xc[m][c] / dxdy;
+          }
+      }
+      geometry(o, o->phi);
+      mix(o, f1, o->q[f1]);
+      mix(o, f2, o->q[f2]);
+      break;
+    }
+    t2 += dt2;
+    geometry(o, o->phi);
+    mix(o, f2, o->q[f2]);
+  }
+  o->t += dt1;
+  if (info) {
+    info->substeps = sub;
+    info->t = o->t;
+  }
+}
+
+int orc_step_multi_dt(orc_ctx *o, int ncycles, double t_end, orc_info *info) {
+  if (o->c.rk_order != 2) {
+    o->err |= ORC_ERR_INVAL;
+    if (info) info->err = o->err;
+    return o->err;
+  }
+  for (int n = 0; n < ncycles; n++) {
+    if (t_end > 0.0 && o->t >= t_end) break;
+    cycle(o, t_end, info);
+  }
+  if (info) info->err = o->err;
+  return o->err;
+}
+
+/* ------------------------------------------------------------------ */
+/* context                                                             */
+
+static double *plane(orc_ctx *o) { return (double *)calloc((size_t)o->NP, sizeof(double)); }
+
+orc_ctx *orc_create(const orc_config *cfg) {
+  if (cfg->nx < GH || (cfg->dim == 2 && cfg->ny < GH) || (cfg->dim == 1 && cfg->ny != 1))
+    return NULL;
+  if (cfg->rk_order != 2 && cfg->rk_order != 3) return NULL;
+  orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  o->c = *cfg;
+  if (o->c.dim == 1) o->c.bc[2] = o->c.bc[3] = ORC_BC_ZEROGRAD;
+  o->PX = cfg->nx + 2 * GH;
+  o->PY = cfg->ny + 2 * GH;
+  o->NP = o->PX * o->PY;
+  o->h = cfg->dim == 2 ? dmin(cfg->dx, cfg->dy) : cfg->dx;
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      o->q[k][m] = plane(o);
+      o->w[k][m] = plane(o);
+      o->q0[k][m] = plane(o);
+      o->L[k][m] = plane(o);
+    }
+  for (int m = 0; m < 4; m++) {
+    o->old[m] = plane(o);
+    o->fx[m] = plane(o);
+    o->fy[m] = plane(o);
+    o->prev[m] = plane(o);
+    o->fut[m] = plane(o);
+    o->qi[m] = plane(o);
+  }
+  for (int m = 0; m < 3; m++) {
+    o->xn[m] = plane(o);
+    o->xc[m] = plane(o);
+  }
+  o->ul[0] = plane(o);
+  o->ul[1] = plane(o);
+  o->phi = plane(o);
+  o->alpha = plane(o);
+  o->ax = plane(o);
+  o->ay = plane(o);
+  o->sx = plane(o);
+  o->sy = plane(o);
+  o->phi0 = plane(o);
+  o->lphi = plane(o);
+  o->p0 = plane(o);
+  o->band = (unsigned char *)calloc((size_t)o->NP, 1);
+  o->rext = (unsigned char *)calloc((size_t)o->NP, 1);
+  return o;
+}
+
+void orc_destroy(orc_ctx *o) {
+  if (!o) return;
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      free(o->q[k][m]);
+      free(o->w[k][m]);
+      free(o->q0[k][m]);
+      free(o->L[k][m]);
+    }
+  for (int m = 0; m < 4; m++) {
+    free(o->old[m]);
+    free(o->fx[m]);
+    free(o->fy[m]);
+    free(o->prev[m]);
+    free(o->fut[m]);
+    free(o->qi[m]);
+  }
+  for (int m = 0; m < 3; m++) {
+    free(o->xn[m]);
+    free(o->xc[m]);
+  }
+  free(o->ul[0]);
+  free(o->ul[1]);
+  free(o->phi);
+  free(o->alpha);
+  free(o->ax);
+  free(o->ay);
+  free(o->sx);
+  free(o->sy);
+  free(o->phi0);
+  free(o->lphi);
+  free(o->p0);
+  free(o->band);
+  free(o->rext);
+  free(o);
+}
+
+int orc_init(orc_ctx *o, const double *phi, const double *pN, const double *pP) {
+  int nx = o->c.nx, ny = o->c.ny, n = nx * ny;
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) o->phi[ID(o, i, j)] = phi[i + j * nx];
+  geometry(o, o->phi);
+  for (int k = 0; k < 2; k++) {
+    const double *pr = k == 0 ? pN : pP;
+    double g = o->c.gamma[k], pi = o->c.pinf[k];
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int c = ID(o, i, j), s = i + j * nx;
+        double rho = pr[s], u = pr[n + s], v = pr[2 * n + s], p = pr[3 * n + s];
+        o->w[k][0][c] = rho;
+        o->w[k][1][c] = u;
+        o->w[k][2][c] = v;
+        o->w[k][3][c] = p;
+        double E = (p + g * pi) / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+        double a = vol(o, k, c);
+        o->q[k][0][c] = a * rho;
+        o->q[k][1][c] = a * (rho * u);
+        o->q[k][2][c] = a * (rho * v);
+        o->q[k][3][c] = a * E;
+      }
+  }
+  mix(o, 0, o->q[0]);
+  mix(o, 1, o->q[1]);
+  o->t = 0.0;
+  o->err = 0;
+  return 0;
+}
+
+static void copy_out(const orc_ctx *o, const double *src, double *dst) {
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) dst[i + j * o->c.nx] = src[ID(o, i, j)];
+}
+
+static void copy_in(orc_ctx *o, const double *src, double *dst) {
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) dst[ID(o, i, j)] = src[i + j * o->c.nx];
+}
+
+int orc_get_state(const orc_ctx *o, double *qN, double *qP, double *phi) {
+  int n = o->c.nx * o->c.ny;
+  for (int m = 0; m < 4; m++) {
+    if (qN) copy_out(o, o->q[0][m], qN + m * n);
+    if (qP) copy_out(o, o->q[1][m], qP + m * n);
+  }
+  if (phi) copy_out(o, o->phi, phi);
+  return 0;
+}
+
+int orc_set_state(orc_ctx *o, const double *qN, const double *qP, const double *phi) {
+  int n = o->c.nx * o->c.ny;
+  for (int m = 0; m < 4; m++) {
+    if (qN) copy_in(o, qN + m * n, o->q[0][m]);
+    if (qP) copy_in(o, qP + m * n, o->q[1][m]);
+  }
+  if (phi) copy_in(o, phi, o->phi);
+  geometry(o, o->phi);
+  return 0;
+}
+
+int orc_integrals(const orc_ctx *o, double *out) {
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      double s = 0.0;
+      for (int j = 0; j < o->c.ny; j++)
+        for (int i = 0; i < o->c.nx; i++) s += o->q[k][m][ID(o, i, j)];
+      out[k * 4 + m] = s * (o->c.dx * o->c.dy);
+    }
+  return 0;
+}
+
+double orc_time(const orc_ctx *o) { return o->t; }
+int orc_status(const orc_ctx *o) { return o->err; }
+
+int orc_geometry(orc_ctx *o, double *alpha, double *ax, double *ay, double *sx,
+                 double *sy) {
+  int nx = o->c.nx, ny = o->c.ny;
+  geometry(o, o->phi);
+  if (alpha) copy_out(o, o->alpha, alpha);
+  if (sx) copy_out(o, o->sx, sx);
+  if (sy) copy_out(o, o->sy, sy);
+  if (ax)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i <= nx; i++) ax[i + j * (nx + 1)] = o->ax[ID(o, i, j)];
+  if (ay)
+    for (int j = 0; j <= ny; j++)
+      for (int i = 0; i < nx; i++) ay[i + j * nx] = o->ay[ID(o, i, j)];
+  return 0;
+}
+
+int orc_rhs(orc_ctx *o, int k, double *out) {
+  int n = o->c.nx * o->c.ny;
+  eval(o, o->q, o->phi);
+  fv_rhs(o, k, o->L[k]);
+  for (int m = 0; m < 4; m++) copy_out(o, o->L[k][m], out + m * n);
+  return o->err;
+}
+
+int orc_stencil_states(orc_ctx *o, int k, double *out) {
+  int n = o->c.nx * o->c.ny;
+  eval(o, o->q, o->phi);
+  for (int m = 0; m < 4; m++) copy_out(o, o->w[k][m], out + m * n);
+  return o->err;
+}
+
+int orc_reinit_only(orc_ctx *o) {
+  make_band(o, o->phi);
+  reinit(o, o->phi);
+  return 0;
+}
+
+int orc_mix_only(orc_ctx *o, int k) {
+  geometry(o, o->phi);
+  mix(o, k, o->q[k]);
+  return 0;
+}

@@ -1,0 +1,99 @@
+/*
+ * sif_oracle.h -- serial FP64 CPU oracle of the conservative sharp-interface
+ * method with multi-time-step sub-cycling (Long, Cai & Pan, arXiv 1905.03917).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+ * CPU-baseline leg of bench.py may load this library.  It shares no code,
+ * header, table or helper with the CUDA library: every formula here is
+ * written out plainly, loop by loop, in the order the paper states it.
+ *
+ * Parity status per function is listed in the header comment of
+ * sif_oracle.c.
+ */
+#ifndef SIF_ORACLE_H
+#define SIF_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Boundary kinds for the four domain sides (-x, +x, -y, +y). */
+#define ORC_BC_REFLECT 0
+#define ORC_BC_ZEROGRAD 1
+#define ORC_BC_PERIODIC 2
+
+/* Sticky error bits reported by orc_status(). */
+#define ORC_ERR_NONPHYS 1  /* rho <= 0 or p + p_inf <= 0 in a real cell */
+#define ORC_ERR_NOCONV 2   /* interface Riemann Newton did not converge */
+#define ORC_ERR_INVAL 4    /* unsupported configuration */
+
+typedef struct {
+  int dim;            /* 1 or 2; dim 1 requires ny == 1 */
+  int nx, ny;
+  double x0, y0, dx, dy;
+  int bc[4];          /* ORC_BC_* for -x, +x, -y, +y */
+  double gamma[2];    /* stiffened gas: [0] fluid N (phi < 0), [1] fluid P */
+  double pinf[2];
+  double cfl;         /* 0.6 */
+  int rk_order;       /* 2 (paper) or 3 (single-dt only) */
+  double weno_eps;    /* 1e-6 */
+  double mix_alpha;   /* small-cell threshold, 0.5 */
+  double ratio_threshold; /* n truncation threshold, 0.7 */
+  int ext_iters;      /* extension Jacobi sweeps, 10 */
+  int reinit_iters;   /* reinitialisation sweeps per level-set step, 2 */
+  double band;        /* narrow band half-width in cells, 6 */
+  int flux_correction;   /* 1 = interfacial flux correction on */
+  int force_ratio_one;   /* test only: multi-dt cycle with dt1 = dt2 */
+} orc_config;
+
+typedef struct {
+  double t, dt1, dt2, n_raw, n_used;
+  int role_fluid1; /* index (0 = N, 1 = P) of the fluid with the larger step */
+  int substeps;    /* fluid-2 sub-steps taken in the last cycle */
+  int err;
+} orc_info;
+
+typedef struct orc_ctx orc_ctx;
+
+orc_ctx *orc_create(const orc_config *cfg);
+void orc_destroy(orc_ctx *o);
+/* phi: nx*ny; prim_N / prim_P: 4 planes (rho, u, v, p) of nx*ny, x fastest. */
+int orc_init(orc_ctx *o, const double *phi, const double *prim_N, const double *prim_P);
+int orc_step_single_dt(orc_ctx *o, int nsteps, double t_end, orc_info *info);
+int orc_step_multi_dt(orc_ctx *o, int ncycles, double t_end, orc_info *info);
+/* q_N / q_P: 4 planes of (alpha U) per fluid; phi: nx*ny. Any may be NULL. */
+int orc_get_state(const orc_ctx *o, double *q_N, double *q_P, double *phi);
+int orc_set_state(orc_ctx *o, const double *q_N, const double *q_P, const double *phi);
+/* out[k*4+m] = sum over cells of (alpha U)_k,m dx dy. */
+int orc_integrals(const orc_ctx *o, double *out);
+double orc_time(const orc_ctx *o);
+int orc_status(const orc_ctx *o);
+
+/* Geometry of the current level set: alpha_P, x-face and y-face P-apertures
+ * (left/bottom face of each cell, nx+1 by ny and nx by ny+1 arrays), and
+ * the interface vector S (N to P) per cell. Any output may be NULL. */
+int orc_geometry(orc_ctx *o, double *alpha, double *ax, double *ay,
+                 double *sx, double *sy);
+/* Right-hand side L_k of the cut-cell update (Eq. 2) for fluid k at the
+ * current state, after the interaction step; out is 4 planes of nx*ny. */
+int orc_rhs(orc_ctx *o, int k, double *out);
+/* One reinitialisation pass (reinit_iters sweeps) on the current phi. */
+int orc_reinit_only(orc_ctx *o);
+/* Small-cell mixing of fluid k on the current state (in place). */
+int orc_mix_only(orc_ctx *o, int k);
+/* Extension: stencil states W_k (4 primitive planes) after extension. */
+int orc_stencil_states(orc_ctx *o, int k, double *out);
+
+/* Pointwise pieces for unit pins. */
+double orc_weno5(const double *v, double eps);
+double orc_edge_fraction(double a, double b);
+double orc_cell_alpha(double c00, double c10, double c11, double c01);
+/* Exact two-material stiffened-gas Riemann problem.
+ * L/R: rho, u, p, gamma, pinf. out: p*, u*, rho*_L, rho*_R, c*_L, c*_R,
+ * iterations. Returns 0, or ORC_ERR_NOCONV. */
+int orc_riemann(const double *L, const double *R, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,202 @@
+"""Seeded synthetic two-fluid initial conditions.
+
+Shared by the CUDA path's tests/bench and by the oracle's tests: it holds
+no arithmetic of the method itself, only initial data (level set, and the
+primitive fields rho, u, v, p of each fluid over the whole grid).  Fluid N
+occupies phi < 0, fluid P occupies phi >= 0.
+
+Every case is a dict ``{"name", "cfg", "phi", "prim_N", "prim_P"}`` with
+``phi`` of shape (ny, nx) and ``prim_*`` of shape (4, ny, nx), x fastest.
+The workloads are the paper's class of problems (Sec. 4.1-4.2: gas-water
+shock tubes and bubbles) with stiffened-gas materials.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+WATER = {"gamma": 4.4, "pinf": 6.0e8}
+AIR = {"gamma": 1.4, "pinf": 0.0}
+HELIUM = {"gamma": 1.67, "pinf": 0.0}
+
+
+def config(nx, ny, dx, dy, matN, matP, bc, dim=2, x0=0.0, y0=0.0, **kw):
+    cfg = {"dim": dim, "nx": nx, "ny": ny, "x0": x0, "y0": y0, "dx": dx, "dy": dy,
+           "bc": list(bc), "gamma": [matN["gamma"], matP["gamma"]],
+           "pinf": [matN["pinf"], matP["pinf"]], "cfl": 0.6, "rk_order": 2,
+           "weno_eps": 1e-6, "mix_alpha": 0.5, "ratio_threshold": 0.7,
+           "ext_iters": 10, "reinit_iters": 2, "band": 6.0,
+           "flux_correction": 1, "force_ratio_one": 0}
+    cfg.update(kw)
+    return cfg
+
+
+def _centres(cfg):
+    x = cfg["x0"] + (np.arange(cfg["nx"]) + 0.5) * cfg["dx"]
+    y = cfg["y0"] + (np.arange(cfg["ny"]) + 0.5) * cfg["dy"]
+    return np.meshgrid(x, y)  # (ny, nx) each
+
+
+def _uniform(shape, rho, u, v, p):
+    out = np.empty((4,) + shape)
+    out[0], out[1], out[2], out[3] = rho, u, v, p
+    return out
+
+
+def _smooth_noise(rng, X, Y, amp, modes=3):
+    """Sum of a few random-phase sine modes, relative amplitude amp."""
+    if amp == 0.0:
+        return np.zeros_like(X)
+    Lx = X.max() - X.min() + 1e-300
+    Ly = Y.max() - Y.min() + 1e-300
+    f = np.zeros_like(X)
+    for _ in range(modes):
+        kx, ky = rng.integers(1, 4, size=2)
+        ph = rng.uniform(0, 2 * np.pi, size=2)
+        f += np.sin(2 * np.pi * kx * X / Lx + ph[0]) * np.cos(2 * np.pi * ky * Y / Ly + ph[1])
+    return amp * f / modes
+
+
+def normal_shock(gamma, rho1, p1, mach):
+    """Post-shock state behind a normal shock of Mach `mach` running into
+    gas at rest (rho1, p1): returns (rho2, u2, p2, shock speed)."""
+    g, M2 = gamma, mach * mach
+    c1 = math.sqrt(g * p1 / rho1)
+    p2 = p1 * (1.0 + 2.0 * g / (g + 1.0) * (M2 - 1.0))
+    rho2 = rho1 * (g + 1.0) * M2 / ((g - 1.0) * M2 + 2.0)
+    s = mach * c1
+    u2 = s * (1.0 - rho1 / rho2)
+    return rho2, u2, p2, s
+
+
+def shock_tube_1d(n=400, rk_order=3, interface=0.5):
+    """Water (left, p = 1e9 Pa) against air (right, p = 1e5 Pa) on [0, 1] m."""
+    dx = 1.0 / n
+    cfg = config(n, 1, dx, dx, WATER, AIR, ["zerograd"] * 4, dim=1, rk_order=rk_order)
+    x = (np.arange(n) + 0.5) * dx
+    phi = (x - interface)[None, :]
+    pN = _uniform((1, n), 1000.0, 0.0, 0.0, 1.0e9)
+    pP = _uniform((1, n), 1.0, 0.0, 0.0, 1.0e5)
+    return {"name": f"shock_tube_1d_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def shock_bubble(nx=1024, ny=256, seed=None, perturb=0.0):
+    """Air-helium shock-bubble interaction, nondimensional: [0,4]x[0,1],
+    helium bubble R = 0.2 at (1, 0.5), Mach 1.22 shock at x = 0.7 moving +x.
+    Zero-gradient left/right, reflective top/bottom."""
+    dx, dy = 4.0 / nx, 1.0 / ny
+    cfg = config(nx, ny, dx, dy, HELIUM, AIR,
+                 ["zerograd", "zerograd", "reflect", "reflect"])
+    X, Y = _centres(cfg)
+    rng = np.random.default_rng(seed)
+    cx, cy, R = 1.0, 0.5, 0.2
+    if seed is not None:
+        cx += rng.uniform(-2, 2) * dx
+        cy += rng.uniform(-2, 2) * dy
+        R += rng.uniform(-2, 2) * min(dx, dy)
+    phi = np.sqrt((X - cx) ** 2 + (Y - cy) ** 2) - R
+    pN = _uniform(X.shape, 0.138, 0.0, 0.0, 1.0)
+    rho2, u2, p2, _ = normal_shock(1.4, 1.0, 1.0, 1.22)
+    post = X < 0.7
+    pP = _uniform(X.shape, 1.0, 0.0, 0.0, 1.0)
+    pP[0][post], pP[1][post], pP[3][post] = rho2, u2, p2
+    if perturb:
+        for arr in (pN, pP):
+            arr[0] *= 1.0 + _smooth_noise(rng, X, Y, perturb)
+            arr[3] *= 1.0 + _smooth_noise(rng, X, Y, perturb)
+    return {"name": f"shock_bubble_{nx}x{ny}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def underwater_explosion(n=2048, seed=None, perturb=0.0, half=1.0, radius=0.12,
+                         centre=(0.0, 0.0), p_gas=8.29e8, rho_gas=1270.0):
+    """Gas bubble (gamma 1.4, rho 1270, p 8.29e8 Pa) of radius 0.12 m in
+    water (p 1e5 Pa) on [-1,1]^2 m, reflective walls."""
+    d = 2.0 * half / n
+    cfg = config(n, n, d, d, AIR, WATER, ["reflect"] * 4, x0=-half, y0=-half)
+    X, Y = _centres(cfg)
+    rng = np.random.default_rng(seed)
+    cx, cy, R = centre[0], centre[1], radius
+    if seed is not None:
+        cx += rng.uniform(-2, 2) * d
+        cy += rng.uniform(-2, 2) * d
+        R += rng.uniform(-2, 2) * d
+    phi = np.sqrt((X - cx) ** 2 + (Y - cy) ** 2) - R
+    pN = _uniform(X.shape, rho_gas, 0.0, 0.0, p_gas)
+    pP = _uniform(X.shape, 1000.0, 0.0, 0.0, 1.0e5)
+    if perturb:
+        for arr in (pN, pP):
+            arr[0] *= 1.0 + _smooth_noise(rng, X, Y, perturb)
+            arr[3] *= 1.0 + _smooth_noise(rng, X, Y, perturb)
+    return {"name": f"underwater_explosion_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def periodic_bubble(n=64, seed=0, ratio=100.0, perturb=1e-2, velocity=5.0):
+    """All-periodic unit box, gas bubble in water with smooth random
+    perturbations of density, pressure and velocity (conservation tests)."""
+    d = 1.0 / n
+    cfg = config(n, n, d, d, AIR, WATER, ["periodic"] * 4)
+    X, Y = _centres(cfg)
+    rng = np.random.default_rng(seed)
+    cx, cy = 0.5 + rng.uniform(-2, 2) * d, 0.5 + rng.uniform(-2, 2) * d
+    R = 0.2 + rng.uniform(-2, 2) * d
+    phi = np.sqrt((X - cx) ** 2 + (Y - cy) ** 2) - R
+    pN = _uniform(X.shape, 1.0, 0.0, 0.0, ratio * 1e5)
+    pP = _uniform(X.shape, 1000.0, 0.0, 0.0, 1e5)
+    for arr in (pN, pP):
+        arr[0] *= 1.0 + _smooth_noise(rng, X, Y, perturb)
+        arr[3] *= 1.0 + _smooth_noise(rng, X, Y, perturb)
+        arr[1] = velocity * _smooth_noise(rng, X, Y, 1.0)
+        arr[2] = velocity * _smooth_noise(rng, X, Y, 1.0)
+    return {"name": f"periodic_bubble_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def static_interface(nx=32, ny=32, angle=0.0, offset=0.013, p=1.0e5):
+    """Planar interface between water-like and gas-like stiffened gases at
+    rest with uniform pressure; reflective box of unit size."""
+    dx, dy = 1.0 / nx, 1.0 / ny
+    matN = {"gamma": 1.4, "pinf": 0.0}
+    matP = {"gamma": 4.4, "pinf": 6.0e8}
+    cfg = config(nx, ny, dx, dy, matN, matP, ["reflect"] * 4)
+    X, Y = _centres(cfg)
+    nvec = (math.cos(angle), math.sin(angle))
+    phi = (X - 0.5) * nvec[0] + (Y - 0.5) * nvec[1] - offset
+    pN = _uniform(X.shape, 1.2, 0.0, 0.0, p)
+    pP = _uniform(X.shape, 1000.0, 0.0, 0.0, p)
+    return {"name": "static_interface", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def single_fluid(nx=32, ny=32, seed=0, amp=0.1):
+    """Whole domain filled by fluid P (phi > 0 everywhere): periodic smooth
+    flow for the single-fluid reduction of the cut-cell update."""
+    dx, dy = 1.0 / nx, 1.0 / ny
+    cfg = config(nx, ny, dx, dy, AIR, AIR, ["periodic"] * 4)
+    X, Y = _centres(cfg)
+    rng = np.random.default_rng(seed)
+    phi = np.ones_like(X)
+    pP = _uniform(X.shape, 1.0, 0.5, -0.25, 1.0)
+    pP[0] *= 1.0 + _smooth_noise(rng, X, Y, amp)
+    pP[3] *= 1.0 + _smooth_noise(rng, X, Y, amp)
+    pN = pP.copy()
+    return {"name": "single_fluid", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def batched_instances(count=256, seed=0, nmin=64, nmax=512):
+    """Independent gas-water bubble instances of uneven sizes: N uniform in
+    [nmin, nmax], bubble radius U[0.05, 0.3] (at least four cells from the
+    walls), bubble/water pressure ratio log-uniform in [10, 1e4], gas
+    density 1, on [-1,1]^2 with reflective walls."""
+    out = []
+    for s in range(count):
+        rng = np.random.default_rng([seed, s])
+        n = int(rng.integers(nmin, nmax + 1))
+        R = float(rng.uniform(0.05, 0.3))
+        ratio = float(10.0 ** rng.uniform(1.0, 4.0))
+        d = 2.0 / n
+        lim = 1.0 - R - 4.0 * d
+        cx, cy = (float(v) for v in rng.uniform(-lim, lim, size=2))
+        case = underwater_explosion(n=n, radius=R, centre=(cx, cy),
+                                    p_gas=ratio * 1.0e5, rho_gas=1.0)
+        case["name"] = f"instance_{s}_{n}"
+        out.append(case)
+    return out

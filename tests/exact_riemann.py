@@ -1,0 +1,83 @@
+"""Independent exact solution of the two-material stiffened-gas Riemann
+problem, used to pin the oracle (tests only).
+
+It is derived differently from the oracle's solver: the shock branch uses
+the Rankine-Hugoniot mass flux m^2 = (p - p_K)/(1/rho_K - 1/rho*) with the
+Hugoniot density of a stiffened gas, the rarefaction branch integrates
+dp/(rho c) along the isentrope numerically, and the star pressure is
+bracketed with Brent's method instead of Newton's.
+"""
+from __future__ import annotations
+
+import math
+
+from scipy.integrate import quad
+from scipy.optimize import brentq
+
+
+def hugoniot_density(p, rho, pk, g, pi):
+    r = (p + pi) / (pk + pi)
+    return rho * ((g + 1.0) * r + (g - 1.0)) / ((g - 1.0) * r + (g + 1.0))
+
+
+def velocity_jump(p, rho, pk, g, pi):
+    """u-change across the wave of side K (positive when p > p_K)."""
+    if p > pk:
+        rs = hugoniot_density(p, rho, pk, g, pi)
+        m = math.sqrt((p - pk) / (1.0 / rho - 1.0 / rs))
+        return (p - pk) / m
+
+    def integrand(s):
+        rs = rho * ((s + pi) / (pk + pi)) ** (1.0 / g)
+        cs = math.sqrt(g * (s + pi) / rs)
+        return 1.0 / (rs * cs)
+
+    val, _ = quad(integrand, p, pk, epsabs=0.0, epsrel=1e-13, limit=200)
+    return -val
+
+
+def star_state(L, R):
+    """L, R = (rho, u, p, gamma, pinf); returns p*, u*."""
+    rl, ul, pl, gl, pil = L
+    rr, ur, pr, gr, pir = R
+
+    def F(p):
+        return velocity_jump(p, rl, pl, gl, pil) + velocity_jump(p, rr, pr, gr, pir) + (ur - ul)
+
+    lo = -min(pil, pir) + 1e-9 * min(pl + pil, pr + pir)
+    hi = max(pl, pr) * 10.0 + 1.0
+    while F(hi) < 0.0:
+        hi *= 10.0
+    p = brentq(F, lo, hi, xtol=1e-300, rtol=1e-15, maxiter=500)
+    us = 0.5 * (ul + ur) + 0.5 * (velocity_jump(p, rr, pr, gr, pir) - velocity_jump(p, rl, pl, gl, pil))
+    return p, us
+
+
+def sample_left_rarefaction_right_shock(L, R, x0, t, x):
+    """Density at positions x (iterable) for a left rarefaction / right
+    shock wave pattern; returns (rho(x) list, p*, u*, contact position)."""
+    rl, ul, pl, gl, pil = L
+    rr, ur, pr, gr, pir = R
+    ps, us = star_state(L, R)
+    assert ps < pl and ps > pr, "wave pattern is not rarefaction | shock"
+    cl = math.sqrt(gl * (pl + pil) / rl)
+    rsl = rl * ((ps + pil) / (pl + pil)) ** (1.0 / gl)
+    csl = math.sqrt(gl * (ps + pil) / rsl)
+    rsr = hugoniot_density(ps, rr, pr, gr, pir)
+    S = (rsr * us - rr * ur) / (rsr - rr)
+    head, tail = ul - cl, us - csl
+    out = []
+    for xi in x:
+        s = (xi - x0) / t
+        if s <= head:
+            out.append(rl)
+        elif s <= tail:
+            c = 2.0 / (gl + 1.0) * (cl + 0.5 * (gl - 1.0) * (ul - s))
+            out.append(rl * (c / cl) ** (2.0 / (gl - 1.0)))
+        elif s <= us:
+            out.append(rsl)
+        elif s <= S:
+            out.append(rsr)
+        else:
+            out.append(rr)
+    return out, ps, us, x0 + us * t
