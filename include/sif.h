@@ -1,0 +1,141 @@
+/*
+ * sif.h -- C-ABI of libsif: GB300-native (sm_103a, FP64) conservative
+ * sharp-interface solver for compressible two-fluid flow with
+ * multi-time-step sub-cycling, after Long, Cai & Pan, "An accelerated
+ * sharp-interface method for multiphase flows simulations" (arXiv
+ * 1905.03917).
+ *
+ * Two stiffened-gas fluids share a uniform Cartesian grid: fluid N fills
+ * phi < 0, fluid P fills phi >= 0 (phi the level set of Sec. 2.3).  Each
+ * fluid k carries its conservative cut-cell variables (alpha U)_k of
+ * Eq. 2 -- mass, x-momentum, y-momentum, total energy -- and is advanced
+ * by the cut-cell finite-volume update of Eq. 2 with WENO5 Lax-Friedrichs
+ * face fluxes weighted by face apertures, plus the interface exchange flux
+ * X from an exact two-material Riemann problem (Sec. 2.1).
+ *
+ * Conventions for every entry point:
+ *  - return 0 on success or a negative SIF_E* code; no exception crosses
+ *    the ABI; sif_last_error() gives a one-line reason;
+ *  - host/device arrays are caller-owned, borrowed for the duration of the
+ *    call only, and always copied; mem_kind tells which memory a pointer
+ *    refers to (SIF_HOST or SIF_DEVICE, the latter on the context's device);
+ *  - grid arrays are x-fastest (index i + j*nx); "planes" are stacked
+ *    component after component (component m at offset m*nx*ny);
+ *  - all device work is issued on the context's stream; calls that return
+ *    results to the host (integrals, get_state with SIF_HOST, step calls
+ *    that fill a sif_cycle_info) synchronise that stream;
+ *  - non-physical states (rho <= 0 or p + p_inf <= 0 in a cell that holds
+ *    the fluid) are never clipped: the step reports SIF_ENONPHYS.
+ */
+#ifndef SIF_H
+#define SIF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIF_OK 0
+#define SIF_EINVAL -1    /* bad argument or configuration */
+#define SIF_ECUDA -2     /* a CUDA call failed (no device, out of memory, ...) */
+#define SIF_ENONPHYS -3  /* rho <= 0 or p + p_inf <= 0 in a real cell */
+#define SIF_ENOCONV -4   /* interface Riemann Newton iteration did not converge */
+#define SIF_ETIMEOUT -5  /* a bounded device wait gave up */
+#define SIF_ESTATE -6    /* call out of order (e.g. step before init) */
+
+#define SIF_HOST 0
+#define SIF_DEVICE 1
+
+#define SIF_BC_REFLECT 0   /* slip wall: normal velocity odd, rest even */
+#define SIF_BC_ZEROGRAD 1  /* zero-gradient outflow */
+#define SIF_BC_PERIODIC 2  /* periodic (both sides of the axis) */
+
+typedef struct sif_ctx sif_ctx;
+
+/* Configuration (all lengths in the units of the initial data). */
+typedef struct {
+  int dim;               /* 1 or 2 (dim 1 requires ny == 1) */
+  int nx, ny;            /* cells; nx >= 3 and, in 2D, ny >= 3 */
+  double x0, y0;         /* lower-left corner of the domain */
+  double dx, dy;         /* cell sizes */
+  int bc[4];             /* SIF_BC_* for the -x, +x, -y, +y sides */
+  double gamma[2];       /* stiffened gas p = (gamma-1) rho e - gamma p_inf; [0] = N, [1] = P */
+  double pinf[2];
+  double cfl;            /* CFL number, 0.6 in the paper (Sec. 4) */
+  int rk_order;          /* 2 = TVD-RK2 (the paper, Sec. 3); 3 = SSP-RK3 (single-dt only) */
+  double weno_eps;       /* WENO5 epsilon, 1e-6 */
+  double mix_alpha;      /* small-cell mixing threshold, 0.5 */
+  double ratio_threshold;/* time-step-ratio truncation threshold, 0.7 (Sec. 3.1) */
+  int ext_iters;         /* extension Jacobi sweeps per interaction step, 10 */
+  int reinit_iters;      /* reinitialisation sweeps per level-set step, 2 */
+  double band;           /* narrow-band half-width in cells, 6 */
+  int flux_correction;   /* 1 = interfacial flux correction on (Eq. 8-9); 0 for tests */
+  int force_ratio_one;   /* test switch: run the multi-dt cycle with dt1 = dt2 */
+  void *cuda_stream;     /* cudaStream_t to issue work on; NULL = the legacy default stream */
+  int device;            /* CUDA device ordinal */
+} sif_config;
+
+/* Per-cycle record of the multi-time-step schedule (Sec. 3.1). */
+typedef struct {
+  double t;          /* time after the call */
+  double dt1, dt2;   /* step of fluid 1 (larger) and first step of fluid 2 */
+  double n_raw;      /* dt1/dt2 before truncation */
+  double n_used;     /* ratio after the 0.7 truncation (1 = single step) */
+  int role_fluid1;   /* 0 = N, 1 = P, -1 for single-dt steps */
+  int substeps;      /* fluid-2 sub-steps in the last cycle */
+  long long cell_updates; /* (cell, fluid) RK stage updates done by the call */
+} sif_cycle_info;
+
+/* Create a context on cfg->device; allocates all device memory it needs.
+ * Errors: SIF_EINVAL for a bad configuration, SIF_ECUDA on allocation
+ * failure (nothing is leaked; *out is set to NULL). */
+int sif_create(const sif_config *cfg, sif_ctx **out);
+
+/* Initial data (Sec. 2.3, Eq. 2): level set phi (nx*ny, a signed distance)
+ * and the primitive fields of both fluids over the whole grid, prim_k =
+ * 4 planes (rho, u, v, p).  Computes the geometry, sets (alpha U)_k =
+ * alpha_k U(prim_k), mixes small cells and resets t = 0. */
+int sif_init_fluids(sif_ctx *ctx, const double *phi, const double *prim_N,
+                    const double *prim_P, int mem_kind);
+
+/* nsteps steps of the original single-time-step method (Sec. 3.1, "the
+ * original method"): both fluids and the level set advance with the
+ * smaller CFL step; t_end > 0 caps the final time.  info (nullable) gets
+ * the last step's record and the call's cell-update count. */
+int sif_step_single_dt(sif_ctx *ctx, int nsteps, double t_end, sif_cycle_info *info);
+
+/* ncycles cycles of the accelerated method (Sec. 3.1 steps 1-5): the fluid
+ * with the larger CFL step (fluid 1) takes one RK2 step of dt1 while the
+ * other sub-cycles against Eq. 7 interpolated states, with the Eq. 8-9
+ * correction applied to fluid 1 at the end of the cycle.  Requires
+ * rk_order == 2 (SIF_EINVAL otherwise). */
+int sif_step_multi_dt(sif_ctx *ctx, int ncycles, double t_end, sif_cycle_info *info);
+
+/* out[k*4+m] = sum over cells of (alpha U)_{k,m} dx dy (k = N, P; m = mass,
+ * x-mom, y-mom, energy), reduced on the device in a fixed order.  Host
+ * pointer; synchronises. */
+int sif_integrals(sif_ctx *ctx, double *out);
+
+/* Copy out the state: q_N, q_P as 4 planes each, phi as one plane; any
+ * pointer may be NULL. */
+int sif_get_state(sif_ctx *ctx, double *q_N, double *q_P, double *phi, int mem_kind);
+
+/* Replace the state (checkpoint restore); geometry is recomputed, nothing
+ * is mixed.  t is set to the given time. */
+int sif_set_state(sif_ctx *ctx, const double *q_N, const double *q_P,
+                  const double *phi, double t, int mem_kind);
+
+/* Current simulation time. */
+int sif_get_time(sif_ctx *ctx, double *t);
+
+/* One-line description of the last error on this context (never NULL). */
+const char *sif_last_error(const sif_ctx *ctx);
+
+/* Free all device memory of the context. NULL is ignored. */
+void sif_destroy(sif_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

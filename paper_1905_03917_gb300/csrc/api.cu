@@ -1,0 +1,608 @@
+// api.cu -- the C-ABI of libsif (include/sif.h): context and device memory,
+// and the host-side sequencing of the kernels for the original
+// single-time-step method and for one cycle of the accelerated method
+// (Sec. 3.1, steps 1-5).  Every arithmetic step runs in the kernels; the
+// host only orders launches and, once per fluid-2 sub-step, reads back the
+// scheduler's branch decision.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "sif_internal.cuh"
+
+struct sif_ctx {
+  sif_config cfg;
+  Grid g;
+  cudaStream_t st;
+  size_t NP;
+  double *q[2][4], *w[2][4], *phi, *alpha, *ax, *ay, *sx, *sy, *xn[3], *ul[2];
+  double *q0[2][4], *prev[4], *fut[4], *qi[4], *xc[3], *phi0, *phiR;
+  double *tmp;       // band-indexed scratch, 4 planes
+  double *partial;   // integrals: 8*ny partial sums + pointer table
+  double *integ;     // 8 totals
+  int *band_ev, *band_ls, *rext_ls, *cut, *tiles[2];
+  Scalars *sc;       // device
+  Scalars *hsc;      // pinned host mirror
+  double *hbuf;      // pinned 8 doubles
+  void *pool;        // single device allocation
+  int inited;
+  int last_status;
+  char err[256];
+};
+
+static void set_err(sif_ctx *c, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->err, sizeof(c->err), fmt, ap);
+  va_end(ap);
+}
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      set_err(c, "%s: %s", #call, cudaGetErrorString(e_));                    \
+      return SIF_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+static int check_launch(sif_ctx *c, const char *where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_err(c, "%s: %s", where, cudaGetErrorString(e));
+    return SIF_ECUDA;
+  }
+  return SIF_OK;
+}
+
+static int validate(const sif_config *f, char *why, size_t n) {
+  if (f->dim != 1 && f->dim != 2) return snprintf(why, n, "dim must be 1 or 2"), SIF_EINVAL;
+  if (f->nx < 3) return snprintf(why, n, "nx must be >= 3"), SIF_EINVAL;
+  if (f->dim == 1 && f->ny != 1) return snprintf(why, n, "dim 1 requires ny == 1"), SIF_EINVAL;
+  if (f->dim == 2 && f->ny < 3) return snprintf(why, n, "ny must be >= 3"), SIF_EINVAL;
+  if ((long long)(f->nx + 2 * SIF_GH) * (f->ny + 2 * SIF_GH) > (1ll << 31) / 4)
+    return snprintf(why, n, "grid too large for 32-bit cell indices"), SIF_EINVAL;
+  if (!(f->dx > 0.0) || !(f->dy > 0.0)) return snprintf(why, n, "dx, dy must be > 0"), SIF_EINVAL;
+  for (int k = 0; k < 2; k++) {
+    if (!(f->gamma[k] > 1.0)) return snprintf(why, n, "gamma must be > 1"), SIF_EINVAL;
+    if (!(f->pinf[k] >= 0.0)) return snprintf(why, n, "p_inf must be >= 0"), SIF_EINVAL;
+  }
+  for (int s = 0; s < 4; s++)
+    if (f->bc[s] < 0 || f->bc[s] > 2) return snprintf(why, n, "bad boundary kind"), SIF_EINVAL;
+  if ((f->bc[0] == SIF_BC_PERIODIC) != (f->bc[1] == SIF_BC_PERIODIC) ||
+      (f->dim == 2 && (f->bc[2] == SIF_BC_PERIODIC) != (f->bc[3] == SIF_BC_PERIODIC)))
+    return snprintf(why, n, "periodic boundaries must be paired"), SIF_EINVAL;
+  if (!(f->cfl > 0.0) || f->cfl > 1.0) return snprintf(why, n, "cfl must be in (0, 1]"), SIF_EINVAL;
+  if (f->rk_order != 2 && f->rk_order != 3) return snprintf(why, n, "rk_order must be 2 or 3"), SIF_EINVAL;
+  if (!(f->weno_eps > 0.0)) return snprintf(why, n, "weno_eps must be > 0"), SIF_EINVAL;
+  if (!(f->mix_alpha >= 0.0 && f->mix_alpha <= 1.0)) return snprintf(why, n, "mix_alpha in [0,1]"), SIF_EINVAL;
+  if (!(f->ratio_threshold >= 0.0 && f->ratio_threshold <= 1.0))
+    return snprintf(why, n, "ratio_threshold in [0,1]"), SIF_EINVAL;
+  if (f->ext_iters < 1 || f->ext_iters > 1000) return snprintf(why, n, "ext_iters in [1,1000]"), SIF_EINVAL;
+  if (f->reinit_iters < 0 || f->reinit_iters > 1000) return snprintf(why, n, "reinit_iters in [0,1000]"), SIF_EINVAL;
+  if (!(f->band >= 3.0)) return snprintf(why, n, "band must be >= 3 cells"), SIF_EINVAL;
+  return SIF_OK;
+}
+
+extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
+  if (!out) return SIF_EINVAL;
+  *out = nullptr;
+  if (!cfg) return SIF_EINVAL;
+  sif_ctx *c = new (std::nothrow) sif_ctx();
+  if (!c) return SIF_ECUDA;
+  c->cfg = *cfg;
+  char why[200];
+  int rc = validate(cfg, why, sizeof(why));
+  if (rc) {
+    // the context is freed; the reason is unavailable to the caller here
+    delete c;
+    return rc;
+  }
+  sif_config &f = c->cfg;
+  if (f.dim == 1) f.bc[2] = f.bc[3] = SIF_BC_ZEROGRAD;
+  if (cudaSetDevice(f.device) != cudaSuccess) {
+    delete c;
+    return SIF_ECUDA;
+  }
+  c->st = (cudaStream_t)f.cuda_stream;
+  Grid &g = c->g;
+  g.dim = f.dim;
+  g.nx = f.nx;
+  g.ny = f.ny;
+  g.PX = ((f.nx + 2 * SIF_GH) + 15) / 16 * 16;
+  g.PY = f.ny + 2 * SIF_GH;
+  g.dx = f.dx;
+  g.dy = f.dy;
+  g.h = f.dim == 2 ? (f.dx < f.dy ? f.dx : f.dy) : f.dx;
+  for (int s = 0; s < 4; s++) g.bc[s] = f.bc[s];
+  for (int k = 0; k < 2; k++) {
+    g.gamma[k] = f.gamma[k];
+    g.pinf[k] = f.pinf[k];
+  }
+  g.cfl = f.cfl;
+  g.weno_eps = f.weno_eps;
+  g.mix_alpha = f.mix_alpha;
+  g.band = f.band;
+  g.ext_iters = f.ext_iters;
+  g.reinit_iters = f.reinit_iters;
+  g.ntx = (f.nx + FV_TX - 1) / FV_TX;
+  g.nty = (f.ny + FV_TY - 1) / FV_TY;
+  c->NP = (size_t)g.PX * g.PY;
+
+  // one pool: 40 planes + band scratch + integrals + lists + scalars
+  const int nplanes = 8 + 8 + 1 + 5 + 3 + 2 + 8 + 4 + 4 + 4 + 3 + 2;
+  size_t ncell = (size_t)f.nx * f.ny;
+  size_t bytes_planes = sizeof(double) * c->NP * nplanes;
+  size_t bytes_tmp = sizeof(double) * 4 * ncell;
+  size_t bytes_part = sizeof(double) * (8 * (size_t)f.ny + 16) + 64;
+  size_t bytes_integ = sizeof(double) * 8;
+  size_t ntiles = (size_t)g.ntx * g.nty;
+  size_t bytes_lists = sizeof(int) * (4 * ncell + 2 * ntiles + 64);
+  size_t total = bytes_planes + bytes_tmp + bytes_part + bytes_integ + bytes_lists +
+                 sizeof(Scalars) + 4096;
+  if (cudaMalloc(&c->pool, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return SIF_ECUDA;
+  }
+  cudaMemset(c->pool, 0, total);
+  char *p = (char *)c->pool;
+  auto take = [&](size_t b) {
+    char *r = p;
+    p += (b + 255) / 256 * 256;
+    return r;
+  };
+  auto plane = [&]() { return (double *)take(sizeof(double) * c->NP); };
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) c->q[k][m] = plane();
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) c->w[k][m] = plane();
+  c->phi = plane();
+  c->alpha = plane();
+  c->ax = plane();
+  c->ay = plane();
+  c->sx = plane();
+  c->sy = plane();
+  for (int m = 0; m < 3; m++) c->xn[m] = plane();
+  for (int m = 0; m < 2; m++) c->ul[m] = plane();
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) c->q0[k][m] = plane();
+  for (int m = 0; m < 4; m++) c->prev[m] = plane();
+  for (int m = 0; m < 4; m++) c->fut[m] = plane();
+  for (int m = 0; m < 4; m++) c->qi[m] = plane();
+  for (int m = 0; m < 3; m++) c->xc[m] = plane();
+  c->phi0 = plane();
+  c->phiR = plane();
+  c->tmp = (double *)take(bytes_tmp);
+  c->partial = (double *)take(bytes_part);
+  c->integ = (double *)take(bytes_integ);
+  c->band_ev = (int *)take(sizeof(int) * ncell);
+  c->band_ls = (int *)take(sizeof(int) * ncell);
+  c->rext_ls = (int *)take(sizeof(int) * ncell);
+  c->cut = (int *)take(sizeof(int) * ncell);
+  c->tiles[0] = (int *)take(sizeof(int) * ntiles);
+  c->tiles[1] = (int *)take(sizeof(int) * ntiles);
+  c->sc = (Scalars *)take(sizeof(Scalars));
+  if (cudaMallocHost(&c->hsc, sizeof(Scalars)) != cudaSuccess ||
+      cudaMallocHost(&c->hbuf, sizeof(double) * 16) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->pool);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    delete c;
+    return SIF_ECUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->pool);
+    cudaFreeHost(c->hsc);
+    cudaFreeHost(c->hbuf);
+    delete c;
+    return SIF_ECUDA;
+  }
+  snprintf(c->err, sizeof(c->err), "ok");
+  *out = c;
+  return SIF_OK;
+}
+
+extern "C" void sif_destroy(sif_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  cudaFree(c->pool);
+  cudaFreeHost(c->hsc);
+  cudaFreeHost(c->hbuf);
+  delete c;
+}
+
+extern "C" const char *sif_last_error(const sif_ctx *c) { return c ? c->err : "null context"; }
+
+// ---------------------------------------------------------------------
+// building blocks, in the order of the CPU reference
+
+static void ghost_phi(sif_ctx *c) {
+  GhostSet gs = {{c->phi}, {0}, 1};
+  launch_fill_ghost(c->g, gs, c->st);
+}
+
+static void ghost_w(sif_ctx *c, int k) {
+  GhostSet gs = {{c->w[k][0], c->w[k][1], c->w[k][2], c->w[k][3]}, {0, 1, 2, 0}, 4};
+  launch_fill_ghost(c->g, gs, c->st);
+}
+
+static int ncell(const sif_ctx *c) { return c->g.nx * c->g.ny; }
+static int ntile(const sif_ctx *c) { return c->g.ntx * c->g.nty; }
+
+// level set changed: ghosts, geometry, cut list, band list, tile lists
+static void geometry(sif_ctx *c) {
+  ghost_phi(c);
+  launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st);
+  launch_band_lists(c->g, c->phi, c->band_ev, nullptr, &c->sc->n_band, c->st);
+  launch_tile_lists(c->g, c->phi, c->tiles[0], c->tiles[1], c->sc, c->st);
+}
+
+static void mix(sif_ctx *c, int k, double *const q[4]) {
+  launch_mix(c->g, k, q, c->alpha, c->phi, c->band_ev, &c->sc->n_band, ncell(c), c->tmp, c->st);
+}
+
+// interaction step for stage states qs of both fluids and the current phi
+static void eval(sif_ctx *c, double *const qs[2][4]) {
+  geometry(c);
+  launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
+  for (int k = 0; k < 2; k++)
+    launch_prim(c->g, k, qs[k], c->w[k], c->alpha, c->tiles[k], ntile(c), c->sc, c->st);
+  for (int k = 0; k < 2; k++)
+    launch_extend(c->g, k, c->w[k], c->alpha, c->phi, c->band_ev, ncell(c), c->tmp, c->sc, c->st);
+  cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
+  cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
+  launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, ncell(c), c->xn[0],
+                   c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
+  launch_ls_extend(c->g, c->ul[0], c->ul[1], c->phi, c->sx, c->sy, c->band_ev, ncell(c), c->tmp,
+                   c->sc, c->st);
+}
+
+static void copy_planes(sif_ctx *c, double *const dst[4], double *const src[4], int n) {
+  for (int m = 0; m < n; m++)
+    cudaMemcpyAsync(dst[m], src[m], sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
+}
+
+static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const base[4],
+               double *const cur[4], const double *dtp) {
+  ghost_w(c, k);
+  launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
+                  c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), dtp, c->sc, c->st);
+}
+
+// start of a level-set RK step: keep phi^n and fix the step's band (and
+// its face-neighbour extension for the reinitialisation) from it
+static void ls_begin(sif_ctx *c) {
+  cudaMemcpyAsync(c->phi0, c->phi, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
+  launch_band_lists(c->g, c->phi, c->band_ls, c->rext_ls, &c->sc->n_band_ls, c->st);
+}
+
+static void ls_stage(sif_ctx *c, int s, const double *dtp) {
+  launch_ls_stage(c->g, s, c->cfg.rk_order, c->phi, c->phi0, c->ul[0], c->ul[1], c->band_ls,
+                  &c->sc->n_band_ls, ncell(c), c->tmp, dtp, c->st);
+}
+
+static void reinit(sif_ctx *c) {
+  launch_reinit(c->g, c->phi, c->phiR, c->rext_ls, &c->sc->n_rext, ncell(c), c->tmp, c->st);
+}
+
+// one RK step of both fluids and the level set, the first interaction
+// step having been evaluated; dtp points to the step size on the device
+static void single_step_after_eval(sif_ctx *c, const double *dtp) {
+  int S = c->cfg.rk_order;
+  for (int k = 0; k < 2; k++) copy_planes(c, c->q0[k], c->q[k], 4);
+  ls_begin(c);
+  for (int s = 1; s <= S; s++) {
+    if (s > 1) eval(c, c->q);
+    for (int k = 0; k < 2; k++) fv(c, k, s, c->q[k], c->q0[k], c->q[k], dtp);
+    ls_stage(c, s, dtp);
+    if (s == S) reinit(c);
+    geometry(c);
+    mix(c, 0, c->q[0]);
+    mix(c, 1, c->q[1]);
+  }
+}
+
+static int finish(sif_ctx *c, sif_cycle_info *info, unsigned long long upd0) {
+  int rc = check_launch(c, "step");
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (info) {
+    info->t = c->hsc->t;
+    info->cell_updates = (long long)(c->hsc->updates - upd0);
+  }
+  if (c->hsc->err & DERR_NONPHYS) {
+    set_err(c, "non-physical state (rho <= 0 or p + p_inf <= 0) in a real cell");
+    return SIF_ENONPHYS;
+  }
+  if (c->hsc->err & DERR_NOCONV) {
+    set_err(c, "interface Riemann Newton iteration did not converge");
+    return SIF_ENOCONV;
+  }
+  return SIF_OK;
+}
+
+static int begin_call(sif_ctx *c, double t_end, unsigned long long *upd0) {
+  if (!c->inited) {
+    set_err(c, "state not initialised");
+    return SIF_ESTATE;
+  }
+  cudaSetDevice(c->cfg.device);
+  CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *upd0 = c->hsc->updates;
+  // reset the error word; set t_end
+  c->hbuf[0] = t_end;
+  CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st));
+  CK(cudaMemcpyAsync(&c->sc->t_end, c->hbuf, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  return SIF_OK;
+}
+
+extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycle_info *info) {
+  if (!c || nsteps < 0) return SIF_EINVAL;
+  unsigned long long upd0;
+  int rc = begin_call(c, t_end, &upd0);
+  if (rc) return rc;
+  for (int n = 0; n < nsteps; n++) {
+    if (t_end > 0.0) {
+      // the host needs the time to stop at t_end
+      CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (c->hsc->t >= t_end) break;
+    }
+    eval(c, c->q);
+    launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
+    single_step_after_eval(c, &c->sc->dt);
+    launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+  }
+  rc = finish(c, info, upd0);
+  if (info) {
+    info->dt1 = info->dt2 = c->hsc->dt;
+    info->n_raw = info->n_used = 1.0;
+    info->role_fluid1 = -1;
+    info->substeps = 1;
+  }
+  return rc;
+}
+
+static int read_scalars(sif_ctx *c) {
+  CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return SIF_OK;
+}
+
+// one cycle of the accelerated method (Sec. 3.1 steps 1-5)
+static int cycle(sif_ctx *c, sif_cycle_info *info) {
+  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  eval(c, c->q);
+  launch_sched(SCHED_CYCLE_BEGIN, c->sc, cfl, thr, c->cfg.force_ratio_one, c->st);
+  int rc = read_scalars(c);
+  if (rc) return rc;
+  if (info) {
+    info->n_raw = c->hsc->n_raw;
+    info->role_fluid1 = c->hsc->f1;
+  }
+  if (c->hsc->mode == 0) {
+    single_step_after_eval(c, &c->sc->dt);
+    launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+    if (info) {
+      info->dt1 = info->dt2 = c->hsc->dt;
+      info->n_used = 1.0;
+      info->substeps = 1;
+    }
+    return SIF_OK;
+  }
+  const int f1 = c->hsc->f1, f2 = 1 - f1;
+  if (info) {
+    info->dt1 = c->hsc->dt1;
+    info->dt2 = c->hsc->dt2;
+    info->n_used = c->hsc->n_used;
+  }
+  for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
+  // step 2: fluid-1 first RK stage with dt1; previous and future states
+  copy_planes(c, c->prev, c->q[f1], 4);
+  fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
+  double *qs[2][4];
+  int sub = 0;
+  for (;;) {
+    sub++;
+    if (sub > 1) {
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+      geometry(c);
+      mix(c, f1, c->qi);
+      for (int m = 0; m < 4; m++) {
+        qs[f1][m] = c->qi[m];
+        qs[f2][m] = c->q[f2][m];
+      }
+      eval(c, qs);
+      launch_sched(SCHED_SUBSTEP, c->sc, cfl, thr, 0, c->st);
+    } else {
+      launch_sched(SCHED_FIRST_SUB, c->sc, cfl, thr, 0, c->st);
+    }
+    rc = read_scalars(c);
+    if (rc) return rc;
+    if (c->hsc->err || !(c->hsc->dt2 > 0.0) || !(c->hsc->dt2 < 1e300)) {
+      // a failed interaction step leaves no usable fluid-2 step: stop here
+      // and let the caller see the device error word
+      if (!c->hsc->err) set_err(c, "fluid-2 time step is not positive and finite");
+      return c->hsc->err ? SIF_OK : SIF_ENONPHYS;
+    }
+    const int last = c->hsc->last;
+    launch_record(c->g, sub == 1, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0],
+                  c->xc[1], c->xc[2], c->sc, c->st);
+    // step 3: fluid-2 and level-set first RK stage with dt2
+    copy_planes(c, c->q0[f2], c->q[f2], 4);
+    ls_begin(c);
+    fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+    ls_stage(c, 1, &c->sc->dt2);
+    geometry(c);
+    mix(c, f2, c->q[f2]);
+    if (last) {
+      mix(c, f1, c->fut);
+      for (int m = 0; m < 4; m++) qs[f1][m] = c->fut[m];
+    } else {
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+      mix(c, f1, c->qi);
+      for (int m = 0; m < 4; m++) qs[f1][m] = c->qi[m];
+    }
+    for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
+    eval(c, qs);
+    launch_record(c->g, last, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0],
+                  c->xc[1], c->xc[2], c->sc, c->st);
+    // step 4 (and 5 on the last sub-step): second RK stage
+    fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+    ls_stage(c, 2, &c->sc->dt2);
+    if (last) fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1);
+    reinit(c);
+    if (last) {
+      if (c->cfg.flux_correction) launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
+      geometry(c);
+      mix(c, f1, c->q[f1]);
+      mix(c, f2, c->q[f2]);
+      break;
+    }
+    launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
+    geometry(c);
+    mix(c, f2, c->q[f2]);
+    if (sub > 100000) {
+      set_err(c, "sub-cycle count exceeded 100000");
+      return SIF_ETIMEOUT;
+    }
+  }
+  launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
+  if (info) info->substeps = sub;
+  return SIF_OK;
+}
+
+extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycle_info *info) {
+  if (!c || ncycles < 0) return SIF_EINVAL;
+  if (c->cfg.rk_order != 2) {
+    set_err(c, "the multi-time-step cycle is defined for rk_order 2");
+    return SIF_EINVAL;
+  }
+  unsigned long long upd0;
+  int rc = begin_call(c, t_end, &upd0);
+  if (rc) return rc;
+  for (int n = 0; n < ncycles; n++) {
+    rc = read_scalars(c);
+    if (rc) return rc;
+    if (t_end > 0.0 && c->hsc->t >= t_end) break;
+    rc = cycle(c, info);
+    if (rc) return rc;
+    if (c->hsc->err) break;
+  }
+  return finish(c, info, upd0);
+}
+
+// ---------------------------------------------------------------------
+// state in and out
+
+static cudaMemcpyKind kind_in(int mem) {
+  return mem == SIF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind kind_out(int mem) {
+  return mem == SIF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+static int put_plane(sif_ctx *c, double *dst, const double *src, int mem) {
+  const Grid &g = c->g;
+  CK(cudaMemcpy2DAsync(dst + gidx(g, 0, 0), sizeof(double) * g.PX, src, sizeof(double) * g.nx,
+                       sizeof(double) * g.nx, g.ny, kind_in(mem), c->st));
+  return SIF_OK;
+}
+
+static int get_plane(sif_ctx *c, double *dst, const double *src, int mem) {
+  const Grid &g = c->g;
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * g.nx, src + gidx(g, 0, 0), sizeof(double) * g.PX,
+                       sizeof(double) * g.nx, g.ny, kind_out(mem), c->st));
+  return SIF_OK;
+}
+
+extern "C" int sif_init_fluids(sif_ctx *c, const double *phi, const double *pN, const double *pP,
+                               int mem) {
+  if (!c || !phi || !pN || !pP || (mem != SIF_HOST && mem != SIF_DEVICE)) return SIF_EINVAL;
+  cudaSetDevice(c->cfg.device);
+  size_t n = (size_t)ncell(c);
+  int rc = put_plane(c, c->phi, phi, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->w[0][m], pN + m * n, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->w[1][m], pP + m * n, mem);
+  if (rc) return rc;
+  geometry(c);
+  launch_init_state(c->g, c->q[0], c->q[1], c->w[0], c->w[1], c->alpha, c->st);
+  mix(c, 0, c->q[0]);
+  mix(c, 1, c->q[1]);
+  CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), c->st));
+  rc = check_launch(c, "init");
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  c->inited = 1;
+  return SIF_OK;
+}
+
+extern "C" int sif_get_state(sif_ctx *c, double *qN, double *qP, double *phi, int mem) {
+  if (!c || (mem != SIF_HOST && mem != SIF_DEVICE)) return SIF_EINVAL;
+  if (!c->inited) {
+    set_err(c, "state not initialised");
+    return SIF_ESTATE;
+  }
+  cudaSetDevice(c->cfg.device);
+  size_t n = (size_t)ncell(c);
+  int rc = SIF_OK;
+  for (int m = 0; m < 4 && !rc; m++) {
+    if (qN) rc = get_plane(c, qN + m * n, c->q[0][m], mem);
+    if (qP && !rc) rc = get_plane(c, qP + m * n, c->q[1][m], mem);
+  }
+  if (phi && !rc) rc = get_plane(c, phi, c->phi, mem);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  return SIF_OK;
+}
+
+extern "C" int sif_set_state(sif_ctx *c, const double *qN, const double *qP, const double *phi,
+                             double t, int mem) {
+  if (!c || !qN || !qP || !phi || (mem != SIF_HOST && mem != SIF_DEVICE)) return SIF_EINVAL;
+  cudaSetDevice(c->cfg.device);
+  size_t n = (size_t)ncell(c);
+  int rc = put_plane(c, c->phi, phi, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->q[0][m], qN + m * n, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->q[1][m], qP + m * n, mem);
+  if (rc) return rc;
+  geometry(c);
+  c->hbuf[0] = t;
+  CK(cudaMemcpyAsync(&c->sc->t, c->hbuf, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  rc = check_launch(c, "set_state");
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  c->inited = 1;
+  return SIF_OK;
+}
+
+extern "C" int sif_integrals(sif_ctx *c, double *out) {
+  if (!c || !out) return SIF_EINVAL;
+  if (!c->inited) {
+    set_err(c, "state not initialised");
+    return SIF_ESTATE;
+  }
+  cudaSetDevice(c->cfg.device);
+  launch_integrals(c->g, c->q[0], c->q[1], c->partial, 0, c->integ, c->st);
+  int rc = check_launch(c, "integrals");
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->hbuf, c->integ, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  memcpy(out, c->hbuf, sizeof(double) * 8);
+  return SIF_OK;
+}
+
+extern "C" int sif_get_time(sif_ctx *c, double *t) {
+  if (!c || !t) return SIF_EINVAL;
+  int rc = read_scalars(c);
+  if (rc) return rc;
+  *t = c->hsc->t;
+  return SIF_OK;
+}

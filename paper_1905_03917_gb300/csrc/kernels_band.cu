@@ -1,0 +1,617 @@
+// kernels_band.cu -- stencil states of each fluid (real cells and the
+// ghost-state extension of Sec. 2.3), the interface interaction (exact
+// two-material Riemann problem giving the exchange flux X of Eq. 2 and the
+// level-set velocity of Eq. 6), level-set advection and reinitialisation,
+// the multi-time-step bookkeeping (Eq. 7 interpolation, Eq. 8-9 correction
+// quantities), conserved totals and the device-side scheduler.
+//
+// Compiled without FMA contraction, like kernels_geom.cu: these kernels
+// follow the CPU reference operation by operation so that threshold and
+// branch decisions agree with it.
+#include "sif_internal.cuh"
+
+static int grid_for(int n, int per = 256, int cap = 4096) {
+  int b = (n + per - 1) / per;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : b;
+}
+
+__device__ inline void block_max2(double a, double b, unsigned long long *pa,
+                                  unsigned long long *pb) {
+  __shared__ double sa[32], sb[32];
+  a = warp_max(a);
+  b = warp_max(b);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    a = warp_max(a);
+    b = warp_max(b);
+    if (lane == 0) {
+      if (pa) atomic_max_pos(pa, a);
+      if (pb) atomic_max_pos(pb, b);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------
+// real-cell stencil states W = prim((alpha U)/alpha) and wave maxima
+
+__global__ void k_prim(Grid g, int k, const double *__restrict__ q0, const double *__restrict__ q1,
+                       const double *__restrict__ q2, const double *__restrict__ q3, double *w0,
+                       double *w1, double *w2, double *w3, const double *__restrict__ alpha,
+                       const int *__restrict__ tiles, const int *ntiles, Scalars *sc) {
+  if ((int)blockIdx.x >= ntiles[k]) return;
+  int tile = tiles[blockIdx.x];
+  int tx = tile % g.ntx, ty = tile / g.ntx;
+  int i = tx * FV_TX + (threadIdx.x % FV_TX), j = ty * FV_TY + threadIdx.x / FV_TX;
+  double lx = 0.0, ly = 0.0, sm = 0.0;
+  if (i < g.nx && j < g.ny) {
+    int c = gidx(g, i, j);
+    double a = vol_k(alpha, k, c);
+    if (a > SIF_ALPHA_REAL) {
+      double gm = g.gamma[k], pi = g.pinf[k];
+      double rho = q0[c] / a;
+      double u = q1[c] / q0[c];
+      double v = q2[c] / q0[c];
+      double E = q3[c] / a;
+      double p = (gm - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - gm * pi;
+      if (!(rho > 0.0) || !(p + pi > 0.0)) atomicOr(&sc->err, DERR_NONPHYS);
+      w0[c] = rho;
+      w1[c] = u;
+      w2[c] = v;
+      w3[c] = p;
+      double cs = sqrt(fmax(gm * (p + pi) / rho, 0.0));
+      lx = fabs(u) + cs;
+      ly = fabs(v) + cs;
+      double s = (fabs(u) + cs) / g.dx;
+      if (g.dim == 2) s += (fabs(v) + cs) / g.dy;
+      sm = s;
+    }
+  }
+  // two reductions share the helper: (lx, ly), then (sm, -)
+  block_max2(lx, ly, &sc->lf[k][0], &sc->lf[k][1]);
+  block_max2(sm, 0.0, &sc->smax[k], nullptr);
+}
+
+void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
+                 const double *alpha, const int *tiles, int tile_cap, Scalars *sc,
+                 cudaStream_t st) {
+  k_prim<<<tile_cap, FV_TX * FV_TY, 0, st>>>(g, k, q[0], q[1], q[2], q[3], w[0], w[1], w[2],
+                                             w[3], alpha, tiles, sc->n_tiles, sc);
+}
+
+// ---------------------------------------------------------------------
+// extension: Jacobi sweeps of the steady upwind discretisation of
+// n_k . grad(W) = 0 into band cells that hold no fluid k
+
+__global__ void k_extend_sweep(Grid g, int k, const double *__restrict__ w0,
+                               const double *__restrict__ w1, const double *__restrict__ w2,
+                               const double *__restrict__ w3, const double *__restrict__ alpha,
+                               const double *__restrict__ phi, const int *__restrict__ band,
+                               const int *nband, double *tmp) {
+  int n = *nband;
+  const double *w[4] = {w0, w1, w2, w3};
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double out[4] = {w0[c], w1[c], w2[c], w3[c]};
+    if (!(vol_k(alpha, k, c) > SIF_ALPHA_REAL)) {
+      double nxv, nyv;
+      unit_normal(g, phi, i, j, nxv, nyv);
+      if (k == 0) {
+        nxv = -nxv;
+        nyv = -nyv;
+      }
+      int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+      double wx = fabs(nxv) / g.dx;
+      double wy = g.dim == 2 ? fabs(nyv) / g.dy : 0.0;
+      if (!inside(g, i + sx, j)) wx = 0.0;
+      if (!inside(g, i, j + sy)) wy = 0.0;
+      double den = wx + wy;
+      if (den > 0.0) {
+        int cx = gidx(g, i + sx, j), cy = gidx(g, i, j + sy);
+        for (int m = 0; m < 4; m++) {
+          double num = 0.0;
+          if (wx > 0.0) num += wx * w[m][cx];
+          if (wy > 0.0) num += wy * w[m][cy];
+          out[m] = num / den;
+        }
+      }
+    }
+    for (int m = 0; m < 4; m++) tmp[(size_t)m * n + idx] = out[m];
+  }
+}
+
+__global__ void k_extend_scatter(Grid g, int k, const int *__restrict__ band, const int *nband,
+                                 const double *tmp, double *w0, double *w1, double *w2,
+                                 double *w3, const double *__restrict__ alpha, int last,
+                                 Scalars *sc) {
+  int n = *nband;
+  double lx = 0.0, ly = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    double r = tmp[idx], u = tmp[(size_t)n + idx], v = tmp[(size_t)2 * n + idx],
+           p = tmp[(size_t)3 * n + idx];
+    w0[c] = r;
+    w1[c] = u;
+    w2[c] = v;
+    w3[c] = p;
+    if (last && !(vol_k(alpha, k, c) > SIF_ALPHA_REAL)) {
+      double cs = sqrt(fmax(g.gamma[k] * (p + g.pinf[k]) / r, 0.0));
+      lx = fmax(lx, fabs(u) + cs);
+      ly = fmax(ly, fabs(v) + cs);
+    }
+  }
+  if (last) block_max2(lx, ly, &sc->lf[k][0], &sc->lf[k][1]);
+}
+
+void launch_extend(const Grid &g, int k, double *const w[4], const double *alpha,
+                   const double *phi, const int *band, int band_cap, double *tmp, Scalars *sc,
+                   cudaStream_t st) {
+  int blocks = grid_for(band_cap, 256, 1216);
+  for (int it = 0; it < g.ext_iters; it++) {
+    k_extend_sweep<<<blocks, 256, 0, st>>>(g, k, w[0], w[1], w[2], w[3], alpha, phi, band,
+                                          &sc->n_band, tmp);
+    k_extend_scatter<<<blocks, 256, 0, st>>>(g, k, band, &sc->n_band, tmp, w[0], w[1], w[2],
+                                            w[3], alpha, it == g.ext_iters - 1, sc);
+  }
+}
+
+// ---------------------------------------------------------------------
+// interface interaction in every cut cell
+
+__global__ void k_interface(Grid g, const double *__restrict__ n0, const double *__restrict__ n1,
+                            const double *__restrict__ n2, const double *__restrict__ n3,
+                            const double *__restrict__ p0, const double *__restrict__ p1,
+                            const double *__restrict__ p2, const double *__restrict__ p3,
+                            const double *__restrict__ phi, const double *__restrict__ sx,
+                            const double *__restrict__ sy, const int *__restrict__ cut,
+                            const int *ncut, double *xn0, double *xn1, double *xn2, double *ul0,
+                            double *ul1, Scalars *sc) {
+  int n = *ncut;
+  double fac = 1.0 / g.dx + (g.dim == 2 ? 1.0 / g.dy : 0.0);
+  double sN = 0.0, sP = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = cut[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double Sx = sx[c], Sy = sy[c];
+    double Sm = sqrt(Sx * Sx + Sy * Sy);
+    double nxv, nyv;
+    unit_normal(g, phi, i, j, nxv, nyv);
+    if (nxv == 0.0 && nyv == 0.0) {
+      nxv = Sx / Sm;
+      nyv = Sy / Sm;
+    }
+    double ps, us, csl, csr;
+    int e = riemann_solve(n0[c], n1[c] * nxv + n2[c] * nyv, n3[c], g.gamma[0], g.pinf[0], p0[c],
+                          p1[c] * nxv + p2[c] * nyv, p3[c], g.gamma[1], g.pinf[1], ps, us, csl,
+                          csr);
+    if (e) atomicOr(&sc->err, e);
+    xn0[c] = -ps * Sx;
+    xn1[c] = -ps * Sy;
+    xn2[c] = -ps * us * Sm;
+    ul0[c] = us * nxv;
+    ul1[c] = us * nyv;
+    sN = fmax(sN, (fabs(us) + csl) * fac);
+    sP = fmax(sP, (fabs(us) + csr) * fac);
+  }
+  block_max2(sN, sP, &sc->smax[0], &sc->smax[1]);
+}
+
+void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
+                      const double *sx, const double *sy, const int *cut, int cut_cap,
+                      double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
+                      Scalars *sc, cudaStream_t st) {
+  int blocks = grid_for(cut_cap, 128, 1216);
+  k_interface<<<blocks, 128, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
+                                      phi, sx, sy, cut, &sc->n_cut, xn0, xn1, xn2, ul0, ul1, sc);
+}
+
+// ---------------------------------------------------------------------
+// level-set velocity carried from the cut cells through the band
+
+__global__ void k_ls_extend_sweep(Grid g, const double *__restrict__ u0,
+                                  const double *__restrict__ u1, const double *__restrict__ phi,
+                                  const double *__restrict__ sx, const double *__restrict__ sy,
+                                  const int *__restrict__ band, const int *nband, double *tmp) {
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double o0 = u0[c], o1 = u1[c];
+    if (sx[c] == 0.0 && sy[c] == 0.0) {
+      double nxv, nyv;
+      unit_normal(g, phi, i, j, nxv, nyv);
+      if (phi[c] >= 0.0) {
+        nxv = -nxv;
+        nyv = -nyv;
+      }
+      int six = nxv >= 0.0 ? 1 : -1, siy = nyv >= 0.0 ? 1 : -1;
+      double wx = fabs(nxv) / g.dx;
+      double wy = g.dim == 2 ? fabs(nyv) / g.dy : 0.0;
+      if (!inside(g, i + six, j)) wx = 0.0;
+      if (!inside(g, i, j + siy)) wy = 0.0;
+      double den = wx + wy;
+      if (den > 0.0) {
+        int cx = gidx(g, i + six, j), cy = gidx(g, i, j + siy);
+        double a0 = 0.0, a1 = 0.0;
+        if (wx > 0.0) {
+          a0 += wx * u0[cx];
+          a1 += wx * u1[cx];
+        }
+        if (wy > 0.0) {
+          a0 += wy * u0[cy];
+          a1 += wy * u1[cy];
+        }
+        o0 = a0 / den;
+        o1 = a1 / den;
+      }
+    }
+    tmp[idx] = o0;
+    tmp[(size_t)n + idx] = o1;
+  }
+}
+
+__global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, const double *tmp,
+                                double *a, double *b) {
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    a[c] = tmp[idx];
+    if (b) b[c] = tmp[(size_t)n + idx];
+  }
+}
+
+void launch_ls_extend(const Grid &g, double *ul0, double *ul1, const double *phi,
+                      const double *sx, const double *sy, const int *band, int band_cap,
+                      double *tmp, Scalars *sc, cudaStream_t st) {
+  int blocks = grid_for(band_cap, 256, 1216);
+  for (int it = 0; it < g.ext_iters; it++) {
+    k_ls_extend_sweep<<<blocks, 256, 0, st>>>(g, ul0, ul1, phi, sx, sy, band, &sc->n_band, tmp);
+    k_band_scatter2<<<blocks, 256, 0, st>>>(band, &sc->n_band, tmp, ul0, ul1);
+  }
+}
+
+// ---------------------------------------------------------------------
+// level-set advection (Eq. 6) with upwind HJ-WENO5, one RK stage
+
+__device__ inline double hj_deriv(const double *p, int c, int s, double h, bool backward,
+                                  double eps) {
+  double v[5];
+  if (backward) {
+#pragma unroll
+    for (int r = 0; r < 5; r++) {
+      int m = c + (r - 2) * s;
+      v[r] = (p[m] - p[m - s]) / h;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 5; r++) {
+      int m = c + (2 - r) * s;
+      v[r] = (p[m + s] - p[m]) / h;
+    }
+  }
+  return weno5_plain(v[0], v[1], v[2], v[3], v[4], eps);
+}
+
+__global__ void k_ls_stage(Grid g, int s, double a, double b, const double *__restrict__ phi,
+                           const double *__restrict__ phi0, const double *__restrict__ u0,
+                           const double *__restrict__ u1, const int *__restrict__ band,
+                           const int *nband, double *tmp, const double *dtp) {
+  int n = *nband;
+  double dt = *dtp;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    double u = u0[c], v = u1[c];
+    double px = 0.0, py = 0.0;
+    if (u != 0.0) px = hj_deriv(phi, c, 1, g.dx, u > 0.0, g.weno_eps);
+    if (g.dim == 2 && v != 0.0) py = hj_deriv(phi, c, g.PX, g.dy, v > 0.0, g.weno_eps);
+    double L = -(u * px + v * py);
+    tmp[idx] = s == 1 ? phi[c] + dt * L : a * phi0[c] + b * (phi[c] + dt * L);
+  }
+}
+
+void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *phi0,
+                     const double *ul0, const double *ul1, const int *band, const int *nband,
+                     int band_cap, double *tmp, const double *dtp, cudaStream_t st) {
+  static const double A2[3] = {0.0, 0.0, 0.5}, B2[3] = {0.0, 1.0, 0.5};
+  static const double A3[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
+  double a = rk == 3 ? A3[s] : A2[s], b = rk == 3 ? B3[s] : B2[s];
+  int blocks = grid_for(band_cap, 256, 1216);
+  GhostSet gs = {{phi}, {0}, 1};
+  launch_fill_ghost(g, gs, st);
+  k_ls_stage<<<blocks, 256, 0, st>>>(g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
+  k_band_scatter2<<<blocks, 256, 0, st>>>(band, nband, tmp, phi, nullptr);
+}
+
+// ---------------------------------------------------------------------
+// reinitialisation sweeps over the band and its face neighbours
+
+__device__ inline double grad_est(const double *p, int c, int s, double h) {
+  double dm = fabs(p[c] - p[c - s]), dp = fabs(p[c + s] - p[c]);
+  double dc = 0.5 * fabs(p[c + s] - p[c - s]);
+  return fmax(fmax(dc, dp), dm) / h;
+}
+
+__global__ void k_reinit(Grid g, const double *__restrict__ q, const double *__restrict__ z,
+                         const int *__restrict__ rext, const int *nrext, double *tmp) {
+  int n = *nrext;
+  bool d2 = g.dim == 2;
+  double h = g.h;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = rext[idx];
+    double s0 = z[c];
+    bool pos = s0 >= 0.0;
+    bool cut = (z[c - 1] >= 0.0) != pos || (z[c + 1] >= 0.0) != pos;
+    if (d2) cut = cut || (z[c - g.PX] >= 0.0) != pos || (z[c + g.PX] >= 0.0) != pos;
+    double out = q[c];
+    if (cut) {
+      double gx = (z[c + 1] - z[c - 1]) / (2.0 * g.dx);
+      double gy = d2 ? (z[c + g.PX] - z[c - g.PX]) / (2.0 * g.dy) : 0.0;
+      double gm = sqrt(gx * gx + gy * gy);
+      if (!(gm > 1e-8)) {
+        gx = grad_est(z, c, 1, g.dx);
+        gy = d2 ? grad_est(z, c, g.PX, g.dy) : 0.0;
+        gm = sqrt(gx * gx + gy * gy);
+      }
+      double dmin = INFINITY;
+      const int nbs[4] = {-1, 1, -g.PX, g.PX};
+      for (int e = 0; e < (d2 ? 4 : 2); e++) {
+        double zn = z[c + nbs[e]];
+        if ((zn >= 0.0) == pos) continue;
+        double hh = e < 2 ? g.dx : g.dy;
+        double dd = fabs(s0) / (fabs(s0) + fabs(zn)) * hh;
+        if (dd < dmin) dmin = dd;
+      }
+      double D = fabs(s0) / gm;
+      if (D > dmin) D = dmin;
+      D = pos ? D : -D;
+      double sg = pos ? 1.0 : -1.0;
+      out = q[c] - 0.5 * (sg * fabs(q[c]) - D);
+    } else {
+      double S = s0 / sqrt(s0 * s0 + h * h);
+      double a = hj_deriv(q, c, 1, g.dx, true, g.weno_eps);
+      double b = hj_deriv(q, c, 1, g.dx, false, g.weno_eps);
+      double cc = 0.0, d = 0.0;
+      if (d2) {
+        cc = hj_deriv(q, c, g.PX, g.dy, true, g.weno_eps);
+        d = hj_deriv(q, c, g.PX, g.dy, false, g.weno_eps);
+      }
+      double G = -1.0;
+      if (s0 > 0.0)
+        G = fmax(sqd(fmax(a, 0.0)), sqd(fmin(b, 0.0))) + fmax(sqd(fmax(cc, 0.0)), sqd(fmin(d, 0.0)));
+      else if (s0 < 0.0)
+        G = fmax(sqd(fmin(a, 0.0)), sqd(fmax(b, 0.0))) + fmax(sqd(fmin(cc, 0.0)), sqd(fmax(d, 0.0)));
+      if (G >= 0.0) out = q[c] - 0.5 * h * S * (sqrt(G) - 1.0);
+    }
+    tmp[idx] = out;
+  }
+}
+
+__global__ void k_copy_plane(const double *src, double *dst, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x)
+    dst[t] = src[t];
+}
+
+void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, const int *nrext,
+                   int rext_cap, double *tmp, cudaStream_t st) {
+  GhostSet gs = {{phi}, {0}, 1};
+  launch_fill_ghost(g, gs, st);
+  cudaMemcpyAsync(phi0, phi, sizeof(double) * (size_t)g.PX * g.PY, cudaMemcpyDeviceToDevice, st);
+  int blocks = grid_for(rext_cap, 256, 1216);
+  for (int it = 0; it < g.reinit_iters; it++) {
+    if (it > 0) launch_fill_ghost(g, gs, st);
+    k_reinit<<<blocks, 256, 0, st>>>(g, phi, phi0, rext, nrext, tmp);
+    k_band_scatter2<<<blocks, 256, 0, st>>>(rext, nrext, tmp, phi, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------
+// Eq. 8 (shared) / Eq. 9 (fluid-2 only) correction quantities, in the
+// frame of fluid 1, accumulated in the cut cells of this interaction
+
+__global__ void k_record(int shared, const int *__restrict__ cut, const int *ncut,
+                         const double *__restrict__ x0, const double *__restrict__ x1,
+                         const double *__restrict__ x2, double *c0, double *c1, double *c2,
+                         const Scalars *sc) {
+  int n = *ncut;
+  double sgn = sc->f1 == 0 ? 1.0 : -1.0;
+  double dt1 = sc->dt1, dt2 = sc->dt2;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = cut[idx];
+    const double *xs[3] = {x0, x1, x2};
+    double *cs[3] = {c0, c1, c2};
+    for (int m = 0; m < 3; m++) {
+      double xv = sgn * xs[m][c];
+      double acc = cs[m][c];
+      if (shared) acc = acc + (-0.5 * xv) * dt1;
+      acc = acc + (0.5 * xv) * dt2;
+      cs[m][c] = acc;
+    }
+  }
+}
+
+void launch_record(const Grid &, int shared, const int *cut, int cut_cap, const double *xn0,
+                   const double *xn1, const double *xn2, double *xc0, double *xc1, double *xc2,
+                   Scalars *sc, cudaStream_t st) {
+  int blocks = grid_for(cut_cap, 128, 1216);
+  k_record<<<blocks, 128, 0, st>>>(shared, cut, &sc->n_cut, xn0, xn1, xn2, xc0, xc1, xc2, sc);
+}
+
+// ---------------------------------------------------------------------
+// Eq. 7: fluid-1 state at the current fluid-2 time
+
+__global__ void k_interp(Grid g, double *i0, double *i1, double *i2, double *i3,
+                         const double *__restrict__ p0, const double *__restrict__ p1,
+                         const double *__restrict__ p2, const double *__restrict__ p3,
+                         const double *__restrict__ f0, const double *__restrict__ f1,
+                         const double *__restrict__ f2, const double *__restrict__ f3,
+                         const double *thp) {
+  double th = *thp;
+  int n = g.nx * g.ny;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int c = gidx(g, t % g.nx, t / g.nx);
+    i0[c] = (1.0 - th) * p0[c] + th * f0[c];
+    i1[c] = (1.0 - th) * p1[c] + th * f1[c];
+    i2[c] = (1.0 - th) * p2[c] + th * f2[c];
+    i3[c] = (1.0 - th) * p3[c] + th * f3[c];
+  }
+}
+
+void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
+                   double *const fut[4], const double *thp, cudaStream_t st) {
+  int n = g.nx * g.ny;
+  k_interp<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g, qi[0], qi[1], qi[2], qi[3], prev[0],
+                                                      prev[1], prev[2], prev[3], fut[0], fut[1],
+                                                      fut[2], fut[3], thp);
+}
+
+// final interfacial flux correction of fluid 1
+
+__global__ void k_correction(Grid g, double *q1, double *q2, double *q3, const double *c0,
+                             const double *c1, const double *c2) {
+  int n = g.nx * g.ny;
+  double dxdy = g.dx * g.dy;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int c = gidx(g, t % g.nx, t / g.nx);
+    q1[c] += c0[c] / dxdy;
+    q2[c] += c1[c] / dxdy;
+    q3[c] += c2[c] / dxdy;
+  }
+}
+
+void launch_correction(const Grid &g, double *const q[4], const double *xc0, const double *xc1,
+                       const double *xc2, cudaStream_t st) {
+  int n = g.nx * g.ny;
+  k_correction<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g, q[1], q[2], q[3], xc0, xc1, xc2);
+}
+
+// ---------------------------------------------------------------------
+// conserved totals: fixed-order per-row partial sums, then a fixed-order
+// sum of the partials (deterministic)
+
+struct Planes8 {
+  const double *p[8];
+};
+
+__global__ void k_integrals_rows(Grid g, Planes8 planes, double *partial) {
+  // blockIdx.y: plane (8), blockIdx.x: group of rows; one warp per row
+  int pl = blockIdx.y;
+  const double *a = planes.p[pl];
+  int rows_per_block = blockDim.x / 32;
+  int j = blockIdx.x * rows_per_block + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (j < g.ny)
+    for (int i = lane; i < g.nx; i += 32) s += a[gidx(g, i, j)];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0 && j < g.ny) partial[(size_t)pl * g.ny + j] = s;
+}
+
+__global__ void k_integrals_final(Grid g, const double *partial, double *out) {
+  int pl = threadIdx.x;
+  if (pl >= 8) return;
+  double s = 0.0;
+  for (int j = 0; j < g.ny; j++) s += partial[(size_t)pl * g.ny + j];
+  out[pl] = s * (g.dx * g.dy);
+}
+
+void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], double *partial,
+                      int, double *out, cudaStream_t st) {
+  Planes8 tab = {{qN[0], qN[1], qN[2], qN[3], qP[0], qP[1], qP[2], qP[3]}};
+  dim3 grid((g.ny + 7) / 8, 8);
+  k_integrals_rows<<<grid, 256, 0, st>>>(g, tab, partial);
+  k_integrals_final<<<1, 32, 0, st>>>(g, partial, out);
+}
+
+// ---------------------------------------------------------------------
+// device-side scheduler of the single- and multi-time-step methods
+
+__global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double sm0 = ull_as_double(sc->smax[0]), sm1 = ull_as_double(sc->smax[1]);
+  double dtk[2] = {sm0 > 0.0 ? cfl / sm0 : INFINITY, sm1 > 0.0 ? cfl / sm1 : INFINITY};
+  switch (op) {
+    case SCHED_RESET_MAX:
+      sc->smax[0] = sc->smax[1] = 0ull;
+      sc->lf[0][0] = sc->lf[0][1] = sc->lf[1][0] = sc->lf[1][1] = 0ull;
+      break;
+    case SCHED_SINGLE_DT: {
+      double dt = fmin(dtk[0], dtk[1]);
+      if (sc->t_end > 0.0 && sc->t + dt > sc->t_end) dt = sc->t_end - sc->t;
+      sc->dt = dt;
+      break;
+    }
+    case SCHED_CYCLE_BEGIN: {
+      for (int k = 0; k < 2; k++)
+        if (sc->t_end > 0.0 && sc->t + dtk[k] > sc->t_end) dtk[k] = sc->t_end - sc->t;
+      int f1 = dtk[1] > dtk[0] ? 1 : 0;
+      double dt1 = dtk[f1], dt2 = dtk[1 - f1];
+      double nraw = dt1 / dt2;
+      sc->f1 = f1;
+      sc->n_raw = nraw;
+      sc->dtk_raw[0] = dtk[0];
+      sc->dtk_raw[1] = dtk[1];
+      int mode = 1;
+      if (force1) {
+        dt1 = dt2;
+      } else {
+        if (isfinite(dt1)) {
+          double fl = floor(nraw);
+          if (nraw - fl < thr) dt1 = fl * dt2;
+        }
+        if (!isfinite(dt1) || dt1 <= dt2) mode = 0;
+      }
+      sc->mode = mode;
+      if (mode == 0) {
+        sc->dt = dt2;
+        sc->dt1 = dt2;
+        sc->dt2 = dt2;
+        sc->n_used = 1.0;
+      } else {
+        sc->dt1 = dt1;
+        sc->dt2 = dt2;
+        sc->n_used = dt1 / dt2;
+      }
+      sc->t2 = 0.0;
+      sc->sub = 0;
+      break;
+    }
+    case SCHED_SUBSTEP:
+      sc->dt2 = dtk[sc->f1 == 0 ? 1 : 0];
+      // fall through to the last-substep test
+    case SCHED_FIRST_SUB: {
+      sc->sub += 1;
+      double dt1 = sc->dt1, t2 = sc->t2, dt2 = sc->dt2;
+      int last = (dt1 - t2) <= dt2 * (1.0 + 1e-12);
+      if (last) dt2 = dt1 - t2;
+      sc->dt2 = dt2;
+      sc->last = last;
+      sc->theta = last ? 1.0 : (t2 + dt2) / dt1;
+      break;
+    }
+    case SCHED_ADVANCE:
+      sc->t2 = sc->t2 + sc->dt2;
+      sc->theta = sc->t2 / sc->dt1;
+      break;
+    case SCHED_T_SINGLE:
+      sc->t = sc->t + sc->dt;
+      break;
+    case SCHED_T_CYCLE:
+      sc->t = sc->t + sc->dt1;
+      break;
+  }
+}
+
+void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st) {
+  k_sched<<<1, 32, 0, st>>>(op, sc, cfl, thr, force1);
+}

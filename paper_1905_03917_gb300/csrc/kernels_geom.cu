@@ -1,0 +1,323 @@
+// kernels_geom.cu -- ghost layers, cut-cell geometry from the level set
+// (Sec. 2.1, Fig. 1), narrow-band / cut-cell / active-tile lists compacted
+// with warp ballots, small-cell mixing (Sec. 2.2) and initial data.
+//
+// Compiled without FMA contraction: these kernels take the branch
+// decisions of the method (signs of corner values, small-cell and
+// real-cell thresholds), so they round exactly like the CPU reference.
+#include "sif_internal.cuh"
+
+// ---------------------------------------------------------------------
+// ghost layers: x ghosts of the interior rows, then y ghosts of every column
+
+__global__ void k_ghost_x(Grid g, GhostSet s) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int per = SIF_GH * g.ny;
+  if (t >= per * s.n) return;
+  int pl = t / per, r = t % per, m = r % SIF_GH, j = r / SIF_GH;
+  double *a = s.p[pl];
+  bool odd = s.vel[pl] == 1;
+  double vl, vr;
+  switch (g.bc[0]) {
+    case SIF_BC_REFLECT: vl = a[gidx(g, m, j)]; break;
+    case SIF_BC_PERIODIC: vl = a[gidx(g, g.nx - 1 - m, j)]; break;
+    default: vl = a[gidx(g, 0, j)];
+  }
+  switch (g.bc[1]) {
+    case SIF_BC_REFLECT: vr = a[gidx(g, g.nx - 1 - m, j)]; break;
+    case SIF_BC_PERIODIC: vr = a[gidx(g, m, j)]; break;
+    default: vr = a[gidx(g, g.nx - 1, j)];
+  }
+  a[gidx(g, -1 - m, j)] = (odd && g.bc[0] == SIF_BC_REFLECT) ? -vl : vl;
+  a[gidx(g, g.nx + m, j)] = (odd && g.bc[1] == SIF_BC_REFLECT) ? -vr : vr;
+}
+
+__global__ void k_ghost_y(Grid g, GhostSet s) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int W = g.nx + 2 * SIF_GH, per = W * SIF_GH;
+  if (t >= per * s.n) return;
+  int pl = t / per, r = t % per, i = r % W - SIF_GH, m = r / W;
+  double *a = s.p[pl];
+  bool odd = s.vel[pl] == 2;
+  double vb, vt;
+  switch (g.bc[2]) {
+    case SIF_BC_REFLECT: vb = a[gidx(g, i, m)]; break;
+    case SIF_BC_PERIODIC: vb = a[gidx(g, i, g.ny - 1 - m)]; break;
+    default: vb = a[gidx(g, i, 0)];
+  }
+  switch (g.bc[3]) {
+    case SIF_BC_REFLECT: vt = a[gidx(g, i, g.ny - 1 - m)]; break;
+    case SIF_BC_PERIODIC: vt = a[gidx(g, i, m)]; break;
+    default: vt = a[gidx(g, i, g.ny - 1)];
+  }
+  a[gidx(g, i, -1 - m)] = (odd && g.bc[2] == SIF_BC_REFLECT) ? -vb : vb;
+  a[gidx(g, i, g.ny + m)] = (odd && g.bc[3] == SIF_BC_REFLECT) ? -vt : vt;
+}
+
+void launch_fill_ghost(const Grid &g, const GhostSet &s, cudaStream_t st) {
+  int nx_threads = SIF_GH * g.ny * s.n;
+  k_ghost_x<<<(nx_threads + 255) / 256, 256, 0, st>>>(g, s);
+  int ny_threads = (g.nx + 2 * SIF_GH) * SIF_GH * s.n;
+  k_ghost_y<<<(ny_threads + 255) / 256, 256, 0, st>>>(g, s);
+}
+
+// ---------------------------------------------------------------------
+// warp-ballot compaction: one atomic per warp
+
+__device__ inline void append_ballot(bool pred, int value, int *list, int *count) {
+  unsigned mask = __ballot_sync(0xffffffffu, pred);
+  if (!mask) return;
+  int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(mask) - 1) base = atomicAdd(count, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+  if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = value;
+}
+
+// ---------------------------------------------------------------------
+// apertures, volume fraction and interface vector; cut-cell list
+
+__global__ void k_geometry(Grid g, const double *__restrict__ p, double *alpha, double *ax,
+                           double *ay, double *sx, double *sy, int *cut, int *ncut) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int W = g.nx + 1;
+  int i = t % W, j = t / W;
+  bool valid = j <= g.ny;
+  bool is_cut = false;
+  int c = 0;
+  if (valid) {
+    c = gidx(g, i, j);
+    double c00 = corner_phi(g, p, i, j);
+    double c01 = corner_phi(g, p, i, j + 1);
+    double c10 = corner_phi(g, p, i + 1, j);
+    if (j < g.ny) ax[c] = edge_fraction(c00, c01);
+    if (i < g.nx) ay[c] = edge_fraction(c00, c10);
+    if (i < g.nx && j < g.ny) {
+      double c11 = corner_phi(g, p, i + 1, j + 1);
+      alpha[c] = cell_alpha(c00, c10, c11, c01);
+      double axl = edge_fraction(c00, c01), axr = edge_fraction(c10, c11);
+      double ayb = edge_fraction(c00, c10), ayt = edge_fraction(c01, c11);
+      double Sx = (axr - axl) * g.dy;
+      double Sy = (ayt - ayb) * g.dx;
+      sx[c] = Sx;
+      sy[c] = Sy;
+      is_cut = (Sx != 0.0 || Sy != 0.0);
+    }
+  }
+  append_ballot(is_cut, c, cut, ncut);
+}
+
+void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax, double *ay,
+                     double *sx, double *sy, int *cut_list, Scalars *sc, cudaStream_t st) {
+  cudaMemsetAsync(&sc->n_cut, 0, sizeof(int), st);
+  int n = (g.nx + 1) * (g.ny + 1);
+  k_geometry<<<(n + 255) / 256, 256, 0, st>>>(g, phi, alpha, ax, ay, sx, sy, cut_list, &sc->n_cut);
+}
+
+// ---------------------------------------------------------------------
+// narrow band |phi| < band*h and its face-neighbour extension
+
+__global__ void k_band(Grid g, const double *__restrict__ p, int *band, int *rext, int *nband,
+                       int *nrext) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t % g.nx, j = t / g.nx;
+  bool valid = j < g.ny;
+  double bw = g.band * g.h;
+  bool in = false, inx = false;
+  int c = 0;
+  if (valid) {
+    c = gidx(g, i, j);
+    in = fabs(p[c]) < bw;
+    inx = in;
+    if (i > 0) inx = inx || fabs(p[c - 1]) < bw;
+    if (i < g.nx - 1) inx = inx || fabs(p[c + 1]) < bw;
+    if (g.dim == 2) {
+      if (j > 0) inx = inx || fabs(p[c - g.PX]) < bw;
+      if (j < g.ny - 1) inx = inx || fabs(p[c + g.PX]) < bw;
+    }
+  }
+  append_ballot(in, c, band, nband);
+  if (rext) append_ballot(inx, c, rext, nrext);
+}
+
+void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, int *counts,
+                       cudaStream_t st) {
+  cudaMemsetAsync(counts, 0, 2 * sizeof(int), st);
+  int n = g.nx * g.ny;
+  k_band<<<(n + 255) / 256, 256, 0, st>>>(g, phi, band, rext, &counts[0], &counts[1]);
+}
+
+// ---------------------------------------------------------------------
+// fv tiles in which fluid k can hold an open face: a cell of the tile or of
+// its one-cell ring (ghosts included) lies on fluid k's side
+
+__global__ void k_tiles(Grid g, const double *__restrict__ p, int *t0, int *t1, int *n) {
+  int tile = blockIdx.x;
+  int tx = tile % g.ntx, ty = tile / g.ntx;
+  int i0 = tx * FV_TX - 1, j0 = ty * FV_TY - 1;
+  int wy = g.dim == 2 ? FV_TY + 2 : 1;
+  if (g.dim == 1) j0 = 0;
+  int any_pos = 0, any_neg = 0;
+  for (int r = threadIdx.x; r < (FV_TX + 2) * wy; r += blockDim.x) {
+    int i = i0 + r % (FV_TX + 2), j = j0 + r / (FV_TX + 2);
+    if (i < -1 || i > g.nx || j < -1 || j > g.ny) continue;
+    double v = p[gidx(g, i, j)];
+    if (v >= 0.0) any_pos = 1;
+    else any_neg = 1;
+  }
+  any_pos = __syncthreads_or(any_pos);
+  any_neg = __syncthreads_or(any_neg);
+  if (threadIdx.x == 0) {
+    if (any_neg) t0[atomicAdd(&n[0], 1)] = tile;
+    if (any_pos) t1[atomicAdd(&n[1], 1)] = tile;
+  }
+}
+
+void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
+                       cudaStream_t st) {
+  cudaMemsetAsync(sc->n_tiles, 0, 2 * sizeof(int), st);
+  k_tiles<<<g.ntx * g.nty, 128, 0, st>>>(g, phi, tiles0, tiles1, sc->n_tiles);
+}
+
+// ---------------------------------------------------------------------
+// small-cell mixing, gather form in the CPU reference's scatter order
+
+struct MixSrc {
+  int nt;
+  int ti[3], tj[3];
+  double beta[3], at[3];
+  double as;
+};
+
+// is cell (i, j) a mixing source of fluid k; if so its targets and weights
+__device__ bool mix_source(const Grid &g, int k, int i, int j, const double *alpha,
+                           const double *phi, double *const q[4], MixSrc &s) {
+  int c = gidx(g, i, j);
+  double as = vol_k(alpha, k, c);
+  if (as >= g.mix_alpha) return false;
+  if (as == 0.0 && q[0][c] == 0.0 && q[1][c] == 0.0 && q[2][c] == 0.0 && q[3][c] == 0.0)
+    return false;
+  double nxv, nyv;
+  unit_normal(g, phi, i, j, nxv, nyv);
+  if (k == 0) {
+    nxv = -nxv;
+    nyv = -nyv;
+  }
+  int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+  int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
+  double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
+  int nt = g.dim == 2 ? 3 : 1;
+  bool keep[3] = {false, false, false};
+  double sum = 0.0;
+  for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
+    for (int t = 0; t < nt; t++) {
+      if (!inside(g, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
+      double at = vol_k(alpha, k, gidx(g, ti[t], tj[t]));
+      if (pass == 0 ? !(at >= g.mix_alpha) : !(at > as)) continue;
+      keep[t] = true;
+      sum += wt[t];
+    }
+  if (!(sum > 0.0)) return false;
+  s.nt = 0;
+  s.as = as;
+  for (int t = 0; t < nt; t++) {
+    if (!keep[t]) continue;
+    s.ti[s.nt] = ti[t];
+    s.tj[s.nt] = tj[t];
+    s.beta[s.nt] = wt[t] / sum;
+    s.at[s.nt] = vol_k(alpha, k, gidx(g, ti[t], tj[t]));
+    s.nt++;
+  }
+  return true;
+}
+
+__global__ void k_mix_gather(Grid g, int k, double *q0, double *q1, double *q2, double *q3,
+                             const double *__restrict__ alpha, const double *__restrict__ phi,
+                             const int *__restrict__ band, const int *nband, double *tmp) {
+  int n = *nband;
+  double *const q[4] = {q0, q1, q2, q3};
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double val[4] = {q0[c], q1[c], q2[c], q3[c]};
+    // sources in raster order; each adds to itself and subtracts at its targets
+    for (int dj = -1; dj <= 1; dj++)
+      for (int di = -1; di <= 1; di++) {
+        int si = i + di, sj = j + dj;
+        if (g.dim == 1 && dj != 0) continue;
+        if (!inside(g, si, sj)) continue;
+        MixSrc s;
+        if (!mix_source(g, k, si, sj, alpha, phi, q, s)) continue;
+        int sc_ = gidx(g, si, sj);
+        for (int t = 0; t < s.nt; t++) {
+          int tc = gidx(g, s.ti[t], s.tj[t]);
+          bool self = (di == 0 && dj == 0);
+          bool tgt = (tc == c);
+          if (!self && !tgt) continue;
+          double den = s.as * s.beta[t] + s.at[t];
+          for (int m = 0; m < 4; m++) {
+            double M = s.beta[t] * (q[m][tc] * s.as - q[m][sc_] * s.at[t]) / den;
+            if (self) val[m] += M;
+            if (tgt) val[m] -= M;
+          }
+        }
+      }
+    for (int m = 0; m < 4; m++) tmp[(size_t)m * n + idx] = val[m];
+  }
+}
+
+__global__ void k_band_scatter4(const int *__restrict__ band, const int *nband, const double *tmp,
+                                double *q0, double *q1, double *q2, double *q3) {
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    q0[c] = tmp[idx];
+    q1[c] = tmp[(size_t)n + idx];
+    q2[c] = tmp[(size_t)2 * n + idx];
+    q3[c] = tmp[(size_t)3 * n + idx];
+  }
+}
+
+void launch_mix(const Grid &g, int k, double *const q[4], const double *alpha, const double *phi,
+                const int *band, const int *nband, int band_cap, double *tmp, cudaStream_t st) {
+  int blocks = (band_cap + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  k_mix_gather<<<blocks, 256, 0, st>>>(g, k, q[0], q[1], q[2], q[3], alpha, phi, band, nband,
+                                      tmp);
+  k_band_scatter4<<<blocks, 256, 0, st>>>(band, nband, tmp, q[0], q[1], q[2], q[3]);
+}
+
+// ---------------------------------------------------------------------
+// initial data: (alpha U)_k = alpha_k U(W_k) from the primitive fields
+
+__global__ void k_init_q(Grid g, double *qN0, double *qN1, double *qN2, double *qN3,
+                         double *qP0, double *qP1, double *qP2, double *qP3, const double *wN0,
+                         const double *wN1, const double *wN2, const double *wN3,
+                         const double *wP0, const double *wP1, const double *wP2,
+                         const double *wP3, const double *alpha) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nx * g.ny) return;
+  int i = t % g.nx, j = t / g.nx, c = gidx(g, i, j);
+  for (int k = 0; k < 2; k++) {
+    const double *w[4] = {k ? wP0 : wN0, k ? wP1 : wN1, k ? wP2 : wN2, k ? wP3 : wN3};
+    double *q[4] = {k ? qP0 : qN0, k ? qP1 : qN1, k ? qP2 : qN2, k ? qP3 : qN3};
+    double gm = g.gamma[k], pi = g.pinf[k];
+    double rho = w[0][c], u = w[1][c], v = w[2][c], p = w[3][c];
+    double E = (p + gm * pi) / (gm - 1.0) + 0.5 * rho * (u * u + v * v);
+    double a = vol_k(alpha, k, c);
+    q[0][c] = a * rho;
+    q[1][c] = a * (rho * u);
+    q[2][c] = a * (rho * v);
+    q[3][c] = a * E;
+  }
+}
+
+void launch_init_state(const Grid &g, double *const qN[4], double *const qP[4],
+                       double *const wN[4], double *const wP[4], const double *alpha,
+                       cudaStream_t st) {
+  int n = g.nx * g.ny;
+  k_init_q<<<(n + 255) / 256, 256, 0, st>>>(g, qN[0], qN[1], qN[2], qN[3], qP[0], qP[1], qP[2],
+                                            qP[3], wN[0], wN[1], wN[2], wN[3], wP[0], wP[1],
+                                            wP[2], wP[3], alpha);
+}

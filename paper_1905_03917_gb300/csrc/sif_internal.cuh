@@ -1,0 +1,315 @@
+// sif_internal.cuh -- device-side data structures and the pointwise
+// formulas shared by the CUDA translation units of libsif.
+//
+// Layout: every field is an FP64 plane of PX x PY doubles with GH ghost
+// layers on each side; cell (i, j), -GH <= i < nx + GH, lives at
+// (i + GH) + (j + GH) * PX.  PX is padded to a multiple of 16 doubles so
+// that every row starts on a 128-byte boundary relative to the plane base.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sif.h"
+
+#define SIF_GH 3
+// a cell holds fluid k for stencil/CFL purposes only if alpha_k exceeds
+// this; round-off slivers take extended states instead
+#define SIF_ALPHA_REAL 1e-6
+
+// fv tile (outputs per CTA) of the cut-cell update kernel
+#define FV_TX 32
+#define FV_TY 8
+
+// device error bits
+#define DERR_NONPHYS 1
+#define DERR_NOCONV 2
+#define DERR_TIMEOUT 4
+
+struct Grid {
+  int dim, nx, ny, PX, PY;
+  double dx, dy, h;
+  int bc[4];
+  double gamma[2], pinf[2];
+  double cfl, weno_eps, mix_alpha, band;
+  int ext_iters, reinit_iters;
+  int ntx, nty;  // fv tiles
+};
+
+// Scalars that live in device memory so that a whole step can run without
+// a host round trip.  Maxima of non-negative doubles are kept as their bit
+// patterns (ordered like the values) for atomicMax.
+struct Scalars {
+  unsigned long long smax[2];   // CFL wave-speed sums per fluid
+  unsigned long long lf[2][2];  // Lax-Friedrichs alpha per fluid, direction
+  double t, t_end;
+  double dt;                    // single-dt step
+  double dt1, dt2, t2, theta;   // multi-dt cycle
+  double n_raw, n_used;
+  int f1, mode, last, sub;
+  int err;
+  int n_band, n_band_spare;   // interaction-step band (and unused slot)
+  int n_band_ls, n_rext;      // level-set step band and its face neighbours
+  int n_cut, n_tiles[2];
+  double dtk_raw[2];
+  unsigned long long updates;   // (cell, fluid) stage updates issued
+};
+
+struct Ctx;  // host-side context, see api.cu
+
+__host__ __device__ inline int gidx(const Grid &g, int i, int j) {
+  return (i + SIF_GH) + (j + SIF_GH) * g.PX;
+}
+
+__device__ inline double ull_as_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ inline unsigned long long double_as_ull(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// max of non-negative doubles via the ordered bit pattern
+__device__ inline void atomic_max_pos(unsigned long long *addr, double v) {
+  if (v > 0.0) atomicMax(addr, double_as_ull(v));
+}
+
+__device__ inline double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------
+// geometry (Sec. 2.1, Fig. 1); operation order identical to the CPU
+// reference so that sign and threshold decisions agree
+
+__device__ inline double edge_fraction(double a, double b) {
+  if (a >= 0.0 && b >= 0.0) return 1.0;
+  if (a < 0.0 && b < 0.0) return 0.0;
+  if (a >= 0.0) return a / (a - b);
+  return b / (b - a);
+}
+
+__device__ inline double cell_alpha(double c00, double c10, double c11, double c01) {
+  const double v[4] = {c00, c10, c11, c01};
+  const double px[4] = {0.0, 1.0, 1.0, 0.0};
+  const double py[4] = {0.0, 0.0, 1.0, 1.0};
+  int npos = 0, changes = 0;
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    if (v[e] >= 0.0) npos++;
+    if ((v[e] >= 0.0) != (v[(e + 1) & 3] >= 0.0)) changes++;
+  }
+  if (npos == 4) return 1.0;
+  if (npos == 0) return 0.0;
+  if (changes == 4) {
+    double area = 0.0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      if (v[e] < 0.0) continue;
+      int n = (e + 1) & 3, p = (e + 3) & 3;
+      double l1 = v[e] / (v[e] - v[n]);
+      double l2 = v[e] / (v[e] - v[p]);
+      area += 0.5 * l1 * l2;
+    }
+    return area;
+  }
+  double X[8], Y[8];
+  int m = 0;
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    int n = (e + 1) & 3;
+    if (v[e] >= 0.0) {
+      X[m] = px[e];
+      Y[m] = py[e];
+      m++;
+    }
+    if ((v[e] >= 0.0) != (v[n] >= 0.0)) {
+      double s = v[e] / (v[e] - v[n]);
+      X[m] = px[e] + s * (px[n] - px[e]);
+      Y[m] = py[e] + s * (py[n] - py[e]);
+      m++;
+    }
+  }
+  double a2 = 0.0;
+  for (int k = 0; k < m; k++) {
+    int k1 = (k + 1) % m;
+    a2 += X[k] * Y[k1] - X[k1] * Y[k];
+  }
+  return 0.5 * a2;
+}
+
+// level set at the lower-left corner of cell (i, j)
+__device__ inline double corner_phi(const Grid &g, const double *p, int i, int j) {
+  return 0.25 * ((p[gidx(g, i - 1, j - 1)] + p[gidx(g, i, j - 1)]) +
+                 (p[gidx(g, i - 1, j)] + p[gidx(g, i, j)]));
+}
+
+__device__ inline void unit_normal(const Grid &g, const double *p, int i, int j,
+                                   double &nx, double &ny) {
+  double gx = (p[gidx(g, i + 1, j)] - p[gidx(g, i - 1, j)]) / (2.0 * g.dx);
+  double gy = g.dim == 2 ? (p[gidx(g, i, j + 1)] - p[gidx(g, i, j - 1)]) / (2.0 * g.dy) : 0.0;
+  double m = sqrt(gx * gx + gy * gy);
+  if (m > 0.0) {
+    nx = gx / m;
+    ny = gy / m;
+  } else {
+    nx = 0.0;
+    ny = 0.0;
+  }
+}
+
+__device__ inline bool inside(const Grid &g, int i, int j) {
+  return i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+}
+
+__device__ inline double vol_k(const double *alphaP, int k, int c) {
+  return k == 1 ? alphaP[c] : 1.0 - alphaP[c];
+}
+
+// ---------------------------------------------------------------------
+// WENO5-JS reconstruction in the plain form (used by the level set and
+// reinitialisation kernels, which follow the CPU reference op by op)
+
+__device__ inline double sqd(double a) { return a * a; }
+
+__device__ inline double weno5_plain(double v1, double v2, double v3, double v4, double v5,
+                                     double eps) {
+  double q0 = (2.0 * v1 - 7.0 * v2 + 11.0 * v3) / 6.0;
+  double q1 = (-v2 + 5.0 * v3 + 2.0 * v4) / 6.0;
+  double q2 = (2.0 * v3 + 5.0 * v4 - v5) / 6.0;
+  double b0 = 13.0 / 12.0 * sqd(v1 - 2.0 * v2 + v3) + 0.25 * sqd(v1 - 4.0 * v2 + 3.0 * v3);
+  double b1 = 13.0 / 12.0 * sqd(v2 - 2.0 * v3 + v4) + 0.25 * sqd(v2 - v4);
+  double b2 = 13.0 / 12.0 * sqd(v3 - 2.0 * v4 + v5) + 0.25 * sqd(3.0 * v3 - 4.0 * v4 + v5);
+  double a0 = 0.1 / sqd(eps + b0);
+  double a1 = 0.6 / sqd(eps + b1);
+  double a2 = 0.3 / sqd(eps + b2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------------
+// exact two-material stiffened-gas Riemann problem (interface interaction)
+
+__device__ inline void riemann_side(double p, double rho, double pk, double g, double pi,
+                                    double ck, double &f, double &df) {
+  double P = pk + pi, Pp = p + pi;
+  if (p > pk) {
+    double A = 2.0 / ((g + 1.0) * rho);
+    double B = (g - 1.0) / (g + 1.0) * P;
+    double qr = sqrt(A / (Pp + B));
+    f = (p - pk) * qr;
+    df = qr * (1.0 - 0.5 * (p - pk) / (Pp + B));
+  } else {
+    double r = Pp / P;
+    f = 2.0 * ck / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
+    df = 1.0 / (rho * ck) * pow(r, -(g + 1.0) / (2.0 * g));
+  }
+}
+
+__device__ inline double riemann_star_density(double p, double rho, double pk, double g, double pi) {
+  double r = (p + pi) / (pk + pi);
+  if (p > pk) {
+    double qq = (g - 1.0) / (g + 1.0);
+    return rho * (r + qq) / (qq * r + 1.0);
+  }
+  return rho * pow(r, 1.0 / g);
+}
+
+// returns 0 or DERR_NOCONV; out: p*, u*, c*_L, c*_R
+__device__ inline int riemann_solve(double rl, double ul, double pl, double gl, double pil,
+                                    double rr, double ur, double pr, double gr, double pir,
+                                    double &ps, double &us, double &csl, double &csr) {
+  double cl = sqrt(gl * (pl + pil) / rl), cr = sqrt(gr * (pr + pir) / rr);
+  double pscale = fmin(pl + pil, pr + pir);
+  double pfloor = -fmin(pil, pir) + 1e-12 * pscale;
+  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  if (p < pfloor) p = pfloor;
+  int it = 0, conv = 0, done = 0;
+  double fl, dfl, fr, dfr;
+  while (it < 50) {
+    it++;
+    riemann_side(p, rl, pl, gl, pil, cl, fl, dfl);
+    riemann_side(p, rr, pr, gr, pir, cr, fr, dfr);
+    double F = fl + fr + (ur - ul);
+    double pn = p - F / (dfl + dfr);
+    if (pn < pfloor) pn = pfloor;
+    double dp = fabs(pn - p);
+    p = pn;
+    if (conv) {
+      done = 1;
+      break;
+    }
+    if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
+  }
+  riemann_side(p, rl, pl, gl, pil, cl, fl, dfl);
+  riemann_side(p, rr, pr, gr, pir, cr, fr, dfr);
+  us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  double rsl = riemann_star_density(p, rl, pl, gl, pil);
+  double rsr = riemann_star_density(p, rr, pr, gr, pir);
+  ps = p;
+  csl = sqrt(gl * (p + pil) / rsl);
+  csr = sqrt(gr * (p + pir) / rsr);
+  return (done || conv) ? 0 : DERR_NOCONV;
+}
+
+// ---------------------------------------------------------------------
+// host-side launch wrappers (defined in the .cu files)
+
+// ghost layers of up to 8 planes; vel[m]: 0 scalar, 1 x-velocity, 2 y-velocity
+struct GhostSet {
+  double *p[8];
+  int vel[8];
+  int n;
+};
+void launch_fill_ghost(const Grid &g, const GhostSet &s, cudaStream_t st);
+void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax, double *ay,
+                     double *sx, double *sy, int *cut_list, Scalars *sc, cudaStream_t st);
+// counts[0] = band size, counts[1] = band + face neighbours (if rext)
+void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, int *counts,
+                       cudaStream_t st);
+void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
+                       cudaStream_t st);
+void launch_mix(const Grid &g, int k, double *const q[4], const double *alpha, const double *phi,
+                const int *band, const int *nband, int band_cap, double *tmp, cudaStream_t st);
+
+void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
+                 const double *alpha, const int *tiles, int tile_cap, Scalars *sc, cudaStream_t st);
+void launch_extend(const Grid &g, int k, double *const w[4], const double *alpha,
+                   const double *phi, const int *band, int band_cap, double *tmp, Scalars *sc,
+                   cudaStream_t st);
+void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
+                      const double *sx, const double *sy, const int *cut, int cut_cap,
+                      double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
+                      Scalars *sc, cudaStream_t st);
+void launch_ls_extend(const Grid &g, double *ul0, double *ul1, const double *phi,
+                      const double *sx, const double *sy, const int *band, int band_cap,
+                      double *tmp, Scalars *sc, cudaStream_t st);
+void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *phi0,
+                     const double *ul0, const double *ul1, const int *band, const int *nband,
+                     int band_cap, double *tmp, const double *dtp, cudaStream_t st);
+void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, const int *nrext,
+                   int rext_cap, double *tmp, cudaStream_t st);
+void launch_record(const Grid &g, int shared, const int *cut, int cut_cap, const double *xn0,
+                   const double *xn1, const double *xn2, double *xc0, double *xc1, double *xc2,
+                   Scalars *sc, cudaStream_t st);
+void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
+                   double *const fut[4], const double *thp, cudaStream_t st);
+void launch_correction(const Grid &g, double *const q[4], const double *xc0, const double *xc1,
+                       const double *xc2, cudaStream_t st);
+void launch_init_state(const Grid &g, double *const qN[4], double *const qP[4],
+                       double *const wN[4], double *const wP[4], const double *alpha,
+                       cudaStream_t st);
+void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], double *partial,
+                      int nblk, double *out, cudaStream_t st);
+void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st);
+
+void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
+                     double *const base[4], double *const cur[4], double *const w[4],
+                     const double *ax, const double *ay, const double *sx, const double *sy,
+                     const double *xn0, const double *xn1, const double *xn2, const int *tiles,
+                     int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st);
+
+// scheduler ops
+#define SCHED_SINGLE_DT 0   // dt = min over fluids, capped by t_end
+#define SCHED_CYCLE_BEGIN 1 // roles, ratio, truncation
+#define SCHED_SUBSTEP 2     // fluid-2 dt from the latest interaction, last-substep test
+#define SCHED_ADVANCE 3     // t2 += dt2 or finish the cycle
+#define SCHED_FIRST_SUB 4   // last-substep test for the first sub-step
+#define SCHED_RESET_MAX 5   // zero the CFL / LF maxima before an interaction step
+#define SCHED_T_SINGLE 6    // t += dt
+#define SCHED_T_CYCLE 7     // t += dt1

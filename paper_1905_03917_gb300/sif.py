@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libsif (include/sif.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Arrays may be numpy arrays (host memory, SIF_HOST) or CUDA
+torch tensors (device memory, SIF_DEVICE, passed by data_ptr()).  There
+is no CPU fallback: if the library cannot be loaded this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ECUDA, ENONPHYS, ENOCONV, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+HOST, DEVICE = 0, 1
+BC = {"reflect": 0, "zerograd": 1, "periodic": 2}
+_NAMES = {EINVAL: "SIF_EINVAL", ECUDA: "SIF_ECUDA", ENONPHYS: "SIF_ENONPHYS",
+          ENOCONV: "SIF_ENOCONV", ETIMEOUT: "SIF_ETIMEOUT", ESTATE: "SIF_ESTATE"}
+
+EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_multi_dt",
+           "sif_integrals", "sif_get_state", "sif_set_state", "sif_get_time",
+           "sif_last_error", "sif_destroy"]
+
+
+class SifError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("bc", ctypes.c_int * 4),
+                ("gamma", ctypes.c_double * 2), ("pinf", ctypes.c_double * 2),
+                ("cfl", ctypes.c_double), ("rk_order", ctypes.c_int),
+                ("weno_eps", ctypes.c_double), ("mix_alpha", ctypes.c_double),
+                ("ratio_threshold", ctypes.c_double),
+                ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
+                ("band", ctypes.c_double),
+                ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class CycleInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt1", ctypes.c_double), ("dt2", ctypes.c_double),
+                ("n_raw", ctypes.c_double), ("n_used", ctypes.c_double),
+                ("role_fluid1", ctypes.c_int), ("substeps", ctypes.c_int),
+                ("cell_updates", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libsif (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsif not found at {path}")
+    L = ctypes.CDLL(path)
+    P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    L.sif_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(P)]
+    L.sif_init_fluids.argtypes = [P, P, P, P, I]
+    L.sif_step_single_dt.argtypes = [P, I, D, ctypes.POINTER(CycleInfo)]
+    L.sif_step_multi_dt.argtypes = [P, I, D, ctypes.POINTER(CycleInfo)]
+    L.sif_integrals.argtypes = [P, P]
+    L.sif_get_state.argtypes = [P, P, P, P, I]
+    L.sif_set_state.argtypes = [P, P, P, P, D, I]
+    L.sif_get_time.argtypes = [P, ctypes.POINTER(D)]
+    L.sif_last_error.argtypes = [P]
+    L.sif_last_error.restype = ctypes.c_char_p
+    L.sif_destroy.argtypes = [P]
+    L.sif_destroy.restype = None
+    for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
+              L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time):
+        f.restype = I
+    _lib = L
+    return L
+
+
+def make_config(cfg: dict, stream=None, device=0) -> Config:
+    c = Config()
+    c.dim, c.nx, c.ny = int(cfg["dim"]), int(cfg["nx"]), int(cfg["ny"])
+    c.x0, c.y0 = float(cfg.get("x0", 0.0)), float(cfg.get("y0", 0.0))
+    c.dx, c.dy = float(cfg["dx"]), float(cfg["dy"])
+    for i, b in enumerate(cfg["bc"]):
+        c.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    for k in range(2):
+        c.gamma[k], c.pinf[k] = float(cfg["gamma"][k]), float(cfg["pinf"][k])
+    c.cfl = float(cfg.get("cfl", 0.6))
+    c.rk_order = int(cfg.get("rk_order", 2))
+    c.weno_eps = float(cfg.get("weno_eps", 1e-6))
+    c.mix_alpha = float(cfg.get("mix_alpha", 0.5))
+    c.ratio_threshold = float(cfg.get("ratio_threshold", 0.7))
+    c.ext_iters = int(cfg.get("ext_iters", 10))
+    c.reinit_iters = int(cfg.get("reinit_iters", 2))
+    c.band = float(cfg.get("band", 6.0))
+    c.flux_correction = int(cfg.get("flux_correction", 1))
+    c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
+    c.cuda_stream = stream
+    c.device = int(device)
+    return c
+
+
+def _ptr(a):
+    """(pointer, mem_kind) of a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, HOST
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous float64")
+        return a.data_ptr(), DEVICE
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Solver:
+    """One two-fluid problem held on the GPU by libsif."""
+
+    def __init__(self, cfg: dict, stream=None, device=0):
+        self.cfg = dict(cfg)
+        self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        L = load()
+        h = ctypes.c_void_p()
+        c = make_config(cfg, stream, device)
+        rc = L.sif_create(ctypes.byref(c), ctypes.byref(h))
+        if rc != OK:
+            raise SifError(rc, "sif_create rejected the configuration or failed to allocate")
+        self._h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = load().sif_last_error(self._h).decode()
+            raise SifError(rc, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sif_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fluids(self, phi, prim_N, prim_P):
+        (p0, k0), (p1, k1), (p2, k2) = _ptr(phi), _ptr(prim_N), _ptr(prim_P)
+        if not (k0 == k1 == k2):
+            raise ValueError("all inputs must be in the same memory")
+        self._keep = (phi, prim_N, prim_P)
+        self._check(load().sif_init_fluids(self._h, p0, p1, p2, k0))
+        self._keep = None
+        return self
+
+    def _info(self, info):
+        return {"t": info.t, "dt1": info.dt1, "dt2": info.dt2, "n_raw": info.n_raw,
+                "n_used": info.n_used, "role_fluid1": info.role_fluid1,
+                "substeps": info.substeps, "cell_updates": info.cell_updates}
+
+    def step_single_dt(self, nsteps=1, t_end=0.0):
+        info = CycleInfo()
+        self._check(load().sif_step_single_dt(self._h, int(nsteps), float(t_end), ctypes.byref(info)))
+        return self._info(info)
+
+    def step_multi_dt(self, ncycles=1, t_end=0.0):
+        info = CycleInfo()
+        self._check(load().sif_step_multi_dt(self._h, int(ncycles), float(t_end), ctypes.byref(info)))
+        return self._info(info)
+
+    def integrals(self):
+        out = np.empty(8)
+        self._check(load().sif_integrals(self._h, out.ctypes.data))
+        return out.reshape(2, 4)
+
+    def state(self):
+        n = self.nx * self.ny
+        qN, qP, phi = np.empty(4 * n), np.empty(4 * n), np.empty(n)
+        self._check(load().sif_get_state(self._h, qN.ctypes.data, qP.ctypes.data, phi.ctypes.data, HOST))
+        sh = (4, self.ny, self.nx)
+        return qN.reshape(sh), qP.reshape(sh), phi.reshape(self.ny, self.nx)
+
+    def state_into(self, qN, qP, phi):
+        (a, ka), (b, kb), (c, kc) = _ptr(qN), _ptr(qP), _ptr(phi)
+        self._check(load().sif_get_state(self._h, a, b, c, ka))
+
+    def set_state(self, qN, qP, phi, t=0.0):
+        (a, ka), (b, kb), (c, kc) = _ptr(qN), _ptr(qP), _ptr(phi)
+        self._check(load().sif_set_state(self._h, a, b, c, float(t), ka))
+
+    @property
+    def t(self):
+        v = ctypes.c_double()
+        self._check(load().sif_get_time(self._h, ctypes.byref(v)))
+        return v.value

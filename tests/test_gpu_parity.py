@@ -1,0 +1,183 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle on
+seeded inputs: relative L1 per fluid and conserved component <= 1e-12 after
+one step, <= 1e-8 after 100 steps, for the single-time-step method and the
+multi-time-step cycle (Sec. 3.1), plus conservation, the ratio-one
+reduction and error reporting on the GPU."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_03917_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _sif():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_03917_gb300 import sif
+    return sif
+
+
+def rel_l1(a, b, floor):
+    return np.abs(a - b).sum() / max(np.abs(b).sum(), floor)
+
+
+def compare(gpu, orc, tol):
+    """Relative L1 of every fluid/component and of phi; returns the worst."""
+    worst = 0.0
+    gs, os_ = gpu.state(), orc.state()
+    for k in range(2):
+        mass = np.abs(os_[k][0]).sum()
+        for m in range(4):
+            # momentum components are measured against the mass times a speed
+            # scale so that a component that is zero stays comparable
+            floor = 1e-300 if m in (0, 3) else 1e-12 * max(mass, 1e-300)
+            e = rel_l1(gs[k][m], os_[k][m], floor)
+            worst = max(worst, e)
+            assert e <= tol, (k, m, e)
+    e = rel_l1(gs[2], os_[2], 1e-300)
+    assert e <= tol, ("phi", e)
+    return max(worst, e)
+
+
+def pair(case, **kw):
+    sif = _sif()
+    cfg = dict(case["cfg"], **kw)
+    g = sif.Solver(cfg).init_fluids(*(np.ascontiguousarray(case[x], dtype=np.float64)
+                                      for x in ("phi", "prim_N", "prim_P")))
+    o = O.Oracle(cfg).init(case["phi"], case["prim_N"], case["prim_P"])
+    return g, o
+
+
+CASES = {
+    "tube_rk3": lambda: inputs.shock_tube_1d(400, rk_order=3),
+    "tube_rk2": lambda: inputs.shock_tube_1d(400, rk_order=2),
+    "tube_ragged": lambda: inputs.shock_tube_1d(203, rk_order=2, interface=0.4913),
+    "bubble_periodic": lambda: inputs.periodic_bubble(48, seed=1),
+    "shock_bubble": lambda: inputs.shock_bubble(128, 32, seed=3, perturb=1e-3),
+    "explosion": lambda: inputs.underwater_explosion(96, seed=5, perturb=1e-3),
+    "explosion_fast_gas": lambda: inputs.underwater_explosion(77, radius=0.3, p_gas=1e8, rho_gas=1.0, seed=7),
+    "static": lambda: inputs.static_interface(37, 21),
+    "single_fluid": lambda: inputs.single_fluid(40, 24),
+}
+MULTI = ["tube_rk2", "bubble_periodic", "shock_bubble", "explosion", "explosion_fast_gas"]
+
+
+def test_init_matches_oracle():
+    g, o = pair(CASES["explosion"]())
+    compare(g, o, 1e-15)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_single_step(name):
+    g, o = pair(CASES[name]())
+    g.step_single_dt(1)
+    o.step_single_dt(1)
+    compare(g, o, 1e-12)
+    assert abs(g.t - o.t) <= 1e-14 * o.t
+
+
+@pytest.mark.parametrize("name", ["tube_rk3", "bubble_periodic", "shock_bubble", "explosion"])
+def test_hundred_single_steps(name):
+    g, o = pair(CASES[name]())
+    g.step_single_dt(100)
+    o.step_single_dt(100)
+    compare(g, o, 1e-8)
+    assert abs(g.t - o.t) <= 1e-10 * o.t
+
+
+@pytest.mark.parametrize("name", MULTI)
+def test_one_multi_dt_cycle(name):
+    g, o = pair(CASES[name]())
+    gi = g.step_multi_dt(1)
+    oi = o.step_multi_dt(1)
+    assert gi["substeps"] == oi["substeps"]
+    assert gi["role_fluid1"] == oi["role_fluid1"] or oi["substeps"] == 1
+    compare(g, o, 1e-12)
+
+
+@pytest.mark.parametrize("name", MULTI)
+def test_fifty_multi_dt_cycles(name):
+    g, o = pair(CASES[name]())
+    subs_g, subs_o = [], []
+    for _ in range(50):
+        subs_g.append(g.step_multi_dt(1)["substeps"])
+        subs_o.append(o.step_multi_dt(1)["substeps"])
+    assert subs_g == subs_o
+    compare(g, o, 1e-8)
+
+
+def test_integrals_match_oracle():
+    g, o = pair(CASES["bubble_periodic"]())
+    g.step_multi_dt(5)
+    o.step_multi_dt(5)
+    gi, oi = g.integrals(), o.integrals()
+    scale = np.abs(oi).max(axis=1, keepdims=True)
+    assert np.abs(gi - oi).max() <= 1e-13 * np.abs(oi).max()
+
+
+def test_gpu_multi_dt_conserves():
+    g, _ = pair(CASES["bubble_periodic"]())
+    I0 = g.integrals().sum(0)
+    subs = [g.step_multi_dt(1)["substeps"] for _ in range(60)]
+    assert max(subs) >= 2
+    I1 = g.integrals().sum(0)
+    scale = np.array([I0[0], I0[0] * 2000.0, I0[0] * 2000.0, I0[3]])
+    assert (np.abs(I1 - I0) / scale).max() <= 1e-13
+
+
+def test_gpu_ratio_one_equals_single_step_bitwise():
+    sif = _sif()
+    case = CASES["bubble_periodic"]()
+    arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
+    a = sif.Solver(case["cfg"]).init_fluids(*arrs)
+    b = sif.Solver(dict(case["cfg"], force_ratio_one=1)).init_fluids(*arrs)
+    for _ in range(10):
+        a.step_single_dt(1)
+        b.step_multi_dt(1)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+
+
+def test_device_pointers_and_state_roundtrip():
+    sif = _sif()
+    import torch
+    case = CASES["shock_bubble"]()
+    dev = [torch.from_numpy(np.ascontiguousarray(case[x])).cuda() for x in ("phi", "prim_N", "prim_P")]
+    a = sif.Solver(case["cfg"]).init_fluids(*dev)
+    a.step_single_dt(3)
+    qN, qP, phi = (torch.empty((4, 32, 128), dtype=torch.float64, device="cuda"),
+                   torch.empty((4, 32, 128), dtype=torch.float64, device="cuda"),
+                   torch.empty((32, 128), dtype=torch.float64, device="cuda"))
+    a.state_into(qN, qP, phi)
+    hN, hP, hphi = a.state()
+    assert np.array_equal(qN.cpu().numpy(), hN) and np.array_equal(phi.cpu().numpy(), hphi)
+    # restore into a fresh context and continue identically
+    b = sif.Solver(case["cfg"])
+    b.set_state(qN, qP, phi, a.t)
+    a.step_single_dt(2)
+    b.step_single_dt(2)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+
+
+def test_nonphysical_input_is_reported():
+    sif = _sif()
+    case = CASES["explosion"]()
+    pN = case["prim_N"].copy()
+    pN[3] = -1.0e9  # gas pressure below -p_inf
+    s = sif.Solver(case["cfg"]).init_fluids(np.ascontiguousarray(case["phi"]), pN,
+                                            np.ascontiguousarray(case["prim_P"]))
+    with pytest.raises(sif.SifError) as e:
+        s.step_single_dt(1)
+    assert e.value.code == sif.ENONPHYS
+
+
+def test_step_before_init_is_a_state_error():
+    sif = _sif()
+    s = sif.Solver(CASES["static"]()["cfg"])
+    with pytest.raises(sif.SifError) as e:
+        s.step_single_dt(1)
+    assert e.value.code == sif.ESTATE
