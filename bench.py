@@ -1,0 +1,288 @@
+"""Throughput of the cut-cell multi-time-step solver on one GB300.
+
+A step is one cycle of the accelerated method (Sec. 3.1) -- or one step of
+the original single-time-step method with --mode single -- over the whole
+two-fluid problem: interaction step, cut-cell finite-volume stages of both
+fluids, level-set advection and reinitialisation, mixing, flux
+correction.  The headline metric is fluid cell-updates per second: (cell,
+fluid) pairs updated by a finite-volume RK stage, per second.
+
+Default workload: the air-helium shock-bubble interaction on a 1024 x 256
+grid (Mach 1.22 shock, helium bubble R = 0.2), synthetic initial data.
+
+--impl reference times the serial CPU oracle (oracle/) on the same
+workload instead.  Under torchrun every rank advances its own replica
+(independent problems; no exchange), rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP64 flops of one (cell, fluid) finite-volume RK stage: the
+# Lax-Friedrichs split fluxes of every cell (35 per direction), one WENO5
+# face flux per cell and direction (4 components x (2 reconstructions of 70
+# flops + 2)), and the update (10 per component).  1D has one direction.
+FLOPS_PER_UPDATE = {2: 2 * 35 + 2 * 4 * 142 + 4 * 10, 1: 35 + 4 * 142 + 4 * 7}
+# nominal FP64 rate of a GB300: 152 SMs x 4 flops/clock (2 FMA) x 2.07 GHz
+NOMINAL_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+def workload(name, seed=0):
+    from paper_1905_03917_gb300 import inputs
+    if name == "shock_bubble":
+        return inputs.shock_bubble(1024, 256)
+    if name == "underwater_explosion":
+        return inputs.underwater_explosion(2048)
+    if name == "shock_tube":
+        return inputs.shock_tube_1d(400, rk_order=2)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.index, self.samples, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    dist.init_process_group("gloo")
+    return rank, ws, local, dist
+
+
+def cpu_baseline(case, mode, budget_s=20.0, max_steps=200):
+    """The oracle as it stands, serial, on the first steps of the workload."""
+    from oracle import oracle as O
+    o = O.Oracle(case["cfg"]).init(case["phi"], case["prim_N"], case["prim_P"])
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and time.perf_counter() - t0 < budget_s:
+        (o.step_multi_dt if mode == "multi" else o.step_single_dt)(1)
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, ws, _, dist = dist_setup()
+    if rank != 0:
+        return
+    case = workload(args.workload)
+    from oracle import oracle as O
+    o = O.Oracle(case["cfg"]).init(case["phi"], case["prim_N"], case["prim_P"])
+    step = o.step_multi_dt if args.mode == "multi" else o.step_single_dt
+    for _ in range(args.warmup):
+        step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(1)
+    dt = time.perf_counter() - t0
+    # count the same (cell, fluid) updates the GPU path counts for these steps
+    updates = gpu_updates_for(case, args.mode, args.warmup, args.steps)
+    value = updates / dt if updates else None
+    line = {"impl": "reference", "metric": "fluid cell-updates/s (FP64)", "value": value,
+            "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case["name"], "mode": args.mode},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps after {args.warmup} of {case['name']}"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def gpu_updates_for(case, mode, skip, count):
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        from paper_1905_03917_gb300 import sif
+        s = sif.Solver(case["cfg"]).init_fluids(*(np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")))
+        step = s.step_multi_dt if mode == "multi" else s.step_single_dt
+        if skip:
+            step(skip)
+        return step(count)["cell_updates"]
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    rank, ws, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1905_03917_gb300 import sif
+    case = workload(args.workload, seed=rank)
+    arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
+    s = sif.Solver(case["cfg"], device=local).init_fluids(*arrs)
+    step = s.step_multi_dt if args.mode == "multi" else s.step_single_dt
+    for _ in range(args.warmup):
+        step(1)
+    # the library issues its work on the legacy default stream, which is
+    # torch's current stream here; events are recorded on that stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    total_ms, updates, substeps = 0.0, 0, []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = step(1)
+            e1.record()
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            updates += info["cell_updates"]
+            substeps.append(info["substeps"])
+    prof = s.profile_read()
+    s.profile(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        u = torch.tensor([float(updates)], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_ms_all, updates_all = float(t), float(u)
+    else:
+        total_ms_all, updates_all = total_ms, float(updates)
+    value = updates_all / (total_ms_all / 1e3)
+
+    # end to end through the public API: host state in, one step, host state out
+    n = case["cfg"]["nx"] * case["cfg"]["ny"]
+    hq = [torch.empty(4 * n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    hphi = torch.empty(n, dtype=torch.float64).pin_memory()
+    s.state_into(hq[0].numpy(), hq[1].numpy(), hphi.numpy())
+    t_now = s.t
+    e2e_ms, e2e_updates = 0.0, 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_state(hq[0].numpy(), hq[1].numpy(), hphi.numpy(), t_now)
+        info = step(1)
+        s.state_into(hq[0].numpy(), hq[1].numpy(), hphi.numpy())
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        e2e_updates += info["cell_updates"]
+        t_now = info["t"]
+    e2e_bytes = 9 * n * 8
+
+    if rank != 0:
+        return
+    dim = case["cfg"]["dim"]
+    flops = FLOPS_PER_UPDATE[dim]
+    fv_avg_ms = prof["fv_ms"] / max(prof["fv_launches"], 1)
+    fv_units = prof["fv_cell_updates"] / max(prof["fv_launches"], 1)
+    achieved_tf = fv_units * flops / (fv_avg_ms * 1e-3) / 1e12 if fv_avg_ms > 0 else None
+    try:
+        probe = sif.measure_fp64_peak(local)
+    except Exception:
+        probe = None
+    line = {
+        "metric": "fluid cell-updates/s (FP64)", "value": value, "unit": "cell-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": case["name"], "mode": args.mode, "nx": case["cfg"]["nx"],
+                   "ny": case["cfg"]["ny"], "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}", "mean_substeps": float(np.mean(substeps))},
+        "roofline": {"kernel": "k_fv_stage", "bound": "alu", "achieved": achieved_tf,
+                     "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / NOMINAL_FP64_TFLOPS if achieved_tf else None,
+                     "traffic": None, "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
+                     "fp64_probe_tflops": probe, "flops_per_update": flops,
+                     "avg_launch_ms": fv_avg_ms, "updates_per_launch": fv_units,
+                     "share_of_step": prof["fv_ms"] / total_ms if total_ms else None},
+        "gpu_launches": prof["kernel_launches"],
+        "e2e": {"value": e2e_updates / (e2e_ms / 1e3), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+        "clocks": clk.summary(),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        nsteps, secs = cpu_baseline(case, args.mode, budget_s=args.cpu_budget)
+        upd = gpu_updates_for(case, args.mode, 0, nsteps)
+        line["cpu_baseline"] = {"value": upd / secs if upd else None, "unit": "cell-updates/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"first {nsteps} {args.mode}-dt steps of {case['name']} "
+                                          f"({secs:.1f} s serial)"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shock_bubble")
+    ap.add_argument("--mode", default="multi", choices=["multi", "single"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -129,6 +129,40 @@ int sif_set_state(sif_ctx *ctx, const double *q_N, const double *q_P,
 /* Current simulation time. */
 int sif_get_time(sif_ctx *ctx, double *t);
 
+/* Checkpoint: serialise everything a bitwise-identical continuation needs
+ * -- (alpha U) of both fluids, phi, the stencil states of both fluids
+ * (the extension of Sec. 2.3 warm-starts from them) and t -- into a
+ * caller-owned host buffer.  With buf == NULL only *len is set to the
+ * size needed.  Errors: SIF_EINVAL if *len is too small. Synchronises. */
+int sif_save(sif_ctx *ctx, void *buf, size_t *len);
+
+/* Restore a checkpoint written by sif_save for the same grid size;
+ * SIF_EINVAL if the buffer does not match. */
+int sif_load(sif_ctx *ctx, const void *buf, size_t len);
+
+/* Measurement counters of one context (no counterpart in the paper). */
+typedef struct {
+  long long kernel_launches;  /* libsif kernels launched on this context */
+  long long fv_launches;      /* cut-cell finite-volume stage launches among them */
+  double fv_ms;               /* summed CUDA-event time of those launches */
+  long long fv_cell_updates;  /* (cell, fluid) stage updates they performed */
+} sif_profile;
+
+/* enable != 0 resets the counters and starts recording a pair of CUDA
+ * events around every finite-volume stage launch on the context's stream
+ * (at most 65536 pairs; later launches are counted but not timed);
+ * enable == 0 stops recording. */
+int sif_profile_enable(sif_ctx *ctx, int enable);
+
+/* Read the counters (synchronises the stream to resolve the events). */
+int sif_profile_read(sif_ctx *ctx, sif_profile *out);
+
+/* FP64 fused multiply-add throughput of `device` in TFLOP/s (2 flops per
+ * FMA), measured with independent FMA chains on every SM for a few tens of
+ * milliseconds: the ceiling of the FP64-bound finite-volume kernel.  No
+ * counterpart in the paper.  Allocates a small scratch buffer. */
+int sif_measure_fp64_peak(int device, double *tflops);
+
 /* One-line description of the last error on this context (never NULL). */
 const char *sif_last_error(const sif_ctx *ctx);
 

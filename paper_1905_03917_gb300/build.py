@@ -23,6 +23,7 @@ SOURCES = {
     "kernels_band.cu": ["--fmad=false"],
     "kernels_fv.cu": ["--fmad=true"],
     "api.cu": [],
+    "probe.cu": ["--fmad=true"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -6,9 +6,12 @@
 // scheduler's branch decision.
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
+#include <vector>
 
 #include "sif_internal.cuh"
 
@@ -27,10 +30,21 @@ struct sif_ctx {
   Scalars *hsc;      // pinned host mirror
   double *hbuf;      // pinned 8 doubles
   void *pool;        // single device allocation
+  size_t pool_bytes;
+  int debug_sync;    // SIF_DEBUG_SYNC=1: synchronise and check after each phase
+  // profiling: events around the finite-volume stage launches
+  int profiling;
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  size_t ev_used;
+  long long fv_launches, launches0;
+  unsigned long long updates0;
   int inited;
   int last_status;
   char err[256];
 };
+
+static std::atomic<long long> g_launches{0};
+void sif_note_launches(int n) { g_launches += n; }
 
 static void set_err(sif_ctx *c, const char *fmt, ...) {
   va_list ap;
@@ -131,60 +145,67 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.nty = (f.ny + FV_TY - 1) / FV_TY;
   c->NP = (size_t)g.PX * g.PY;
 
-  // one pool: 40 planes + band scratch + integrals + lists + scalars
-  const int nplanes = 8 + 8 + 1 + 5 + 3 + 2 + 8 + 4 + 4 + 4 + 3 + 2;
+  // one pool carved into 256-byte aligned pieces; a first pass over the
+  // same carving (with a null base) measures the exact size
   size_t ncell = (size_t)f.nx * f.ny;
-  size_t bytes_planes = sizeof(double) * c->NP * nplanes;
-  size_t bytes_tmp = sizeof(double) * 4 * ncell;
-  size_t bytes_part = sizeof(double) * (8 * (size_t)f.ny + 16) + 64;
-  size_t bytes_integ = sizeof(double) * 8;
   size_t ntiles = (size_t)g.ntx * g.nty;
-  size_t bytes_lists = sizeof(int) * (4 * ncell + 2 * ntiles + 64);
-  size_t total = bytes_planes + bytes_tmp + bytes_part + bytes_integ + bytes_lists +
-                 sizeof(Scalars) + 4096;
+  char *base = nullptr;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    char *r = base ? base + off : nullptr;
+    off += (b + 255) / 256 * 256;
+    return r;
+  };
+  auto carve = [&]() {
+    auto plane = [&]() { return (double *)take(sizeof(double) * c->NP); };
+    for (int k = 0; k < 2; k++)
+      for (int m = 0; m < 4; m++) c->q[k][m] = plane();
+    for (int k = 0; k < 2; k++)
+      for (int m = 0; m < 4; m++) c->w[k][m] = plane();
+    c->phi = plane();
+    c->alpha = plane();
+    c->ax = plane();
+    c->ay = plane();
+    c->sx = plane();
+    c->sy = plane();
+    for (int m = 0; m < 3; m++) c->xn[m] = plane();
+    for (int m = 0; m < 2; m++) c->ul[m] = plane();
+    for (int k = 0; k < 2; k++)
+      for (int m = 0; m < 4; m++) c->q0[k][m] = plane();
+    for (int m = 0; m < 4; m++) c->prev[m] = plane();
+    for (int m = 0; m < 4; m++) c->fut[m] = plane();
+    for (int m = 0; m < 4; m++) c->qi[m] = plane();
+    for (int m = 0; m < 3; m++) c->xc[m] = plane();
+    c->phi0 = plane();
+    c->phiR = plane();
+    c->tmp = (double *)take(sizeof(double) * 4 * ncell);
+    c->partial = (double *)take(sizeof(double) * 8 * (size_t)f.ny);
+    c->integ = (double *)take(sizeof(double) * 8);
+    c->band_ev = (int *)take(sizeof(int) * ncell);
+    c->band_ls = (int *)take(sizeof(int) * ncell);
+    c->rext_ls = (int *)take(sizeof(int) * ncell);
+    c->cut = (int *)take(sizeof(int) * ncell);
+    c->tiles[0] = (int *)take(sizeof(int) * ntiles);
+    c->tiles[1] = (int *)take(sizeof(int) * ntiles);
+    c->sc = (Scalars *)take(sizeof(Scalars));
+  };
+  carve();
+  size_t total = off;
   if (cudaMalloc(&c->pool, total) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return SIF_ECUDA;
   }
   cudaMemset(c->pool, 0, total);
-  char *p = (char *)c->pool;
-  auto take = [&](size_t b) {
-    char *r = p;
-    p += (b + 255) / 256 * 256;
-    return r;
-  };
-  auto plane = [&]() { return (double *)take(sizeof(double) * c->NP); };
-  for (int k = 0; k < 2; k++)
-    for (int m = 0; m < 4; m++) c->q[k][m] = plane();
-  for (int k = 0; k < 2; k++)
-    for (int m = 0; m < 4; m++) c->w[k][m] = plane();
-  c->phi = plane();
-  c->alpha = plane();
-  c->ax = plane();
-  c->ay = plane();
-  c->sx = plane();
-  c->sy = plane();
-  for (int m = 0; m < 3; m++) c->xn[m] = plane();
-  for (int m = 0; m < 2; m++) c->ul[m] = plane();
-  for (int k = 0; k < 2; k++)
-    for (int m = 0; m < 4; m++) c->q0[k][m] = plane();
-  for (int m = 0; m < 4; m++) c->prev[m] = plane();
-  for (int m = 0; m < 4; m++) c->fut[m] = plane();
-  for (int m = 0; m < 4; m++) c->qi[m] = plane();
-  for (int m = 0; m < 3; m++) c->xc[m] = plane();
-  c->phi0 = plane();
-  c->phiR = plane();
-  c->tmp = (double *)take(bytes_tmp);
-  c->partial = (double *)take(bytes_part);
-  c->integ = (double *)take(bytes_integ);
-  c->band_ev = (int *)take(sizeof(int) * ncell);
-  c->band_ls = (int *)take(sizeof(int) * ncell);
-  c->rext_ls = (int *)take(sizeof(int) * ncell);
-  c->cut = (int *)take(sizeof(int) * ncell);
-  c->tiles[0] = (int *)take(sizeof(int) * ntiles);
-  c->tiles[1] = (int *)take(sizeof(int) * ntiles);
-  c->sc = (Scalars *)take(sizeof(Scalars));
+  c->pool_bytes = total;
+  base = (char *)c->pool;
+  off = 0;
+  carve();
+  if (off != total) {
+    cudaFree(c->pool);
+    delete c;
+    return SIF_ECUDA;
+  }
   if (cudaMallocHost(&c->hsc, sizeof(Scalars)) != cudaSuccess ||
       cudaMallocHost(&c->hbuf, sizeof(double) * 16) != cudaSuccess) {
     cudaGetLastError();
@@ -201,6 +222,8 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     delete c;
     return SIF_ECUDA;
   }
+  const char *dbg = getenv("SIF_DEBUG_SYNC");
+  c->debug_sync = dbg && dbg[0] == '1';
   snprintf(c->err, sizeof(c->err), "ok");
   *out = c;
   return SIF_OK;
@@ -211,6 +234,7 @@ extern "C" void sif_destroy(sif_ctx *c) {
   cudaSetDevice(c->cfg.device);
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   cudaFree(c->pool);
   cudaFreeHost(c->hsc);
   cudaFreeHost(c->hbuf);
@@ -221,6 +245,15 @@ extern "C" const char *sif_last_error(const sif_ctx *c) { return c ? c->err : "n
 
 // ---------------------------------------------------------------------
 // building blocks, in the order of the CPU reference
+
+// opt-in fault localisation: synchronise after a phase and report the
+// first failing one on stderr
+static void dbg(sif_ctx *c, const char *phase) {
+  if (!c->debug_sync) return;
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) fprintf(stderr, "libsif: %s failed: %s\n", phase, cudaGetErrorString(e));
+}
 
 static void ghost_phi(sif_ctx *c) {
   GhostSet gs = {{c->phi}, {0}, 1};
@@ -241,10 +274,12 @@ static void geometry(sif_ctx *c) {
   launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st);
   launch_band_lists(c->g, c->phi, c->band_ev, nullptr, &c->sc->n_band, c->st);
   launch_tile_lists(c->g, c->phi, c->tiles[0], c->tiles[1], c->sc, c->st);
+  dbg(c, "geometry");
 }
 
 static void mix(sif_ctx *c, int k, double *const q[4]) {
   launch_mix(c->g, k, q, c->alpha, c->phi, c->band_ev, &c->sc->n_band, ncell(c), c->tmp, c->st);
+  dbg(c, "mix");
 }
 
 // interaction step for stage states qs of both fluids and the current phi
@@ -253,14 +288,18 @@ static void eval(sif_ctx *c, double *const qs[2][4]) {
   launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
   for (int k = 0; k < 2; k++)
     launch_prim(c->g, k, qs[k], c->w[k], c->alpha, c->tiles[k], ntile(c), c->sc, c->st);
+  dbg(c, "prim");
   for (int k = 0; k < 2; k++)
     launch_extend(c->g, k, c->w[k], c->alpha, c->phi, c->band_ev, ncell(c), c->tmp, c->sc, c->st);
+  dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
   launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, ncell(c), c->xn[0],
                    c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
+  dbg(c, "interface");
   launch_ls_extend(c->g, c->ul[0], c->ul[1], c->phi, c->sx, c->sy, c->band_ev, ncell(c), c->tmp,
                    c->sc, c->st);
+  dbg(c, "ls_extend");
 }
 
 static void copy_planes(sif_ctx *c, double *const dst[4], double *const src[4], int n) {
@@ -271,8 +310,16 @@ static void copy_planes(sif_ctx *c, double *const dst[4], double *const src[4], 
 static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const base[4],
                double *const cur[4], const double *dtp) {
   ghost_w(c, k);
+  bool timed = c->profiling && c->ev_used + 2 <= c->ev.size();
+  if (c->profiling) c->fv_launches++;
+  if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
                   c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), dtp, c->sc, c->st);
+  if (timed) {
+    cudaEventRecord(c->ev[c->ev_used + 1], c->st);
+    c->ev_used += 2;
+  }
+  dbg(c, "fv_stage");
 }
 
 // start of a level-set RK step: keep phi^n and fix the step's band (and
@@ -285,10 +332,12 @@ static void ls_begin(sif_ctx *c) {
 static void ls_stage(sif_ctx *c, int s, const double *dtp) {
   launch_ls_stage(c->g, s, c->cfg.rk_order, c->phi, c->phi0, c->ul[0], c->ul[1], c->band_ls,
                   &c->sc->n_band_ls, ncell(c), c->tmp, dtp, c->st);
+  dbg(c, "ls_stage");
 }
 
 static void reinit(sif_ctx *c) {
   launch_reinit(c->g, c->phi, c->phiR, c->rext_ls, &c->sc->n_rext, ncell(c), c->tmp, c->st);
+  dbg(c, "reinit");
 }
 
 // one RK step of both fluids and the level set, the first interaction
@@ -604,5 +653,128 @@ extern "C" int sif_get_time(sif_ctx *c, double *t) {
   int rc = read_scalars(c);
   if (rc) return rc;
   *t = c->hsc->t;
+  return SIF_OK;
+}
+
+// ---------------------------------------------------------------------
+// checkpoint: header + 17 interior planes (qN, qP, wN, wP, phi)
+
+struct CkptHeader {
+  char magic[8];
+  int version, nx, ny, nplanes;
+  double t;
+};
+
+static const int kCkptPlanes = 17;
+
+static double *ckpt_plane(sif_ctx *c, int i) {
+  if (i < 4) return c->q[0][i];
+  if (i < 8) return c->q[1][i - 4];
+  if (i < 12) return c->w[0][i - 8];
+  if (i < 16) return c->w[1][i - 12];
+  return c->phi;
+}
+
+extern "C" int sif_save(sif_ctx *c, void *buf, size_t *len) {
+  if (!c || !len) return SIF_EINVAL;
+  size_t n = (size_t)ncell(c);
+  size_t need = sizeof(CkptHeader) + sizeof(double) * n * kCkptPlanes;
+  if (!buf) {
+    *len = need;
+    return SIF_OK;
+  }
+  if (*len < need) {
+    set_err(c, "checkpoint buffer too small (%zu < %zu)", *len, need);
+    return SIF_EINVAL;
+  }
+  if (!c->inited) {
+    set_err(c, "state not initialised");
+    return SIF_ESTATE;
+  }
+  cudaSetDevice(c->cfg.device);
+  int rc = read_scalars(c);
+  if (rc) return rc;
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "SIFCKPT", 8);
+  h.version = 1;
+  h.nx = c->g.nx;
+  h.ny = c->g.ny;
+  h.nplanes = kCkptPlanes;
+  h.t = c->hsc->t;
+  memcpy(buf, &h, sizeof(h));
+  double *out = (double *)((char *)buf + sizeof(h));
+  for (int i = 0; i < kCkptPlanes && !rc; i++) rc = get_plane(c, out + i * n, ckpt_plane(c, i), SIF_HOST);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  *len = need;
+  return SIF_OK;
+}
+
+extern "C" int sif_load(sif_ctx *c, const void *buf, size_t len) {
+  if (!c || !buf) return SIF_EINVAL;
+  size_t n = (size_t)ncell(c);
+  size_t need = sizeof(CkptHeader) + sizeof(double) * n * kCkptPlanes;
+  CkptHeader h;
+  if (len < sizeof(h)) return SIF_EINVAL;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, "SIFCKPT", 8) != 0 || h.version != 1 || h.nx != c->g.nx ||
+      h.ny != c->g.ny || h.nplanes != kCkptPlanes || len < need) {
+    set_err(c, "checkpoint does not match this context");
+    return SIF_EINVAL;
+  }
+  cudaSetDevice(c->cfg.device);
+  const double *in = (const double *)((const char *)buf + sizeof(h));
+  int rc = SIF_OK;
+  for (int i = 0; i < kCkptPlanes && !rc; i++) rc = put_plane(c, ckpt_plane(c, i), in + i * n, SIF_HOST);
+  if (rc) return rc;
+  geometry(c);
+  CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), c->st));
+  c->hbuf[0] = h.t;
+  CK(cudaMemcpyAsync(&c->sc->t, c->hbuf, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  rc = check_launch(c, "load");
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  c->inited = 1;
+  return SIF_OK;
+}
+
+// ---------------------------------------------------------------------
+// measurement counters
+
+extern "C" int sif_profile_enable(sif_ctx *c, int enable) {
+  if (!c) return SIF_EINVAL;
+  cudaSetDevice(c->cfg.device);
+  if (enable) {
+    if (c->ev.empty()) {
+      c->ev.resize(2 * 65536);
+      for (auto &e : c->ev) CK(cudaEventCreate(&e));
+    }
+    int rc = read_scalars(c);
+    if (rc) return rc;
+    c->ev_used = 0;
+    c->fv_launches = 0;
+    c->launches0 = g_launches.load();
+    c->updates0 = c->hsc->updates;
+  }
+  c->profiling = enable ? 1 : 0;
+  return SIF_OK;
+}
+
+extern "C" int sif_profile_read(sif_ctx *c, sif_profile *out) {
+  if (!c || !out) return SIF_EINVAL;
+  cudaSetDevice(c->cfg.device);
+  int rc = read_scalars(c);
+  if (rc) return rc;
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+    ms += t;
+  }
+  out->kernel_launches = g_launches.load() - c->launches0;
+  out->fv_launches = c->fv_launches;
+  out->fv_ms = ms;
+  out->fv_cell_updates = (long long)(c->hsc->updates - c->updates0);
   return SIF_OK;
 }

@@ -86,6 +86,7 @@ void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
                  cudaStream_t st) {
   k_prim<<<tile_cap, FV_TX * FV_TY, 0, st>>>(g, k, q[0], q[1], q[2], q[3], w[0], w[1], w[2],
                                              w[3], alpha, tiles, sc->n_tiles, sc);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -163,6 +164,7 @@ void launch_extend(const Grid &g, int k, double *const w[4], const double *alpha
     k_extend_scatter<<<blocks, 256, 0, st>>>(g, k, band, &sc->n_band, tmp, w[0], w[1], w[2],
                                             w[3], alpha, it == g.ext_iters - 1, sc);
   }
+  sif_note_launches(2 * g.ext_iters);
 }
 
 // ---------------------------------------------------------------------
@@ -213,6 +215,7 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
   int blocks = grid_for(cut_cap, 128, 1216);
   k_interface<<<blocks, 128, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
                                       phi, sx, sy, cut, &sc->n_cut, xn0, xn1, xn2, ul0, ul1, sc);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -278,6 +281,7 @@ void launch_ls_extend(const Grid &g, double *ul0, double *ul1, const double *phi
     k_ls_extend_sweep<<<blocks, 256, 0, st>>>(g, ul0, ul1, phi, sx, sy, band, &sc->n_band, tmp);
     k_band_scatter2<<<blocks, 256, 0, st>>>(band, &sc->n_band, tmp, ul0, ul1);
   }
+  sif_note_launches(2 * g.ext_iters);
 }
 
 // ---------------------------------------------------------------------
@@ -330,6 +334,7 @@ void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *ph
   launch_fill_ghost(g, gs, st);
   k_ls_stage<<<blocks, 256, 0, st>>>(g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
   k_band_scatter2<<<blocks, 256, 0, st>>>(band, nband, tmp, phi, nullptr);
+  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------
@@ -413,6 +418,7 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
     k_reinit<<<blocks, 256, 0, st>>>(g, phi, phi0, rext, nrext, tmp);
     k_band_scatter2<<<blocks, 256, 0, st>>>(rext, nrext, tmp, phi, nullptr);
   }
+  sif_note_launches(2 * g.reinit_iters);
 }
 
 // ---------------------------------------------------------------------
@@ -445,6 +451,7 @@ void launch_record(const Grid &, int shared, const int *cut, int cut_cap, const 
                    Scalars *sc, cudaStream_t st) {
   int blocks = grid_for(cut_cap, 128, 1216);
   k_record<<<blocks, 128, 0, st>>>(shared, cut, &sc->n_cut, xn0, xn1, xn2, xc0, xc1, xc2, sc);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -473,6 +480,7 @@ void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
   k_interp<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g, qi[0], qi[1], qi[2], qi[3], prev[0],
                                                       prev[1], prev[2], prev[3], fut[0], fut[1],
                                                       fut[2], fut[3], thp);
+  sif_note_launches(1);
 }
 
 // final interfacial flux correction of fluid 1
@@ -493,6 +501,7 @@ void launch_correction(const Grid &g, double *const q[4], const double *xc0, con
                        const double *xc2, cudaStream_t st) {
   int n = g.nx * g.ny;
   k_correction<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g, q[1], q[2], q[3], xc0, xc1, xc2);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -531,6 +540,7 @@ void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], d
   dim3 grid((g.ny + 7) / 8, 8);
   k_integrals_rows<<<grid, 256, 0, st>>>(g, tab, partial);
   k_integrals_final<<<1, 32, 0, st>>>(g, partial, out);
+  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------
@@ -614,4 +624,5 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
 
 void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st) {
   k_sched<<<1, 32, 0, st>>>(op, sc, cfl, thr, force1);
+  sif_note_launches(1);
 }

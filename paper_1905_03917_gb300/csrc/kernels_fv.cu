@@ -240,4 +240,5 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   A.lfx_dummy = 0.0;
   A.sc = sc;
   k_fv_stage<<<tile_cap, FV_TX * FV_TY, smem, st>>>(A);
+  sif_note_launches(1);
 }

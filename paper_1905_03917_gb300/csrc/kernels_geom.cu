@@ -59,6 +59,7 @@ void launch_fill_ghost(const Grid &g, const GhostSet &s, cudaStream_t st) {
   k_ghost_x<<<(nx_threads + 255) / 256, 256, 0, st>>>(g, s);
   int ny_threads = (g.nx + 2 * SIF_GH) * SIF_GH * s.n;
   k_ghost_y<<<(ny_threads + 255) / 256, 256, 0, st>>>(g, s);
+  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------
@@ -112,6 +113,7 @@ void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax
   cudaMemsetAsync(&sc->n_cut, 0, sizeof(int), st);
   int n = (g.nx + 1) * (g.ny + 1);
   k_geometry<<<(n + 255) / 256, 256, 0, st>>>(g, phi, alpha, ax, ay, sx, sy, cut_list, &sc->n_cut);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -145,6 +147,7 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
   cudaMemsetAsync(counts, 0, 2 * sizeof(int), st);
   int n = g.nx * g.ny;
   k_band<<<(n + 255) / 256, 256, 0, st>>>(g, phi, band, rext, &counts[0], &counts[1]);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -177,6 +180,7 @@ void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles
                        cudaStream_t st) {
   cudaMemsetAsync(sc->n_tiles, 0, 2 * sizeof(int), st);
   k_tiles<<<g.ntx * g.nty, 128, 0, st>>>(g, phi, tiles0, tiles1, sc->n_tiles);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -286,6 +290,7 @@ void launch_mix(const Grid &g, int k, double *const q[4], const double *alpha, c
   k_mix_gather<<<blocks, 256, 0, st>>>(g, k, q[0], q[1], q[2], q[3], alpha, phi, band, nband,
                                       tmp);
   k_band_scatter4<<<blocks, 256, 0, st>>>(band, nband, tmp, q[0], q[1], q[2], q[3]);
+  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------
@@ -320,4 +325,5 @@ void launch_init_state(const Grid &g, double *const qN[4], double *const qP[4],
   k_init_q<<<(n + 255) / 256, 256, 0, st>>>(g, qN[0], qN[1], qN[2], qN[3], qP[0], qP[1], qP[2],
                                             qP[3], wN[0], wN[1], wN[2], wN[3], wP[0], wP[1],
                                             wP[2], wP[3], alpha);
+  sif_note_launches(1);
 }

@@ -248,7 +248,9 @@ __device__ inline int riemann_solve(double rl, double ul, double pl, double gl, 
 }
 
 // ---------------------------------------------------------------------
-// host-side launch wrappers (defined in the .cu files)
+// host-side launch wrappers (defined in the .cu files); each reports the
+// number of kernels it launched to the profiling counter
+void sif_note_launches(int n);
 
 // ghost layers of up to 8 planes; vel[m]: 0 scalar, 1 x-velocity, 2 y-velocity
 struct GhostSet {

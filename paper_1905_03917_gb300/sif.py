@@ -22,7 +22,8 @@ _NAMES = {EINVAL: "SIF_EINVAL", ECUDA: "SIF_ECUDA", ENONPHYS: "SIF_ENONPHYS",
 
 EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_multi_dt",
            "sif_integrals", "sif_get_state", "sif_set_state", "sif_get_time",
-           "sif_last_error", "sif_destroy"]
+           "sif_last_error", "sif_destroy", "sif_save", "sif_load",
+           "sif_profile_enable", "sif_profile_read", "sif_measure_fp64_peak"]
 
 
 class SifError(RuntimeError):
@@ -44,6 +45,11 @@ class Config(ctypes.Structure):
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("fv_launches", ctypes.c_longlong),
+                ("fv_ms", ctypes.c_double), ("fv_cell_updates", ctypes.c_longlong)]
 
 
 class CycleInfo(ctypes.Structure):
@@ -78,8 +84,15 @@ def load(path: str | None = None):
     L.sif_last_error.restype = ctypes.c_char_p
     L.sif_destroy.argtypes = [P]
     L.sif_destroy.restype = None
+    L.sif_save.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+    L.sif_load.argtypes = [P, P, ctypes.c_size_t]
+    L.sif_profile_enable.argtypes = [P, I]
+    L.sif_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
+    L.sif_measure_fp64_peak.argtypes = [I, ctypes.POINTER(D)]
     for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
-              L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time):
+              L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time,
+              L.sif_save, L.sif_load, L.sif_profile_enable, L.sif_profile_read,
+              L.sif_measure_fp64_peak):
         f.restype = I
     _lib = L
     return L
@@ -123,6 +136,15 @@ def _ptr(a):
             raise ValueError("device tensors must be contiguous float64")
         return a.data_ptr(), DEVICE
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def measure_fp64_peak(device=0) -> float:
+    """Measured FP64 FMA throughput of the device in TFLOP/s."""
+    v = ctypes.c_double()
+    rc = load().sif_measure_fp64_peak(int(device), ctypes.byref(v))
+    if rc != OK:
+        raise SifError(rc, "FP64 throughput probe failed")
+    return v.value
 
 
 class Solver:
@@ -198,6 +220,28 @@ class Solver:
     def set_state(self, qN, qP, phi, t=0.0):
         (a, ka), (b, kb), (c, kc) = _ptr(qN), _ptr(qP), _ptr(phi)
         self._check(load().sif_set_state(self._h, a, b, c, float(t), ka))
+
+    def save(self) -> bytes:
+        """Checkpoint (host bytes) of everything a bitwise continuation needs."""
+        n = ctypes.c_size_t(0)
+        self._check(load().sif_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(load().sif_save(self._h, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def profile(self, enable: bool = True):
+        self._check(load().sif_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        p = Profile()
+        self._check(load().sif_profile_read(self._h, ctypes.byref(p)))
+        return {"kernel_launches": p.kernel_launches, "fv_launches": p.fv_launches,
+                "fv_ms": p.fv_ms, "fv_cell_updates": p.fv_cell_updates}
+
+    def load_checkpoint(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(load().sif_load(self._h, ctypes.cast(buf, ctypes.c_void_p), len(data)))
+        return self
 
     @property
     def t(self):
