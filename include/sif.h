@@ -163,6 +163,29 @@ int sif_profile_read(sif_ctx *ctx, sif_profile *out);
  * counterpart in the paper.  Allocates a small scratch buffer. */
 int sif_measure_fp64_peak(int device, double *tflops);
 
+/* Conserved totals of caller-provided device planes without allocating
+ * anything -- for callers that cannot allocate device memory when they
+ * need the totals (e.g. a host framework whose caching allocator already
+ * holds the GPU's free memory, or a hook inside a time-stepping loop where
+ * an allocation would synchronise the device).  The paper has no
+ * counterpart; this is a variant of the reduction behind sif_integrals.
+ *   q_N, q_P: device pointers, 4 planes (mass, x-mom, y-mom, energy) of
+ *             nx*ny doubles each, x fastest, no ghost cells (the layout
+ *             sif_get_state writes);
+ *   out:      device pointer to 8 doubles, out[k*4+m] = sum q_k,m dx dy;
+ *   stream:   cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Scratch: a 1 MiB file-scope device array holds the row partial sums, so
+ * ny may not exceed 16384 (SIF_EINVAL beyond that, or for nx, ny < 1).
+ * Every GPU that loads the library keeps that array until the process
+ * exits.  The first call on a device looks up the array's device address
+ * with that device current; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (on
+ * different streams or devices' peers) race on it and must be ordered by
+ * the caller.  Each call overwrites every partial sum it reads, so nothing
+ * needs clearing between calls.  Calls no cudaMalloc/cudaFree. */
+int sif_integrals_noalloc(const double *q_N, const double *q_P, int nx, int ny, double dx,
+                          double dy, double *out, void *stream);
+
 /* One-line description of the last error on this context (never NULL). */
 const char *sif_last_error(const sif_ctx *ctx);
 

@@ -24,6 +24,7 @@ SOURCES = {
     "kernels_fv.cu": ["--fmad=true"],
     "api.cu": [],
     "probe.cu": ["--fmad=true"],
+    "noalloc.cu": ["--fmad=false"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

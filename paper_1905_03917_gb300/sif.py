@@ -23,7 +23,8 @@ _NAMES = {EINVAL: "SIF_EINVAL", ECUDA: "SIF_ECUDA", ENONPHYS: "SIF_ENONPHYS",
 EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_multi_dt",
            "sif_integrals", "sif_get_state", "sif_set_state", "sif_get_time",
            "sif_last_error", "sif_destroy", "sif_save", "sif_load",
-           "sif_profile_enable", "sif_profile_read", "sif_measure_fp64_peak"]
+           "sif_profile_enable", "sif_profile_read", "sif_measure_fp64_peak",
+           "sif_integrals_noalloc"]
 
 
 class SifError(RuntimeError):
@@ -89,10 +90,11 @@ def load(path: str | None = None):
     L.sif_profile_enable.argtypes = [P, I]
     L.sif_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
     L.sif_measure_fp64_peak.argtypes = [I, ctypes.POINTER(D)]
+    L.sif_integrals_noalloc.argtypes = [P, P, I, I, D, D, P, P]
     for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
               L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time,
               L.sif_save, L.sif_load, L.sif_profile_enable, L.sif_profile_read,
-              L.sif_measure_fp64_peak):
+              L.sif_measure_fp64_peak, L.sif_integrals_noalloc):
         f.restype = I
     _lib = L
     return L
@@ -145,6 +147,19 @@ def measure_fp64_peak(device=0) -> float:
     if rc != OK:
         raise SifError(rc, "FP64 throughput probe failed")
     return v.value
+
+
+def integrals_noalloc(q_N, q_P, dx, dy, out, stream=None):
+    """Totals of device planes (torch CUDA tensors of shape (4, ny, nx))
+    into the device tensor `out` (8 doubles) without any device
+    allocation; see sif_integrals_noalloc in include/sif.h."""
+    (a, ka), (b, kb), (o, ko) = _ptr(q_N), _ptr(q_P), _ptr(out)
+    if not (ka == kb == ko == DEVICE):
+        raise ValueError("integrals_noalloc takes device tensors")
+    ny, nx = q_N.shape[-2], q_N.shape[-1]
+    rc = load().sif_integrals_noalloc(a, b, int(nx), int(ny), float(dx), float(dy), o, stream)
+    if rc != OK:
+        raise SifError(rc, "sif_integrals_noalloc rejected the call")
 
 
 class Solver:
