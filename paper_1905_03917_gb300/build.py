@@ -21,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 SOURCES = {
     "kernels_geom.cu": ["--fmad=false"],
     "kernels_band.cu": ["--fmad=false"],
+    "kernels_plan.cu": ["--fmad=false"],
     "kernels_fv.cu": ["--fmad=true"],
     "api.cu": [],
     "probe.cu": ["--fmad=true"],

@@ -22,7 +22,11 @@ struct sif_ctx {
   size_t NP;
   double *q[2][4], *w[2][4], *phi, *alpha, *ax, *ay, *sx, *sy, *xn[3], *ul[2];
   double *q0[2][4], *prev[4], *fut[4], *qi[4], *xc[3], *phi0, *phiR;
-  double *tmp;       // band-indexed scratch, 4 planes
+  double *tmp;       // band-indexed scratch, 8 planes
+  int *bandmap;      // cell -> position in the interaction band, -1 outside
+  ExtPlan *ext_plan; // 3 x ncell
+  MixPlan *mix_plan; // 2 x ncell
+  int band_work;     // recent interaction-band size, sizes band grids
   double *partial;   // integrals: 8*ny partial sums + pointer table
   double *integ;     // 8 totals
   int *band_ev, *band_ls, *rext_ls, *cut, *tiles[2];
@@ -178,7 +182,10 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     for (int m = 0; m < 3; m++) c->xc[m] = plane();
     c->phi0 = plane();
     c->phiR = plane();
-    c->tmp = (double *)take(sizeof(double) * 4 * ncell);
+    c->tmp = (double *)take(sizeof(double) * 8 * ncell);
+    c->bandmap = (int *)take(sizeof(int) * c->NP);
+    c->ext_plan = (ExtPlan *)take(sizeof(ExtPlan) * 3 * ncell);
+    c->mix_plan = (MixPlan *)take(sizeof(MixPlan) * 2 * ncell);
     c->partial = (double *)take(sizeof(double) * 8 * (size_t)f.ny);
     c->integ = (double *)take(sizeof(double) * 8);
     c->band_ev = (int *)take(sizeof(int) * ncell);
@@ -197,10 +204,12 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     return SIF_ECUDA;
   }
   cudaMemset(c->pool, 0, total);
+  c->band_work = (int)ncell;
   c->pool_bytes = total;
   base = (char *)c->pool;
   off = 0;
   carve();
+  cudaMemset(c->bandmap, 0xff, sizeof(int) * c->NP);
   if (off != total) {
     cudaFree(c->pool);
     delete c;
@@ -268,18 +277,31 @@ static void ghost_w(sif_ctx *c, int k) {
 static int ncell(const sif_ctx *c) { return c->g.nx * c->g.ny; }
 static int ntile(const sif_ctx *c) { return c->g.ntx * c->g.nty; }
 
-// level set changed: ghosts, geometry, cut list, band list, tile lists
+// level set changed: ghosts, geometry, cut list, band list and map, tile lists
 static void geometry(sif_ctx *c) {
   ghost_phi(c);
   launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st);
-  launch_band_lists(c->g, c->phi, c->band_ev, nullptr, &c->sc->n_band, c->st);
+  launch_band_map(c->g, c->phi, c->band_ev, c->bandmap, &c->sc->n_band, c->st);
   launch_tile_lists(c->g, c->phi, c->tiles[0], c->tiles[1], c->sc, c->st);
   dbg(c, "geometry");
 }
 
-static void mix(sif_ctx *c, int k, double *const q[4]) {
-  launch_mix(c->g, k, q, c->alpha, c->phi, c->band_ev, &c->sc->n_band, ncell(c), c->tmp, c->st);
+// grids of the band kernels are sized from the last band size seen on the
+// host (the kernels loop over the device count, so any size is correct)
+static int band_work(const sif_ctx *c) {
+  int w = c->band_work + c->band_work / 4 + 1024;
+  return w < ncell(c) ? w : ncell(c);
+}
+
+// small-cell mixing of the fluids in mask (bit k = fluid k)
+static void mix2(sif_ctx *c, int mask, double *const qN[4], double *const qP[4]) {
+  launch_mix2(c->g, mask, qN, qP, c->alpha, c->phi, c->band_ev, c->bandmap, &c->sc->n_band,
+              c->mix_plan, ncell(c), band_work(c), c->tmp, c->st);
   dbg(c, "mix");
+}
+static void mix_both(sif_ctx *c) { mix2(c, 3, c->q[0], c->q[1]); }
+static void mix_one(sif_ctx *c, int k, double *const q[4]) {
+  mix2(c, 1 << k, k == 0 ? q : nullptr, k == 1 ? q : nullptr);
 }
 
 // interaction step for stage states qs of both fluids and the current phi
@@ -289,16 +311,18 @@ static void eval(sif_ctx *c, double *const qs[2][4]) {
   for (int k = 0; k < 2; k++)
     launch_prim(c->g, k, qs[k], c->w[k], c->alpha, c->tiles[k], ntile(c), c->sc, c->st);
   dbg(c, "prim");
-  for (int k = 0; k < 2; k++)
-    launch_extend(c->g, k, c->w[k], c->alpha, c->phi, c->band_ev, ncell(c), c->tmp, c->sc, c->st);
+  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->ext_plan,
+                   ncell(c), band_work(c), c->st);
+  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
+                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->sc, c->st);
   dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
   launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, ncell(c), c->xn[0],
                    c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
   dbg(c, "interface");
-  launch_ls_extend(c->g, c->ul[0], c->ul[1], c->phi, c->sx, c->sy, c->band_ev, ncell(c), c->tmp,
-                   c->sc, c->st);
+  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
+                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->sc, c->st);
   dbg(c, "ls_extend");
 }
 
@@ -352,8 +376,7 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp) {
     ls_stage(c, s, dtp);
     if (s == S) reinit(c);
     geometry(c);
-    mix(c, 0, c->q[0]);
-    mix(c, 1, c->q[1]);
+    mix_both(c);
   }
 }
 
@@ -423,6 +446,7 @@ extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycl
 static int read_scalars(sif_ctx *c) {
   CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  c->band_work = c->hsc->n_band;
   return SIF_OK;
 }
 
@@ -464,7 +488,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     if (sub > 1) {
       launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
       geometry(c);
-      mix(c, f1, c->qi);
+      mix_one(c, f1, c->qi);
       for (int m = 0; m < 4; m++) {
         qs[f1][m] = c->qi[m];
         qs[f2][m] = c->q[f2][m];
@@ -491,13 +515,13 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
     ls_stage(c, 1, &c->sc->dt2);
     geometry(c);
-    mix(c, f2, c->q[f2]);
+    mix_one(c, f2, c->q[f2]);
     if (last) {
-      mix(c, f1, c->fut);
+      mix_one(c, f1, c->fut);
       for (int m = 0; m < 4; m++) qs[f1][m] = c->fut[m];
     } else {
       launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
-      mix(c, f1, c->qi);
+      mix_one(c, f1, c->qi);
       for (int m = 0; m < 4; m++) qs[f1][m] = c->qi[m];
     }
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
@@ -512,13 +536,12 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     if (last) {
       if (c->cfg.flux_correction) launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
       geometry(c);
-      mix(c, f1, c->q[f1]);
-      mix(c, f2, c->q[f2]);
+      mix_both(c);
       break;
     }
     launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
     geometry(c);
-    mix(c, f2, c->q[f2]);
+    mix_one(c, f2, c->q[f2]);
     if (sub > 100000) {
       set_err(c, "sub-cycle count exceeded 100000");
       return SIF_ETIMEOUT;
@@ -584,8 +607,7 @@ extern "C" int sif_init_fluids(sif_ctx *c, const double *phi, const double *pN, 
   if (rc) return rc;
   geometry(c);
   launch_init_state(c->g, c->q[0], c->q[1], c->w[0], c->w[1], c->alpha, c->st);
-  mix(c, 0, c->q[0]);
-  mix(c, 1, c->q[1]);
+  mix_both(c);
   CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), c->st));
   rc = check_launch(c, "init");
   if (rc) return rc;

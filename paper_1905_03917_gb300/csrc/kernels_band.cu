@@ -58,10 +58,11 @@ __global__ void k_prim(Grid g, int k, const double *__restrict__ q0, const doubl
     double a = vol_k(alpha, k, c);
     if (a > SIF_ALPHA_REAL) {
       double gm = g.gamma[k], pi = g.pinf[k];
-      double rho = q0[c] / a;
+      // a full cell divides by exactly 1: skip those two divisions
+      double rho = a == 1.0 ? q0[c] : q0[c] / a;
       double u = q1[c] / q0[c];
       double v = q2[c] / q0[c];
-      double E = q3[c] / a;
+      double E = a == 1.0 ? q3[c] : q3[c] / a;
       double p = (gm - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - gm * pi;
       if (!(rho > 0.0) || !(p + pi > 0.0)) atomicOr(&sc->err, DERR_NONPHYS);
       w0[c] = rho;
@@ -87,84 +88,6 @@ void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
   k_prim<<<tile_cap, FV_TX * FV_TY, 0, st>>>(g, k, q[0], q[1], q[2], q[3], w[0], w[1], w[2],
                                              w[3], alpha, tiles, sc->n_tiles, sc);
   sif_note_launches(1);
-}
-
-// ---------------------------------------------------------------------
-// extension: Jacobi sweeps of the steady upwind discretisation of
-// n_k . grad(W) = 0 into band cells that hold no fluid k
-
-__global__ void k_extend_sweep(Grid g, int k, const double *__restrict__ w0,
-                               const double *__restrict__ w1, const double *__restrict__ w2,
-                               const double *__restrict__ w3, const double *__restrict__ alpha,
-                               const double *__restrict__ phi, const int *__restrict__ band,
-                               const int *nband, double *tmp) {
-  int n = *nband;
-  const double *w[4] = {w0, w1, w2, w3};
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
-    double out[4] = {w0[c], w1[c], w2[c], w3[c]};
-    if (!(vol_k(alpha, k, c) > SIF_ALPHA_REAL)) {
-      double nxv, nyv;
-      unit_normal(g, phi, i, j, nxv, nyv);
-      if (k == 0) {
-        nxv = -nxv;
-        nyv = -nyv;
-      }
-      int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
-      double wx = fabs(nxv) / g.dx;
-      double wy = g.dim == 2 ? fabs(nyv) / g.dy : 0.0;
-      if (!inside(g, i + sx, j)) wx = 0.0;
-      if (!inside(g, i, j + sy)) wy = 0.0;
-      double den = wx + wy;
-      if (den > 0.0) {
-        int cx = gidx(g, i + sx, j), cy = gidx(g, i, j + sy);
-        for (int m = 0; m < 4; m++) {
-          double num = 0.0;
-          if (wx > 0.0) num += wx * w[m][cx];
-          if (wy > 0.0) num += wy * w[m][cy];
-          out[m] = num / den;
-        }
-      }
-    }
-    for (int m = 0; m < 4; m++) tmp[(size_t)m * n + idx] = out[m];
-  }
-}
-
-__global__ void k_extend_scatter(Grid g, int k, const int *__restrict__ band, const int *nband,
-                                 const double *tmp, double *w0, double *w1, double *w2,
-                                 double *w3, const double *__restrict__ alpha, int last,
-                                 Scalars *sc) {
-  int n = *nband;
-  double lx = 0.0, ly = 0.0;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    double r = tmp[idx], u = tmp[(size_t)n + idx], v = tmp[(size_t)2 * n + idx],
-           p = tmp[(size_t)3 * n + idx];
-    w0[c] = r;
-    w1[c] = u;
-    w2[c] = v;
-    w3[c] = p;
-    if (last && !(vol_k(alpha, k, c) > SIF_ALPHA_REAL)) {
-      double cs = sqrt(fmax(g.gamma[k] * (p + g.pinf[k]) / r, 0.0));
-      lx = fmax(lx, fabs(u) + cs);
-      ly = fmax(ly, fabs(v) + cs);
-    }
-  }
-  if (last) block_max2(lx, ly, &sc->lf[k][0], &sc->lf[k][1]);
-}
-
-void launch_extend(const Grid &g, int k, double *const w[4], const double *alpha,
-                   const double *phi, const int *band, int band_cap, double *tmp, Scalars *sc,
-                   cudaStream_t st) {
-  int blocks = grid_for(band_cap, 256, 1216);
-  for (int it = 0; it < g.ext_iters; it++) {
-    k_extend_sweep<<<blocks, 256, 0, st>>>(g, k, w[0], w[1], w[2], w[3], alpha, phi, band,
-                                          &sc->n_band, tmp);
-    k_extend_scatter<<<blocks, 256, 0, st>>>(g, k, band, &sc->n_band, tmp, w[0], w[1], w[2],
-                                            w[3], alpha, it == g.ext_iters - 1, sc);
-  }
-  sif_note_launches(2 * g.ext_iters);
 }
 
 // ---------------------------------------------------------------------
@@ -218,51 +141,6 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
   sif_note_launches(1);
 }
 
-// ---------------------------------------------------------------------
-// level-set velocity carried from the cut cells through the band
-
-__global__ void k_ls_extend_sweep(Grid g, const double *__restrict__ u0,
-                                  const double *__restrict__ u1, const double *__restrict__ phi,
-                                  const double *__restrict__ sx, const double *__restrict__ sy,
-                                  const int *__restrict__ band, const int *nband, double *tmp) {
-  int n = *nband;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
-    double o0 = u0[c], o1 = u1[c];
-    if (sx[c] == 0.0 && sy[c] == 0.0) {
-      double nxv, nyv;
-      unit_normal(g, phi, i, j, nxv, nyv);
-      if (phi[c] >= 0.0) {
-        nxv = -nxv;
-        nyv = -nyv;
-      }
-      int six = nxv >= 0.0 ? 1 : -1, siy = nyv >= 0.0 ? 1 : -1;
-      double wx = fabs(nxv) / g.dx;
-      double wy = g.dim == 2 ? fabs(nyv) / g.dy : 0.0;
-      if (!inside(g, i + six, j)) wx = 0.0;
-      if (!inside(g, i, j + siy)) wy = 0.0;
-      double den = wx + wy;
-      if (den > 0.0) {
-        int cx = gidx(g, i + six, j), cy = gidx(g, i, j + siy);
-        double a0 = 0.0, a1 = 0.0;
-        if (wx > 0.0) {
-          a0 += wx * u0[cx];
-          a1 += wx * u1[cx];
-        }
-        if (wy > 0.0) {
-          a0 += wy * u0[cy];
-          a1 += wy * u1[cy];
-        }
-        o0 = a0 / den;
-        o1 = a1 / den;
-      }
-    }
-    tmp[idx] = o0;
-    tmp[(size_t)n + idx] = o1;
-  }
-}
-
 __global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, const double *tmp,
                                 double *a, double *b) {
   int n = *nband;
@@ -271,17 +149,6 @@ __global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, 
     a[c] = tmp[idx];
     if (b) b[c] = tmp[(size_t)n + idx];
   }
-}
-
-void launch_ls_extend(const Grid &g, double *ul0, double *ul1, const double *phi,
-                      const double *sx, const double *sy, const int *band, int band_cap,
-                      double *tmp, Scalars *sc, cudaStream_t st) {
-  int blocks = grid_for(band_cap, 256, 1216);
-  for (int it = 0; it < g.ext_iters; it++) {
-    k_ls_extend_sweep<<<blocks, 256, 0, st>>>(g, ul0, ul1, phi, sx, sy, band, &sc->n_band, tmp);
-    k_band_scatter2<<<blocks, 256, 0, st>>>(band, &sc->n_band, tmp, ul0, ul1);
-  }
-  sif_note_launches(2 * g.ext_iters);
 }
 
 // ---------------------------------------------------------------------

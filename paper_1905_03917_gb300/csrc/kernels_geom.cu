@@ -86,8 +86,29 @@ __global__ void k_geometry(Grid g, const double *__restrict__ p, double *alpha, 
   bool valid = j <= g.ny;
   bool is_cut = false;
   int c = 0;
+  bool uniform = false;
   if (valid) {
     c = gidx(g, i, j);
+    // away from the interface all nine cells around the four corners share
+    // a sign: every corner has it too, so the cell is full or empty
+    int npos = 0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; dj++)
+#pragma unroll
+      for (int di = -1; di <= 1; di++) npos += p[gidx(g, i + di, j + dj)] >= 0.0;
+    if (npos == 9 || npos == 0) {
+      uniform = true;
+      double v = npos == 9 ? 1.0 : 0.0;
+      if (j < g.ny) ax[c] = v;
+      if (i < g.nx) ay[c] = v;
+      if (i < g.nx && j < g.ny) {
+        alpha[c] = v;
+        sx[c] = 0.0;
+        sy[c] = 0.0;
+      }
+    }
+  }
+  if (valid && !uniform) {
     double c00 = corner_phi(g, p, i, j);
     double c01 = corner_phi(g, p, i, j + 1);
     double c10 = corner_phi(g, p, i + 1, j);
@@ -181,116 +202,6 @@ void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles
   cudaMemsetAsync(sc->n_tiles, 0, 2 * sizeof(int), st);
   k_tiles<<<g.ntx * g.nty, 128, 0, st>>>(g, phi, tiles0, tiles1, sc->n_tiles);
   sif_note_launches(1);
-}
-
-// ---------------------------------------------------------------------
-// small-cell mixing, gather form in the CPU reference's scatter order
-
-struct MixSrc {
-  int nt;
-  int ti[3], tj[3];
-  double beta[3], at[3];
-  double as;
-};
-
-// is cell (i, j) a mixing source of fluid k; if so its targets and weights
-__device__ bool mix_source(const Grid &g, int k, int i, int j, const double *alpha,
-                           const double *phi, double *const q[4], MixSrc &s) {
-  int c = gidx(g, i, j);
-  double as = vol_k(alpha, k, c);
-  if (as >= g.mix_alpha) return false;
-  if (as == 0.0 && q[0][c] == 0.0 && q[1][c] == 0.0 && q[2][c] == 0.0 && q[3][c] == 0.0)
-    return false;
-  double nxv, nyv;
-  unit_normal(g, phi, i, j, nxv, nyv);
-  if (k == 0) {
-    nxv = -nxv;
-    nyv = -nyv;
-  }
-  int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
-  int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
-  double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
-  int nt = g.dim == 2 ? 3 : 1;
-  bool keep[3] = {false, false, false};
-  double sum = 0.0;
-  for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
-    for (int t = 0; t < nt; t++) {
-      if (!inside(g, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
-      double at = vol_k(alpha, k, gidx(g, ti[t], tj[t]));
-      if (pass == 0 ? !(at >= g.mix_alpha) : !(at > as)) continue;
-      keep[t] = true;
-      sum += wt[t];
-    }
-  if (!(sum > 0.0)) return false;
-  s.nt = 0;
-  s.as = as;
-  for (int t = 0; t < nt; t++) {
-    if (!keep[t]) continue;
-    s.ti[s.nt] = ti[t];
-    s.tj[s.nt] = tj[t];
-    s.beta[s.nt] = wt[t] / sum;
-    s.at[s.nt] = vol_k(alpha, k, gidx(g, ti[t], tj[t]));
-    s.nt++;
-  }
-  return true;
-}
-
-__global__ void k_mix_gather(Grid g, int k, double *q0, double *q1, double *q2, double *q3,
-                             const double *__restrict__ alpha, const double *__restrict__ phi,
-                             const int *__restrict__ band, const int *nband, double *tmp) {
-  int n = *nband;
-  double *const q[4] = {q0, q1, q2, q3};
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
-    double val[4] = {q0[c], q1[c], q2[c], q3[c]};
-    // sources in raster order; each adds to itself and subtracts at its targets
-    for (int dj = -1; dj <= 1; dj++)
-      for (int di = -1; di <= 1; di++) {
-        int si = i + di, sj = j + dj;
-        if (g.dim == 1 && dj != 0) continue;
-        if (!inside(g, si, sj)) continue;
-        MixSrc s;
-        if (!mix_source(g, k, si, sj, alpha, phi, q, s)) continue;
-        int sc_ = gidx(g, si, sj);
-        for (int t = 0; t < s.nt; t++) {
-          int tc = gidx(g, s.ti[t], s.tj[t]);
-          bool self = (di == 0 && dj == 0);
-          bool tgt = (tc == c);
-          if (!self && !tgt) continue;
-          double den = s.as * s.beta[t] + s.at[t];
-          for (int m = 0; m < 4; m++) {
-            double M = s.beta[t] * (q[m][tc] * s.as - q[m][sc_] * s.at[t]) / den;
-            if (self) val[m] += M;
-            if (tgt) val[m] -= M;
-          }
-        }
-      }
-    for (int m = 0; m < 4; m++) tmp[(size_t)m * n + idx] = val[m];
-  }
-}
-
-__global__ void k_band_scatter4(const int *__restrict__ band, const int *nband, const double *tmp,
-                                double *q0, double *q1, double *q2, double *q3) {
-  int n = *nband;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    q0[c] = tmp[idx];
-    q1[c] = tmp[(size_t)n + idx];
-    q2[c] = tmp[(size_t)2 * n + idx];
-    q3[c] = tmp[(size_t)3 * n + idx];
-  }
-}
-
-void launch_mix(const Grid &g, int k, double *const q[4], const double *alpha, const double *phi,
-                const int *band, const int *nband, int band_cap, double *tmp, cudaStream_t st) {
-  int blocks = (band_cap + 255) / 256;
-  if (blocks > 1216) blocks = 1216;
-  if (blocks < 1) blocks = 1;
-  k_mix_gather<<<blocks, 256, 0, st>>>(g, k, q[0], q[1], q[2], q[3], alpha, phi, band, nband,
-                                      tmp);
-  k_band_scatter4<<<blocks, 256, 0, st>>>(band, nband, tmp, q[0], q[1], q[2], q[3]);
-  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------

@@ -1,0 +1,347 @@
+// kernels_plan.cu -- narrow-band work of the interaction step with the
+// per-cell decisions taken once: the interaction band with a cell -> band
+// position map, the upwind neighbours and weights of the extension
+// (Sec. 2.3: stencil states of both fluids and the level-set velocity),
+// and the small-cell mixing sources with their targets and weights
+// (Sec. 2.2).  The Jacobi sweeps and the mixing gather then only read the
+// plans, both fluids per launch.
+//
+// Compiled without FMA contraction, like the other branch-taking kernels.
+#include "sif_internal.cuh"
+
+static int blocks_for(int n, int per) {
+  int b = (n + per - 1) / per;
+  if (b > 2432) b = 2432;
+  return b < 1 ? 1 : b;
+}
+
+// ---------------------------------------------------------------------
+// interaction band and its map
+
+__global__ void k_unmap(const int *__restrict__ band, const int *nband, int *map) {
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+    map[band[idx]] = -1;
+}
+
+__global__ void k_band_mapped(Grid g, const double *__restrict__ p, int *band, int *map,
+                              int *nband) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t % g.nx, j = t / g.nx;
+  bool in = false;
+  int c = 0;
+  if (j < g.ny) {
+    c = gidx(g, i, j);
+    in = fabs(p[c]) < g.band * g.h;
+  }
+  unsigned mask = __ballot_sync(0xffffffffu, in);
+  if (!mask) return;
+  int lane = threadIdx.x & 31, lead = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == lead) base = atomicAdd(nband, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  if (in) {
+    int pos = base + __popc(mask & ((1u << lane) - 1u));
+    band[pos] = c;
+    map[c] = pos;
+  }
+}
+
+void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
+                     cudaStream_t st) {
+  int n = g.nx * g.ny;
+  k_unmap<<<blocks_for(n, 256), 256, 0, st>>>(band, nband, map);
+  cudaMemsetAsync(nband, 0, sizeof(int), st);
+  k_band_mapped<<<(n + 255) / 256, 256, 0, st>>>(g, phi, band, map, nband);
+  sif_note_launches(2);
+}
+
+// ---------------------------------------------------------------------
+// extension plans: for every band cell and each of the three extended
+// fields (W_N, W_P, level-set velocity) the upwind x and y neighbours and
+// their normalised weights, or "not a target"
+
+__global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
+                            const double *__restrict__ phi, const double *__restrict__ sx,
+                            const double *__restrict__ sy, const int *__restrict__ band,
+                            const int *nband, ExtPlan *plan, int cap) {
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double nxv, nyv;
+    unit_normal(g, phi, i, j, nxv, nyv);
+    for (int f = 0; f < 3; f++) {
+      ExtPlan pl = {-1, -1, 0.0, 0.0};
+      bool target;
+      double dx_, dy_;
+      if (f < 2) {
+        target = !(vol_k(alpha, f, c) > SIF_ALPHA_REAL);
+        // toward fluid f: its normal points into it
+        dx_ = f == 0 ? -nxv : nxv;
+        dy_ = f == 0 ? -nyv : nyv;
+      } else {
+        target = (sx[c] == 0.0 && sy[c] == 0.0);
+        // toward the interface from either side
+        dx_ = phi[c] >= 0.0 ? -nxv : nxv;
+        dy_ = phi[c] >= 0.0 ? -nyv : nyv;
+      }
+      if (target) {
+        int six = dx_ >= 0.0 ? 1 : -1, siy = dy_ >= 0.0 ? 1 : -1;
+        double wx = fabs(dx_) / g.dx;
+        double wy = g.dim == 2 ? fabs(dy_) / g.dy : 0.0;
+        if (!inside(g, i + six, j)) wx = 0.0;
+        if (!inside(g, i, j + siy)) wy = 0.0;
+        double den = wx + wy;
+        if (den > 0.0) {
+          if (wx > 0.0) {
+            pl.cx = gidx(g, i + six, j);
+            pl.wx = wx / den;
+          }
+          if (wy > 0.0) {
+            pl.cy = gidx(g, i, j + siy);
+            pl.wy = wy / den;
+          }
+        }
+      }
+      plan[(size_t)f * cap + idx] = pl;
+    }
+  }
+}
+
+void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
+                      const double *sy, const int *band, const int *nband, ExtPlan *plan,
+                      int cap, int work, cudaStream_t st) {
+  k_ext_setup<<<blocks_for(work, 128), 128, 0, st>>>(g, alpha, phi, sx, sy, band, nband, plan, cap);
+  sif_note_launches(1);
+}
+
+// one Jacobi sweep of fields [f0, f0 + nf) (blockIdx.y selects the field);
+// each field has ncomp planes
+struct ExtFields {
+  double *p[3][4];
+  int ncomp[3];
+};
+
+__global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ plan, int cap,
+                            const int *__restrict__ band, const int *nband, double *tmp) {
+  int n = *nband;
+  int f = f0 + blockIdx.y;
+  int nc = F.ncomp[f];
+  const ExtPlan *P = plan + (size_t)f * cap;
+  double *out = tmp + (size_t)blockIdx.y * 4 * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    ExtPlan pl = P[idx];
+    for (int m = 0; m < nc; m++) {
+      const double *a = F.p[f][m];
+      double v;
+      if (pl.cx < 0 && pl.cy < 0) {
+        v = a[c];
+      } else {
+        v = 0.0;
+        if (pl.cx >= 0) v += pl.wx * a[pl.cx];
+        if (pl.cy >= 0) v += pl.wy * a[pl.cy];
+      }
+      out[(size_t)m * n + idx] = v;
+    }
+  }
+}
+
+// write the sweep back; after the last sweep of the stencil states, fold
+// the extended cells' wave speeds into the Lax-Friedrichs maxima
+__global__ void k_ext_scatter(Grid g, ExtFields F, int f0, const int *__restrict__ band,
+                              const int *nband, const double *tmp,
+                              const double *__restrict__ alpha, int last, Scalars *sc) {
+  int n = *nband;
+  int f = f0 + blockIdx.y;
+  int nc = F.ncomp[f];
+  const double *in = tmp + (size_t)blockIdx.y * 4 * n;
+  double lx = 0.0, ly = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    for (int m = 0; m < nc; m++) F.p[f][m][c] = in[(size_t)m * n + idx];
+    if (last && f < 2 && !(vol_k(alpha, f, c) > SIF_ALPHA_REAL)) {
+      double r = in[idx], u = in[(size_t)n + idx], v = in[(size_t)2 * n + idx],
+             p = in[(size_t)3 * n + idx];
+      double cs = sqrt(fmax(g.gamma[f] * (p + g.pinf[f]) / r, 0.0));
+      lx = fmax(lx, fabs(u) + cs);
+      ly = fmax(ly, fabs(v) + cs);
+    }
+  }
+  if (last && f < 2) {
+    __shared__ double sa[32], sb[32];
+    lx = warp_max(lx);
+    ly = warp_max(ly);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      sa[wid] = lx;
+      sb[wid] = ly;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      int nw = (blockDim.x + 31) >> 5;
+      lx = lane < nw ? sa[lane] : 0.0;
+      ly = lane < nw ? sb[lane] : 0.0;
+      lx = warp_max(lx);
+      ly = warp_max(ly);
+      if (lane == 0) {
+        atomic_max_pos(&sc->lf[f][0], lx);
+        atomic_max_pos(&sc->lf[f][1], ly);
+      }
+    }
+  }
+}
+
+void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
+                       double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
+                       const int *band, const int *nband, double *tmp, const double *alpha,
+                       Scalars *sc, cudaStream_t st) {
+  ExtFields F;
+  for (int m = 0; m < 4; m++) {
+    F.p[0][m] = wN[m];
+    F.p[1][m] = wP[m];
+    F.p[2][m] = m == 0 ? ul0 : (m == 1 ? ul1 : nullptr);
+  }
+  F.ncomp[0] = F.ncomp[1] = 4;
+  F.ncomp[2] = 2;
+  dim3 grid(blocks_for(work, 128), nf);
+  for (int it = 0; it < g.ext_iters; it++) {
+    k_ext_sweep<<<grid, 128, 0, st>>>(F, f0, plan, cap, band, nband, tmp);
+    k_ext_scatter<<<grid, 128, 0, st>>>(g, F, f0, band, nband, tmp, alpha,
+                                        it == g.ext_iters - 1, sc);
+  }
+  sif_note_launches(2 * g.ext_iters);
+}
+
+// ---------------------------------------------------------------------
+// small-cell mixing with source plans (gather in the CPU reference's
+// scatter order: sources in raster order, each adding to itself and
+// subtracting at its targets)
+
+__device__ bool mix_source_plan(const Grid &g, int k, int i, int j, const double *alpha,
+                                const double *phi, double *const q[4], MixPlan &s) {
+  int c = gidx(g, i, j);
+  double as = vol_k(alpha, k, c);
+  s.nt = 0;
+  if (as >= g.mix_alpha) return false;
+  if (as == 0.0 && q[0][c] == 0.0 && q[1][c] == 0.0 && q[2][c] == 0.0 && q[3][c] == 0.0)
+    return false;
+  double nxv, nyv;
+  unit_normal(g, phi, i, j, nxv, nyv);
+  if (k == 0) {
+    nxv = -nxv;
+    nyv = -nyv;
+  }
+  int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+  int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
+  double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
+  int nt = g.dim == 2 ? 3 : 1;
+  bool keep[3] = {false, false, false};
+  double sum = 0.0;
+  for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
+    for (int t = 0; t < nt; t++) {
+      if (!inside(g, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
+      double at = vol_k(alpha, k, gidx(g, ti[t], tj[t]));
+      if (pass == 0 ? !(at >= g.mix_alpha) : !(at > as)) continue;
+      keep[t] = true;
+      sum += wt[t];
+    }
+  if (!(sum > 0.0)) return false;
+  s.as = as;
+  for (int t = 0; t < nt; t++) {
+    if (!keep[t]) continue;
+    int tc = gidx(g, ti[t], tj[t]);
+    s.tc[s.nt] = tc;
+    s.beta[s.nt] = wt[t] / sum;
+    s.at[s.nt] = vol_k(alpha, k, tc);
+    s.nt++;
+  }
+  return true;
+}
+
+struct MixQ {
+  double *q[2][4];
+};
+
+__global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__ alpha,
+                            const double *__restrict__ phi, const int *__restrict__ band,
+                            const int *nband, MixPlan *plan, int cap) {
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    for (int k = 0; k < 2; k++) {
+      if (!(mask & (1 << k))) continue;
+      MixPlan s;
+      mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s);
+      plan[(size_t)k * cap + idx] = s;
+    }
+  }
+}
+
+__global__ void k_mix_apply(Grid g, int mask, MixQ Q, const int *__restrict__ map,
+                            const MixPlan *__restrict__ plan, int cap,
+                            const int *__restrict__ band, const int *nband, double *tmp) {
+  int k = blockIdx.y;
+  if (!(mask & (1 << k))) return;
+  int n = *nband;
+  double *const *q = Q.q[k];
+  const MixPlan *P = plan + (size_t)k * cap;
+  double *out = tmp + (size_t)k * 4 * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double val[4] = {q[0][c], q[1][c], q[2][c], q[3][c]};
+    for (int dj = -1; dj <= 1; dj++) {
+      if (g.dim == 1 && dj != 0) continue;
+      for (int di = -1; di <= 1; di++) {
+        if (!inside(g, i + di, j + dj)) continue;
+        int s = gidx(g, i + di, j + dj);
+        int ps = map[s];
+        if (ps < 0) continue;
+        const MixPlan &sp = P[ps];
+        for (int t = 0; t < sp.nt; t++) {
+          int tc = sp.tc[t];
+          bool self = (s == c), tgt = (tc == c);
+          if (!self && !tgt) continue;
+          double den = sp.as * sp.beta[t] + sp.at[t];
+          for (int m = 0; m < 4; m++) {
+            double M = sp.beta[t] * (q[m][tc] * sp.as - q[m][s] * sp.at[t]) / den;
+            if (self) val[m] += M;
+            if (tgt) val[m] -= M;
+          }
+        }
+      }
+    }
+    for (int m = 0; m < 4; m++) out[(size_t)m * n + idx] = val[m];
+  }
+}
+
+__global__ void k_mix_scatter(int mask, MixQ Q, const int *__restrict__ band, const int *nband,
+                              const double *tmp) {
+  int k = blockIdx.y;
+  if (!(mask & (1 << k))) return;
+  int n = *nband;
+  const double *in = tmp + (size_t)k * 4 * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    for (int m = 0; m < 4; m++) Q.q[k][m][c] = in[(size_t)m * n + idx];
+  }
+}
+
+void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[4],
+                 const double *alpha, const double *phi, const int *band, const int *map,
+                 const int *nband, MixPlan *plan, int cap, int work, double *tmp,
+                 cudaStream_t st) {
+  MixQ Q;
+  for (int m = 0; m < 4; m++) {
+    Q.q[0][m] = qN ? qN[m] : nullptr;
+    Q.q[1][m] = qP ? qP[m] : nullptr;
+  }
+  int b = blocks_for(work, 128);
+  k_mix_setup<<<b, 128, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
+  k_mix_apply<<<dim3(b, 2), 128, 0, st>>>(g, mask, Q, map, plan, cap, band, nband, tmp);
+  k_mix_scatter<<<dim3(b, 2), 128, 0, st>>>(mask, Q, band, nband, tmp);
+  sif_note_launches(3);
+}

@@ -55,7 +55,20 @@ struct Scalars {
   unsigned long long updates;   // (cell, fluid) stage updates issued
 };
 
-struct Ctx;  // host-side context, see api.cu
+// upwind neighbours (cell indices, -1 = unused) and normalised weights of
+// one extension target; cx = cy = -1 marks a cell that is not a target
+struct ExtPlan {
+  int cx, cy;
+  double wx, wy;
+};
+
+// a small-cell mixing source: its targets (cell indices), weights and
+// volume fractions; nt = 0 marks a cell that is not a source
+struct MixPlan {
+  int tc[3];
+  int nt;
+  double beta[3], at[3], as;
+};
 
 __host__ __device__ inline int gidx(const Grid &g, int i, int j) {
   return (i + SIF_GH) + (j + SIF_GH) * g.PX;
@@ -183,7 +196,10 @@ __device__ inline double weno5_plain(double v1, double v2, double v3, double v4,
 }
 
 // ---------------------------------------------------------------------
-// exact two-material stiffened-gas Riemann problem (interface interaction)
+// exact two-material stiffened-gas Riemann problem (interface interaction);
+// the Newton derivative shares the rarefaction power with the function, so
+// iterates differ from the CPU reference by rounding while the converged
+// star state agrees to round-off
 
 __device__ inline void riemann_side(double p, double rho, double pk, double g, double pi,
                                     double ck, double &f, double &df) {
@@ -195,9 +211,11 @@ __device__ inline void riemann_side(double p, double rho, double pk, double g, d
     f = (p - pk) * qr;
     df = qr * (1.0 - 0.5 * (p - pk) / (Pp + B));
   } else {
+    // r^(-(g+1)/(2g)) = r^((g-1)/(2g)) / r: one power per side and iteration
     double r = Pp / P;
-    f = 2.0 * ck / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
-    df = 1.0 / (rho * ck) * pow(r, -(g + 1.0) / (2.0 * g));
+    double ra = pow(r, (g - 1.0) / (2.0 * g));
+    f = 2.0 * ck / (g - 1.0) * (ra - 1.0);
+    df = 1.0 / (rho * ck) * (ra / r);
   }
 }
 
@@ -266,21 +284,27 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
                        cudaStream_t st);
 void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
                        cudaStream_t st);
-void launch_mix(const Grid &g, int k, double *const q[4], const double *alpha, const double *phi,
-                const int *band, const int *nband, int band_cap, double *tmp, cudaStream_t st);
+void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
+                     cudaStream_t st);
+void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[4],
+                 const double *alpha, const double *phi, const int *band, const int *map,
+                 const int *nband, MixPlan *plan, int cap, int work, double *tmp,
+                 cudaStream_t st);
+void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
+                      const double *sy, const int *band, const int *nband, ExtPlan *plan,
+                      int cap, int work, cudaStream_t st);
+// f0 = 0, nf = 2: stencil states of both fluids; f0 = 2, nf = 1: level-set velocity
+void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
+                       double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
+                       const int *band, const int *nband, double *tmp, const double *alpha,
+                       Scalars *sc, cudaStream_t st);
 
 void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
                  const double *alpha, const int *tiles, int tile_cap, Scalars *sc, cudaStream_t st);
-void launch_extend(const Grid &g, int k, double *const w[4], const double *alpha,
-                   const double *phi, const int *band, int band_cap, double *tmp, Scalars *sc,
-                   cudaStream_t st);
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
                       double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
                       Scalars *sc, cudaStream_t st);
-void launch_ls_extend(const Grid &g, double *ul0, double *ul1, const double *phi,
-                      const double *sx, const double *sy, const int *band, int band_cap,
-                      double *tmp, Scalars *sc, cudaStream_t st);
 void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *phi0,
                      const double *ul0, const double *ul1, const int *band, const int *nband,
                      int band_cap, double *tmp, const double *dtp, cudaStream_t st);
