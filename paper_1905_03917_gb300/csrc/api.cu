@@ -9,7 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include <atomic>
+#include <stddef.h>
 #include <new>
 #include <vector>
 
@@ -36,19 +36,29 @@ struct sif_ctx {
   void *pool;        // single device allocation
   size_t pool_bytes;
   int debug_sync;    // SIF_DEBUG_SYNC=1: synchronise and check after each phase
-  // profiling: events around the finite-volume stage launches
+  // profiling: device counters (kernel launches, finite-volume launch time)
   int profiling;
-  std::vector<cudaEvent_t> ev;  // start/stop pairs
-  size_t ev_used;
-  long long fv_launches, launches0;
-  unsigned long long updates0;
+  unsigned long long launches0, updates0;
+  // work stream: the caller's, or a private blocking stream (ordered with
+  // the legacy default stream) when the caller passes none
+  cudaStream_t own_stream;
+  // device-driven cycle graphs (conditional nodes) and capture state
+  cudaStream_t cap[4];
+  int cap_depth, capturing, gerr;
+  int use_graphs;
+  int graph_bucket;  // band grid size baked into the graphs
+  cudaGraphExec_t g_cycle, g_single;
   int inited;
   int last_status;
   char err[256];
 };
 
-static std::atomic<long long> g_launches{0};
-void sif_note_launches(int n) { g_launches += n; }
+// launch counting happens on the device (SIF_TICK); the host-side notes
+// the wrappers make are not used for measurement
+void sif_note_launches(int) {}
+static unsigned long long device_launches() {
+  return sif_launches_geom() + sif_launches_band() + sif_launches_plan() + sif_launches_fv();
+}
 
 static void set_err(sif_ctx *c, const char *fmt, ...) {
   va_list ap;
@@ -65,6 +75,8 @@ static void set_err(sif_ctx *c, const char *fmt, ...) {
       return SIF_ECUDA;                                                       \
     }                                                                         \
   } while (0)
+
+static int ensure_graphs(sif_ctx *c);
 
 static int check_launch(sif_ctx *c, const char *where) {
   cudaError_t e = cudaGetLastError();
@@ -125,6 +137,19 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     return SIF_ECUDA;
   }
   c->st = (cudaStream_t)f.cuda_stream;
+  if (!c->st) {
+    if (cudaStreamCreate(&c->own_stream) != cudaSuccess) {
+      delete c;
+      return SIF_ECUDA;
+    }
+    c->st = c->own_stream;
+  }
+  for (int i = 0; i < 4; i++) cudaStreamCreateWithFlags(&c->cap[i], cudaStreamNonBlocking);
+  fv_prepare();
+  {
+    const char *ng = getenv("SIF_NO_GRAPH");
+    c->use_graphs = !(ng && ng[0] == '1');
+  }
   Grid &g = c->g;
   g.dim = f.dim;
   g.nx = f.nx;
@@ -182,7 +207,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     for (int m = 0; m < 3; m++) c->xc[m] = plane();
     c->phi0 = plane();
     c->phiR = plane();
-    c->tmp = (double *)take(sizeof(double) * 8 * ncell);
+    c->tmp = (double *)take(sizeof(double) * 16 * ncell);
     c->bandmap = (int *)take(sizeof(int) * c->NP);
     c->ext_plan = (ExtPlan *)take(sizeof(ExtPlan) * 3 * ncell);
     c->mix_plan = (MixPlan *)take(sizeof(MixPlan) * 2 * ncell);
@@ -243,7 +268,11 @@ extern "C" void sif_destroy(sif_ctx *c) {
   cudaSetDevice(c->cfg.device);
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
-  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
+  if (c->g_single) cudaGraphExecDestroy(c->g_single);
+  for (int i = 0; i < 4; i++)
+    if (c->cap[i]) cudaStreamDestroy(c->cap[i]);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
   cudaFree(c->pool);
   cudaFreeHost(c->hsc);
   cudaFreeHost(c->hbuf);
@@ -258,7 +287,7 @@ extern "C" const char *sif_last_error(const sif_ctx *c) { return c ? c->err : "n
 // opt-in fault localisation: synchronise after a phase and report the
 // first failing one on stderr
 static void dbg(sif_ctx *c, const char *phase) {
-  if (!c->debug_sync) return;
+  if (!c->debug_sync || c->capturing) return;
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) fprintf(stderr, "libsif: %s failed: %s\n", phase, cudaGetErrorString(e));
@@ -304,15 +333,17 @@ static void mix_one(sif_ctx *c, int k, double *const q[4]) {
   mix2(c, 1 << k, k == 0 ? q : nullptr, k == 1 ? q : nullptr);
 }
 
-// interaction step for stage states qs of both fluids and the current phi
+// interaction step for stage states qs of both fluids and the current phi.
+// The geometry of the current phi is already in place: every change of phi
+// (level-set stage, reinitialisation, initial data, restored state) is
+// followed by geometry() before anything else reads it.
 static void eval(sif_ctx *c, double *const qs[2][4]) {
-  geometry(c);
   launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
-  for (int k = 0; k < 2; k++)
-    launch_prim(c->g, k, qs[k], c->w[k], c->alpha, c->tiles[k], ntile(c), c->sc, c->st);
+  launch_prim2(c->g, qs[0], qs[1], c->w[0], c->w[1], c->alpha, c->tiles[0], c->tiles[1],
+               ntile(c), c->sc, c->st);
   dbg(c, "prim");
-  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->ext_plan,
-                   ncell(c), band_work(c), c->st);
+  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
+                   c->ext_plan, ncell(c), band_work(c), c->st);
   launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
                     band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->sc, c->st);
   dbg(c, "extend");
@@ -334,15 +365,8 @@ static void copy_planes(sif_ctx *c, double *const dst[4], double *const src[4], 
 static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const base[4],
                double *const cur[4], const double *dtp) {
   ghost_w(c, k);
-  bool timed = c->profiling && c->ev_used + 2 <= c->ev.size();
-  if (c->profiling) c->fv_launches++;
-  if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
                   c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), dtp, c->sc, c->st);
-  if (timed) {
-    cudaEventRecord(c->ev[c->ev_used + 1], c->st);
-    c->ev_used += 2;
-  }
   dbg(c, "fv_stage");
 }
 
@@ -385,6 +409,7 @@ static int finish(sif_ctx *c, sif_cycle_info *info, unsigned long long upd0) {
   if (rc) return rc;
   CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  c->band_work = c->hsc->n_band;
   if (info) {
     info->t = c->hsc->t;
     info->cell_updates = (long long)(c->hsc->updates - upd0);
@@ -428,10 +453,14 @@ extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycl
       CK(cudaStreamSynchronize(c->st));
       if (c->hsc->t >= t_end) break;
     }
-    eval(c, c->q);
-    launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
-    single_step_after_eval(c, &c->sc->dt);
-    launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+    if (ensure_graphs(c) == SIF_OK) {
+      CK(cudaGraphLaunch(c->g_single, c->st));
+    } else {
+      eval(c, c->q);
+      launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
+      single_step_after_eval(c, &c->sc->dt);
+      launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+    }
   }
   rc = finish(c, info, upd0);
   if (info) {
@@ -487,7 +516,6 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     sub++;
     if (sub > 1) {
       launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
-      geometry(c);
       mix_one(c, f1, c->qi);
       for (int m = 0; m < 4; m++) {
         qs[f1][m] = c->qi[m];
@@ -552,6 +580,224 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
   return SIF_OK;
 }
 
+
+// ---------------------------------------------------------------------
+// device-driven graphs: one CUDA graph runs a whole accelerated cycle;
+// conditional IF nodes follow the scheduler's decisions (single step or
+// cycle, fluid 1's identity, first and last sub-step) and a WHILE node
+// repeats the fluid-2 sub-step, so no host round trip remains inside a
+// cycle.  The kernels are exactly those of the host-driven path.
+
+#define GCK(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess && !c->gerr) c->gerr = e_; \
+  } while (0)
+
+static const int kMaxSubsteps = 4096;
+
+static cudaGraph_t capture_graph(sif_ctx *c) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  GCK(cudaStreamGetCaptureInfo(c->st, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  return g;
+}
+
+static cudaGraphConditionalHandle new_handle(sif_ctx *c) {
+  cudaGraphConditionalHandle h = 0;
+  GCK(cudaGraphConditionalHandleCreate(&h, capture_graph(c), 0, cudaGraphCondAssignDefault));
+  return h;
+}
+
+// append a conditional node to the graph being captured on c->st and
+// capture `body` into its body graph on the next capture stream
+template <class F>
+static void cond_node(sif_ctx *c, cudaGraphConditionalHandle h, bool loop, F body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  GCK(cudaStreamGetCaptureInfo(c->st, &st, nullptr, &g, &deps, &ed, &nd));
+  if (c->gerr) return;
+  // the parameter union has no default constructor: zeroed raw storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams &p = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = loop ? cudaGraphCondTypeWhile : cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  GCK(cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+  if (c->gerr) return;
+  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+  GCK(cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  if (c->cap_depth >= 3) {
+    c->gerr = cudaErrorNotSupported;
+    return;
+  }
+  cudaStream_t outer = c->st, inner = c->cap[++c->cap_depth];
+  GCK(cudaStreamBeginCaptureToGraph(inner, bodyg, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal));
+  c->st = inner;
+  if (!c->gerr) body();
+  c->st = outer;
+  cudaGraph_t out = nullptr;
+  GCK(cudaStreamEndCapture(inner, &out));
+  c->cap_depth--;
+}
+
+static void copy4(sif_ctx *c, double *const dst[4], double *const src[4]) { copy_planes(c, dst, src, 4); }
+
+// one fluid-2 sub-step of the cycle with fluid 1 = f1 (the body of the
+// sub-cycle loop); hloop is the loop's condition
+static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) {
+  const int f2 = 1 - f1;
+  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  double *qs[2][4];
+  for (int m = 0; m < 4; m++) {
+    qs[f1][m] = c->qi[m];
+    qs[f2][m] = c->q[f2][m];
+  }
+  // after the first sub-step: fluid 1 at t2 (Eq. 7), interaction, fluid-2 step
+  cudaGraphConditionalHandle hnf = new_handle(c);
+  launch_cond(COND_NOT_FIRST, c->sc, hnf, 0, 0, 0, c->st);
+  cond_node(c, hnf, false, [&] {
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+    mix_one(c, f1, c->qi);
+    eval(c, qs);
+    launch_sched(SCHED_DT2, c->sc, cfl, thr, 0, c->st);
+  });
+  launch_sched(SCHED_LAST, c->sc, cfl, thr, 0, c->st);
+  cudaGraphConditionalHandle hl1 = new_handle(c), hn1 = new_handle(c);
+  cudaGraphConditionalHandle hl2 = new_handle(c), hn2 = new_handle(c);
+  cudaGraphConditionalHandle hl3 = new_handle(c);
+  launch_cond(COND_LAST, c->sc, hl1, hn1, 0, 0, c->st);
+  launch_cond(COND_LAST, c->sc, hl2, hn2, 0, 0, c->st);
+  launch_cond(COND_LAST, c->sc, hl3, 0, 0, 0, c->st);
+  launch_record(c->g, -1, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0], c->xc[1],
+                c->xc[2], c->sc, c->st);
+  // step 3: fluid-2 and level-set first RK stage with dt2
+  copy4(c, c->q0[f2], c->q[f2]);
+  ls_begin(c);
+  fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+  ls_stage(c, 1, &c->sc->dt2);
+  geometry(c);
+  mix_one(c, f2, c->q[f2]);
+  cond_node(c, hl1, false, [&] {
+    mix_one(c, f1, c->fut);
+    copy4(c, c->qi, c->fut);
+  });
+  cond_node(c, hn1, false, [&] {
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+    mix_one(c, f1, c->qi);
+  });
+  eval(c, qs);
+  launch_record(c->g, -2, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0], c->xc[1],
+                c->xc[2], c->sc, c->st);
+  // step 4 (and 5 on the last sub-step): second RK stage
+  fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+  ls_stage(c, 2, &c->sc->dt2);
+  cond_node(c, hl2, false, [&] { fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1); });
+  reinit(c);
+  cond_node(c, hl3, false, [&] {
+    if (c->cfg.flux_correction)
+      launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
+    geometry(c);
+    mix_both(c);
+  });
+  cond_node(c, hn2, false, [&] {
+    launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
+    geometry(c);
+    mix_one(c, f2, c->q[f2]);
+  });
+  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, kMaxSubsteps, c->st);
+}
+
+static void graph_cycle_body(sif_ctx *c, int f1) {
+  for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
+  // step 2: fluid-1 first RK stage with dt1; previous and future states
+  copy4(c, c->prev, c->q[f1]);
+  fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
+  cudaGraphConditionalHandle hloop = new_handle(c);
+  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, kMaxSubsteps, c->st);  // last = 0 here
+  cond_node(c, hloop, true, [&] { graph_substep(c, f1, hloop); });
+  launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
+}
+
+static void free_graphs(sif_ctx *c) {
+  if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
+  if (c->g_single) cudaGraphExecDestroy(c->g_single);
+  c->g_cycle = c->g_single = nullptr;
+}
+
+static int bucket_for(int n) {
+  int b = 1024;
+  while (b < n + n / 2 + 1024) b *= 2;
+  return b;
+}
+
+static int build_graphs(sif_ctx *c) {
+  free_graphs(c);
+  c->graph_bucket = bucket_for(c->band_work);
+  int saved_work = c->band_work;
+  c->band_work = c->graph_bucket;  // grids of the band kernels in the graphs
+  c->gerr = 0;
+  c->capturing = 1;
+  c->cap_depth = 0;
+  cudaGraph_t gc = nullptr, gs = nullptr;
+  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  // accelerated cycle
+  GCK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  if (!c->gerr) {
+    cudaGraphConditionalHandle hs = new_handle(c), h0 = new_handle(c), h1 = new_handle(c);
+    eval(c, c->q);
+    launch_sched(SCHED_CYCLE_BEGIN, c->sc, cfl, thr, c->cfg.force_ratio_one, c->st);
+    launch_cond(COND_CYCLE, c->sc, hs, h0, h1, 0, c->st);
+    cond_node(c, hs, false, [&] {
+      single_step_after_eval(c, &c->sc->dt);
+      launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+    });
+    cond_node(c, h0, false, [&] { graph_cycle_body(c, 0); });
+    cond_node(c, h1, false, [&] { graph_cycle_body(c, 1); });
+  }
+  cudaError_t e = cudaStreamEndCapture(c->st, &gc);
+  if (!c->gerr && e != cudaSuccess) c->gerr = e;
+  // original single-time-step method
+  if (!c->gerr) {
+    GCK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    eval(c, c->q);
+    launch_sched(SCHED_SINGLE_DT, c->sc, cfl, 0, 0, c->st);
+    single_step_after_eval(c, &c->sc->dt);
+    launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+    e = cudaStreamEndCapture(c->st, &gs);
+    if (!c->gerr && e != cudaSuccess) c->gerr = e;
+  }
+  c->capturing = 0;
+  c->band_work = saved_work;
+  if (!c->gerr && gc) GCK(cudaGraphInstantiate(&c->g_cycle, gc, 0));
+  if (!c->gerr && gs) GCK(cudaGraphInstantiate(&c->g_single, gs, 0));
+  if (gc) cudaGraphDestroy(gc);
+  if (gs) cudaGraphDestroy(gs);
+  cudaGetLastError();
+  if (c->gerr) {
+    free_graphs(c);
+    c->use_graphs = 0;  // fall back to the host-driven sequence
+    return SIF_ECUDA;
+  }
+  return SIF_OK;
+}
+
+static int ensure_graphs(sif_ctx *c) {
+  if (!c->use_graphs) return SIF_ECUDA;
+  // rebuild when the band outgrew the baked grid sizes or shrank far below
+  int want = bucket_for(c->band_work);
+  if (c->g_cycle && c->g_single && want <= c->graph_bucket && c->graph_bucket <= 4 * want)
+    return SIF_OK;
+  return build_graphs(c);
+}
+
 extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycle_info *info) {
   if (!c || ncycles < 0) return SIF_EINVAL;
   if (c->cfg.rk_order != 2) {
@@ -561,6 +807,31 @@ extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycl
   unsigned long long upd0;
   int rc = begin_call(c, t_end, &upd0);
   if (rc) return rc;
+  if (ensure_graphs(c) == SIF_OK) {
+    for (int n = 0; n < ncycles; n++) {
+      if (t_end > 0.0) {
+        rc = read_scalars(c);
+        if (rc) return rc;
+        if (c->hsc->t >= t_end || c->hsc->err) break;
+      }
+      CK(cudaGraphLaunch(c->g_cycle, c->st));
+    }
+    rc = finish(c, info, upd0);
+    if (info) {
+      const Scalars *h = c->hsc;
+      info->role_fluid1 = h->f1;
+      info->n_raw = h->n_raw;
+      info->n_used = h->mode == 0 ? 1.0 : h->n_used;
+      info->dt1 = h->mode == 0 ? h->dt : h->dt1;
+      info->dt2 = h->mode == 0 ? h->dt : h->dt2_first;
+      info->substeps = h->mode == 0 ? 1 : h->sub;
+    }
+    if (!rc && c->hsc->mode == 1 && c->hsc->sub >= kMaxSubsteps) {
+      set_err(c, "sub-cycle count reached %d", kMaxSubsteps);
+      return SIF_ETIMEOUT;
+    }
+    return rc;
+  }
   for (int n = 0; n < ncycles; n++) {
     rc = read_scalars(c);
     if (rc) return rc;
@@ -605,13 +876,17 @@ extern "C" int sif_init_fluids(sif_ctx *c, const double *phi, const double *pN, 
   for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->w[0][m], pN + m * n, mem);
   for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->w[1][m], pP + m * n, mem);
   if (rc) return rc;
+  // scalars first: the geometry below fills the list counts in them
+  CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), c->st));
   geometry(c);
   launch_init_state(c->g, c->q[0], c->q[1], c->w[0], c->w[1], c->alpha, c->st);
   mix_both(c);
-  CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), c->st));
+  int nb = 0;
+  CK(cudaMemcpyAsync(&nb, &c->sc->n_band, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   rc = check_launch(c, "init");
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->st));
+  c->band_work = nb;
   c->inited = 1;
   return SIF_OK;
 }
@@ -750,10 +1025,10 @@ extern "C" int sif_load(sif_ctx *c, const void *buf, size_t len) {
   int rc = SIF_OK;
   for (int i = 0; i < kCkptPlanes && !rc; i++) rc = put_plane(c, ckpt_plane(c, i), in + i * n, SIF_HOST);
   if (rc) return rc;
-  geometry(c);
   CK(cudaMemsetAsync(c->sc, 0, sizeof(Scalars), c->st));
   c->hbuf[0] = h.t;
   CK(cudaMemcpyAsync(&c->sc->t, c->hbuf, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  geometry(c);
   rc = check_launch(c, "load");
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->st));
@@ -767,17 +1042,23 @@ extern "C" int sif_load(sif_ctx *c, const void *buf, size_t len) {
 extern "C" int sif_profile_enable(sif_ctx *c, int enable) {
   if (!c) return SIF_EINVAL;
   cudaSetDevice(c->cfg.device);
+  int rc = read_scalars(c);
+  if (rc) return rc;
   if (enable) {
-    if (c->ev.empty()) {
-      c->ev.resize(2 * 65536);
-      for (auto &e : c->ev) CK(cudaEventCreate(&e));
-    }
-    int rc = read_scalars(c);
-    if (rc) return rc;
-    c->ev_used = 0;
-    c->fv_launches = 0;
-    c->launches0 = g_launches.load();
+    // re-arm the finite-volume launch timer and zero its sums
+    struct {
+      int timing;
+      unsigned int done;
+      unsigned long long t0, t1, ns, n;
+    } z = {1, 0u, ~0ull, 0ull, 0ull, 0ull};
+    static_assert(sizeof(z) == offsetof(Scalars, fv_launches) + sizeof(unsigned long long) -
+                                   offsetof(Scalars, timing), "timer block layout");
+    CK(cudaMemcpy((char *)c->sc + offsetof(Scalars, timing), &z, sizeof(z), cudaMemcpyHostToDevice));
+    c->launches0 = device_launches();
     c->updates0 = c->hsc->updates;
+  } else {
+    int zero = 0;
+    CK(cudaMemcpy(&c->sc->timing, &zero, sizeof(int), cudaMemcpyHostToDevice));
   }
   c->profiling = enable ? 1 : 0;
   return SIF_OK;
@@ -788,15 +1069,9 @@ extern "C" int sif_profile_read(sif_ctx *c, sif_profile *out) {
   cudaSetDevice(c->cfg.device);
   int rc = read_scalars(c);
   if (rc) return rc;
-  double ms = 0.0;
-  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
-    float t = 0.0f;
-    CK(cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
-    ms += t;
-  }
-  out->kernel_launches = g_launches.load() - c->launches0;
-  out->fv_launches = c->fv_launches;
-  out->fv_ms = ms;
+  out->kernel_launches = (long long)(device_launches() - c->launches0);
+  out->fv_launches = (long long)c->hsc->fv_launches;
+  out->fv_ms = (double)c->hsc->fv_ns * 1e-6;
   out->fv_cell_updates = (long long)(c->hsc->updates - c->updates0);
   return SIF_OK;
 }

@@ -44,12 +44,21 @@ __device__ inline void block_max2(double a, double b, unsigned long long *pa,
 // ---------------------------------------------------------------------
 // real-cell stencil states W = prim((alpha U)/alpha) and wave maxima
 
-__global__ void k_prim(Grid g, int k, const double *__restrict__ q0, const double *__restrict__ q1,
-                       const double *__restrict__ q2, const double *__restrict__ q3, double *w0,
-                       double *w1, double *w2, double *w3, const double *__restrict__ alpha,
-                       const int *__restrict__ tiles, const int *ntiles, Scalars *sc) {
+struct PrimArgs {
+  const double *q[2][4];
+  double *w[2][4];
+  const int *tiles[2];
+};
+
+// blockIdx.y = fluid
+__global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, const int *ntiles,
+                       Scalars *sc) {
+  SIF_TICK();
+  const int k = blockIdx.y;
   if ((int)blockIdx.x >= ntiles[k]) return;
-  int tile = tiles[blockIdx.x];
+  const double *q0 = P.q[k][0], *q1 = P.q[k][1], *q2 = P.q[k][2], *q3 = P.q[k][3];
+  double *w0 = P.w[k][0], *w1 = P.w[k][1], *w2 = P.w[k][2], *w3 = P.w[k][3];
+  int tile = P.tiles[k][blockIdx.x];
   int tx = tile % g.ntx, ty = tile / g.ntx;
   int i = tx * FV_TX + (threadIdx.x % FV_TX), j = ty * FV_TY + threadIdx.x / FV_TX;
   double lx = 0.0, ly = 0.0, sm = 0.0;
@@ -82,11 +91,19 @@ __global__ void k_prim(Grid g, int k, const double *__restrict__ q0, const doubl
   block_max2(sm, 0.0, &sc->smax[k], nullptr);
 }
 
-void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
-                 const double *alpha, const int *tiles, int tile_cap, Scalars *sc,
-                 cudaStream_t st) {
-  k_prim<<<tile_cap, FV_TX * FV_TY, 0, st>>>(g, k, q[0], q[1], q[2], q[3], w[0], w[1], w[2],
-                                             w[3], alpha, tiles, sc->n_tiles, sc);
+void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], double *const wN[4],
+                  double *const wP[4], const double *alpha, const int *tilesN,
+                  const int *tilesP, int tile_cap, Scalars *sc, cudaStream_t st) {
+  PrimArgs P;
+  for (int m = 0; m < 4; m++) {
+    P.q[0][m] = qN[m];
+    P.q[1][m] = qP[m];
+    P.w[0][m] = wN[m];
+    P.w[1][m] = wP[m];
+  }
+  P.tiles[0] = tilesN;
+  P.tiles[1] = tilesP;
+  k_prim<<<dim3(tile_cap, 2), FV_TX * FV_TY, 0, st>>>(g, P, alpha, sc->n_tiles, sc);
   sif_note_launches(1);
 }
 
@@ -101,6 +118,7 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
                             const double *__restrict__ sy, const int *__restrict__ cut,
                             const int *ncut, double *xn0, double *xn1, double *xn2, double *ul0,
                             double *ul1, Scalars *sc) {
+  SIF_TICK();
   int n = *ncut;
   double fac = 1.0 / g.dx + (g.dim == 2 ? 1.0 / g.dy : 0.0);
   double sN = 0.0, sP = 0.0;
@@ -143,6 +161,7 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
 
 __global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, const double *tmp,
                                 double *a, double *b) {
+  SIF_TICK();
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
@@ -177,6 +196,7 @@ __global__ void k_ls_stage(Grid g, int s, double a, double b, const double *__re
                            const double *__restrict__ phi0, const double *__restrict__ u0,
                            const double *__restrict__ u1, const int *__restrict__ band,
                            const int *nband, double *tmp, const double *dtp) {
+  SIF_TICK();
   int n = *nband;
   double dt = *dtp;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
@@ -215,6 +235,7 @@ __device__ inline double grad_est(const double *p, int c, int s, double h) {
 
 __global__ void k_reinit(Grid g, const double *__restrict__ q, const double *__restrict__ z,
                          const int *__restrict__ rext, const int *nrext, double *tmp) {
+  SIF_TICK();
   int n = *nrext;
   bool d2 = g.dim == 2;
   double h = g.h;
@@ -269,6 +290,7 @@ __global__ void k_reinit(Grid g, const double *__restrict__ q, const double *__r
 }
 
 __global__ void k_copy_plane(const double *src, double *dst, size_t n) {
+  SIF_TICK();
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x)
     dst[t] = src[t];
@@ -296,9 +318,12 @@ __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncu
                          const double *__restrict__ x0, const double *__restrict__ x1,
                          const double *__restrict__ x2, double *c0, double *c1, double *c2,
                          const Scalars *sc) {
+  SIF_TICK();
   int n = *ncut;
   double sgn = sc->f1 == 0 ? 1.0 : -1.0;
   double dt1 = sc->dt1, dt2 = sc->dt2;
+  if (shared == -1) shared = sc->sub == 1;
+  else if (shared == -2) shared = sc->last;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = cut[idx];
     const double *xs[3] = {x0, x1, x2};
@@ -330,6 +355,7 @@ __global__ void k_interp(Grid g, double *i0, double *i1, double *i2, double *i3,
                          const double *__restrict__ f0, const double *__restrict__ f1,
                          const double *__restrict__ f2, const double *__restrict__ f3,
                          const double *thp) {
+  SIF_TICK();
   double th = *thp;
   int n = g.nx * g.ny;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -354,6 +380,7 @@ void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
 
 __global__ void k_correction(Grid g, double *q1, double *q2, double *q3, const double *c0,
                              const double *c1, const double *c2) {
+  SIF_TICK();
   int n = g.nx * g.ny;
   double dxdy = g.dx * g.dy;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -380,6 +407,7 @@ struct Planes8 {
 };
 
 __global__ void k_integrals_rows(Grid g, Planes8 planes, double *partial) {
+  SIF_TICK();
   // blockIdx.y: plane (8), blockIdx.x: group of rows; one warp per row
   int pl = blockIdx.y;
   const double *a = planes.p[pl];
@@ -394,6 +422,7 @@ __global__ void k_integrals_rows(Grid g, Planes8 planes, double *partial) {
 }
 
 __global__ void k_integrals_final(Grid g, const double *partial, double *out) {
+  SIF_TICK();
   int pl = threadIdx.x;
   if (pl >= 8) return;
   double s = 0.0;
@@ -414,6 +443,7 @@ void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], d
 // device-side scheduler of the single- and multi-time-step methods
 
 __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1) {
+  SIF_TICK();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double sm0 = ull_as_double(sc->smax[0]), sm1 = ull_as_double(sc->smax[1]);
   double dtk[2] = {sm0 > 0.0 ? cfl / sm0 : INFINITY, sm1 > 0.0 ? cfl / sm1 : INFINITY};
@@ -461,6 +491,8 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
       }
       sc->t2 = 0.0;
       sc->sub = 0;
+      sc->last = 0;
+      sc->dt2_first = sc->dt2;
       break;
     }
     case SCHED_SUBSTEP:
@@ -480,6 +512,19 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
       sc->t2 = sc->t2 + sc->dt2;
       sc->theta = sc->t2 / sc->dt1;
       break;
+    case SCHED_DT2:
+      sc->dt2 = dtk[sc->f1 == 0 ? 1 : 0];
+      break;
+    case SCHED_LAST: {
+      sc->sub += 1;
+      double dt1 = sc->dt1, t2 = sc->t2, dt2 = sc->dt2;
+      int last = (dt1 - t2) <= dt2 * (1.0 + 1e-12);
+      if (last) dt2 = dt1 - t2;
+      sc->dt2 = dt2;
+      sc->last = last;
+      sc->theta = last ? 1.0 : (t2 + dt2) / dt1;
+      break;
+    }
     case SCHED_T_SINGLE:
       sc->t = sc->t + sc->dt;
       break;
@@ -489,7 +534,42 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
   }
 }
 
+// graph conditions from the scheduler's decisions
+__global__ void k_cond(int op, const Scalars *sc, cudaGraphConditionalHandle h0,
+                       cudaGraphConditionalHandle h1, cudaGraphConditionalHandle h2, int max_sub) {
+  SIF_TICK();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  switch (op) {
+    case COND_CYCLE:
+      cudaGraphSetConditional(h0, sc->mode == 0 ? 1u : 0u);
+      cudaGraphSetConditional(h1, (sc->mode == 1 && sc->f1 == 0) ? 1u : 0u);
+      cudaGraphSetConditional(h2, (sc->mode == 1 && sc->f1 == 1) ? 1u : 0u);
+      break;
+    case COND_NOT_FIRST:
+      cudaGraphSetConditional(h0, sc->sub > 0 ? 1u : 0u);
+      break;
+    case COND_LAST:
+      cudaGraphSetConditional(h0, sc->last ? 1u : 0u);
+      cudaGraphSetConditional(h1, sc->last ? 0u : 1u);
+      break;
+    case COND_LOOP: {
+      // stop after the last sub-step, on a device error, or when the
+      // sub-step count or step size has gone wrong
+      bool go = !sc->last && sc->err == 0 && sc->sub < max_sub && sc->dt2 > 0.0;
+      cudaGraphSetConditional(h0, go ? 1u : 0u);
+      break;
+    }
+  }
+}
+
+void launch_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
+                 cudaGraphConditionalHandle h2, int max_sub, cudaStream_t st) {
+  k_cond<<<1, 32, 0, st>>>(op, sc, h0, h1, h2, max_sub);
+}
+
 void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st) {
   k_sched<<<1, 32, 0, st>>>(op, sc, cfl, thr, force1);
   sif_note_launches(1);
 }
+
+SIF_TU_LAUNCH_READER(band)

@@ -55,10 +55,42 @@ __device__ __forceinline__ double weno5_fast(double v1, double v2, double v3, do
   return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// end-of-block bookkeeping of the launch timer: the last block of the
+// launch adds the launch span and re-arms the timer for the next launch
+__device__ void fv_timer_block_done(const Scalars *csc, bool worked) {
+  Scalars *sc = (Scalars *)csc;
+  if (worked) atomicMax((unsigned long long *)&sc->fv_t1, globaltimer_ns());
+  __threadfence();
+  unsigned int done = atomicAdd(&sc->fv_blocks_done, 1u);
+  if (done == gridDim.x - 1) {
+    __threadfence();
+    unsigned long long t0 = atomicAdd((unsigned long long *)&sc->fv_t0, 0ull);
+    unsigned long long t1 = atomicAdd((unsigned long long *)&sc->fv_t1, 0ull);
+    if (t1 > t0 && t0 != ~0ull) atomicAdd((unsigned long long *)&sc->fv_ns, t1 - t0);
+    atomicAdd((unsigned long long *)&sc->fv_launches, 1ull);
+    atomicExch((unsigned long long *)&sc->fv_t0, ~0ull);
+    atomicExch((unsigned long long *)&sc->fv_t1, 0ull);
+    atomicExch(&sc->fv_blocks_done, 0u);
+  }
+}
+
+__device__ __forceinline__ void fv_update_cell(const FvArgs &A, int k, int i, int j, int li, int lj,
+                                               const double *Fx, const double *Fy, bool d2);
+
 __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
+  SIF_TICK();
   const Grid &g = A.g;
   const int k = A.k;
-  if ((int)blockIdx.x >= A.ntiles[k]) return;
+  if ((int)blockIdx.x >= A.ntiles[k]) {
+    if (A.sc->timing && threadIdx.x == 0) fv_timer_block_done(A.sc, false);
+    return;
+  }
   extern __shared__ double smem[];
   // split fluxes: x for rows of the tile with x-halo, y for columns with y-halo
   double *fxp = smem;                       // [4][HX*FV_TY]
@@ -74,6 +106,8 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
     int w_ = min(FV_TX, g.nx - i0), h_ = min(FV_TY, g.ny - j0);
     atomicAdd((unsigned long long *)&A.sc->updates, (unsigned long long)(w_ * h_));
   }
+  const bool timed = A.sc->timing;
+  if (timed && threadIdx.x == 0) atomicMin((unsigned long long *)&A.sc->fv_t0, globaltimer_ns());
   const double gm = g.gamma[k], pi = g.pinf[k];
   const double inv_gm1 = 1.0 / (gm - 1.0), e0c = gm * pi * inv_gm1;
   const double lfx = ull_as_double(A.sc->lf[k][0]), lfy = ull_as_double(A.sc->lf[k][1]);
@@ -176,7 +210,16 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
   // phase 3: update of the tile's cells
   int li = tid % FV_TX, lj = tid / FV_TX;
   int i = i0 + li, j = j0 + lj;
-  if (i >= g.nx || j >= g.ny) return;
+  if (i < g.nx && j < g.ny) fv_update_cell(A, k, i, j, li, lj, Fx, Fy, d2);
+  if (timed) {
+    __syncthreads();
+    if (threadIdx.x == 0) fv_timer_block_done(A.sc, true);
+  }
+}
+
+__device__ __forceinline__ void fv_update_cell(const FvArgs &A, int k, int i, int j, int li, int lj,
+                                               const double *Fx, const double *Fy, bool d2) {
+  const Grid &g = A.g;
   int c = gidx(g, i, j);
   double dt = *A.dtp;
   double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
@@ -197,6 +240,15 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
   }
 }
 
+static size_t fv_smem_bytes();
+
+// opt the finite-volume kernel into its shared-memory size on the current
+// device (outside any stream capture)
+void fv_prepare() {
+  cudaFuncSetAttribute(k_fv_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fv_smem_bytes());
+}
+
 static size_t fv_smem_bytes() {
   return sizeof(double) * (size_t)(8 * HX * FV_TY + 8 * FV_TX * HY + 4 * (FV_TX + 1) * FV_TY +
                                    4 * FV_TX * (FV_TY + 1));
@@ -209,12 +261,7 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st) {
   static const double A2[3] = {0.0, 0.0, 0.5}, B2[3] = {0.0, 1.0, 0.5};
   static const double A3[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
-  static bool attr = false;
   size_t smem = fv_smem_bytes();
-  if (!attr) {
-    cudaFuncSetAttribute(k_fv_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
   FvArgs A;
   A.g = g;
   A.k = k;
@@ -242,3 +289,5 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   k_fv_stage<<<tile_cap, FV_TX * FV_TY, smem, st>>>(A);
   sif_note_launches(1);
 }
+
+SIF_TU_LAUNCH_READER(fv)

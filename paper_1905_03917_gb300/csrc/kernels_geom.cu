@@ -8,58 +8,65 @@
 #include "sif_internal.cuh"
 
 // ---------------------------------------------------------------------
-// ghost layers: x ghosts of the interior rows, then y ghosts of every column
+// ghost layers in one pass: a ghost cell takes the value of the interior
+// cell its x and y images map to (reflect / zero-gradient / periodic),
+// negated once per reflecting wall for the matching velocity component --
+// the same values as filling the x ghosts of the interior rows first and
+// then the y ghosts of every column from them
 
-__global__ void k_ghost_x(Grid g, GhostSet s) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int per = SIF_GH * g.ny;
-  if (t >= per * s.n) return;
-  int pl = t / per, r = t % per, m = r % SIF_GH, j = r / SIF_GH;
-  double *a = s.p[pl];
-  bool odd = s.vel[pl] == 1;
-  double vl, vr;
-  switch (g.bc[0]) {
-    case SIF_BC_REFLECT: vl = a[gidx(g, m, j)]; break;
-    case SIF_BC_PERIODIC: vl = a[gidx(g, g.nx - 1 - m, j)]; break;
-    default: vl = a[gidx(g, 0, j)];
+__device__ inline int ghost_image(int i, int n, int bl, int br, bool &flip) {
+  flip = false;
+  if (i < 0) {
+    int m = -1 - i;
+    if (bl == SIF_BC_REFLECT) {
+      flip = true;
+      return m;
+    }
+    return bl == SIF_BC_PERIODIC ? n - 1 - m : 0;
   }
-  switch (g.bc[1]) {
-    case SIF_BC_REFLECT: vr = a[gidx(g, g.nx - 1 - m, j)]; break;
-    case SIF_BC_PERIODIC: vr = a[gidx(g, m, j)]; break;
-    default: vr = a[gidx(g, g.nx - 1, j)];
+  if (i >= n) {
+    int m = i - n;
+    if (br == SIF_BC_REFLECT) {
+      flip = true;
+      return n - 1 - m;
+    }
+    return br == SIF_BC_PERIODIC ? m : n - 1;
   }
-  a[gidx(g, -1 - m, j)] = (odd && g.bc[0] == SIF_BC_REFLECT) ? -vl : vl;
-  a[gidx(g, g.nx + m, j)] = (odd && g.bc[1] == SIF_BC_REFLECT) ? -vr : vr;
+  return i;
 }
 
-__global__ void k_ghost_y(Grid g, GhostSet s) {
+__global__ void k_ghost(Grid g, GhostSet s) {
+  int W = g.nx + 2 * SIF_GH;
+  // ghost cells: the top and bottom strips (full width) and the left and
+  // right strips of the interior rows
+  int strip_y = W * SIF_GH, strip_x = SIF_GH * g.ny;
+  int per = 2 * strip_y + 2 * strip_x;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int W = g.nx + 2 * SIF_GH, per = W * SIF_GH;
   if (t >= per * s.n) return;
-  int pl = t / per, r = t % per, i = r % W - SIF_GH, m = r / W;
+  int pl = t / per, r = t % per, i, j;
+  if (r < 2 * strip_y) {
+    int q = r % strip_y;
+    i = q % W - SIF_GH;
+    j = r < strip_y ? -1 - q / W : g.ny + q / W;
+  } else {
+    r -= 2 * strip_y;
+    int q = r % strip_x;
+    j = q / SIF_GH;
+    i = r < strip_x ? -1 - q % SIF_GH : g.nx + q % SIF_GH;
+  }
+  bool fx, fy;
+  int si = ghost_image(i, g.nx, g.bc[0], g.bc[1], fx);
+  int sj = ghost_image(j, g.ny, g.bc[2], g.bc[3], fy);
   double *a = s.p[pl];
-  bool odd = s.vel[pl] == 2;
-  double vb, vt;
-  switch (g.bc[2]) {
-    case SIF_BC_REFLECT: vb = a[gidx(g, i, m)]; break;
-    case SIF_BC_PERIODIC: vb = a[gidx(g, i, g.ny - 1 - m)]; break;
-    default: vb = a[gidx(g, i, 0)];
-  }
-  switch (g.bc[3]) {
-    case SIF_BC_REFLECT: vt = a[gidx(g, i, g.ny - 1 - m)]; break;
-    case SIF_BC_PERIODIC: vt = a[gidx(g, i, m)]; break;
-    default: vt = a[gidx(g, i, g.ny - 1)];
-  }
-  a[gidx(g, i, -1 - m)] = (odd && g.bc[2] == SIF_BC_REFLECT) ? -vb : vb;
-  a[gidx(g, i, g.ny + m)] = (odd && g.bc[3] == SIF_BC_REFLECT) ? -vt : vt;
+  double v = a[gidx(g, si, sj)];
+  bool neg = (s.vel[pl] == 1 && fx) || (s.vel[pl] == 2 && fy);
+  a[gidx(g, i, j)] = neg ? -v : v;
 }
 
 void launch_fill_ghost(const Grid &g, const GhostSet &s, cudaStream_t st) {
-  int nx_threads = SIF_GH * g.ny * s.n;
-  k_ghost_x<<<(nx_threads + 255) / 256, 256, 0, st>>>(g, s);
-  int ny_threads = (g.nx + 2 * SIF_GH) * SIF_GH * s.n;
-  k_ghost_y<<<(ny_threads + 255) / 256, 256, 0, st>>>(g, s);
-  sif_note_launches(2);
+  int n = (2 * (g.nx + 2 * SIF_GH) * SIF_GH + 2 * SIF_GH * g.ny) * s.n;
+  k_ghost<<<(n + 255) / 256, 256, 0, st>>>(g, s);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -80,6 +87,7 @@ __device__ inline void append_ballot(bool pred, int value, int *list, int *count
 
 __global__ void k_geometry(Grid g, const double *__restrict__ p, double *alpha, double *ax,
                            double *ay, double *sx, double *sy, int *cut, int *ncut) {
+  SIF_TICK();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int W = g.nx + 1;
   int i = t % W, j = t / W;
@@ -142,6 +150,7 @@ void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax
 
 __global__ void k_band(Grid g, const double *__restrict__ p, int *band, int *rext, int *nband,
                        int *nrext) {
+  SIF_TICK();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t % g.nx, j = t / g.nx;
   bool valid = j < g.ny;
@@ -176,6 +185,7 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
 // its one-cell ring (ghosts included) lies on fluid k's side
 
 __global__ void k_tiles(Grid g, const double *__restrict__ p, int *t0, int *t1, int *n) {
+  SIF_TICK();
   int tile = blockIdx.x;
   int tx = tile % g.ntx, ty = tile / g.ntx;
   int i0 = tx * FV_TX - 1, j0 = ty * FV_TY - 1;
@@ -212,6 +222,7 @@ __global__ void k_init_q(Grid g, double *qN0, double *qN1, double *qN2, double *
                          const double *wN1, const double *wN2, const double *wN3,
                          const double *wP0, const double *wP1, const double *wP2,
                          const double *wP3, const double *alpha) {
+  SIF_TICK();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.nx * g.ny) return;
   int i = t % g.nx, j = t / g.nx, c = gidx(g, i, j);
@@ -238,3 +249,5 @@ void launch_init_state(const Grid &g, double *const qN[4], double *const qP[4],
                                             wP[2], wP[3], alpha);
   sif_note_launches(1);
 }
+
+SIF_TU_LAUNCH_READER(geom)

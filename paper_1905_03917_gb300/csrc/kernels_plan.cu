@@ -19,6 +19,7 @@ static int blocks_for(int n, int per) {
 // interaction band and its map
 
 __global__ void k_unmap(const int *__restrict__ band, const int *nband, int *map) {
+  SIF_TICK();
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
     map[band[idx]] = -1;
@@ -26,6 +27,7 @@ __global__ void k_unmap(const int *__restrict__ band, const int *nband, int *map
 
 __global__ void k_band_mapped(Grid g, const double *__restrict__ p, int *band, int *map,
                               int *nband) {
+  SIF_TICK();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t % g.nx, j = t / g.nx;
   bool in = false;
@@ -64,7 +66,9 @@ void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int 
 __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
                             const double *__restrict__ phi, const double *__restrict__ sx,
                             const double *__restrict__ sy, const int *__restrict__ band,
-                            const int *nband, ExtPlan *plan, int cap) {
+                            const int *nband, const int *__restrict__ map, ExtPlan *plan,
+                            int cap) {
+  SIF_TICK();
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
@@ -72,7 +76,7 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
     double nxv, nyv;
     unit_normal(g, phi, i, j, nxv, nyv);
     for (int f = 0; f < 3; f++) {
-      ExtPlan pl = {-1, -1, 0.0, 0.0};
+      ExtPlan pl = {-1, -1, -1, -1, 0.0, 0.0};
       bool target;
       double dx_, dy_;
       if (f < 2) {
@@ -96,10 +100,12 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
         if (den > 0.0) {
           if (wx > 0.0) {
             pl.cx = gidx(g, i + six, j);
+            pl.bx = map[pl.cx];
             pl.wx = wx / den;
           }
           if (wy > 0.0) {
             pl.cy = gidx(g, i, j + siy);
+            pl.by = map[pl.cy];
             pl.wy = wy / den;
           }
         }
@@ -110,66 +116,73 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
 }
 
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
-                      const double *sy, const int *band, const int *nband, ExtPlan *plan,
-                      int cap, int work, cudaStream_t st) {
-  k_ext_setup<<<blocks_for(work, 128), 128, 0, st>>>(g, alpha, phi, sx, sy, band, nband, plan, cap);
+                      const double *sy, const int *band, const int *nband, const int *map,
+                      ExtPlan *plan, int cap, int work, cudaStream_t st) {
+  k_ext_setup<<<blocks_for(work, 128), 128, 0, st>>>(g, alpha, phi, sx, sy, band, nband, map,
+                                                    plan, cap);
   sif_note_launches(1);
 }
 
-// one Jacobi sweep of fields [f0, f0 + nf) (blockIdx.y selects the field);
-// each field has ncomp planes
+// Jacobi sweeps of fields [f0, f0 + nf) (blockIdx.y selects the field),
+// ping-ponging between two band-indexed buffers: sweep 0 reads the planes,
+// later sweeps read the previous sweep's buffer for band neighbours and the
+// planes for neighbours outside the band (whose values never change)
 struct ExtFields {
   double *p[3][4];
   int ncomp[3];
 };
 
 __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ plan, int cap,
-                            const int *__restrict__ band, const int *nband, double *tmp) {
+                            const int *__restrict__ band, const int *nband,
+                            const double *__restrict__ src, double *dst) {
+  SIF_TICK();
   int n = *nband;
   int f = f0 + blockIdx.y;
   int nc = F.ncomp[f];
   const ExtPlan *P = plan + (size_t)f * cap;
-  double *out = tmp + (size_t)blockIdx.y * 4 * n;
+  const size_t slot = (size_t)blockIdx.y * 4 * cap;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
     ExtPlan pl = P[idx];
     for (int m = 0; m < nc; m++) {
       const double *a = F.p[f][m];
+      const double *b = src ? src + slot + (size_t)m * cap : nullptr;
       double v;
       if (pl.cx < 0 && pl.cy < 0) {
-        v = a[c];
+        v = b ? b[idx] : a[c];
       } else {
         v = 0.0;
-        if (pl.cx >= 0) v += pl.wx * a[pl.cx];
-        if (pl.cy >= 0) v += pl.wy * a[pl.cy];
+        if (pl.cx >= 0) v += pl.wx * ((b && pl.bx >= 0) ? b[pl.bx] : a[pl.cx]);
+        if (pl.cy >= 0) v += pl.wy * ((b && pl.by >= 0) ? b[pl.by] : a[pl.cy]);
       }
-      out[(size_t)m * n + idx] = v;
+      dst[slot + (size_t)m * cap + idx] = v;
     }
   }
 }
 
-// write the sweep back; after the last sweep of the stencil states, fold
-// the extended cells' wave speeds into the Lax-Friedrichs maxima
-__global__ void k_ext_scatter(Grid g, ExtFields F, int f0, const int *__restrict__ band,
-                              const int *nband, const double *tmp,
-                              const double *__restrict__ alpha, int last, Scalars *sc) {
+// write the last sweep back; for the stencil states fold the extended
+// cells' wave speeds into the Lax-Friedrichs maxima
+__global__ void k_ext_scatter(Grid g, ExtFields F, int f0, int cap, const int *__restrict__ band,
+                              const int *nband, const double *buf,
+                              const double *__restrict__ alpha, Scalars *sc) {
+  SIF_TICK();
   int n = *nband;
   int f = f0 + blockIdx.y;
   int nc = F.ncomp[f];
-  const double *in = tmp + (size_t)blockIdx.y * 4 * n;
+  const double *in = buf + (size_t)blockIdx.y * 4 * cap;
   double lx = 0.0, ly = 0.0;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
-    for (int m = 0; m < nc; m++) F.p[f][m][c] = in[(size_t)m * n + idx];
-    if (last && f < 2 && !(vol_k(alpha, f, c) > SIF_ALPHA_REAL)) {
-      double r = in[idx], u = in[(size_t)n + idx], v = in[(size_t)2 * n + idx],
-             p = in[(size_t)3 * n + idx];
+    for (int m = 0; m < nc; m++) F.p[f][m][c] = in[(size_t)m * cap + idx];
+    if (f < 2 && !(vol_k(alpha, f, c) > SIF_ALPHA_REAL)) {
+      double r = in[idx], u = in[(size_t)cap + idx], v = in[(size_t)2 * cap + idx],
+             p = in[(size_t)3 * cap + idx];
       double cs = sqrt(fmax(g.gamma[f] * (p + g.pinf[f]) / r, 0.0));
       lx = fmax(lx, fabs(u) + cs);
       ly = fmax(ly, fabs(v) + cs);
     }
   }
-  if (last && f < 2) {
+  if (f < 2) {
     __shared__ double sa[32], sb[32];
     lx = warp_max(lx);
     ly = warp_max(ly);
@@ -206,12 +219,16 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
   F.ncomp[0] = F.ncomp[1] = 4;
   F.ncomp[2] = 2;
   dim3 grid(blocks_for(work, 128), nf);
+  double *buf[2] = {tmp, tmp + (size_t)8 * cap};
+  const double *src = nullptr;
+  int cur = 0;
   for (int it = 0; it < g.ext_iters; it++) {
-    k_ext_sweep<<<grid, 128, 0, st>>>(F, f0, plan, cap, band, nband, tmp);
-    k_ext_scatter<<<grid, 128, 0, st>>>(g, F, f0, band, nband, tmp, alpha,
-                                        it == g.ext_iters - 1, sc);
+    k_ext_sweep<<<grid, 128, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur]);
+    src = buf[cur];
+    cur ^= 1;
   }
-  sif_note_launches(2 * g.ext_iters);
+  k_ext_scatter<<<grid, 128, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, sc);
+  sif_note_launches(g.ext_iters + 1);
 }
 
 // ---------------------------------------------------------------------
@@ -267,6 +284,7 @@ struct MixQ {
 __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__ alpha,
                             const double *__restrict__ phi, const int *__restrict__ band,
                             const int *nband, MixPlan *plan, int cap) {
+  SIF_TICK();
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
@@ -283,6 +301,7 @@ __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__
 __global__ void k_mix_apply(Grid g, int mask, MixQ Q, const int *__restrict__ map,
                             const MixPlan *__restrict__ plan, int cap,
                             const int *__restrict__ band, const int *nband, double *tmp) {
+  SIF_TICK();
   int k = blockIdx.y;
   if (!(mask & (1 << k))) return;
   int n = *nband;
@@ -320,6 +339,7 @@ __global__ void k_mix_apply(Grid g, int mask, MixQ Q, const int *__restrict__ ma
 
 __global__ void k_mix_scatter(int mask, MixQ Q, const int *__restrict__ band, const int *nband,
                               const double *tmp) {
+  SIF_TICK();
   int k = blockIdx.y;
   if (!(mask & (1 << k))) return;
   int n = *nband;
@@ -345,3 +365,5 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
   k_mix_scatter<<<dim3(b, 2), 128, 0, st>>>(mask, Q, band, nband, tmp);
   sif_note_launches(3);
 }
+
+SIF_TU_LAUNCH_READER(plan)

@@ -52,13 +52,40 @@ struct Scalars {
   int n_band_ls, n_rext;      // level-set step band and its face neighbours
   int n_cut, n_tiles[2];
   double dtk_raw[2];
+  double dt2_first;             // fluid-2 step chosen at the start of the cycle
   unsigned long long updates;   // (cell, fluid) stage updates issued
+  // finite-volume launch timing on the GPU's global timer (graph-safe):
+  // each launch keeps its earliest block start and latest block end, the
+  // last block to finish adds the span to fv_ns
+  int timing;
+  unsigned int fv_blocks_done;
+  unsigned long long fv_t0, fv_t1, fv_ns, fv_launches;
 };
+
+// every kernel counts its own launches on the device (one atomic by the
+// first thread of the first block); each translation unit has its counter
+static __device__ unsigned long long g_tu_launches;
+#define SIF_TICK()                                                                    \
+  do {                                                                                \
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)     \
+      atomicAdd(&g_tu_launches, 1ull);                                                \
+  } while (0)
+unsigned long long sif_launches_geom();
+unsigned long long sif_launches_band();
+unsigned long long sif_launches_plan();
+unsigned long long sif_launches_fv();
+#define SIF_TU_LAUNCH_READER(name)                                                    \
+  unsigned long long sif_launches_##name() {                                          \
+    unsigned long long v = 0;                                                         \
+    cudaMemcpyFromSymbol(&v, g_tu_launches, sizeof(v));                               \
+    return v;                                                                         \
+  }
 
 // upwind neighbours (cell indices, -1 = unused) and normalised weights of
 // one extension target; cx = cy = -1 marks a cell that is not a target
 struct ExtPlan {
-  int cx, cy;
+  int cx, cy;  // upwind neighbours (cell index) or -1
+  int bx, by;  // their band positions, -1 outside the band
   double wx, wy;
 };
 
@@ -291,16 +318,17 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
                  const int *nband, MixPlan *plan, int cap, int work, double *tmp,
                  cudaStream_t st);
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
-                      const double *sy, const int *band, const int *nband, ExtPlan *plan,
-                      int cap, int work, cudaStream_t st);
+                      const double *sy, const int *band, const int *nband, const int *map,
+                      ExtPlan *plan, int cap, int work, cudaStream_t st);
 // f0 = 0, nf = 2: stencil states of both fluids; f0 = 2, nf = 1: level-set velocity
 void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
                        const int *band, const int *nband, double *tmp, const double *alpha,
                        Scalars *sc, cudaStream_t st);
 
-void launch_prim(const Grid &g, int k, double *const q[4], double *const w[4],
-                 const double *alpha, const int *tiles, int tile_cap, Scalars *sc, cudaStream_t st);
+void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], double *const wN[4],
+                  double *const wP[4], const double *alpha, const int *tilesN,
+                  const int *tilesP, int tile_cap, Scalars *sc, cudaStream_t st);
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
                       double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
@@ -310,6 +338,8 @@ void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *ph
                      int band_cap, double *tmp, const double *dtp, cudaStream_t st);
 void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, const int *nrext,
                    int rext_cap, double *tmp, cudaStream_t st);
+// shared: 1 = Eq. 8, 0 = Eq. 9, -1 = Eq. 8 on the first sub-step (device
+// decides), -2 = Eq. 8 on the last sub-step (device decides)
 void launch_record(const Grid &g, int shared, const int *cut, int cut_cap, const double *xn0,
                    const double *xn1, const double *xn2, double *xc0, double *xc1, double *xc2,
                    Scalars *sc, cudaStream_t st);
@@ -324,6 +354,7 @@ void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], d
                       int nblk, double *out, cudaStream_t st);
 void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st);
 
+void fv_prepare();
 void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      double *const base[4], double *const cur[4], double *const w[4],
                      const double *ax, const double *ay, const double *sx, const double *sy,
@@ -339,3 +370,13 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
 #define SCHED_RESET_MAX 5   // zero the CFL / LF maxima before an interaction step
 #define SCHED_T_SINGLE 6    // t += dt
 #define SCHED_T_CYCLE 7     // t += dt1
+#define SCHED_DT2 8         // fluid-2 dt from the latest interaction
+#define SCHED_LAST 9        // count the sub-step, last-substep test, theta
+
+// conditions of the device-driven cycle graph (cudaGraphSetConditional)
+#define COND_CYCLE 0        // h0 = single step, h1 = cycle with f1 = 0, h2 = cycle with f1 = 1
+#define COND_NOT_FIRST 1    // h0 = sub-step after the first
+#define COND_LAST 2         // h0 = last sub-step, h1 = not last
+#define COND_LOOP 3         // h0 = keep sub-cycling
+void launch_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
+                 cudaGraphConditionalHandle h2, int max_sub, cudaStream_t st);
