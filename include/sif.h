@@ -140,6 +140,39 @@ int sif_save(sif_ctx *ctx, void *buf, size_t *len);
  * SIF_EINVAL if the buffer does not match. */
 int sif_load(sif_ctx *ctx, const void *buf, size_t len);
 
+/* Tile shape (output cells per CTA) of the finite-volume kernel: one of
+ * 32x8 (default), 32x4, 16x8, 16x16, 64x4.  Results do not depend on it;
+ * the autotuner (paper_1905_03917_gb300/autotune.py) picks the fastest
+ * per grid-size bucket.  SIF_EINVAL for other shapes.  Synchronises. */
+int sif_set_tile_shape(sif_ctx *ctx, int tx, int ty);
+int sif_get_tile_shape(const sif_ctx *ctx, int *tx, int *ty);
+
+/* ---------------------------------------------------------------------
+ * Batches of independent problems (uneven grid sizes) advanced together:
+ * every instance's accelerated cycle is one device-driven CUDA graph
+ * (conditional nodes follow each instance's own schedule), and a batch
+ * cycle launches all of them as parallel branches of one graph.  Each
+ * instance is an ordinary context (sif_batch_instance) for initial data,
+ * state access, tile shape and integrals. */
+typedef struct sif_batch sif_batch;
+
+/* n contexts from cfgs[0..n-1] (their cuda_stream fields are ignored: the
+ * batch owns its streams).  SIF_EINVAL / SIF_ECUDA as for sif_create. */
+int sif_batch_create(int n, const sif_config *cfgs, sif_batch **out);
+
+/* The i-th instance's context (owned by the batch: do not destroy). */
+int sif_batch_instance(sif_batch *b, int i, sif_ctx **out);
+
+/* ncycles accelerated cycles of every instance (each at its own time
+ * step and sub-step count).  *cell_updates (nullable) receives the
+ * (cell, fluid) stage updates of all instances.  Every instance must have
+ * been initialised.  Synchronises at the end; the first error of any
+ * instance is returned (sif_batch_last_error names the instance). */
+int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates);
+
+const char *sif_batch_last_error(const sif_batch *b);
+void sif_batch_destroy(sif_batch *b);
+
 /* Measurement counters of one context (no counterpart in the paper). */
 typedef struct {
   long long kernel_launches;  /* libsif kernels launched on this context */

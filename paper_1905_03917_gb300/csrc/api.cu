@@ -48,6 +48,8 @@ struct sif_ctx {
   int use_graphs;
   int graph_bucket;  // band grid size baked into the graphs
   cudaGraphExec_t g_cycle, g_single;
+  cudaGraph_t g_cycle_tmpl;  // kept for embedding in batch graphs
+  int graph_gen;             // bumped whenever the graphs are rebuilt
   int inited;
   int last_status;
   char err[256];
@@ -77,6 +79,7 @@ static void set_err(sif_ctx *c, const char *fmt, ...) {
   } while (0)
 
 static int ensure_graphs(sif_ctx *c);
+static void free_graphs(sif_ctx *c);
 
 static int check_launch(sif_ctx *c, const char *where) {
   cudaError_t e = cudaGetLastError();
@@ -170,14 +173,17 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.band = f.band;
   g.ext_iters = f.ext_iters;
   g.reinit_iters = f.reinit_iters;
-  g.ntx = (f.nx + FV_TX - 1) / FV_TX;
-  g.nty = (f.ny + FV_TY - 1) / FV_TY;
+  g.tx = FV_TX;
+  g.ty = FV_TY;
+  g.ntx = (f.nx + g.tx - 1) / g.tx;
+  g.nty = (f.ny + g.ty - 1) / g.ty;
   c->NP = (size_t)g.PX * g.PY;
 
   // one pool carved into 256-byte aligned pieces; a first pass over the
   // same carving (with a null base) measures the exact size
   size_t ncell = (size_t)f.nx * f.ny;
-  size_t ntiles = (size_t)g.ntx * g.nty;
+  // tile lists sized for the smallest supported tile (16 x 8 or 32 x 4)
+  size_t ntiles = (size_t)((f.nx + 15) / 16) * ((f.ny + 3) / 4);
   char *base = nullptr;
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -268,8 +274,7 @@ extern "C" void sif_destroy(sif_ctx *c) {
   cudaSetDevice(c->cfg.device);
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
-  if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
-  if (c->g_single) cudaGraphExecDestroy(c->g_single);
+  free_graphs(c);
   for (int i = 0; i < 4; i++)
     if (c->cap[i]) cudaStreamDestroy(c->cap[i]);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -729,7 +734,10 @@ static void graph_cycle_body(sif_ctx *c, int f1) {
 static void free_graphs(sif_ctx *c) {
   if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
   if (c->g_single) cudaGraphExecDestroy(c->g_single);
+  if (c->g_cycle_tmpl) cudaGraphDestroy(c->g_cycle_tmpl);
   c->g_cycle = c->g_single = nullptr;
+  c->g_cycle_tmpl = nullptr;
+  c->graph_gen++;
 }
 
 static int bucket_for(int n) {
@@ -778,7 +786,8 @@ static int build_graphs(sif_ctx *c) {
   c->band_work = saved_work;
   if (!c->gerr && gc) GCK(cudaGraphInstantiate(&c->g_cycle, gc, 0));
   if (!c->gerr && gs) GCK(cudaGraphInstantiate(&c->g_single, gs, 0));
-  if (gc) cudaGraphDestroy(gc);
+  if (gc && !c->gerr) c->g_cycle_tmpl = gc;
+  else if (gc) cudaGraphDestroy(gc);
   if (gs) cudaGraphDestroy(gs);
   cudaGetLastError();
   if (c->gerr) {
@@ -1074,4 +1083,169 @@ extern "C" int sif_profile_read(sif_ctx *c, sif_profile *out) {
   out->fv_ms = (double)c->hsc->fv_ns * 1e-6;
   out->fv_cell_updates = (long long)(c->hsc->updates - c->updates0);
   return SIF_OK;
+}
+
+// ---------------------------------------------------------------------
+// tile shape of the finite-volume kernel (chosen by the autotuner)
+
+extern "C" int sif_set_tile_shape(sif_ctx *c, int tx, int ty) {
+  if (!c) return SIF_EINVAL;
+  if (!fv_shape_supported(tx, ty)) {
+    set_err(c, "unsupported tile shape %d x %d", tx, ty);
+    return SIF_EINVAL;
+  }
+  if (c->g.tx == tx && c->g.ty == ty) return SIF_OK;
+  cudaSetDevice(c->cfg.device);
+  CK(cudaStreamSynchronize(c->st));
+  c->g.tx = tx;
+  c->g.ty = ty;
+  c->g.ntx = (c->g.nx + tx - 1) / tx;
+  c->g.nty = (c->g.ny + ty - 1) / ty;
+  free_graphs(c);
+  if (c->inited) {
+    geometry(c);  // tile lists for the new shape
+    int rc = check_launch(c, "tile shape");
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->st));
+  }
+  return SIF_OK;
+}
+
+extern "C" int sif_get_tile_shape(const sif_ctx *c, int *tx, int *ty) {
+  if (!c || !tx || !ty) return SIF_EINVAL;
+  *tx = c->g.tx;
+  *ty = c->g.ty;
+  return SIF_OK;
+}
+
+// ---------------------------------------------------------------------
+// batches of independent instances
+
+struct sif_batch {
+  int n;
+  sif_ctx **ctx;
+  cudaStream_t st;
+  cudaGraphExec_t exec;
+  std::vector<int> gens;  // instance graph generations the batch graph embeds
+  int parent_ok;          // 0 after a failed attempt: launch instance graphs directly
+  char err[256];
+};
+
+extern "C" int sif_batch_create(int n, const sif_config *cfgs, sif_batch **out) {
+  if (!out) return SIF_EINVAL;
+  *out = nullptr;
+  if (n < 1 || !cfgs) return SIF_EINVAL;
+  sif_batch *b = new (std::nothrow) sif_batch();
+  if (!b) return SIF_ECUDA;
+  b->n = n;
+  b->parent_ok = 1;
+  b->ctx = new (std::nothrow) sif_ctx *[n]();
+  if (!b->ctx) {
+    delete b;
+    return SIF_ECUDA;
+  }
+  int rc = SIF_OK;
+  for (int i = 0; i < n && rc == SIF_OK; i++) {
+    sif_config f = cfgs[i];
+    f.cuda_stream = nullptr;  // every instance gets its own stream
+    rc = sif_create(&f, &b->ctx[i]);
+  }
+  if (rc == SIF_OK && cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess)
+    rc = SIF_ECUDA;
+  if (rc != SIF_OK) {
+    sif_batch_destroy(b);
+    return rc;
+  }
+  snprintf(b->err, sizeof(b->err), "ok");
+  *out = b;
+  return SIF_OK;
+}
+
+extern "C" int sif_batch_instance(sif_batch *b, int i, sif_ctx **out) {
+  if (!b || !out || i < 0 || i >= b->n) return SIF_EINVAL;
+  *out = b->ctx[i];
+  return SIF_OK;
+}
+
+extern "C" const char *sif_batch_last_error(const sif_batch *b) { return b ? b->err : "null batch"; }
+
+extern "C" void sif_batch_destroy(sif_batch *b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->ctx)
+    for (int i = 0; i < b->n; i++) sif_destroy(b->ctx[i]);
+  delete[] b->ctx;
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+// one graph whose parallel branches are the instances' cycle graphs
+static int batch_build(sif_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  for (int i = 0; i < b->n && e == cudaSuccess; i++) {
+    cudaGraphNode_t node;
+    e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, b->ctx[i]->g_cycle_tmpl);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b->exec = nullptr;
+    b->parent_ok = 0;
+    return SIF_ECUDA;
+  }
+  b->gens.resize(b->n);
+  for (int i = 0; i < b->n; i++) b->gens[i] = b->ctx[i]->graph_gen;
+  return SIF_OK;
+}
+
+extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates) {
+  if (!b || ncycles < 0) return SIF_EINVAL;
+  std::vector<unsigned long long> upd0(b->n);
+  bool rebuild = !b->exec;
+  for (int i = 0; i < b->n; i++) {
+    sif_ctx *c = b->ctx[i];
+    if (!c->inited || c->cfg.rk_order != 2) {
+      snprintf(b->err, sizeof(b->err), "instance %d: %s", i,
+               c->inited ? "rk_order must be 2" : "not initialised");
+      return c->inited ? SIF_EINVAL : SIF_ESTATE;
+    }
+    int rc = begin_call(c, 0.0, &upd0[i]);
+    if (rc == SIF_OK) rc = ensure_graphs(c);
+    if (rc != SIF_OK) {
+      snprintf(b->err, sizeof(b->err), "instance %d: graph set-up failed: %s", i, c->err);
+      return rc == SIF_OK ? SIF_ECUDA : rc;
+    }
+    if (b->exec && b->gens.size() == (size_t)b->n && b->gens[i] != c->graph_gen) rebuild = true;
+  }
+  if (rebuild && b->parent_ok) batch_build(b);
+  for (int i = 0; i < b->n; i++) cudaStreamSynchronize(b->ctx[i]->st);
+  for (int n = 0; n < ncycles; n++) {
+    if (b->exec) {
+      if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) break;
+    } else {
+      for (int i = 0; i < b->n; i++) cudaGraphLaunch(b->ctx[i]->g_cycle, b->ctx[i]->st);
+    }
+  }
+  cudaError_t e = b->exec ? cudaStreamSynchronize(b->st) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    snprintf(b->err, sizeof(b->err), "batch cycle: %s", cudaGetErrorString(e));
+    return SIF_ECUDA;
+  }
+  long long total = 0;
+  int first_rc = SIF_OK;
+  for (int i = 0; i < b->n; i++) {
+    int rc = finish(b->ctx[i], nullptr, upd0[i]);
+    total += (long long)(b->ctx[i]->hsc->updates - upd0[i]);
+    if (rc != SIF_OK && first_rc == SIF_OK) {
+      first_rc = rc;
+      snprintf(b->err, sizeof(b->err), "instance %d: %s", i, b->ctx[i]->err);
+    }
+  }
+  if (cell_updates) *cell_updates = total;
+  return first_rc;
 }

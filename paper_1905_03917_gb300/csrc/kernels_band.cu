@@ -60,7 +60,7 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
   double *w0 = P.w[k][0], *w1 = P.w[k][1], *w2 = P.w[k][2], *w3 = P.w[k][3];
   int tile = P.tiles[k][blockIdx.x];
   int tx = tile % g.ntx, ty = tile / g.ntx;
-  int i = tx * FV_TX + (threadIdx.x % FV_TX), j = ty * FV_TY + threadIdx.x / FV_TX;
+  int i = tx * g.tx + (threadIdx.x % g.tx), j = ty * g.ty + threadIdx.x / g.tx;
   double lx = 0.0, ly = 0.0, sm = 0.0;
   if (i < g.nx && j < g.ny) {
     int c = gidx(g, i, j);
@@ -103,7 +103,7 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
   }
   P.tiles[0] = tilesN;
   P.tiles[1] = tilesP;
-  k_prim<<<dim3(tile_cap, 2), FV_TX * FV_TY, 0, st>>>(g, P, alpha, sc->n_tiles, sc);
+  k_prim<<<dim3(tile_cap, 2), g.tx * g.ty, 0, st>>>(g, P, alpha, sc->n_tiles, sc);
   sif_note_launches(1);
 }
 

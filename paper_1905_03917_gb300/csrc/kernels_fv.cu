@@ -3,21 +3,19 @@
 // face, face fluxes weighted by the fluid's apertures, the interface
 // exchange flux X in cut cells and the Runge-Kutta stage combination.
 //
-// One CTA owns a FV_TX x FV_TY tile of output cells.  The split fluxes of
-// the tile and its 3-cell halo are built once in shared memory, every
+// One CTA owns a TX x TY tile of output cells (a compile-time shape chosen
+// per context from a small set; see sif_set_tile_shape).  The split fluxes
+// of the tile and its 3-cell halo are built once in shared memory, every
 // face flux is reconstructed once per CTA, and the update is written in
 // place (a cell reads only its own conserved values).  Only the tiles in
 // which the fluid can have an open face are launched.  FP64 throughout;
 // the reconstruction uses one division per face and component.
 #include "sif_internal.cuh"
 
-#define HX (FV_TX + 6)
-#define HY (FV_TY + 6)
-
 struct FvArgs {
   Grid g;
   int k, s;
-  double a, b;           // RK stage weights
+  double a, b;  // RK stage weights
   double *dst[4];
   const double *base[4];
   const double *cur[4];
@@ -27,7 +25,6 @@ struct FvArgs {
   const int *tiles;
   const int *ntiles;
   const double *dtp;
-  double lfx_dummy;
   const Scalars *sc;
 };
 
@@ -80,11 +77,19 @@ __device__ void fv_timer_block_done(const Scalars *csc, bool worked) {
   }
 }
 
-__device__ __forceinline__ void fv_update_cell(const FvArgs &A, int k, int i, int j, int li, int lj,
-                                               const double *Fx, const double *Fy, bool d2);
+template <int TX, int TY>
+struct FvShape {
+  static constexpr int HX = TX + 6, HY = TY + 6;
+  static constexpr size_t smem() {
+    return sizeof(double) *
+           (size_t)(8 * HX * TY + 8 * TX * HY + 4 * (TX + 1) * TY + 4 * TX * (TY + 1));
+  }
+};
 
-__global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_fv_stage(FvArgs A) {
   SIF_TICK();
+  constexpr int HX = TX + 6, HY = TY + 6;
   const Grid &g = A.g;
   const int k = A.k;
   if ((int)blockIdx.x >= A.ntiles[k]) {
@@ -93,17 +98,17 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
   }
   extern __shared__ double smem[];
   // split fluxes: x for rows of the tile with x-halo, y for columns with y-halo
-  double *fxp = smem;                       // [4][HX*FV_TY]
-  double *fxm = fxp + 4 * HX * FV_TY;       // [4][HX*FV_TY]
-  double *fyp = fxm + 4 * HX * FV_TY;       // [4][FV_TX*HY]
-  double *fym = fyp + 4 * FV_TX * HY;       // [4][FV_TX*HY]
-  double *Fx = fym + 4 * FV_TX * HY;        // [4][(FV_TX+1)*FV_TY]
-  double *Fy = Fx + 4 * (FV_TX + 1) * FV_TY;  // [4][FV_TX*(FV_TY+1)]
+  double *fxp = smem;                   // [4][HX*TY]
+  double *fxm = fxp + 4 * HX * TY;      // [4][HX*TY]
+  double *fyp = fxm + 4 * HX * TY;      // [4][TX*HY]
+  double *fym = fyp + 4 * TX * HY;      // [4][TX*HY]
+  double *Fx = fym + 4 * TX * HY;       // [4][(TX+1)*TY]
+  double *Fy = Fx + 4 * (TX + 1) * TY;  // [4][TX*(TY+1)]
 
   int tile = A.tiles[blockIdx.x];
-  int i0 = (tile % g.ntx) * FV_TX, j0 = (tile / g.ntx) * FV_TY;
+  int i0 = (tile % g.ntx) * TX, j0 = (tile / g.ntx) * TY;
   if (threadIdx.x == 0) {
-    int w_ = min(FV_TX, g.nx - i0), h_ = min(FV_TY, g.ny - j0);
+    int w_ = min(TX, g.nx - i0), h_ = min(TY, g.ny - j0);
     atomicAdd((unsigned long long *)&A.sc->updates, (unsigned long long)(w_ * h_));
   }
   const bool timed = A.sc->timing;
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // phase 1: Lax-Friedrichs split fluxes of the stencil states
-  for (int r = tid; r < HX * FV_TY; r += nth) {
+  for (int r = tid; r < HX * TY; r += nth) {
     int i = i0 - 3 + r % HX, j = j0 + r / HX;
     double fp[4] = {0, 0, 0, 0}, fm[4] = {0, 0, 0, 0};
     if (i <= g.nx + 2 && j < g.ny) {
@@ -133,13 +138,13 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
     }
 #pragma unroll
     for (int m = 0; m < 4; m++) {
-      fxp[m * HX * FV_TY + r] = fp[m];
-      fxm[m * HX * FV_TY + r] = fm[m];
+      fxp[m * HX * TY + r] = fp[m];
+      fxm[m * HX * TY + r] = fm[m];
     }
   }
   if (d2) {
-    for (int r = tid; r < FV_TX * HY; r += nth) {
-      int i = i0 + r % FV_TX, j = j0 - 3 + r / FV_TX;
+    for (int r = tid; r < TX * HY; r += nth) {
+      int i = i0 + r % TX, j = j0 - 3 + r / TX;
       double fp[4] = {0, 0, 0, 0}, fm[4] = {0, 0, 0, 0};
       if (i < g.nx && j <= g.ny + 2) {
         int c = gidx(g, i, j);
@@ -156,8 +161,8 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
       }
 #pragma unroll
       for (int m = 0; m < 4; m++) {
-        fyp[m * FV_TX * HY + r] = fp[m];
-        fym[m * FV_TX * HY + r] = fm[m];
+        fyp[m * TX * HY + r] = fp[m];
+        fym[m * TX * HY + r] = fm[m];
       }
     }
   }
@@ -165,9 +170,9 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
 
   // phase 2: x faces (left face of cell i0 + fi), one (face, component) per item
   const double eps = g.weno_eps;
-  for (int r = tid; r < 4 * (FV_TX + 1) * FV_TY; r += nth) {
-    int m = r / ((FV_TX + 1) * FV_TY), f = r % ((FV_TX + 1) * FV_TY);
-    int fi = f % (FV_TX + 1), fj = f / (FV_TX + 1);
+  for (int r = tid; r < 4 * (TX + 1) * TY; r += nth) {
+    int m = r / ((TX + 1) * TY), f = r % ((TX + 1) * TY);
+    int fi = f % (TX + 1), fj = f / (TX + 1);
     int i = i0 + fi, j = j0 + fj;
     double val = 0.0;
     if (i <= g.nx && j < g.ny) {
@@ -175,83 +180,86 @@ __global__ void __launch_bounds__(FV_TX *FV_TY) k_fv_stage(FvArgs A) {
       if (k == 0) A_ = 1.0 - A_;
       if (A_ != 0.0) {
         // cells i-3..i+2 are at halo columns fi..fi+5
-        const double *P = fxp + m * HX * FV_TY + fj * HX + fi;
-        const double *M = fxm + m * HX * FV_TY + fj * HX + fi;
+        const double *P = fxp + m * HX * TY + fj * HX + fi;
+        const double *M = fxm + m * HX * TY + fj * HX + fi;
         double fl = weno5_fast(P[0], P[1], P[2], P[3], P[4], eps);
         double fr = weno5_fast(M[5], M[4], M[3], M[2], M[1], eps);
         val = A_ * (fl + fr);
       }
     }
-    Fx[m * (FV_TX + 1) * FV_TY + f] = val;
+    Fx[m * (TX + 1) * TY + f] = val;
   }
   if (d2) {
-    for (int r = tid; r < 4 * FV_TX * (FV_TY + 1); r += nth) {
-      int m = r / (FV_TX * (FV_TY + 1)), f = r % (FV_TX * (FV_TY + 1));
-      int fi = f % FV_TX, fj = f / FV_TX;
+    for (int r = tid; r < 4 * TX * (TY + 1); r += nth) {
+      int m = r / (TX * (TY + 1)), f = r % (TX * (TY + 1));
+      int fi = f % TX, fj = f / TX;
       int i = i0 + fi, j = j0 + fj;
       double val = 0.0;
       if (i < g.nx && j <= g.ny) {
         double A_ = A.ay[gidx(g, i, j)];
         if (k == 0) A_ = 1.0 - A_;
         if (A_ != 0.0) {
-          const double *P = fyp + m * FV_TX * HY + fj * FV_TX + fi;
-          const double *M = fym + m * FV_TX * HY + fj * FV_TX + fi;
-          double fl = weno5_fast(P[0], P[FV_TX], P[2 * FV_TX], P[3 * FV_TX], P[4 * FV_TX], eps);
-          double fr = weno5_fast(M[5 * FV_TX], M[4 * FV_TX], M[3 * FV_TX], M[2 * FV_TX],
-                                 M[FV_TX], eps);
+          const double *P = fyp + m * TX * HY + fj * TX + fi;
+          const double *M = fym + m * TX * HY + fj * TX + fi;
+          double fl = weno5_fast(P[0], P[TX], P[2 * TX], P[3 * TX], P[4 * TX], eps);
+          double fr = weno5_fast(M[5 * TX], M[4 * TX], M[3 * TX], M[2 * TX], M[TX], eps);
           val = A_ * (fl + fr);
         }
       }
-      Fy[m * FV_TX * (FV_TY + 1) + f] = val;
+      Fy[m * TX * (TY + 1) + f] = val;
     }
   }
   __syncthreads();
 
   // phase 3: update of the tile's cells
-  int li = tid % FV_TX, lj = tid / FV_TX;
-  int i = i0 + li, j = j0 + lj;
-  if (i < g.nx && j < g.ny) fv_update_cell(A, k, i, j, li, lj, Fx, Fy, d2);
+  const double dt = *A.dtp;
+  const double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
+  const double sgn = k == 0 ? 1.0 : -1.0;
+  for (int r = tid; r < TX * TY; r += nth) {
+    int li = r % TX, lj = r / TX;
+    int i = i0 + li, j = j0 + lj;
+    if (i >= g.nx || j >= g.ny) continue;
+    int c = gidx(g, i, j);
+    bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      const double *fx = Fx + m * (TX + 1) * TY + lj * (TX + 1) + li;
+      double L = (fx[0] - fx[1]) * inv_dx;
+      if (d2) {
+        const double *fy = Fy + m * TX * (TY + 1) + lj * TX + li;
+        L += (fy[0] - fy[TX]) * inv_dy;
+      }
+      if (m > 0 && cut) L += sgn * A.xn[m - 1][c] * inv_dxdy;
+      double cur = A.cur[m][c];
+      double out = A.s == 1 ? cur + dt * L : A.a * A.base[m][c] + A.b * (cur + dt * L);
+      A.dst[m][c] = out;
+    }
+  }
   if (timed) {
     __syncthreads();
     if (threadIdx.x == 0) fv_timer_block_done(A.sc, true);
   }
 }
 
-__device__ __forceinline__ void fv_update_cell(const FvArgs &A, int k, int i, int j, int li, int lj,
-                                               const double *Fx, const double *Fy, bool d2) {
-  const Grid &g = A.g;
-  int c = gidx(g, i, j);
-  double dt = *A.dtp;
-  double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
-  bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
-  double sgn = k == 0 ? 1.0 : -1.0;
-#pragma unroll
-  for (int m = 0; m < 4; m++) {
-    const double *fx = Fx + m * (FV_TX + 1) * FV_TY + lj * (FV_TX + 1) + li;
-    double L = (fx[0] - fx[1]) * inv_dx;
-    if (d2) {
-      const double *fy = Fy + m * FV_TX * (FV_TY + 1) + lj * FV_TX + li;
-      L += (fy[0] - fy[FV_TX]) * inv_dy;
-    }
-    if (m > 0 && cut) L += sgn * A.xn[m - 1][c] * inv_dxdy;
-    double cur = A.cur[m][c];
-    double out = A.s == 1 ? cur + dt * L : A.a * A.base[m][c] + A.b * (cur + dt * L);
-    A.dst[m][c] = out;
-  }
+// the supported tile shapes (output cells per CTA)
+#define FV_SHAPES(X) X(32, 8) X(32, 4) X(16, 8) X(16, 16) X(64, 4)
+
+bool fv_shape_supported(int tx, int ty) {
+#define FV_IS(a, b) \
+  if (tx == a && ty == b) return true;
+  FV_SHAPES(FV_IS)
+#undef FV_IS
+  return false;
 }
 
-static size_t fv_smem_bytes();
-
-// opt the finite-volume kernel into its shared-memory size on the current
+// opt every instantiation into its shared-memory size on the current
 // device (outside any stream capture)
 void fv_prepare() {
-  cudaFuncSetAttribute(k_fv_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)fv_smem_bytes());
-}
-
-static size_t fv_smem_bytes() {
-  return sizeof(double) * (size_t)(8 * HX * FV_TY + 8 * FV_TX * HY + 4 * (FV_TX + 1) * FV_TY +
-                                   4 * FV_TX * (FV_TY + 1));
+#define FV_PREP(a, b)                                                                   \
+  cudaFuncSetAttribute(k_fv_stage<a, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)FvShape<a, b>::smem());
+  FV_SHAPES(FV_PREP)
+#undef FV_PREP
 }
 
 void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
@@ -261,7 +269,6 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st) {
   static const double A2[3] = {0.0, 0.0, 0.5}, B2[3] = {0.0, 1.0, 0.5};
   static const double A3[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
-  size_t smem = fv_smem_bytes();
   FvArgs A;
   A.g = g;
   A.k = k;
@@ -284,10 +291,14 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   A.tiles = tiles;
   A.ntiles = sc->n_tiles;
   A.dtp = dtp;
-  A.lfx_dummy = 0.0;
   A.sc = sc;
-  k_fv_stage<<<tile_cap, FV_TX * FV_TY, smem, st>>>(A);
-  sif_note_launches(1);
+#define FV_LAUNCH(a, b)                                                     \
+  if (g.tx == a && g.ty == b) {                                            \
+    k_fv_stage<a, b><<<tile_cap, a * b, FvShape<a, b>::smem(), st>>>(A);   \
+    return;                                                                \
+  }
+  FV_SHAPES(FV_LAUNCH)
+#undef FV_LAUNCH
 }
 
 SIF_TU_LAUNCH_READER(fv)

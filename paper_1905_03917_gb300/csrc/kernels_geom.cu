@@ -188,12 +188,12 @@ __global__ void k_tiles(Grid g, const double *__restrict__ p, int *t0, int *t1, 
   SIF_TICK();
   int tile = blockIdx.x;
   int tx = tile % g.ntx, ty = tile / g.ntx;
-  int i0 = tx * FV_TX - 1, j0 = ty * FV_TY - 1;
-  int wy = g.dim == 2 ? FV_TY + 2 : 1;
+  int i0 = tx * g.tx - 1, j0 = ty * g.ty - 1;
+  int wy = g.dim == 2 ? g.ty + 2 : 1;
   if (g.dim == 1) j0 = 0;
   int any_pos = 0, any_neg = 0;
-  for (int r = threadIdx.x; r < (FV_TX + 2) * wy; r += blockDim.x) {
-    int i = i0 + r % (FV_TX + 2), j = j0 + r / (FV_TX + 2);
+  for (int r = threadIdx.x; r < (g.tx + 2) * wy; r += blockDim.x) {
+    int i = i0 + r % (g.tx + 2), j = j0 + r / (g.tx + 2);
     if (i < -1 || i > g.nx || j < -1 || j > g.ny) continue;
     double v = p[gidx(g, i, j)];
     if (v >= 0.0) any_pos = 1;

@@ -17,7 +17,7 @@
 // this; round-off slivers take extended states instead
 #define SIF_ALPHA_REAL 1e-6
 
-// fv tile (outputs per CTA) of the cut-cell update kernel
+// default finite-volume tile (outputs per CTA); others: sif_set_tile_shape
 #define FV_TX 32
 #define FV_TY 8
 
@@ -33,7 +33,8 @@ struct Grid {
   double gamma[2], pinf[2];
   double cfl, weno_eps, mix_alpha, band;
   int ext_iters, reinit_iters;
-  int ntx, nty;  // fv tiles
+  int tx, ty;    // finite-volume tile shape (output cells per CTA)
+  int ntx, nty;  // tiles per direction
 };
 
 // Scalars that live in device memory so that a whole step can run without
@@ -355,6 +356,7 @@ void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], d
 void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st);
 
 void fv_prepare();
+bool fv_shape_supported(int tx, int ty);
 void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      double *const base[4], double *const cur[4], double *const w[4],
                      const double *ax, const double *ay, const double *sx, const double *sy,

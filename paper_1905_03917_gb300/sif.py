@@ -24,7 +24,9 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif_integrals", "sif_get_state", "sif_set_state", "sif_get_time",
            "sif_last_error", "sif_destroy", "sif_save", "sif_load",
            "sif_profile_enable", "sif_profile_read", "sif_measure_fp64_peak",
-           "sif_integrals_noalloc"]
+           "sif_integrals_noalloc", "sif_set_tile_shape", "sif_get_tile_shape",
+           "sif_batch_create", "sif_batch_instance", "sif_batch_step_multi_dt",
+           "sif_batch_last_error", "sif_batch_destroy"]
 
 
 class SifError(RuntimeError):
@@ -91,10 +93,21 @@ def load(path: str | None = None):
     L.sif_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
     L.sif_measure_fp64_peak.argtypes = [I, ctypes.POINTER(D)]
     L.sif_integrals_noalloc.argtypes = [P, P, I, I, D, D, P, P]
+    L.sif_set_tile_shape.argtypes = [P, I, I]
+    L.sif_get_tile_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.sif_batch_create.argtypes = [I, ctypes.POINTER(Config), ctypes.POINTER(P)]
+    L.sif_batch_instance.argtypes = [P, I, ctypes.POINTER(P)]
+    L.sif_batch_step_multi_dt.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong)]
+    L.sif_batch_last_error.argtypes = [P]
+    L.sif_batch_last_error.restype = ctypes.c_char_p
+    L.sif_batch_destroy.argtypes = [P]
+    L.sif_batch_destroy.restype = None
     for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
               L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time,
               L.sif_save, L.sif_load, L.sif_profile_enable, L.sif_profile_read,
-              L.sif_measure_fp64_peak, L.sif_integrals_noalloc):
+              L.sif_measure_fp64_peak, L.sif_integrals_noalloc, L.sif_set_tile_shape,
+              L.sif_get_tile_shape, L.sif_batch_create, L.sif_batch_instance,
+              L.sif_batch_step_multi_dt):
         f.restype = I
     _lib = L
     return L
@@ -165,9 +178,13 @@ def integrals_noalloc(q_N, q_P, dx, dy, out, stream=None):
 class Solver:
     """One two-fluid problem held on the GPU by libsif."""
 
-    def __init__(self, cfg: dict, stream=None, device=0):
+    def __init__(self, cfg: dict, stream=None, device=0, _handle=None):
         self.cfg = dict(cfg)
         self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        self._owned = _handle is None
+        if _handle is not None:  # an instance owned by a Batch
+            self._h = _handle
+            return
         L = load()
         h = ctypes.c_void_p()
         c = make_config(cfg, stream, device)
@@ -183,7 +200,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "_h", None):
-            load().sif_destroy(self._h)
+            if getattr(self, "_owned", True):
+                load().sif_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -244,6 +262,15 @@ class Solver:
         self._check(load().sif_save(self._h, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)))
         return buf.raw[: n.value]
 
+    def set_tile_shape(self, tx: int, ty: int):
+        self._check(load().sif_set_tile_shape(self._h, int(tx), int(ty)))
+
+    @property
+    def tile_shape(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(load().sif_get_tile_shape(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def profile(self, enable: bool = True):
         self._check(load().sif_profile_enable(self._h, 1 if enable else 0))
 
@@ -263,3 +290,51 @@ class Solver:
         v = ctypes.c_double()
         self._check(load().sif_get_time(self._h, ctypes.byref(v)))
         return v.value
+
+
+class Batch:
+    """Independent two-fluid problems advanced together (one graph launch
+    per batch cycle; see sif_batch_* in include/sif.h)."""
+
+    def __init__(self, cfgs, device=0):
+        L = load()
+        n = len(cfgs)
+        arr = (Config * n)(*[make_config(c, None, device) for c in cfgs])
+        h = ctypes.c_void_p()
+        rc = L.sif_batch_create(n, arr, ctypes.byref(h))
+        if rc != OK:
+            raise SifError(rc, "sif_batch_create failed")
+        self._h = h
+        self.instances = []
+        for i, c in enumerate(cfgs):
+            ih = ctypes.c_void_p()
+            rc = L.sif_batch_instance(h, i, ctypes.byref(ih))
+            if rc != OK:
+                raise SifError(rc, "sif_batch_instance failed")
+            self.instances.append(Solver(c, _handle=ih))
+
+    def __len__(self):
+        return len(self.instances)
+
+    def __getitem__(self, i):
+        return self.instances[i]
+
+    def step_multi_dt(self, ncycles=1):
+        n = ctypes.c_longlong(0)
+        rc = load().sif_batch_step_multi_dt(self._h, int(ncycles), ctypes.byref(n))
+        if rc != OK:
+            raise SifError(rc, load().sif_batch_last_error(self._h).decode())
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for s in self.instances:
+                s._h = None
+            load().sif_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
