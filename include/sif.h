@@ -72,7 +72,9 @@ typedef struct {
   double band;           /* narrow-band half-width in cells, 6 */
   int flux_correction;   /* 1 = interfacial flux correction on (Eq. 8-9); 0 for tests */
   int force_ratio_one;   /* test switch: run the multi-dt cycle with dt1 = dt2 */
-  void *cuda_stream;     /* cudaStream_t to issue work on; NULL = the legacy default stream */
+  void *cuda_stream;     /* cudaStream_t to issue work on; NULL = a private stream of the
+                            context, created blocking (ordered with the legacy default
+                            stream; a stream capture needs a non-legacy stream) */
   int device;            /* CUDA device ordinal */
 } sif_config;
 
@@ -171,6 +173,10 @@ int sif_batch_instance(sif_batch *b, int i, sif_ctx **out);
 int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates);
 
 const char *sif_batch_last_error(const sif_batch *b);
+
+/* 1 if the last batch step ran as one graph launch per batch cycle, 0 if
+ * it fell back to one graph launch per instance and cycle. */
+int sif_batch_one_graph(const sif_batch *b);
 void sif_batch_destroy(sif_batch *b);
 
 /* Measurement counters of one context (no counterpart in the paper). */

@@ -731,6 +731,21 @@ static void graph_cycle_body(sif_ctx *c, int f1) {
   launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
 }
 
+// one accelerated cycle, captured onto c->st (which must be capturing)
+static void capture_cycle(sif_ctx *c) {
+  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  cudaGraphConditionalHandle hs = new_handle(c), h0 = new_handle(c), h1 = new_handle(c);
+  eval(c, c->q);
+  launch_sched(SCHED_CYCLE_BEGIN, c->sc, cfl, thr, c->cfg.force_ratio_one, c->st);
+  launch_cond(COND_CYCLE, c->sc, hs, h0, h1, 0, c->st);
+  cond_node(c, hs, false, [&] {
+    single_step_after_eval(c, &c->sc->dt);
+    launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+  });
+  cond_node(c, h0, false, [&] { graph_cycle_body(c, 0); });
+  cond_node(c, h1, false, [&] { graph_cycle_body(c, 1); });
+}
+
 static void free_graphs(sif_ctx *c) {
   if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
   if (c->g_single) cudaGraphExecDestroy(c->g_single);
@@ -758,18 +773,7 @@ static int build_graphs(sif_ctx *c) {
   const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
   // accelerated cycle
   GCK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  if (!c->gerr) {
-    cudaGraphConditionalHandle hs = new_handle(c), h0 = new_handle(c), h1 = new_handle(c);
-    eval(c, c->q);
-    launch_sched(SCHED_CYCLE_BEGIN, c->sc, cfl, thr, c->cfg.force_ratio_one, c->st);
-    launch_cond(COND_CYCLE, c->sc, hs, h0, h1, 0, c->st);
-    cond_node(c, hs, false, [&] {
-      single_step_after_eval(c, &c->sc->dt);
-      launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
-    });
-    cond_node(c, h0, false, [&] { graph_cycle_body(c, 0); });
-    cond_node(c, h1, false, [&] { graph_cycle_body(c, 1); });
-  }
+  if (!c->gerr) capture_cycle(c);
   cudaError_t e = cudaStreamEndCapture(c->st, &gc);
   if (!c->gerr && e != cudaSuccess) c->gerr = e;
   // original single-time-step method
@@ -1127,6 +1131,7 @@ struct sif_batch {
   cudaStream_t st;
   cudaGraphExec_t exec;
   std::vector<int> gens;  // instance graph generations the batch graph embeds
+  std::vector<cudaEvent_t> events;  // fork/join of the batch capture
   int parent_ok;          // 0 after a failed attempt: launch instance graphs directly
   char err[256];
 };
@@ -1173,6 +1178,7 @@ extern "C" void sif_batch_destroy(sif_batch *b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto ev : b->events) cudaEventDestroy(ev);
   if (b->ctx)
     for (int i = 0; i < b->n; i++) sif_destroy(b->ctx[i]);
   delete[] b->ctx;
@@ -1180,16 +1186,37 @@ extern "C" void sif_batch_destroy(sif_batch *b) {
   delete b;
 }
 
-// one graph whose parallel branches are the instances' cycle graphs
+// one graph whose parallel branches are the instances' cycles: a single
+// capture on the batch stream forks every instance stream off it, captures
+// that instance's cycle (with its conditional nodes) on it, and joins back
 static int batch_build(sif_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  for (int i = 0; i < b->n && e == cudaSuccess; i++) {
-    cudaGraphNode_t node;
-    e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, b->ctx[i]->g_cycle_tmpl);
+  if (b->events.empty()) {
+    b->events.resize(b->n + 1);
+    for (auto &ev : b->events) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(b->events[b->n], b->st);
+  for (int i = 0; i < b->n && e == cudaSuccess; i++) {
+    sif_ctx *c = b->ctx[i];
+    e = cudaStreamWaitEvent(c->st, b->events[b->n], 0);
+    if (e != cudaSuccess) break;
+    int saved = c->band_work;
+    c->band_work = c->graph_bucket;
+    c->gerr = 0;
+    c->capturing = 1;
+    c->cap_depth = 0;
+    capture_cycle(c);
+    c->capturing = 0;
+    c->band_work = saved;
+    if (c->gerr) e = (cudaError_t)c->gerr;
+    if (e == cudaSuccess) e = cudaEventRecord(b->events[i], c->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->events[i], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+  if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
   if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -1249,3 +1276,5 @@ extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cel
   if (cell_updates) *cell_updates = total;
   return first_rc;
 }
+
+extern "C" int sif_batch_one_graph(const sif_batch *b) { return b && b->exec ? 1 : 0; }

@@ -26,7 +26,7 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif_profile_enable", "sif_profile_read", "sif_measure_fp64_peak",
            "sif_integrals_noalloc", "sif_set_tile_shape", "sif_get_tile_shape",
            "sif_batch_create", "sif_batch_instance", "sif_batch_step_multi_dt",
-           "sif_batch_last_error", "sif_batch_destroy"]
+           "sif_batch_last_error", "sif_batch_destroy", "sif_batch_one_graph"]
 
 
 class SifError(RuntimeError):
@@ -102,6 +102,8 @@ def load(path: str | None = None):
     L.sif_batch_last_error.restype = ctypes.c_char_p
     L.sif_batch_destroy.argtypes = [P]
     L.sif_batch_destroy.restype = None
+    L.sif_batch_one_graph.argtypes = [P]
+    L.sif_batch_one_graph.restype = I
     for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
               L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time,
               L.sif_save, L.sif_load, L.sif_profile_enable, L.sif_profile_read,
@@ -325,6 +327,10 @@ class Batch:
         if rc != OK:
             raise SifError(rc, load().sif_batch_last_error(self._h).decode())
         return n.value
+
+    @property
+    def one_graph(self) -> bool:
+        return bool(load().sif_batch_one_graph(self._h))
 
     def close(self):
         if getattr(self, "_h", None):
