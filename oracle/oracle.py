@@ -88,6 +88,16 @@ def lib():
         L.orc_cell_alpha.restype = D
         L.orc_cell_alpha.argtypes = [D, D, D, D]
         L.orc_riemann.argtypes = [dp, dp, dp]
+        L.orc_step_taped.argtypes = [P, dp, dp, dp, dp]
+        L.orc_replay_step.argtypes = [P, D, dp, dp, dp]
+        L.orc_adjoint_step.argtypes = [P, D, dp, dp, dp, dp, dp]
+        L.orc_rhs_frozen.argtypes = [P, dp, dp]
+        L.orc_rhs_adjoint.argtypes = [P, dp, dp, dp]
+        L.orc_mix_adjoint.argtypes = [P, I, dp]
+        L.orc_adjoint_init.argtypes = [P, dp, dp, dp, dp]
+        L.orc_weno5_grad.restype = None
+        L.orc_weno5_grad.argtypes = [dp, D, dp]
+        L.orc_riemann_grad.argtypes = [dp, dp, D, D, dp, dp]
         _lib_handle = L
     return _lib_handle
 
@@ -212,10 +222,77 @@ class Oracle:
     def mix_only(self, k):
         lib().orc_mix_only(self._h, int(k))
 
+    # -- frozen-schedule step and its adjoint (RK2 single-dt) --
+
+    def step_taped(self):
+        """One single-dt step; returns its schedule {dt, lf[8], phi1, phi2}."""
+        n = self.nx * self.ny
+        dt = np.zeros(1)
+        lf, phi1, phi2 = np.empty(8), np.empty(n), np.empty(n)
+        rc = lib().orc_step_taped(self._h, _ptr(dt), _ptr(lf), _ptr(phi1), _ptr(phi2))
+        if rc:
+            raise RuntimeError(f"oracle step failed: {rc}")
+        sh = (self.ny, self.nx)
+        return {"dt": float(dt[0]), "lf": lf, "phi1": phi1.reshape(sh), "phi2": phi2.reshape(sh)}
+
+    def replay_step(self, rec):
+        lf, p1, p2 = _f64(rec["lf"]), _f64(rec["phi1"]), _f64(rec["phi2"])
+        return lib().orc_replay_step(self._h, float(rec["dt"]), _ptr(lf), _ptr(p1), _ptr(p2))
+
+    def rhs_frozen(self, lf):
+        """L of both fluids (2, 4, ny, nx) with LF speeds lf[4] given."""
+        lf, out = _f64(lf), np.empty(8 * self.nx * self.ny)
+        lib().orc_rhs_frozen(self._h, _ptr(lf), _ptr(out))
+        return out.reshape(2, 4, self.ny, self.nx)
+
+    def rhs_adjoint(self, lf, mu):
+        lf, mu = _f64(lf), _f64(mu)
+        out = np.empty_like(mu)
+        lib().orc_rhs_adjoint(self._h, _ptr(lf), _ptr(mu), _ptr(out))
+        return out.reshape(2, 4, self.ny, self.nx)
+
+    def mix_adjoint(self, k, lam):
+        lam = _f64(lam).copy()
+        lib().orc_mix_adjoint(self._h, int(k), _ptr(lam))
+        return lam.reshape(4, self.ny, self.nx)
+
+    def adjoint_init(self, prim_N, prim_P, lam):
+        """Adjoint of the state after init -> adjoint of the primitive fields
+        (2, 4, ny, nx), at the current level set."""
+        pN, pP, li = _f64(prim_N), _f64(prim_P), _f64(lam)
+        out = np.empty(8 * self.nx * self.ny)
+        lib().orc_adjoint_init(self._h, _ptr(pN), _ptr(pP), _ptr(li), _ptr(out))
+        return out.reshape(2, 4, self.ny, self.nx)
+
+    def adjoint_step(self, rec, lam):
+        """lam (2, 4, ny, nx) adjoint of the state after the step -> adjoint of
+        the state before it (the current state)."""
+        lf, p1, p2 = _f64(rec["lf"]), _f64(rec["phi1"]), _f64(rec["phi2"])
+        li = _f64(lam)
+        lo = np.empty_like(li)
+        rc = lib().orc_adjoint_step(self._h, float(rec["dt"]), _ptr(lf), _ptr(p1), _ptr(p2),
+                                    _ptr(li), _ptr(lo))
+        if rc:
+            raise RuntimeError(f"oracle adjoint failed: {rc}")
+        return lo.reshape(2, 4, self.ny, self.nx)
+
 
 def weno5(v, eps=1e-6):
     a = _f64(v)
     return lib().orc_weno5(_ptr(a), float(eps))
+
+
+def weno5_grad(v, eps=1e-6):
+    a, g = _f64(v), np.empty(5)
+    lib().orc_weno5_grad(_ptr(a), float(eps), _ptr(g))
+    return g
+
+
+def riemann_grad(left, right, lam_p, lam_u):
+    """Row vector lam_p dp* + lam_u du* over (rho, u, p) of each side."""
+    L, R, gL, gR = _f64(left), _f64(right), np.empty(3), np.empty(3)
+    lib().orc_riemann_grad(_ptr(L), _ptr(R), float(lam_p), float(lam_u), _ptr(gL), _ptr(gR))
+    return gL, gR
 
 
 def edge_fraction(a, b):

@@ -32,6 +32,15 @@
  *          pinned by exact conservation with the correction on (and its
  *          visible loss with it off) and by the bitwise ratio-one
  *          reduction to the single-step method.
+ *   discrete adjoint of the frozen single-time-step RK2 step and of the
+ *          initialisation (the transposes of every operation of the step
+ *          with its schedule -- dt, Lax-Friedrichs speeds, level sets --
+ *          taken as given) -- pinned by central differences of the
+ *          pointwise pieces (WENO5 with its weights, the Riemann problem),
+ *          a brute-force Jacobian of both right-hand sides on a 16 x 16
+ *          bubble, exact transposition of the mixing, the conservation
+ *          identities of the transposed step, and central differences of
+ *          a wall-pressure functional over 20 replayed steps.
  * Parity unpinned (checked only against the GPU): the number of extension
  * and reinitialisation sweeps and the band width (the paper gives none).
  */
@@ -245,6 +254,45 @@ static int inside(const orc_ctx *o, int i, int j) {
 /* ------------------------------------------------------------------ */
 /* small-cell mixing (Sec. 2.2, last paragraph)                        */
 
+/* targets of small cell (i, j) of fluid k: the normal-direction neighbours
+ * of larger volume fraction; neighbours that are not small cells themselves
+ * are preferred, and only when there is none do smaller (but still larger
+ * than the source) neighbours take part.  Returns the number of targets,
+ * their cells and weights beta (summing to one). */
+static int mix_targets(orc_ctx *o, int k, int i, int j, int tc[3], double beta[3]) {
+  int c = ID(o, i, j);
+  double as = vol(o, k, c);
+  double nxv, nyv;
+  normal(o, o->phi, i, j, &nxv, &nyv);
+  if (k == 0) {
+    nxv = -nxv;
+    nyv = -nyv;
+  }
+  int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+  int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
+  double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
+  int nt = o->c.dim == 2 ? 3 : 1;
+  int keep[3] = {0, 0, 0};
+  double sum = 0.0;
+  for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
+    for (int t = 0; t < nt; t++) {
+      if (!inside(o, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
+      double at = vol(o, k, ID(o, ti[t], tj[t]));
+      if (pass == 0 ? !(at >= o->c.mix_alpha) : !(at > as)) continue;
+      keep[t] = 1;
+      sum += wt[t];
+    }
+  if (!(sum > 0.0)) return 0;
+  int n = 0;
+  for (int t = 0; t < nt; t++) {
+    if (!keep[t]) continue;
+    tc[n] = ID(o, ti[t], tj[t]);
+    beta[n] = wt[t] / sum;
+    n++;
+  }
+  return n;
+}
+
 static void mix(orc_ctx *o, int k, double *const q[4]) {
   int nx = o->c.nx, ny = o->c.ny;
   for (int m = 0; m < 4; m++) memcpy(o->old[m], q[m], sizeof(double) * o->NP);
@@ -256,35 +304,12 @@ static void mix(orc_ctx *o, int k, double *const q[4]) {
       if (as == 0.0 && o->old[0][c] == 0.0 && o->old[1][c] == 0.0 &&
           o->old[2][c] == 0.0 && o->old[3][c] == 0.0)
         continue;
-      double nxv, nyv;
-      normal(o, o->phi, i, j, &nxv, &nyv);
-      if (k == 0) {
-        nxv = -nxv;
-        nyv = -nyv;
-      }
-      int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
-      int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
-      double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
-      int nt = o->c.dim == 2 ? 3 : 1;
-      /* targets: normal-direction neighbours of larger volume fraction;
-       * neighbours that are not small cells themselves are preferred, and
-       * only when there is none do smaller (but still larger than the
-       * source) neighbours take part */
-      int keep[3] = {0, 0, 0};
-      double sum = 0.0;
-      for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
-        for (int t = 0; t < nt; t++) {
-          if (!inside(o, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
-          double at = vol(o, k, ID(o, ti[t], tj[t]));
-          if (pass == 0 ? !(at >= o->c.mix_alpha) : !(at > as)) continue;
-          keep[t] = 1;
-          sum += wt[t];
-        }
-      if (!(sum > 0.0)) continue;
+      int tcs[3];
+      double betas[3];
+      int nt = mix_targets(o, k, i, j, tcs, betas);
       for (int t = 0; t < nt; t++) {
-        if (!keep[t]) continue;
-        int tc = ID(o, ti[t], tj[t]);
-        double beta = wt[t] / sum;
+        int tc = tcs[t];
+        double beta = betas[t];
         double at = vol(o, k, tc);
         double den = as * beta + at;
         for (int m = 0; m < 4; m++) {
@@ -797,21 +822,34 @@ static void copy_planes(orc_ctx *o, double *const dst[4], double *const src[4], 
   for (int m = 0; m < n; m++) memcpy(dst[m], src[m], sizeof(double) * o->NP);
 }
 
+static void copy_out(const orc_ctx *o, const double *src, double *dst);
+
+/* what a recorded step keeps of its schedule: the Lax-Friedrichs speeds of
+ * each stage (stage, fluid, direction) and the level set after stage 1 */
+typedef struct {
+  double *lf;   /* 8 */
+  double *phi1; /* nx*ny */
+} step_record;
+
 /* one RK step of both fluids and the level set with a common dt, the
  * first interaction step having been evaluated already */
-static void single_step_after_eval(orc_ctx *o, double dt) {
+static void single_step_after_eval(orc_ctx *o, double dt, step_record *rec) {
   int S = o->c.rk_order;
   for (int k = 0; k < 2; k++) copy_planes(o, o->q0[k], o->q[k], 4);
   memcpy(o->phi0, o->phi, sizeof(double) * o->NP);
   make_band(o, o->phi0);
   for (int s = 1; s <= S; s++) {
     if (s > 1) eval(o, o->q, o->phi);
+    if (rec && s <= 2)
+      for (int k = 0; k < 2; k++)
+        for (int d = 0; d < 2; d++) rec->lf[(s - 1) * 4 + k * 2 + d] = o->lf[k][d];
     for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
     ls_rhs(o, o->phi, o->lphi);
     for (int k = 0; k < 2; k++)
       for (int m = 0; m < 4; m++)
         rk_plane(o, s, o->q[k][m], o->q0[k][m], o->q[k][m], o->L[k][m], dt, NULL);
     rk_plane(o, s, o->phi, o->phi0, o->phi, o->lphi, dt, o->band);
+    if (rec && s == 1) copy_out(o, o->phi, rec->phi1);
     if (s == S) reinit(o, o->phi);
     geometry(o, o->phi);
     mix(o, 0, o->q[0]);
@@ -826,7 +864,7 @@ int orc_step_single_dt(orc_ctx *o, int nsteps, double t_end, orc_info *info) {
     eval(o, o->q, o->phi);
     double dt = dmin(dt_of(o, 0), dt_of(o, 1));
     if (t_end > 0.0 && o->t + dt > t_end) dt = t_end - o->t;
-    single_step_after_eval(o, dt);
+    single_step_after_eval(o, dt, NULL);
     if (info) {
       info->t = o->t;
       info->dt1 = dt;
@@ -888,7 +926,7 @@ static void cycle(orc_ctx *o, double t_end, orc_info *info) {
       if (nraw - fl < o->c.ratio_threshold) dt1 = fl * dt2;
     }
     if (!isfinite(dt1) || dt1 <= dt2) {
-      single_step_after_eval(o, dt2);
+      single_step_after_eval(o, dt2, NULL);
       if (info) {
         info->dt1 = dt2;
         info->n_used = 1.0;
@@ -1203,5 +1241,626 @@ int orc_reinit_only(orc_ctx *o) {
 int orc_mix_only(orc_ctx *o, int k) {
   geometry(o, o->phi);
   mix(o, k, o->q[k]);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* discrete adjoint of the single-time-step RK2 step with its schedule  */
+/* frozen                                                               */
+/*                                                                      */
+/* The frozen step takes the step size, the Lax-Friedrichs speeds of    */
+/* both stages and the level sets after stage 1 and after the step as   */
+/* given, so every geometric decision (volume fractions, apertures,     */
+/* interface vectors, extension and mixing targets and weights, which   */
+/* cells are real) is fixed; what remains is a differentiable map of    */
+/* the conserved states (alpha U)_k: primitive recovery, extension      */
+/* (linear), the interface Riemann problem (implicit function of its    */
+/* two side states), WENO5 with its nonlinear weights, the LF split     */
+/* fluxes, the aperture-weighted divergence of Eq. 2, the RK2           */
+/* combination and the mixing (linear).  The adjoint below is the       */
+/* transpose of that map's Jacobian, written operation by operation in  */
+/* reverse order.  Pins: central finite differences of the replayed     */
+/* step (orc_replay_step), exact conservation identities of the         */
+/* transposed step, and finite differences of the pointwise pieces.     */
+
+int orc_step_taped(orc_ctx *o, double *dt_out, double *lf, double *phi1, double *phi2) {
+  if (o->c.rk_order != 2) {
+    o->err |= ORC_ERR_INVAL;
+    return o->err;
+  }
+  eval(o, o->q, o->phi);
+  double dt = dmin(dt_of(o, 0), dt_of(o, 1));
+  step_record rec = {lf, phi1};
+  single_step_after_eval(o, dt, &rec);
+  *dt_out = dt;
+  copy_out(o, o->phi, phi2);
+  return o->err;
+}
+
+/* interaction step with the stage's Lax-Friedrichs speeds given */
+static void eval_frozen(orc_ctx *o, double *const qs[2][4], const double *lf) {
+  eval(o, qs, o->phi);
+  for (int k = 0; k < 2; k++)
+    for (int d = 0; d < 2; d++) o->lf[k][d] = lf[k * 2 + d];
+}
+
+/* stage s of the frozen step, ending with the level set phi_after in
+ * place (geometry refreshed) and the mixing done */
+static void frozen_stage(orc_ctx *o, int s, double dt, const double *lf, const double *phi_after) {
+  eval_frozen(o, o->q, lf);
+  for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, s, o->q[k][m], o->q0[k][m], o->q[k][m], o->L[k][m], dt, NULL);
+  copy_in(o, phi_after, o->phi);
+  geometry(o, o->phi);
+  mix(o, 0, o->q[0]);
+  mix(o, 1, o->q[1]);
+}
+
+int orc_replay_step(orc_ctx *o, double dt, const double *lf, const double *phi1,
+                    const double *phi2) {
+  if (o->c.rk_order != 2) {
+    o->err |= ORC_ERR_INVAL;
+    return o->err;
+  }
+  for (int k = 0; k < 2; k++) copy_planes(o, o->q0[k], o->q[k], 4);
+  frozen_stage(o, 1, dt, lf, phi1);
+  frozen_stage(o, 2, dt, lf + 4, phi2);
+  o->t += dt;
+  return o->err;
+}
+
+/* d weno5 / d v, the nonlinear weights included */
+void orc_weno5_grad(const double *v, double eps, double *g) {
+  double v1 = v[0], v2 = v[1], v3 = v[2], v4 = v[3], v5 = v[4];
+  double q[3] = {(2.0 * v1 - 7.0 * v2 + 11.0 * v3) / 6.0, (-v2 + 5.0 * v3 + 2.0 * v4) / 6.0,
+                 (2.0 * v3 + 5.0 * v4 - v5) / 6.0};
+  static const double dq[3][5] = {{2.0 / 6.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0},
+                                  {0.0, -1.0 / 6.0, 5.0 / 6.0, 2.0 / 6.0, 0.0},
+                                  {0.0, 0.0, 2.0 / 6.0, 5.0 / 6.0, -1.0 / 6.0}};
+  /* beta_i = 13/12 s_i^2 + 1/4 t_i^2 with s_i, t_i linear in v */
+  static const double ds[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
+  static const double dt_[3][5] = {{1, -4, 3, 0, 0}, {0, 1, 0, -1, 0}, {0, 0, 3, -4, 1}};
+  static const double d[3] = {0.1, 0.6, 0.3};
+  double b[3], db[3][5], a[3], S = 0.0;
+  for (int i = 0; i < 3; i++) {
+    double si = 0.0, ti = 0.0;
+    for (int r = 0; r < 5; r++) {
+      si += ds[i][r] * v[r];
+      ti += dt_[i][r] * v[r];
+    }
+    b[i] = 13.0 / 12.0 * si * si + 0.25 * ti * ti;
+    for (int r = 0; r < 5; r++) db[i][r] = 13.0 / 6.0 * si * ds[i][r] + 0.5 * ti * dt_[i][r];
+    a[i] = d[i] / sq(eps + b[i]);
+    S += a[i];
+  }
+  double res = (a[0] * q[0] + a[1] * q[1] + a[2] * q[2]) / S;
+  for (int r = 0; r < 5; r++) {
+    double acc = 0.0;
+    for (int i = 0; i < 3; i++) {
+      double dai = -2.0 * a[i] / (eps + b[i]) * db[i][r];
+      acc += a[i] * dq[i][r] + (q[i] - res) * dai;
+    }
+    g[r] = acc / S;
+  }
+}
+
+/* side function of the Riemann problem and its partial derivatives with
+ * respect to p, the side density and the side pressure */
+static void side_grad(double p, double rho, double pk, double g, double pi, double *f,
+                      double *fp, double *fr, double *fk) {
+  double P = pk + pi, Pp = p + pi;
+  double ck = sqrt(g * P / rho);
+  if (p > pk) {
+    double A = 2.0 / ((g + 1.0) * rho);
+    double B = (g - 1.0) / (g + 1.0) * P;
+    double qr = sqrt(A / (Pp + B));
+    *f = (p - pk) * qr;
+    *fp = qr * (1.0 - 0.5 * (p - pk) / (Pp + B));
+    *fk = -qr - 0.5 * (p - pk) * qr / (Pp + B) * (g - 1.0) / (g + 1.0);
+  } else {
+    double r = Pp / P, e = (g - 1.0) / (2.0 * g);
+    double re = pow(r, e);
+    *f = 2.0 * ck / (g - 1.0) * (re - 1.0);
+    *fp = 1.0 / (rho * ck) * pow(r, -(g + 1.0) / (2.0 * g));
+    *fk = *f / (2.0 * P) - ck * re / (g * P);
+  }
+  *fr = -*f / (2.0 * rho);
+}
+
+/* vector-Jacobian product of (p*, u*) of the exact Riemann problem with
+ * respect to (rho, u, p) of each side, by the implicit-function theorem
+ * on f_L(p) + f_R(p) + u_R - u_L = 0 at the converged p*. */
+int orc_riemann_grad(const double *L, const double *R, double lam_p, double lam_u, double *gL,
+                     double *gR) {
+  double out[7];
+  int rc = orc_riemann(L, R, out);
+  double p = out[0];
+  double fL, fpL, frL, fkL, fR, fpR, frR, fkR;
+  side_grad(p, L[0], L[2], L[3], L[4], &fL, &fpL, &frL, &fkL);
+  side_grad(p, R[0], R[2], R[3], R[4], &fR, &fpR, &frR, &fkR);
+  /* u* = (uL + uR)/2 + (fR - fL)/2 depends on p* as well */
+  double lp = lam_p + lam_u * 0.5 * (fpR - fpL);
+  double kappa = lp / (fpL + fpR);
+  gL[0] = -0.5 * lam_u * frL - kappa * frL;
+  gL[1] = 0.5 * lam_u + kappa;
+  gL[2] = -0.5 * lam_u * fkL - kappa * fkL;
+  gR[0] = 0.5 * lam_u * frR - kappa * frR;
+  gR[1] = 0.5 * lam_u - kappa;
+  gR[2] = 0.5 * lam_u * fkR - kappa * fkR;
+  return rc;
+}
+
+/* transpose of the split flux: lam_fp, lam_fm at one cell into the
+ * primitive adjoint lw of that cell (direction d, LF speed a) */
+static void split_T(const orc_ctx *o, int k, const double *const W[4], int c, int d, double a,
+                    const double *lfp, const double *lfm, double *const lw[4]) {
+  double g = o->c.gamma[k], pi = o->c.pinf[k];
+  double rho = W[0][c], u = W[1][c], v = W[2][c], p = W[3][c];
+  double E = (p + g * pi) / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+  double lF[4], lU[4];
+  for (int m = 0; m < 4; m++) {
+    lF[m] = 0.5 * (lfp[m] + lfm[m]);
+    lU[m] = 0.5 * a * (lfp[m] - lfm[m]);
+  }
+  double ke = 0.5 * (u * u + v * v);
+  /* U = (rho, rho u, rho v, E) */
+  double gr = lU[0] + lU[1] * u + lU[2] * v + lU[3] * ke;
+  double gu = lU[1] * rho + lU[3] * rho * u;
+  double gv = lU[2] * rho + lU[3] * rho * v;
+  double gp = lU[3] / (g - 1.0);
+  if (d == 0) {
+    /* F = (rho u, rho u^2 + p, rho u v, u (E + p)) */
+    gr += lF[0] * u + lF[1] * u * u + lF[2] * u * v + lF[3] * u * ke;
+    gu += lF[0] * rho + lF[1] * 2.0 * rho * u + lF[2] * rho * v + lF[3] * (E + p + rho * u * u);
+    gv += lF[2] * rho * u + lF[3] * rho * u * v;
+    gp += lF[1] + lF[3] * u * (1.0 / (g - 1.0) + 1.0);
+  } else {
+    /* F = (rho v, rho u v, rho v^2 + p, v (E + p)) */
+    gr += lF[0] * v + lF[1] * u * v + lF[2] * v * v + lF[3] * v * ke;
+    gu += lF[1] * rho * v + lF[3] * rho * u * v;
+    gv += lF[0] * rho + lF[1] * rho * u + lF[2] * 2.0 * rho * v + lF[3] * (E + p + rho * v * v);
+    gp += lF[2] + lF[3] * v * (1.0 / (g - 1.0) + 1.0);
+  }
+  lw[0][c] += gr;
+  lw[1][c] += gu;
+  lw[2][c] += gv;
+  lw[3][c] += gp;
+}
+
+/* transpose of the face flux of direction d (stride s, spacing hd) at the
+ * face between cells c - s and c, weighted by lam_F (4 components) */
+static void face_flux_T(const orc_ctx *o, int k, const double *const W[4], int c, int s, int d,
+                        double a, const double *lamF, double *const lw[4]) {
+  double g = o->c.gamma[k], pi = o->c.pinf[k];
+  double fp[6][4], fm[6][4];
+  for (int r = 0; r < 6; r++) {
+    int cc = c + (r - 3) * s;
+    double rho = W[0][cc], u = W[1][cc], v = W[2][cc], p = W[3][cc];
+    double E = (p + g * pi) / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+    double U[4] = {rho, rho * u, rho * v, E}, F[4];
+    if (d == 0) {
+      F[0] = rho * u;
+      F[1] = rho * u * u + p;
+      F[2] = rho * u * v;
+      F[3] = u * (E + p);
+    } else {
+      F[0] = rho * v;
+      F[1] = rho * u * v;
+      F[2] = rho * v * v + p;
+      F[3] = v * (E + p);
+    }
+    for (int m = 0; m < 4; m++) {
+      fp[r][m] = 0.5 * (F[m] + a * U[m]);
+      fm[r][m] = 0.5 * (F[m] - a * U[m]);
+    }
+  }
+  double lfp[6][4] = {{0}}, lfm[6][4] = {{0}};
+  for (int m = 0; m < 4; m++) {
+    double vp[5] = {fp[0][m], fp[1][m], fp[2][m], fp[3][m], fp[4][m]};
+    double vm[5] = {fm[5][m], fm[4][m], fm[3][m], fm[2][m], fm[1][m]};
+    double gp[5], gm[5];
+    orc_weno5_grad(vp, o->c.weno_eps, gp);
+    orc_weno5_grad(vm, o->c.weno_eps, gm);
+    for (int r = 0; r < 5; r++) {
+      lfp[r][m] += lamF[m] * gp[r];
+      lfm[5 - r][m] += lamF[m] * gm[r];
+    }
+  }
+  for (int r = 0; r < 6; r++) split_T(o, k, W, c + (r - 3) * s, d, a, lfp[r], lfm[r], lw);
+}
+
+/* transpose of the aperture-weighted flux divergence of Eq. 2 for fluid k:
+ * mu (4 planes) is the adjoint of L_k; accumulates into lw (4 padded
+ * planes, ghost cells included) */
+static void fluxdiv_T(orc_ctx *o, int k, const double *const W[4], const double *lf,
+                      double *const mu[4], double *const lw[4]) {
+  int nx = o->c.nx, ny = o->c.ny;
+  double lamF[4];
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i <= nx; i++) {
+      int c = ID(o, i, j);
+      double A = k == 1 ? o->ax[c] : 1.0 - o->ax[c];
+      if (A == 0.0) continue;
+      for (int m = 0; m < 4; m++) {
+        double r = i < nx ? mu[m][c] : 0.0, l = i > 0 ? mu[m][c - 1] : 0.0;
+        lamF[m] = A * (r - l) / o->c.dx;
+      }
+      face_flux_T(o, k, W, c, 1, 0, lf[0], lamF, lw);
+    }
+  if (o->c.dim == 2)
+    for (int j = 0; j <= ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int c = ID(o, i, j);
+        double A = k == 1 ? o->ay[c] : 1.0 - o->ay[c];
+        if (A == 0.0) continue;
+        for (int m = 0; m < 4; m++) {
+          double r = j < ny ? mu[m][c] : 0.0, l = j > 0 ? mu[m][c - o->PX] : 0.0;
+          lamF[m] = A * (r - l) / o->c.dy;
+        }
+        face_flux_T(o, k, W, c, o->PX, 1, lf[1], lamF, lw);
+      }
+}
+
+/* transpose of fill_ghost: ghost adjoints move back to the interior cells
+ * they were copied from (the y pass first, as it ran last) */
+static void ghost_T(orc_ctx *o, double *a, int vel) {
+  int nx = o->c.nx, ny = o->c.ny;
+  for (int i = -GH; i < nx + GH; i++)
+    for (int m = 0; m < GH; m++) {
+      double sb = (vel == 2 && o->c.bc[2] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      double st = (vel == 2 && o->c.bc[3] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      int jb, jt;
+      switch (o->c.bc[2]) {
+        case ORC_BC_REFLECT: jb = m; break;
+        case ORC_BC_PERIODIC: jb = ny - 1 - m; break;
+        default: jb = 0;
+      }
+      switch (o->c.bc[3]) {
+        case ORC_BC_REFLECT: jt = ny - 1 - m; break;
+        case ORC_BC_PERIODIC: jt = m; break;
+        default: jt = ny - 1;
+      }
+      double gb = a[ID(o, i, -1 - m)], gt = a[ID(o, i, ny + m)];
+      a[ID(o, i, -1 - m)] = 0.0;
+      a[ID(o, i, ny + m)] = 0.0;
+      a[ID(o, i, jb)] += sb * gb;
+      a[ID(o, i, jt)] += st * gt;
+    }
+  for (int j = 0; j < ny; j++)
+    for (int m = 0; m < GH; m++) {
+      double sl = (vel == 1 && o->c.bc[0] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      double sr = (vel == 1 && o->c.bc[1] == ORC_BC_REFLECT) ? -1.0 : 1.0;
+      int il, ir;
+      switch (o->c.bc[0]) {
+        case ORC_BC_REFLECT: il = m; break;
+        case ORC_BC_PERIODIC: il = nx - 1 - m; break;
+        default: il = 0;
+      }
+      switch (o->c.bc[1]) {
+        case ORC_BC_REFLECT: ir = nx - 1 - m; break;
+        case ORC_BC_PERIODIC: ir = m; break;
+        default: ir = nx - 1;
+      }
+      double gl = a[ID(o, -1 - m, j)], gr = a[ID(o, nx + m, j)];
+      a[ID(o, -1 - m, j)] = 0.0;
+      a[ID(o, nx + m, j)] = 0.0;
+      a[ID(o, il, j)] += sl * gl;
+      a[ID(o, ir, j)] += sr * gr;
+    }
+}
+
+/* transpose of the interface exchange: mu_N, mu_P are the adjoints of the
+ * right-hand sides; the Riemann problem's side states are the stencil
+ * states of both fluids at each cut cell */
+static void interface_T(orc_ctx *o, double *const W[2][4], double *const mu[2][4],
+                        double *const lw[2][4]) {
+  double dxdy = o->c.dx * o->c.dy;
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      double Sx = o->sx[c], Sy = o->sy[c];
+      if (Sx == 0.0 && Sy == 0.0) continue;
+      double Sm = sqrt(Sx * Sx + Sy * Sy);
+      double nxv, nyv;
+      normal(o, o->phi, i, j, &nxv, &nyv);
+      if (nxv == 0.0 && nyv == 0.0) {
+        nxv = Sx / Sm;
+        nyv = Sy / Sm;
+      }
+      double L[5] = {W[0][0][c], W[0][1][c] * nxv + W[0][2][c] * nyv, W[0][3][c],
+                     o->c.gamma[0], o->c.pinf[0]};
+      double R[5] = {W[1][0][c], W[1][1][c] * nxv + W[1][2][c] * nyv, W[1][3][c],
+                     o->c.gamma[1], o->c.pinf[1]};
+      double out[7];
+      orc_riemann(L, R, out);
+      double ps = out[0], us = out[1];
+      /* X as applied to fluid N enters L_N with +1/dxdy and L_P with -1/dxdy */
+      double lx0 = (mu[0][1][c] - mu[1][1][c]) / dxdy;
+      double lx1 = (mu[0][2][c] - mu[1][2][c]) / dxdy;
+      double lx2 = (mu[0][3][c] - mu[1][3][c]) / dxdy;
+      double lam_p = -Sx * lx0 - Sy * lx1 - us * Sm * lx2;
+      double lam_u = -ps * Sm * lx2;
+      double gL[3], gR[3];
+      orc_riemann_grad(L, R, lam_p, lam_u, gL, gR);
+      lw[0][0][c] += gL[0];
+      lw[0][1][c] += gL[1] * nxv;
+      lw[0][2][c] += gL[1] * nyv;
+      lw[0][3][c] += gL[2];
+      lw[1][0][c] += gR[0];
+      lw[1][1][c] += gR[1] * nxv;
+      lw[1][2][c] += gR[1] * nyv;
+      lw[1][3][c] += gR[2];
+    }
+}
+
+/* transpose of the extension sweeps of fluid k (each sweep is the same
+ * linear map: targets take the upwind-weighted mean of their upwind
+ * neighbours, every other cell keeps its value) */
+static void extend_T(orc_ctx *o, int k, double *const lw[4]) {
+  double bw = o->c.band * o->h;
+  const double *p = o->phi;
+  for (int it = 0; it < o->c.ext_iters; it++) {
+    for (int m = 0; m < 4; m++) memcpy(o->old[m], lw[m], sizeof(double) * o->NP);
+    for (int j = 0; j < o->c.ny; j++)
+      for (int i = 0; i < o->c.nx; i++) {
+        int c = ID(o, i, j);
+        if (!(fabs(p[c]) < bw) || vol(o, k, c) > ALPHA_REAL) continue;
+        double nxv, nyv;
+        normal(o, p, i, j, &nxv, &nyv);
+        if (k == 0) {
+          nxv = -nxv;
+          nyv = -nyv;
+        }
+        int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+        double wx = fabs(nxv) / o->c.dx;
+        double wy = o->c.dim == 2 ? fabs(nyv) / o->c.dy : 0.0;
+        if (!inside(o, i + sx, j)) wx = 0.0;
+        if (!inside(o, i, j + sy)) wy = 0.0;
+        double den = wx + wy;
+        if (!(den > 0.0)) continue;
+        /* the target's own value is overwritten: its adjoint moves to the
+         * neighbours it was computed from */
+        for (int m = 0; m < 4; m++) lw[m][c] -= o->old[m][c];
+        for (int m = 0; m < 4; m++) {
+          if (wx > 0.0) lw[m][ID(o, i + sx, j)] += wx / den * o->old[m][c];
+          if (wy > 0.0) lw[m][ID(o, i, j + sy)] += wy / den * o->old[m][c];
+        }
+      }
+  }
+}
+
+/* transpose of the primitive recovery of fluid k at its real cells; the
+ * stencil states of other cells are extension or carried values, whose
+ * adjoint ends here */
+static void prim_T(orc_ctx *o, int k, const double *const W[4], double *const lw[4],
+                   double *const lq[4]) {
+  double g = o->c.gamma[k];
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      double a = vol(o, k, c);
+      for (int m = 0; m < 4; m++) lq[m][c] = 0.0;
+      if (!(a > ALPHA_REAL)) continue;
+      double rho = W[0][c], u = W[1][c], v = W[2][c];
+      double lr = lw[0][c], lu = lw[1][c], lv = lw[2][c], lp = lw[3][c];
+      double m0 = a * rho;
+      lq[0][c] = lr / a - (lu * u + lv * v) / m0 + lp * (g - 1.0) * 0.5 * (u * u + v * v) / a;
+      lq[1][c] = lu / m0 - lp * (g - 1.0) * u / a;
+      lq[2][c] = lv / m0 - lp * (g - 1.0) * v / a;
+      lq[3][c] = lp * (g - 1.0) / a;
+    }
+}
+
+/* transpose of mixing fluid k (its incoming adjoint lam, in place); the
+ * mixing is linear in the state, and a small cell with no fluid and no
+ * content would mix as any other once it had content, so it is included */
+static void mix_T(orc_ctx *o, int k, double *const lam[4]) {
+  for (int m = 0; m < 4; m++) memcpy(o->old[m], lam[m], sizeof(double) * o->NP);
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      double as = vol(o, k, c);
+      if (as >= o->c.mix_alpha) continue;
+      int tcs[3];
+      double betas[3];
+      int nt = mix_targets(o, k, i, j, tcs, betas);
+      for (int t = 0; t < nt; t++) {
+        int tc = tcs[t];
+        double beta = betas[t];
+        double at = vol(o, k, tc);
+        double den = as * beta + at;
+        for (int m = 0; m < 4; m++) {
+          /* M = beta (q_t as - q_s at) / den adds to the source and
+           * subtracts at the target */
+          double dM = o->old[m][c] - o->old[m][tc];
+          lam[m][tc] += dM * beta * as / den;
+          lam[m][c] -= dM * beta * at / den;
+        }
+      }
+    }
+}
+
+/* adjoint of the right-hand sides of both fluids at the stage whose
+ * stencil states are W (ghosts filled) and whose geometry is in place:
+ * mu (adjoint of L, both fluids) -> lq (adjoint of the stage state) */
+static void rhs_T(orc_ctx *o, double *const W[2][4], const double *lf, double *const mu[2][4],
+                  double *const lw[2][4], double *const lq[2][4]) {
+  static const int vel[4] = {0, 1, 2, 0};
+  for (int k = 0; k < 2; k++) {
+    for (int m = 0; m < 4; m++) memset(lw[k][m], 0, sizeof(double) * o->NP);
+    fluxdiv_T(o, k, (const double *const *)W[k], lf + 2 * k, mu[k], lw[k]);
+    for (int m = 0; m < 4; m++) ghost_T(o, lw[k][m], vel[m]);
+  }
+  interface_T(o, W, mu, lw);
+  for (int k = 0; k < 2; k++) {
+    extend_T(o, k, lw[k]);
+    prim_T(o, k, (const double *const *)W[k], lw[k], lq[k]);
+  }
+}
+
+int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1,
+                     const double *phi2, const double *lam_in, double *lam_out) {
+  if (o->c.rk_order != 2) {
+    o->err |= ORC_ERR_INVAL;
+    return o->err;
+  }
+  int n = o->c.nx * o->c.ny;
+  double *Qn[2][4], *W1[2][4], *W2[2][4], *lam[2][4], *ls[2][4], *mu[2][4], *lw[2][4],
+      *lq[2][4], *lnew[2][4];
+  double **all[9] = {&Qn[0][0], &W1[0][0], &W2[0][0], &lam[0][0], &ls[0][0],
+                     &mu[0][0], &lw[0][0], &lq[0][0], &lnew[0][0]};
+  for (int a = 0; a < 9; a++)
+    for (int x = 0; x < 8; x++) all[a][x] = plane(o);
+  double *phin = plane(o);
+  double t0 = o->t;
+  for (int k = 0; k < 2; k++) copy_planes(o, Qn[k], o->q[k], 4);
+  memcpy(phin, o->phi, sizeof(double) * o->NP);
+
+  /* forward, keeping the stencil states of both stages */
+  for (int k = 0; k < 2; k++) copy_planes(o, o->q0[k], o->q[k], 4);
+  eval_frozen(o, o->q, lf);
+  for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
+  for (int k = 0; k < 2; k++) copy_planes(o, W1[k], o->w[k], 4);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 1, o->q[k][m], o->q0[k][m], o->q[k][m], o->L[k][m], dt, NULL);
+  copy_in(o, phi1, o->phi);
+  geometry(o, o->phi);
+  mix(o, 0, o->q[0]);
+  mix(o, 1, o->q[1]);
+  eval_frozen(o, o->q, lf + 4);
+  for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
+  for (int k = 0; k < 2; k++) copy_planes(o, W2[k], o->w[k], 4);
+
+  /* reverse */
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) copy_in(o, lam_in + (k * 4 + m) * n, lam[k][m]);
+  /* Q^{n+1} = mix_2(Q**) */
+  copy_in(o, phi2, o->phi);
+  geometry(o, o->phi);
+  mix_T(o, 0, lam[0]);
+  mix_T(o, 1, lam[1]);
+  /* Q** = Q^n / 2 + (Q1 + dt L(Q1)) / 2 */
+  copy_in(o, phi1, o->phi);
+  geometry(o, o->phi);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++)
+      for (int c = 0; c < o->NP; c++) mu[k][m][c] = 0.5 * dt * lam[k][m][c];
+  rhs_T(o, W2, lf + 4, mu, lw, lq);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++)
+      for (int c = 0; c < o->NP; c++) ls[k][m][c] = 0.5 * lam[k][m][c] + lq[k][m][c];
+  /* Q1 = mix_1(Q*) */
+  mix_T(o, 0, ls[0]);
+  mix_T(o, 1, ls[1]);
+  /* Q* = Q^n + dt L(Q^n) */
+  memcpy(o->phi, phin, sizeof(double) * o->NP);
+  geometry(o, o->phi);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++)
+      for (int c = 0; c < o->NP; c++) mu[k][m][c] = dt * ls[k][m][c];
+  rhs_T(o, W1, lf, mu, lw, lq);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++)
+      for (int c = 0; c < o->NP; c++)
+        lnew[k][m][c] = 0.5 * lam[k][m][c] + ls[k][m][c] + lq[k][m][c];
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) copy_out(o, lnew[k][m], lam_out + (k * 4 + m) * n);
+
+  /* the context's state is left as it was */
+  for (int k = 0; k < 2; k++) copy_planes(o, o->q[k], Qn[k], 4);
+  memcpy(o->phi, phin, sizeof(double) * o->NP);
+  geometry(o, o->phi);
+  o->t = t0;
+  for (int a = 0; a < 9; a++)
+    for (int x = 0; x < 8; x++) free(all[a][x]);
+  free(phin);
+  return o->err;
+}
+
+/* right-hand sides of both fluids at the current state with the
+ * Lax-Friedrichs speeds lf[4] (fluid*2 + direction) given, and the
+ * transpose of their Jacobian: the stage-level pieces of the adjoint */
+int orc_rhs_frozen(orc_ctx *o, const double *lf, double *out) {
+  int n = o->c.nx * o->c.ny;
+  eval_frozen(o, o->q, lf);
+  for (int k = 0; k < 2; k++) {
+    fv_rhs(o, k, o->L[k]);
+    for (int m = 0; m < 4; m++) copy_out(o, o->L[k][m], out + (k * 4 + m) * n);
+  }
+  return o->err;
+}
+
+int orc_rhs_adjoint(orc_ctx *o, const double *lf, const double *mu_in, double *lq_out) {
+  int n = o->c.nx * o->c.ny;
+  double *W[2][4], *mu[2][4], *lw[2][4], *lq[2][4];
+  double **all[4] = {&W[0][0], &mu[0][0], &lw[0][0], &lq[0][0]};
+  for (int a = 0; a < 4; a++)
+    for (int x = 0; x < 8; x++) all[a][x] = plane(o);
+  eval_frozen(o, o->q, lf);
+  for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
+  for (int k = 0; k < 2; k++) copy_planes(o, W[k], o->w[k], 4);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) copy_in(o, mu_in + (k * 4 + m) * n, mu[k][m]);
+  rhs_T(o, W, lf, mu, lw, lq);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) copy_out(o, lq[k][m], lq_out + (k * 4 + m) * n);
+  for (int a = 0; a < 4; a++)
+    for (int x = 0; x < 8; x++) free(all[a][x]);
+  return o->err;
+}
+
+/* transpose of mixing fluid k with the current geometry: lam (4 planes of
+ * nx*ny) in place */
+int orc_mix_adjoint(orc_ctx *o, int k, double *lam) {
+  int n = o->c.nx * o->c.ny;
+  double *l[4];
+  for (int m = 0; m < 4; m++) {
+    l[m] = plane(o);
+    copy_in(o, lam + m * n, l[m]);
+  }
+  geometry(o, o->phi);
+  mix_T(o, k, l);
+  for (int m = 0; m < 4; m++) {
+    copy_out(o, l[m], lam + m * n);
+    free(l[m]);
+  }
+  return 0;
+}
+
+/* transpose of the initialisation (alpha U from primitive fields, then
+ * mixing) with the current level set: lam_q (8 planes) -> lam_prim (8
+ * planes: rho, u, v, p of fluid N, then of fluid P) */
+int orc_adjoint_init(orc_ctx *o, const double *pN, const double *pP, const double *lam_q,
+                     double *lam_prim) {
+  int nx = o->c.nx, ny = o->c.ny, n = nx * ny;
+  double *l[2][4];
+  geometry(o, o->phi);
+  for (int k = 0; k < 2; k++) {
+    for (int m = 0; m < 4; m++) {
+      l[k][m] = plane(o);
+      copy_in(o, lam_q + (k * 4 + m) * n, l[k][m]);
+    }
+    mix_T(o, k, l[k]);
+  }
+  for (int k = 0; k < 2; k++) {
+    const double *pr = k == 0 ? pN : pP;
+    double g = o->c.gamma[k];
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int c = ID(o, i, j), s = i + j * nx;
+        double rho = pr[s], u = pr[n + s], v = pr[2 * n + s];
+        double a = vol(o, k, c);
+        double l0 = l[k][0][c], l1 = l[k][1][c], l2 = l[k][2][c], l3 = l[k][3][c];
+        double *out = lam_prim + k * 4 * n;
+        out[s] = a * (l0 + l1 * u + l2 * v + l3 * 0.5 * (u * u + v * v));
+        out[n + s] = a * (l1 * rho + l3 * rho * u);
+        out[2 * n + s] = a * (l2 * rho + l3 * rho * v);
+        out[3 * n + s] = a * l3 / (g - 1.0);
+      }
+    for (int m = 0; m < 4; m++) free(l[k][m]);
+  }
   return 0;
 }

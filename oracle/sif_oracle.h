@@ -93,6 +93,42 @@ double orc_cell_alpha(double c00, double c10, double c11, double c01);
  * iterations. Returns 0, or ORC_ERR_NOCONV. */
 int orc_riemann(const double *L, const double *R, double *out);
 
+/* Discrete adjoint of the single-time-step RK2 step with its schedule
+ * frozen (rk_order 2 only; ORC_ERR_INVAL otherwise).
+ * orc_step_taped: one ordinary single-dt step that also returns its
+ *   schedule: dt, the Lax-Friedrichs speeds lf[8] (index stage*4 + fluid*2
+ *   + direction) and the level sets after stage 1 (phi1) and after the step
+ *   (phi2), nx*ny each.
+ * orc_replay_step: the same step from the current state with that schedule
+ *   taken as given (the frozen map; bitwise equal to the taped step when
+ *   started from the taped state).
+ * orc_adjoint_step: lam_out = J^T lam_in for the frozen map J at the
+ *   current state; lam_in / lam_out are 8 planes of nx*ny (fluid N
+ *   components 0-3, then fluid P).  The context's state is unchanged. */
+int orc_step_taped(orc_ctx *o, double *dt, double *lf, double *phi1, double *phi2);
+int orc_replay_step(orc_ctx *o, double dt, const double *lf, const double *phi1,
+                    const double *phi2);
+int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1,
+                     const double *phi2, const double *lam_in, double *lam_out);
+/* Stage-level pieces: both fluids' right-hand sides (8 planes) at the
+ * current state with Lax-Friedrichs speeds lf[4] (fluid*2 + direction)
+ * taken as given; the transpose of their Jacobian applied to mu (8
+ * planes); the transpose of mixing fluid k (4 planes, in place). */
+int orc_rhs_frozen(orc_ctx *o, const double *lf, double *out);
+int orc_rhs_adjoint(orc_ctx *o, const double *lf, const double *mu, double *lq);
+int orc_mix_adjoint(orc_ctx *o, int k, double *lam);
+/* Transpose of orc_init with respect to the primitive fields, at the
+ * current level set: lam_q (8 planes) -> lam_prim (8 planes, rho u v p of
+ * fluid N then fluid P); prim_N / prim_P as given to orc_init. */
+int orc_adjoint_init(orc_ctx *o, const double *prim_N, const double *prim_P,
+                     const double *lam_q, double *lam_prim);
+/* d weno5(v) / d v (5 values). */
+void orc_weno5_grad(const double *v, double eps, double *g);
+/* lam_p dp* + lam_u du* of the Riemann problem as a row vector over
+ * (rho, u, p) of each side: gL[3], gR[3]. */
+int orc_riemann_grad(const double *L, const double *R, double lam_p, double lam_u, double *gL,
+                     double *gR);
+
 #ifdef __cplusplus
 }
 #endif

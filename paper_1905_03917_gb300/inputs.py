@@ -131,6 +131,33 @@ def underwater_explosion(n=2048, seed=None, perturb=0.0, half=1.0, radius=0.12,
     return {"name": f"underwater_explosion_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
 
 
+# reference scales of the nondimensional gas-water units: rho_ref = 1000
+# kg/m^3, p_ref = 1e9 Pa, L_ref = 1 m (so u_ref = 1000 m/s, t_ref = 1 ms)
+RHO_REF, P_REF = 1000.0, 1.0e9
+WATER_ND = {"gamma": 4.4, "pinf": 6.0e8 / P_REF}
+
+
+def adjoint_bubble(n=512, centre=(0.0, 0.0), radius=0.12, p_gas=8.29e8, rho_gas=1270.0,
+                   seed=None):
+    """Gas bubble in water on [-1,1]^2 with reflective walls (the
+    underwater-explosion setup at reduced size) in nondimensional units
+    (rho / 1000 kg/m^3, p / 1e9 Pa, lengths in m), in which the states and
+    fluxes are of order one.  The gradient of the wall-pressure functional
+    is taken with respect to this case's initial gas pressure."""
+    d = 2.0 / n
+    cfg = config(n, n, d, d, AIR, WATER_ND, ["reflect"] * 4, x0=-1.0, y0=-1.0)
+    X, Y = _centres(cfg)
+    rng = np.random.default_rng(seed)
+    cx, cy, R = centre[0], centre[1], radius
+    if seed is not None:
+        cx += rng.uniform(-1, 1) * d
+        cy += rng.uniform(-1, 1) * d
+    phi = np.sqrt((X - cx) ** 2 + (Y - cy) ** 2) - R
+    pN = _uniform(X.shape, rho_gas / RHO_REF, 0.0, 0.0, p_gas / P_REF)
+    pP = _uniform(X.shape, 1.0, 0.0, 0.0, 1.0e5 / P_REF)
+    return {"name": f"adjoint_bubble_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
 def periodic_bubble(n=64, seed=0, ratio=100.0, perturb=1e-2, velocity=5.0):
     """All-periodic unit box, gas bubble in water with smooth random
     perturbations of density, pressure and velocity (conservation tests)."""
