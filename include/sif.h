@@ -179,6 +179,63 @@ const char *sif_batch_last_error(const sif_batch *b);
 int sif_batch_one_graph(const sif_batch *b);
 void sif_batch_destroy(sif_batch *b);
 
+/* ---------------------------------------------------------------------
+ * Discrete adjoint of the single-time-step method (rk_order 2) with each
+ * step's schedule frozen.  The paper defines the forward step only
+ * (Eq. 2 with the interface exchange of Sec. 2.1, mixing of Sec. 2.2,
+ * extension of Sec. 2.3, TVD-RK2 of Sec. 4); the frozen step takes that
+ * step's dt, its Lax-Friedrichs speeds of both stages and its level sets
+ * after stage 1 and after the step as given, so that the geometry
+ * (volume fractions, apertures, interface vectors, extension and mixing
+ * targets and weights) is fixed and the step is a differentiable map of
+ * the conserved states; the adjoint applies the transpose of its
+ * Jacobian (WENO5 weights, LF splitting, the interface Riemann problem by
+ * the implicit-function theorem, the aperture-weighted update, mixing,
+ * extension, primitive recovery).
+ *
+ * Adjoint and state arrays in these calls are 8 planes of nx*ny doubles,
+ * x fastest: the 4 components (mass, x-momentum, y-momentum, energy) of
+ * (alpha U)_N, then those of (alpha U)_P.  mem_kind says whether the
+ * caller's pointers are host or device memory; the context only reads
+ * and writes them during the call. */
+
+/* Start recording: every later sif_step_single_dt step (up to capacity in
+ * total) records what its frozen replay needs (state, stencil states, level
+ * sets, dt, LF speeds: 19 planes and 9 scalars per step, device memory
+ * owned by the context).  Resets the tape to length 0.  capacity 0 stops
+ * recording and frees the tape.  While recording, steps run without the
+ * captured graphs (same kernels, same results) and sif_step_multi_dt
+ * returns SIF_ESTATE.  SIF_EINVAL for rk_order != 2 or capacity < 0;
+ * SIF_ECUDA if the tape cannot be allocated.  A step beyond capacity fails
+ * with SIF_EINVAL before anything runs. */
+int sif_tape_reset(sif_ctx *ctx, int capacity);
+/* Number of steps recorded since the last sif_tape_reset. */
+int sif_tape_length(const sif_ctx *ctx, int *len);
+
+/* Frozen replay of recorded step `step` (0-based) from the state q_in,
+ * written to q_out (may alias q_in).  From the recorded state it
+ * reproduces the recorded step bitwise.  The context's own state is left
+ * unchanged.  SIF_EINVAL for a step not on the tape; SIF_ENONPHYS if the
+ * replayed state is non-physical in a real cell. */
+int sif_replay_step(sif_ctx *ctx, int step, const double *q_in, double *q_out, int mem_kind);
+
+/* lam_out = J^T lam_in with J the Jacobian of the frozen replay of
+ * recorded step `step` at its recorded state: lam_in is the adjoint of
+ * the state after the step, lam_out that of the state before it (may
+ * alias lam_in).  The context's own state is left unchanged.
+ * SIF_EINVAL for a step not on the tape or bad pointers. */
+int sif_adjoint_step(sif_ctx *ctx, int step, const double *lam_in, double *lam_out,
+                     int mem_kind);
+
+/* Transpose of sif_init_fluids (conversion to (alpha U) and mixing, with
+ * the geometry of phi) with respect to the primitive fields: lam_q (8
+ * planes, adjoint of the initial state) -> lam_prim (8 planes: rho, u, v,
+ * p of fluid N, then of fluid P).  phi, prim_N, prim_P as given to
+ * sif_init_fluids.  The context's own state is left unchanged. */
+int sif_adjoint_init(sif_ctx *ctx, const double *phi, const double *prim_N,
+                     const double *prim_P, const double *lam_q, double *lam_prim,
+                     int mem_kind);
+
 /* Measurement counters of one context (no counterpart in the paper). */
 typedef struct {
   long long kernel_launches;  /* libsif kernels launched on this context */

@@ -26,6 +26,7 @@ SOURCES = {
     "api.cu": [],
     "probe.cu": ["--fmad=true"],
     "noalloc.cu": ["--fmad=false"],
+    "adjoint.cu": ["--fmad=true"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -52,14 +52,28 @@ struct sif_ctx {
   int graph_gen;             // bumped whenever the graphs are rebuilt
   int inited;
   int last_status;
+  // adjoint: tape of recorded single-time-step steps (own allocation) and
+  // the adjoint's scratch planes (allocated on first use)
+  int tape_cap, tape_len, tape_alloc;
+  double *tape_planes;  // tape_alloc x kTapePlanes planes
+  double *tape_scal;    // tape_alloc x 16: dt, LF speeds of stage 1 and 2 (bit patterns)
+  void *adj_pool;
+  double *lamA[2][4], *lamB[2][4], *lamC[2][4], *lw[2][4], *W1[2][4], *W2[2][4], *G[40];
+  double *sv_q[2][4], *sv_w[2][4], *sv_phi;
+  Scalars *sv_sc;
   char err[256];
 };
+
+// per recorded step: q (8), the stencil states the step starts from (8),
+// phi^n, phi after stage 1, phi^{n+1}
+static const int kTapePlanes = 19;
 
 // launch counting happens on the device (SIF_TICK); the host-side notes
 // the wrappers make are not used for measurement
 void sif_note_launches(int) {}
 static unsigned long long device_launches() {
-  return sif_launches_geom() + sif_launches_band() + sif_launches_plan() + sif_launches_fv();
+  return sif_launches_geom() + sif_launches_band() + sif_launches_plan() + sif_launches_fv() +
+         sif_launches_adj();
 }
 
 static void set_err(sif_ctx *c, const char *fmt, ...) {
@@ -275,6 +289,8 @@ extern "C" void sif_destroy(sif_ctx *c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   free_graphs(c);
+  if (c->tape_planes) cudaFree(c->tape_planes);
+  if (c->adj_pool) cudaFree(c->adj_pool);
   for (int i = 0; i < 4; i++)
     if (c->cap[i]) cudaStreamDestroy(c->cap[i]);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -393,16 +409,27 @@ static void reinit(sif_ctx *c) {
   dbg(c, "reinit");
 }
 
+// where a recorded step keeps its level set after stage 1 and the
+// Lax-Friedrichs speeds of stage 2
+struct TapeHook {
+  double *phi1;
+  double *lf2;
+};
+
 // one RK step of both fluids and the level set, the first interaction
 // step having been evaluated; dtp points to the step size on the device
-static void single_step_after_eval(sif_ctx *c, const double *dtp) {
+static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook *rec = nullptr) {
   int S = c->cfg.rk_order;
   for (int k = 0; k < 2; k++) copy_planes(c, c->q0[k], c->q[k], 4);
   ls_begin(c);
   for (int s = 1; s <= S; s++) {
     if (s > 1) eval(c, c->q);
+    if (rec && s == 2)
+      cudaMemcpyAsync(rec->lf2, c->sc->lf, sizeof(c->sc->lf), cudaMemcpyDeviceToDevice, c->st);
     for (int k = 0; k < 2; k++) fv(c, k, s, c->q[k], c->q0[k], c->q[k], dtp);
     ls_stage(c, s, dtp);
+    if (rec && s == 1)
+      cudaMemcpyAsync(rec->phi1, c->phi, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
     if (s == S) reinit(c);
     geometry(c);
     mix_both(c);
@@ -446,8 +473,14 @@ static int begin_call(sif_ctx *c, double t_end, unsigned long long *upd0) {
   return SIF_OK;
 }
 
+static void taped_step(sif_ctx *c);
+
 extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycle_info *info) {
   if (!c || nsteps < 0) return SIF_EINVAL;
+  if (c->tape_cap > 0 && c->tape_len + nsteps > c->tape_cap) {
+    set_err(c, "adjoint tape full (%d of %d steps recorded)", c->tape_len, c->tape_cap);
+    return SIF_EINVAL;
+  }
   unsigned long long upd0;
   int rc = begin_call(c, t_end, &upd0);
   if (rc) return rc;
@@ -458,7 +491,9 @@ extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycl
       CK(cudaStreamSynchronize(c->st));
       if (c->hsc->t >= t_end) break;
     }
-    if (ensure_graphs(c) == SIF_OK) {
+    if (c->tape_cap > 0) {
+      taped_step(c);  // the same kernels in the same order, recording
+    } else if (ensure_graphs(c) == SIF_OK) {
       CK(cudaGraphLaunch(c->g_single, c->st));
     } else {
       eval(c, c->q);
@@ -817,6 +852,10 @@ extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycl
     set_err(c, "the multi-time-step cycle is defined for rk_order 2");
     return SIF_EINVAL;
   }
+  if (c->tape_cap > 0) {
+    set_err(c, "the adjoint tape records single-time-step steps only");
+    return SIF_ESTATE;
+  }
   unsigned long long upd0;
   int rc = begin_call(c, t_end, &upd0);
   if (rc) return rc;
@@ -1046,6 +1085,313 @@ extern "C" int sif_load(sif_ctx *c, const void *buf, size_t len) {
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->st));
   c->inited = 1;
+  return SIF_OK;
+}
+
+// ---------------------------------------------------------------------
+// adjoint of the single-time-step method with its schedule frozen
+//
+// While a tape is active every single-dt step records what its frozen
+// replay needs: the state, the stencil states it starts from (the
+// extension's starting values), phi at its start, after stage 1 and at its
+// end, dt and the Lax-Friedrichs speeds of both stages.  The replay runs
+// the same kernels with that schedule imposed; the adjoint replays one
+// step keeping both stages' stencil states, then applies the transposed
+// kernels in reverse order.
+
+static double *tape_plane(sif_ctx *c, int step, int i) {
+  return c->tape_planes + ((size_t)step * kTapePlanes + i) * c->NP;
+}
+static double *tape_scal(sif_ctx *c, int step) { return c->tape_scal + (size_t)step * 16; }
+
+static void d2d(sif_ctx *c, void *dst, const void *src, size_t bytes) {
+  cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->st);
+}
+
+static void taped_step(sif_ctx *c) {
+  const int s = c->tape_len;
+  const size_t pb = sizeof(double) * c->NP;
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      d2d(c, tape_plane(c, s, k * 4 + m), c->q[k][m], pb);
+      d2d(c, tape_plane(c, s, 8 + k * 4 + m), c->w[k][m], pb);
+    }
+  d2d(c, tape_plane(c, s, 16), c->phi, pb);
+  eval(c, c->q);
+  launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
+  d2d(c, tape_scal(c, s), &c->sc->dt, sizeof(double));
+  d2d(c, tape_scal(c, s) + 1, c->sc->lf, sizeof(c->sc->lf));
+  TapeHook hook = {tape_plane(c, s, 17), tape_scal(c, s) + 5};
+  single_step_after_eval(c, &c->sc->dt, &hook);
+  d2d(c, tape_plane(c, s, 18), c->phi, pb);
+  launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+  c->tape_len++;
+}
+
+static int ensure_adj_scratch(sif_ctx *c) {
+  if (c->adj_pool) return SIF_OK;
+  const int nplanes = 24 + 8 + 16 + 40 + 17;
+  size_t pb = sizeof(double) * c->NP;
+  size_t bytes = pb * nplanes + sizeof(Scalars) + 256;
+  if (cudaMalloc(&c->adj_pool, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->adj_pool = nullptr;
+    set_err(c, "cannot allocate %zu bytes of adjoint scratch", bytes);
+    return SIF_ECUDA;
+  }
+  double *p = (double *)c->adj_pool;
+  auto take = [&]() {
+    double *r = p;
+    p += c->NP;
+    return r;
+  };
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      c->lamA[k][m] = take();
+      c->lamB[k][m] = take();
+      c->lamC[k][m] = take();
+      c->lw[k][m] = take();
+      c->W1[k][m] = take();
+      c->W2[k][m] = take();
+      c->sv_q[k][m] = take();
+      c->sv_w[k][m] = take();
+    }
+  for (int q = 0; q < 40; q++) c->G[q] = take();
+  c->sv_phi = take();
+  c->sv_sc = (Scalars *)p;
+  CK(cudaMemsetAsync(c->adj_pool, 0, bytes, c->st));
+  return SIF_OK;
+}
+
+// the caller's state (q, stencil states, phi, scalars) around an adjoint call
+static void save_state(sif_ctx *c) {
+  const size_t pb = sizeof(double) * c->NP;
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      d2d(c, c->sv_q[k][m], c->q[k][m], pb);
+      d2d(c, c->sv_w[k][m], c->w[k][m], pb);
+    }
+  d2d(c, c->sv_phi, c->phi, pb);
+  d2d(c, c->sv_sc, c->sc, sizeof(Scalars));
+}
+
+static void restore_state(sif_ctx *c) {
+  const size_t pb = sizeof(double) * c->NP;
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) {
+      d2d(c, c->q[k][m], c->sv_q[k][m], pb);
+      d2d(c, c->w[k][m], c->sv_w[k][m], pb);
+    }
+  d2d(c, c->phi, c->sv_phi, pb);
+  geometry(c);
+  // the saved scalars hold the same list counts as the geometry just made
+  d2d(c, c->sc, c->sv_sc, sizeof(Scalars));
+}
+
+static void set_phi(sif_ctx *c, const double *src) {
+  d2d(c, c->phi, src, sizeof(double) * c->NP);
+  geometry(c);
+}
+
+// recorded step `step` from the current q with its schedule imposed; with
+// keep, both stages' stencil states (ghosts filled) go to W1 and W2
+static void frozen_forward(sif_ctx *c, int step, bool keep) {
+  const size_t pb = sizeof(double) * c->NP;
+  double *sc = tape_scal(c, step);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) d2d(c, c->w[k][m], tape_plane(c, step, 8 + k * 4 + m), pb);
+  set_phi(c, tape_plane(c, step, 16));
+  d2d(c, &c->sc->dt, sc, sizeof(double));
+  for (int k = 0; k < 2; k++) copy_planes(c, c->q0[k], c->q[k], 4);
+  for (int s = 1; s <= 2; s++) {
+    eval(c, c->q);
+    d2d(c, c->sc->lf, sc + (s == 1 ? 1 : 5), sizeof(c->sc->lf));
+    for (int k = 0; k < 2; k++) fv(c, k, s, c->q[k], c->q0[k], c->q[k], &c->sc->dt);
+    if (keep)
+      for (int k = 0; k < 2; k++) copy_planes(c, s == 1 ? c->W1[k] : c->W2[k], c->w[k], 4);
+    set_phi(c, tape_plane(c, step, s == 1 ? 17 : 18));
+    mix_both(c);
+  }
+}
+
+// transposed right-hand side of the stage with stencil states W and LF
+// speeds lf, applied to mu scaled by fac * dt, then primitive^T combined:
+// out = ca A + cb B + J^T (fac dt mu).  The stage's geometry is in place.
+static void adj_stage(sif_ctx *c, double *const W[2][4], const double *lf, const double *dtp,
+                      double fac, double *const mu[2][4], double *const out[2][4],
+                      double *const A[2][4], double ca, double *const B[2][4], double cb) {
+  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
+                   c->ext_plan, ncell(c), band_work(c), c->st);
+  launch_adj_rhs(c->g, W, (const unsigned long long *)lf, dtp, fac, mu, c->ax, c->ay, c->phi,
+                 c->sx, c->sy, c->cut, &c->sc->n_cut, ncell(c), c->G, c->lw, c->st);
+  launch_adj_extension(c->g, c->lw, c->ext_plan, ncell(c), band_work(c), c->band_ev,
+                       &c->sc->n_band, c->bandmap, c->tmp, c->st);
+  launch_adj_prim(c->g, W, c->alpha, c->lw, out, A, ca, B, cb, c->st);
+  dbg(c, "adjoint stage");
+}
+
+static void adj_mix(sif_ctx *c, double *const lam[2][4]) {
+  launch_mix_adjoint(c->g, lam[0], lam[1], c->alpha, c->phi, c->band_ev, c->bandmap,
+                     &c->sc->n_band, c->mix_plan, ncell(c), band_work(c), c->tmp, c->st);
+}
+
+// lamA = adjoint after step `step` -> lamC = adjoint before it
+static void adjoint_step_impl(sif_ctx *c, int step) {
+  const size_t pb = sizeof(double) * c->NP;
+  double *sc = tape_scal(c, step);
+  for (int k = 0; k < 2; k++)
+    for (int m = 0; m < 4; m++) d2d(c, c->q[k][m], tape_plane(c, step, k * 4 + m), pb);
+  frozen_forward(c, step, true);
+  // Q^{n+1} = mix(Q**) with the geometry of phi^{n+1}
+  set_phi(c, tape_plane(c, step, 18));
+  adj_mix(c, c->lamA);
+  // Q** = Q^n / 2 + (Q1 + dt L(Q1)) / 2, stage-2 geometry
+  set_phi(c, tape_plane(c, step, 17));
+  adj_stage(c, c->W2, sc + 5, sc, 0.5, c->lamA, c->lamB, c->lamA, 0.5, nullptr, 0.0);
+  // Q1 = mix(Q*) with the same geometry
+  adj_mix(c, c->lamB);
+  // Q* = Q^n + dt L(Q^n), stage-1 geometry
+  set_phi(c, tape_plane(c, step, 16));
+  adj_stage(c, c->W1, sc + 1, sc, 1.0, c->lamB, c->lamC, c->lamA, 0.5, c->lamB, 1.0);
+}
+
+static int put_state8(sif_ctx *c, double *const dst[2][4], const double *src, int mem) {
+  size_t n = (size_t)ncell(c);
+  int rc = SIF_OK;
+  for (int k = 0; k < 2 && !rc; k++)
+    for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, dst[k][m], src + (k * 4 + m) * n, mem);
+  return rc;
+}
+
+static int get_state8(sif_ctx *c, double *dst, double *const src[2][4], int mem) {
+  size_t n = (size_t)ncell(c);
+  int rc = SIF_OK;
+  for (int k = 0; k < 2 && !rc; k++)
+    for (int m = 0; m < 4 && !rc; m++) rc = get_plane(c, dst + (k * 4 + m) * n, src[k][m], mem);
+  return rc;
+}
+
+extern "C" int sif_tape_reset(sif_ctx *c, int capacity) {
+  if (!c || capacity < 0) return SIF_EINVAL;
+  if (c->cfg.rk_order != 2) {
+    set_err(c, "the adjoint is defined for rk_order 2");
+    return SIF_EINVAL;
+  }
+  cudaSetDevice(c->cfg.device);
+  CK(cudaStreamSynchronize(c->st));
+  c->tape_len = 0;
+  if (capacity == 0) {
+    if (c->tape_planes) cudaFree(c->tape_planes);
+    if (c->adj_pool) cudaFree(c->adj_pool);
+    c->tape_planes = c->tape_scal = nullptr;
+    c->adj_pool = nullptr;
+    c->tape_cap = c->tape_alloc = 0;
+    return SIF_OK;
+  }
+  if (capacity > c->tape_alloc) {
+    if (c->tape_planes) cudaFree(c->tape_planes);
+    c->tape_planes = c->tape_scal = nullptr;
+    c->tape_alloc = 0;
+    size_t bytes = sizeof(double) * ((size_t)capacity * kTapePlanes * c->NP + (size_t)capacity * 16);
+    if (cudaMalloc(&c->tape_planes, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->tape_planes = nullptr;
+      c->tape_cap = 0;
+      set_err(c, "cannot allocate %zu bytes for a %d-step adjoint tape", bytes, capacity);
+      return SIF_ECUDA;
+    }
+    c->tape_scal = c->tape_planes + (size_t)capacity * kTapePlanes * c->NP;
+    c->tape_alloc = capacity;
+  }
+  c->tape_cap = capacity;
+  return ensure_adj_scratch(c);
+}
+
+extern "C" int sif_tape_length(const sif_ctx *c, int *len) {
+  if (!c || !len) return SIF_EINVAL;
+  *len = c->tape_len;
+  return SIF_OK;
+}
+
+static int adj_check(sif_ctx *c, int step, const void *a, const void *b, int mem) {
+  if (!a || !b || (mem != SIF_HOST && mem != SIF_DEVICE)) return SIF_EINVAL;
+  if (step < 0 || step >= c->tape_len) {
+    set_err(c, "step %d not on the tape (%d recorded)", step, c->tape_len);
+    return SIF_EINVAL;
+  }
+  if (!c->inited) {
+    set_err(c, "state not initialised");
+    return SIF_ESTATE;
+  }
+  return SIF_OK;
+}
+
+extern "C" int sif_replay_step(sif_ctx *c, int step, const double *q_in, double *q_out, int mem) {
+  if (!c) return SIF_EINVAL;
+  int rc = adj_check(c, step, q_in, q_out, mem);
+  if (rc) return rc;
+  cudaSetDevice(c->cfg.device);
+  save_state(c);
+  rc = put_state8(c, c->q, q_in, mem);
+  if (rc) return rc;
+  frozen_forward(c, step, false);
+  rc = get_state8(c, q_out, c->q, mem);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(&c->hsc->err, &c->sc->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  restore_state(c);
+  rc = check_launch(c, "replay");
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  if (c->hsc->err & DERR_NONPHYS) {
+    set_err(c, "non-physical state (rho <= 0 or p + p_inf <= 0) in a real cell");
+    return SIF_ENONPHYS;
+  }
+  return SIF_OK;
+}
+
+extern "C" int sif_adjoint_step(sif_ctx *c, int step, const double *lam_in, double *lam_out,
+                                int mem) {
+  if (!c) return SIF_EINVAL;
+  int rc = adj_check(c, step, lam_in, lam_out, mem);
+  if (rc) return rc;
+  cudaSetDevice(c->cfg.device);
+  save_state(c);
+  rc = put_state8(c, c->lamA, lam_in, mem);
+  if (rc) return rc;
+  adjoint_step_impl(c, step);
+  rc = get_state8(c, lam_out, c->lamC, mem);
+  if (rc) return rc;
+  restore_state(c);
+  rc = check_launch(c, "adjoint step");
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  return SIF_OK;
+}
+
+extern "C" int sif_adjoint_init(sif_ctx *c, const double *phi, const double *pN, const double *pP,
+                                const double *lam_q, double *lam_prim, int mem) {
+  if (!c || !phi || !pN || !pP || !lam_q || !lam_prim || (mem != SIF_HOST && mem != SIF_DEVICE))
+    return SIF_EINVAL;
+  cudaSetDevice(c->cfg.device);
+  int rc = ensure_adj_scratch(c);
+  if (rc) return rc;
+  const bool had_state = c->inited;
+  if (had_state) save_state(c);
+  size_t n = (size_t)ncell(c);
+  rc = put_plane(c, c->phi, phi, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->W1[0][m], pN + m * n, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->W1[1][m], pP + m * n, mem);
+  if (!rc) rc = put_state8(c, c->lamA, lam_q, mem);
+  if (rc) return rc;
+  geometry(c);
+  adj_mix(c, c->lamA);
+  launch_adj_init(c->g, c->W1, c->alpha, c->lamA, c->lamC, c->st);
+  rc = get_state8(c, lam_prim, c->lamC, mem);
+  if (rc) return rc;
+  if (had_state) restore_state(c);
+  rc = check_launch(c, "adjoint init");
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->st));
   return SIF_OK;
 }
 

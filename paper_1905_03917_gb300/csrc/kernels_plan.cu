@@ -18,13 +18,6 @@ static int blocks_for(int n, int per) {
 // ---------------------------------------------------------------------
 // interaction band and its map
 
-__global__ void k_unmap(const int *__restrict__ band, const int *nband, int *map) {
-  SIF_TICK();
-  int n = *nband;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
-    map[band[idx]] = -1;
-}
-
 __global__ void k_band_mapped(Grid g, const double *__restrict__ p, int *band, int *map,
                               int *nband) {
   SIF_TICK();
@@ -49,13 +42,16 @@ __global__ void k_band_mapped(Grid g, const double *__restrict__ p, int *band, i
   }
 }
 
+// the whole map is cleared (not only the previous band's entries): a reset
+// of the device scalars (initialisation, checkpoint restore) loses the
+// previous band's count, and the clear must not depend on it
 void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
                      cudaStream_t st) {
   int n = g.nx * g.ny;
-  k_unmap<<<blocks_for(n, 256), 256, 0, st>>>(band, nband, map);
+  cudaMemsetAsync(map, 0xff, sizeof(int) * (size_t)g.PX * g.PY, st);
   cudaMemsetAsync(nband, 0, sizeof(int), st);
   k_band_mapped<<<(n + 255) / 256, 256, 0, st>>>(g, phi, band, map, nband);
-  sif_note_launches(2);
+  sif_note_launches(1);
 }
 
 // ---------------------------------------------------------------------
@@ -242,7 +238,9 @@ __device__ bool mix_source_plan(const Grid &g, int k, int i, int j, const double
   double as = vol_k(alpha, k, c);
   s.nt = 0;
   if (as >= g.mix_alpha) return false;
-  if (as == 0.0 && q[0][c] == 0.0 && q[1][c] == 0.0 && q[2][c] == 0.0 && q[3][c] == 0.0)
+  // an empty small cell with no content has nothing to mix (q == nullptr:
+  // the linearised mixing of the adjoint, which mixes it like any other)
+  if (q && as == 0.0 && q[0][c] == 0.0 && q[1][c] == 0.0 && q[2][c] == 0.0 && q[3][c] == 0.0)
     return false;
   double nxv, nyv;
   unit_normal(g, phi, i, j, nxv, nyv);
@@ -363,6 +361,82 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
   k_mix_setup<<<b, 128, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
   k_mix_apply<<<dim3(b, 2), 128, 0, st>>>(g, mask, Q, map, plan, cap, band, nband, tmp);
   k_mix_scatter<<<dim3(b, 2), 128, 0, st>>>(mask, Q, band, nband, tmp);
+  sif_note_launches(3);
+}
+
+// ---------------------------------------------------------------------
+// transpose of the small-cell mixing (the adjoint of a frozen step): each
+// source-target pair moved M = beta (q_t as - q_s at) / den from the
+// target to the source, so the adjoint of the old states picks up
+// (lam_s - lam_t) dM/dq.  Gathered per band cell like the forward.
+
+__global__ void k_mix_adj_setup(Grid g, const double *__restrict__ alpha,
+                                const double *__restrict__ phi, const int *__restrict__ band,
+                                const int *nband, MixPlan *plan, int cap) {
+  SIF_TICK();
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    for (int k = 0; k < 2; k++) {
+      MixPlan s;
+      mix_source_plan(g, k, i, j, alpha, phi, nullptr, s);
+      plan[(size_t)k * cap + idx] = s;
+    }
+  }
+}
+
+__global__ void k_mix_adj_apply(Grid g, MixQ L, const int *__restrict__ map,
+                                const MixPlan *__restrict__ plan, int cap,
+                                const int *__restrict__ band, const int *nband, double *tmp) {
+  SIF_TICK();
+  int k = blockIdx.y;
+  int n = *nband;
+  double *const *lam = L.q[k];
+  const MixPlan *P = plan + (size_t)k * cap;
+  double *out = tmp + (size_t)k * 4 * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    double val[4] = {lam[0][c], lam[1][c], lam[2][c], lam[3][c]};
+    for (int dj = -1; dj <= 1; dj++) {
+      if (g.dim == 1 && dj != 0) continue;
+      for (int di = -1; di <= 1; di++) {
+        if (!inside(g, i + di, j + dj)) continue;
+        int s = gidx(g, i + di, j + dj);
+        int ps = map[s];
+        if (ps < 0) continue;
+        const MixPlan &sp = P[ps];
+        for (int t = 0; t < sp.nt; t++) {
+          int tc = sp.tc[t];
+          bool self = (s == c), tgt = (tc == c);
+          if (!self && !tgt) continue;
+          double den = sp.as * sp.beta[t] + sp.at[t];
+          for (int m = 0; m < 4; m++) {
+            double dM = lam[m][s] - lam[m][tc];
+            if (self) val[m] -= dM * sp.beta[t] * sp.at[t] / den;
+            if (tgt) val[m] += dM * sp.beta[t] * sp.as / den;
+          }
+        }
+      }
+    }
+    for (int m = 0; m < 4; m++) out[(size_t)m * n + idx] = val[m];
+  }
+}
+
+void launch_mix_adjoint(const Grid &g, double *const lN[4], double *const lP[4],
+                        const double *alpha, const double *phi, const int *band, const int *map,
+                        const int *nband, MixPlan *plan, int cap, int work, double *tmp,
+                        cudaStream_t st) {
+  MixQ L;
+  for (int m = 0; m < 4; m++) {
+    L.q[0][m] = lN[m];
+    L.q[1][m] = lP[m];
+  }
+  int b = blocks_for(work, 128);
+  k_mix_adj_setup<<<b, 128, 0, st>>>(g, alpha, phi, band, nband, plan, cap);
+  k_mix_adj_apply<<<dim3(b, 2), 128, 0, st>>>(g, L, map, plan, cap, band, nband, tmp);
+  k_mix_scatter<<<dim3(b, 2), 128, 0, st>>>(3, L, band, nband, tmp);
   sif_note_launches(3);
 }
 

@@ -363,6 +363,26 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      const double *xn0, const double *xn1, const double *xn2, const int *tiles,
                      int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st);
 
+// adjoint of the frozen single-time-step step (adjoint.cu, kernels_plan.cu)
+void launch_adj_rhs(const Grid &g, double *const W[2][4], const unsigned long long *lf,
+                    const double *dtp, double fac, double *const mu[2][4], const double *ax,
+                    const double *ay, const double *phi, const double *sx, const double *sy,
+                    const int *cut, const int *ncut, int cut_cap, double *const G[40],
+                    double *const lw[2][4], cudaStream_t st);
+void launch_adj_extension(const Grid &g, double *const lw[2][4], const ExtPlan *plan, int cap,
+                          int work, const int *band, const int *nband, const int *map,
+                          double *tmp, cudaStream_t st);
+void launch_adj_prim(const Grid &g, double *const W[2][4], const double *alpha,
+                     double *const lw[2][4], double *const out[2][4], double *const A[2][4],
+                     double ca, double *const B[2][4], double cb, cudaStream_t st);
+void launch_adj_init(const Grid &g, double *const prim[2][4], const double *alpha,
+                     double *const lam[2][4], double *const out[2][4], cudaStream_t st);
+void launch_mix_adjoint(const Grid &g, double *const lN[4], double *const lP[4],
+                        const double *alpha, const double *phi, const int *band, const int *map,
+                        const int *nband, MixPlan *plan, int cap, int work, double *tmp,
+                        cudaStream_t st);
+unsigned long long sif_launches_adj();
+
 // scheduler ops
 #define SCHED_SINGLE_DT 0   // dt = min over fluids, capped by t_end
 #define SCHED_CYCLE_BEGIN 1 // roles, ratio, truncation

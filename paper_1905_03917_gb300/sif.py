@@ -26,7 +26,9 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif_profile_enable", "sif_profile_read", "sif_measure_fp64_peak",
            "sif_integrals_noalloc", "sif_set_tile_shape", "sif_get_tile_shape",
            "sif_batch_create", "sif_batch_instance", "sif_batch_step_multi_dt",
-           "sif_batch_last_error", "sif_batch_destroy", "sif_batch_one_graph"]
+           "sif_batch_last_error", "sif_batch_destroy", "sif_batch_one_graph",
+           "sif_tape_reset", "sif_tape_length", "sif_replay_step", "sif_adjoint_step",
+           "sif_adjoint_init"]
 
 
 class SifError(RuntimeError):
@@ -104,6 +106,14 @@ def load(path: str | None = None):
     L.sif_batch_destroy.restype = None
     L.sif_batch_one_graph.argtypes = [P]
     L.sif_batch_one_graph.restype = I
+    L.sif_tape_reset.argtypes = [P, I]
+    L.sif_tape_length.argtypes = [P, ctypes.POINTER(I)]
+    L.sif_replay_step.argtypes = [P, I, P, P, I]
+    L.sif_adjoint_step.argtypes = [P, I, P, P, I]
+    L.sif_adjoint_init.argtypes = [P, P, P, P, P, P, I]
+    for f in (L.sif_tape_reset, L.sif_tape_length, L.sif_replay_step, L.sif_adjoint_step,
+              L.sif_adjoint_init):
+        f.restype = I
     for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
               L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time,
               L.sif_save, L.sif_load, L.sif_profile_enable, L.sif_profile_read,
@@ -292,6 +302,55 @@ class Solver:
         v = ctypes.c_double()
         self._check(load().sif_get_time(self._h, ctypes.byref(v)))
         return v.value
+
+    # -- adjoint of the frozen single-dt step (sif_tape_* / sif_adjoint_*) --
+
+    def tape_reset(self, capacity: int):
+        self._check(load().sif_tape_reset(self._h, int(capacity)))
+
+    @property
+    def tape_length(self) -> int:
+        v = ctypes.c_int()
+        self._check(load().sif_tape_length(self._h, ctypes.byref(v)))
+        return v.value
+
+    def _pair(self, a, b):
+        (pa, ka), (pb, kb) = _ptr(a), _ptr(b)
+        if ka != kb:
+            raise ValueError("both arrays must be in the same memory")
+        n = 8 * self.nx * self.ny
+        for x in (a, b):
+            size = x.size if isinstance(x, np.ndarray) else x.numel()
+            if size != n:
+                raise ValueError(f"expected {n} doubles (2 x 4 x ny x nx)")
+        return pa, pb, ka
+
+    def replay_step(self, step, q_in, q_out=None):
+        """Frozen replay of recorded step `step` from q_in (2, 4, ny, nx)."""
+        if q_out is None:
+            q_out = np.empty((2, 4, self.ny, self.nx))
+        a, b, k = self._pair(q_in, q_out)
+        self._check(load().sif_replay_step(self._h, int(step), a, b, k))
+        return q_out
+
+    def adjoint_step(self, step, lam_in, lam_out=None):
+        """Adjoint of the state before recorded step `step` from that after it."""
+        if lam_out is None:
+            lam_out = np.empty((2, 4, self.ny, self.nx))
+        a, b, k = self._pair(lam_in, lam_out)
+        self._check(load().sif_adjoint_step(self._h, int(step), a, b, k))
+        return lam_out
+
+    def adjoint_init(self, phi, prim_N, prim_P, lam_q, lam_prim=None):
+        """Adjoint of the primitive initial fields from that of the initial state."""
+        if lam_prim is None:
+            lam_prim = np.empty((2, 4, self.ny, self.nx))
+        ptrs = [_ptr(x) for x in (phi, prim_N, prim_P, lam_q, lam_prim)]
+        kinds = {k for _, k in ptrs}
+        if len(kinds) != 1:
+            raise ValueError("all arrays must be in the same memory")
+        self._check(load().sif_adjoint_init(self._h, *[p for p, _ in ptrs], kinds.pop()))
+        return lam_prim
 
 
 class Batch:
