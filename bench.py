@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 # face flux per cell and direction (4 components x (2 reconstructions of 70
 # flops + 2)), and the update (10 per component).  1D has one direction.
 FLOPS_PER_UPDATE = {2: 2 * 35 + 2 * 4 * 142 + 4 * 10, 1: 35 + 4 * 142 + 4 * 7}
+METRIC = "fluid cell-updates/s (FP64), % HBM peak; multi-dt vs single-dt speedup at equal err"
 # nominal FP64 rate of a GB300: 152 SMs x 4 flops/clock (2 FMA) x 2.07 GHz
 NOMINAL_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
@@ -137,11 +138,12 @@ def run_reference(args):
     # count the same (cell, fluid) updates the GPU path counts for these steps
     updates = gpu_updates_for(case, args.mode, args.warmup, args.steps)
     value = updates / dt if updates else None
-    line = {"impl": "reference", "metric": "fluid cell-updates/s (FP64)", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": case["name"], "mode": args.mode},
+            "config": {"workload": case["name"], "mode": args.mode, "nx": case["cfg"]["nx"],
+                       "ny": case["cfg"]["ny"]},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed steps after {args.warmup} of {case['name']}"},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
@@ -162,6 +164,131 @@ def gpu_updates_for(case, mode, skip, count):
         return step(count)["cell_updates"]
     except Exception:
         return None
+
+
+# Algorithmic DRAM bytes of one (cell, fluid) finite-volume RK stage: the
+# stencil state (4 doubles), apertures (2), interface vector (2), exchange
+# flux (3), the current and (second stage) base states (4 + 4 / 2 on
+# average) read once, the new state (4) written once.
+BYTES_PER_UPDATE = 8 * (4 + 2 + 2 + 3 + 4 + 2 + 4)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _hbm_context(units, avg_ms):
+    """The finite-volume kernel's algorithmic bytes per launch over its time,
+    against the HBM copy bandwidth (the kernel is bound by FP64 issue, not
+    by HBM: this fraction is context for the % HBM part of the metric)."""
+    peak, src = _hbm_peak()
+    if not avg_ms:
+        return None
+    gbs = units * BYTES_PER_UPDATE / (avg_ms * 1e-3) / 1e9
+    return {"bytes_per_update": BYTES_PER_UPDATE, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "peak_source": src}
+
+
+def _prim_arrays(case):
+    return [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
+
+
+def multi_vs_single(case, device, steps_single=600):
+    """Both forms advance the same problem to the same time T (the time 600
+    single-dt steps reach: through the shock-bubble interaction) on the GPU; the error of each is the relative L1
+    of the mixture density and energy fields against the single-dt method
+    at a quarter of the CFL number (temporal error about 16x smaller) on the
+    same grid.  speedup = GPU time of single-dt / GPU time of multi-dt."""
+    import torch
+    from paper_1905_03917_gb300 import sif
+    arrs = _prim_arrays(case)
+    probe = sif.Solver(case["cfg"], device=device).init_fluids(*arrs)
+    probe.step_single_dt(steps_single)
+    T = probe.t
+    probe.close()
+
+    def fields(s):
+        qN, qP, _ = s.state()
+        return qN[0] + qP[0], qN[3] + qP[3]
+
+    def run(cfg, multi, warm=True):
+        s = sif.Solver(cfg, device=device).init_fluids(*arrs)
+        step = s.step_multi_dt if multi else s.step_single_dt
+        if warm:
+            step(10 ** 6, t_end=T)      # graphs built for this problem
+            s.init_fluids(*arrs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = step(10 ** 6, t_end=T)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        out = fields(s), ms, info
+        s.close()
+        return out
+
+    (ref_rho, ref_E), _, _ = run(dict(case["cfg"], cfl=case["cfg"].get("cfl", 0.6) / 4), False,
+                                 warm=False)
+    res = {}
+    for name, multi in (("single", False), ("multi", True)):
+        (rho, E), ms, info = run(case["cfg"], multi)
+        res[name] = {"ms": ms,
+                     "err_rho": float(np.abs(rho - ref_rho).sum() / np.abs(ref_rho).sum()),
+                     "err_E": float(np.abs(E - ref_E).sum() / np.abs(ref_E).sum())}
+    return {"T": T, "speedup": res["single"]["ms"] / res["multi"]["ms"],
+            "err_ratio_rho": res["multi"]["err_rho"] / res["single"]["err_rho"],
+            "single": res["single"], "multi": res["multi"],
+            "reference": "single-dt at CFL 0.15 on the same grid (GPU; parity-tested against the oracle)",
+            "timing": "host wall clock around synchronising calls that run to t_end"}
+
+
+def adjoint_cost(device, n=512, nsteps=200, every=20):
+    """Gradient of the x = 1 wall pressure after nsteps single-dt steps with
+    respect to the initial gas pressure field (gas-water bubble, n x n,
+    nondimensional units) through the checkpointed autograd Function."""
+    import torch
+    from paper_1905_03917_gb300 import adjoint, inputs, sif
+    case = inputs.adjoint_bubble(n, centre=(0.7, 0.0))
+    cfg = case["cfg"]
+    dev = torch.device("cuda", device)
+    phi, pN, pP = (torch.tensor(a, dtype=torch.float64, device=dev) for a in _prim_arrays(case))
+    s = sif.Solver(cfg, device=device).init_fluids(phi, pN, pP)
+    s.step_single_dt(3)                       # warm-up (graphs)
+    s.init_fluids(phi, pN, pP)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step_single_dt(nsteps)
+    torch.cuda.synchronize()
+    plain_ms = 1e3 * (time.perf_counter() - t0)
+    pNg = pN.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q, _ = adjoint.frozen_steps(s, phi, pNg, pP, nsteps=nsteps, every=every)
+    J = adjoint.wall_pressure(q, cfg)
+    torch.cuda.synchronize()
+    fwd_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    bwd_ms = 1e3 * (time.perf_counter() - t0)
+    g = pNg.grad[3]
+    s.close()
+    return {"workload": f"adjoint_bubble_{n}x{n} (gas-water, nondimensional, bubble at x=0.7)",
+            "steps": nsteps, "checkpoint_every": every,
+            "forward_ms_per_step": plain_ms / nsteps,
+            "checkpointed_forward_ms_per_step": fwd_ms / nsteps,
+            "backward_ms_per_step": bwd_ms / nsteps,
+            "backward_over_forward": bwd_ms / plain_ms,
+            "J": float(J), "grad_norm": float(torch.linalg.vector_norm(g)),
+            "timing": "host wall clock around synchronising calls; backward re-runs each "
+                      "segment from its checkpoint, recording, then its adjoint steps"}
 
 
 def run_ours(args):
@@ -240,7 +367,7 @@ def run_ours(args):
     except Exception:
         probe = None
     line = {
-        "metric": "fluid cell-updates/s (FP64)", "value": value, "unit": "cell-updates/s",
+        "metric": METRIC, "value": value, "unit": "cell-updates/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -254,12 +381,16 @@ def run_ours(args):
                      "traffic": None, "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
                      "fp64_probe_tflops": probe, "flops_per_update": flops,
                      "avg_launch_ms": fv_avg_ms, "updates_per_launch": fv_units,
-                     "share_of_step": prof["fv_ms"] / total_ms if total_ms else None},
+                     "share_of_step": prof["fv_ms"] / total_ms if total_ms else None,
+                     "hbm": _hbm_context(fv_units, fv_avg_ms)},
         "gpu_launches": prof["kernel_launches"],
         "e2e": {"value": e2e_updates / (e2e_ms / 1e3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
         "clocks": clk.summary(),
     }
+    if ws == 1 and not args.no_extras and case["cfg"]["dim"] == 2:
+        line["multi_vs_single"] = multi_vs_single(case, local)
+        line["adjoint"] = adjoint_cost(local)
     if ws == 1 and not args.no_cpu_baseline:
         nsteps, secs = cpu_baseline(case, args.mode, budget_s=args.cpu_budget)
         upd = gpu_updates_for(case, args.mode, 0, nsteps)
@@ -305,7 +436,7 @@ def run_batched(args):
     if rank != 0:
         return
     cells = sum(c["cfg"]["nx"] * c["cfg"]["ny"] for c in cases)
-    line = {"metric": "fluid cell-updates/s (FP64)", "value": updates / (total_ms / 1e3),
+    line = {"metric": METRIC, "value": updates / (total_ms / 1e3),
             "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -328,6 +459,8 @@ def main():
     ap.add_argument("--mode", default="multi", choices=["multi", "single"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the multi-vs-single and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

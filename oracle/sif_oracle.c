@@ -784,7 +784,19 @@ static void reinit(orc_ctx *o, double *p) {
                 dmax(sq(dmin(cc, 0.0)), sq(dmax(d, 0.0)));
           else
             continue;
-          p[c] = q[c] - 0.5 * h * S * (sqrt(G) - 1.0);
+          double nv = q[c] - 0.5 * h * S * (sqrt(G) - 1.0);
+          /* no new extremum: a positive value stays at or above its
+           * smallest face neighbour, a negative one at or below its
+           * largest (the WENO derivatives can overshoot at the kinks that
+           * form where the moving band meets the level set outside it) */
+          double lo = dmin(q[c - 1], q[c + 1]), hi = dmax(q[c - 1], q[c + 1]);
+          if (d2) {
+            lo = dmin(lo, dmin(q[c - o->PX], q[c + o->PX]));
+            hi = dmax(hi, dmax(q[c - o->PX], q[c + o->PX]));
+          }
+          if (s0 > 0.0 && nv < lo) nv = lo;
+          if (s0 < 0.0 && nv > hi) nv = hi;
+          p[c] = nv;
         }
       }
   }

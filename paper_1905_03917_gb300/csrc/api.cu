@@ -58,15 +58,17 @@ struct sif_ctx {
   double *tape_planes;  // tape_alloc x kTapePlanes planes
   double *tape_scal;    // tape_alloc x 16: dt, LF speeds of stage 1 and 2 (bit patterns)
   void *adj_pool;
-  double *lamA[2][4], *lamB[2][4], *lamC[2][4], *lw[2][4], *W1[2][4], *W2[2][4], *G[40];
+  double *lamA[2][4], *lamB[2][4], *lamC[2][4], *lw[2][4], *prim[2][4], *G[40];
   double *sv_q[2][4], *sv_w[2][4], *sv_phi;
   Scalars *sv_sc;
   char err[256];
 };
 
 // per recorded step: q (8), the stencil states the step starts from (8),
-// phi^n, phi after stage 1, phi^{n+1}
-static const int kTapePlanes = 19;
+// phi^n, phi after stage 1, phi^{n+1}, and the stencil states (ghosts
+// filled) that stage 1 and stage 2 used (8 + 8)
+static const int kTapePlanes = 35;
+static const int kTapeW1 = 19, kTapeW2 = 27;
 
 // launch counting happens on the device (SIF_TICK); the host-side notes
 // the wrappers make are not used for measurement
@@ -414,6 +416,7 @@ static void reinit(sif_ctx *c) {
 struct TapeHook {
   double *phi1;
   double *lf2;
+  double *W[2][2][4];  // stage, fluid, component
 };
 
 // one RK step of both fluids and the level set, the first interaction
@@ -427,6 +430,11 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
     if (rec && s == 2)
       cudaMemcpyAsync(rec->lf2, c->sc->lf, sizeof(c->sc->lf), cudaMemcpyDeviceToDevice, c->st);
     for (int k = 0; k < 2; k++) fv(c, k, s, c->q[k], c->q0[k], c->q[k], dtp);
+    if (rec && s <= 2)
+      for (int k = 0; k < 2; k++)
+        for (int m = 0; m < 4; m++)
+          cudaMemcpyAsync(rec->W[s - 1][k][m], c->w[k][m], sizeof(double) * c->NP,
+                          cudaMemcpyDeviceToDevice, c->st);
     ls_stage(c, s, dtp);
     if (rec && s == 1)
       cudaMemcpyAsync(rec->phi1, c->phi, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
@@ -1094,10 +1102,11 @@ extern "C" int sif_load(sif_ctx *c, const void *buf, size_t len) {
 // While a tape is active every single-dt step records what its frozen
 // replay needs: the state, the stencil states it starts from (the
 // extension's starting values), phi at its start, after stage 1 and at its
-// end, dt and the Lax-Friedrichs speeds of both stages.  The replay runs
-// the same kernels with that schedule imposed; the adjoint replays one
-// step keeping both stages' stencil states, then applies the transposed
-// kernels in reverse order.
+// end, dt and the Lax-Friedrichs speeds of both stages, and the stencil
+// states both stages used.  The replay runs the same kernels with that
+// schedule imposed; the adjoint takes the stages' stencil states from the
+// tape, refreshes each stage's geometry from its level set and applies the
+// transposed kernels in reverse order.
 
 static double *tape_plane(sif_ctx *c, int step, int i) {
   return c->tape_planes + ((size_t)step * kTapePlanes + i) * c->NP;
@@ -1121,7 +1130,13 @@ static void taped_step(sif_ctx *c) {
   launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
   d2d(c, tape_scal(c, s), &c->sc->dt, sizeof(double));
   d2d(c, tape_scal(c, s) + 1, c->sc->lf, sizeof(c->sc->lf));
-  TapeHook hook = {tape_plane(c, s, 17), tape_scal(c, s) + 5};
+  TapeHook hook;
+  hook.phi1 = tape_plane(c, s, 17);
+  hook.lf2 = tape_scal(c, s) + 5;
+  for (int st = 0; st < 2; st++)
+    for (int k = 0; k < 2; k++)
+      for (int m = 0; m < 4; m++)
+        hook.W[st][k][m] = tape_plane(c, s, (st == 0 ? kTapeW1 : kTapeW2) + k * 4 + m);
   single_step_after_eval(c, &c->sc->dt, &hook);
   d2d(c, tape_plane(c, s, 18), c->phi, pb);
   launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
@@ -1130,7 +1145,7 @@ static void taped_step(sif_ctx *c) {
 
 static int ensure_adj_scratch(sif_ctx *c) {
   if (c->adj_pool) return SIF_OK;
-  const int nplanes = 24 + 8 + 16 + 40 + 17;
+  const int nplanes = 24 + 8 + 8 + 40 + 17;
   size_t pb = sizeof(double) * c->NP;
   size_t bytes = pb * nplanes + sizeof(Scalars) + 256;
   if (cudaMalloc(&c->adj_pool, bytes) != cudaSuccess) {
@@ -1151,8 +1166,7 @@ static int ensure_adj_scratch(sif_ctx *c) {
       c->lamB[k][m] = take();
       c->lamC[k][m] = take();
       c->lw[k][m] = take();
-      c->W1[k][m] = take();
-      c->W2[k][m] = take();
+      c->prim[k][m] = take();
       c->sv_q[k][m] = take();
       c->sv_w[k][m] = take();
     }
@@ -1193,9 +1207,8 @@ static void set_phi(sif_ctx *c, const double *src) {
   geometry(c);
 }
 
-// recorded step `step` from the current q with its schedule imposed; with
-// keep, both stages' stencil states (ghosts filled) go to W1 and W2
-static void frozen_forward(sif_ctx *c, int step, bool keep) {
+// recorded step `step` from the current q with its schedule imposed
+static void frozen_forward(sif_ctx *c, int step) {
   const size_t pb = sizeof(double) * c->NP;
   double *sc = tape_scal(c, step);
   for (int k = 0; k < 2; k++)
@@ -1207,8 +1220,6 @@ static void frozen_forward(sif_ctx *c, int step, bool keep) {
     eval(c, c->q);
     d2d(c, c->sc->lf, sc + (s == 1 ? 1 : 5), sizeof(c->sc->lf));
     for (int k = 0; k < 2; k++) fv(c, k, s, c->q[k], c->q0[k], c->q[k], &c->sc->dt);
-    if (keep)
-      for (int k = 0; k < 2; k++) copy_planes(c, s == 1 ? c->W1[k] : c->W2[k], c->w[k], 4);
     set_phi(c, tape_plane(c, step, s == 1 ? 17 : 18));
     mix_both(c);
   }
@@ -1235,24 +1246,27 @@ static void adj_mix(sif_ctx *c, double *const lam[2][4]) {
                      &c->sc->n_band, c->mix_plan, ncell(c), band_work(c), c->tmp, c->st);
 }
 
-// lamA = adjoint after step `step` -> lamC = adjoint before it
+// lamA = adjoint after step `step` -> lamC = adjoint before it; both
+// stages' stencil states come from the tape
 static void adjoint_step_impl(sif_ctx *c, int step) {
-  const size_t pb = sizeof(double) * c->NP;
   double *sc = tape_scal(c, step);
+  double *W1[2][4], *W2[2][4];
   for (int k = 0; k < 2; k++)
-    for (int m = 0; m < 4; m++) d2d(c, c->q[k][m], tape_plane(c, step, k * 4 + m), pb);
-  frozen_forward(c, step, true);
+    for (int m = 0; m < 4; m++) {
+      W1[k][m] = tape_plane(c, step, kTapeW1 + k * 4 + m);
+      W2[k][m] = tape_plane(c, step, kTapeW2 + k * 4 + m);
+    }
   // Q^{n+1} = mix(Q**) with the geometry of phi^{n+1}
   set_phi(c, tape_plane(c, step, 18));
   adj_mix(c, c->lamA);
   // Q** = Q^n / 2 + (Q1 + dt L(Q1)) / 2, stage-2 geometry
   set_phi(c, tape_plane(c, step, 17));
-  adj_stage(c, c->W2, sc + 5, sc, 0.5, c->lamA, c->lamB, c->lamA, 0.5, nullptr, 0.0);
+  adj_stage(c, W2, sc + 5, sc, 0.5, c->lamA, c->lamB, c->lamA, 0.5, nullptr, 0.0);
   // Q1 = mix(Q*) with the same geometry
   adj_mix(c, c->lamB);
   // Q* = Q^n + dt L(Q^n), stage-1 geometry
   set_phi(c, tape_plane(c, step, 16));
-  adj_stage(c, c->W1, sc + 1, sc, 1.0, c->lamB, c->lamC, c->lamA, 0.5, c->lamB, 1.0);
+  adj_stage(c, W1, sc + 1, sc, 1.0, c->lamB, c->lamC, c->lamA, 0.5, c->lamB, 1.0);
 }
 
 static int put_state8(sif_ctx *c, double *const dst[2][4], const double *src, int mem) {
@@ -1334,7 +1348,7 @@ extern "C" int sif_replay_step(sif_ctx *c, int step, const double *q_in, double 
   save_state(c);
   rc = put_state8(c, c->q, q_in, mem);
   if (rc) return rc;
-  frozen_forward(c, step, false);
+  frozen_forward(c, step);
   rc = get_state8(c, q_out, c->q, mem);
   if (rc) return rc;
   CK(cudaMemcpyAsync(&c->hsc->err, &c->sc->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1379,13 +1393,13 @@ extern "C" int sif_adjoint_init(sif_ctx *c, const double *phi, const double *pN,
   if (had_state) save_state(c);
   size_t n = (size_t)ncell(c);
   rc = put_plane(c, c->phi, phi, mem);
-  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->W1[0][m], pN + m * n, mem);
-  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->W1[1][m], pP + m * n, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->prim[0][m], pN + m * n, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->prim[1][m], pP + m * n, mem);
   if (!rc) rc = put_state8(c, c->lamA, lam_q, mem);
   if (rc) return rc;
   geometry(c);
   adj_mix(c, c->lamA);
-  launch_adj_init(c->g, c->W1, c->alpha, c->lamA, c->lamC, c->st);
+  launch_adj_init(c->g, c->prim, c->alpha, c->lamA, c->lamC, c->st);
   rc = get_state8(c, lam_prim, c->lamC, mem);
   if (rc) return rc;
   if (had_state) restore_state(c);

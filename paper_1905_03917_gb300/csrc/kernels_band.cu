@@ -283,7 +283,20 @@ __global__ void k_reinit(Grid g, const double *__restrict__ q, const double *__r
         G = fmax(sqd(fmax(a, 0.0)), sqd(fmin(b, 0.0))) + fmax(sqd(fmax(cc, 0.0)), sqd(fmin(d, 0.0)));
       else if (s0 < 0.0)
         G = fmax(sqd(fmin(a, 0.0)), sqd(fmax(b, 0.0))) + fmax(sqd(fmin(cc, 0.0)), sqd(fmax(d, 0.0)));
-      if (G >= 0.0) out = q[c] - 0.5 * h * S * (sqrt(G) - 1.0);
+      if (G >= 0.0) {
+        out = q[c] - 0.5 * h * S * (sqrt(G) - 1.0);
+        // no new extremum: a positive value stays at or above its smallest
+        // face neighbour, a negative one at or below its largest (the WENO
+        // derivatives can overshoot at kinks where the moving band meets
+        // the level set outside it)
+        double lo = fmin(q[c - 1], q[c + 1]), hi = fmax(q[c - 1], q[c + 1]);
+        if (d2) {
+          lo = fmin(lo, fmin(q[c - g.PX], q[c + g.PX]));
+          hi = fmax(hi, fmax(q[c - g.PX], q[c + g.PX]));
+        }
+        if (s0 > 0.0 && out < lo) out = lo;
+        if (s0 < 0.0 && out > hi) out = hi;
+      }
     }
     tmp[idx] = out;
   }

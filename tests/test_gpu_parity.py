@@ -200,3 +200,18 @@ def test_step_before_init_is_a_state_error():
     with pytest.raises(sif.SifError) as e:
         s.step_single_dt(1)
     assert e.value.code == sif.ESTATE
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_shock_bubble_through_the_interaction(multi):
+    """GPU and oracle through the whole shock-bubble interaction (t = 1.0,
+    hundreds of steps): both run clean and stay close."""
+    case = inputs.shock_bubble(128, 32)
+    g, o = pair(case)
+    for s in (g, o):
+        step = s.step_multi_dt if multi else s.step_single_dt
+        step(100000, t_end=1.0)
+    assert o.status == 0
+    assert abs(g.t - o.t) <= 1e-12 * o.t
+    worst = compare(g, o, 1e-6)
+    print("relative L1 after t = 1.0:", worst)
