@@ -201,8 +201,8 @@ void sif_batch_destroy(sif_batch *b);
 
 /* Start recording: every later sif_step_single_dt step (up to capacity in
  * total) records what its frozen replay needs (state, stencil states, level
- * sets, dt, LF speeds, both stages' stencil states: 35 planes and 9
- * scalars per step, device memory
+ * sets, dt, LF speeds, both stages' stencil states and cut-cell flags:
+ * 36 planes and 9 scalars per step, device memory
  * owned by the context).  Resets the tape to length 0.  capacity 0 stops
  * recording and frees the tape.  While recording, steps run without the
  * captured graphs (same kernels, same results) and sif_step_multi_dt

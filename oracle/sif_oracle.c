@@ -57,6 +57,8 @@
  * states like empty cells while their (alpha U) is still carried and
  * mixed. */
 #define ALPHA_REAL 1e-6
+/* (a cut cell whose content is not a physical state is treated the same
+ * way: see is_real and prim) */
 
 struct orc_ctx {
   orc_config c;
@@ -77,6 +79,9 @@ struct orc_ctx {
   double *prev[4], *fut[4], *qi[4], *xc[3];
   double *phi0, *lphi, *p0;
   unsigned char *band, *rext;
+  /* per fluid: 1 where a small cell's content is not a physical state
+   * (set by prim for the current stage) */
+  unsigned char *nostate[2];
 };
 
 #define ID(o, i, j) ((i) + GH + ((j) + GH) * (o)->PX)
@@ -255,10 +260,12 @@ static int inside(const orc_ctx *o, int i, int j) {
 /* small-cell mixing (Sec. 2.2, last paragraph)                        */
 
 /* targets of small cell (i, j) of fluid k: the normal-direction neighbours
- * of larger volume fraction; neighbours that are not small cells themselves
- * are preferred, and only when there is none do smaller (but still larger
- * than the source) neighbours take part.  Returns the number of targets,
- * their cells and weights beta (summing to one). */
+ * that are not small cells themselves, weighted by the squared normal
+ * components; when there is none, the largest of the eight neighbours if
+ * it is not small; failing that, the normal-direction neighbours larger
+ * than the source.  (Mixing a small cell into another small one lets
+ * inconsistent content pile up in thin, under-resolved films.)  Returns
+ * the number of targets, their cells and weights beta (summing to one). */
 static int mix_targets(orc_ctx *o, int k, int i, int j, int tc[3], double beta[3]) {
   int c = ID(o, i, j);
   double as = vol(o, k, c);
@@ -274,14 +281,37 @@ static int mix_targets(orc_ctx *o, int k, int i, int j, int tc[3], double beta[3
   int nt = o->c.dim == 2 ? 3 : 1;
   int keep[3] = {0, 0, 0};
   double sum = 0.0;
-  for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
+  for (int t = 0; t < nt; t++) {
+    if (!inside(o, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
+    if (!(vol(o, k, ID(o, ti[t], tj[t])) >= o->c.mix_alpha)) continue;
+    keep[t] = 1;
+    sum += wt[t];
+  }
+  if (!(sum > 0.0)) {
+    int best = -1;
+    double ab = 0.0;
+    for (int dj = -1; dj <= 1; dj++)
+      for (int di = -1; di <= 1; di++) {
+        if ((di == 0 && dj == 0) || (o->c.dim == 1 && dj != 0) || !inside(o, i + di, j + dj))
+          continue;
+        double at = vol(o, k, ID(o, i + di, j + dj));
+        if (at > ab) {
+          ab = at;
+          best = ID(o, i + di, j + dj);
+        }
+      }
+    if (best >= 0 && ab >= o->c.mix_alpha) {
+      tc[0] = best;
+      beta[0] = 1.0;
+      return 1;
+    }
     for (int t = 0; t < nt; t++) {
       if (!inside(o, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
-      double at = vol(o, k, ID(o, ti[t], tj[t]));
-      if (pass == 0 ? !(at >= o->c.mix_alpha) : !(at > as)) continue;
+      if (!(vol(o, k, ID(o, ti[t], tj[t])) > as)) continue;
       keep[t] = 1;
       sum += wt[t];
     }
+  }
   if (!(sum > 0.0)) return 0;
   int n = 0;
   for (int t = 0; t < nt; t++) {
@@ -324,19 +354,37 @@ static void mix(orc_ctx *o, int k, double *const q[4]) {
 /* ------------------------------------------------------------------ */
 /* stencil states: real cells and extension (Sec. 2.3, last paragraph) */
 
+/* a cell holds fluid k for stencil and CFL purposes if its volume
+ * fraction exceeds the sliver threshold and, for a cut cell, its content
+ * is a physical state */
+static int is_real(const orc_ctx *o, int k, int c) {
+  return vol(o, k, c) > ALPHA_REAL && !o->nostate[k][c];
+}
+
+/* Cut cells whose content is not a physical state -- a cell that has just
+ * opened with no neighbour to mix from, or an under-resolved film whose
+ * content ran away -- take extended states like slivers; their content is
+ * carried, updated and mixed.  A full cell with such content is an error. */
 static void prim(orc_ctx *o, int k, double *const q[4]) {
   double g = o->c.gamma[k], pi = o->c.pinf[k];
   for (int j = 0; j < o->c.ny; j++)
     for (int i = 0; i < o->c.nx; i++) {
       int c = ID(o, i, j);
       double a = vol(o, k, c);
+      o->nostate[k][c] = 0;
       if (!(a > ALPHA_REAL)) continue;
       double rho = q[0][c] / a;
       double u = q[1][c] / q[0][c];
       double v = q[2][c] / q[0][c];
       double E = q[3][c] / a;
       double p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - g * pi;
-      if (!(rho > 0.0) || !(p + pi > 0.0)) o->err |= ORC_ERR_NONPHYS;
+      if (!(rho > 0.0) || !(p + pi > 0.0)) {
+        if (a < 1.0) {
+          o->nostate[k][c] = 1;
+          continue;
+        }
+        o->err |= ORC_ERR_NONPHYS;
+      }
       o->w[k][0][c] = rho;
       o->w[k][1][c] = u;
       o->w[k][2][c] = v;
@@ -355,7 +403,7 @@ static void extend(orc_ctx *o, int k, const double *p) {
     for (int j = 0; j < o->c.ny; j++)
       for (int i = 0; i < o->c.nx; i++) {
         int c = ID(o, i, j);
-        if (!(fabs(p[c]) < bw) || vol(o, k, c) > ALPHA_REAL) continue;
+        if (!(fabs(p[c]) < bw) || is_real(o, k, c)) continue;
         double nxv, nyv;
         normal(o, p, i, j, &nxv, &nyv);
         if (k == 0) {
@@ -388,7 +436,7 @@ static void wave_maxima(orc_ctx *o, int k, const double *p) {
   for (int j = 0; j < o->c.ny; j++)
     for (int i = 0; i < o->c.nx; i++) {
       int c = ID(o, i, j);
-      int real = vol(o, k, c) > ALPHA_REAL;
+      int real = is_real(o, k, c);
       if (!real && !(fabs(p[c]) < bw)) continue;
       double rho = o->w[k][0][c], u = o->w[k][1][c], v = o->w[k][2][c];
       double pr = o->w[k][3][c];
@@ -1097,6 +1145,8 @@ orc_ctx *orc_create(const orc_config *cfg) {
   o->p0 = plane(o);
   o->band = (unsigned char *)calloc((size_t)o->NP, 1);
   o->rext = (unsigned char *)calloc((size_t)o->NP, 1);
+  o->nostate[0] = (unsigned char *)calloc((size_t)o->NP, 1);
+  o->nostate[1] = (unsigned char *)calloc((size_t)o->NP, 1);
   return o;
 }
 
@@ -1134,6 +1184,8 @@ void orc_destroy(orc_ctx *o) {
   free(o->p0);
   free(o->band);
   free(o->rext);
+  free(o->nostate[0]);
+  free(o->nostate[1]);
   free(o);
 }
 
@@ -1618,7 +1670,7 @@ static void extend_T(orc_ctx *o, int k, double *const lw[4]) {
     for (int j = 0; j < o->c.ny; j++)
       for (int i = 0; i < o->c.nx; i++) {
         int c = ID(o, i, j);
-        if (!(fabs(p[c]) < bw) || vol(o, k, c) > ALPHA_REAL) continue;
+        if (!(fabs(p[c]) < bw) || is_real(o, k, c)) continue;
         double nxv, nyv;
         normal(o, p, i, j, &nxv, &nyv);
         if (k == 0) {
@@ -1654,7 +1706,7 @@ static void prim_T(orc_ctx *o, int k, const double *const W[4], double *const lw
       int c = ID(o, i, j);
       double a = vol(o, k, c);
       for (int m = 0; m < 4; m++) lq[m][c] = 0.0;
-      if (!(a > ALPHA_REAL)) continue;
+      if (!is_real(o, k, c)) continue;
       double rho = W[0][c], u = W[1][c], v = W[2][c];
       double lr = lw[0][c], lu = lw[1][c], lv = lw[2][c], lp = lw[3][c];
       double m0 = a * rho;
@@ -1726,6 +1778,11 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
   for (int a = 0; a < 9; a++)
     for (int x = 0; x < 8; x++) all[a][x] = plane(o);
   double *phin = plane(o);
+  unsigned char *ns1[2], *ns2[2];
+  for (int k = 0; k < 2; k++) {
+    ns1[k] = (unsigned char *)malloc((size_t)o->NP);
+    ns2[k] = (unsigned char *)malloc((size_t)o->NP);
+  }
   double t0 = o->t;
   for (int k = 0; k < 2; k++) copy_planes(o, Qn[k], o->q[k], 4);
   memcpy(phin, o->phi, sizeof(double) * o->NP);
@@ -1735,6 +1792,7 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
   eval_frozen(o, o->q, lf);
   for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
   for (int k = 0; k < 2; k++) copy_planes(o, W1[k], o->w[k], 4);
+  for (int k = 0; k < 2; k++) memcpy(ns1[k], o->nostate[k], (size_t)o->NP);
   for (int k = 0; k < 2; k++)
     for (int m = 0; m < 4; m++)
       rk_plane(o, 1, o->q[k][m], o->q0[k][m], o->q[k][m], o->L[k][m], dt, NULL);
@@ -1745,6 +1803,7 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
   eval_frozen(o, o->q, lf + 4);
   for (int k = 0; k < 2; k++) fv_rhs(o, k, o->L[k]);
   for (int k = 0; k < 2; k++) copy_planes(o, W2[k], o->w[k], 4);
+  for (int k = 0; k < 2; k++) memcpy(ns2[k], o->nostate[k], (size_t)o->NP);
 
   /* reverse */
   for (int k = 0; k < 2; k++)
@@ -1757,6 +1816,7 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
   /* Q** = Q^n / 2 + (Q1 + dt L(Q1)) / 2 */
   copy_in(o, phi1, o->phi);
   geometry(o, o->phi);
+  for (int k = 0; k < 2; k++) memcpy(o->nostate[k], ns2[k], (size_t)o->NP);
   for (int k = 0; k < 2; k++)
     for (int m = 0; m < 4; m++)
       for (int c = 0; c < o->NP; c++) mu[k][m][c] = 0.5 * dt * lam[k][m][c];
@@ -1770,6 +1830,7 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
   /* Q* = Q^n + dt L(Q^n) */
   memcpy(o->phi, phin, sizeof(double) * o->NP);
   geometry(o, o->phi);
+  for (int k = 0; k < 2; k++) memcpy(o->nostate[k], ns1[k], (size_t)o->NP);
   for (int k = 0; k < 2; k++)
     for (int m = 0; m < 4; m++)
       for (int c = 0; c < o->NP; c++) mu[k][m][c] = dt * ls[k][m][c];
@@ -1789,6 +1850,10 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
   for (int a = 0; a < 9; a++)
     for (int x = 0; x < 8; x++) free(all[a][x]);
   free(phin);
+  for (int k = 0; k < 2; k++) {
+    free(ns1[k]);
+    free(ns2[k]);
+  }
   return o->err;
 }
 

@@ -13,7 +13,9 @@
 //   ghost^T            (ghost adjoints back to the cells they copy)
 //   interface^T        (implicit-function theorem on the Riemann equation)
 //   extension^T        (the Jacobi sweeps transposed, band-indexed)
-//   primitive^T        (at real cells), combined with the RK coefficients.
+//   primitive^T        (at real cells: above the sliver threshold and, for
+//                       cut cells, holding a physical state), combined
+//                       with the RK coefficients.
 // Nothing here takes a branch that depends on rounding: every decision
 // (real cells, targets, Riemann wave types at the converged state) is the
 // forward's, so FMA contraction is allowed.
@@ -423,8 +425,10 @@ __global__ void k_adj_ext_store(Planes8 lw, const int *__restrict__ band, const 
 // 6. primitive^T at real cells, combined: out = ca A + cb B + lq
 // (A, B may be null; out may alias either)
 
-__global__ void k_adj_prim(Grid g, Planes8 W, const double *__restrict__ alpha, Planes8 lw,
-                           Planes8 out, Planes8 A, double ca, Planes8 B, double cb) {
+__global__ void k_adj_prim(Grid g, Planes8 W, const double *__restrict__ alpha,
+                           const unsigned char *__restrict__ ns0,
+                           const unsigned char *__restrict__ ns1, Planes8 lw, Planes8 out,
+                           Planes8 A, double ca, Planes8 B, double cb) {
   SIF_TICK();
   const long long n = (long long)g.nx * g.ny;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
@@ -434,7 +438,7 @@ __global__ void k_adj_prim(Grid g, Planes8 W, const double *__restrict__ alpha, 
     for (int k = 0; k < 2; k++) {
       double a = vol_k(alpha, k, c);
       double lq[4] = {0.0, 0.0, 0.0, 0.0};
-      if (a > SIF_ALPHA_REAL) {
+      if (a > SIF_ALPHA_REAL && !(k == 0 ? ns0 : ns1)[c]) {
         double gm1 = g.gamma[k] - 1.0;
         double rho = W.p[k * 4][c], u = W.p[k * 4 + 1][c], v = W.p[k * 4 + 2][c];
         double lr = lw.p[k * 4][c], lu = lw.p[k * 4 + 1][c], lv = lw.p[k * 4 + 2][c],
@@ -540,10 +544,12 @@ void launch_adj_extension(const Grid &g, double *const lw[2][4], const ExtPlan *
 }
 
 void launch_adj_prim(const Grid &g, double *const W[2][4], const double *alpha,
-                     double *const lw[2][4], double *const out[2][4], double *const A[2][4],
-                     double ca, double *const B[2][4], double cb, cudaStream_t st) {
+                     const unsigned char *const nostate[2], double *const lw[2][4],
+                     double *const out[2][4], double *const A[2][4], double ca,
+                     double *const B[2][4], double cb, cudaStream_t st) {
   long long n = (long long)g.nx * g.ny;
-  k_adj_prim<<<blocks_for(n), 256, 0, st>>>(g, p8(W), alpha, p8(lw), p8(out), p8(A), ca, p8(B), cb);
+  k_adj_prim<<<blocks_for(n), 256, 0, st>>>(g, p8(W), alpha, nostate[0], nostate[1], p8(lw),
+                                            p8(out), p8(A), ca, p8(B), cb);
   sif_note_launches(1);
 }
 

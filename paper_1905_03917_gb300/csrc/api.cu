@@ -30,6 +30,7 @@ struct sif_ctx {
   double *partial;   // integrals: 8*ny partial sums + pointer table
   double *integ;     // 8 totals
   int *band_ev, *band_ls, *rext_ls, *cut, *tiles[2];
+  unsigned char *nostate[2];  // per fluid: cut cells holding no physical state
   Scalars *sc;       // device
   Scalars *hsc;      // pinned host mirror
   double *hbuf;      // pinned 8 doubles
@@ -65,10 +66,11 @@ struct sif_ctx {
 };
 
 // per recorded step: q (8), the stencil states the step starts from (8),
-// phi^n, phi after stage 1, phi^{n+1}, and the stencil states (ghosts
-// filled) that stage 1 and stage 2 used (8 + 8)
-static const int kTapePlanes = 35;
-static const int kTapeW1 = 19, kTapeW2 = 27;
+// phi^n, phi after stage 1, phi^{n+1}, the stencil states (ghosts filled)
+// that stage 1 and stage 2 used (8 + 8), and one plane holding, as bytes,
+// the cut cells without a physical state of both stages and fluids
+static const int kTapePlanes = 36;
+static const int kTapeW1 = 19, kTapeW2 = 27, kTapeFlags = 35;
 
 // launch counting happens on the device (SIF_TICK); the host-side notes
 // the wrappers make are not used for measurement
@@ -241,6 +243,8 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     c->cut = (int *)take(sizeof(int) * ncell);
     c->tiles[0] = (int *)take(sizeof(int) * ntiles);
     c->tiles[1] = (int *)take(sizeof(int) * ntiles);
+    c->nostate[0] = (unsigned char *)take(c->NP);
+    c->nostate[1] = (unsigned char *)take(c->NP);
     c->sc = (Scalars *)take(sizeof(Scalars));
   };
   carve();
@@ -363,12 +367,13 @@ static void mix_one(sif_ctx *c, int k, double *const q[4]) {
 static void eval(sif_ctx *c, double *const qs[2][4]) {
   launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
   launch_prim2(c->g, qs[0], qs[1], c->w[0], c->w[1], c->alpha, c->tiles[0], c->tiles[1],
-               ntile(c), c->sc, c->st);
+               ntile(c), c->nostate, c->sc, c->st);
   dbg(c, "prim");
   launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
-                   c->ext_plan, ncell(c), band_work(c), c->st);
+                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st);
   launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
-                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->sc, c->st);
+                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
+                    c->sc, c->st);
   dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
@@ -376,7 +381,8 @@ static void eval(sif_ctx *c, double *const qs[2][4]) {
                    c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
   dbg(c, "interface");
   launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
-                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->sc, c->st);
+                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
+                    c->sc, c->st);
   dbg(c, "ls_extend");
 }
 
@@ -416,7 +422,8 @@ static void reinit(sif_ctx *c) {
 struct TapeHook {
   double *phi1;
   double *lf2;
-  double *W[2][2][4];  // stage, fluid, component
+  double *W[2][2][4];          // stage, fluid, component
+  unsigned char *flags2[2];    // stage 2, fluid
 };
 
 // one RK step of both fluids and the level set, the first interaction
@@ -427,8 +434,11 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
   ls_begin(c);
   for (int s = 1; s <= S; s++) {
     if (s > 1) eval(c, c->q);
-    if (rec && s == 2)
+    if (rec && s == 2) {
       cudaMemcpyAsync(rec->lf2, c->sc->lf, sizeof(c->sc->lf), cudaMemcpyDeviceToDevice, c->st);
+      for (int k = 0; k < 2; k++)
+        cudaMemcpyAsync(rec->flags2[k], c->nostate[k], c->NP, cudaMemcpyDeviceToDevice, c->st);
+    }
     for (int k = 0; k < 2; k++) fv(c, k, s, c->q[k], c->q0[k], c->q[k], dtp);
     if (rec && s <= 2)
       for (int k = 0; k < 2; k++)
@@ -557,6 +567,9 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
   for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
   // step 2: fluid-1 first RK stage with dt1; previous and future states
   copy_planes(c, c->prev, c->q[f1], 4);
+  // the stage writes fluid 1's tiles only; elsewhere the future state is
+  // the state itself (no open face, no exchange)
+  copy_planes(c, c->fut, c->q[f1], 4);
   fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
   double *qs[2][4];
   int sub = 0;
@@ -767,6 +780,9 @@ static void graph_cycle_body(sif_ctx *c, int f1) {
   for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
   // step 2: fluid-1 first RK stage with dt1; previous and future states
   copy4(c, c->prev, c->q[f1]);
+  // the stage writes fluid 1's tiles only; elsewhere the future state is
+  // the state itself (no open face, no exchange)
+  copy4(c, c->fut, c->q[f1]);
   fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
   cudaGraphConditionalHandle hloop = new_handle(c);
   launch_cond(COND_LOOP, c->sc, hloop, 0, 0, kMaxSubsteps, c->st);  // last = 0 here
@@ -1112,6 +1128,9 @@ static double *tape_plane(sif_ctx *c, int step, int i) {
   return c->tape_planes + ((size_t)step * kTapePlanes + i) * c->NP;
 }
 static double *tape_scal(sif_ctx *c, int step) { return c->tape_scal + (size_t)step * 16; }
+static unsigned char *tape_flags(sif_ctx *c, int step, int stage, int k) {
+  return (unsigned char *)tape_plane(c, step, kTapeFlags) + (size_t)(stage * 2 + k) * c->NP;
+}
 
 static void d2d(sif_ctx *c, void *dst, const void *src, size_t bytes) {
   cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->st);
@@ -1130,9 +1149,11 @@ static void taped_step(sif_ctx *c) {
   launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
   d2d(c, tape_scal(c, s), &c->sc->dt, sizeof(double));
   d2d(c, tape_scal(c, s) + 1, c->sc->lf, sizeof(c->sc->lf));
+  for (int k = 0; k < 2; k++) d2d(c, tape_flags(c, s, 0, k), c->nostate[k], c->NP);
   TapeHook hook;
   hook.phi1 = tape_plane(c, s, 17);
   hook.lf2 = tape_scal(c, s) + 5;
+  for (int k = 0; k < 2; k++) hook.flags2[k] = tape_flags(c, s, 1, k);
   for (int st = 0; st < 2; st++)
     for (int k = 0; k < 2; k++)
       for (int m = 0; m < 4; m++)
@@ -1228,16 +1249,17 @@ static void frozen_forward(sif_ctx *c, int step) {
 // transposed right-hand side of the stage with stencil states W and LF
 // speeds lf, applied to mu scaled by fac * dt, then primitive^T combined:
 // out = ca A + cb B + J^T (fac dt mu).  The stage's geometry is in place.
-static void adj_stage(sif_ctx *c, double *const W[2][4], const double *lf, const double *dtp,
-                      double fac, double *const mu[2][4], double *const out[2][4],
-                      double *const A[2][4], double ca, double *const B[2][4], double cb) {
+static void adj_stage(sif_ctx *c, double *const W[2][4], const unsigned char *const flags[2],
+                      const double *lf, const double *dtp, double fac, double *const mu[2][4],
+                      double *const out[2][4], double *const A[2][4], double ca,
+                      double *const B[2][4], double cb) {
   launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
-                   c->ext_plan, ncell(c), band_work(c), c->st);
+                   c->ext_plan, ncell(c), band_work(c), flags, c->st);
   launch_adj_rhs(c->g, W, (const unsigned long long *)lf, dtp, fac, mu, c->ax, c->ay, c->phi,
                  c->sx, c->sy, c->cut, &c->sc->n_cut, ncell(c), c->G, c->lw, c->st);
   launch_adj_extension(c->g, c->lw, c->ext_plan, ncell(c), band_work(c), c->band_ev,
                        &c->sc->n_band, c->bandmap, c->tmp, c->st);
-  launch_adj_prim(c->g, W, c->alpha, c->lw, out, A, ca, B, cb, c->st);
+  launch_adj_prim(c->g, W, c->alpha, flags, c->lw, out, A, ca, B, cb, c->st);
   dbg(c, "adjoint stage");
 }
 
@@ -1251,22 +1273,26 @@ static void adj_mix(sif_ctx *c, double *const lam[2][4]) {
 static void adjoint_step_impl(sif_ctx *c, int step) {
   double *sc = tape_scal(c, step);
   double *W1[2][4], *W2[2][4];
-  for (int k = 0; k < 2; k++)
+  const unsigned char *F1[2], *F2[2];
+  for (int k = 0; k < 2; k++) {
     for (int m = 0; m < 4; m++) {
       W1[k][m] = tape_plane(c, step, kTapeW1 + k * 4 + m);
       W2[k][m] = tape_plane(c, step, kTapeW2 + k * 4 + m);
     }
+    F1[k] = tape_flags(c, step, 0, k);
+    F2[k] = tape_flags(c, step, 1, k);
+  }
   // Q^{n+1} = mix(Q**) with the geometry of phi^{n+1}
   set_phi(c, tape_plane(c, step, 18));
   adj_mix(c, c->lamA);
   // Q** = Q^n / 2 + (Q1 + dt L(Q1)) / 2, stage-2 geometry
   set_phi(c, tape_plane(c, step, 17));
-  adj_stage(c, W2, sc + 5, sc, 0.5, c->lamA, c->lamB, c->lamA, 0.5, nullptr, 0.0);
+  adj_stage(c, W2, F2, sc + 5, sc, 0.5, c->lamA, c->lamB, c->lamA, 0.5, nullptr, 0.0);
   // Q1 = mix(Q*) with the same geometry
   adj_mix(c, c->lamB);
   // Q* = Q^n + dt L(Q^n), stage-1 geometry
   set_phi(c, tape_plane(c, step, 16));
-  adj_stage(c, W1, sc + 1, sc, 1.0, c->lamB, c->lamC, c->lamA, 0.5, c->lamB, 1.0);
+  adj_stage(c, W1, F1, sc + 1, sc, 1.0, c->lamB, c->lamC, c->lamA, 0.5, c->lamB, 1.0);
 }
 
 static int put_state8(sif_ctx *c, double *const dst[2][4], const double *src, int mem) {

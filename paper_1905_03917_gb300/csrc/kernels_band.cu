@@ -48,6 +48,7 @@ struct PrimArgs {
   const double *q[2][4];
   double *w[2][4];
   const int *tiles[2];
+  unsigned char *nostate[2];
 };
 
 // blockIdx.y = fluid
@@ -65,6 +66,7 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
   if (i < g.nx && j < g.ny) {
     int c = gidx(g, i, j);
     double a = vol_k(alpha, k, c);
+    unsigned char nostate = 0;
     if (a > SIF_ALPHA_REAL) {
       double gm = g.gamma[k], pi = g.pinf[k];
       // a full cell divides by exactly 1: skip those two divisions
@@ -73,18 +75,27 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
       double v = q2[c] / q0[c];
       double E = a == 1.0 ? q3[c] : q3[c] / a;
       double p = (gm - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - gm * pi;
-      if (!(rho > 0.0) || !(p + pi > 0.0)) atomicOr(&sc->err, DERR_NONPHYS);
-      w0[c] = rho;
-      w1[c] = u;
-      w2[c] = v;
-      w3[c] = p;
-      double cs = sqrt(fmax(gm * (p + pi) / rho, 0.0));
-      lx = fabs(u) + cs;
-      ly = fabs(v) + cs;
-      double s = (fabs(u) + cs) / g.dx;
-      if (g.dim == 2) s += (fabs(v) + cs) / g.dy;
-      sm = s;
+      bool phys = rho > 0.0 && p + pi > 0.0;
+      // a cut cell whose content is not a physical state takes an
+      // extended state like a sliver; a full cell with such content is an
+      // error
+      if (!phys && a < 1.0) {
+        nostate = 1;
+      } else {
+        if (!phys) atomicOr(&sc->err, DERR_NONPHYS);
+        w0[c] = rho;
+        w1[c] = u;
+        w2[c] = v;
+        w3[c] = p;
+        double cs = sqrt(fmax(gm * (p + pi) / rho, 0.0));
+        lx = fabs(u) + cs;
+        ly = fabs(v) + cs;
+        double s = (fabs(u) + cs) / g.dx;
+        if (g.dim == 2) s += (fabs(v) + cs) / g.dy;
+        sm = s;
+      }
     }
+    P.nostate[k][c] = nostate;
   }
   // two reductions share the helper: (lx, ly), then (sm, -)
   block_max2(lx, ly, &sc->lf[k][0], &sc->lf[k][1]);
@@ -93,8 +104,11 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
 
 void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], double *const wN[4],
                   double *const wP[4], const double *alpha, const int *tilesN,
-                  const int *tilesP, int tile_cap, Scalars *sc, cudaStream_t st) {
+                  const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
+                  cudaStream_t st) {
   PrimArgs P;
+  P.nostate[0] = nostate[0];
+  P.nostate[1] = nostate[1];
   for (int m = 0; m < 4; m++) {
     P.q[0][m] = qN[m];
     P.q[1][m] = qP[m];

@@ -63,7 +63,8 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
                             const double *__restrict__ phi, const double *__restrict__ sx,
                             const double *__restrict__ sy, const int *__restrict__ band,
                             const int *nband, const int *__restrict__ map, ExtPlan *plan,
-                            int cap) {
+                            int cap, const unsigned char *__restrict__ ns0,
+                            const unsigned char *__restrict__ ns1) {
   SIF_TICK();
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
@@ -76,7 +77,7 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
       bool target;
       double dx_, dy_;
       if (f < 2) {
-        target = !(vol_k(alpha, f, c) > SIF_ALPHA_REAL);
+        target = !(vol_k(alpha, f, c) > SIF_ALPHA_REAL) || (f == 0 ? ns0 : ns1)[c];
         // toward fluid f: its normal points into it
         dx_ = f == 0 ? -nxv : nxv;
         dy_ = f == 0 ? -nyv : nyv;
@@ -113,9 +114,10 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
 
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
                       const double *sy, const int *band, const int *nband, const int *map,
-                      ExtPlan *plan, int cap, int work, cudaStream_t st) {
+                      ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
+                      cudaStream_t st) {
   k_ext_setup<<<blocks_for(work, 128), 128, 0, st>>>(g, alpha, phi, sx, sy, band, nband, map,
-                                                    plan, cap);
+                                                    plan, cap, nostate[0], nostate[1]);
   sif_note_launches(1);
 }
 
@@ -160,7 +162,9 @@ __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ pla
 // cells' wave speeds into the Lax-Friedrichs maxima
 __global__ void k_ext_scatter(Grid g, ExtFields F, int f0, int cap, const int *__restrict__ band,
                               const int *nband, const double *buf,
-                              const double *__restrict__ alpha, Scalars *sc) {
+                              const double *__restrict__ alpha,
+                              const unsigned char *__restrict__ ns0,
+                              const unsigned char *__restrict__ ns1, Scalars *sc) {
   SIF_TICK();
   int n = *nband;
   int f = f0 + blockIdx.y;
@@ -170,7 +174,7 @@ __global__ void k_ext_scatter(Grid g, ExtFields F, int f0, int cap, const int *_
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
     for (int m = 0; m < nc; m++) F.p[f][m][c] = in[(size_t)m * cap + idx];
-    if (f < 2 && !(vol_k(alpha, f, c) > SIF_ALPHA_REAL)) {
+    if (f < 2 && (!(vol_k(alpha, f, c) > SIF_ALPHA_REAL) || (f == 0 ? ns0 : ns1)[c])) {
       double r = in[idx], u = in[(size_t)cap + idx], v = in[(size_t)2 * cap + idx],
              p = in[(size_t)3 * cap + idx];
       double cs = sqrt(fmax(g.gamma[f] * (p + g.pinf[f]) / r, 0.0));
@@ -205,7 +209,7 @@ __global__ void k_ext_scatter(Grid g, ExtFields F, int f0, int cap, const int *_
 void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
                        const int *band, const int *nband, double *tmp, const double *alpha,
-                       Scalars *sc, cudaStream_t st) {
+                       const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st) {
   ExtFields F;
   for (int m = 0; m < 4; m++) {
     F.p[0][m] = wN[m];
@@ -223,7 +227,8 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
     src = buf[cur];
     cur ^= 1;
   }
-  k_ext_scatter<<<grid, 128, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, sc);
+  k_ext_scatter<<<grid, 128, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
+                                      nostate[1], sc);
   sif_note_launches(g.ext_iters + 1);
 }
 
@@ -252,18 +257,46 @@ __device__ bool mix_source_plan(const Grid &g, int k, int i, int j, const double
   int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
   double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
   int nt = g.dim == 2 ? 3 : 1;
+  // targets: the normal-direction neighbours that are not small cells;
+  // else the largest of the eight neighbours if it is not small; else the
+  // normal-direction neighbours larger than the source
   bool keep[3] = {false, false, false};
   double sum = 0.0;
-  for (int pass = 0; pass < 2 && !(sum > 0.0); pass++)
+  for (int t = 0; t < nt; t++) {
+    if (!inside(g, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
+    if (!(vol_k(alpha, k, gidx(g, ti[t], tj[t])) >= g.mix_alpha)) continue;
+    keep[t] = true;
+    sum += wt[t];
+  }
+  s.as = as;
+  if (!(sum > 0.0)) {
+    int best = -1;
+    double ab = 0.0;
+    for (int dj = -1; dj <= 1; dj++)
+      for (int di = -1; di <= 1; di++) {
+        if ((di == 0 && dj == 0) || (g.dim == 1 && dj != 0) || !inside(g, i + di, j + dj))
+          continue;
+        double at = vol_k(alpha, k, gidx(g, i + di, j + dj));
+        if (at > ab) {
+          ab = at;
+          best = gidx(g, i + di, j + dj);
+        }
+      }
+    if (best >= 0 && ab >= g.mix_alpha) {
+      s.tc[0] = best;
+      s.beta[0] = 1.0;
+      s.at[0] = ab;
+      s.nt = 1;
+      return true;
+    }
     for (int t = 0; t < nt; t++) {
       if (!inside(g, ti[t], tj[t]) || !(wt[t] > 0.0)) continue;
-      double at = vol_k(alpha, k, gidx(g, ti[t], tj[t]));
-      if (pass == 0 ? !(at >= g.mix_alpha) : !(at > as)) continue;
+      if (!(vol_k(alpha, k, gidx(g, ti[t], tj[t])) > as)) continue;
       keep[t] = true;
       sum += wt[t];
     }
+  }
   if (!(sum > 0.0)) return false;
-  s.as = as;
   for (int t = 0; t < nt; t++) {
     if (!keep[t]) continue;
     int tc = gidx(g, ti[t], tj[t]);

@@ -318,18 +318,22 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
                  const double *alpha, const double *phi, const int *band, const int *map,
                  const int *nband, MixPlan *plan, int cap, int work, double *tmp,
                  cudaStream_t st);
+// nostate[k]: 1 where a cut cell of fluid k holds no physical state (set by
+// the primitive recovery of the same interaction step)
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
                       const double *sy, const int *band, const int *nband, const int *map,
-                      ExtPlan *plan, int cap, int work, cudaStream_t st);
+                      ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
+                      cudaStream_t st);
 // f0 = 0, nf = 2: stencil states of both fluids; f0 = 2, nf = 1: level-set velocity
 void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
                        const int *band, const int *nband, double *tmp, const double *alpha,
-                       Scalars *sc, cudaStream_t st);
+                       const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st);
 
 void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], double *const wN[4],
                   double *const wP[4], const double *alpha, const int *tilesN,
-                  const int *tilesP, int tile_cap, Scalars *sc, cudaStream_t st);
+                  const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
+                  cudaStream_t st);
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
                       double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
@@ -373,8 +377,9 @@ void launch_adj_extension(const Grid &g, double *const lw[2][4], const ExtPlan *
                           int work, const int *band, const int *nband, const int *map,
                           double *tmp, cudaStream_t st);
 void launch_adj_prim(const Grid &g, double *const W[2][4], const double *alpha,
-                     double *const lw[2][4], double *const out[2][4], double *const A[2][4],
-                     double ca, double *const B[2][4], double cb, cudaStream_t st);
+                     const unsigned char *const nostate[2], double *const lw[2][4],
+                     double *const out[2][4], double *const A[2][4], double ca,
+                     double *const B[2][4], double cb, cudaStream_t st);
 void launch_adj_init(const Grid &g, double *const prim[2][4], const double *alpha,
                      double *const lam[2][4], double *const out[2][4], cudaStream_t st);
 void launch_mix_adjoint(const Grid &g, double *const lN[4], double *const lP[4],
