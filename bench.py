@@ -300,7 +300,7 @@ def run_ours(args):
     arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
     s = sif.Solver(case["cfg"], device=local).init_fluids(*arrs)
     from paper_1905_03917_gb300 import autotune
-    shape, _ = autotune.tune(s, device=local, cycles=1)
+    shape, tune_rec = autotune.tune(s, device=local, cycles=1)
     step = s.step_multi_dt if args.mode == "multi" else s.step_single_dt
     for _ in range(args.warmup):
         step(1)
@@ -374,7 +374,8 @@ def run_ours(args):
         "config": {"workload": case["name"], "mode": args.mode, "nx": case["cfg"]["nx"],
                    "ny": case["cfg"]["ny"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}", "mean_substeps": float(np.mean(substeps)),
-                   "tile_shape": list(shape)},
+                   "tile_shape": list(shape),
+                   "autotune_ns_per_update": tune_rec.get("ns_per_update")},
         "roofline": {"kernel": "k_fv_stage", "bound": "alu", "achieved": achieved_tf,
                      "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / NOMINAL_FP64_TFLOPS if achieved_tf else None,

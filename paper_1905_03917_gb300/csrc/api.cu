@@ -48,6 +48,7 @@ struct sif_ctx {
   int cap_depth, capturing, gerr;
   int use_graphs;
   int graph_bucket;  // band grid size baked into the graphs
+  int num_sms;
   cudaGraphExec_t g_cycle, g_single;
   cudaGraph_t g_cycle_tmpl;  // kept for embedding in batch graphs
   int graph_gen;             // bumped whenever the graphs are rebuilt
@@ -167,6 +168,12 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   }
   for (int i = 0; i < 4; i++) cudaStreamCreateWithFlags(&c->cap[i], cudaStreamNonBlocking);
   fv_prepare();
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->num_sms = sms > 0 ? sms : 1;
+  }
   {
     const char *ng = getenv("SIF_NO_GRAPH");
     c->use_graphs = !(ng && ng[0] == '1');
@@ -395,7 +402,8 @@ static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const bas
                double *const cur[4], const double *dtp) {
   ghost_w(c, k);
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
-                  c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), dtp, c->sc, c->st);
+                  c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), dtp, c->sc,
+                  c->st);
   dbg(c, "fv_stage");
 }
 
@@ -957,12 +965,11 @@ extern "C" int sif_init_fluids(sif_ctx *c, const double *phi, const double *pN, 
   geometry(c);
   launch_init_state(c->g, c->q[0], c->q[1], c->w[0], c->w[1], c->alpha, c->st);
   mix_both(c);
-  int nb = 0;
-  CK(cudaMemcpyAsync(&nb, &c->sc->n_band, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   rc = check_launch(c, "init");
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->st));
-  c->band_work = nb;
+  c->band_work = c->hsc->n_band;
   c->inited = 1;
   return SIF_OK;
 }

@@ -167,8 +167,11 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
                       const double *sx, const double *sy, const int *cut, int cut_cap,
                       double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
                       Scalars *sc, cudaStream_t st) {
-  int blocks = grid_for(cut_cap, 128, 1216);
-  k_interface<<<blocks, 128, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
+  // one warp per block: the Newton solves are FP64-throughput bound, and
+  // a few hundred cut cells in 128-thread blocks would occupy a handful of
+  // SMs
+  int blocks = grid_for(cut_cap, 32, 4864);
+  k_interface<<<blocks, 32, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
                                       phi, sx, sy, cut, &sc->n_cut, xn0, xn1, xn2, ul0, ul1, sc);
   sif_note_launches(1);
 }
@@ -230,11 +233,11 @@ void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *ph
   static const double A2[3] = {0.0, 0.0, 0.5}, B2[3] = {0.0, 1.0, 0.5};
   static const double A3[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
   double a = rk == 3 ? A3[s] : A2[s], b = rk == 3 ? B3[s] : B2[s];
-  int blocks = grid_for(band_cap, 256, 1216);
+  int blocks = grid_for(band_cap, 64, 2432);
   GhostSet gs = {{phi}, {0}, 1};
   launch_fill_ghost(g, gs, st);
-  k_ls_stage<<<blocks, 256, 0, st>>>(g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
-  k_band_scatter2<<<blocks, 256, 0, st>>>(band, nband, tmp, phi, nullptr);
+  k_ls_stage<<<blocks, 64, 0, st>>>(g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
+  k_band_scatter2<<<blocks, 64, 0, st>>>(band, nband, tmp, phi, nullptr);
   sif_note_launches(2);
 }
 
@@ -328,11 +331,11 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
   GhostSet gs = {{phi}, {0}, 1};
   launch_fill_ghost(g, gs, st);
   cudaMemcpyAsync(phi0, phi, sizeof(double) * (size_t)g.PX * g.PY, cudaMemcpyDeviceToDevice, st);
-  int blocks = grid_for(rext_cap, 256, 1216);
+  int blocks = grid_for(rext_cap, 64, 2432);
   for (int it = 0; it < g.reinit_iters; it++) {
     if (it > 0) launch_fill_ghost(g, gs, st);
-    k_reinit<<<blocks, 256, 0, st>>>(g, phi, phi0, rext, nrext, tmp);
-    k_band_scatter2<<<blocks, 256, 0, st>>>(rext, nrext, tmp, phi, nullptr);
+    k_reinit<<<blocks, 64, 0, st>>>(g, phi, phi0, rext, nrext, tmp);
+    k_band_scatter2<<<blocks, 64, 0, st>>>(rext, nrext, tmp, phi, nullptr);
   }
   sif_note_launches(2 * g.reinit_iters);
 }

@@ -9,7 +9,7 @@
 // face flux is reconstructed once per CTA, and the update is written in
 // place (a cell reads only its own conserved values).  Only the tiles in
 // which the fluid can have an open face are launched.  FP64 throughout;
-// the reconstruction uses one division per face and component.
+// the two reconstructions of a face and component share one division.
 #include "sif_internal.cuh"
 
 struct FvArgs {
@@ -28,8 +28,10 @@ struct FvArgs {
   const Scalars *sc;
 };
 
-__device__ __forceinline__ double weno5_fast(double v1, double v2, double v3, double v4, double v5,
-                                             double eps) {
+// WENO5-JS reconstruction as a fraction num / den (the face flux adds two
+// of them over one division)
+__device__ __forceinline__ void weno5_frac(double v1, double v2, double v3, double v4, double v5,
+                                          double eps, double &num, double &den) {
   const double c13_12 = 13.0 / 12.0, s6 = 1.0 / 6.0;
   double d0 = (v1 + v3) - 2.0 * v2;
   double e0 = (v1 + 3.0 * v3) - 4.0 * v2;
@@ -47,9 +49,18 @@ __device__ __forceinline__ double weno5_fast(double v1, double v2, double v3, do
   t0 *= t0;
   t1 *= t1;
   t2 *= t2;
-  // weights d_r / t_r normalised with a single division
+  // weights d_r / t_r scaled by t0 t1 t2: numerator and denominator
   double w0 = 0.1 * (t1 * t2), w1 = 0.6 * (t0 * t2), w2 = 0.3 * (t0 * t1);
-  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+  num = w0 * q0 + w1 * q1 + w2 * q2;
+  den = w0 + w1 + w2;
+}
+
+// A (num_l / den_l + num_r / den_r) with one division; two if the
+// cross products leave the double range
+__device__ __forceinline__ double face_value(double A, double nl, double dl, double nr, double dr) {
+  double v = A * (nl * dr + nr * dl) / (dl * dr);
+  if (!isfinite(v)) v = A * (nl / dl + nr / dr);
+  return v;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -58,14 +69,16 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// end-of-block bookkeeping of the launch timer: the last block of the
-// launch adds the launch span and re-arms the timer for the next launch
-__device__ void fv_timer_block_done(const Scalars *csc, bool worked) {
+// end-of-block bookkeeping of the launch timer, by the blocks that had a
+// tile (nwork of them): the last one adds the launch span and re-arms the
+// timer for the next launch.  Blocks without a tile return at once and
+// touch nothing.
+__device__ void fv_timer_block_done(const Scalars *csc, unsigned int nwork) {
   Scalars *sc = (Scalars *)csc;
-  if (worked) atomicMax((unsigned long long *)&sc->fv_t1, globaltimer_ns());
+  atomicMax((unsigned long long *)&sc->fv_t1, globaltimer_ns());
   __threadfence();
   unsigned int done = atomicAdd(&sc->fv_blocks_done, 1u);
-  if (done == gridDim.x - 1) {
+  if (done == nwork - 1) {
     __threadfence();
     unsigned long long t0 = atomicAdd((unsigned long long *)&sc->fv_t0, 0ull);
     unsigned long long t1 = atomicAdd((unsigned long long *)&sc->fv_t1, 0ull);
@@ -82,20 +95,21 @@ struct FvShape {
   static constexpr int HX = TX + 6, HY = TY + 6;
   static constexpr size_t smem() {
     return sizeof(double) *
-           (size_t)(8 * HX * TY + 8 * TX * HY + 4 * (TX + 1) * TY + 4 * TX * (TY + 1));
+           (size_t)4 * (2 * HX * TY + 2 * TX * HY + (TX + 1) * TY + TX * (TY + 1));
   }
+  // two threads per output cell: a CTA's phases finish in half the time,
+  // which matters when a fluid has few tiles (the sub-cycled fluid)
+  static constexpr int threads = 2 * TX * TY;
 };
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_fv_stage(FvArgs A) {
+__global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A) {
   SIF_TICK();
   constexpr int HX = TX + 6, HY = TY + 6;
   const Grid &g = A.g;
   const int k = A.k;
-  if ((int)blockIdx.x >= A.ntiles[k]) {
-    if (A.sc->timing && threadIdx.x == 0) fv_timer_block_done(A.sc, false);
-    return;
-  }
+  const int ntiles = A.ntiles[k];
+  if ((int)blockIdx.x >= ntiles) return;
   extern __shared__ double smem[];
   // split fluxes: x for rows of the tile with x-halo, y for columns with y-halo
   double *fxp = smem;                   // [4][HX*TY]
@@ -182,9 +196,10 @@ __global__ void __launch_bounds__(TX *TY) k_fv_stage(FvArgs A) {
         // cells i-3..i+2 are at halo columns fi..fi+5
         const double *P = fxp + m * HX * TY + fj * HX + fi;
         const double *M = fxm + m * HX * TY + fj * HX + fi;
-        double fl = weno5_fast(P[0], P[1], P[2], P[3], P[4], eps);
-        double fr = weno5_fast(M[5], M[4], M[3], M[2], M[1], eps);
-        val = A_ * (fl + fr);
+        double nl, dl, nr, dr;
+        weno5_frac(P[0], P[1], P[2], P[3], P[4], eps, nl, dl);
+        weno5_frac(M[5], M[4], M[3], M[2], M[1], eps, nr, dr);
+        val = face_value(A_, nl, dl, nr, dr);
       }
     }
     Fx[m * (TX + 1) * TY + f] = val;
@@ -201,9 +216,10 @@ __global__ void __launch_bounds__(TX *TY) k_fv_stage(FvArgs A) {
         if (A_ != 0.0) {
           const double *P = fyp + m * TX * HY + fj * TX + fi;
           const double *M = fym + m * TX * HY + fj * TX + fi;
-          double fl = weno5_fast(P[0], P[TX], P[2 * TX], P[3 * TX], P[4 * TX], eps);
-          double fr = weno5_fast(M[5 * TX], M[4 * TX], M[3 * TX], M[2 * TX], M[TX], eps);
-          val = A_ * (fl + fr);
+          double nl, dl, nr, dr;
+          weno5_frac(P[0], P[TX], P[2 * TX], P[3 * TX], P[4 * TX], eps, nl, dl);
+          weno5_frac(M[5 * TX], M[4 * TX], M[3 * TX], M[2 * TX], M[TX], eps, nr, dr);
+          val = face_value(A_, nl, dl, nr, dr);
         }
       }
       Fy[m * TX * (TY + 1) + f] = val;
@@ -237,7 +253,7 @@ __global__ void __launch_bounds__(TX *TY) k_fv_stage(FvArgs A) {
   }
   if (timed) {
     __syncthreads();
-    if (threadIdx.x == 0) fv_timer_block_done(A.sc, true);
+    if (threadIdx.x == 0) fv_timer_block_done(A.sc, (unsigned int)ntiles);
   }
 }
 
@@ -292,10 +308,10 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   A.ntiles = sc->n_tiles;
   A.dtp = dtp;
   A.sc = sc;
-#define FV_LAUNCH(a, b)                                                     \
-  if (g.tx == a && g.ty == b) {                                            \
-    k_fv_stage<a, b><<<tile_cap, a * b, FvShape<a, b>::smem(), st>>>(A);   \
-    return;                                                                \
+#define FV_LAUNCH(a, b)                                                                 \
+  if (g.tx == a && g.ty == b) {                                                        \
+    k_fv_stage<a, b><<<tile_cap, FvShape<a, b>::threads, FvShape<a, b>::smem(), st>>>(A); \
+    return;                                                                            \
   }
   FV_SHAPES(FV_LAUNCH)
 #undef FV_LAUNCH

@@ -116,7 +116,7 @@ void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, con
                       const double *sy, const int *band, const int *nband, const int *map,
                       ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
                       cudaStream_t st) {
-  k_ext_setup<<<blocks_for(work, 128), 128, 0, st>>>(g, alpha, phi, sx, sy, band, nband, map,
+  k_ext_setup<<<blocks_for(work, 64), 64, 0, st>>>(g, alpha, phi, sx, sy, band, nband, map,
                                                     plan, cap, nostate[0], nostate[1]);
   sif_note_launches(1);
 }
@@ -218,16 +218,16 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
   }
   F.ncomp[0] = F.ncomp[1] = 4;
   F.ncomp[2] = 2;
-  dim3 grid(blocks_for(work, 128), nf);
+  dim3 grid(blocks_for(work, 64), nf);
   double *buf[2] = {tmp, tmp + (size_t)8 * cap};
   const double *src = nullptr;
   int cur = 0;
   for (int it = 0; it < g.ext_iters; it++) {
-    k_ext_sweep<<<grid, 128, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur]);
+    k_ext_sweep<<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur]);
     src = buf[cur];
     cur ^= 1;
   }
-  k_ext_scatter<<<grid, 128, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
+  k_ext_scatter<<<grid, 64, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
                                       nostate[1], sc);
   sif_note_launches(g.ext_iters + 1);
 }
@@ -390,10 +390,11 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
     Q.q[0][m] = qN ? qN[m] : nullptr;
     Q.q[1][m] = qP ? qP[m] : nullptr;
   }
-  int b = blocks_for(work, 128);
-  k_mix_setup<<<b, 128, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
-  k_mix_apply<<<dim3(b, 2), 128, 0, st>>>(g, mask, Q, map, plan, cap, band, nband, tmp);
-  k_mix_scatter<<<dim3(b, 2), 128, 0, st>>>(mask, Q, band, nband, tmp);
+  // small blocks spread the band's few thousand cells over the SMs
+  int b = blocks_for(work, 64);
+  k_mix_setup<<<b, 64, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
+  k_mix_apply<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, map, plan, cap, band, nband, tmp);
+  k_mix_scatter<<<dim3(b, 2), 64, 0, st>>>(mask, Q, band, nband, tmp);
   sif_note_launches(3);
 }
 
