@@ -300,7 +300,11 @@ def run_ours(args):
     arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
     s = sif.Solver(case["cfg"], device=local).init_fluids(*arrs)
     from paper_1905_03917_gb300 import autotune
-    shape, tune_rec = autotune.tune(s, device=local, cycles=1)
+    if args.tile:
+        shape, tune_rec = tuple(int(x) for x in args.tile.split("x")), {}
+        s.set_tile_shape(*shape)
+    else:
+        shape, tune_rec = autotune.tune(s, device=local, cycles=2)
     step = s.step_multi_dt if args.mode == "multi" else s.step_single_dt
     for _ in range(args.warmup):
         step(1)
@@ -460,6 +464,8 @@ def main():
     ap.add_argument("--mode", default="multi", choices=["multi", "single"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default="",
+                    help="finite-volume tile shape TXxTY instead of the autotuner's choice")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-vs-single and adjoint measurements")
     args = ap.parse_args()

@@ -288,7 +288,7 @@ __device__ inline void side_partials(double p, double rho, double pk, double g, 
     fk = -qr - 0.5 * (p - pk) * qr / (Pp + B) * (g - 1.0) / (g + 1.0);
   } else {
     double r = Pp / P;
-    double re = pow(r, (g - 1.0) / (2.0 * g));
+    double re = pos_pow(r, (g - 1.0) / (2.0 * g));
     f = 2.0 * ck / (g - 1.0) * (re - 1.0);
     fp = re / (r * rho * ck);
     fk = f / (2.0 * P) - ck * re / (g * P);

@@ -69,10 +69,12 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
     unsigned char nostate = 0;
     if (a > SIF_ALPHA_REAL) {
       double gm = g.gamma[k], pi = g.pinf[k];
-      // a full cell divides by exactly 1: skip those two divisions
+      // one reciprocal of the mass serves u, v and 1/rho = alpha / (alpha
+      // rho); a full cell divides by exactly 1 and skips two more divisions
+      double iq = 1.0 / q0[c];
       double rho = a == 1.0 ? q0[c] : q0[c] / a;
-      double u = q1[c] / q0[c];
-      double v = q2[c] / q0[c];
+      double u = q1[c] * iq;
+      double v = q2[c] * iq;
       double E = a == 1.0 ? q3[c] : q3[c] / a;
       double p = (gm - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - gm * pi;
       bool phys = rho > 0.0 && p + pi > 0.0;
@@ -87,7 +89,7 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
         w1[c] = u;
         w2[c] = v;
         w3[c] = p;
-        double cs = sqrt(fmax(gm * (p + pi) / rho, 0.0));
+        double cs = sqrt(fmax(gm * (p + pi) * (a * iq), 0.0));
         lx = fabs(u) + cs;
         ly = fabs(v) + cs;
         double s = (fabs(u) + cs) / g.dx;

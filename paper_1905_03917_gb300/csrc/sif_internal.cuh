@@ -225,9 +225,13 @@ __device__ inline double weno5_plain(double v1, double v2, double v3, double v4,
 
 // ---------------------------------------------------------------------
 // exact two-material stiffened-gas Riemann problem (interface interaction);
-// the Newton derivative shares the rarefaction power with the function, so
-// iterates differ from the CPU reference by rounding while the converged
-// star state agrees to round-off
+// the Newton derivative shares the rarefaction power with the function, and
+// powers of a positive pressure ratio are taken as exp2(e log2 r) (shorter
+// dependent chains than a general pow), so iterates differ from the CPU
+// reference by rounding while the converged star state agrees to round-off
+
+// r^e for r > 0
+__device__ inline double pos_pow(double r, double e) { return exp2(e * log2(r)); }
 
 __device__ inline void riemann_side(double p, double rho, double pk, double g, double pi,
                                     double ck, double &f, double &df) {
@@ -241,7 +245,7 @@ __device__ inline void riemann_side(double p, double rho, double pk, double g, d
   } else {
     // r^(-(g+1)/(2g)) = r^((g-1)/(2g)) / r: one power per side and iteration
     double r = Pp / P;
-    double ra = pow(r, (g - 1.0) / (2.0 * g));
+    double ra = pos_pow(r, (g - 1.0) / (2.0 * g));
     f = 2.0 * ck / (g - 1.0) * (ra - 1.0);
     df = 1.0 / (rho * ck) * (ra / r);
   }
@@ -253,7 +257,7 @@ __device__ inline double riemann_star_density(double p, double rho, double pk, d
     double qq = (g - 1.0) / (g + 1.0);
     return rho * (r + qq) / (qq * r + 1.0);
   }
-  return rho * pow(r, 1.0 / g);
+  return rho * pos_pow(r, 1.0 / g);
 }
 
 // returns 0 or DERR_NOCONV; out: p*, u*, c*_L, c*_R
