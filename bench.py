@@ -46,6 +46,8 @@ def workload(name, seed=0):
         return inputs.batched_instances(count=256, seed=seed)
     if name == "shock_bubble":
         return inputs.shock_bubble(1024, 256)
+    if name == "shock_bubble_512":  # the small case kernel captures run on
+        return inputs.shock_bubble(512, 128)
     if name == "underwater_explosion":
         return inputs.underwater_explosion(2048)
     if name == "shock_tube":
@@ -171,6 +173,11 @@ def gpu_updates_for(case, mode, skip, count):
 # flux (3), the current and (second stage) base states (4 + 4 / 2 on
 # average) read once, the new state (4) written once.
 BYTES_PER_UPDATE = 8 * (4 + 2 + 2 + 3 + 4 + 2 + 4)
+# DRAM bytes per update measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of an air launch, 6.66 MB for 65 536 updates) on
+# the 512 x 128 shock-bubble with 16 x 8 tiles; scaled by the updates of a
+# launch for the roofline's traffic
+MEASURED_DRAM_BYTES_PER_UPDATE = 6.66e6 / 65536
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -383,7 +390,9 @@ def run_ours(args):
         "roofline": {"kernel": "k_fv_stage", "bound": "alu", "achieved": achieved_tf,
                      "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / NOMINAL_FP64_TFLOPS if achieved_tf else None,
-                     "traffic": None, "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
+                     "traffic": fv_units * MEASURED_DRAM_BYTES_PER_UPDATE,
+                     "traffic_source": "ncu DRAM bytes per update of the 512 x 128 capture x updates per launch",
+                     "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
                      "fp64_probe_tflops": probe, "flops_per_update": flops,
                      "avg_launch_ms": fv_avg_ms, "updates_per_launch": fv_units,
                      "share_of_step": prof["fv_ms"] / total_ms if total_ms else None,
