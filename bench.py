@@ -111,6 +111,19 @@ def dist_setup():
     return rank, ws, local, dist
 
 
+def over_ranks(dist, total_ms, updates):
+    """Whole-job figures of independent replicas: the slowest rank's timed
+    milliseconds and the sum of the updates of all ranks."""
+    if dist is None:
+        return total_ms, float(updates)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64)
+    u = torch.tensor([float(updates)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t), float(u)
+
+
 def cpu_baseline(case, mode, budget_s=20.0, max_steps=200):
     """The oracle as it stands, serial, on the first steps of the workload."""
     from oracle import oracle as O
@@ -208,14 +221,36 @@ def _prim_arrays(case):
     return [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
 
 
-def multi_vs_single(case, device, steps_single=600):
-    """Both forms advance the same problem to the same time T (the time 600
-    single-dt steps reach: through the shock-bubble interaction) on the GPU; the error of each is the relative L1
-    of the mixture density and energy fields against the single-dt method
-    at a quarter of the CFL number (temporal error about 16x smaller) on the
-    same grid.  speedup = GPU time of single-dt / GPU time of multi-dt."""
+def _coarsen(a):
+    """Conservative 2 x 2 average of a fine field onto the coarse grid."""
+    ny, nx = a.shape[-2] // 2, a.shape[-1] // 2
+    return a.reshape(a.shape[:-2] + (ny, 2, nx, 2)).mean(axis=(-3, -1))
+
+
+def _eq13(n, substeps, m):
+    """Speedup of the multi-time-step method predicted by Eq. 13 from the
+    time-step ratio n, the fluid-2 steps per cycle [n] and the share m of
+    fluid 1's Runge-Kutta stages in a single-time-step step."""
+    return n / (substeps - (substeps - 1.0) * m)
+
+
+def multi_vs_single(case, fine_case, device, steps_single=600, cfls=(0.6, 0.5, 0.4, 0.3)):
+    """Speedup of the multi-time-step method at equal error (Sec. 4.2).
+
+    T is the time steps_single single-dt steps at CFL 0.6 reach (through
+    the shock-bubble interaction).  The reference is the single-dt method
+    on the twice finer grid, run to T on the GPU and averaged 2 x 2.  The
+    error of a run is the relative L1 of the mixture density (and, for
+    information, of the fluid-P indicator phi > 0) against it.  Multi-dt
+    runs sweep the CFL number; the multi-dt time at the error of single-dt
+    at CFL 0.6 is interpolated log-log between the two CFL numbers that
+    bracket it (multi-dt at CFL 0.6 itself when its error is already no
+    larger).  Also reported: the equivalent-grid rate (nx ny x single-dt
+    steps to T per second of each method) and the speedup Eq. 13 predicts
+    from the measured n, [n] and m."""
     import torch
     from paper_1905_03917_gb300 import sif
+    cfl0 = case["cfg"].get("cfl", 0.6)
     arrs = _prim_arrays(case)
     probe = sif.Solver(case["cfg"], device=device).init_fluids(*arrs)
     probe.step_single_dt(steps_single)
@@ -223,37 +258,113 @@ def multi_vs_single(case, device, steps_single=600):
     probe.close()
 
     def fields(s):
-        qN, qP, _ = s.state()
-        return qN[0] + qP[0], qN[3] + qP[3]
+        qN, qP, phi = s.state()
+        return qN[0] + qP[0], (phi > 0).astype(np.float64)
 
-    def run(cfg, multi, warm=True):
-        s = sif.Solver(cfg, device=device).init_fluids(*arrs)
-        step = s.step_multi_dt if multi else s.step_single_dt
-        if warm:
-            step(10 ** 6, t_end=T)      # graphs built for this problem
-            s.init_fluids(*arrs)
+    def timed(s, step):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         info = step(10 ** 6, t_end=T)
         torch.cuda.synchronize()
-        ms = 1e3 * (time.perf_counter() - t0)
-        out = fields(s), ms, info
-        s.close()
-        return out
+        return 1e3 * (time.perf_counter() - t0), info
 
-    (ref_rho, ref_E), _, _ = run(dict(case["cfg"], cfl=case["cfg"].get("cfl", 0.6) / 4), False,
-                                 warm=False)
-    res = {}
-    for name, multi in (("single", False), ("multi", True)):
-        (rho, E), ms, info = run(case["cfg"], multi)
-        res[name] = {"ms": ms,
-                     "err_rho": float(np.abs(rho - ref_rho).sum() / np.abs(ref_rho).sum()),
-                     "err_E": float(np.abs(E - ref_E).sum() / np.abs(ref_E).sum())}
-    return {"T": T, "speedup": res["single"]["ms"] / res["multi"]["ms"],
-            "err_ratio_rho": res["multi"]["err_rho"] / res["single"]["err_rho"],
-            "single": res["single"], "multi": res["multi"],
-            "reference": "single-dt at CFL 0.15 on the same grid (GPU; parity-tested against the oracle)",
-            "timing": "host wall clock around synchronising calls that run to t_end"}
+    def err(f, ref):
+        return float(np.abs(f - ref).sum() / np.abs(ref).sum()) if ref is not None else None
+
+    # reference: single-dt on the finer grid (GPU; parity-tested against the oracle)
+    if fine_case is not None:
+        fine = sif.Solver(fine_case["cfg"], device=device).init_fluids(*_prim_arrays(fine_case))
+        fine.step_single_dt(10 ** 7, t_end=T)
+        assert abs(fine.t - T) <= 1e-12 * T
+        ref_rho, ref_ind = (_coarsen(f) for f in fields(fine))
+        fine.close()
+    else:
+        ref_rho = ref_ind = None
+        cfls = (cfl0,)
+
+    # single-dt at CFL 0.6, first a profiled pass that also builds the graphs
+    s = sif.Solver(case["cfg"], device=device).init_fluids(*arrs)
+    s.profile(True)
+    n_single = 0
+    while s.t < T:
+        s.step_single_dt(1, t_end=T)
+        n_single += 1
+    ps = s.profile_read()
+    s.profile(False)
+    s.init_fluids(*arrs)
+    single_ms, _ = timed(s, s.step_single_dt)
+    rho, ind = fields(s)
+    single = {"ms": single_ms, "steps": n_single, "err_rho": err(rho, ref_rho),
+              "err_indicator": err(ind, ref_ind)}
+    s.close()
+
+    sweep = []
+    for cfl in cfls:
+        cfg = dict(case["cfg"], cfl=cfl)
+        m = sif.Solver(cfg, device=device).init_fluids(*arrs)
+        rec = {"cfl": cfl}
+        if cfl == cfl0:
+            # profiled pass cycle by cycle: the n(t) trace and the updates
+            m.profile(True)
+            trace = []
+            while m.t < T:
+                info = m.step_multi_dt(1, t_end=T)
+                trace.append((info["t"], info["n_raw"], info["substeps"]))
+            pm = m.profile_read()
+            m.profile(False)
+            rec["cycles"] = len(trace)
+            rec["mean_substeps"] = float(np.mean([x[2] for x in trace]))
+            rec["mean_n"] = float(np.mean([x[1] for x in trace]))
+            stride = max(1, len(trace) // 12)
+            rec["n_trace"] = [[round(x[0], 5), round(x[1], 3), x[2]] for x in trace[::stride]]
+        else:
+            m.step_multi_dt(10 ** 6, t_end=T)   # graphs built for this CFL
+        m.init_fluids(*arrs)
+        rec["ms"], _ = timed(m, m.step_multi_dt)
+        rho, ind = fields(m)
+        rec["err_rho"], rec["err_indicator"] = err(rho, ref_rho), err(ind, ref_ind)
+        m.close()
+        sweep.append(rec)
+
+    # multi-dt time at the error of single-dt at CFL 0.6
+    e_s = single["err_rho"]
+    t_eq = None
+    if e_s is None:
+        pass
+    elif sweep[0]["err_rho"] <= e_s:
+        t_eq = sweep[0]["ms"]
+    else:
+        for a, b in zip(sweep, sweep[1:]):
+            if (a["err_rho"] - e_s) * (b["err_rho"] - e_s) <= 0 and a["err_rho"] != b["err_rho"]:
+                w = (np.log(e_s) - np.log(a["err_rho"])) / (np.log(b["err_rho"]) - np.log(a["err_rho"]))
+                t_eq = float(np.exp(np.log(a["ms"]) + w * (np.log(b["ms"]) - np.log(a["ms"]))))
+                break
+
+    # Eq. 13 from measured quantities: over the run, single-dt does
+    # 2 (u1 + u2) updates a step and a multi-dt cycle 2 (u1 + [n] u2), which
+    # gives fluid 1's share of the updates; m is that share of the finite-
+    # volume time of the single-dt run over its whole time
+    m0 = sweep[0]
+    s_bar = m0["mean_substeps"]
+    a_s = ps["fv_cell_updates"] / (2.0 * n_single)             # u1 + u2 per step
+    a_m = pm["fv_cell_updates"] / (2.0 * m0["cycles"])        # u1 + [n] u2 per cycle
+    u2 = (a_m - a_s) / (s_bar - 1.0) if s_bar > 1.0 else 0.0
+    u1 = a_s - u2
+    m_share = (u1 / a_s) * (ps["fv_ms"] / single_ms)
+    n_eff = n_single / m0["cycles"]
+    cells = case["cfg"]["nx"] * case["cfg"]["ny"]
+    ref = f"single-dt on {fine_case['name']} averaged 2x2 (GPU)" if fine_case else None
+    return {"T": T, "reference": ref,
+            "speedup_at_equal_error": single_ms / t_eq if t_eq else None,
+            "speedup_same_cfl": single_ms / m0["ms"],
+            "single": single, "multi_sweep": sweep,
+            "eq13": {"n": n_eff, "substeps": s_bar, "m": m_share,
+                     "fluid1_update_share": u1 / a_s,
+                     "fv_share_of_single_step": ps["fv_ms"] / single_ms,
+                     "predicted_speedup": _eq13(n_eff, s_bar, m_share)},
+            "equivalent_grid_updates_per_s": {"single": cells * n_single / (single_ms * 1e-3),
+                                              "multi": cells * n_single / (m0["ms"] * 1e-3)},
+            "timing": "host wall clock around synchronising calls that run to T"}
 
 
 def adjoint_cost(device, n=512, nsteps=200, every=20):
@@ -339,13 +450,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        u = torch.tensor([float(updates)], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_ms_all, updates_all = float(t), float(u)
-    else:
-        total_ms_all, updates_all = total_ms, float(updates)
+    total_ms_all, updates_all = over_ranks(dist, total_ms, updates)
     value = updates_all / (total_ms_all / 1e3)
 
     # end to end through the public API: host state in, one step, host state out
@@ -402,9 +507,16 @@ def run_ours(args):
                 "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
         "clocks": clk.summary(),
     }
-    if ws == 1 and not args.no_extras and case["cfg"]["dim"] == 2:
-        line["multi_vs_single"] = multi_vs_single(case, local)
+    if ws == 1 and not args.no_extras and case["name"].startswith("shock_bubble"):
+        from paper_1905_03917_gb300 import inputs
+        fine = inputs.shock_bubble(2 * case["cfg"]["nx"], 2 * case["cfg"]["ny"])
+        line["multi_vs_single"] = multi_vs_single(case, fine, local)
         line["adjoint"] = adjoint_cost(local)
+    elif ws == 1 and not args.no_extras and case["name"].startswith("underwater_explosion"):
+        # water, the fast fluid, fills almost the whole domain: the same-grid
+        # comparison over about 500 cycles with the n(t) trace, no finer
+        # reference (4096^2 to the same time would take minutes)
+        line["multi_vs_single"] = multi_vs_single(case, None, local, steps_single=1000)
     if ws == 1 and not args.no_cpu_baseline:
         nsteps, secs = cpu_baseline(case, args.mode, budget_s=args.cpu_budget)
         upd = gpu_updates_for(case, args.mode, 0, nsteps)
@@ -442,11 +554,8 @@ def run_batched(args):
             updates += b.step_multi_dt(1)
             total_ms += 1e3 * (time.perf_counter() - t0)
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        u = torch.tensor([float(updates)], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_ms, updates = float(t), float(u)
+        dist.barrier()
+    total_ms, updates = over_ranks(dist, total_ms, updates)
     if rank != 0:
         return
     cells = sum(c["cfg"]["nx"] * c["cfg"]["ny"] for c in cases)

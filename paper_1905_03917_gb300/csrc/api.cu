@@ -371,10 +371,17 @@ static void mix_one(sif_ctx *c, int k, double *const q[4]) {
 // The geometry of the current phi is already in place: every change of phi
 // (level-set stage, reinitialisation, initial data, restored state) is
 // followed by geometry() before anything else reads it.
-static void eval(sif_ctx *c, double *const qs[2][4]) {
+//
+// band_fluid >= 0 names a fluid whose stencil states are read only by this
+// interaction step (a sub-step of the other fluid, Sec. 3.1 step 3): its
+// states are recovered in the interaction band only, unless *band_flag is
+// set on the device (the last sub-step, whose second stage advances it).
+static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
+                 const int *band_flag = nullptr) {
   launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
   launch_prim2(c->g, qs[0], qs[1], c->w[0], c->w[1], c->alpha, c->tiles[0], c->tiles[1],
-               ntile(c), c->nostate, c->sc, c->st);
+               ntile(c), c->nostate, c->sc, band_fluid, band_flag, c->band_ev,
+               &c->sc->n_band, c->st);
   dbg(c, "prim");
   launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
                    c->ext_plan, ncell(c), band_work(c), c->nostate, c->st);
@@ -402,8 +409,8 @@ static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const bas
                double *const cur[4], const double *dtp) {
   ghost_w(c, k);
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
-                  c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), dtp, c->sc,
-                  c->st);
+                  c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), c->num_sms, dtp,
+                  c->sc, c->st);
   dbg(c, "fv_stage");
 }
 
@@ -590,7 +597,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
         qs[f1][m] = c->qi[m];
         qs[f2][m] = c->q[f2][m];
       }
-      eval(c, qs);
+      eval(c, qs, f1);
       launch_sched(SCHED_SUBSTEP, c->sc, cfl, thr, 0, c->st);
     } else {
       launch_sched(SCHED_FIRST_SUB, c->sc, cfl, thr, 0, c->st);
@@ -622,7 +629,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
       for (int m = 0; m < 4; m++) qs[f1][m] = c->qi[m];
     }
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
-    eval(c, qs);
+    eval(c, qs, last ? -1 : f1);
     launch_record(c->g, last, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0],
                   c->xc[1], c->xc[2], c->sc, c->st);
     // step 4 (and 5 on the last sub-step): second RK stage
@@ -735,7 +742,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   cond_node(c, hnf, false, [&] {
     launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
     mix_one(c, f1, c->qi);
-    eval(c, qs);
+    eval(c, qs, f1);
     launch_sched(SCHED_DT2, c->sc, cfl, thr, 0, c->st);
   });
   launch_sched(SCHED_LAST, c->sc, cfl, thr, 0, c->st);
@@ -762,7 +769,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
     launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
     mix_one(c, f1, c->qi);
   });
-  eval(c, qs);
+  eval(c, qs, f1, &c->sc->last);
   launch_record(c->g, -2, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 4 (and 5 on the last sub-step): second RK stage

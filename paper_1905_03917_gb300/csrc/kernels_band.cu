@@ -49,22 +49,40 @@ struct PrimArgs {
   double *w[2][4];
   const int *tiles[2];
   unsigned char *nostate[2];
+  // fluid whose states are needed in the interaction band only (-1: none),
+  // unless *band_flag is set (then everywhere, like the other fluid)
+  int band_fluid;
+  const int *band_flag;
+  const int *band;
+  const int *nband;
 };
 
-// blockIdx.y = fluid
+// blockIdx.y = fluid; the cells of the fluid's tiles, or of the band
 __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, const int *ntiles,
                        Scalars *sc) {
   SIF_TICK();
   const int k = blockIdx.y;
-  if ((int)blockIdx.x >= ntiles[k]) return;
+  const bool band_only = k == P.band_fluid && !(P.band_flag && *P.band_flag);
+  bool valid;
+  int c = 0;
+  if (band_only) {
+    int nb = *P.nband;
+    if ((int)(blockIdx.x * blockDim.x) >= nb) return;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    valid = idx < nb;
+    if (valid) c = P.band[idx];
+  } else {
+    if ((int)blockIdx.x >= ntiles[k]) return;
+    int tile = P.tiles[k][blockIdx.x];
+    int tx = tile % g.ntx, ty = tile / g.ntx;
+    int i = tx * g.tx + (threadIdx.x % g.tx), j = ty * g.ty + threadIdx.x / g.tx;
+    valid = i < g.nx && j < g.ny;
+    if (valid) c = gidx(g, i, j);
+  }
   const double *q0 = P.q[k][0], *q1 = P.q[k][1], *q2 = P.q[k][2], *q3 = P.q[k][3];
   double *w0 = P.w[k][0], *w1 = P.w[k][1], *w2 = P.w[k][2], *w3 = P.w[k][3];
-  int tile = P.tiles[k][blockIdx.x];
-  int tx = tile % g.ntx, ty = tile / g.ntx;
-  int i = tx * g.tx + (threadIdx.x % g.tx), j = ty * g.ty + threadIdx.x / g.tx;
   double lx = 0.0, ly = 0.0, sm = 0.0;
-  if (i < g.nx && j < g.ny) {
-    int c = gidx(g, i, j);
+  if (valid) {
     double a = vol_k(alpha, k, c);
     unsigned char nostate = 0;
     if (a > SIF_ALPHA_REAL) {
@@ -107,8 +125,13 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
 void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], double *const wN[4],
                   double *const wP[4], const double *alpha, const int *tilesN,
                   const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
+                  int band_fluid, const int *band_flag, const int *band, const int *nband,
                   cudaStream_t st) {
   PrimArgs P;
+  P.band_fluid = band_fluid;
+  P.band_flag = band_flag;
+  P.band = band;
+  P.nband = nband;
   P.nostate[0] = nostate[0];
   P.nostate[1] = nostate[1];
   for (int m = 0; m < 4; m++) {

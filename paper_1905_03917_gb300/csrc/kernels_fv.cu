@@ -24,6 +24,7 @@ struct FvArgs {
   const double *xn[3];
   const int *tiles;
   const int *ntiles;
+  int split_below;  // tile count under which each tile is split over two CTAs
   const double *dtp;
   const Scalars *sc;
 };
@@ -102,31 +103,20 @@ struct FvShape {
   static constexpr int threads = 2 * TX * TY;
 };
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A) {
-  SIF_TICK();
-  constexpr int HX = TX + 6, HY = TY + 6;
+// the three phases over an SX x SY block of output cells at (i0, j0), with
+// the CTA's threads (any count)
+template <int SX, int SY>
+__device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, int j0) {
+  constexpr int HX = SX + 6, HY = SY + 6;
   const Grid &g = A.g;
   const int k = A.k;
-  const int ntiles = A.ntiles[k];
-  if ((int)blockIdx.x >= ntiles) return;
-  extern __shared__ double smem[];
-  // split fluxes: x for rows of the tile with x-halo, y for columns with y-halo
-  double *fxp = smem;                   // [4][HX*TY]
-  double *fxm = fxp + 4 * HX * TY;      // [4][HX*TY]
-  double *fyp = fxm + 4 * HX * TY;      // [4][TX*HY]
-  double *fym = fyp + 4 * TX * HY;      // [4][TX*HY]
-  double *Fx = fym + 4 * TX * HY;       // [4][(TX+1)*TY]
-  double *Fy = Fx + 4 * (TX + 1) * TY;  // [4][TX*(TY+1)]
-
-  int tile = A.tiles[blockIdx.x];
-  int i0 = (tile % g.ntx) * TX, j0 = (tile / g.ntx) * TY;
-  if (threadIdx.x == 0) {
-    int w_ = min(TX, g.nx - i0), h_ = min(TY, g.ny - j0);
-    atomicAdd((unsigned long long *)&A.sc->updates, (unsigned long long)(w_ * h_));
-  }
-  const bool timed = A.sc->timing;
-  if (timed && threadIdx.x == 0) atomicMin((unsigned long long *)&A.sc->fv_t0, globaltimer_ns());
+  // split fluxes: x for rows of the block with x-halo, y for columns with y-halo
+  double *fxp = smem;                   // [4][HX*SY]
+  double *fxm = fxp + 4 * HX * SY;      // [4][HX*SY]
+  double *fyp = fxm + 4 * HX * SY;      // [4][SX*HY]
+  double *fym = fyp + 4 * SX * HY;      // [4][SX*HY]
+  double *Fx = fym + 4 * SX * HY;       // [4][(SX+1)*SY]
+  double *Fy = Fx + 4 * (SX + 1) * SY;  // [4][SX*(SY+1)]
   const double gm = g.gamma[k], pi = g.pinf[k];
   const double inv_gm1 = 1.0 / (gm - 1.0), e0c = gm * pi * inv_gm1;
   const double lfx = ull_as_double(A.sc->lf[k][0]), lfy = ull_as_double(A.sc->lf[k][1]);
@@ -134,7 +124,7 @@ __global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A)
   const int tid = threadIdx.x, nth = blockDim.x;
 
   // phase 1: Lax-Friedrichs split fluxes of the stencil states
-  for (int r = tid; r < HX * TY; r += nth) {
+  for (int r = tid; r < HX * SY; r += nth) {
     int i = i0 - 3 + r % HX, j = j0 + r / HX;
     double fp[4] = {0, 0, 0, 0}, fm[4] = {0, 0, 0, 0};
     if (i <= g.nx + 2 && j < g.ny) {
@@ -152,13 +142,13 @@ __global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A)
     }
 #pragma unroll
     for (int m = 0; m < 4; m++) {
-      fxp[m * HX * TY + r] = fp[m];
-      fxm[m * HX * TY + r] = fm[m];
+      fxp[m * HX * SY + r] = fp[m];
+      fxm[m * HX * SY + r] = fm[m];
     }
   }
   if (d2) {
-    for (int r = tid; r < TX * HY; r += nth) {
-      int i = i0 + r % TX, j = j0 - 3 + r / TX;
+    for (int r = tid; r < SX * HY; r += nth) {
+      int i = i0 + r % SX, j = j0 - 3 + r / SX;
       double fp[4] = {0, 0, 0, 0}, fm[4] = {0, 0, 0, 0};
       if (i < g.nx && j <= g.ny + 2) {
         int c = gidx(g, i, j);
@@ -175,8 +165,8 @@ __global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A)
       }
 #pragma unroll
       for (int m = 0; m < 4; m++) {
-        fyp[m * TX * HY + r] = fp[m];
-        fym[m * TX * HY + r] = fm[m];
+        fyp[m * SX * HY + r] = fp[m];
+        fym[m * SX * HY + r] = fm[m];
       }
     }
   }
@@ -184,9 +174,9 @@ __global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A)
 
   // phase 2: x faces (left face of cell i0 + fi), one (face, component) per item
   const double eps = g.weno_eps;
-  for (int r = tid; r < 4 * (TX + 1) * TY; r += nth) {
-    int m = r / ((TX + 1) * TY), f = r % ((TX + 1) * TY);
-    int fi = f % (TX + 1), fj = f / (TX + 1);
+  for (int r = tid; r < 4 * (SX + 1) * SY; r += nth) {
+    int m = r / ((SX + 1) * SY), f = r % ((SX + 1) * SY);
+    int fi = f % (SX + 1), fj = f / (SX + 1);
     int i = i0 + fi, j = j0 + fj;
     double val = 0.0;
     if (i <= g.nx && j < g.ny) {
@@ -194,56 +184,56 @@ __global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A)
       if (k == 0) A_ = 1.0 - A_;
       if (A_ != 0.0) {
         // cells i-3..i+2 are at halo columns fi..fi+5
-        const double *P = fxp + m * HX * TY + fj * HX + fi;
-        const double *M = fxm + m * HX * TY + fj * HX + fi;
+        const double *P = fxp + m * HX * SY + fj * HX + fi;
+        const double *M = fxm + m * HX * SY + fj * HX + fi;
         double nl, dl, nr, dr;
         weno5_frac(P[0], P[1], P[2], P[3], P[4], eps, nl, dl);
         weno5_frac(M[5], M[4], M[3], M[2], M[1], eps, nr, dr);
         val = face_value(A_, nl, dl, nr, dr);
       }
     }
-    Fx[m * (TX + 1) * TY + f] = val;
+    Fx[m * (SX + 1) * SY + f] = val;
   }
   if (d2) {
-    for (int r = tid; r < 4 * TX * (TY + 1); r += nth) {
-      int m = r / (TX * (TY + 1)), f = r % (TX * (TY + 1));
-      int fi = f % TX, fj = f / TX;
+    for (int r = tid; r < 4 * SX * (SY + 1); r += nth) {
+      int m = r / (SX * (SY + 1)), f = r % (SX * (SY + 1));
+      int fi = f % SX, fj = f / SX;
       int i = i0 + fi, j = j0 + fj;
       double val = 0.0;
       if (i < g.nx && j <= g.ny) {
         double A_ = A.ay[gidx(g, i, j)];
         if (k == 0) A_ = 1.0 - A_;
         if (A_ != 0.0) {
-          const double *P = fyp + m * TX * HY + fj * TX + fi;
-          const double *M = fym + m * TX * HY + fj * TX + fi;
+          const double *P = fyp + m * SX * HY + fj * SX + fi;
+          const double *M = fym + m * SX * HY + fj * SX + fi;
           double nl, dl, nr, dr;
-          weno5_frac(P[0], P[TX], P[2 * TX], P[3 * TX], P[4 * TX], eps, nl, dl);
-          weno5_frac(M[5 * TX], M[4 * TX], M[3 * TX], M[2 * TX], M[TX], eps, nr, dr);
+          weno5_frac(P[0], P[SX], P[2 * SX], P[3 * SX], P[4 * SX], eps, nl, dl);
+          weno5_frac(M[5 * SX], M[4 * SX], M[3 * SX], M[2 * SX], M[SX], eps, nr, dr);
           val = face_value(A_, nl, dl, nr, dr);
         }
       }
-      Fy[m * TX * (TY + 1) + f] = val;
+      Fy[m * SX * (SY + 1) + f] = val;
     }
   }
   __syncthreads();
 
-  // phase 3: update of the tile's cells
+  // phase 3: update of the block's cells
   const double dt = *A.dtp;
   const double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
   const double sgn = k == 0 ? 1.0 : -1.0;
-  for (int r = tid; r < TX * TY; r += nth) {
-    int li = r % TX, lj = r / TX;
+  for (int r = tid; r < SX * SY; r += nth) {
+    int li = r % SX, lj = r / SX;
     int i = i0 + li, j = j0 + lj;
     if (i >= g.nx || j >= g.ny) continue;
     int c = gidx(g, i, j);
     bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
 #pragma unroll
     for (int m = 0; m < 4; m++) {
-      const double *fx = Fx + m * (TX + 1) * TY + lj * (TX + 1) + li;
+      const double *fx = Fx + m * (SX + 1) * SY + lj * (SX + 1) + li;
       double L = (fx[0] - fx[1]) * inv_dx;
       if (d2) {
-        const double *fy = Fy + m * TX * (TY + 1) + lj * TX + li;
-        L += (fy[0] - fy[TX]) * inv_dy;
+        const double *fy = Fy + m * SX * (SY + 1) + lj * SX + li;
+        L += (fy[0] - fy[SX]) * inv_dy;
       }
       if (m > 0 && cut) L += sgn * A.xn[m - 1][c] * inv_dxdy;
       double cur = A.cur[m][c];
@@ -251,9 +241,49 @@ __global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A)
       A.dst[m][c] = out;
     }
   }
+}
+
+// A fluid with fewer active tiles than the GPU has SMs (the sub-cycled
+// fluid of a small region) has each tile computed by two CTAs, one half of
+// the tile each along its longer side: twice the SMs for the same face
+// fluxes (the halo share grows, the arithmetic per face is the same).
+template <int TX, int TY>
+struct FvHalf {
+  static constexpr bool along_x = TX >= TY;
+  static constexpr int SX = along_x ? TX / 2 : TX, SY = along_x ? TY : TY / 2;
+};
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A) {
+  SIF_TICK();
+  const Grid &g = A.g;
+  const int ntiles = A.ntiles[A.k];
+  const bool split = ntiles < A.split_below;
+  const int t = split ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  if (t >= ntiles) return;
+  extern __shared__ double smem[];
+  const int tile = A.tiles[t];
+  int i0 = (tile % g.ntx) * TX, j0 = (tile / g.ntx) * TY;
+  using H = FvHalf<TX, TY>;
+  if (split) {
+    if (blockIdx.x & 1) {
+      if (H::along_x) i0 += H::SX;
+      else j0 += H::SY;
+    }
+  }
+  if (threadIdx.x == 0) {
+    int w_ = min(split ? H::SX : TX, g.nx - i0), h_ = min(split ? H::SY : TY, g.ny - j0);
+    if (w_ > 0 && h_ > 0)
+      atomicAdd((unsigned long long *)&A.sc->updates, (unsigned long long)(w_ * h_));
+  }
+  const bool timed = A.sc->timing;
+  if (timed && threadIdx.x == 0) atomicMin((unsigned long long *)&A.sc->fv_t0, globaltimer_ns());
+  if (split) fv_cells<H::SX, H::SY>(A, smem, i0, j0);
+  else fv_cells<TX, TY>(A, smem, i0, j0);
   if (timed) {
     __syncthreads();
-    if (threadIdx.x == 0) fv_timer_block_done(A.sc, (unsigned int)ntiles);
+    if (threadIdx.x == 0)
+      fv_timer_block_done(A.sc, (unsigned int)(split ? 2 * ntiles : ntiles));
   }
 }
 
@@ -282,7 +312,8 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      double *const base[4], double *const cur[4], double *const w[4],
                      const double *ax, const double *ay, const double *sx, const double *sy,
                      const double *xn0, const double *xn1, const double *xn2, const int *tiles,
-                     int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st) {
+                     int tile_cap, int num_sms, const double *dtp, Scalars *sc,
+                     cudaStream_t st) {
   static const double A2[3] = {0.0, 0.0, 0.5}, B2[3] = {0.0, 1.0, 0.5};
   static const double A3[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
   FvArgs A;
@@ -308,10 +339,12 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   A.ntiles = sc->n_tiles;
   A.dtp = dtp;
   A.sc = sc;
-#define FV_LAUNCH(a, b)                                                                 \
-  if (g.tx == a && g.ty == b) {                                                        \
-    k_fv_stage<a, b><<<tile_cap, FvShape<a, b>::threads, FvShape<a, b>::smem(), st>>>(A); \
-    return;                                                                            \
+  A.split_below = num_sms;
+  const int grid = tile_cap > 2 * num_sms ? tile_cap : 2 * num_sms;
+#define FV_LAUNCH(a, b)                                                             \
+  if (g.tx == a && g.ty == b) {                                                    \
+    k_fv_stage<a, b><<<grid, FvShape<a, b>::threads, FvShape<a, b>::smem(), st>>>(A); \
+    return;                                                                        \
   }
   FV_SHAPES(FV_LAUNCH)
 #undef FV_LAUNCH

@@ -312,6 +312,9 @@ struct MixQ {
   double *q[2][4];
 };
 
+// plan of every band cell as a source, with the amounts it exchanges with
+// its targets, M = beta (q_t as - q_s at) / (as beta + at), computed from
+// the states before mixing
 __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__ alpha,
                             const double *__restrict__ phi, const int *__restrict__ band,
                             const int *nband, MixPlan *plan, int cap) {
@@ -324,47 +327,60 @@ __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__
       if (!(mask & (1 << k))) continue;
       MixPlan s;
       mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s);
+      double *const *q = Q.q[k];
+      for (int t = 0; t < s.nt; t++) {
+        int tc = s.tc[t];
+        double den = s.as * s.beta[t] + s.at[t];
+        for (int m = 0; m < 4; m++)
+          s.M[t][m] = s.beta[t] * (q[m][tc] * s.as - q[m][c] * s.at[t]) / den;
+      }
       plan[(size_t)k * cap + idx] = s;
     }
   }
 }
 
+// each band cell adds what it receives as a source and subtracts what it
+// gives as a target, in the CPU reference's scatter order (sources in
+// raster order, targets in plan order).  A cell reads only its own state
+// and the plans, so the update is written in place.
 __global__ void k_mix_apply(Grid g, int mask, MixQ Q, const int *__restrict__ map,
                             const MixPlan *__restrict__ plan, int cap,
-                            const int *__restrict__ band, const int *nband, double *tmp) {
+                            const int *__restrict__ band, const int *nband) {
   SIF_TICK();
   int k = blockIdx.y;
   if (!(mask & (1 << k))) return;
   int n = *nband;
   double *const *q = Q.q[k];
   const MixPlan *P = plan + (size_t)k * cap;
-  double *out = tmp + (size_t)k * 4 * n;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
     int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+    // the neighbours' plan positions and target counts, loaded together
+    int ps[9], nts[9];
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+      int di = e % 3 - 1, dj = e / 3 - 1;
+      bool ok = (g.dim == 2 || dj == 0) && inside(g, i + di, j + dj);
+      ps[e] = ok ? map[gidx(g, i + di, j + dj)] : -1;
+    }
+#pragma unroll
+    for (int e = 0; e < 9; e++) nts[e] = ps[e] >= 0 ? P[ps[e]].nt : 0;
     double val[4] = {q[0][c], q[1][c], q[2][c], q[3][c]};
-    for (int dj = -1; dj <= 1; dj++) {
-      if (g.dim == 1 && dj != 0) continue;
-      for (int di = -1; di <= 1; di++) {
-        if (!inside(g, i + di, j + dj)) continue;
-        int s = gidx(g, i + di, j + dj);
-        int ps = map[s];
-        if (ps < 0) continue;
-        const MixPlan &sp = P[ps];
-        for (int t = 0; t < sp.nt; t++) {
-          int tc = sp.tc[t];
-          bool self = (s == c), tgt = (tc == c);
-          if (!self && !tgt) continue;
-          double den = sp.as * sp.beta[t] + sp.at[t];
-          for (int m = 0; m < 4; m++) {
-            double M = sp.beta[t] * (q[m][tc] * sp.as - q[m][s] * sp.at[t]) / den;
-            if (self) val[m] += M;
-            if (tgt) val[m] -= M;
-          }
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+      if (!nts[e]) continue;
+      const MixPlan &sp = P[ps[e]];
+      bool self = e == 4;
+      for (int t = 0; t < nts[e]; t++) {
+        bool tgt = sp.tc[t] == c;
+        if (!self && !tgt) continue;
+        for (int m = 0; m < 4; m++) {
+          if (self) val[m] += sp.M[t][m];
+          if (tgt) val[m] -= sp.M[t][m];
         }
       }
     }
-    for (int m = 0; m < 4; m++) out[(size_t)m * n + idx] = val[m];
+    for (int m = 0; m < 4; m++) q[m][c] = val[m];
   }
 }
 
@@ -393,9 +409,8 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
   // small blocks spread the band's few thousand cells over the SMs
   int b = blocks_for(work, 64);
   k_mix_setup<<<b, 64, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
-  k_mix_apply<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, map, plan, cap, band, nband, tmp);
-  k_mix_scatter<<<dim3(b, 2), 64, 0, st>>>(mask, Q, band, nband, tmp);
-  sif_note_launches(3);
+  k_mix_apply<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, map, plan, cap, band, nband);
+  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------

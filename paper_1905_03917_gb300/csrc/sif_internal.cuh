@@ -96,6 +96,7 @@ struct MixPlan {
   int tc[3];
   int nt;
   double beta[3], at[3], as;
+  double M[3][4];  // conserved amount moved from target t to the source
 };
 
 __host__ __device__ inline int gidx(const Grid &g, int i, int j) {
@@ -334,9 +335,12 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
                        const int *band, const int *nband, double *tmp, const double *alpha,
                        const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st);
 
+// band_fluid >= 0: that fluid's states are recovered in the interaction
+// band only (band, nband), unless band_flag is non-null and *band_flag != 0
 void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], double *const wN[4],
                   double *const wP[4], const double *alpha, const int *tilesN,
                   const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
+                  int band_fluid, const int *band_flag, const int *band, const int *nband,
                   cudaStream_t st);
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
@@ -369,7 +373,8 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
                      double *const base[4], double *const cur[4], double *const w[4],
                      const double *ax, const double *ay, const double *sx, const double *sy,
                      const double *xn0, const double *xn1, const double *xn2, const int *tiles,
-                     int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st);
+                     int tile_cap, int num_sms, const double *dtp, Scalars *sc,
+                     cudaStream_t st);
 
 // adjoint of the frozen single-time-step step (adjoint.cu, kernels_plan.cu)
 void launch_adj_rhs(const Grid &g, double *const W[2][4], const unsigned long long *lf,
