@@ -391,7 +391,7 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
   dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
-  launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, ncell(c), c->xn[0],
+  launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, band_work(c), c->xn[0],
                    c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
   dbg(c, "interface");
   launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),

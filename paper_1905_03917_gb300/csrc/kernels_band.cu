@@ -149,6 +149,57 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
 // ---------------------------------------------------------------------
 // interface interaction in every cut cell
 
+// riemann_solve with one side of the problem per lane of a lane pair (even
+// lane: fluid N on the left, odd lane: fluid P on the right).  Each lane
+// evaluates its own side's wave function and derivative, the pair
+// exchanges them, and both lanes take the same Newton step with the same
+// operations in the same order as riemann_solve, so the star state is the
+// same to the bit.  Returns 0 or DERR_NOCONV; out: p*, u*, and the lane's
+// own star sound speed.
+__device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, double un,
+                                         double pk, double gk, double pik, double &ps,
+                                         double &us, double &cs) {
+  double ck = sqrt(gk * (pk + pik) / rho);
+  double ro = __shfl_xor_sync(pair, rho, 1), uo = __shfl_xor_sync(pair, un, 1);
+  double po = __shfl_xor_sync(pair, pk, 1), pio = __shfl_xor_sync(pair, pik, 1);
+  double co = __shfl_xor_sync(pair, ck, 1);
+  const bool L = side == 0;
+  double rl = L ? rho : ro, ul = L ? un : uo, pl = L ? pk : po, pil = L ? pik : pio;
+  double rr = L ? ro : rho, ur = L ? uo : un, pr = L ? po : pk, pir = L ? pio : pik;
+  double cl = L ? ck : co, cr = L ? co : ck;
+  double pscale = fmin(pl + pil, pr + pir);
+  double pfloor = -fmin(pil, pir) + 1e-12 * pscale;
+  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  if (p < pfloor) p = pfloor;
+  int it = 0, conv = 0, done = 0;
+  double f, df;
+  while (it < 50) {
+    it++;
+    riemann_side(p, rho, pk, gk, pik, ck, f, df);
+    double fo = __shfl_xor_sync(pair, f, 1), dfo = __shfl_xor_sync(pair, df, 1);
+    double fl = L ? f : fo, fr = L ? fo : f, dfl = L ? df : dfo, dfr = L ? dfo : df;
+    double F = fl + fr + (ur - ul);
+    double pn = p - F / (dfl + dfr);
+    if (pn < pfloor) pn = pfloor;
+    double dp = fabs(pn - p);
+    p = pn;
+    if (conv) {
+      done = 1;
+      break;
+    }
+    if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
+  }
+  riemann_side(p, rho, pk, gk, pik, ck, f, df);
+  double fo = __shfl_xor_sync(pair, f, 1);
+  double fl = L ? f : fo, fr = L ? fo : f;
+  us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  double rs = riemann_star_density(p, rho, pk, gk, pik);
+  ps = p;
+  cs = sqrt(gk * (p + pik) / rs);
+  return (done || conv) ? 0 : DERR_NOCONV;
+}
+
+// two lanes per cut cell (blockDim a multiple of 32)
 __global__ void k_interface(Grid g, const double *__restrict__ n0, const double *__restrict__ n1,
                             const double *__restrict__ n2, const double *__restrict__ n3,
                             const double *__restrict__ p0, const double *__restrict__ p1,
@@ -161,8 +212,11 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
   int n = *ncut;
   double fac = 1.0 / g.dx + (g.dim == 2 ? 1.0 / g.dy : 0.0);
   double sN = 0.0, sP = 0.0;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = cut[idx];
+  const int side = threadIdx.x & 1;
+  const unsigned pair = 3u << (threadIdx.x & 30);
+  // the stride is even: both lanes of a pair stay on the same cell
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; (t >> 1) < n; t += gridDim.x * blockDim.x) {
+    int c = cut[t >> 1];
     int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
     double Sx = sx[c], Sy = sy[c];
     double Sm = sqrt(Sx * Sx + Sy * Sy);
@@ -172,18 +226,29 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
       nxv = Sx / Sm;
       nyv = Sy / Sm;
     }
-    double ps, us, csl, csr;
-    int e = riemann_solve(n0[c], n1[c] * nxv + n2[c] * nyv, n3[c], g.gamma[0], g.pinf[0], p0[c],
-                          p1[c] * nxv + p2[c] * nyv, p3[c], g.gamma[1], g.pinf[1], ps, us, csl,
-                          csr);
-    if (e) atomicOr(&sc->err, e);
-    xn0[c] = -ps * Sx;
-    xn1[c] = -ps * Sy;
-    xn2[c] = -ps * us * Sm;
-    ul0[c] = us * nxv;
-    ul1[c] = us * nyv;
-    sN = fmax(sN, (fabs(us) + csl) * fac);
-    sP = fmax(sP, (fabs(us) + csr) * fac);
+    double rho, un, pk;
+    if (side == 0) {
+      rho = n0[c];
+      un = n1[c] * nxv + n2[c] * nyv;
+      pk = n3[c];
+    } else {
+      rho = p0[c];
+      un = p1[c] * nxv + p2[c] * nyv;
+      pk = p3[c];
+    }
+    double ps, us, cs;
+    int e = riemann_solve_pair(pair, side, rho, un, pk, g.gamma[side], g.pinf[side], ps, us, cs);
+    if (e && side == 0) atomicOr(&sc->err, e);
+    if (side == 0) {
+      xn0[c] = -ps * Sx;
+      xn1[c] = -ps * Sy;
+      xn2[c] = -ps * us * Sm;
+      ul0[c] = us * nxv;
+      ul1[c] = us * nyv;
+      sN = fmax(sN, (fabs(us) + cs) * fac);
+    } else {
+      sP = fmax(sP, (fabs(us) + cs) * fac);
+    }
   }
   block_max2(sN, sP, &sc->smax[0], &sc->smax[1]);
 }
@@ -192,10 +257,11 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
                       const double *sx, const double *sy, const int *cut, int cut_cap,
                       double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
                       Scalars *sc, cudaStream_t st) {
-  // one warp per block: the Newton solves are FP64-throughput bound, and
-  // a few hundred cut cells in 128-thread blocks would occupy a handful of
-  // SMs
-  int blocks = grid_for(cut_cap, 32, 4864);
+  // one warp (16 cut cells) per block: the Newton solves are bound by the
+  // FP64 lanes of the SMs they occupy, and a few hundred cut cells in
+  // larger blocks would occupy a handful of SMs.  cut_cap bounds the cut
+  // count (the kernel loops over the device count).
+  int blocks = grid_for(2 * cut_cap, 32, 9728);
   k_interface<<<blocks, 32, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
                                       phi, sx, sy, cut, &sc->n_cut, xn0, xn1, xn2, ul0, ul1, sc);
   sif_note_launches(1);

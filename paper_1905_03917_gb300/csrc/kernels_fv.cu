@@ -29,11 +29,15 @@ struct FvArgs {
   const Scalars *sc;
 };
 
-// WENO5-JS reconstruction as a fraction num / den (the face flux adds two
-// of them over one division)
+// WENO5-JS reconstruction as a fraction num / den, up to a factor common
+// to both (the face flux adds two of them over one division).  With
+// t_r = (eps + b_r)^2 the nonlinear weights d_r / t_r, scaled by t0 t1 t2,
+// are d_r u_r with u_0 = t1 t2, u_1 = t0 t2, u_2 = t0 t1; the linear
+// weights d_r = (0.1, 0.6, 0.3) and the candidates' 1/6 are folded into
+// the candidates' coefficients.
 __device__ __forceinline__ void weno5_frac(double v1, double v2, double v3, double v4, double v5,
                                           double eps, double &num, double &den) {
-  const double c13_12 = 13.0 / 12.0, s6 = 1.0 / 6.0;
+  const double c13_12 = 13.0 / 12.0;
   double d0 = (v1 + v3) - 2.0 * v2;
   double e0 = (v1 + 3.0 * v3) - 4.0 * v2;
   double d1 = (v2 + v4) - 2.0 * v3;
@@ -43,17 +47,18 @@ __device__ __forceinline__ void weno5_frac(double v1, double v2, double v3, doub
   double b0 = c13_12 * d0 * d0 + 0.25 * e0 * e0;
   double b1 = c13_12 * d1 * d1 + 0.25 * e1 * e1;
   double b2 = c13_12 * d2 * d2 + 0.25 * e2 * e2;
-  double q0 = (2.0 * v1 - 7.0 * v2 + 11.0 * v3) * s6;
-  double q1 = (-v2 + 5.0 * v3 + 2.0 * v4) * s6;
-  double q2 = (2.0 * v3 + 5.0 * v4 - v5) * s6;
+  // d_r q_r: 0.1 (2 v1 - 7 v2 + 11 v3) / 6, 0.6 (-v2 + 5 v3 + 2 v4) / 6,
+  // 0.3 (2 v3 + 5 v4 - v5) / 6
+  double q0 = (1.0 / 30.0) * v1 - (7.0 / 60.0) * v2 + (11.0 / 60.0) * v3;
+  double q1 = 0.5 * v3 - 0.1 * v2 + 0.2 * v4;
+  double q2 = 0.1 * v3 + 0.25 * v4 - 0.05 * v5;
   double t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
   t0 *= t0;
   t1 *= t1;
   t2 *= t2;
-  // weights d_r / t_r scaled by t0 t1 t2: numerator and denominator
-  double w0 = 0.1 * (t1 * t2), w1 = 0.6 * (t0 * t2), w2 = 0.3 * (t0 * t1);
-  num = w0 * q0 + w1 * q1 + w2 * q2;
-  den = w0 + w1 + w2;
+  double u0 = t1 * t2, u1 = t0 * t2, u2 = t0 * t1;
+  num = u0 * q0 + u1 * q1 + u2 * q2;
+  den = 0.1 * u0 + 0.6 * u1 + 0.3 * u2;
 }
 
 // A (num_l / den_l + num_r / den_r) with one division; two if the
@@ -119,7 +124,9 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
   double *Fy = Fx + 4 * (SX + 1) * SY;  // [4][SX*(SY+1)]
   const double gm = g.gamma[k], pi = g.pinf[k];
   const double inv_gm1 = 1.0 / (gm - 1.0), e0c = gm * pi * inv_gm1;
-  const double lfx = ull_as_double(A.sc->lf[k][0]), lfy = ull_as_double(A.sc->lf[k][1]);
+  // Lax-Friedrichs splitting f+- = F/2 +- (alpha/2) U
+  const double hlx = 0.5 * ull_as_double(A.sc->lf[k][0]);
+  const double hly = 0.5 * ull_as_double(A.sc->lf[k][1]);
   const bool d2 = g.dim == 2;
   const int tid = threadIdx.x, nth = blockDim.x;
 
@@ -136,8 +143,8 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
       double U[4] = {rho, mu, rho * v, E};
 #pragma unroll
       for (int m = 0; m < 4; m++) {
-        fp[m] = 0.5 * (F[m] + lfx * U[m]);
-        fm[m] = 0.5 * (F[m] - lfx * U[m]);
+        fp[m] = 0.5 * F[m] + hlx * U[m];
+        fm[m] = 0.5 * F[m] - hlx * U[m];
       }
     }
 #pragma unroll
@@ -159,8 +166,8 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
         double U[4] = {rho, rho * u, mv, E};
 #pragma unroll
         for (int m = 0; m < 4; m++) {
-          fp[m] = 0.5 * (F[m] + lfy * U[m]);
-          fm[m] = 0.5 * (F[m] - lfy * U[m]);
+          fp[m] = 0.5 * F[m] + hly * U[m];
+          fm[m] = 0.5 * F[m] - hly * U[m];
         }
       }
 #pragma unroll
