@@ -383,11 +383,14 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
                ntile(c), c->nostate, c->sc, band_fluid, band_flag, c->band_ev,
                &c->sc->n_band, c->st);
   dbg(c, "prim");
+  // the plan kernel also takes the stencil states' first sweep
+  const bool first = c->g.ext_iters >= 1;
   launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
-                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st);
+                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st, c->w[0], c->w[1],
+                   first ? c->tmp : nullptr);
   launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
                     band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
-                    c->sc, c->st);
+                    c->sc, c->st, first ? 1 : 0);
   dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);

@@ -54,6 +54,16 @@ void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int 
   sif_note_launches(1);
 }
 
+// Jacobi sweeps of fields [f0, f0 + nf) (blockIdx.y selects the field),
+// ping-ponging between two band-indexed buffers: sweep 0 reads the planes,
+// later sweeps read the previous sweep's buffer for band neighbours and the
+// planes for neighbours outside the band (whose values never change)
+struct ExtFields {
+  double *p[3][4];
+  int ncomp[3];
+  double gamma[2], pinf[2];
+};
+
 // ---------------------------------------------------------------------
 // extension plans: for every band cell and each of the three extended
 // fields (W_N, W_P, level-set velocity) the upwind x and y neighbours and
@@ -64,7 +74,7 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
                             const double *__restrict__ sy, const int *__restrict__ band,
                             const int *nband, const int *__restrict__ map, ExtPlan *plan,
                             int cap, const unsigned char *__restrict__ ns0,
-                            const unsigned char *__restrict__ ns1) {
+                            const unsigned char *__restrict__ ns1, ExtFields F, double *sweep0) {
   SIF_TICK();
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
@@ -108,6 +118,23 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
         }
       }
       plan[(size_t)f * cap + idx] = pl;
+      // the first sweep of the stencil states (k_ext_sweep without a
+      // previous sweep), while the plan is at hand
+      if (sweep0 && f < 2) {
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+          const double *a = F.p[f][m];
+          double v;
+          if (pl.cx < 0 && pl.cy < 0) {
+            v = a[c];
+          } else {
+            v = 0.0;
+            if (pl.cx >= 0) v += pl.wx * a[pl.cx];
+            if (pl.cy >= 0) v += pl.wy * a[pl.cy];
+          }
+          sweep0[(size_t)f * 4 * cap + (size_t)m * cap + idx] = v;
+        }
+      }
     }
   }
 }
@@ -115,34 +142,76 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
                       const double *sy, const int *band, const int *nband, const int *map,
                       ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
-                      cudaStream_t st) {
+                      cudaStream_t st, double *const wN[4], double *const wP[4],
+                      double *sweep0) {
+  ExtFields F = {};
+  if (sweep0)
+    for (int m = 0; m < 4; m++) {
+      F.p[0][m] = wN[m];
+      F.p[1][m] = wP[m];
+    }
   k_ext_setup<<<blocks_for(work, 64), 64, 0, st>>>(g, alpha, phi, sx, sy, band, nband, map,
-                                                    plan, cap, nostate[0], nostate[1]);
+                                                    plan, cap, nostate[0], nostate[1], F,
+                                                    sweep0);
   sif_note_launches(1);
 }
 
-// Jacobi sweeps of fields [f0, f0 + nf) (blockIdx.y selects the field),
-// ping-ponging between two band-indexed buffers: sweep 0 reads the planes,
-// later sweeps read the previous sweep's buffer for band neighbours and the
-// planes for neighbours outside the band (whose values never change)
-struct ExtFields {
-  double *p[3][4];
-  int ncomp[3];
-};
 
+// fold a block's wave speeds of extended stencil states into the
+// Lax-Friedrichs maxima of fluid f (every thread of the block calls it)
+__device__ void ext_fold_lf(double lx, double ly, unsigned long long *lf) {
+  __shared__ double sa[32], sb[32];
+  lx = warp_max(lx);
+  ly = warp_max(ly);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = lx;
+    sb[wid] = ly;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    lx = lane < nw ? sa[lane] : 0.0;
+    ly = lane < nw ? sb[lane] : 0.0;
+    lx = warp_max(lx);
+    ly = warp_max(ly);
+    if (lane == 0) {
+      atomic_max_pos(&lf[0], lx);
+      atomic_max_pos(&lf[1], ly);
+    }
+  }
+}
+
+// One Jacobi sweep.  With writeback (a sweep after the first: band cells
+// read only the previous sweep's buffer) the results go straight to the
+// planes, and the extended stencil states fold their wave speeds into the
+// Lax-Friedrichs maxima, as k_ext_scatter would.  The band position and
+// plan of a thread's first cell are loaded together with the band count.
 __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ plan, int cap,
                             const int *__restrict__ band, const int *nband,
-                            const double *__restrict__ src, double *dst) {
+                            const double *__restrict__ src, double *dst, int writeback,
+                            const double *__restrict__ alpha,
+                            const unsigned char *__restrict__ ns0,
+                            const unsigned char *__restrict__ ns1, Scalars *sc) {
   SIF_TICK();
-  int n = *nband;
-  int f = f0 + blockIdx.y;
-  int nc = F.ncomp[f];
+  const int f = f0 + blockIdx.y;
+  const int nc = F.ncomp[f];
   const ExtPlan *P = plan + (size_t)f * cap;
   const size_t slot = (size_t)blockIdx.y * 4 * cap;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    ExtPlan pl = P[idx];
-    for (int m = 0; m < nc; m++) {
+  const int idx0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool inb = idx0 < cap;
+  const int c0 = inb ? band[idx0] : 0;
+  const ExtPlan pl0 = inb ? P[idx0] : ExtPlan{-1, -1, -1, -1, 0.0, 0.0};
+  const int n = *nband;
+  const bool fold = writeback && f < 2;
+  double lx = 0.0, ly = 0.0;
+  for (int idx = idx0; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = idx == idx0 ? c0 : band[idx];
+    ExtPlan pl = idx == idx0 ? pl0 : P[idx];
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      if (m >= nc) break;
       const double *a = F.p[f][m];
       const double *b = src ? src + slot + (size_t)m * cap : nullptr;
       double v;
@@ -153,9 +222,24 @@ __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ pla
         if (pl.cx >= 0) v += pl.wx * ((b && pl.bx >= 0) ? b[pl.bx] : a[pl.cx]);
         if (pl.cy >= 0) v += pl.wy * ((b && pl.by >= 0) ? b[pl.by] : a[pl.cy]);
       }
-      dst[slot + (size_t)m * cap + idx] = v;
+      out[m] = v;
+    }
+    if (writeback) {
+#pragma unroll
+      for (int m = 0; m < 4; m++)
+        if (m < nc) F.p[f][m][c] = out[m];
+      if (fold && (!(vol_k(alpha, f, c) > SIF_ALPHA_REAL) || (f == 0 ? ns0 : ns1)[c])) {
+        double cs = sqrt(fmax(F.gamma[f] * (out[3] + F.pinf[f]) / out[0], 0.0));
+        lx = fmax(lx, fabs(out[1]) + cs);
+        ly = fmax(ly, fabs(out[2]) + cs);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 4; m++)
+        if (m < nc) dst[slot + (size_t)m * cap + idx] = out[m];
     }
   }
+  if (fold) ext_fold_lf(lx, ly, sc->lf[f]);
 }
 
 // write the last sweep back; for the stencil states fold the extended
@@ -182,34 +266,14 @@ __global__ void k_ext_scatter(Grid g, ExtFields F, int f0, int cap, const int *_
       ly = fmax(ly, fabs(v) + cs);
     }
   }
-  if (f < 2) {
-    __shared__ double sa[32], sb[32];
-    lx = warp_max(lx);
-    ly = warp_max(ly);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-      sa[wid] = lx;
-      sb[wid] = ly;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      int nw = (blockDim.x + 31) >> 5;
-      lx = lane < nw ? sa[lane] : 0.0;
-      ly = lane < nw ? sb[lane] : 0.0;
-      lx = warp_max(lx);
-      ly = warp_max(ly);
-      if (lane == 0) {
-        atomic_max_pos(&sc->lf[f][0], lx);
-        atomic_max_pos(&sc->lf[f][1], ly);
-      }
-    }
-  }
+  if (f < 2) ext_fold_lf(lx, ly, sc->lf[f]);
 }
 
 void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
                        const int *band, const int *nband, double *tmp, const double *alpha,
-                       const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st) {
+                       const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st,
+                       int first_done) {
   ExtFields F;
   for (int m = 0; m < 4; m++) {
     F.p[0][m] = wN[m];
@@ -218,18 +282,33 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
   }
   F.ncomp[0] = F.ncomp[1] = 4;
   F.ncomp[2] = 2;
+  for (int k = 0; k < 2; k++) {
+    F.gamma[k] = g.gamma[k];
+    F.pinf[k] = g.pinf[k];
+  }
   dim3 grid(blocks_for(work, 64), nf);
   double *buf[2] = {tmp, tmp + (size_t)8 * cap};
-  const double *src = nullptr;
-  int cur = 0;
-  for (int it = 0; it < g.ext_iters; it++) {
-    k_ext_sweep<<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur]);
+  // first_done: sweep 0 is already in buf[0] (written by k_ext_setup)
+  const double *src = first_done ? buf[0] : nullptr;
+  int cur = first_done ? 1 : 0;
+  // the last sweep writes the planes itself when it is not the first
+  // (the first reads band neighbours from the planes it would overwrite)
+  const int iters = g.ext_iters;
+  int launched = 0;
+  for (int it = first_done ? 1 : 0; it < iters; it++) {
+    const int wb = it == iters - 1 && it > 0;
+    k_ext_sweep<<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur], wb, alpha,
+                                      nostate[0], nostate[1], sc);
     src = buf[cur];
     cur ^= 1;
+    launched++;
   }
-  k_ext_scatter<<<grid, 64, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
-                                      nostate[1], sc);
-  sif_note_launches(g.ext_iters + 1);
+  if (iters <= 1 && src) {
+    k_ext_scatter<<<grid, 64, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
+                                        nostate[1], sc);
+    launched++;
+  }
+  sif_note_launches(launched);
 }
 
 // ---------------------------------------------------------------------

@@ -325,15 +325,19 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
                  cudaStream_t st);
 // nostate[k]: 1 where a cut cell of fluid k holds no physical state (set by
 // the primitive recovery of the same interaction step)
+// sweep0 != null: also the first Jacobi sweep of both fluids' stencil
+// states wN, wP into the sweep buffer (then launch_ext_sweeps with first_done)
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
                       const double *sy, const int *band, const int *nband, const int *map,
                       ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
-                      cudaStream_t st);
+                      cudaStream_t st, double *const wN[4] = nullptr,
+                      double *const wP[4] = nullptr, double *sweep0 = nullptr);
 // f0 = 0, nf = 2: stencil states of both fluids; f0 = 2, nf = 1: level-set velocity
 void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,
                        const int *band, const int *nband, double *tmp, const double *alpha,
-                       const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st);
+                       const unsigned char *const nostate[2], Scalars *sc, cudaStream_t st,
+                       int first_done = 0);
 
 // band_fluid >= 0: that fluid's states are recovered in the interaction
 // band only (band, nband), unless band_flag is non-null and *band_flag != 0
