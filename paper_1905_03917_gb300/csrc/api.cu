@@ -340,10 +340,19 @@ static void ghost_w(sif_ctx *c, int k) {
 static int ncell(const sif_ctx *c) { return c->g.nx * c->g.ny; }
 static int ntile(const sif_ctx *c) { return c->g.ntx * c->g.nty; }
 
-// level set changed: ghosts, geometry, cut list, band list and map, tile lists
-static void geometry(sif_ctx *c) {
+static int band_work(const sif_ctx *c);
+
+// level set changed: ghosts, geometry, cut list, band list and map, tile
+// lists.  after_ls: phi changed by a level-set stage or reinitialisation
+// since the last call (inside the band only, the interface by less than a
+// cell), so only the previous band's cells can change their geometry;
+// otherwise (initial data, a restored or replayed phi) the whole grid.
+static void geometry(sif_ctx *c, bool after_ls = false) {
   ghost_phi(c);
-  launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st);
+  const bool band = after_ls && c->g.band >= 3.0;
+  launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st,
+                  band ? c->band_ev : nullptr, band ? &c->sc->n_band : nullptr,
+                  band ? band_work(c) : 0);
   launch_band_map(c->g, c->phi, c->band_ev, c->bandmap, &c->sc->n_band, c->st);
   launch_tile_lists(c->g, c->phi, c->tiles[0], c->tiles[1], c->sc, c->st);
   dbg(c, "geometry");
@@ -467,7 +476,7 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
     if (rec && s == 1)
       cudaMemcpyAsync(rec->phi1, c->phi, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
     if (s == S) reinit(c);
-    geometry(c);
+    geometry(c, true);
     mix_both(c);
   }
 }
@@ -621,7 +630,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     ls_begin(c);
     fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
     ls_stage(c, 1, &c->sc->dt2);
-    geometry(c);
+    geometry(c, true);
     mix_one(c, f2, c->q[f2]);
     if (last) {
       mix_one(c, f1, c->fut);
@@ -642,12 +651,12 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     reinit(c);
     if (last) {
       if (c->cfg.flux_correction) launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
-      geometry(c);
+      geometry(c, true);
       mix_both(c);
       break;
     }
     launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
-    geometry(c);
+    geometry(c, true);
     mix_one(c, f2, c->q[f2]);
     if (sub > 100000) {
       set_err(c, "sub-cycle count exceeded 100000");
@@ -762,7 +771,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   ls_begin(c);
   fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
   ls_stage(c, 1, &c->sc->dt2);
-  geometry(c);
+  geometry(c, true);
   mix_one(c, f2, c->q[f2]);
   cond_node(c, hl1, false, [&] {
     mix_one(c, f1, c->fut);
@@ -783,12 +792,12 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   cond_node(c, hl3, false, [&] {
     if (c->cfg.flux_correction)
       launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
-    geometry(c);
+    geometry(c, true);
     mix_both(c);
   });
   cond_node(c, hn2, false, [&] {
     launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
-    geometry(c);
+    geometry(c, true);
     mix_one(c, f2, c->q[f2]);
   });
   launch_cond(COND_LOOP, c->sc, hloop, 0, 0, kMaxSubsteps, c->st);

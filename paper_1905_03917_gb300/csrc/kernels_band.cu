@@ -7,7 +7,9 @@
 //
 // Compiled without FMA contraction, like kernels_geom.cu: these kernels
 // follow the CPU reference operation by operation so that threshold and
-// branch decisions agree with it.
+// branch decisions agree with it -- except the level-set derivatives, whose
+// WENO5 weights take one division (rounding-level differences; their only
+// decisions are clamps, continuous in the value).
 #include "sif_internal.cuh"
 
 static int grid_for(int n, int per = 256, int cap = 4096) {
@@ -281,23 +283,44 @@ __global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, 
 // ---------------------------------------------------------------------
 // level-set advection (Eq. 6) with upwind HJ-WENO5, one RK stage
 
-__device__ inline double hj_deriv(const double *p, int c, int s, double h, bool backward,
+// WENO5-JS value of five differences with one division: the nonlinear
+// weights d_r / t_r (t_r = (eps + b_r)^2) scaled by t0 t1 t2 and the
+// candidates' common 1/6 moved into the final division.  Equal to
+// weno5_plain up to rounding; weno5_plain where the scaled products leave
+// the double range.
+__device__ inline double weno5_hj(double v1, double v2, double v3, double v4, double v5,
+                                  double eps) {
+  double b0 = 13.0 / 12.0 * sqd(v1 - 2.0 * v2 + v3) + 0.25 * sqd(v1 - 4.0 * v2 + 3.0 * v3);
+  double b1 = 13.0 / 12.0 * sqd(v2 - 2.0 * v3 + v4) + 0.25 * sqd(v2 - v4);
+  double b2 = 13.0 / 12.0 * sqd(v3 - 2.0 * v4 + v5) + 0.25 * sqd(3.0 * v3 - 4.0 * v4 + v5);
+  double q0 = 2.0 * v1 - 7.0 * v2 + 11.0 * v3;
+  double q1 = -v2 + 5.0 * v3 + 2.0 * v4;
+  double q2 = 2.0 * v3 + 5.0 * v4 - v5;
+  double t0 = sqd(eps + b0), t1 = sqd(eps + b1), t2 = sqd(eps + b2);
+  double u0 = 0.1 * (t1 * t2), u1 = 0.6 * (t0 * t2), u2 = 0.3 * (t0 * t1);
+  double r = (u0 * q0 + u1 * q1 + u2 * q2) / (6.0 * (u0 + u1 + u2));
+  if (!isfinite(r)) r = weno5_plain(v1, v2, v3, v4, v5, eps);
+  return r;
+}
+
+// upwind HJ-WENO5 derivative along stride s; inv_h = 1 / h
+__device__ inline double hj_deriv(const double *p, int c, int s, double inv_h, bool backward,
                                   double eps) {
   double v[5];
   if (backward) {
 #pragma unroll
     for (int r = 0; r < 5; r++) {
       int m = c + (r - 2) * s;
-      v[r] = (p[m] - p[m - s]) / h;
+      v[r] = (p[m] - p[m - s]) * inv_h;
     }
   } else {
 #pragma unroll
     for (int r = 0; r < 5; r++) {
       int m = c + (2 - r) * s;
-      v[r] = (p[m + s] - p[m]) / h;
+      v[r] = (p[m + s] - p[m]) * inv_h;
     }
   }
-  return weno5_plain(v[0], v[1], v[2], v[3], v[4], eps);
+  return weno5_hj(v[0], v[1], v[2], v[3], v[4], eps);
 }
 
 __global__ void k_ls_stage(Grid g, int s, double a, double b, const double *__restrict__ phi,
@@ -311,8 +334,8 @@ __global__ void k_ls_stage(Grid g, int s, double a, double b, const double *__re
     int c = band[idx];
     double u = u0[c], v = u1[c];
     double px = 0.0, py = 0.0;
-    if (u != 0.0) px = hj_deriv(phi, c, 1, g.dx, u > 0.0, g.weno_eps);
-    if (g.dim == 2 && v != 0.0) py = hj_deriv(phi, c, g.PX, g.dy, v > 0.0, g.weno_eps);
+    if (u != 0.0) px = hj_deriv(phi, c, 1, 1.0 / g.dx, u > 0.0, g.weno_eps);
+    if (g.dim == 2 && v != 0.0) py = hj_deriv(phi, c, g.PX, 1.0 / g.dy, v > 0.0, g.weno_eps);
     double L = -(u * px + v * py);
     tmp[idx] = s == 1 ? phi[c] + dt * L : a * phi0[c] + b * (phi[c] + dt * L);
   }
@@ -379,12 +402,13 @@ __global__ void k_reinit(Grid g, const double *__restrict__ q, const double *__r
       out = q[c] - 0.5 * (sg * fabs(q[c]) - D);
     } else {
       double S = s0 / sqrt(s0 * s0 + h * h);
-      double a = hj_deriv(q, c, 1, g.dx, true, g.weno_eps);
-      double b = hj_deriv(q, c, 1, g.dx, false, g.weno_eps);
+      const double idx_ = 1.0 / g.dx, idy_ = 1.0 / g.dy;
+      double a = hj_deriv(q, c, 1, idx_, true, g.weno_eps);
+      double b = hj_deriv(q, c, 1, idx_, false, g.weno_eps);
       double cc = 0.0, d = 0.0;
       if (d2) {
-        cc = hj_deriv(q, c, g.PX, g.dy, true, g.weno_eps);
-        d = hj_deriv(q, c, g.PX, g.dy, false, g.weno_eps);
+        cc = hj_deriv(q, c, g.PX, idy_, true, g.weno_eps);
+        d = hj_deriv(q, c, g.PX, idy_, false, g.weno_eps);
       }
       double G = -1.0;
       if (s0 > 0.0)

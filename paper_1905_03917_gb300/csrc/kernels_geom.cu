@@ -85,63 +85,104 @@ __device__ inline void append_ballot(bool pred, int value, int *list, int *count
 // ---------------------------------------------------------------------
 // apertures, volume fraction and interface vector; cut-cell list
 
+// geometry of grid point (i, j): the left x-face and bottom y-face of cell
+// (i, j) and, for a cell inside the domain, its volume fraction and
+// interface vector; returns whether the cell is cut
+__device__ inline bool geom_point(const Grid &g, const double *__restrict__ p, int i, int j,
+                                  double *alpha, double *ax, double *ay, double *sx,
+                                  double *sy) {
+  int c = gidx(g, i, j);
+  // away from the interface all nine cells around the four corners share
+  // a sign: every corner has it too, so the cell is full or empty
+  int npos = 0;
+#pragma unroll
+  for (int dj = -1; dj <= 1; dj++)
+#pragma unroll
+    for (int di = -1; di <= 1; di++) npos += p[gidx(g, i + di, j + dj)] >= 0.0;
+  if (npos == 9 || npos == 0) {
+    double v = npos == 9 ? 1.0 : 0.0;
+    if (j < g.ny) ax[c] = v;
+    if (i < g.nx) ay[c] = v;
+    if (i < g.nx && j < g.ny) {
+      alpha[c] = v;
+      sx[c] = 0.0;
+      sy[c] = 0.0;
+    }
+    return false;
+  }
+  double c00 = corner_phi(g, p, i, j);
+  double c01 = corner_phi(g, p, i, j + 1);
+  double c10 = corner_phi(g, p, i + 1, j);
+  if (j < g.ny) ax[c] = edge_fraction(c00, c01);
+  if (i < g.nx) ay[c] = edge_fraction(c00, c10);
+  if (i < g.nx && j < g.ny) {
+    double c11 = corner_phi(g, p, i + 1, j + 1);
+    alpha[c] = cell_alpha(c00, c10, c11, c01);
+    double axl = edge_fraction(c00, c01), axr = edge_fraction(c10, c11);
+    double ayb = edge_fraction(c00, c10), ayt = edge_fraction(c01, c11);
+    double Sx = (axr - axl) * g.dy;
+    double Sy = (ayt - ayb) * g.dx;
+    sx[c] = Sx;
+    sy[c] = Sy;
+    return Sx != 0.0 || Sy != 0.0;
+  }
+  return false;
+}
+
 __global__ void k_geometry(Grid g, const double *__restrict__ p, double *alpha, double *ax,
                            double *ay, double *sx, double *sy, int *cut, int *ncut) {
   SIF_TICK();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int W = g.nx + 1;
   int i = t % W, j = t / W;
-  bool valid = j <= g.ny;
   bool is_cut = false;
   int c = 0;
-  bool uniform = false;
-  if (valid) {
+  if (j <= g.ny) {
     c = gidx(g, i, j);
-    // away from the interface all nine cells around the four corners share
-    // a sign: every corner has it too, so the cell is full or empty
-    int npos = 0;
-#pragma unroll
-    for (int dj = -1; dj <= 1; dj++)
-#pragma unroll
-      for (int di = -1; di <= 1; di++) npos += p[gidx(g, i + di, j + dj)] >= 0.0;
-    if (npos == 9 || npos == 0) {
-      uniform = true;
-      double v = npos == 9 ? 1.0 : 0.0;
-      if (j < g.ny) ax[c] = v;
-      if (i < g.nx) ay[c] = v;
-      if (i < g.nx && j < g.ny) {
-        alpha[c] = v;
-        sx[c] = 0.0;
-        sy[c] = 0.0;
-      }
-    }
-  }
-  if (valid && !uniform) {
-    double c00 = corner_phi(g, p, i, j);
-    double c01 = corner_phi(g, p, i, j + 1);
-    double c10 = corner_phi(g, p, i + 1, j);
-    if (j < g.ny) ax[c] = edge_fraction(c00, c01);
-    if (i < g.nx) ay[c] = edge_fraction(c00, c10);
-    if (i < g.nx && j < g.ny) {
-      double c11 = corner_phi(g, p, i + 1, j + 1);
-      alpha[c] = cell_alpha(c00, c10, c11, c01);
-      double axl = edge_fraction(c00, c01), axr = edge_fraction(c10, c11);
-      double ayb = edge_fraction(c00, c10), ayt = edge_fraction(c01, c11);
-      double Sx = (axr - axl) * g.dy;
-      double Sy = (ayt - ayb) * g.dx;
-      sx[c] = Sx;
-      sy[c] = Sy;
-      is_cut = (Sx != 0.0 || Sy != 0.0);
-    }
+    is_cut = geom_point(g, p, i, j, alpha, ax, ay, sx, sy);
   }
   append_ballot(is_cut, c, cut, ncut);
 }
 
+// the same over the cells of a band list (and the domain's last x-face /
+// y-face next to them): after a level-set step, which moves the interface
+// by less than a cell and changes phi only inside the band, every grid
+// point whose geometry can differ belongs to a cell of the previous band
+__global__ void k_geometry_band(Grid g, const double *__restrict__ p, double *alpha, double *ax,
+                                double *ay, double *sx, double *sy, const int *__restrict__ band,
+                                const int *nband, int *cut, int *ncut) {
+  SIF_TICK();
+  int n = *nband;
+  int nloop = (n + 31) / 32 * 32;  // whole warps for the ballot
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nloop;
+       idx += gridDim.x * blockDim.x) {
+    bool is_cut = false;
+    int c = 0;
+    if (idx < n) {
+      c = band[idx];
+      int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
+      is_cut = geom_point(g, p, i, j, alpha, ax, ay, sx, sy);
+      if (i == g.nx - 1) geom_point(g, p, g.nx, j, alpha, ax, ay, sx, sy);
+      if (j == g.ny - 1) geom_point(g, p, i, g.ny, alpha, ax, ay, sx, sy);
+    }
+    append_ballot(is_cut, c, cut, ncut);
+  }
+}
+
 void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax, double *ay,
-                     double *sx, double *sy, int *cut_list, Scalars *sc, cudaStream_t st) {
+                     double *sx, double *sy, int *cut_list, Scalars *sc, cudaStream_t st,
+                     const int *band, const int *nband, int band_cap) {
   cudaMemsetAsync(&sc->n_cut, 0, sizeof(int), st);
-  int n = (g.nx + 1) * (g.ny + 1);
-  k_geometry<<<(n + 255) / 256, 256, 0, st>>>(g, phi, alpha, ax, ay, sx, sy, cut_list, &sc->n_cut);
+  if (band) {
+    int blocks = (band_cap + 127) / 128;
+    if (blocks > 2432) blocks = 2432;
+    k_geometry_band<<<blocks < 1 ? 1 : blocks, 128, 0, st>>>(g, phi, alpha, ax, ay, sx, sy,
+                                                             band, nband, cut_list, &sc->n_cut);
+  } else {
+    int n = (g.nx + 1) * (g.ny + 1);
+    k_geometry<<<(n + 255) / 256, 256, 0, st>>>(g, phi, alpha, ax, ay, sx, sy, cut_list,
+                                                &sc->n_cut);
+  }
   sif_note_launches(1);
 }
 

@@ -310,8 +310,11 @@ struct GhostSet {
   int n;
 };
 void launch_fill_ghost(const Grid &g, const GhostSet &s, cudaStream_t st);
+// band != null: only the cells of that band list (the band of the phi the
+// geometry was last computed from, with a level-set step since)
 void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax, double *ay,
-                     double *sx, double *sy, int *cut_list, Scalars *sc, cudaStream_t st);
+                     double *sx, double *sy, int *cut_list, Scalars *sc, cudaStream_t st,
+                     const int *band = nullptr, const int *nband = nullptr, int band_cap = 0);
 // counts[0] = band size, counts[1] = band + face neighbours (if rext)
 void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, int *counts,
                        cudaStream_t st);
