@@ -46,6 +46,16 @@ struct sif_ctx {
   // device-driven cycle graphs (conditional nodes) and capture state
   cudaStream_t cap[4];
   int cap_depth, capturing, gerr;
+  // graph branch of the level-set velocity's extension: captured after the
+  // interface interaction beside what follows, joined after the next
+  // finite-volume launch (the capture's dependency set is saved before
+  // the branch and restored after it; the branch's tail is added back at
+  // the join)
+  cudaGraphNode_t br_base[8], br_tail[8];
+  cudaGraphEdgeData br_base_ed[8], br_tail_ed[8];
+  size_t br_nbase, br_ntail;
+  int br_base_has_ed, br_tail_has_ed;
+  int side_pending;
   int use_graphs;
   int graph_bucket;  // band grid size baked into the graphs
   int num_sms;
@@ -327,6 +337,62 @@ static void dbg(sif_ctx *c, const char *phase) {
   if (e != cudaSuccess) fprintf(stderr, "libsif: %s failed: %s\n", phase, cudaGetErrorString(e));
 }
 
+// record the first error of a graph-building call in c->gerr
+#define GCK(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess && !c->gerr) c->gerr = e_; \
+  } while (0)
+
+// a captured branch pending: what is captured next depends on its tail too
+static void side_join(sif_ctx *c) {
+  if (!c->side_pending) return;
+  c->side_pending = 0;
+  GCK(cudaStreamUpdateCaptureDependencies(c->st, c->br_tail,
+                                          c->br_tail_has_ed ? c->br_tail_ed : nullptr,
+                                          c->br_ntail, cudaStreamAddCaptureDependencies));
+}
+
+// capture launch(), which starts from the current dependency set, as a
+// branch: afterwards the capture continues from the same set, and the
+// branch is joined by side_join.  Outside capture launch() just runs.
+template <class F>
+static void side_branch(sif_ctx *c, F launch) {
+  side_join(c);
+  if (!c->capturing) {
+    launch();
+    return;
+  }
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  GCK(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, nullptr, &deps, &ed, &nd));
+  if (c->gerr || nd > 8) {
+    launch();  // no branch (in order)
+    return;
+  }
+  c->br_nbase = nd;
+  c->br_base_has_ed = ed != nullptr;
+  for (size_t i = 0; i < nd; i++) {
+    c->br_base[i] = deps[i];
+    if (ed) c->br_base_ed[i] = ed[i];
+  }
+  launch();
+  GCK(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, nullptr, &deps, &ed, &nd));
+  if (c->gerr || nd > 8) return;  // the branch stays in order
+  c->br_ntail = nd;
+  c->br_tail_has_ed = ed != nullptr;
+  for (size_t i = 0; i < nd; i++) {
+    c->br_tail[i] = deps[i];
+    if (ed) c->br_tail_ed[i] = ed[i];
+  }
+  GCK(cudaStreamUpdateCaptureDependencies(c->st, c->br_base,
+                                          c->br_base_has_ed ? c->br_base_ed : nullptr,
+                                          c->br_nbase, cudaStreamSetCaptureDependencies));
+  if (!c->gerr) c->side_pending = 1;
+}
+
 static void ghost_phi(sif_ctx *c) {
   GhostSet gs = {{c->phi}, {0}, 1};
   launch_fill_ghost(c->g, gs, c->st);
@@ -367,6 +433,7 @@ static int band_work(const sif_ctx *c) {
 
 // small-cell mixing of the fluids in mask (bit k = fluid k)
 static void mix2(sif_ctx *c, int mask, double *const qN[4], double *const qP[4]) {
+  side_join(c);
   launch_mix2(c->g, mask, qN, qP, c->alpha, c->phi, c->band_ev, c->bandmap, &c->sc->n_band,
               c->mix_plan, ncell(c), band_work(c), c->tmp, c->st);
   dbg(c, "mix");
@@ -387,6 +454,7 @@ static void mix_one(sif_ctx *c, int k, double *const q[4]) {
 // set on the device (the last sub-step, whose second stage advances it).
 static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
                  const int *band_flag = nullptr) {
+  side_join(c);
   launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
   launch_prim2(c->g, qs[0], qs[1], c->w[0], c->w[1], c->alpha, c->tiles[0], c->tiles[1],
                ntile(c), c->nostate, c->sc, band_fluid, band_flag, c->band_ev,
@@ -406,9 +474,14 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
   launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, band_work(c), c->xn[0],
                    c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
   dbg(c, "interface");
-  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
-                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
-                    c->sc, c->st);
+  // the level-set velocity's extension is read first by the next level-set
+  // stage: in a captured graph it is a branch beside the finite-volume
+  // stage that follows every interaction step
+  side_branch(c, [&] {
+    launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
+                      band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
+                      c->sc, c->st);
+  });
   dbg(c, "ls_extend");
 }
 
@@ -423,6 +496,7 @@ static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const bas
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
                   c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), c->num_sms, dtp,
                   c->sc, c->st);
+  side_join(c);
   dbg(c, "fv_stage");
 }
 
@@ -434,12 +508,14 @@ static void ls_begin(sif_ctx *c) {
 }
 
 static void ls_stage(sif_ctx *c, int s, const double *dtp) {
+  side_join(c);
   launch_ls_stage(c->g, s, c->cfg.rk_order, c->phi, c->phi0, c->ul[0], c->ul[1], c->band_ls,
                   &c->sc->n_band_ls, ncell(c), c->tmp, dtp, c->st);
   dbg(c, "ls_stage");
 }
 
 static void reinit(sif_ctx *c) {
+  side_join(c);
   launch_reinit(c->g, c->phi, c->phiR, c->rext_ls, &c->sc->n_rext, ncell(c), c->tmp, c->st);
   dbg(c, "reinit");
 }
@@ -482,6 +558,7 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
 }
 
 static int finish(sif_ctx *c, sif_cycle_info *info, unsigned long long upd0) {
+  side_join(c);
   int rc = check_launch(c, "step");
   if (rc) return rc;
   CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
@@ -508,6 +585,7 @@ static int begin_call(sif_ctx *c, double t_end, unsigned long long *upd0) {
     return SIF_ESTATE;
   }
   cudaSetDevice(c->cfg.device);
+  side_join(c);
   CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   *upd0 = c->hsc->updates;
@@ -558,6 +636,7 @@ extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycl
 }
 
 static int read_scalars(sif_ctx *c) {
+  side_join(c);
   CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   c->band_work = c->hsc->n_band;
@@ -603,7 +682,8 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
   for (;;) {
     sub++;
     if (sub > 1) {
-      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
       mix_one(c, f1, c->qi);
       for (int m = 0; m < 4; m++) {
         qs[f1][m] = c->qi[m];
@@ -636,7 +716,8 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
       mix_one(c, f1, c->fut);
       for (int m = 0; m < 4; m++) qs[f1][m] = c->fut[m];
     } else {
-      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
       mix_one(c, f1, c->qi);
       for (int m = 0; m < 4; m++) qs[f1][m] = c->qi[m];
     }
@@ -668,19 +749,12 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
   return SIF_OK;
 }
 
-
 // ---------------------------------------------------------------------
 // device-driven graphs: one CUDA graph runs a whole accelerated cycle;
 // conditional IF nodes follow the scheduler's decisions (single step or
 // cycle, fluid 1's identity, first and last sub-step) and a WHILE node
 // repeats the fluid-2 sub-step, so no host round trip remains inside a
 // cycle.  The kernels are exactly those of the host-driven path.
-
-#define GCK(call)                                  \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess && !c->gerr) c->gerr = e_; \
-  } while (0)
 
 static const int kMaxSubsteps = 4096;
 
@@ -706,6 +780,7 @@ static void cond_node(sif_ctx *c, cudaGraphConditionalHandle h, bool loop, F bod
   const cudaGraphNode_t *deps = nullptr;
   const cudaGraphEdgeData *ed = nullptr;
   size_t nd = 0;
+  side_join(c);  // the side stream joins no graph across a conditional node
   GCK(cudaStreamGetCaptureInfo(c->st, &st, nullptr, &g, &deps, &ed, &nd));
   if (c->gerr) return;
   // the parameter union has no default constructor: zeroed raw storage
@@ -730,6 +805,7 @@ static void cond_node(sif_ctx *c, cudaGraphConditionalHandle h, bool loop, F bod
                                     cudaStreamCaptureModeThreadLocal));
   c->st = inner;
   if (!c->gerr) body();
+  side_join(c);
   c->st = outer;
   cudaGraph_t out = nullptr;
   GCK(cudaStreamEndCapture(inner, &out));
@@ -752,7 +828,8 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   cudaGraphConditionalHandle hnf = new_handle(c);
   launch_cond(COND_NOT_FIRST, c->sc, hnf, 0, 0, 0, c->st);
   cond_node(c, hnf, false, [&] {
-    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
     mix_one(c, f1, c->qi);
     eval(c, qs, f1);
     launch_sched(SCHED_DT2, c->sc, cfl, thr, 0, c->st);
@@ -778,7 +855,8 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
     copy4(c, c->qi, c->fut);
   });
   cond_node(c, hn1, false, [&] {
-    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->st);
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
     mix_one(c, f1, c->qi);
   });
   eval(c, qs, f1, &c->sc->last);
@@ -860,6 +938,7 @@ static int build_graphs(sif_ctx *c) {
   // accelerated cycle
   GCK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
   if (!c->gerr) capture_cycle(c);
+  side_join(c);
   cudaError_t e = cudaStreamEndCapture(c->st, &gc);
   if (!c->gerr && e != cudaSuccess) c->gerr = e;
   // original single-time-step method
@@ -869,6 +948,7 @@ static int build_graphs(sif_ctx *c) {
     launch_sched(SCHED_SINGLE_DT, c->sc, cfl, 0, 0, c->st);
     single_step_after_eval(c, &c->sc->dt);
     launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
+    side_join(c);
     e = cudaStreamEndCapture(c->st, &gs);
     if (!c->gerr && e != cudaSuccess) c->gerr = e;
   }

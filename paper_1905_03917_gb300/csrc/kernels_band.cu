@@ -494,17 +494,20 @@ void launch_record(const Grid &, int shared, const int *cut, int cut_cap, const 
 // ---------------------------------------------------------------------
 // Eq. 7: fluid-1 state at the current fluid-2 time
 
+// Eq. 7 over the cells of a band list: every use of the intermediate
+// fluid-1 state (mixing, the interaction step's stencil states with fluid 1
+// in the band only) reads it inside the band
 __global__ void k_interp(Grid g, double *i0, double *i1, double *i2, double *i3,
                          const double *__restrict__ p0, const double *__restrict__ p1,
                          const double *__restrict__ p2, const double *__restrict__ p3,
                          const double *__restrict__ f0, const double *__restrict__ f1,
                          const double *__restrict__ f2, const double *__restrict__ f3,
-                         const double *thp) {
+                         const double *thp, const int *__restrict__ band, const int *nband) {
   SIF_TICK();
   double th = *thp;
-  int n = g.nx * g.ny;
+  int n = *nband;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    int c = gidx(g, t % g.nx, t / g.nx);
+    int c = band[t];
     i0[c] = (1.0 - th) * p0[c] + th * f0[c];
     i1[c] = (1.0 - th) * p1[c] + th * f1[c];
     i2[c] = (1.0 - th) * p2[c] + th * f2[c];
@@ -513,11 +516,11 @@ __global__ void k_interp(Grid g, double *i0, double *i1, double *i2, double *i3,
 }
 
 void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
-                   double *const fut[4], const double *thp, cudaStream_t st) {
-  int n = g.nx * g.ny;
-  k_interp<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g, qi[0], qi[1], qi[2], qi[3], prev[0],
-                                                      prev[1], prev[2], prev[3], fut[0], fut[1],
-                                                      fut[2], fut[3], thp);
+                   double *const fut[4], const double *thp, const int *band, const int *nband,
+                   int band_cap, cudaStream_t st) {
+  k_interp<<<grid_for(band_cap, 64, 2432), 64, 0, st>>>(g, qi[0], qi[1], qi[2], qi[3], prev[0],
+                                                       prev[1], prev[2], prev[3], fut[0],
+                                                       fut[1], fut[2], fut[3], thp, band, nband);
   sif_note_launches(1);
 }
 
@@ -528,11 +531,13 @@ __global__ void k_correction(Grid g, double *q1, double *q2, double *q3, const d
   SIF_TICK();
   int n = g.nx * g.ny;
   double dxdy = g.dx * g.dy;
+  // cells without a recorded correction would add exactly zero
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     int c = gidx(g, t % g.nx, t / g.nx);
-    q1[c] += c0[c] / dxdy;
-    q2[c] += c1[c] / dxdy;
-    q3[c] += c2[c] / dxdy;
+    double a = c0[c], b = c1[c], d = c2[c];
+    if (a != 0.0) q1[c] += a / dxdy;
+    if (b != 0.0) q2[c] += b / dxdy;
+    if (d != 0.0) q3[c] += d / dxdy;
   }
 }
 

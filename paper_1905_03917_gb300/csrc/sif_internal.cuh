@@ -363,8 +363,10 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
 void launch_record(const Grid &g, int shared, const int *cut, int cut_cap, const double *xn0,
                    const double *xn1, const double *xn2, double *xc0, double *xc1, double *xc2,
                    Scalars *sc, cudaStream_t st);
+// Eq. 7 interpolation of fluid 1 at theta over the cells of a band list
 void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
-                   double *const fut[4], const double *thp, cudaStream_t st);
+                   double *const fut[4], const double *thp, const int *band, const int *nband,
+                   int band_cap, cudaStream_t st);
 void launch_correction(const Grid &g, double *const q[4], const double *xc0, const double *xc1,
                        const double *xc2, cudaStream_t st);
 void launch_init_state(const Grid &g, double *const qN[4], double *const qP[4],
