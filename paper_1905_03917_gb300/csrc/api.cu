@@ -414,6 +414,7 @@ static int band_work(const sif_ctx *c);
 // cell), so only the previous band's cells can change their geometry;
 // otherwise (initial data, a restored or replayed phi) the whole grid.
 static void geometry(sif_ctx *c, bool after_ls = false) {
+  side_join(c);  // the band list changes
   ghost_phi(c);
   const bool band = after_ls && c->g.band >= 3.0;
   launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st,
@@ -443,10 +444,13 @@ static void mix_one(sif_ctx *c, int k, double *const q[4]) {
   mix2(c, 1 << k, k == 0 ? q : nullptr, k == 1 ? q : nullptr);
 }
 
-// interaction step for stage states qs of both fluids and the current phi.
-// The geometry of the current phi is already in place: every change of phi
-// (level-set stage, reinitialisation, initial data, restored state) is
-// followed by geometry() before anything else reads it.
+// interaction step for stage states qs of both fluids and the current phi:
+// stencil states and their extension, interface Riemann problems, exchange
+// flux and the level-set velocity in cut cells (whose extension over the
+// band is ul_extend, run before the stage that follows).  The geometry of
+// the current phi is already in place: every change of phi (level-set
+// stage, reinitialisation, initial data, restored state) is followed by
+// geometry() before anything else reads it.
 //
 // band_fluid >= 0 names a fluid whose stencil states are read only by this
 // interaction step (a sub-step of the other fluid, Sec. 3.1 step 3): its
@@ -474,9 +478,15 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
   launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, band_work(c), c->xn[0],
                    c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
   dbg(c, "interface");
-  // the level-set velocity's extension is read first by the next level-set
-  // stage: in a captured graph it is a branch beside the finite-volume
-  // stage that follows every interaction step
+}
+
+// extension of the level-set velocity set by the last interaction step
+// (its plan, band and sweep buffers stay untouched until a level-set
+// stage, a reinitialisation, a mixing, a geometry or the next interaction
+// step, each of which joins it first).  Called just before the
+// finite-volume stage that follows the interaction step: in a captured
+// graph the sweeps are a branch beside that stage.
+static void ul_extend(sif_ctx *c) {
   side_branch(c, [&] {
     launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
                       band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
@@ -496,7 +506,6 @@ static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const bas
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
                   c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), c->num_sms, dtp,
                   c->sc, c->st);
-  side_join(c);
   dbg(c, "fv_stage");
 }
 
@@ -537,6 +546,7 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
   ls_begin(c);
   for (int s = 1; s <= S; s++) {
     if (s > 1) eval(c, c->q);
+    ul_extend(c);
     if (rec && s == 2) {
       cudaMemcpyAsync(rec->lf2, c->sc->lf, sizeof(c->sc->lf), cudaMemcpyDeviceToDevice, c->st);
       for (int k = 0; k < 2; k++)
@@ -708,6 +718,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     // step 3: fluid-2 and level-set first RK stage with dt2
     copy_planes(c, c->q0[f2], c->q[f2], 4);
     ls_begin(c);
+    ul_extend(c);  // of the cycle's first or this sub-step's interaction step
     fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
     ls_stage(c, 1, &c->sc->dt2);
     geometry(c, true);
@@ -723,6 +734,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     }
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
     eval(c, qs, last ? -1 : f1);
+    ul_extend(c);
     launch_record(c->g, last, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0],
                   c->xc[1], c->xc[2], c->sc, c->st);
     // step 4 (and 5 on the last sub-step): second RK stage
@@ -780,7 +792,7 @@ static void cond_node(sif_ctx *c, cudaGraphConditionalHandle h, bool loop, F bod
   const cudaGraphNode_t *deps = nullptr;
   const cudaGraphEdgeData *ed = nullptr;
   size_t nd = 0;
-  side_join(c);  // the side stream joins no graph across a conditional node
+  side_join(c);  // a pending branch joins before a conditional node
   GCK(cudaStreamGetCaptureInfo(c->st, &st, nullptr, &g, &deps, &ed, &nd));
   if (c->gerr) return;
   // the parameter union has no default constructor: zeroed raw storage
@@ -846,6 +858,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   // step 3: fluid-2 and level-set first RK stage with dt2
   copy4(c, c->q0[f2], c->q[f2]);
   ls_begin(c);
+  ul_extend(c);  // of the cycle's first or this sub-step's interaction step
   fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
   ls_stage(c, 1, &c->sc->dt2);
   geometry(c, true);
@@ -860,6 +873,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
     mix_one(c, f1, c->qi);
   });
   eval(c, qs, f1, &c->sc->last);
+  ul_extend(c);
   launch_record(c->g, -2, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 4 (and 5 on the last sub-step): second RK stage
