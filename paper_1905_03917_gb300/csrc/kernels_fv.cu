@@ -179,48 +179,50 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
   }
   __syncthreads();
 
-  // phase 2: x faces (left face of cell i0 + fi), one (face, component) per item
+  // phase 2: one (face, component) per item, x faces (left face of cell
+  // i0 + fi) then y faces (bottom face of cell j0 + fj) in one item range,
+  // so that no thread takes more than one item above the CTA's average
   const double eps = g.weno_eps;
-  for (int r = tid; r < 4 * (SX + 1) * SY; r += nth) {
-    int m = r / ((SX + 1) * SY), f = r % ((SX + 1) * SY);
-    int fi = f % (SX + 1), fj = f / (SX + 1);
-    int i = i0 + fi, j = j0 + fj;
-    double val = 0.0;
-    if (i <= g.nx && j < g.ny) {
-      double A_ = A.ax[gidx(g, i, j)];
-      if (k == 0) A_ = 1.0 - A_;
-      if (A_ != 0.0) {
-        // cells i-3..i+2 are at halo columns fi..fi+5
-        const double *P = fxp + m * HX * SY + fj * HX + fi;
-        const double *M = fxm + m * HX * SY + fj * HX + fi;
-        double nl, dl, nr, dr;
-        weno5_frac(P[0], P[1], P[2], P[3], P[4], eps, nl, dl);
-        weno5_frac(M[5], M[4], M[3], M[2], M[1], eps, nr, dr);
-        val = face_value(A_, nl, dl, nr, dr);
-      }
-    }
-    Fx[m * (SX + 1) * SY + f] = val;
-  }
-  if (d2) {
-    for (int r = tid; r < 4 * SX * (SY + 1); r += nth) {
-      int m = r / (SX * (SY + 1)), f = r % (SX * (SY + 1));
+  constexpr int NXI = 4 * (SX + 1) * SY;
+  const int NI = NXI + (d2 ? 4 * SX * (SY + 1) : 0);
+  for (int r = tid; r < NI; r += nth) {
+    const double *P, *M;
+    double *out;
+    int st;
+    bool open;
+    double A_ = 0.0;
+    if (r < NXI) {
+      int m = r / ((SX + 1) * SY), f = r % ((SX + 1) * SY);
+      int fi = f % (SX + 1), fj = f / (SX + 1);
+      int i = i0 + fi, j = j0 + fj;
+      open = i <= g.nx && j < g.ny;
+      if (open) A_ = A.ax[gidx(g, i, j)];
+      // cells i-3..i+2 are at halo columns fi..fi+5
+      P = fxp + m * HX * SY + fj * HX + fi;
+      M = fxm + m * HX * SY + fj * HX + fi;
+      st = 1;
+      out = Fx + m * (SX + 1) * SY + f;
+    } else {
+      int q = r - NXI;
+      int m = q / (SX * (SY + 1)), f = q % (SX * (SY + 1));
       int fi = f % SX, fj = f / SX;
       int i = i0 + fi, j = j0 + fj;
-      double val = 0.0;
-      if (i < g.nx && j <= g.ny) {
-        double A_ = A.ay[gidx(g, i, j)];
-        if (k == 0) A_ = 1.0 - A_;
-        if (A_ != 0.0) {
-          const double *P = fyp + m * SX * HY + fj * SX + fi;
-          const double *M = fym + m * SX * HY + fj * SX + fi;
-          double nl, dl, nr, dr;
-          weno5_frac(P[0], P[SX], P[2 * SX], P[3 * SX], P[4 * SX], eps, nl, dl);
-          weno5_frac(M[5 * SX], M[4 * SX], M[3 * SX], M[2 * SX], M[SX], eps, nr, dr);
-          val = face_value(A_, nl, dl, nr, dr);
-        }
-      }
-      Fy[m * SX * (SY + 1) + f] = val;
+      open = i < g.nx && j <= g.ny;
+      if (open) A_ = A.ay[gidx(g, i, j)];
+      P = fyp + m * SX * HY + fj * SX + fi;
+      M = fym + m * SX * HY + fj * SX + fi;
+      st = SX;
+      out = Fy + m * SX * (SY + 1) + f;
     }
+    if (k == 0) A_ = 1.0 - A_;
+    double val = 0.0;
+    if (open && A_ != 0.0) {
+      double nl, dl, nr, dr;
+      weno5_frac(P[0], P[st], P[2 * st], P[3 * st], P[4 * st], eps, nl, dl);
+      weno5_frac(M[5 * st], M[4 * st], M[3 * st], M[2 * st], M[st], eps, nr, dr);
+      val = face_value(A_, nl, dl, nr, dr);
+    }
+    *out = val;
   }
   __syncthreads();
 
@@ -261,7 +263,8 @@ struct FvHalf {
 };
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(FvShape<TX, TY>::threads) k_fv_stage(FvArgs A) {
+__global__ void __launch_bounds__(FvShape<TX, TY>::threads, 1536 / FvShape<TX, TY>::threads)
+k_fv_stage(FvArgs A) {
   SIF_TICK();
   const Grid &g = A.g;
   const int ntiles = A.ntiles[A.k];
