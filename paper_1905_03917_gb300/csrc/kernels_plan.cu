@@ -405,7 +405,11 @@ __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__
     for (int k = 0; k < 2; k++) {
       if (!(mask & (1 << k))) continue;
       MixPlan s;
-      mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s);
+      if (!mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s)) {
+        // not a source: the apply kernel reads only the target count
+        plan[(size_t)k * cap + idx].nt = 0;
+        continue;
+      }
       double *const *q = Q.q[k];
       for (int t = 0; t < s.nt; t++) {
         int tc = s.tc[t];
