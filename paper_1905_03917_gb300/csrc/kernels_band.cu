@@ -83,6 +83,7 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
   }
   const double *q0 = P.q[k][0], *q1 = P.q[k][1], *q2 = P.q[k][2], *q3 = P.q[k][3];
   double *w0 = P.w[k][0], *w1 = P.w[k][1], *w2 = P.w[k][2], *w3 = P.w[k][3];
+  const double idx_ = 1.0 / g.dx, idy_ = 1.0 / g.dy;
   double lx = 0.0, ly = 0.0, sm = 0.0;
   if (valid) {
     double a = vol_k(alpha, k, c);
@@ -112,8 +113,10 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
         double cs = sqrt(fmax(gm * (p + pi) * (a * iq), 0.0));
         lx = fabs(u) + cs;
         ly = fabs(v) + cs;
-        double s = (fabs(u) + cs) / g.dx;
-        if (g.dim == 2) s += (fabs(v) + cs) / g.dy;
+        // CFL rate (|u| + c) / dx + (|v| + c) / dy with the reciprocals
+        // taken once (an ulp from the quotients in the step size)
+        double s = lx * idx_;
+        if (g.dim == 2) s += ly * idy_;
         sm = s;
       }
     }
