@@ -415,7 +415,9 @@ static int band_work(const sif_ctx *c);
 // otherwise (initial data, a restored or replayed phi) the whole grid.
 static void geometry(sif_ctx *c, bool after_ls = false) {
   side_join(c);  // the band list changes
-  ghost_phi(c);
+  // a level-set stage and the reinitialisation write phi's ghost images
+  // with its band values; anything else that sets phi needs the fill
+  if (!after_ls) ghost_phi(c);
   const bool band = after_ls && c->g.band >= 3.0;
   launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st,
                   band ? c->band_ev : nullptr, band ? &c->sc->n_band : nullptr,

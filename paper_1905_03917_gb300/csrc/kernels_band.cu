@@ -283,6 +283,28 @@ __global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, 
   }
 }
 
+// the level set's new band values, each also written to the ghost cells
+// whose image it is (the values the ghost fill would give them): phi
+// changes only through these writes, so its ghost layers stay filled
+__global__ void k_band_scatter_phi(Grid g, const int *__restrict__ band, const int *nband,
+                                   const double *tmp, double *phi) {
+  SIF_TICK();
+  int n = *nband;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    int c = band[idx];
+    int a = (c % g.PX) - SIF_GH, b = (c / g.PX) - SIF_GH;
+    double v = tmp[idx];
+    phi[c] = v;
+    if (a >= SIF_GH && a < g.nx - SIF_GH && b >= SIF_GH && b < g.ny - SIF_GH) continue;
+    int xs[1 + 2 * SIF_GH], ys[1 + 2 * SIF_GH];
+    int nx_ = ghost_preimages(a, g.nx, g.bc[0], g.bc[1], xs);
+    int ny_ = ghost_preimages(b, g.ny, g.bc[2], g.bc[3], ys);
+    for (int p = 0; p < nx_; p++)
+      for (int q = 0; q < ny_; q++)
+        if (p || q) phi[gidx(g, xs[p], ys[q])] = v;
+  }
+}
+
 // ---------------------------------------------------------------------
 // level-set advection (Eq. 6) with upwind HJ-WENO5, one RK stage
 
@@ -351,10 +373,9 @@ void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *ph
   static const double A3[4] = {0.0, 0.0, 0.75, 1.0 / 3.0}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
   double a = rk == 3 ? A3[s] : A2[s], b = rk == 3 ? B3[s] : B2[s];
   int blocks = grid_for(band_cap, 64, 2432);
-  GhostSet gs = {{phi}, {0}, 1};
-  launch_fill_ghost(g, gs, st);
+  // phi's ghost layers are current: every change of phi fills them
   k_ls_stage<<<blocks, 64, 0, st>>>(g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
-  k_band_scatter2<<<blocks, 64, 0, st>>>(band, nband, tmp, phi, nullptr);
+  k_band_scatter_phi<<<blocks, 64, 0, st>>>(g, band, nband, tmp, phi);
   sif_note_launches(2);
 }
 
@@ -446,14 +467,13 @@ __global__ void k_copy_plane(const double *src, double *dst, size_t n) {
 
 void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, const int *nrext,
                    int rext_cap, double *tmp, cudaStream_t st) {
-  GhostSet gs = {{phi}, {0}, 1};
-  launch_fill_ghost(g, gs, st);
+  // phi's ghost layers are current (every change of phi fills them), so
+  // the copy carries them too
   cudaMemcpyAsync(phi0, phi, sizeof(double) * (size_t)g.PX * g.PY, cudaMemcpyDeviceToDevice, st);
   int blocks = grid_for(rext_cap, 64, 2432);
   for (int it = 0; it < g.reinit_iters; it++) {
-    if (it > 0) launch_fill_ghost(g, gs, st);
     k_reinit<<<blocks, 64, 0, st>>>(g, phi, phi0, rext, nrext, tmp);
-    k_band_scatter2<<<blocks, 64, 0, st>>>(rext, nrext, tmp, phi, nullptr);
+    k_band_scatter_phi<<<blocks, 64, 0, st>>>(g, rext, nrext, tmp, phi);
   }
   sif_note_launches(2 * g.reinit_iters);
 }

@@ -14,28 +14,8 @@
 // the same values as filling the x ghosts of the interior rows first and
 // then the y ghosts of every column from them
 
-__device__ inline int ghost_image(int i, int n, int bl, int br, bool &flip) {
-  flip = false;
-  if (i < 0) {
-    int m = -1 - i;
-    if (bl == SIF_BC_REFLECT) {
-      flip = true;
-      return m;
-    }
-    return bl == SIF_BC_PERIODIC ? n - 1 - m : 0;
-  }
-  if (i >= n) {
-    int m = i - n;
-    if (br == SIF_BC_REFLECT) {
-      flip = true;
-      return n - 1 - m;
-    }
-    return br == SIF_BC_PERIODIC ? m : n - 1;
-  }
-  return i;
-}
-
 __global__ void k_ghost(Grid g, GhostSet s) {
+  SIF_TICK();
   int W = g.nx + 2 * SIF_GH;
   // ghost cells: the top and bottom strips (full width) and the left and
   // right strips of the interior rows

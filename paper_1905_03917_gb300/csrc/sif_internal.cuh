@@ -196,6 +196,43 @@ __device__ inline void unit_normal(const Grid &g, const double *p, int i, int j,
   }
 }
 
+// index of the interior cell whose value ghost index i (of n interior
+// cells, boundary kinds bl / br) takes, and whether a reflecting wall lies
+// between them (the velocity component normal to it changes sign)
+__device__ inline int ghost_image(int i, int n, int bl, int br, bool &flip) {
+  flip = false;
+  if (i < 0) {
+    int m = -1 - i;
+    if (bl == SIF_BC_REFLECT) {
+      flip = true;
+      return m;
+    }
+    return bl == SIF_BC_PERIODIC ? n - 1 - m : 0;
+  }
+  if (i >= n) {
+    int m = i - n;
+    if (br == SIF_BC_REFLECT) {
+      flip = true;
+      return n - 1 - m;
+    }
+    return br == SIF_BC_PERIODIC ? m : n - 1;
+  }
+  return i;
+}
+
+// the indices along one direction that take interior cell a's value: a
+// itself and the ghost indices whose image is a (at most 1 + 2 SIF_GH)
+__device__ inline int ghost_preimages(int a, int n, int bl, int br, int out[1 + 2 * SIF_GH]) {
+  int k = 0;
+  out[k++] = a;
+  for (int m = 0; m < SIF_GH; m++) {
+    bool f;
+    if (ghost_image(-1 - m, n, bl, br, f) == a) out[k++] = -1 - m;
+    if (ghost_image(n + m, n, bl, br, f) == a) out[k++] = n + m;
+  }
+  return k;
+}
+
 __device__ inline bool inside(const Grid &g, int i, int j) {
   return i >= 0 && i < g.nx && j >= 0 && j < g.ny;
 }
