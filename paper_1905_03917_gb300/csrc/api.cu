@@ -445,6 +445,11 @@ static void mix_both(sif_ctx *c) { mix2(c, 3, c->q[0], c->q[1]); }
 static void mix_one(sif_ctx *c, int k, double *const q[4]) {
   mix2(c, 1 << k, k == 0 ? q : nullptr, k == 1 ? q : nullptr);
 }
+// both fluids on the same geometry in one mixing pass: fluid 1's state q1,
+// the other fluid's q2 (the fluids' mixings are independent)
+static void mix_pair(sif_ctx *c, int f1, double *const q1[4], double *const q2[4]) {
+  mix2(c, 3, f1 == 0 ? q1 : q2, f1 == 0 ? q2 : q1);
+}
 
 // interaction step for stage states qs of both fluids and the current phi:
 // stencil states and their extension, interface Riemann problems, exchange
@@ -724,14 +729,13 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
     ls_stage(c, 1, &c->sc->dt2);
     geometry(c, true);
-    mix_one(c, f2, c->q[f2]);
     if (last) {
-      mix_one(c, f1, c->fut);
+      mix_pair(c, f1, c->fut, c->q[f2]);
       for (int m = 0; m < 4; m++) qs[f1][m] = c->fut[m];
     } else {
       launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
                   band_work(c), c->st);
-      mix_one(c, f1, c->qi);
+      mix_pair(c, f1, c->qi, c->q[f2]);
       for (int m = 0; m < 4; m++) qs[f1][m] = c->qi[m];
     }
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
@@ -864,15 +868,14 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
   ls_stage(c, 1, &c->sc->dt2);
   geometry(c, true);
-  mix_one(c, f2, c->q[f2]);
   cond_node(c, hl1, false, [&] {
-    mix_one(c, f1, c->fut);
+    mix_pair(c, f1, c->fut, c->q[f2]);
     copy4(c, c->qi, c->fut);
   });
   cond_node(c, hn1, false, [&] {
     launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
                   band_work(c), c->st);
-    mix_one(c, f1, c->qi);
+    mix_pair(c, f1, c->qi, c->q[f2]);
   });
   eval(c, qs, f1, &c->sc->last);
   ul_extend(c);
