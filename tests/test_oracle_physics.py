@@ -233,3 +233,67 @@ def test_shock_bubble_runs_through_the_interaction(multi):
     X, Y = np.meshgrid(np.arange(128) * case["cfg"]["dx"], np.arange(32) * case["cfg"]["dy"])
     cx, cy = X[neg].mean(), Y[neg].mean()
     assert np.max(np.hypot(X[neg] - cx, Y[neg] - cy)) < 0.4
+
+
+def _mixture(o):
+    qN, qP, _ = o.state()
+    return np.concatenate([(qN[0] + qP[0]).ravel(), (qN[3] + qP[3]).ravel()])
+
+
+def test_multi_and_single_dt_meet_as_the_step_shrinks():
+    """Both forms discretise the same semi-discrete system: at a fixed time
+    their difference shrinks monotonically with the CFL number (the gas
+    sub-cycles twice per water step in this tube)."""
+    c = inputs.shock_tube_1d(400, rk_order=2)
+    T = 1.0e-4
+    diffs = []
+    for cfl in (0.6, 0.3, 0.15, 0.075):
+        cfg = dict(c["cfg"], cfl=cfl)
+        runs = []
+        for multi in (False, True):
+            o = O.Oracle(cfg).init(c["phi"], c["prim_N"], c["prim_P"])
+            subs = []
+            while o.t < T * (1 - 1e-14):
+                info = (o.step_multi_dt if multi else o.step_single_dt)(1, T)
+                subs.append(info["substeps"])
+            assert o.status == 0
+            runs.append(_mixture(o))
+            if multi:
+                assert max(subs) >= 2
+        diffs.append(np.abs(runs[1] - runs[0]).sum() / np.abs(runs[0]).sum())
+    assert all(b < a for a, b in zip(diffs, diffs[1:])), diffs
+    assert diffs[-1] < 0.3 * diffs[0], diffs
+
+
+def test_mirror_symmetry_of_centred_explosion():
+    """A gas bubble at the centre of a reflective box stays symmetric about
+    both axes (x-momentum odd in x, y-momentum odd in y)."""
+    c = inputs.underwater_explosion(64)
+    for multi in (False, True):
+        o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+        for _ in range(40):
+            o.step_multi_dt(1) if multi else o.step_single_dt(1)
+        assert o.status == 0
+        qN, qP, phi = o.state()
+        for q in (qN, qP):
+            mass = np.abs(q[0]).sum()
+            for m, sx, sy in ((0, 1, 1), (1, -1, 1), (2, 1, -1), (3, 1, 1)):
+                scale = max(np.abs(q[m]).sum(), mass if m in (1, 2) else 0.0, 1e-300)
+                ax = np.abs(q[m] - sx * q[m][:, ::-1]).sum() / scale
+                ay = np.abs(q[m] - sy * q[m][::-1, :]).sum() / scale
+                assert ax <= 1e-12 and ay <= 1e-12, (multi, m, ax, ay)
+        assert np.abs(phi - phi[:, ::-1]).max() <= 1e-12
+        assert np.abs(phi - phi[::-1, :]).max() <= 1e-12
+
+
+def test_reflective_box_conserves_mass_and_energy():
+    """Walls exchange momentum but no mass or energy: the multi-time-step
+    cycle with the correction keeps both totals of the two fluids."""
+    c = inputs.underwater_explosion(48)
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    I0 = o.integrals().sum(0)
+    subs = [o.step_multi_dt(1)["substeps"] for _ in range(40)]
+    assert o.status == 0 and max(subs) >= 2
+    I1 = o.integrals().sum(0)
+    assert abs(I1[0] - I0[0]) <= 1e-13 * abs(I0[0])
+    assert abs(I1[3] - I0[3]) <= 1e-13 * abs(I0[3])
