@@ -138,10 +138,12 @@ def _tube_errors(n, rk, multi, T=2e-4):
 
 @pytest.mark.parametrize("rk,multi", [(3, False), (2, False), (2, True)])
 def test_shock_tube_converges_to_exact_solution(rk, multi):
-    e200, c200 = _tube_errors(200, rk, multi)
-    e400, c400 = _tube_errors(400, rk, multi)
-    assert e400 < 0.8 * e200, (e200, e400)
-    assert c200 <= 2.0 and c400 <= 2.0
+    """L1 error of the mixture density against the cell-averaged exact
+    solution falls at every refinement from 200 to 1600 cells (about first
+    order at the discontinuities), and the contact sits within 2 cells."""
+    errs, cons = zip(*(_tube_errors(n, rk, multi) for n in (200, 400, 800, 1600)))
+    assert all(b < 0.8 * a for a, b in zip(errs, errs[1:])), errs
+    assert max(cons) <= 2.0, cons
 
 
 def test_level_set_rigid_translation():
