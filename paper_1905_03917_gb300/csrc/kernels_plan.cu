@@ -76,13 +76,14 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
                             int cap, const unsigned char *__restrict__ ns0,
                             const unsigned char *__restrict__ ns1, ExtFields F, double *sweep0) {
   SIF_TICK();
+  const int f = blockIdx.y;  // field: W_N, W_P, level-set velocity
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
     int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
     double nxv, nyv;
     unit_normal(g, phi, i, j, nxv, nyv);
-    for (int f = 0; f < 3; f++) {
+    {
       ExtPlan pl = {-1, -1, -1, -1, 0.0, 0.0};
       bool target;
       double dx_, dy_;
@@ -150,9 +151,9 @@ void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, con
       F.p[0][m] = wN[m];
       F.p[1][m] = wP[m];
     }
-  k_ext_setup<<<blocks_for(work, 64), 64, 0, st>>>(g, alpha, phi, sx, sy, band, nband, map,
-                                                    plan, cap, nostate[0], nostate[1], F,
-                                                    sweep0);
+  // one block row per field
+  k_ext_setup<<<dim3(blocks_for(work, 64), 3), 64, 0, st>>>(
+      g, alpha, phi, sx, sy, band, nband, map, plan, cap, nostate[0], nostate[1], F, sweep0);
   sif_note_launches(1);
 }
 
@@ -398,27 +399,26 @@ __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__
                             const double *__restrict__ phi, const int *__restrict__ band,
                             const int *nband, MixPlan *plan, int cap) {
   SIF_TICK();
+  const int k = blockIdx.y;  // fluid
+  if (!(mask & (1 << k))) return;
   int n = *nband;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
     int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
-    for (int k = 0; k < 2; k++) {
-      if (!(mask & (1 << k))) continue;
-      MixPlan s;
-      if (!mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s)) {
-        // not a source: the apply kernel reads only the target count
-        plan[(size_t)k * cap + idx].nt = 0;
-        continue;
-      }
-      double *const *q = Q.q[k];
-      for (int t = 0; t < s.nt; t++) {
-        int tc = s.tc[t];
-        double den = s.as * s.beta[t] + s.at[t];
-        for (int m = 0; m < 4; m++)
-          s.M[t][m] = s.beta[t] * (q[m][tc] * s.as - q[m][c] * s.at[t]) / den;
-      }
-      plan[(size_t)k * cap + idx] = s;
+    MixPlan s;
+    if (!mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s)) {
+      // not a source: the apply kernel reads only the target count
+      plan[(size_t)k * cap + idx].nt = 0;
+      continue;
     }
+    double *const *q = Q.q[k];
+    for (int t = 0; t < s.nt; t++) {
+      int tc = s.tc[t];
+      double den = s.as * s.beta[t] + s.at[t];
+      for (int m = 0; m < 4; m++)
+        s.M[t][m] = s.beta[t] * (q[m][tc] * s.as - q[m][c] * s.at[t]) / den;
+    }
+    plan[(size_t)k * cap + idx] = s;
   }
 }
 
@@ -491,7 +491,7 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
   }
   // small blocks spread the band's few thousand cells over the SMs
   int b = blocks_for(work, 64);
-  k_mix_setup<<<b, 64, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
+  k_mix_setup<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
   k_mix_apply<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, map, plan, cap, band, nband);
   sif_note_launches(2);
 }
