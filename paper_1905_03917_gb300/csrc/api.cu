@@ -953,7 +953,7 @@ static int build_graphs(sif_ctx *c) {
   c->capturing = 1;
   c->cap_depth = 0;
   cudaGraph_t gc = nullptr, gs = nullptr;
-  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  const double cfl = c->g.cfl;
   // accelerated cycle
   GCK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
   if (!c->gerr) capture_cycle(c);
@@ -1755,7 +1755,7 @@ extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cel
     int rc = begin_call(c, 0.0, &upd0[i]);
     if (rc == SIF_OK) rc = ensure_graphs(c);
     if (rc != SIF_OK) {
-      snprintf(b->err, sizeof(b->err), "instance %d: graph set-up failed: %s", i, c->err);
+      snprintf(b->err, sizeof(b->err), "instance %d: graph set-up failed: %.200s", i, c->err);
       return rc == SIF_OK ? SIF_ECUDA : rc;
     }
     if (b->exec && b->gens.size() == (size_t)b->n && b->gens[i] != c->graph_gen) rebuild = true;
@@ -1781,7 +1781,7 @@ extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cel
     total += (long long)(b->ctx[i]->hsc->updates - upd0[i]);
     if (rc != SIF_OK && first_rc == SIF_OK) {
       first_rc = rc;
-      snprintf(b->err, sizeof(b->err), "instance %d: %s", i, b->ctx[i]->err);
+      snprintf(b->err, sizeof(b->err), "instance %d: %.200s", i, b->ctx[i]->err);
     }
   }
   if (cell_updates) *cell_updates = total;

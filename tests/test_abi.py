@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_entry_points():
-    txt = open(os.path.join(ROOT, "include", "sif.h")).read()
+    with open(os.path.join(ROOT, "include", "sif.h")) as f:
+        txt = f.read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(sif_[a-z_0-9]+)\s*\(", txt)))
 
@@ -26,7 +27,8 @@ def test_library_exports_every_declared_entry_point():
 
 
 def test_config_struct_matches_header_field_order():
-    txt = open(os.path.join(ROOT, "include", "sif.h")).read()
+    with open(os.path.join(ROOT, "include", "sif.h")) as f:
+        txt = f.read()
     body = txt[txt.index("typedef struct {\n  int dim;"):]
     body = body[:body.index("} sif_config;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)

@@ -47,7 +47,11 @@ def _rank_main(rank, world, port, out_dir, what):
 def _spawn(tmp_path, what, world=2):
     port = _free_port()
     mp.spawn(_rank_main, args=(world, port, str(tmp_path), what), nprocs=world, join=True)
-    return [open(tmp_path / f"rank{r}.txt").read() for r in range(world)]
+    outs = []
+    for r in range(world):
+        with open(tmp_path / f"rank{r}.txt") as f:
+            outs.append(f.read())
+    return outs
 
 
 def test_two_ranks_report_max_time_and_summed_updates(tmp_path):

@@ -15,7 +15,9 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden", "toro_ideal_gas_riemann
 
 def _toro_rows():
     rows = []
-    for line in open(GOLD):
+    with open(GOLD) as f:
+        lines = f.readlines()
+    for line in lines:
         if line.startswith("#") or not line.strip():
             continue
         a, b = line.split("|")
