@@ -496,11 +496,13 @@ __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncu
     int c = cut[idx];
     const double *xs[3] = {x0, x1, x2};
     double *cs[3] = {c0, c1, c2};
+    // explicitly rounded products and sums (never contracted into FMAs):
+    // with dt1 = dt2 the fluid-1 and fluid-2 records must cancel exactly
     for (int m = 0; m < 3; m++) {
-      double xv = sgn * xs[m][c];
+      double xv = __dmul_rn(sgn, xs[m][c]);
       double acc = cs[m][c];
-      if (shared) acc = acc + (-0.5 * xv) * dt1;
-      acc = acc + (0.5 * xv) * dt2;
+      if (shared) acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(-0.5, xv), dt1));
+      acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(0.5, xv), dt2));
       cs[m][c] = acc;
     }
   }
