@@ -183,11 +183,29 @@ __device__ void ext_fold_lf(double lx, double ly, unsigned long long *lf) {
   }
 }
 
-// One Jacobi sweep.  With writeback (a sweep after the first: band cells
-// read only the previous sweep's buffer) the results go straight to the
-// planes, and the extended stencil states fold their wave speeds into the
-// Lax-Friedrichs maxima, as k_ext_scatter would.  The band position and
-// plan of a thread's first cell are loaded together with the band count.
+// value of band cell `cell` (band position bp, plan px) after one Jacobi
+// sweep from the values b of the previous sweep (the planes a when b is
+// null): the upwind-weighted mean of its upwind neighbours for a target,
+// its own value otherwise
+__device__ __forceinline__ double ext_one(const ExtPlan &px, int bp, int cell, const double *a,
+                                          const double *b) {
+  if (px.cx < 0 && px.cy < 0) return b ? b[bp] : a[cell];
+  double v = 0.0;
+  if (px.cx >= 0) v += px.wx * ((b && px.bx >= 0) ? b[px.bx] : a[px.cx]);
+  if (px.cy >= 0) v += px.wy * ((b && px.by >= 0) ? b[px.by] : a[px.cy]);
+  return v;
+}
+
+// S (1 or 2) Jacobi sweeps in one launch.  With S = 2 a target recomputes
+// its upwind neighbours' intermediate values from their plans (the same
+// operations as the sweep in between), which takes one dependent load
+// level more and one launch fewer.  With writeback (a launch whose first
+// sweep is not the first: band cells then read only the previous sweep's
+// buffer) the results go straight to the planes, and the extended stencil
+// states fold their wave speeds into the Lax-Friedrichs maxima, as
+// k_ext_scatter would.  The band position and plan of a thread's first
+// cell are loaded together with the band count.
+template <int S>
 __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ plan, int cap,
                             const int *__restrict__ band, const int *nband,
                             const double *__restrict__ src, double *dst, int writeback,
@@ -209,6 +227,12 @@ __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ pla
   for (int idx = idx0; idx < n; idx += gridDim.x * blockDim.x) {
     int c = idx == idx0 ? c0 : band[idx];
     ExtPlan pl = idx == idx0 ? pl0 : P[idx];
+    // the upwind neighbours' plans (two sweeps: their intermediate values)
+    const bool hx = S == 2 && pl.cx >= 0 && pl.bx >= 0;
+    const bool hy = S == 2 && pl.cy >= 0 && pl.by >= 0;
+    ExtPlan px = {-1, -1, -1, -1, 0.0, 0.0}, py = {-1, -1, -1, -1, 0.0, 0.0};
+    if (hx) px = P[pl.bx];
+    if (hy) py = P[pl.by];
     double out[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int m = 0; m < 4; m++) {
@@ -216,12 +240,14 @@ __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ pla
       const double *a = F.p[f][m];
       const double *b = src ? src + slot + (size_t)m * cap : nullptr;
       double v;
-      if (pl.cx < 0 && pl.cy < 0) {
+      if (S == 1) {
+        v = ext_one(pl, idx, c, a, b);
+      } else if (pl.cx < 0 && pl.cy < 0) {
         v = b ? b[idx] : a[c];
       } else {
         v = 0.0;
-        if (pl.cx >= 0) v += pl.wx * ((b && pl.bx >= 0) ? b[pl.bx] : a[pl.cx]);
-        if (pl.cy >= 0) v += pl.wy * ((b && pl.by >= 0) ? b[pl.by] : a[pl.cy]);
+        if (pl.cx >= 0) v += pl.wx * (hx ? ext_one(px, pl.bx, pl.cx, a, b) : a[pl.cx]);
+        if (pl.cy >= 0) v += pl.wy * (hy ? ext_one(py, pl.by, pl.cy, a, b) : a[pl.cy]);
       }
       out[m] = v;
     }
@@ -289,22 +315,38 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
   }
   dim3 grid(blocks_for(work, 64), nf);
   double *buf[2] = {tmp, tmp + (size_t)8 * cap};
-  // first_done: sweep 0 is already in buf[0] (written by k_ext_setup)
+  // first_done: sweep 0 is already in buf[0] (written by k_ext_setup).
+  // The stencil states' remaining sweeps (on the interaction step's
+  // critical path) go two per launch, one first when their number is odd;
+  // the level-set velocity's (a graph branch beside the finite-volume
+  // stage, where a heavier kernel slows the stage) one per launch.  The
+  // last launch writes the planes itself unless its first sweep is the
+  // very first (which reads band neighbours from the planes it would
+  // overwrite), in which case the scatter writes them back.
   const double *src = first_done ? buf[0] : nullptr;
   int cur = first_done ? 1 : 0;
-  // the last sweep writes the planes itself when it is not the first
-  // (the first reads band neighbours from the planes it would overwrite)
   const int iters = g.ext_iters;
+  int remaining = iters - (first_done ? 1 : 0);
   int launched = 0;
-  for (int it = first_done ? 1 : 0; it < iters; it++) {
-    const int wb = it == iters - 1 && it > 0;
-    k_ext_sweep<<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur], wb, alpha,
-                                      nostate[0], nostate[1], sc);
+  while (remaining > 0) {
+    const int S = (f0 == 0 && remaining % 2 == 0) ? 2 : 1;
+    const int wb = remaining == S && src != nullptr;
+    if (S == 1)
+      k_ext_sweep<1><<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur], wb,
+                                          alpha, nostate[0], nostate[1], sc);
+    else
+      k_ext_sweep<2><<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur], wb,
+                                          alpha, nostate[0], nostate[1], sc);
+    remaining -= S;
+    launched++;
+    if (wb) {
+      src = nullptr;  // written back
+      break;
+    }
     src = buf[cur];
     cur ^= 1;
-    launched++;
   }
-  if (iters <= 1 && src) {
+  if (src) {
     k_ext_scatter<<<grid, 64, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
                                         nostate[1], sc);
     launched++;
