@@ -313,12 +313,20 @@ bool fv_shape_supported(int tx, int ty) {
 
 // opt every instantiation into its shared-memory size on the current
 // device (outside any stream capture)
+// launch priority of the finite-volume stage: the device's greatest, so
+// that its pending CTAs go before those of work branched beside it (the
+// level-set velocity's extension in a captured cycle)
+static int g_fv_priority = 0;
+
 void fv_prepare() {
 #define FV_PREP(a, b)                                                                   \
   cudaFuncSetAttribute(k_fv_stage<a, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                        (int)FvShape<a, b>::smem());
   FV_SHAPES(FV_PREP)
 #undef FV_PREP
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess) g_fv_priority = greatest;
+  cudaGetLastError();
 }
 
 void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
@@ -354,10 +362,20 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   A.sc = sc;
   A.split_below = num_sms;
   const int grid = tile_cap > 2 * num_sms ? tile_cap : 2 * num_sms;
-#define FV_LAUNCH(a, b)                                                             \
-  if (g.tx == a && g.ty == b) {                                                    \
-    k_fv_stage<a, b><<<grid, FvShape<a, b>::threads, FvShape<a, b>::smem(), st>>>(A); \
-    return;                                                                        \
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributePriority;
+  at.val.priority = g_fv_priority;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+#define FV_LAUNCH(a, b)                            \
+  if (g.tx == a && g.ty == b) {                   \
+    cfg.blockDim = dim3(FvShape<a, b>::threads);  \
+    cfg.dynamicSmemBytes = FvShape<a, b>::smem(); \
+    cudaLaunchKernelEx(&cfg, k_fv_stage<a, b>, A); \
+    return;                                       \
   }
   FV_SHAPES(FV_LAUNCH)
 #undef FV_LAUNCH
