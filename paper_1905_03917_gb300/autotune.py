@@ -1,9 +1,10 @@
 """Autotuner of the finite-volume tile shape.
 
 For a grid-size bucket, every supported tile shape is timed on a real
-problem of that bucket (the kernel times itself on the GPU's global timer,
-see sif_profile_read) and the fastest is kept in a JSON cache keyed by
-(kernel, bucket, device).  Tuning runs from a checkpoint and restores it,
+problem of that bucket -- whole multi-time-step cycles, since the shape
+also sets which cells a fluid's active tiles cover, how a small fluid's
+tiles split and the tiles of the primitive recovery -- and the fastest is
+kept in a JSON cache keyed by (kernel, bucket, device).  Tuning runs from a checkpoint and restores it,
 so the tuned problem's state is unchanged.  Results never depend on the
 tile shape (each face flux is computed by the same formula whichever tile
 holds it).
@@ -12,6 +13,7 @@ from __future__ import annotations
 
 import json
 import os
+import time
 
 SHAPES = [(32, 8), (32, 4), (16, 8), (16, 16), (64, 4)]
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
@@ -51,20 +53,17 @@ def _store(path, data):
     os.replace(tmp, path)
 
 
-def measure(solver, shape, cycles=2):
-    """ns per (cell, fluid) finite-volume update with the given tile shape."""
+def measure(solver, shape, cycles=3):
+    """Wall-clock milliseconds per multi-time-step cycle with the given tile
+    shape (the stepping call returns once the GPU has finished)."""
     solver.set_tile_shape(*shape)
     solver.step_multi_dt(1)  # warm-up with this shape (graph rebuild)
-    solver.profile(True)
+    t0 = time.perf_counter()
     solver.step_multi_dt(cycles)
-    p = solver.profile_read()
-    solver.profile(False)
-    if not p["fv_cell_updates"]:
-        return float("inf")
-    return p["fv_ms"] * 1e6 / p["fv_cell_updates"]
+    return 1e3 * (time.perf_counter() - t0) / cycles
 
 
-def tune(solver, cache=DEFAULT_CACHE, device=0, cycles=2, force=False):
+def tune(solver, cache=DEFAULT_CACHE, device=0, cycles=3, force=False):
     """Pick (and cache) the fastest tile shape for this solver's bucket,
     apply it to the solver and return (shape, record)."""
     key = f"k_fv_stage|{bucket(solver.nx, solver.ny)}|{device_key(device)}"
@@ -79,7 +78,7 @@ def tune(solver, cache=DEFAULT_CACHE, device=0, cycles=2, force=False):
         times[f"{shape[0]}x{shape[1]}"] = measure(solver, shape, cycles)
         solver.load_checkpoint(ckpt)
     best = min(SHAPES, key=lambda s: times[f"{s[0]}x{s[1]}"])
-    rec = {"shape": list(best), "ns_per_update": times, "grid": [solver.nx, solver.ny]}
+    rec = {"shape": list(best), "ms_per_cycle": times, "grid": [solver.nx, solver.ny]}
     data = _load(cache)
     data[key] = rec
     _store(cache, data)
@@ -87,7 +86,7 @@ def tune(solver, cache=DEFAULT_CACHE, device=0, cycles=2, force=False):
     return best, rec
 
 
-def tune_batch(batch, cache=DEFAULT_CACHE, device=0, cycles=2):
+def tune_batch(batch, cache=DEFAULT_CACHE, device=0, cycles=3):
     """Tune one representative instance per bucket and apply its shape to
     every instance of the bucket; returns {bucket: shape}."""
     chosen = {}
