@@ -272,17 +272,6 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
   sif_note_launches(1);
 }
 
-__global__ void k_band_scatter2(const int *__restrict__ band, const int *nband, const double *tmp,
-                                double *a, double *b) {
-  SIF_TICK();
-  int n = *nband;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    int c = band[idx];
-    a[c] = tmp[idx];
-    if (b) b[c] = tmp[(size_t)n + idx];
-  }
-}
-
 // the level set's new band values, each also written to the ghost cells
 // whose image it is (the values the ghost fill would give them): phi
 // changes only through these writes, so its ghost layers stay filled
@@ -456,13 +445,6 @@ __global__ void k_reinit(Grid g, const double *__restrict__ q, const double *__r
     }
     tmp[idx] = out;
   }
-}
-
-__global__ void k_copy_plane(const double *src, double *dst, size_t n) {
-  SIF_TICK();
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
-       t += (size_t)gridDim.x * blockDim.x)
-    dst[t] = src[t];
 }
 
 void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, const int *nrext,
