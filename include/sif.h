@@ -64,7 +64,7 @@ typedef struct {
   double pinf[2];
   double cfl;            /* CFL number, 0.6 in the paper (Sec. 4) */
   int rk_order;          /* 2 = TVD-RK2 (the paper, Sec. 3); 3 = SSP-RK3 (single-dt only) */
-  double weno_eps;       /* WENO5 epsilon, 1e-6 */
+  double weno_eps;       /* WENO5 epsilon, 1e-6; at least 1e-20 */
   double mix_alpha;      /* small-cell mixing threshold, 0.5 */
   double ratio_threshold;/* time-step-ratio truncation threshold, 0.7 (Sec. 3.1) */
   int ext_iters;         /* extension Jacobi sweeps per interaction step, 10 */
@@ -259,6 +259,19 @@ int sif_profile_read(sif_ctx *ctx, sif_profile *out);
  * milliseconds: the ceiling of the FP64-bound finite-volume kernel.  No
  * counterpart in the paper.  Allocates a small scratch buffer. */
 int sif_measure_fp64_peak(int device, double *tflops);
+
+/* The reciprocal the finite-volume kernel uses for its WENO5 face values
+ * (one per face and component, Eq. 2's numerical flux): r[i] = 1 / d[i]
+ * by Newton's iteration to third order from the device's approximate
+ * reciprocal, within 1 ulp of the correctly rounded value.  d and r are
+ * device pointers to n doubles (n >= 0; r may equal d); d[i] must be
+ * positive, normal and below 2^1000, other inputs give unspecified values
+ * (the kernel divides instead outside that range).  Launched on `stream`
+ * (a cudaStream_t, NULL = default) and not synchronised.  SIF_EINVAL for
+ * n < 0 or a null pointer with n > 0, SIF_ECUDA for a launch failure.  No
+ * counterpart in the paper: it exists so that tests can hold the kernel's
+ * arithmetic to IEEE division. */
+int sif_probe_reciprocal(const double *d, double *r, long long n, void *stream);
 
 /* Conserved totals of caller-provided device planes without allocating
  * anything -- for callers that cannot allocate device memory when they

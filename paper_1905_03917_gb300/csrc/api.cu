@@ -138,7 +138,9 @@ static int validate(const sif_config *f, char *why, size_t n) {
     return snprintf(why, n, "periodic boundaries must be paired"), SIF_EINVAL;
   if (!(f->cfl > 0.0) || f->cfl > 1.0) return snprintf(why, n, "cfl must be in (0, 1]"), SIF_EINVAL;
   if (f->rk_order != 2 && f->rk_order != 3) return snprintf(why, n, "rk_order must be 2 or 3"), SIF_EINVAL;
-  if (!(f->weno_eps > 0.0)) return snprintf(why, n, "weno_eps must be > 0"), SIF_EINVAL;
+  // the face values' reciprocal needs the product of two denominators,
+  // each at least eps^4, to stay normal
+  if (!(f->weno_eps >= 1e-20)) return snprintf(why, n, "weno_eps must be >= 1e-20"), SIF_EINVAL;
   if (!(f->mix_alpha >= 0.0 && f->mix_alpha <= 1.0)) return snprintf(why, n, "mix_alpha in [0,1]"), SIF_EINVAL;
   if (!(f->ratio_threshold >= 0.0 && f->ratio_threshold <= 1.0))
     return snprintf(why, n, "ratio_threshold in [0,1]"), SIF_EINVAL;

@@ -64,12 +64,13 @@ __device__ __forceinline__ void weno5_frac(double v1, double v2, double v3, doub
   den = 0.1 * u0 + 0.6 * u1 + 0.3 * u2;
 }
 
-// A (num_l / den_l + num_r / den_r) with one division; two if the
-// cross products leave the double range
+// A (num_l / den_l + num_r / den_r) over one reciprocal of den_l den_r
+// (positive: the denominators are sums of products of squares plus
+// epsilon); two divisions if the products leave the reciprocal's range
 __device__ __forceinline__ double face_value(double A, double nl, double dl, double nr, double dr) {
-  double v = A * (nl * dr + nr * dl) / (dl * dr);
-  if (!isfinite(v)) v = A * (nl / dl + nr / dr);
-  return v;
+  double n = nl * dr + nr * dl, d = dl * dr;
+  if (d < 0x1p1000 && isfinite(n)) return A * n * recip_newton3(d);
+  return A * (nl / dl + nr / dr);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

@@ -1,6 +1,7 @@
 // probe.cu -- FP64 fused multiply-add throughput of the device: the
 // arithmetic ceiling of the finite-volume kernel, which is bound by the
-// FP64 pipe rather than by HBM bandwidth.
+// FP64 pipe rather than by HBM bandwidth; and the finite-volume kernel's
+// reciprocal over caller data, for tests against IEEE division.
 #include "sif_internal.cuh"
 
 // eight independent FMA chains per thread, ILP enough to fill the pipe
@@ -49,4 +50,22 @@ extern "C" int sif_measure_fp64_peak(int device, double *tflops) {
   double flops = 2.0 * 8.0 * 16.0 * iters * (double)threads * blocks;
   *tflops = flops / (ms * 1e-3) / 1e12;
   return SIF_OK;
+}
+
+__global__ void k_recip(const double *d, double *r, long long n) {
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += step)
+    r[i] = recip_newton3(d[i]);
+}
+
+extern "C" int sif_probe_reciprocal(const double *d, double *r, long long n, void *stream) {
+  if (n < 0 || (n > 0 && (!d || !r))) return SIF_EINVAL;
+  if (n == 0) return SIF_OK;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long want = (n + 255) / 256, cap = (long long)(sms > 0 ? sms : 1) * 8;
+  int blocks = (int)(want < cap ? want : cap);
+  k_recip<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
+  return cudaGetLastError() == cudaSuccess ? SIF_OK : SIF_ECUDA;
 }

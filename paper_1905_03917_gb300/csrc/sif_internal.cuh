@@ -242,6 +242,21 @@ __device__ inline double vol_k(const double *alphaP, int k, int c) {
 }
 
 // ---------------------------------------------------------------------
+// 1/d for a positive normal d below 2^1000 (so that 1/d is normal too):
+// Newton's iteration for the reciprocal, x <- x + x e with e = 1 - d x,
+// taken to third order, x <- x + x (e + e^2), from the device's approximate
+// reciprocal (rcp.approx.ftz.f64).  The relative error after the step is
+// the cube of the seed's; measured on GB300 the seed is good to 2^-19.9 and
+// the result within 1 ulp of the correctly rounded 1/d
+// (sif_probe_reciprocal checks it against IEEE division).
+__device__ inline double recip_newton3(double d) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+  double e = fma(-d, x, 1.0);
+  return fma(x, fma(e, e, e), x);
+}
+
+// ---------------------------------------------------------------------
 // WENO5-JS reconstruction in the plain form (used by the level set and
 // reinitialisation kernels, which follow the CPU reference op by op)
 

@@ -28,7 +28,7 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif_batch_create", "sif_batch_instance", "sif_batch_step_multi_dt",
            "sif_batch_last_error", "sif_batch_destroy", "sif_batch_one_graph",
            "sif_tape_reset", "sif_tape_length", "sif_replay_step", "sif_adjoint_step",
-           "sif_adjoint_init"]
+           "sif_adjoint_init", "sif_probe_reciprocal"]
 
 
 class SifError(RuntimeError):
@@ -94,6 +94,7 @@ def load(path: str | None = None):
     L.sif_profile_enable.argtypes = [P, I]
     L.sif_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
     L.sif_measure_fp64_peak.argtypes = [I, ctypes.POINTER(D)]
+    L.sif_probe_reciprocal.argtypes = [P, P, ctypes.c_longlong, P]
     L.sif_integrals_noalloc.argtypes = [P, P, I, I, D, D, P, P]
     L.sif_set_tile_shape.argtypes = [P, I, I]
     L.sif_get_tile_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -117,9 +118,9 @@ def load(path: str | None = None):
     for f in (L.sif_create, L.sif_init_fluids, L.sif_step_single_dt, L.sif_step_multi_dt,
               L.sif_integrals, L.sif_get_state, L.sif_set_state, L.sif_get_time,
               L.sif_save, L.sif_load, L.sif_profile_enable, L.sif_profile_read,
-              L.sif_measure_fp64_peak, L.sif_integrals_noalloc, L.sif_set_tile_shape,
-              L.sif_get_tile_shape, L.sif_batch_create, L.sif_batch_instance,
-              L.sif_batch_step_multi_dt):
+              L.sif_measure_fp64_peak, L.sif_probe_reciprocal, L.sif_integrals_noalloc,
+              L.sif_set_tile_shape, L.sif_get_tile_shape, L.sif_batch_create,
+              L.sif_batch_instance, L.sif_batch_step_multi_dt):
         f.restype = I
     _lib = L
     return L
@@ -172,6 +173,21 @@ def measure_fp64_peak(device=0) -> float:
     if rc != OK:
         raise SifError(rc, "FP64 throughput probe failed")
     return v.value
+
+
+def probe_reciprocal(d):
+    """The finite-volume kernel's reciprocal of every element of a
+    contiguous float64 CUDA tensor (sif_probe_reciprocal), as a new tensor
+    on the current stream."""
+    import torch
+    if not (getattr(d, "is_cuda", False) and d.dtype == torch.float64 and d.is_contiguous()):
+        raise ValueError("a contiguous float64 CUDA tensor is required")
+    r = torch.empty_like(d)
+    stream = torch.cuda.current_stream(d.device).cuda_stream
+    rc = load().sif_probe_reciprocal(d.data_ptr(), r.data_ptr(), d.numel(), stream)
+    if rc != OK:
+        raise SifError(rc, "reciprocal probe failed")
+    return r
 
 
 def integrals_noalloc(q_N, q_P, dx, dy, out, stream=None):

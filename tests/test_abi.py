@@ -53,3 +53,15 @@ def test_invalid_configuration_is_rejected_without_gpu_work():
     assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
     assert not h.value
     assert lib.sif_last_error(None) == b"null context"
+
+
+def test_weno_epsilon_below_the_reciprocal_range_is_rejected():
+    # the finite-volume face values take one reciprocal of a product of two
+    # WENO5 denominators (each at least eps^4): eps below 1e-20 is refused
+    from paper_1905_03917_gb300 import inputs
+    lib = sif.load()
+    cfg = dict(inputs.shock_tube_1d(64)["cfg"], weno_eps=1e-30)
+    c = sif.make_config(cfg)
+    h = ctypes.c_void_p()
+    assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
+    assert not h.value
