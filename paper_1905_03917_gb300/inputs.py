@@ -227,3 +227,49 @@ def batched_instances(count=256, seed=0, nmin=64, nmax=512):
         case["name"] = f"instance_{s}_{n}"
         out.append(case)
     return out
+
+
+def degenerate(kind, seed=0):
+    """Geometries at the edges of the cut-cell rules, gas (fluid N) against
+    water (fluid P, at ten times the pressure; the water's sound speed about
+    five times the gas's, so the water steps are sub-cycled) at rest in a
+    reflective box:
+
+    * ``face``: a vertical interface exactly on a column of cell faces, so
+      the corner values on it are exactly zero (ties count as fluid P);
+    * ``diagonal``: a 45-degree interface through cell centres and corners
+      (phi exactly zero at both) on a square grid;
+    * ``saddle``: gas in two opposite quadrants around a point inside a
+      cell (phi the signed distance to the two lines), so that the corner
+      values of the cells around that point alternate in sign (four edge
+      crossings);
+    * ``tiny``: a 5 x 3 grid, smaller than one finite-volume tile, holding
+      a gas pocket 1.5 cells across;
+    * ``film``: a gas layer 0.8 to 1.8 cells thick across the box, so that
+      most interface cells are small cells of one fluid or the other.
+    """
+    n = {"face": (32, 12), "diagonal": (24, 24), "saddle": (26, 22), "tiny": (5, 3),
+         "film": (40, 30)}[kind]
+    nx, ny = n
+    dx, dy = 1.0 / nx, 1.0 / ny
+    matN = {"gamma": 1.4, "pinf": 0.0}
+    cfg = config(nx, ny, dx, dy, matN, WATER, ["reflect"] * 4)
+    X, Y = _centres(cfg)
+    rng = np.random.default_rng(seed)
+    if kind == "face":
+        phi = X - 0.5
+    elif kind == "diagonal":
+        # (i - j) dx from integers: exact zeros, and exactly antisymmetric
+        # under the reflection (x, y) -> (1 - y, 1 - x)
+        phi = (np.arange(nx)[None, :] - np.arange(ny)[:, None]) * dx
+    elif kind == "saddle":
+        xc, yc = 0.5 + 0.3 * dx, 0.5 + 0.2 * dy
+        phi = np.where((X - xc) * (Y - yc) > 0, -1.0, 1.0) * np.minimum(abs(X - xc), abs(Y - yc))
+    elif kind == "tiny":
+        phi = np.hypot(X - 0.45, Y - 0.5) - 0.3
+    else:
+        thick = (1.3 + 0.5 * np.sin(2 * np.pi * X + rng.uniform(0, 2 * np.pi))) * dy
+        phi = np.abs(Y - 0.5) - 0.5 * thick
+    pN = _uniform(X.shape, 1.2, 0.0, 0.0, 1.0e5)
+    pP = _uniform(X.shape, 1000.0, 0.0, 0.0, 1.0e6)
+    return {"name": f"degenerate_{kind}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
