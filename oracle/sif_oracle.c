@@ -648,16 +648,87 @@ static void split(const orc_ctx *o, int k, int c, int d, double a, double *fp,
   }
 }
 
+/* Eigenvectors of the flux Jacobian dF_d/dU of the 2D Euler equations.
+ * With un the velocity along d, ut the one across it, q = (u^2+v^2)/2,
+ * c^2 = g (p + pinf)/rho and H = (E + p)/rho = c^2/(g-1) + q (the
+ * stiffened gas shifts p by a constant, so the ideal-gas structure holds
+ * with this c), the fields are the acoustic waves un -+ c, the entropy wave
+ * and the shear wave (both un).  Right eigenvectors, in (rho, rho un,
+ * rho ut, E) order: (1, un - c, ut, H - un c), (1, un, ut, q), (0, 0, 1, ut),
+ * (1, un + c, ut, H + un c); with b1 = (g-1)/c^2 and b2 = b1 q the left
+ * ones are (b2 + un/c, -b1 un - 1/c, -b1 ut, b1)/2, (1 - b2, b1 un, b1 ut,
+ * -b1), (-ut, 0, 1, 0), (b2 - un/c, -b1 un + 1/c, -b1 ut, b1)/2.  The x and y
+ * momentum components are then placed in the grid's order. */
+int orc_char_basis(double g, double pinf, double rho, double u, double v, double p, int d,
+                   double *L, double *R) {
+  if (!(rho > 0.0) || !(p + pinf > 0.0) || !(g > 1.0) || (d != 0 && d != 1))
+    return ORC_ERR_INVAL;
+  double un = d == 0 ? u : v, ut = d == 0 ? v : u;
+  double c = sqrt(g * (p + pinf) / rho);
+  double q = 0.5 * (u * u + v * v);
+  double H = c * c / (g - 1.0) + q;
+  double b1 = (g - 1.0) / (c * c), b2 = b1 * q;
+  /* in (rho, rho un, rho ut, E) order */
+  double Rn[4][4] = {{1.0, 1.0, 0.0, 1.0},
+                     {un - c, un, 0.0, un + c},
+                     {ut, ut, 1.0, ut},
+                     {H - un * c, q, ut, H + un * c}};
+  double Ln[4][4] = {{0.5 * (b2 + un / c), 0.5 * (-b1 * un - 1.0 / c), 0.5 * (-b1 * ut), 0.5 * b1},
+                     {1.0 - b2, b1 * un, b1 * ut, -b1},
+                     {-ut, 0.0, 1.0, 0.0},
+                     {0.5 * (b2 - un / c), 0.5 * (-b1 * un + 1.0 / c), 0.5 * (-b1 * ut), 0.5 * b1}};
+  /* grid component m of (rho, rho u, rho v, E) is component perm[m] of the
+   * (rho, rho un, rho ut, E) ordering */
+  int perm[4] = {0, d == 0 ? 1 : 2, d == 0 ? 2 : 1, 3};
+  for (int m = 0; m < 4; m++)
+    for (int f = 0; f < 4; f++) {
+      R[m * 4 + f] = Rn[perm[m]][f];
+      L[f * 4 + m] = Ln[f][perm[m]];
+    }
+  return 0;
+}
+
 /* numerical flux through the face between cells c - s and c, where s is
- * the index stride of direction d */
+ * the index stride of direction d.  Component-wise: WENO5 of each
+ * conserved component of the split fluxes.  Characteristic-wise: the split
+ * fluxes of the stencil are projected on the left eigenvectors of the face
+ * state (the mean of the two adjacent cells' stencil states), each field is
+ * reconstructed by WENO5, and the fields are mapped back by the right
+ * eigenvectors. */
 static void face_flux(const orc_ctx *o, int k, int c, int s, int d, double *Fh) {
   double a = o->lf[k][d];
   double fp[6][4], fm[6][4];
   for (int r = 0; r < 6; r++) split(o, k, c + (r - 3) * s, d, a, fp[r], fm[r]);
+  if (!o->c.weno_char) {
+    for (int m = 0; m < 4; m++) {
+      double vp[5] = {fp[0][m], fp[1][m], fp[2][m], fp[3][m], fp[4][m]};
+      double vm[5] = {fm[5][m], fm[4][m], fm[3][m], fm[2][m], fm[1][m]};
+      Fh[m] = orc_weno5(vp, o->c.weno_eps) + orc_weno5(vm, o->c.weno_eps);
+    }
+    return;
+  }
+  int cl = c - s, cr = c;
+  double rho = 0.5 * (o->w[k][0][cl] + o->w[k][0][cr]);
+  double u = 0.5 * (o->w[k][1][cl] + o->w[k][1][cr]);
+  double v = 0.5 * (o->w[k][2][cl] + o->w[k][2][cr]);
+  double p = 0.5 * (o->w[k][3][cl] + o->w[k][3][cr]);
+  double L[16], R[16], h[4];
+  orc_char_basis(o->c.gamma[k], o->c.pinf[k], rho, u, v, p, d, L, R);
+  for (int f = 0; f < 4; f++) {
+    double vp[5], vm[5];
+    for (int r = 0; r < 5; r++) {
+      vp[r] = 0.0;
+      vm[r] = 0.0;
+      for (int m = 0; m < 4; m++) {
+        vp[r] += L[f * 4 + m] * fp[r][m];
+        vm[r] += L[f * 4 + m] * fm[5 - r][m];
+      }
+    }
+    h[f] = orc_weno5(vp, o->c.weno_eps) + orc_weno5(vm, o->c.weno_eps);
+  }
   for (int m = 0; m < 4; m++) {
-    double vp[5] = {fp[0][m], fp[1][m], fp[2][m], fp[3][m], fp[4][m]};
-    double vm[5] = {fm[5][m], fm[4][m], fm[3][m], fm[2][m], fm[1][m]};
-    Fh[m] = orc_weno5(vp, o->c.weno_eps) + orc_weno5(vm, o->c.weno_eps);
+    Fh[m] = 0.0;
+    for (int f = 0; f < 4; f++) Fh[m] += R[m * 4 + f] * h[f];
   }
 }
 

@@ -44,6 +44,7 @@ typedef struct {
   double band;        /* narrow band half-width in cells, 6 */
   int flux_correction;   /* 1 = interfacial flux correction on */
   int force_ratio_one;   /* test only: multi-dt cycle with dt1 = dt2 */
+  int weno_char;         /* 1 = WENO5 on characteristic fields, 0 = component-wise */
 } orc_config;
 
 typedef struct {
@@ -74,6 +75,13 @@ int orc_status(const orc_ctx *o);
  * the interface vector S (N to P) per cell. Any output may be NULL. */
 int orc_geometry(orc_ctx *o, double *alpha, double *ax, double *ay,
                  double *sx, double *sy);
+/* Characteristic basis of the Euler flux Jacobian in direction d (0 = x,
+ * 1 = y) at the primitive state (rho, u, v, p) of a stiffened gas (g, pinf):
+ * R[m*4+f] = component m of the right eigenvector of field f (eigenvalues
+ * un - c, un, un, un + c with un the velocity along d), L[f*4+m] = row f
+ * of the inverse.  Returns ORC_ERR_INVAL for a non-physical state. */
+int orc_char_basis(double g, double pinf, double rho, double u, double v, double p, int d,
+                   double *L, double *R);
 /* Right-hand side L_k of the cut-cell update (Eq. 2) for fluid k at the
  * current state, after the interaction step; out is 4 planes of nx*ny. */
 int orc_rhs(orc_ctx *o, int k, double *out);

@@ -244,7 +244,7 @@ def degenerate(kind, seed=0):
       values of the cells around that point alternate in sign (four edge
       crossings);
     * ``tiny``: a 5 x 3 grid, smaller than one finite-volume tile, holding
-      a gas pocket 1.5 cells across;
+      a gas pocket of radius 0.3 (1.5 cells in x, 0.9 in y);
     * ``film``: a gas layer 0.8 to 1.8 cells thick across the box, so that
       most interface cells are small cells of one fluid or the other.
     """
