@@ -35,6 +35,14 @@ sys.path.insert(0, ROOT)
 # face flux per cell and direction (4 components x (2 reconstructions of 70
 # flops + 2)), and the update (10 per component).  1D has one direction.
 FLOPS_PER_UPDATE = {2: 2 * 35 + 2 * 4 * 142 + 4 * 10, 1: 35 + 4 * 142 + 4 * 7}
+# The characteristic-wise reconstruction (weno_char = 1) adds per face the
+# face state (22), the left and right eigenvectors (28), the projection of
+# both splits' five stencil values on four fields (2 x 5 x 4 x 7) and the
+# mapping back with the aperture (4 x 7 + 4): 930 flops a face instead of
+# 568.
+FLOPS_PER_FACE_CHAR = 22 + 28 + 2 * 5 * 4 * 7 + 4 * 142 + 4 * 7 + 4
+FLOPS_PER_UPDATE_CHAR = {2: 2 * 35 + 2 * FLOPS_PER_FACE_CHAR + 4 * 10,
+                         1: 35 + FLOPS_PER_FACE_CHAR + 4 * 7}
 METRIC = "fluid cell-updates/s (FP64), % HBM peak; multi-dt vs single-dt speedup at equal err"
 # nominal FP64 rate of a GB300: 152 SMs x 4 flops/clock (2 FMA) x 2.07 GHz
 NOMINAL_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
@@ -141,6 +149,9 @@ def run_reference(args):
     if rank != 0:
         return
     case = workload(args.workload)
+    weno = getattr(args, "weno", "componentwise")
+    if weno == "characteristic":
+        case["cfg"]["weno_char"] = 1
     from oracle import oracle as O
     o = O.Oracle(case["cfg"]).init(case["phi"], case["prim_N"], case["prim_P"])
     step = o.step_multi_dt if args.mode == "multi" else o.step_single_dt
@@ -158,7 +169,7 @@ def run_reference(args):
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": case["name"], "mode": args.mode, "nx": case["cfg"]["nx"],
-                       "ny": case["cfg"]["ny"]},
+                       "ny": case["cfg"]["ny"], "reconstruction": weno},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed steps after {args.warmup} of {case['name']}"},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
@@ -422,6 +433,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_1905_03917_gb300 import sif
     case = workload(args.workload, seed=rank)
+    char = args.weno == "characteristic"
+    if char:
+        case["cfg"]["weno_char"] = 1
     arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
     s = sif.Solver(case["cfg"], device=local).init_fluids(*arrs)
     from paper_1905_03917_gb300 import autotune
@@ -481,7 +495,8 @@ def run_ours(args):
     if rank != 0:
         return
     dim = case["cfg"]["dim"]
-    flops = FLOPS_PER_UPDATE[dim]
+    flops = (FLOPS_PER_UPDATE_CHAR if char else FLOPS_PER_UPDATE)[dim]
+    traffic_per_update = None if char else MEASURED_DRAM_BYTES_PER_UPDATE.get(tuple(shape))
     fv_avg_ms = prof["fv_ms"] / max(prof["fv_launches"], 1)
     fv_units = prof["fv_cell_updates"] / max(prof["fv_launches"], 1)
     achieved_tf = fv_units * flops / (fv_avg_ms * 1e-3) / 1e12 if fv_avg_ms > 0 else None
@@ -497,13 +512,13 @@ def run_ours(args):
         "config": {"workload": case["name"], "mode": args.mode, "nx": case["cfg"]["nx"],
                    "ny": case["cfg"]["ny"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}", "mean_substeps": float(np.mean(substeps)),
-                   "tile_shape": list(shape),
+                   "tile_shape": list(shape), "reconstruction": args.weno,
                    "autotune_ms_per_cycle": tune_rec.get("ms_per_cycle")},
         "roofline": {"kernel": "k_fv_stage", "bound": "alu", "achieved": achieved_tf,
                      "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / NOMINAL_FP64_TFLOPS if achieved_tf else None,
-                     "traffic": (fv_units * MEASURED_DRAM_BYTES_PER_UPDATE[tuple(shape)]
-                                 if tuple(shape) in MEASURED_DRAM_BYTES_PER_UPDATE else None),
+                     "traffic": (fv_units * traffic_per_update
+                                 if traffic_per_update is not None else None),
                      "traffic_source": f"ncu DRAM bytes per update of the 512 x 128 capture with "
                                        f"{shape[0]} x {shape[1]} tiles x updates per launch",
                      "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
@@ -544,6 +559,9 @@ def run_batched(args):
     torch.cuda.set_device(local)
     from paper_1905_03917_gb300 import autotune, sif
     cases = workload("batched", seed=rank)
+    if args.weno == "characteristic":
+        for c in cases:
+            c["cfg"]["weno_char"] = 1
     b = sif.Batch([c["cfg"] for c in cases], device=local)
     for s_, c in zip(b.instances, cases):
         s_.init_fluids(*(np.ascontiguousarray(c[x]) for x in ("phi", "prim_N", "prim_P")))
@@ -593,6 +611,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="",
                     help="finite-volume tile shape TXxTY instead of the autotuner's choice")
+    ap.add_argument("--weno", default="componentwise", choices=["componentwise", "characteristic"],
+                    help="finite-volume reconstruction: on conserved components (the paper's "
+                         "WENO-LF) or on characteristic fields")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-vs-single and adjoint measurements")
     args = ap.parse_args()

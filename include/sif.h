@@ -76,6 +76,10 @@ typedef struct {
                             context, created blocking (ordered with the legacy default
                             stream; a stream capture needs a non-legacy stream) */
   int device;            /* CUDA device ordinal */
+  int weno_char;         /* 0 = WENO5 on each conserved component (the paper's WENO-LF,
+                            Sec. 4); 1 = on the characteristic fields of the face state
+                            (the mean of the two adjacent cells' stencil states), mapped
+                            back by the right eigenvectors.  The adjoint calls require 0. */
 } sif_config;
 
 /* Per-cycle record of the multi-time-step schedule (Sec. 3.1). */
@@ -206,7 +210,8 @@ void sif_batch_destroy(sif_batch *b);
  * owned by the context).  Resets the tape to length 0.  capacity 0 stops
  * recording and frees the tape.  While recording, steps run without the
  * captured graphs (same kernels, same results) and sif_step_multi_dt
- * returns SIF_ESTATE.  SIF_EINVAL for rk_order != 2 or capacity < 0;
+ * returns SIF_ESTATE.  SIF_EINVAL for rk_order != 2, weno_char != 0 or
+ * capacity < 0;
  * SIF_ECUDA if the tape cannot be allocated.  A step beyond capacity fails
  * with SIF_EINVAL before anything runs. */
 int sif_tape_reset(sif_ctx *ctx, int capacity);

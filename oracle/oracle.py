@@ -45,7 +45,8 @@ class _Config(ctypes.Structure):
                 ("ratio_threshold", ctypes.c_double),
                 ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
                 ("band", ctypes.c_double),
-                ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int)]
+                ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
+                ("weno_char", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -88,6 +89,7 @@ def lib():
         L.orc_cell_alpha.restype = D
         L.orc_cell_alpha.argtypes = [D, D, D, D]
         L.orc_riemann.argtypes = [dp, dp, dp]
+        L.orc_char_basis.argtypes = [D, D, D, D, D, D, I, dp, dp]
         L.orc_step_taped.argtypes = [P, dp, dp, dp, dp]
         L.orc_replay_step.argtypes = [P, D, dp, dp, dp]
         L.orc_adjoint_step.argtypes = [P, D, dp, dp, dp, dp, dp]
@@ -133,6 +135,7 @@ def make_config(cfg: dict) -> _Config:
     c.band = float(cfg.get("band", 6.0))
     c.flux_correction = int(cfg.get("flux_correction", 1))
     c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
+    c.weno_char = int(cfg.get("weno_char", 0))
     return c
 
 
@@ -301,6 +304,18 @@ def edge_fraction(a, b):
 
 def cell_alpha(c00, c10, c11, c01):
     return lib().orc_cell_alpha(float(c00), float(c10), float(c11), float(c01))
+
+
+def char_basis(gamma, pinf, rho, u, v, p, d):
+    """(L, R): left and right eigenvectors of the Euler flux Jacobian in
+    direction d (0 = x, 1 = y), R's columns the fields (un - c, un, un,
+    un + c), both 4 x 4 over the conserved components (rho, rho u, rho v, E)."""
+    L, R = np.empty(16), np.empty(16)
+    rc = lib().orc_char_basis(float(gamma), float(pinf), float(rho), float(u), float(v),
+                              float(p), int(d), _ptr(L), _ptr(R))
+    if rc:
+        raise ValueError("non-physical state")
+    return L.reshape(4, 4), R.reshape(4, 4)
 
 
 def riemann(left, right):

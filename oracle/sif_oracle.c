@@ -1177,6 +1177,7 @@ orc_ctx *orc_create(const orc_config *cfg) {
   if (cfg->nx < GH || (cfg->dim == 2 && cfg->ny < GH) || (cfg->dim == 1 && cfg->ny != 1))
     return NULL;
   if (cfg->rk_order != 2 && cfg->rk_order != 3) return NULL;
+  if (cfg->weno_char != 0 && cfg->weno_char != 1) return NULL;
   orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   o->c = *cfg;
   if (o->c.dim == 1) o->c.bc[2] = o->c.bc[3] = ORC_BC_ZEROGRAD;
@@ -1837,7 +1838,8 @@ static void rhs_T(orc_ctx *o, double *const W[2][4], const double *lf, double *c
 
 int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1,
                      const double *phi2, const double *lam_in, double *lam_out) {
-  if (o->c.rk_order != 2) {
+  /* the adjoint is written for the component-wise reconstruction */
+  if (o->c.rk_order != 2 || o->c.weno_char) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }
@@ -1942,6 +1944,10 @@ int orc_rhs_frozen(orc_ctx *o, const double *lf, double *out) {
 }
 
 int orc_rhs_adjoint(orc_ctx *o, const double *lf, const double *mu_in, double *lq_out) {
+  if (o->c.weno_char) {
+    o->err |= ORC_ERR_INVAL;
+    return o->err;
+  }
   int n = o->c.nx * o->c.ny;
   double *W[2][4], *mu[2][4], *lw[2][4], *lq[2][4];
   double **all[4] = {&W[0][0], &mu[0][0], &lw[0][0], &lq[0][0]};

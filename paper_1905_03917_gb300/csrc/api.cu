@@ -138,6 +138,7 @@ static int validate(const sif_config *f, char *why, size_t n) {
     return snprintf(why, n, "periodic boundaries must be paired"), SIF_EINVAL;
   if (!(f->cfl > 0.0) || f->cfl > 1.0) return snprintf(why, n, "cfl must be in (0, 1]"), SIF_EINVAL;
   if (f->rk_order != 2 && f->rk_order != 3) return snprintf(why, n, "rk_order must be 2 or 3"), SIF_EINVAL;
+  if (f->weno_char != 0 && f->weno_char != 1) return snprintf(why, n, "weno_char must be 0 or 1"), SIF_EINVAL;
   // the face values' reciprocal needs the product of two denominators,
   // each at least eps^4, to stay normal
   if (!(f->weno_eps >= 1e-20)) return snprintf(why, n, "weno_eps must be >= 1e-20"), SIF_EINVAL;
@@ -210,6 +211,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.band = f.band;
   g.ext_iters = f.ext_iters;
   g.reinit_iters = f.reinit_iters;
+  g.weno_char = f.weno_char;
   g.tx = FV_TX;
   g.ty = FV_TY;
   g.ntx = (f.nx + g.tx - 1) / g.tx;
@@ -1442,6 +1444,10 @@ extern "C" int sif_tape_reset(sif_ctx *c, int capacity) {
   if (!c || capacity < 0) return SIF_EINVAL;
   if (c->cfg.rk_order != 2) {
     set_err(c, "the adjoint is defined for rk_order 2");
+    return SIF_EINVAL;
+  }
+  if (c->cfg.weno_char) {
+    set_err(c, "the adjoint is defined for the component-wise reconstruction (weno_char 0)");
     return SIF_EINVAL;
   }
   cudaSetDevice(c->cfg.device);

@@ -73,6 +73,73 @@ __device__ __forceinline__ double face_value(double A, double nl, double dl, dou
   return A * (nl / dl + nr / dr);
 }
 
+// Characteristic reconstruction: the state of a face is the mean of the
+// stencil states of the two cells beside it (cl, cr), taken in the face's
+// frame (un along the face normal, ut across it).  For a stiffened gas the
+// Euler flux Jacobian has the ideal-gas eigenstructure with c^2 = g (p +
+// p_inf) / rho and H = c^2 / (g - 1) + q, q = (u^2 + v^2) / 2.
+struct CharFace {
+  double un, ut, c, q, H, b1, b2;
+};
+
+__device__ __forceinline__ CharFace char_face(const FvArgs &A, int cl, int cr, bool ydir,
+                                              double gm, double pi) {
+  double rho = 0.5 * (A.w[0][cl] + A.w[0][cr]);
+  double u = 0.5 * (A.w[1][cl] + A.w[1][cr]);
+  double v = 0.5 * (A.w[2][cl] + A.w[2][cr]);
+  double p = 0.5 * (A.w[3][cl] + A.w[3][cr]);
+  CharFace f;
+  f.un = ydir ? v : u;
+  f.ut = ydir ? u : v;
+  f.c = sqrt(gm * (p + pi) / rho);
+  f.q = 0.5 * (u * u + v * v);
+  f.H = f.c * f.c / (gm - 1.0) + f.q;
+  f.b1 = (gm - 1.0) / (f.c * f.c);
+  f.b2 = f.b1 * f.q;
+  return f;
+}
+
+// left eigenvector of field fld (0: un - c, 1: entropy, 2: shear, 3: un + c)
+// over the grid's conserved components (rho, rho u, rho v, E)
+__device__ __forceinline__ void char_left(const CharFace &f, int fld, bool ydir, double l[4]) {
+  double n0, n1, n2, n3;  // over (rho, rho un, rho ut, E)
+  if (fld == 0 || fld == 3) {
+    const double s = fld == 0 ? 1.0 : -1.0, ic = 1.0 / f.c;
+    n0 = 0.5 * (f.b2 + s * f.un * ic);
+    n1 = 0.5 * (-f.b1 * f.un - s * ic);
+    n2 = 0.5 * (-f.b1 * f.ut);
+    n3 = 0.5 * f.b1;
+  } else if (fld == 1) {
+    n0 = 1.0 - f.b2;
+    n1 = f.b1 * f.un;
+    n2 = f.b1 * f.ut;
+    n3 = -f.b1;
+  } else {
+    n0 = -f.ut;
+    n1 = 0.0;
+    n2 = 1.0;
+    n3 = 0.0;
+  }
+  l[0] = n0;
+  l[1] = ydir ? n2 : n1;
+  l[2] = ydir ? n1 : n2;
+  l[3] = n3;
+}
+
+// row m (grid component) of the right eigenvectors, over the four fields
+__device__ __forceinline__ void char_right_row(const CharFace &f, int m, bool ydir, double r[4]) {
+  const int nm = (m == 1 || m == 2) && ydir ? 3 - m : m;  // row in (rho, rho un, rho ut, E)
+  if (nm == 0) {
+    r[0] = 1.0, r[1] = 1.0, r[2] = 0.0, r[3] = 1.0;
+  } else if (nm == 1) {
+    r[0] = f.un - f.c, r[1] = f.un, r[2] = 0.0, r[3] = f.un + f.c;
+  } else if (nm == 2) {
+    r[0] = f.ut, r[1] = f.ut, r[2] = 1.0, r[3] = f.ut;
+  } else {
+    r[0] = f.H - f.un * f.c, r[1] = f.q, r[2] = f.ut, r[3] = f.H + f.un * f.c;
+  }
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -114,7 +181,7 @@ struct FvShape {
 
 // the three phases over an SX x SY block of output cells at (i0, j0), with
 // the CTA's threads (any count)
-template <int SX, int SY>
+template <int SX, int SY, bool CH>
 __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, int j0) {
   constexpr int HX = SX + 6, HY = SY + 6;
   const Grid &g = A.g;
@@ -222,13 +289,74 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
     double val = 0.0;
     if (open && A_ != 0.0) {
       double nl, dl, nr, dr;
-      weno5_frac(P[0], P[st], P[2 * st], P[3 * st], P[4 * st], eps, nl, dl);
-      weno5_frac(M[5 * st], M[4 * st], M[3 * st], M[2 * st], M[st], eps, nr, dr);
-      val = face_value(A_, nl, dl, nr, dr);
+      if constexpr (CH) {
+        // item (field, face): the field's left eigenvector applied to the
+        // four components of each stencil value, then the field's
+        // reconstructed split fluxes (the aperture comes with the mapping
+        // back)
+        const bool yd = r >= NXI;
+        const int fld = yd ? (r - NXI) / (SX * (SY + 1)) : r / ((SX + 1) * SY);
+        const int cs = yd ? SX * HY : HX * SY;  // component stride of the split fluxes
+        const int f = yd ? (r - NXI) % (SX * (SY + 1)) : r % ((SX + 1) * SY);
+        const int fi = yd ? f % SX : f % (SX + 1), fj = yd ? f / SX : f / (SX + 1);
+        const int cr = gidx(g, i0 + fi, j0 + fj);
+        const int cl = yd ? gidx(g, i0 + fi, j0 + fj - 1) : gidx(g, i0 + fi - 1, j0 + fj);
+        const CharFace cf = char_face(A, cl, cr, yd, g.gamma[k], g.pinf[k]);
+        double l[4];
+        char_left(cf, fld, yd, l);
+        const double *P0 = P - fld * cs, *M0 = M - fld * cs;
+        double vp[5], vm[5];
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+          vp[q] = l[0] * P0[q * st] + l[1] * P0[cs + q * st] + l[2] * P0[2 * cs + q * st] +
+                  l[3] * P0[3 * cs + q * st];
+          vm[q] = l[0] * M0[(5 - q) * st] + l[1] * M0[cs + (5 - q) * st] +
+                  l[2] * M0[2 * cs + (5 - q) * st] + l[3] * M0[3 * cs + (5 - q) * st];
+        }
+        weno5_frac(vp[0], vp[1], vp[2], vp[3], vp[4], eps, nl, dl);
+        weno5_frac(vm[0], vm[1], vm[2], vm[3], vm[4], eps, nr, dr);
+        val = face_value(1.0, nl, dl, nr, dr);
+      } else {
+        weno5_frac(P[0], P[st], P[2 * st], P[3 * st], P[4 * st], eps, nl, dl);
+        weno5_frac(M[5 * st], M[4 * st], M[3 * st], M[2 * st], M[st], eps, nr, dr);
+        val = face_value(A_, nl, dl, nr, dr);
+      }
     }
     *out = val;
   }
   __syncthreads();
+
+  // characteristic reconstruction: map the four fields of each face back
+  // to the conserved components with the face's right eigenvectors, times
+  // the aperture, into the split-flux storage (free after phase 2)
+  double *FXo = Fx, *FYo = Fy;
+  if constexpr (CH) {
+    FXo = fxp;
+    FYo = fyp;
+    for (int r = tid; r < NI; r += nth) {
+      const bool yd = r >= NXI;
+      const int q = yd ? r - NXI : r;
+      const int nf = yd ? SX * (SY + 1) : (SX + 1) * SY;
+      const int m = q / nf, f = q % nf;
+      const int fi = yd ? f % SX : f % (SX + 1), fj = yd ? f / SX : f / (SX + 1);
+      const int i = i0 + fi, j = j0 + fj;
+      const bool open = yd ? (i < g.nx && j <= g.ny) : (i <= g.nx && j < g.ny);
+      double A_ = 0.0;
+      if (open) A_ = yd ? A.ay[gidx(g, i, j)] : A.ax[gidx(g, i, j)];
+      if (k == 0) A_ = 1.0 - A_;
+      double val = 0.0;
+      if (open && A_ != 0.0) {
+        const int cr = gidx(g, i, j), cl = yd ? gidx(g, i, j - 1) : gidx(g, i - 1, j);
+        const CharFace cf = char_face(A, cl, cr, yd, g.gamma[k], g.pinf[k]);
+        double rr[4];
+        char_right_row(cf, m, yd, rr);
+        const double *h = (yd ? Fy : Fx) + f;
+        val = A_ * (rr[0] * h[0] + rr[1] * h[nf] + rr[2] * h[2 * nf] + rr[3] * h[3 * nf]);
+      }
+      (yd ? FYo : FXo)[m * nf + f] = val;
+    }
+    __syncthreads();
+  }
 
   // phase 3: update of the block's cells
   const double dt = *A.dtp;
@@ -242,10 +370,10 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
     bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
 #pragma unroll
     for (int m = 0; m < 4; m++) {
-      const double *fx = Fx + m * (SX + 1) * SY + lj * (SX + 1) + li;
+      const double *fx = FXo + m * (SX + 1) * SY + lj * (SX + 1) + li;
       double L = (fx[0] - fx[1]) * inv_dx;
       if (d2) {
-        const double *fy = Fy + m * SX * (SY + 1) + lj * SX + li;
+        const double *fy = FYo + m * SX * (SY + 1) + lj * SX + li;
         L += (fy[0] - fy[SX]) * inv_dy;
       }
       if (m > 0 && cut) L += sgn * A.xn[m - 1][c] * inv_dxdy;
@@ -266,8 +394,11 @@ struct FvHalf {
   static constexpr int SX = along_x ? TX / 2 : TX, SY = along_x ? TY : TY / 2;
 };
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(FvShape<TX, TY>::threads, 1536 / FvShape<TX, TY>::threads)
+// CH: characteristic-wise reconstruction (more registers a thread: two
+// CTAs per SM instead of three)
+template <int TX, int TY, bool CH>
+__global__ void __launch_bounds__(FvShape<TX, TY>::threads,
+                                  (CH ? 1024 : 1536) / FvShape<TX, TY>::threads)
 k_fv_stage(FvArgs A) {
   SIF_TICK();
   const Grid &g = A.g;
@@ -292,8 +423,8 @@ k_fv_stage(FvArgs A) {
   }
   const bool timed = A.sc->timing;
   if (timed && threadIdx.x == 0) atomicMin((unsigned long long *)&A.sc->fv_t0, globaltimer_ns());
-  if (split) fv_cells<H::SX, H::SY>(A, smem, i0, j0);
-  else fv_cells<TX, TY>(A, smem, i0, j0);
+  if (split) fv_cells<H::SX, H::SY, CH>(A, smem, i0, j0);
+  else fv_cells<TX, TY, CH>(A, smem, i0, j0);
   if (timed) {
     __syncthreads();
     if (threadIdx.x == 0)
@@ -320,8 +451,10 @@ bool fv_shape_supported(int tx, int ty) {
 static int g_fv_priority = 0;
 
 void fv_prepare() {
-#define FV_PREP(a, b)                                                                   \
-  cudaFuncSetAttribute(k_fv_stage<a, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+#define FV_PREP(a, b)                                                                          \
+  cudaFuncSetAttribute(k_fv_stage<a, b, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)FvShape<a, b>::smem());                                          \
+  cudaFuncSetAttribute(k_fv_stage<a, b, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                        (int)FvShape<a, b>::smem());
   FV_SHAPES(FV_PREP)
 #undef FV_PREP
@@ -371,12 +504,15 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
   at.val.priority = g_fv_priority;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
-#define FV_LAUNCH(a, b)                            \
-  if (g.tx == a && g.ty == b) {                   \
-    cfg.blockDim = dim3(FvShape<a, b>::threads);  \
-    cfg.dynamicSmemBytes = FvShape<a, b>::smem(); \
-    cudaLaunchKernelEx(&cfg, k_fv_stage<a, b>, A); \
-    return;                                       \
+#define FV_LAUNCH(a, b)                                    \
+  if (g.tx == a && g.ty == b) {                           \
+    cfg.blockDim = dim3(FvShape<a, b>::threads);          \
+    cfg.dynamicSmemBytes = FvShape<a, b>::smem();         \
+    if (g.weno_char)                                      \
+      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, true>, A);  \
+    else                                                  \
+      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, false>, A); \
+    return;                                               \
   }
   FV_SHAPES(FV_LAUNCH)
 #undef FV_LAUNCH

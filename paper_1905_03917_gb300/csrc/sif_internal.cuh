@@ -33,6 +33,7 @@ struct Grid {
   double gamma[2], pinf[2];
   double cfl, weno_eps, mix_alpha, band;
   int ext_iters, reinit_iters;
+  int weno_char;  // finite-volume reconstruction on characteristic fields
   int tx, ty;    // finite-volume tile shape (output cells per CTA)
   int ntx, nty;  // tiles per direction
 };

@@ -49,7 +49,8 @@ class Config(ctypes.Structure):
                 ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("weno_char", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -147,6 +148,7 @@ def make_config(cfg: dict, stream=None, device=0) -> Config:
     c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
     c.cuda_stream = stream
     c.device = int(device)
+    c.weno_char = int(cfg.get("weno_char", 0))
     return c
 
 

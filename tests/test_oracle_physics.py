@@ -115,8 +115,9 @@ def test_mirror_symmetry_of_shock_bubble():
         assert np.abs(phi - phi[::-1, :]).max() <= 1e-12
 
 
-def _tube_errors(n, rk, multi, T=2e-4):
+def _tube_errors(n, rk, multi, T=2e-4, weno_char=0):
     c = inputs.shock_tube_1d(n, rk_order=rk)
+    c["cfg"]["weno_char"] = weno_char
     o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
     while o.t < T * (1 - 1e-14):
         (o.step_multi_dt if multi else o.step_single_dt)(1, T)
