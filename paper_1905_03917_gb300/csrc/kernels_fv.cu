@@ -79,8 +79,9 @@ __device__ __forceinline__ double face_value(double A, double nl, double dl, dou
 // Euler flux Jacobian has the ideal-gas eigenstructure with c^2 = g (p +
 // p_inf) / rho and H = c^2 / (g - 1) + q, q = (u^2 + v^2) / 2.
 struct CharFace {
-  double un, ut, c, q, H, b1, b2;
+  double un, ut, c, ic, q, H, b1, b2;  // ic = 1 / c
 };
+constexpr int kCharFaceVals = 8;
 
 __device__ __forceinline__ CharFace char_face(const FvArgs &A, int cl, int cr, bool ydir,
                                               double gm, double pi) {
@@ -92,10 +93,27 @@ __device__ __forceinline__ CharFace char_face(const FvArgs &A, int cl, int cr, b
   f.un = ydir ? v : u;
   f.ut = ydir ? u : v;
   f.c = sqrt(gm * (p + pi) / rho);
+  f.ic = 1.0 / f.c;
   f.q = 0.5 * (u * u + v * v);
   f.H = f.c * f.c / (gm - 1.0) + f.q;
   f.b1 = (gm - 1.0) / (f.c * f.c);
   f.b2 = f.b1 * f.q;
+  return f;
+}
+
+// the face states of a block live in shared memory as kCharFaceVals planes
+// of nf values
+__device__ __forceinline__ void char_store(double *fs, int nf, int face, const CharFace &f) {
+  fs[face] = f.un, fs[nf + face] = f.ut, fs[2 * nf + face] = f.c, fs[3 * nf + face] = f.ic;
+  fs[4 * nf + face] = f.q, fs[5 * nf + face] = f.H, fs[6 * nf + face] = f.b1;
+  fs[7 * nf + face] = f.b2;
+}
+
+__device__ __forceinline__ CharFace char_load(const double *fs, int nf, int face) {
+  CharFace f;
+  f.un = fs[face], f.ut = fs[nf + face], f.c = fs[2 * nf + face], f.ic = fs[3 * nf + face];
+  f.q = fs[4 * nf + face], f.H = fs[5 * nf + face], f.b1 = fs[6 * nf + face];
+  f.b2 = fs[7 * nf + face];
   return f;
 }
 
@@ -104,7 +122,7 @@ __device__ __forceinline__ CharFace char_face(const FvArgs &A, int cl, int cr, b
 __device__ __forceinline__ void char_left(const CharFace &f, int fld, bool ydir, double l[4]) {
   double n0, n1, n2, n3;  // over (rho, rho un, rho ut, E)
   if (fld == 0 || fld == 3) {
-    const double s = fld == 0 ? 1.0 : -1.0, ic = 1.0 / f.c;
+    const double s = fld == 0 ? 1.0 : -1.0, ic = f.ic;
     n0 = 0.5 * (f.b2 + s * f.un * ic);
     n1 = 0.5 * (-f.b1 * f.un - s * ic);
     n2 = 0.5 * (-f.b1 * f.ut);
@@ -170,9 +188,14 @@ __device__ void fv_timer_block_done(const Scalars *csc, unsigned int nwork) {
 template <int TX, int TY>
 struct FvShape {
   static constexpr int HX = TX + 6, HY = TY + 6;
+  static constexpr int nfaces = (TX + 1) * TY + TX * (TY + 1);
   static constexpr size_t smem() {
     return sizeof(double) *
            (size_t)4 * (2 * HX * TY + 2 * TX * HY + (TX + 1) * TY + TX * (TY + 1));
+  }
+  // the characteristic form also keeps one face state per face
+  static constexpr size_t smem_char() {
+    return smem() + sizeof(double) * (size_t)kCharFaceVals * nfaces;
   }
   // two threads per output cell: a CTA's phases finish in half the time,
   // which matters when a fluid has few tiles (the sub-cycled fluid)
@@ -193,6 +216,9 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
   double *fym = fyp + 4 * SX * HY;      // [4][SX*HY]
   double *Fx = fym + 4 * SX * HY;       // [4][(SX+1)*SY]
   double *Fy = Fx + 4 * (SX + 1) * SY;  // [4][SX*(SY+1)]
+  // characteristic form: face states, x faces then y faces
+  constexpr int NXF = (SX + 1) * SY, NF = NXF + SX * (SY + 1);
+  double *fs = Fy + 4 * SX * (SY + 1);  // [kCharFaceVals][NF]
   const double gm = g.gamma[k], pi = g.pinf[k];
   const double inv_gm1 = 1.0 / (gm - 1.0), e0c = gm * pi * inv_gm1;
   // Lax-Friedrichs splitting f+- = F/2 +- (alpha/2) U
@@ -248,6 +274,23 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
       }
     }
   }
+  if constexpr (CH) {
+    // the state of every open face (2D: also the y faces)
+    const int nf = d2 ? NF : NXF;
+    for (int r = tid; r < nf; r += nth) {
+      const bool yd = r >= NXF;
+      const int f = yd ? r - NXF : r;
+      const int fi = yd ? f % SX : f % (SX + 1), fj = yd ? f / SX : f / (SX + 1);
+      const int i = i0 + fi, j = j0 + fj;
+      const bool open = yd ? (i < g.nx && j <= g.ny) : (i <= g.nx && j < g.ny);
+      if (!open) continue;
+      double A_ = yd ? A.ay[gidx(g, i, j)] : A.ax[gidx(g, i, j)];
+      if (k == 0) A_ = 1.0 - A_;
+      if (A_ == 0.0) continue;
+      const int cr = gidx(g, i, j), cl = yd ? gidx(g, i, j - 1) : gidx(g, i - 1, j);
+      char_store(fs, NF, r, char_face(A, cl, cr, yd, gm, pi));
+    }
+  }
   __syncthreads();
 
   // phase 2: one (face, component) per item, x faces (left face of cell
@@ -298,10 +341,7 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
         const int fld = yd ? (r - NXI) / (SX * (SY + 1)) : r / ((SX + 1) * SY);
         const int cs = yd ? SX * HY : HX * SY;  // component stride of the split fluxes
         const int f = yd ? (r - NXI) % (SX * (SY + 1)) : r % ((SX + 1) * SY);
-        const int fi = yd ? f % SX : f % (SX + 1), fj = yd ? f / SX : f / (SX + 1);
-        const int cr = gidx(g, i0 + fi, j0 + fj);
-        const int cl = yd ? gidx(g, i0 + fi, j0 + fj - 1) : gidx(g, i0 + fi - 1, j0 + fj);
-        const CharFace cf = char_face(A, cl, cr, yd, g.gamma[k], g.pinf[k]);
+        const CharFace cf = char_load(fs, NF, yd ? NXF + f : f);
         double l[4];
         char_left(cf, fld, yd, l);
         const double *P0 = P - fld * cs, *M0 = M - fld * cs;
@@ -346,8 +386,7 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
       if (k == 0) A_ = 1.0 - A_;
       double val = 0.0;
       if (open && A_ != 0.0) {
-        const int cr = gidx(g, i, j), cl = yd ? gidx(g, i, j - 1) : gidx(g, i - 1, j);
-        const CharFace cf = char_face(A, cl, cr, yd, g.gamma[k], g.pinf[k]);
+        const CharFace cf = char_load(fs, NF, yd ? NXF + f : f);
         double rr[4];
         char_right_row(cf, m, yd, rr);
         const double *h = (yd ? Fy : Fx) + f;
@@ -455,7 +494,7 @@ void fv_prepare() {
   cudaFuncSetAttribute(k_fv_stage<a, b, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                        (int)FvShape<a, b>::smem());                                          \
   cudaFuncSetAttribute(k_fv_stage<a, b, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                       (int)FvShape<a, b>::smem());
+                       (int)FvShape<a, b>::smem_char());
   FV_SHAPES(FV_PREP)
 #undef FV_PREP
   int least = 0, greatest = 0;
@@ -507,11 +546,13 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
 #define FV_LAUNCH(a, b)                                    \
   if (g.tx == a && g.ty == b) {                           \
     cfg.blockDim = dim3(FvShape<a, b>::threads);          \
-    cfg.dynamicSmemBytes = FvShape<a, b>::smem();         \
-    if (g.weno_char)                                      \
+    if (g.weno_char) {                                    \
+      cfg.dynamicSmemBytes = FvShape<a, b>::smem_char();  \
       cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, true>, A);  \
-    else                                                  \
+    } else {                                              \
+      cfg.dynamicSmemBytes = FvShape<a, b>::smem();       \
       cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, false>, A); \
+    }                                                     \
     return;                                               \
   }
   FV_SHAPES(FV_LAUNCH)
