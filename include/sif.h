@@ -80,6 +80,13 @@ typedef struct {
                             Sec. 4); 1 = on the characteristic fields of the face state
                             (the mean of the two adjacent cells' stencil states), mapped
                             back by the right eigenvectors.  The adjoint calls require 0. */
+  double sigma;          /* surface tension coefficient (Eq. 10), >= 0; 0 = none.  The
+                            interface Riemann problem then carries the pressure jump
+                            p_N - p_P = sigma kappa, kappa = div(grad phi / |grad phi|)
+                            (positive where fluid N is convex), and each fluid receives
+                            the exchange flux of its own interface pressure (Eq. 11-12
+                            follow from recording fluid 1's).  2D only has curvature;
+                            the adjoint calls require 0. */
 } sif_config;
 
 /* Per-cycle record of the multi-time-step schedule (Sec. 3.1). */
@@ -210,8 +217,8 @@ void sif_batch_destroy(sif_batch *b);
  * owned by the context).  Resets the tape to length 0.  capacity 0 stops
  * recording and frees the tape.  While recording, steps run without the
  * captured graphs (same kernels, same results) and sif_step_multi_dt
- * returns SIF_ESTATE.  SIF_EINVAL for rk_order != 2, weno_char != 0 or
- * capacity < 0;
+ * returns SIF_ESTATE.  SIF_EINVAL for rk_order != 2, weno_char != 0,
+ * sigma != 0 or capacity < 0;
  * SIF_ECUDA if the tape cannot be allocated.  A step beyond capacity fails
  * with SIF_EINVAL before anything runs. */
 int sif_tape_reset(sif_ctx *ctx, int capacity);

@@ -46,7 +46,7 @@ class _Config(ctypes.Structure):
                 ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
-                ("weno_char", ctypes.c_int)]
+                ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -90,6 +90,9 @@ def lib():
         L.orc_cell_alpha.argtypes = [D, D, D, D]
         L.orc_riemann.argtypes = [dp, dp, dp]
         L.orc_char_basis.argtypes = [D, D, D, D, D, D, I, dp, dp]
+        L.orc_riemann_jump.argtypes = [dp, dp, D, dp]
+        L.orc_curvature.restype = D
+        L.orc_curvature.argtypes = [P, I, I]
         L.orc_step_taped.argtypes = [P, dp, dp, dp, dp]
         L.orc_replay_step.argtypes = [P, D, dp, dp, dp]
         L.orc_adjoint_step.argtypes = [P, D, dp, dp, dp, dp, dp]
@@ -136,6 +139,7 @@ def make_config(cfg: dict) -> _Config:
     c.flux_correction = int(cfg.get("flux_correction", 1))
     c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
     c.weno_char = int(cfg.get("weno_char", 0))
+    c.sigma = float(cfg.get("sigma", 0.0))
     return c
 
 
@@ -199,6 +203,9 @@ class Oracle:
     @property
     def status(self):
         return lib().orc_status(self._h)
+
+    def curvature(self, i, j):
+        return lib().orc_curvature(self._h, int(i), int(j))
 
     def geometry(self):
         nx, ny = self.nx, self.ny
@@ -316,6 +323,15 @@ def char_basis(gamma, pinf, rho, u, v, p, d):
     if rc:
         raise ValueError("non-physical state")
     return L.reshape(4, 4), R.reshape(4, 4)
+
+
+def riemann_jump(left, right, jump):
+    """As riemann() with the left star pressure exceeding the right one by
+    jump; p is the right star pressure, p_L the left one."""
+    L, R, out = _f64(left), _f64(right), np.empty(8)
+    rc = lib().orc_riemann_jump(_ptr(L), _ptr(R), float(jump), _ptr(out))
+    return {"p": out[0], "u": out[1], "rho_L": out[2], "rho_R": out[3],
+            "c_L": out[4], "c_R": out[5], "iters": int(out[6]), "p_L": out[7], "rc": rc}
 
 
 def riemann(left, right):

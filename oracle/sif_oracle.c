@@ -69,6 +69,7 @@ struct orc_ctx {
   double *phi;
   double *alpha, *ax, *ay, *sx, *sy; /* alpha_P, P-apertures, S (N to P) */
   double *xn[3];    /* interface exchange X as applied to fluid N */
+  double *xp[3];    /* and to fluid P (-xn without surface tension) */
   double *ul[2];    /* level-set velocity */
   double smax[2];   /* CFL maxima per fluid (cells and star states) */
   double lf[2][2];  /* Lax-Friedrichs alpha per fluid and direction */
@@ -482,19 +483,22 @@ static double star_density(double p, double rho, double pk, double g, double pi)
   return rho * pow(r, 1.0 / g);
 }
 
-int orc_riemann(const double *L, const double *R, double *out) {
+/* The star state satisfies u*_L = u*_R with p*_L = p*_R + jump: Newton on
+ * the right star pressure p for f_L(p + jump) + f_R(p) + u_R - u_L = 0,
+ * from the acoustic guess, each side's p + p_inf floored. */
+int orc_riemann_jump(const double *L, const double *R, double jump, double *out) {
   double rl = L[0], ul = L[1], pl = L[2], gl = L[3], pil = L[4];
   double rr = R[0], ur = R[1], pr = R[2], gr = R[3], pir = R[4];
   double cl = sqrt(gl * (pl + pil) / rl), cr = sqrt(gr * (pr + pir) / rr);
   double pscale = dmin(pl + pil, pr + pir);
-  double pfloor = -dmin(pil, pir) + 1e-12 * pscale;
-  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  double pfloor = dmax(-pir, -pil - jump) + 1e-12 * pscale;
+  double p = 0.5 * ((pl - jump) + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
   if (p < pfloor) p = pfloor;
   int it = 0, conv = 0, done = 0;
   double fl, dfl, fr, dfr;
   while (it < 50) {
     it++;
-    side_f(p, rl, pl, gl, pil, cl, &fl, &dfl);
+    side_f(p + jump, rl, pl, gl, pil, cl, &fl, &dfl);
     side_f(p, rr, pr, gr, pir, cr, &fr, &dfr);
     double F = fl + fr + (ur - ul);
     double pn = p - F / (dfl + dfr);
@@ -507,25 +511,55 @@ int orc_riemann(const double *L, const double *R, double *out) {
     }
     if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
   }
-  side_f(p, rl, pl, gl, pil, cl, &fl, &dfl);
+  double plst = p + jump;
+  side_f(plst, rl, pl, gl, pil, cl, &fl, &dfl);
   side_f(p, rr, pr, gr, pir, cr, &fr, &dfr);
   double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
-  double rsl = star_density(p, rl, pl, gl, pil);
+  double rsl = star_density(plst, rl, pl, gl, pil);
   double rsr = star_density(p, rr, pr, gr, pir);
   out[0] = p;
   out[1] = us;
   out[2] = rsl;
   out[3] = rsr;
-  out[4] = sqrt(gl * (p + pil) / rsl);
+  out[4] = sqrt(gl * (plst + pil) / rsl);
   out[5] = sqrt(gr * (p + pir) / rsr);
   out[6] = (double)it;
+  out[7] = plst;
   return (done || conv) ? 0 : ORC_ERR_NOCONV;
 }
 
-/* X for every cut cell (|S| > 0): fluid N receives momentum -p_I S and
- * energy -p_I u_I |S|, fluid P the opposite; no mass crosses. */
+int orc_riemann(const double *L, const double *R, double *out) {
+  double o8[8];
+  int rc = orc_riemann_jump(L, R, 0.0, o8);
+  for (int q = 0; q < 7; q++) out[q] = o8[q];
+  return rc;
+}
+
+/* curvature of the level set: (phi_xx phi_y^2 - 2 phi_x phi_y phi_xy +
+ * phi_yy phi_x^2) / |grad phi|^3, second-order central differences */
+static double curvature(const orc_ctx *o, const double *p, int i, int j) {
+  if (o->c.dim != 2) return 0.0;
+  double dx = o->c.dx, dy = o->c.dy;
+  double c0 = p[ID(o, i, j)];
+  double px = (p[ID(o, i + 1, j)] - p[ID(o, i - 1, j)]) / (2.0 * dx);
+  double py = (p[ID(o, i, j + 1)] - p[ID(o, i, j - 1)]) / (2.0 * dy);
+  double pxx = (p[ID(o, i + 1, j)] - 2.0 * c0 + p[ID(o, i - 1, j)]) / (dx * dx);
+  double pyy = (p[ID(o, i, j + 1)] - 2.0 * c0 + p[ID(o, i, j - 1)]) / (dy * dy);
+  double pxy = (p[ID(o, i + 1, j + 1)] - p[ID(o, i + 1, j - 1)] - p[ID(o, i - 1, j + 1)] +
+                p[ID(o, i - 1, j - 1)]) / (4.0 * dx * dy);
+  double g2 = px * px + py * py;
+  if (!(g2 > 0.0)) return 0.0;
+  return (pxx * py * py - 2.0 * px * py * pxy + pyy * px * px) / (g2 * sqrt(g2));
+}
+
+/* X for every cut cell (|S| > 0): fluid N receives momentum -p_I,N S and
+ * energy -p_I,N u_I |S|, fluid P momentum p_I,P S and energy p_I,P u_I |S|;
+ * no mass crosses.  Without surface tension p_I,N = p_I,P; with it the
+ * pressure jumps by sigma kappa from fluid P into fluid N (Eq. 10; kappa
+ * > 0 where fluid N is convex, as inside a drop of fluid N). */
 static void interface(orc_ctx *o, const double *p) {
   for (int m = 0; m < 3; m++) memset(o->xn[m], 0, sizeof(double) * o->NP);
+  for (int m = 0; m < 3; m++) memset(o->xp[m], 0, sizeof(double) * o->NP);
   for (int m = 0; m < 2; m++) memset(o->ul[m], 0, sizeof(double) * o->NP);
   double fac = 1.0 / o->c.dx + (o->c.dim == 2 ? 1.0 / o->c.dy : 0.0);
   for (int j = 0; j < o->c.ny; j++)
@@ -544,12 +578,16 @@ static void interface(orc_ctx *o, const double *p) {
                      o->w[0][3][c], o->c.gamma[0], o->c.pinf[0]};
       double R[5] = {o->w[1][0][c], o->w[1][1][c] * nxv + o->w[1][2][c] * nyv,
                      o->w[1][3][c], o->c.gamma[1], o->c.pinf[1]};
-      double out[7];
-      if (orc_riemann(L, R, out)) o->err |= ORC_ERR_NOCONV;
-      double ps = out[0], us = out[1];
-      o->xn[0][c] = -ps * Sx;
-      o->xn[1][c] = -ps * Sy;
-      o->xn[2][c] = -ps * us * Sm;
+      double out[8];
+      double jump = o->c.sigma != 0.0 ? o->c.sigma * curvature(o, p, i, j) : 0.0;
+      if (orc_riemann_jump(L, R, jump, out)) o->err |= ORC_ERR_NOCONV;
+      double psN = out[7], psP = out[0], us = out[1];
+      o->xn[0][c] = -psN * Sx;
+      o->xn[1][c] = -psN * Sy;
+      o->xn[2][c] = -psN * us * Sm;
+      o->xp[0][c] = psP * Sx;
+      o->xp[1][c] = psP * Sy;
+      o->xp[2][c] = psP * us * Sm;
       o->ul[0][c] = us * nxv;
       o->ul[1][c] = us * nyv;
       o->smax[0] = dmax(o->smax[0], (fabs(us) + out[4]) * fac);
@@ -760,14 +798,14 @@ static void fv_rhs(orc_ctx *o, int k, double *const L[4]) {
         face_flux(o, k, c, o->PX, 1, Fh);
         for (int m = 0; m < 4; m++) o->fy[m][c] = A * Fh[m];
       }
-  double sgn = k == 0 ? 1.0 : -1.0, dxdy = o->c.dx * o->c.dy;
+  double dxdy = o->c.dx * o->c.dy;
   for (int j = 0; j < ny; j++)
     for (int i = 0; i < nx; i++) {
       int c = ID(o, i, j);
       for (int m = 0; m < 4; m++) {
         double r = (o->fx[m][c] - o->fx[m][ID(o, i + 1, j)]) / o->c.dx;
         if (o->c.dim == 2) r += (o->fy[m][c] - o->fy[m][ID(o, i, j + 1)]) / o->c.dy;
-        if (m > 0) r += sgn * o->xn[m - 1][c] / dxdy;
+        if (m > 0) r += (k == 0 ? o->xn : o->xp)[m - 1][c] / dxdy;
         L[m][c] = r;
       }
     }
@@ -1013,12 +1051,11 @@ int orc_step_single_dt(orc_ctx *o, int nsteps, double t_end, orc_info *info) {
 /* Eq. 8 (shared evaluation) or Eq. 9 (fluid-2-only evaluation): update of
  * the correction quantities with the exchange flux as applied to fluid 1 */
 static void record(orc_ctx *o, int f1, int shared, double dt1, double dt2) {
-  double sgn = f1 == 0 ? 1.0 : -1.0;
   for (int j = 0; j < o->c.ny; j++)
     for (int i = 0; i < o->c.nx; i++) {
       int c = ID(o, i, j);
       for (int m = 0; m < 3; m++) {
-        double x1 = sgn * o->xn[m][c];
+        double x1 = (f1 == 0 ? o->xn : o->xp)[m][c];
         if (shared) o->xc[m][c] = o->xc[m][c] + (-0.5 * x1) * dt1;
         o->xc[m][c] = o->xc[m][c] + (0.5 * x1) * dt2;
       }
@@ -1178,6 +1215,7 @@ orc_ctx *orc_create(const orc_config *cfg) {
     return NULL;
   if (cfg->rk_order != 2 && cfg->rk_order != 3) return NULL;
   if (cfg->weno_char != 0 && cfg->weno_char != 1) return NULL;
+  if (!(cfg->sigma >= 0.0) || !isfinite(cfg->sigma)) return NULL;
   orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   o->c = *cfg;
   if (o->c.dim == 1) o->c.bc[2] = o->c.bc[3] = ORC_BC_ZEROGRAD;
@@ -1202,6 +1240,7 @@ orc_ctx *orc_create(const orc_config *cfg) {
   }
   for (int m = 0; m < 3; m++) {
     o->xn[m] = plane(o);
+    o->xp[m] = plane(o);
     o->xc[m] = plane(o);
   }
   o->ul[0] = plane(o);
@@ -1241,6 +1280,7 @@ void orc_destroy(orc_ctx *o) {
   }
   for (int m = 0; m < 3; m++) {
     free(o->xn[m]);
+    free(o->xp[m]);
     free(o->xc[m]);
   }
   free(o->ul[0]);
@@ -1332,6 +1372,11 @@ int orc_integrals(const orc_ctx *o, double *out) {
       out[k * 4 + m] = s * (o->c.dx * o->c.dy);
     }
   return 0;
+}
+
+double orc_curvature(orc_ctx *o, int i, int j) {
+  fill_ghost(o, o->phi, 0);
+  return curvature(o, o->phi, i, j);
 }
 
 double orc_time(const orc_ctx *o) { return o->t; }
@@ -1838,8 +1883,9 @@ static void rhs_T(orc_ctx *o, double *const W[2][4], const double *lf, double *c
 
 int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1,
                      const double *phi2, const double *lam_in, double *lam_out) {
-  /* the adjoint is written for the component-wise reconstruction */
-  if (o->c.rk_order != 2 || o->c.weno_char) {
+  /* the adjoint is written for the component-wise reconstruction without
+   * surface tension */
+  if (o->c.rk_order != 2 || o->c.weno_char || o->c.sigma != 0.0) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }
@@ -1944,7 +1990,7 @@ int orc_rhs_frozen(orc_ctx *o, const double *lf, double *out) {
 }
 
 int orc_rhs_adjoint(orc_ctx *o, const double *lf, const double *mu_in, double *lq_out) {
-  if (o->c.weno_char) {
+  if (o->c.weno_char || o->c.sigma != 0.0) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }

@@ -45,6 +45,7 @@ typedef struct {
   int flux_correction;   /* 1 = interfacial flux correction on */
   int force_ratio_one;   /* test only: multi-dt cycle with dt1 = dt2 */
   int weno_char;         /* 1 = WENO5 on characteristic fields, 0 = component-wise */
+  double sigma;          /* surface tension coefficient (Eq. 10); 0 = none */
 } orc_config;
 
 typedef struct {
@@ -75,6 +76,16 @@ int orc_status(const orc_ctx *o);
  * the interface vector S (N to P) per cell. Any output may be NULL. */
 int orc_geometry(orc_ctx *o, double *alpha, double *ax, double *ay,
                  double *sx, double *sy);
+/* Exact two-material Riemann problem with a pressure jump across the
+ * contact: the left star pressure exceeds the right one by jump (surface
+ * tension, Eq. 10).  L, R = (rho, u, p, gamma, pinf).  out = right star
+ * pressure, star velocity, left and right star densities and sound
+ * speeds, Newton iterations, left star pressure.  Returns ORC_ERR_NOCONV if
+ * Newton does not converge in 50 iterations. */
+int orc_riemann_jump(const double *L, const double *R, double jump, double *out);
+/* Curvature div(grad phi / |grad phi|) of the current level set at cell
+ * (i, j) by central differences (0 in 1D or where grad phi = 0). */
+double orc_curvature(orc_ctx *o, int i, int j);
 /* Characteristic basis of the Euler flux Jacobian in direction d (0 = x,
  * 1 = y) at the primitive state (rho, u, v, p) of a stiffened gas (g, pinf):
  * R[m*4+f] = component m of the right eigenvector of field f (eigenvalues

@@ -20,7 +20,7 @@ struct sif_ctx {
   Grid g;
   cudaStream_t st;
   size_t NP;
-  double *q[2][4], *w[2][4], *phi, *alpha, *ax, *ay, *sx, *sy, *xn[3], *ul[2];
+  double *q[2][4], *w[2][4], *phi, *alpha, *ax, *ay, *sx, *sy, *xn[3], *xm[3], *ul[2];
   double *q0[2][4], *prev[4], *fut[4], *qi[4], *xc[3], *phi0, *phiR;
   double *tmp;       // band-indexed scratch, 8 planes
   int *bandmap;      // cell -> position in the interaction band, -1 outside
@@ -139,6 +139,7 @@ static int validate(const sif_config *f, char *why, size_t n) {
   if (!(f->cfl > 0.0) || f->cfl > 1.0) return snprintf(why, n, "cfl must be in (0, 1]"), SIF_EINVAL;
   if (f->rk_order != 2 && f->rk_order != 3) return snprintf(why, n, "rk_order must be 2 or 3"), SIF_EINVAL;
   if (f->weno_char != 0 && f->weno_char != 1) return snprintf(why, n, "weno_char must be 0 or 1"), SIF_EINVAL;
+  if (!(f->sigma >= 0.0 && f->sigma < 1e300)) return snprintf(why, n, "sigma must be finite and >= 0"), SIF_EINVAL;
   // the face values' reciprocal needs the product of two denominators,
   // each at least eps^4, to stay normal
   if (!(f->weno_eps >= 1e-20)) return snprintf(why, n, "weno_eps must be >= 1e-20"), SIF_EINVAL;
@@ -212,6 +213,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.ext_iters = f.ext_iters;
   g.reinit_iters = f.reinit_iters;
   g.weno_char = f.weno_char;
+  g.sigma = f.sigma;
   g.tx = FV_TX;
   g.ty = FV_TY;
   g.ntx = (f.nx + g.tx - 1) / g.tx;
@@ -243,6 +245,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     c->sx = plane();
     c->sy = plane();
     for (int m = 0; m < 3; m++) c->xn[m] = plane();
+    for (int m = 0; m < 3; m++) c->xm[m] = plane();
     for (int m = 0; m < 2; m++) c->ul[m] = plane();
     for (int k = 0; k < 2; k++)
       for (int m = 0; m < 4; m++) c->q0[k][m] = plane();
@@ -486,8 +489,8 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
   dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
-  launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, band_work(c), c->xn[0],
-                   c->xn[1], c->xn[2], c->ul[0], c->ul[1], c->sc, c->st);
+  launch_interface(c->g, c->w[0], c->w[1], c->phi, c->sx, c->sy, c->cut, band_work(c), c->xn,
+                   c->xm, c->ul[0], c->ul[1], c->sc, c->st);
   dbg(c, "interface");
 }
 
@@ -513,9 +516,11 @@ static void copy_planes(sif_ctx *c, double *const dst[4], double *const src[4], 
 
 static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const base[4],
                double *const cur[4], const double *dtp) {
+  // the exchange flux planes of fluid k (fluid P's negated)
+  double *const *X = k == 0 ? c->xn : c->xm;
   ghost_w(c, k);
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
-                  c->sy, c->xn[0], c->xn[1], c->xn[2], c->tiles[k], ntile(c), c->num_sms, dtp,
+                  c->sy, X[0], X[1], X[2], c->tiles[k], ntile(c), c->num_sms, dtp,
                   c->sc, c->st);
   dbg(c, "fv_stage");
 }
@@ -724,7 +729,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
       return c->hsc->err ? SIF_OK : SIF_ENONPHYS;
     }
     const int last = c->hsc->last;
-    launch_record(c->g, sub == 1, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0],
+    launch_record(c->g, sub == 1, c->cut, ncell(c), c->xn, c->xm, c->xc[0],
                   c->xc[1], c->xc[2], c->sc, c->st);
     // step 3: fluid-2 and level-set first RK stage with dt2
     copy_planes(c, c->q0[f2], c->q[f2], 4);
@@ -745,7 +750,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
     eval(c, qs, last ? -1 : f1);
     ul_extend(c);
-    launch_record(c->g, last, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0],
+    launch_record(c->g, last, c->cut, ncell(c), c->xn, c->xm, c->xc[0],
                   c->xc[1], c->xc[2], c->sc, c->st);
     // step 4 (and 5 on the last sub-step): second RK stage
     fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
@@ -863,7 +868,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   launch_cond(COND_LAST, c->sc, hl1, hn1, 0, 0, c->st);
   launch_cond(COND_LAST, c->sc, hl2, hn2, 0, 0, c->st);
   launch_cond(COND_LAST, c->sc, hl3, 0, 0, 0, c->st);
-  launch_record(c->g, -1, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0], c->xc[1],
+  launch_record(c->g, -1, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 3: fluid-2 and level-set first RK stage with dt2
   copy4(c, c->q0[f2], c->q[f2]);
@@ -883,7 +888,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   });
   eval(c, qs, f1, &c->sc->last);
   ul_extend(c);
-  launch_record(c->g, -2, c->cut, ncell(c), c->xn[0], c->xn[1], c->xn[2], c->xc[0], c->xc[1],
+  launch_record(c->g, -2, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 4 (and 5 on the last sub-step): second RK stage
   fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
@@ -1446,8 +1451,9 @@ extern "C" int sif_tape_reset(sif_ctx *c, int capacity) {
     set_err(c, "the adjoint is defined for rk_order 2");
     return SIF_EINVAL;
   }
-  if (c->cfg.weno_char) {
-    set_err(c, "the adjoint is defined for the component-wise reconstruction (weno_char 0)");
+  if (c->cfg.weno_char || c->cfg.sigma != 0.0) {
+    set_err(c, "the adjoint is defined for the component-wise reconstruction (weno_char 0) "
+               "without surface tension (sigma 0)");
     return SIF_EINVAL;
   }
   cudaSetDevice(c->cfg.device);

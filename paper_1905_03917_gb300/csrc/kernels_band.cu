@@ -159,11 +159,14 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
 // evaluates its own side's wave function and derivative, the pair
 // exchanges them, and both lanes take the same Newton step with the same
 // operations in the same order as riemann_solve, so the star state is the
-// same to the bit.  Returns 0 or DERR_NOCONV; out: p*, u*, and the lane's
-// own star sound speed.
+// same to the bit.  With surface tension the left star pressure exceeds
+// the right one by jump (Eq. 10): Newton runs on the right star pressure p,
+// the left lane evaluating its wave function at p + jump.  Returns 0 or
+// DERR_NOCONV; out: the lane's own star pressure, u*, and the lane's own
+// star sound speed.
 __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, double un,
-                                         double pk, double gk, double pik, double &ps,
-                                         double &us, double &cs) {
+                                         double pk, double gk, double pik, double jump,
+                                         double &ps, double &us, double &cs) {
   double ck = sqrt(gk * (pk + pik) / rho);
   double ro = __shfl_xor_sync(pair, rho, 1), uo = __shfl_xor_sync(pair, un, 1);
   double po = __shfl_xor_sync(pair, pk, 1), pio = __shfl_xor_sync(pair, pik, 1);
@@ -173,14 +176,15 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
   double rr = L ? ro : rho, ur = L ? uo : un, pr = L ? po : pk, pir = L ? pio : pik;
   double cl = L ? ck : co, cr = L ? co : ck;
   double pscale = fmin(pl + pil, pr + pir);
-  double pfloor = -fmin(pil, pir) + 1e-12 * pscale;
-  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  double pfloor = fmax(-pir, -pil - jump) + 1e-12 * pscale;
+  double p = 0.5 * ((pl - jump) + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
   if (p < pfloor) p = pfloor;
+  const double own = L ? jump : 0.0;  // this lane's star pressure is p + own
   int it = 0, conv = 0, done = 0;
   double f, df;
   while (it < 50) {
     it++;
-    riemann_side(p, rho, pk, gk, pik, ck, f, df);
+    riemann_side(p + own, rho, pk, gk, pik, ck, f, df);
     double fo = __shfl_xor_sync(pair, f, 1), dfo = __shfl_xor_sync(pair, df, 1);
     double fl = L ? f : fo, fr = L ? fo : f, dfl = L ? df : dfo, dfr = L ? dfo : df;
     double F = fl + fr + (ur - ul);
@@ -194,14 +198,33 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
     }
     if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
   }
-  riemann_side(p, rho, pk, gk, pik, ck, f, df);
+  ps = p + own;
+  riemann_side(ps, rho, pk, gk, pik, ck, f, df);
   double fo = __shfl_xor_sync(pair, f, 1);
   double fl = L ? f : fo, fr = L ? fo : f;
   us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
-  double rs = riemann_star_density(p, rho, pk, gk, pik);
-  ps = p;
-  cs = sqrt(gk * (p + pik) / rs);
+  double rs = riemann_star_density(ps, rho, pk, gk, pik);
+  cs = sqrt(gk * (ps + pik) / rs);
   return (done || conv) ? 0 : DERR_NOCONV;
+}
+
+// curvature div(grad phi / |grad phi|) at cell (i, j): (phi_xx phi_y^2 -
+// 2 phi_x phi_y phi_xy + phi_yy phi_x^2) / |grad phi|^3 from second-order
+// central differences; 0 in 1D or where grad phi vanishes
+__device__ inline double curvature(const Grid &g, const double *phi, int i, int j) {
+  if (g.dim != 2) return 0.0;
+  const double dx = g.dx, dy = g.dy;
+  const double c0 = phi[gidx(g, i, j)];
+  const double e = phi[gidx(g, i + 1, j)], w = phi[gidx(g, i - 1, j)];
+  const double n = phi[gidx(g, i, j + 1)], s = phi[gidx(g, i, j - 1)];
+  const double px = (e - w) / (2.0 * dx), py = (n - s) / (2.0 * dy);
+  const double pxx = (e - 2.0 * c0 + w) / (dx * dx), pyy = (n - 2.0 * c0 + s) / (dy * dy);
+  const double pxy = (phi[gidx(g, i + 1, j + 1)] - phi[gidx(g, i + 1, j - 1)] -
+                      phi[gidx(g, i - 1, j + 1)] + phi[gidx(g, i - 1, j - 1)]) /
+                     (4.0 * dx * dy);
+  const double g2 = px * px + py * py;
+  if (!(g2 > 0.0)) return 0.0;
+  return (pxx * py * py - 2.0 * px * py * pxy + pyy * px * px) / (g2 * sqrt(g2));
 }
 
 // two lanes per cut cell (blockDim a multiple of 32)
@@ -211,8 +234,9 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
                             const double *__restrict__ p2, const double *__restrict__ p3,
                             const double *__restrict__ phi, const double *__restrict__ sx,
                             const double *__restrict__ sy, const int *__restrict__ cut,
-                            const int *ncut, double *xn0, double *xn1, double *xn2, double *ul0,
-                            double *ul1, Scalars *sc) {
+                            const int *ncut, double *xn0, double *xn1, double *xn2,
+                            double *xm0, double *xm1, double *xm2, double *ul0, double *ul1,
+                            Scalars *sc) {
   SIF_TICK();
   int n = *ncut;
   double fac = 1.0 / g.dx + (g.dim == 2 ? 1.0 / g.dy : 0.0);
@@ -241,9 +265,16 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
       un = p1[c] * nxv + p2[c] * nyv;
       pk = p3[c];
     }
+    // surface tension: the pressure jumps by sigma kappa from fluid P into
+    // fluid N (Eq. 10; kappa > 0 where fluid N is convex)
+    const double jump = g.sigma != 0.0 ? g.sigma * curvature(g, phi, i, j) : 0.0;
     double ps, us, cs;
-    int e = riemann_solve_pair(pair, side, rho, un, pk, g.gamma[side], g.pinf[side], ps, us, cs);
+    int e = riemann_solve_pair(pair, side, rho, un, pk, g.gamma[side], g.pinf[side], jump, ps,
+                               us, cs);
     if (e && side == 0) atomicOr(&sc->err, e);
+    // each fluid's exchange flux with its own interface pressure: fluid N
+    // -p_N (S, u* |S|) in xn, fluid P +p_P (S, u* |S|), stored negated in xm
+    // (so that without surface tension xm equals xn bitwise)
     if (side == 0) {
       xn0[c] = -ps * Sx;
       xn1[c] = -ps * Sy;
@@ -252,6 +283,9 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
       ul1[c] = us * nyv;
       sN = fmax(sN, (fabs(us) + cs) * fac);
     } else {
+      xm0[c] = -ps * Sx;
+      xm1[c] = -ps * Sy;
+      xm2[c] = -ps * us * Sm;
       sP = fmax(sP, (fabs(us) + cs) * fac);
     }
   }
@@ -260,7 +294,7 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
 
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
-                      double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
+                      double *const xn[3], double *const xm[3], double *ul0, double *ul1,
                       Scalars *sc, cudaStream_t st) {
   // one warp (16 cut cells) per block: the Newton solves are bound by the
   // FP64 lanes of the SMs they occupy, and a few hundred cut cells in
@@ -268,7 +302,8 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
   // count (the kernel loops over the device count).
   int blocks = grid_for(2 * cut_cap, 32, 9728);
   k_interface<<<blocks, 32, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
-                                      phi, sx, sy, cut, &sc->n_cut, xn0, xn1, xn2, ul0, ul1, sc);
+                                      phi, sx, sy, cut, &sc->n_cut, xn[0], xn[1], xn[2], xm[0],
+                                      xm[1], xm[2], ul0, ul1, sc);
   sif_note_launches(1);
 }
 
@@ -464,13 +499,19 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
 // Eq. 8 (shared) / Eq. 9 (fluid-2 only) correction quantities, in the
 // frame of fluid 1, accumulated in the cut cells of this interaction
 
+// X_1, the exchange flux as applied to fluid 1 (with fluid 1's own
+// interface pressure): fluid N's planes, or fluid P's negated planes
+// negated back, by the cycle's role
 __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncut,
-                         const double *__restrict__ x0, const double *__restrict__ x1,
-                         const double *__restrict__ x2, double *c0, double *c1, double *c2,
-                         const Scalars *sc) {
+                         const double *__restrict__ n0, const double *__restrict__ n1,
+                         const double *__restrict__ n2, const double *__restrict__ m0,
+                         const double *__restrict__ m1, const double *__restrict__ m2,
+                         double *c0, double *c1, double *c2, const Scalars *sc) {
   SIF_TICK();
   int n = *ncut;
-  double sgn = sc->f1 == 0 ? 1.0 : -1.0;
+  const bool fN = sc->f1 == 0;
+  const double sgn = fN ? 1.0 : -1.0;
+  const double *x0 = fN ? n0 : m0, *x1 = fN ? n1 : m1, *x2 = fN ? n2 : m2;
   double dt1 = sc->dt1, dt2 = sc->dt2;
   if (shared == -1) shared = sc->sub == 1;
   else if (shared == -2) shared = sc->last;
@@ -490,11 +531,12 @@ __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncu
   }
 }
 
-void launch_record(const Grid &, int shared, const int *cut, int cut_cap, const double *xn0,
-                   const double *xn1, const double *xn2, double *xc0, double *xc1, double *xc2,
-                   Scalars *sc, cudaStream_t st) {
+void launch_record(const Grid &, int shared, const int *cut, int cut_cap, double *const xn[3],
+                   double *const xm[3], double *xc0, double *xc1, double *xc2, Scalars *sc,
+                   cudaStream_t st) {
   int blocks = grid_for(cut_cap, 128, 1216);
-  k_record<<<blocks, 128, 0, st>>>(shared, cut, &sc->n_cut, xn0, xn1, xn2, xc0, xc1, xc2, sc);
+  k_record<<<blocks, 128, 0, st>>>(shared, cut, &sc->n_cut, xn[0], xn[1], xn[2], xm[0], xm[1],
+                                   xm[2], xc0, xc1, xc2, sc);
   sif_note_launches(1);
 }
 

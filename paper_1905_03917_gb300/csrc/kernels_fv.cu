@@ -21,7 +21,7 @@ struct FvArgs {
   const double *cur[4];
   const double *w[4];
   const double *ax, *ay, *sx, *sy;
-  const double *xn[3];
+  const double *xn[3];  // exchange flux planes: X applied to fluid k is (k ? -1 : 1) xn
   const int *tiles;
   const int *ntiles;
   int split_below;  // tile count under which each tile is split over two CTAs

@@ -34,6 +34,7 @@ struct Grid {
   double cfl, weno_eps, mix_alpha, band;
   int ext_iters, reinit_iters;
   int weno_char;  // finite-volume reconstruction on characteristic fields
+  double sigma;   // surface tension coefficient (Eq. 10), 0 = none
   int tx, ty;    // finite-volume tile shape (output cells per CTA)
   int ntx, nty;  // tiles per direction
 };
@@ -404,7 +405,7 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
                   cudaStream_t st);
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
-                      double *xn0, double *xn1, double *xn2, double *ul0, double *ul1,
+                      double *const xn[3], double *const xm[3], double *ul0, double *ul1,
                       Scalars *sc, cudaStream_t st);
 void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *phi0,
                      const double *ul0, const double *ul1, const int *band, const int *nband,
@@ -413,9 +414,9 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
                    int rext_cap, double *tmp, cudaStream_t st);
 // shared: 1 = Eq. 8, 0 = Eq. 9, -1 = Eq. 8 on the first sub-step (device
 // decides), -2 = Eq. 8 on the last sub-step (device decides)
-void launch_record(const Grid &g, int shared, const int *cut, int cut_cap, const double *xn0,
-                   const double *xn1, const double *xn2, double *xc0, double *xc1, double *xc2,
-                   Scalars *sc, cudaStream_t st);
+void launch_record(const Grid &g, int shared, const int *cut, int cut_cap, double *const xn[3],
+                   double *const xm[3], double *xc0, double *xc1, double *xc2, Scalars *sc,
+                   cudaStream_t st);
 // Eq. 7 interpolation of fluid 1 at theta over the cells of a band list
 void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
                    double *const fut[4], const double *thp, const int *band, const int *nband,

@@ -273,3 +273,28 @@ def degenerate(kind, seed=0):
     pN = _uniform(X.shape, 1.2, 0.0, 0.0, 1.0e5)
     pP = _uniform(X.shape, 1000.0, 0.0, 0.0, 1.0e6)
     return {"name": f"degenerate_{kind}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def static_drop(n=64, sigma=36.0, equilibrium=False, liquid=True):
+    """The static drop of Sec. 4.3 (Laplace law): a drop of radius 0.1
+    (fluid N, phi = r - 0.1) at the centre of the unit box in air, both at
+    rest at p0 = 1e3, surface tension sigma = 36, so that the pressure jump
+    tends to sigma / R = 360.  The paper's Tait liquid (rho0 = 1000, B =
+    5e5, gamma = 7.15) is the isentrope of a stiffened gas with gamma 7.15
+    and p_inf = B - p0; air is an ideal gas (gamma 1.4, rho 1).  liquid=False
+    makes the drop a gas too (gamma 1.4, rho 10): its rho c^2 is ~1000 times
+    smaller, so the pressure noise of sub-cell interface motion stays far
+    below the Laplace jump.  Reflective walls stand in for the paper's
+    no-slip walls (no viscosity here).  equilibrium=True starts the drop at
+    p0 + sigma / R instead of p0."""
+    d = 1.0 / n
+    p0 = 1.0e3
+    matN = {"gamma": 7.15, "pinf": 5.0e5 - p0} if liquid else {"gamma": 1.4, "pinf": 0.0}
+    matP = {"gamma": 1.4, "pinf": 0.0}
+    cfg = config(n, n, d, d, matN, matP, ["reflect"] * 4, sigma=sigma)
+    X, Y = _centres(cfg)
+    phi = np.hypot(X - 0.5, Y - 0.5) - 0.1
+    pN = _uniform(X.shape, 1000.0 if liquid else 10.0, 0.0, 0.0,
+                  p0 + (sigma / 0.1 if equilibrium else 0.0))
+    pP = _uniform(X.shape, 1.0, 0.0, 0.0, p0)
+    return {"name": f"static_drop_{'liquid' if liquid else 'gas'}_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}

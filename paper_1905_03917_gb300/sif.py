@@ -50,7 +50,7 @@ class Config(ctypes.Structure):
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("weno_char", ctypes.c_int)]
+                ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -149,6 +149,7 @@ def make_config(cfg: dict, stream=None, device=0) -> Config:
     c.cuda_stream = stream
     c.device = int(device)
     c.weno_char = int(cfg.get("weno_char", 0))
+    c.sigma = float(cfg.get("sigma", 0.0))
     return c
 
 

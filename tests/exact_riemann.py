@@ -53,6 +53,27 @@ def star_state(L, R):
     return p, us
 
 
+def star_state_jump(L, R, jump):
+    """As star_state with the left star pressure exceeding the right one by
+    jump (a surface-tension pressure jump): returns the right star pressure
+    p*, u*; the left star pressure is p* + jump."""
+    rl, ul, pl, gl, pil = L
+    rr, ur, pr, gr, pir = R
+
+    def F(p):
+        return (velocity_jump(p + jump, rl, pl, gl, pil) + velocity_jump(p, rr, pr, gr, pir)
+                + (ur - ul))
+
+    lo = max(-pir, -pil - jump) + 1e-9 * min(pl + pil, pr + pir)
+    hi = max(pl, pr) * 10.0 + abs(jump) + 1.0
+    while F(hi) < 0.0:
+        hi *= 10.0
+    p = brentq(F, lo, hi, xtol=1e-300, rtol=1e-15, maxiter=500)
+    us = 0.5 * (ul + ur) + 0.5 * (velocity_jump(p, rr, pr, gr, pir)
+                                  - velocity_jump(p + jump, rl, pl, gl, pil))
+    return p, us
+
+
 def sample_left_rarefaction_right_shock(L, R, x0, t, x):
     """Density at positions x (iterable) for a left rarefaction / right
     shock wave pattern; returns (rho(x) list, p*, u*, contact position)."""

@@ -1,0 +1,141 @@
+"""Pins of the oracle's surface tension (Eq. 10, Sec. 4.3; not part of the
+compressible method's hot path, the survey's NEXT-2 item): the interface
+Riemann problem with a pressure jump against an independent solver and
+the static equilibrium it must keep, the level-set curvature against the
+exact curvature of circles and lines, and the Laplace law of a static
+drop, whose pressure jump must be sigma / R."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_03917_gb300 import inputs
+from tests import exact_riemann as ER
+
+LIQUID = (1000.0, 0.0, 1.36e3, 7.15, 4.99e5)
+GAS = (1.0, 0.0, 1.0e3, 1.4, 0.0)
+CASES = [
+    ((1000.0, 2.0, 1.0e6, 4.4, 6.0e8), (1.0, -30.0, 1.0e5, 1.4, 0.0), 2.0e3),
+    ((1.0, 50.0, 1.0e5, 1.4, 0.0), (1000.0, 0.0, 1.0e9, 4.4, 6.0e8), -5.0e4),
+    ((10.0, 0.0, 1.4e3, 1.4, 0.0), (1.0, 0.0, 1.0e3, 1.4, 0.0), 360.0),
+    ((1.2, -100.0, 2.0e5, 1.4, 0.0), (0.9, 100.0, 1.0e5, 1.67, 0.0), 500.0),
+]
+
+
+def test_laplace_equilibrium_is_a_static_solution():
+    # at rest with p_L - p_R equal to the jump: nothing moves
+    r = O.riemann_jump(LIQUID, GAS, 360.0)
+    assert r["rc"] == 0
+    assert r["p"] == pytest.approx(1.0e3, rel=1e-12)
+    assert r["p_L"] == pytest.approx(1.36e3, rel=1e-12)
+    assert abs(r["u"]) <= 1e-12
+    assert r["rho_L"] == pytest.approx(1000.0, rel=1e-12)
+    assert r["rho_R"] == pytest.approx(1.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("L,R,jump", CASES)
+def test_jump_solution_against_independent_solver(L, R, jump):
+    r = O.riemann_jump(L, R, jump)
+    ps, us = ER.star_state_jump(L, R, jump)
+    assert r["rc"] == 0 and r["iters"] < 50
+    assert abs(r["p"] - ps) <= 1e-11 * (abs(ps) + R[4])
+    assert r["p_L"] == r["p"] + jump
+    assert abs(r["u"] - us) <= 1e-10 * max(abs(us), 1.0)
+
+
+def test_zero_jump_is_the_plain_solver():
+    for L, R, _ in CASES:
+        a, b = O.riemann_jump(L, R, 0.0), O.riemann(L, R)
+        for k in ("p", "u", "rho_L", "rho_R", "c_L", "c_R"):
+            assert a[k] == b[k]
+        assert a["p_L"] == a["p"]
+
+
+def _curvature_errors(n):
+    c = inputs.static_drop(n)
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    g = o.geometry()
+    d = 1.0 / n
+    x = (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(x, x)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    cut = (g["sx"] != 0) | (g["sy"] != 0)
+    err = [abs(o.curvature(i, j) - 1.0 / r[j, i]) for j, i in zip(*np.nonzero(cut))]
+    return max(err) * 0.1  # relative to 1/R
+
+
+def test_curvature_of_circles_converges_second_order():
+    # phi = r - R: every level set is a circle, of curvature 1/r
+    errs = [_curvature_errors(n) for n in (32, 64, 128)]
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 2e-3 and min(orders) >= 1.8, (errs, orders)
+
+
+def test_curvature_of_a_line_is_zero():
+    c = inputs.static_interface(32, 32, angle=0.7)
+    c["cfg"]["sigma"] = 1.0
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    assert max(abs(o.curvature(i, j)) for i in range(1, 31) for j in range(1, 31)) <= 1e-9
+
+
+def _laplace_jump(n, steps, multi=False):
+    c = inputs.static_drop(n, equilibrium=True, liquid=False)
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    d = 1.0 / n
+    x = (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(x, x)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    I0 = o.integrals()
+    hist = []
+    for s in range(steps):
+        (o.step_multi_dt if multi else o.step_single_dt)(1)
+        if s % 10 == 9:
+            qN, qP, _ = o.state()
+            a = o.geometry()["alpha"]
+            inn, out = (r < 0.1 - 2 * d) & (a < 1e-3), (r > 0.1 + 2 * d) & (a > 0.999)
+
+            def pres(q, al, mask):
+                rho = q[0][mask] / al[mask]
+                u, v = q[1][mask] / q[0][mask], q[2][mask] / q[0][mask]
+                return (0.4 * (q[3][mask] / al[mask] - 0.5 * rho * (u * u + v * v))).mean()
+            hist.append(pres(qN, 1 - a, inn) - pres(qP, a, out))
+    assert o.status == 0
+    return np.array(hist), I0, o
+
+
+def test_static_drop_keeps_the_laplace_jump():
+    """A gas drop started in Laplace equilibrium (p inside = p outside +
+    sigma / R) keeps the jump sigma / R = 360 within a few per cent, and the
+    mean jump over the run approaches 360 as the grid refines."""
+    h32, _, _ = _laplace_jump(32, 300)
+    h64, _, _ = _laplace_jump(64, 300)
+    assert np.abs(h64 / 360.0 - 1.0).max() <= 0.05, h64
+    e32, e64 = abs(h32.mean() / 360.0 - 1.0), abs(h64.mean() / 360.0 - 1.0)
+    assert e64 < e32 and e64 < 0.03, (e32, e64)
+
+
+def test_surface_tension_keeps_each_fluids_mass():
+    # no mass crosses the interface; the sub-cycled cycle with the
+    # correction keeps both fluids' masses
+    h, I0, o = _laplace_jump(32, 60, multi=True)
+    I1 = o.integrals()
+    for k in range(2):
+        assert abs(I1[k, 0] - I0[k, 0]) <= 1e-13 * I0[k, 0]
+
+
+def test_no_jump_without_sigma():
+    # the same drop at uniform pressure without surface tension: the
+    # pressure difference stays near zero (the spurious motion of a curved
+    # sharp interface at rest is a few pascals here), against 360 with it
+    c = inputs.static_drop(32, sigma=0.0, equilibrium=False, liquid=False)
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    d = 1.0 / 32
+    x = (np.arange(32) + 0.5) * d
+    X, Y = np.meshgrid(x, x)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    o.step_single_dt(100)
+    qN, qP, _ = o.state()
+    a = o.geometry()["alpha"]
+    inn, out = (r < 0.1 - 2 * d) & (a < 1e-3), (r > 0.1 + 2 * d) & (a > 0.999)
+    pin = (0.4 * qN[3][inn] / (1 - a[inn])).mean()  # nearly at rest: p = (g-1) E
+    pout = (0.4 * qP[3][out] / a[out]).mean()
+    assert abs(pin - pout) <= 0.05 * 360.0
