@@ -87,6 +87,12 @@ typedef struct {
                             the exchange flux of its own interface pressure (Eq. 11-12
                             follow from recording fluid 1's).  2D only has curvature;
                             the adjoint calls require 0. */
+  double mu[2];          /* dynamic viscosities of fluids N and P (Eq. 3, 5), >= 0; 0 =
+                            inviscid.  Face viscous fluxes by central differences of the
+                            stencil states times the apertures; each fluid's viscous
+                            traction on its interface boundary through S; the explicit
+                            viscous limit 2 nu (1/dx^2 + 1/dy^2) joins the CFL rate.  The
+                            adjoint calls require 0. */
 } sif_config;
 
 /* Per-cycle record of the multi-time-step schedule (Sec. 3.1). */
@@ -218,7 +224,7 @@ void sif_batch_destroy(sif_batch *b);
  * recording and frees the tape.  While recording, steps run without the
  * captured graphs (same kernels, same results) and sif_step_multi_dt
  * returns SIF_ESTATE.  SIF_EINVAL for rk_order != 2, weno_char != 0,
- * sigma != 0 or capacity < 0;
+ * sigma != 0, mu != 0 or capacity < 0;
  * SIF_ECUDA if the tape cannot be allocated.  A step beyond capacity fails
  * with SIF_EINVAL before anything runs. */
 int sif_tape_reset(sif_ctx *ctx, int capacity);

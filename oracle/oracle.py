@@ -46,7 +46,8 @@ class _Config(ctypes.Structure):
                 ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
-                ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double)]
+                ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("mu", ctypes.c_double * 2)]
 
 
 class _Info(ctypes.Structure):
@@ -140,6 +141,8 @@ def make_config(cfg: dict) -> _Config:
     c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
     c.weno_char = int(cfg.get("weno_char", 0))
     c.sigma = float(cfg.get("sigma", 0.0))
+    mu = cfg.get("mu", (0.0, 0.0))
+    c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
     return c
 
 

@@ -447,6 +447,11 @@ static void wave_maxima(orc_ctx *o, int k, const double *p) {
       if (real) {
         double s = (fabs(u) + cs) / o->c.dx;
         if (o->c.dim == 2) s += (fabs(v) + cs) / o->c.dy;
+        /* explicit viscous limit: 2 nu (1/dx^2 + 1/dy^2) added to the rate */
+        if (o->c.mu[k] > 0.0) {
+          double id2 = 1.0 / (o->c.dx * o->c.dx) + (o->c.dim == 2 ? 1.0 / (o->c.dy * o->c.dy) : 0.0);
+          s += 2.0 * o->c.mu[k] / rho * id2;
+        }
         sm = dmax(sm, s);
       }
     }
@@ -552,6 +557,9 @@ static double curvature(const orc_ctx *o, const double *p, int i, int j) {
   return (pxx * py * py - 2.0 * px * py * pxy + pyy * px * px) / (g2 * sqrt(g2));
 }
 
+static void visc_stress(double mu, double ux, double uy, double vx, double vy, double *txx,
+                        double *txy, double *tyy);
+
 /* X for every cut cell (|S| > 0): fluid N receives momentum -p_I,N S and
  * energy -p_I,N u_I |S|, fluid P momentum p_I,P S and energy p_I,P u_I |S|;
  * no mass crosses.  Without surface tension p_I,N = p_I,P; with it the
@@ -588,6 +596,29 @@ static void interface(orc_ctx *o, const double *p) {
       o->xp[0][c] = psP * Sx;
       o->xp[1][c] = psP * Sy;
       o->xp[2][c] = psP * us * Sm;
+      /* viscous traction of each fluid on its side of the interface: tau_k
+       * from its stencil state's central differences at the cut cell,
+       * applied through its outward interface vector (+S for N, -S for P) */
+      for (int k = 0; k < 2; k++) {
+        if (!(o->c.mu[k] > 0.0)) continue;
+        const double *u = o->w[k][1], *v = o->w[k][2];
+        double ux = (u[ID(o, i + 1, j)] - u[ID(o, i - 1, j)]) / (2.0 * o->c.dx);
+        double vx = (v[ID(o, i + 1, j)] - v[ID(o, i - 1, j)]) / (2.0 * o->c.dx);
+        double uy = 0.0, vy = 0.0;
+        if (o->c.dim == 2) {
+          uy = (u[ID(o, i, j + 1)] - u[ID(o, i, j - 1)]) / (2.0 * o->c.dy);
+          vy = (v[ID(o, i, j + 1)] - v[ID(o, i, j - 1)]) / (2.0 * o->c.dy);
+        }
+        double txx, txy, tyy;
+        visc_stress(o->c.mu[k], ux, uy, vx, vy, &txx, &txy, &tyy);
+        double sg = k == 0 ? 1.0 : -1.0;
+        double fx = sg * (txx * Sx + txy * Sy), fy = sg * (txy * Sx + tyy * Sy);
+        double e = u[c] * fx + v[c] * fy;
+        double *const *X = k == 0 ? o->xn : o->xp;
+        X[0][c] = X[0][c] + fx;
+        X[1][c] = X[1][c] + fy;
+        X[2][c] = X[2][c] + e;
+      }
       o->ul[0][c] = us * nxv;
       o->ul[1][c] = us * nyv;
       o->smax[0] = dmax(o->smax[0], (fabs(us) + out[4]) * fac);
@@ -770,6 +801,55 @@ static void face_flux(const orc_ctx *o, int k, int c, int s, int d, double *Fh) 
   }
 }
 
+/* Viscous stress of fluid k (Stokes' hypothesis, no heat conduction):
+ * tau_xx = mu (4/3 u_x - 2/3 v_y), tau_yy = mu (4/3 v_y - 2/3 u_x),
+ * tau_xy = mu (u_y + v_x). */
+static void visc_stress(double mu, double ux, double uy, double vx, double vy, double *txx,
+                        double *txy, double *tyy) {
+  *txx = mu * (4.0 / 3.0 * ux - 2.0 / 3.0 * vy);
+  *tyy = mu * (4.0 / 3.0 * vy - 2.0 / 3.0 * ux);
+  *txy = mu * (uy + vx);
+}
+
+/* viscous flux through the face between cells c - s and c (direction d)
+ * from the stencil states by central differences: the normal derivatives
+ * across the face, the tangential ones averaged over the two cells */
+static void viscous_face(const orc_ctx *o, int k, int c, int s, int d, double *Fv) {
+  const double *u = o->w[k][1], *v = o->w[k][2];
+  double dx = o->c.dx, dy = o->c.dy;
+  int cl = c - s;
+  double ux, uy, vx, vy;
+  if (d == 0) {
+    ux = (u[c] - u[cl]) / dx;
+    vx = (v[c] - v[cl]) / dx;
+    if (o->c.dim == 2) {
+      int t = o->PX;
+      uy = ((u[c + t] - u[c - t]) + (u[cl + t] - u[cl - t])) / (4.0 * dy);
+      vy = ((v[c + t] - v[c - t]) + (v[cl + t] - v[cl - t])) / (4.0 * dy);
+    } else {
+      uy = vy = 0.0;
+    }
+  } else {
+    uy = (u[c] - u[cl]) / dy;
+    vy = (v[c] - v[cl]) / dy;
+    ux = ((u[c + 1] - u[c - 1]) + (u[cl + 1] - u[cl - 1])) / (4.0 * dx);
+    vx = ((v[c + 1] - v[c - 1]) + (v[cl + 1] - v[cl - 1])) / (4.0 * dx);
+  }
+  double txx, txy, tyy;
+  visc_stress(o->c.mu[k], ux, uy, vx, vy, &txx, &txy, &tyy);
+  double uf = 0.5 * (u[cl] + u[c]), vf = 0.5 * (v[cl] + v[c]);
+  Fv[0] = 0.0;
+  if (d == 0) {
+    Fv[1] = txx;
+    Fv[2] = txy;
+    Fv[3] = uf * txx + vf * txy;
+  } else {
+    Fv[1] = txy;
+    Fv[2] = tyy;
+    Fv[3] = uf * txy + vf * tyy;
+  }
+}
+
 static void fv_rhs(orc_ctx *o, int k, double *const L[4]) {
   int nx = o->c.nx, ny = o->c.ny;
   fill_ghost(o, o->w[k][0], 0);
@@ -787,6 +867,11 @@ static void fv_rhs(orc_ctx *o, int k, double *const L[4]) {
       double A = k == 1 ? o->ax[c] : 1.0 - o->ax[c];
       if (A == 0.0) continue;
       face_flux(o, k, c, 1, 0, Fh);
+      if (o->c.mu[k] > 0.0) {
+        double Fv[4];
+        viscous_face(o, k, c, 1, 0, Fv);
+        for (int m = 0; m < 4; m++) Fh[m] = Fh[m] - Fv[m];
+      }
       for (int m = 0; m < 4; m++) o->fx[m][c] = A * Fh[m];
     }
   if (o->c.dim == 2)
@@ -796,6 +881,11 @@ static void fv_rhs(orc_ctx *o, int k, double *const L[4]) {
         double A = k == 1 ? o->ay[c] : 1.0 - o->ay[c];
         if (A == 0.0) continue;
         face_flux(o, k, c, o->PX, 1, Fh);
+        if (o->c.mu[k] > 0.0) {
+          double Fv[4];
+          viscous_face(o, k, c, o->PX, 1, Fv);
+          for (int m = 0; m < 4; m++) Fh[m] = Fh[m] - Fv[m];
+        }
         for (int m = 0; m < 4; m++) o->fy[m][c] = A * Fh[m];
       }
   double dxdy = o->c.dx * o->c.dy;
@@ -1216,6 +1306,8 @@ orc_ctx *orc_create(const orc_config *cfg) {
   if (cfg->rk_order != 2 && cfg->rk_order != 3) return NULL;
   if (cfg->weno_char != 0 && cfg->weno_char != 1) return NULL;
   if (!(cfg->sigma >= 0.0) || !isfinite(cfg->sigma)) return NULL;
+  for (int k = 0; k < 2; k++)
+    if (!(cfg->mu[k] >= 0.0) || !isfinite(cfg->mu[k])) return NULL;
   orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   o->c = *cfg;
   if (o->c.dim == 1) o->c.bc[2] = o->c.bc[3] = ORC_BC_ZEROGRAD;
@@ -1885,7 +1977,8 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
                      const double *phi2, const double *lam_in, double *lam_out) {
   /* the adjoint is written for the component-wise reconstruction without
    * surface tension */
-  if (o->c.rk_order != 2 || o->c.weno_char || o->c.sigma != 0.0) {
+  if (o->c.rk_order != 2 || o->c.weno_char || o->c.sigma != 0.0 || o->c.mu[0] != 0.0 ||
+      o->c.mu[1] != 0.0) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }
@@ -1990,7 +2083,7 @@ int orc_rhs_frozen(orc_ctx *o, const double *lf, double *out) {
 }
 
 int orc_rhs_adjoint(orc_ctx *o, const double *lf, const double *mu_in, double *lq_out) {
-  if (o->c.weno_char || o->c.sigma != 0.0) {
+  if (o->c.weno_char || o->c.sigma != 0.0 || o->c.mu[0] != 0.0 || o->c.mu[1] != 0.0) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }

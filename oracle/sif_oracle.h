@@ -46,6 +46,7 @@ typedef struct {
   int force_ratio_one;   /* test only: multi-dt cycle with dt1 = dt2 */
   int weno_char;         /* 1 = WENO5 on characteristic fields, 0 = component-wise */
   double sigma;          /* surface tension coefficient (Eq. 10); 0 = none */
+  double mu[2];          /* dynamic viscosities of fluids N and P (Eq. 3, 5); 0 = inviscid */
 } orc_config;
 
 typedef struct {

@@ -140,6 +140,8 @@ static int validate(const sif_config *f, char *why, size_t n) {
   if (f->rk_order != 2 && f->rk_order != 3) return snprintf(why, n, "rk_order must be 2 or 3"), SIF_EINVAL;
   if (f->weno_char != 0 && f->weno_char != 1) return snprintf(why, n, "weno_char must be 0 or 1"), SIF_EINVAL;
   if (!(f->sigma >= 0.0 && f->sigma < 1e300)) return snprintf(why, n, "sigma must be finite and >= 0"), SIF_EINVAL;
+  for (int k = 0; k < 2; k++)
+    if (!(f->mu[k] >= 0.0 && f->mu[k] < 1e300)) return snprintf(why, n, "mu must be finite and >= 0"), SIF_EINVAL;
   // the face values' reciprocal needs the product of two denominators,
   // each at least eps^4, to stay normal
   if (!(f->weno_eps >= 1e-20)) return snprintf(why, n, "weno_eps must be >= 1e-20"), SIF_EINVAL;
@@ -214,6 +216,8 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.reinit_iters = f.reinit_iters;
   g.weno_char = f.weno_char;
   g.sigma = f.sigma;
+  g.mu[0] = f.mu[0];
+  g.mu[1] = f.mu[1];
   g.tx = FV_TX;
   g.ty = FV_TY;
   g.ntx = (f.nx + g.tx - 1) / g.tx;
@@ -522,6 +526,9 @@ static void fv(sif_ctx *c, int k, int s, double *const dst[4], double *const bas
   launch_fv_stage(c->g, k, s, c->cfg.rk_order, dst, base, cur, c->w[k], c->ax, c->ay, c->sx,
                   c->sy, X[0], X[1], X[2], c->tiles[k], ntile(c), c->num_sms, dtp,
                   c->sc, c->st);
+  if (c->g.mu[k] > 0.0)
+    launch_viscous(c->g, k, s, c->cfg.rk_order, dst, c->w[k], c->ax, c->ay, c->tiles[k], ntile(c),
+                   dtp, c->sc, c->st);
   dbg(c, "fv_stage");
 }
 
@@ -1451,9 +1458,9 @@ extern "C" int sif_tape_reset(sif_ctx *c, int capacity) {
     set_err(c, "the adjoint is defined for rk_order 2");
     return SIF_EINVAL;
   }
-  if (c->cfg.weno_char || c->cfg.sigma != 0.0) {
+  if (c->cfg.weno_char || c->cfg.sigma != 0.0 || c->cfg.mu[0] != 0.0 || c->cfg.mu[1] != 0.0) {
     set_err(c, "the adjoint is defined for the component-wise reconstruction (weno_char 0) "
-               "without surface tension (sigma 0)");
+               "of the inviscid model without surface tension (sigma 0, mu 0)");
     return SIF_EINVAL;
   }
   cudaSetDevice(c->cfg.device);

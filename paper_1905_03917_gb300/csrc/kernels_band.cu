@@ -117,6 +117,11 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
         // taken once (an ulp from the quotients in the step size)
         double s = lx * idx_;
         if (g.dim == 2) s += ly * idy_;
+        // explicit viscous limit: 2 nu (1/dx^2 + 1/dy^2) added to the rate
+        if (g.mu[k] > 0.0) {
+          const double id2 = 1.0 / (g.dx * g.dx) + (g.dim == 2 ? 1.0 / (g.dy * g.dy) : 0.0);
+          s += 2.0 * g.mu[k] / rho * id2;
+        }
         sm = s;
       }
     }
@@ -287,6 +292,28 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
       xm1[c] = -ps * Sy;
       xm2[c] = -ps * us * Sm;
       sP = fmax(sP, (fabs(us) + cs) * fac);
+    }
+    // viscous traction of the lane's fluid on its side of the interface:
+    // its stencil state's stress by central differences at the cut cell,
+    // through its outward interface vector (+S for N, -S for P; fluid P's
+    // planes hold the negated flux)
+    if (g.mu[side] > 0.0) {
+      const double *u = side == 0 ? n1 : p1, *v = side == 0 ? n2 : p2;
+      const double ux = (u[gidx(g, i + 1, j)] - u[gidx(g, i - 1, j)]) / (2.0 * g.dx);
+      const double vx = (v[gidx(g, i + 1, j)] - v[gidx(g, i - 1, j)]) / (2.0 * g.dx);
+      double uy = 0.0, vy = 0.0;
+      if (g.dim == 2) {
+        uy = (u[gidx(g, i, j + 1)] - u[gidx(g, i, j - 1)]) / (2.0 * g.dy);
+        vy = (v[gidx(g, i, j + 1)] - v[gidx(g, i, j - 1)]) / (2.0 * g.dy);
+      }
+      double txx, txy, tyy;
+      visc_stress(g.mu[side], ux, uy, vx, vy, txx, txy, tyy);
+      const double fx = txx * Sx + txy * Sy, fy = txy * Sx + tyy * Sy;
+      const double e = u[c] * fx + v[c] * fy;
+      double *X0 = side == 0 ? xn0 : xm0, *X1 = side == 0 ? xn1 : xm1, *X2 = side == 0 ? xn2 : xm2;
+      X0[c] = X0[c] + fx;
+      X1[c] = X1[c] + fy;
+      X2[c] = X2[c] + e;
     }
   }
   block_max2(sN, sP, &sc->smax[0], &sc->smax[1]);

@@ -559,4 +559,97 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
 #undef FV_LAUNCH
 }
 
+// ---------------------------------------------------------------------
+// viscous fluxes (Eq. 5's face terms): the viscous face flux from the
+// stencil states by central differences (normal derivatives across the
+// face, tangential ones averaged over the two cells), times the aperture;
+// the stage result gains b dt times their divergence.  One thread per cell,
+// each face computed by both of its cells.
+
+// viscous flux of fluid k through the face between cells cl and cr of
+// direction d (0: x, cr = cl + 1; 1: y, cr = cl + PX)
+__device__ __forceinline__ void viscous_face(const Grid &g, double mu, const double *u,
+                                             const double *v, int cl, int cr, int d,
+                                             double Fv[3]) {
+  double ux, uy, vx, vy;
+  if (d == 0) {
+    ux = (u[cr] - u[cl]) / g.dx;
+    vx = (v[cr] - v[cl]) / g.dx;
+    if (g.dim == 2) {
+      const int t = g.PX;
+      uy = ((u[cr + t] - u[cr - t]) + (u[cl + t] - u[cl - t])) / (4.0 * g.dy);
+      vy = ((v[cr + t] - v[cr - t]) + (v[cl + t] - v[cl - t])) / (4.0 * g.dy);
+    } else {
+      uy = vy = 0.0;
+    }
+  } else {
+    uy = (u[cr] - u[cl]) / g.dy;
+    vy = (v[cr] - v[cl]) / g.dy;
+    ux = ((u[cr + 1] - u[cr - 1]) + (u[cl + 1] - u[cl - 1])) / (4.0 * g.dx);
+    vx = ((v[cr + 1] - v[cr - 1]) + (v[cl + 1] - v[cl - 1])) / (4.0 * g.dx);
+  }
+  double txx, txy, tyy;
+  visc_stress(mu, ux, uy, vx, vy, txx, txy, tyy);
+  const double uf = 0.5 * (u[cl] + u[cr]), vf = 0.5 * (v[cl] + v[cr]);
+  if (d == 0) {
+    Fv[0] = txx, Fv[1] = txy, Fv[2] = uf * txx + vf * txy;
+  } else {
+    Fv[0] = txy, Fv[1] = tyy, Fv[2] = uf * txy + vf * tyy;
+  }
+}
+
+__global__ void k_viscous(Grid g, int k, double bw, const double *dtp, const int *tiles,
+                          const int *ntiles, const double *__restrict__ u,
+                          const double *__restrict__ v, const double *__restrict__ ax,
+                          const double *__restrict__ ay, double *d1, double *d2, double *d3) {
+  SIF_TICK();
+  if ((int)blockIdx.x >= ntiles[k]) return;
+  const int tile = tiles[blockIdx.x];
+  const int i0 = (tile % g.ntx) * g.tx, j0 = (tile / g.ntx) * g.ty;
+  const double mu = g.mu[k], dt = *dtp;
+  for (int r = threadIdx.x; r < g.tx * g.ty; r += blockDim.x) {
+    const int i = i0 + r % g.tx, j = j0 + r / g.tx;
+    if (i >= g.nx || j >= g.ny) continue;
+    const int c = gidx(g, i, j);
+    double L[3] = {0.0, 0.0, 0.0};
+    // x faces: left (i) and right (i + 1)
+    for (int side = 0; side < 2; side++) {
+      const int cf = c + side;  // the face's right cell
+      double A_ = ax[cf];
+      if (k == 0) A_ = 1.0 - A_;
+      if (A_ == 0.0) continue;
+      double Fv[3];
+      viscous_face(g, mu, u, v, cf - 1, cf, 0, Fv);
+      const double w_ = (side ? A_ : -A_) / g.dx;
+      for (int m = 0; m < 3; m++) L[m] += w_ * Fv[m];
+    }
+    if (g.dim == 2)
+      for (int side = 0; side < 2; side++) {
+        const int cf = c + side * g.PX;
+        double A_ = ay[cf];
+        if (k == 0) A_ = 1.0 - A_;
+        if (A_ == 0.0) continue;
+        double Fv[3];
+        viscous_face(g, mu, u, v, cf - g.PX, cf, 1, Fv);
+        const double w_ = (side ? A_ : -A_) / g.dy;
+        for (int m = 0; m < 3; m++) L[m] += w_ * Fv[m];
+      }
+    const double f = bw * dt;
+    d1[c] += f * L[0];
+    d2[c] += f * L[1];
+    d3[c] += f * L[2];
+  }
+}
+
+void launch_viscous(const Grid &g, int k, int s, int rk, double *const dst[4],
+                    double *const w[4], const double *ax, const double *ay, const int *tiles,
+                    int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st) {
+  static const double B2[3] = {0.0, 1.0, 0.5}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
+  const double bw = rk == 3 ? B3[s] : B2[s];
+  k_viscous<<<tile_cap > 0 ? tile_cap : 1, 128, 0, st>>>(g, k, bw, dtp, tiles, sc->n_tiles,
+                                                        w[1], w[2], ax, ay, dst[1], dst[2],
+                                                        dst[3]);
+  sif_note_launches(1);
+}
+
 SIF_TU_LAUNCH_READER(fv)

@@ -35,6 +35,7 @@ struct Grid {
   int ext_iters, reinit_iters;
   int weno_char;  // finite-volume reconstruction on characteristic fields
   double sigma;   // surface tension coefficient (Eq. 10), 0 = none
+  double mu[2];   // dynamic viscosities of fluids N and P, 0 = inviscid
   int tx, ty;    // finite-volume tile shape (output cells per CTA)
   int ntx, nty;  // tiles per direction
 };
@@ -403,6 +404,18 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
                   const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
                   int band_fluid, const int *band_flag, const int *band, const int *nband,
                   cudaStream_t st);
+// viscous part of a finite-volume stage of fluid k (mu[k] > 0): dst +=
+// b dt div(A Fv) over the cells of fluid k's active tiles
+void launch_viscous(const Grid &g, int k, int s, int rk, double *const dst[4],
+                    double *const w[4], const double *ax, const double *ay, const int *tiles,
+                    int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st);
+// viscous stress with Stokes' hypothesis
+__device__ inline void visc_stress(double mu, double ux, double uy, double vx, double vy,
+                                   double &txx, double &txy, double &tyy) {
+  txx = mu * (4.0 / 3.0 * ux - 2.0 / 3.0 * vy);
+  tyy = mu * (4.0 / 3.0 * vy - 2.0 / 3.0 * ux);
+  txy = mu * (uy + vx);
+}
 void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], const double *phi,
                       const double *sx, const double *sy, const int *cut, int cut_cap,
                       double *const xn[3], double *const xm[3], double *ul0, double *ul1,

@@ -298,3 +298,38 @@ def static_drop(n=64, sigma=36.0, equilibrium=False, liquid=True):
                   p0 + (sigma / 0.1 if equilibrium else 0.0))
     pP = _uniform(X.shape, 1.0, 0.0, 0.0, p0)
     return {"name": f"static_drop_{'liquid' if liquid else 'gas'}_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def shear_wave(n=32, m=8, mu=0.01, amp=0.01, p=100.0, across="y"):
+    """Decaying shear wave in one viscous gas (fluid P everywhere) at
+    uniform density 1 and pressure p on a periodic box of n cells across
+    the wave (length 1) and m along it: u = amp sin(2 pi y), v = 0
+    (across="y") or v = amp sin(2 pi x), u = 0 (across="x").  The velocity
+    varies across the wave only, so u_t = nu u_yy (or v_t = nu v_xx) holds
+    exactly and the amplitude decays as exp(-nu (2 pi)^2 t), nu = mu."""
+    d = 1.0 / n
+    nx, ny = (m, n) if across == "y" else (n, m)
+    cfg = config(nx, ny, d, d, AIR, AIR, ["periodic"] * 4, mu=(mu, mu))
+    X, Y = _centres(cfg)
+    phi = np.ones_like(X)
+    pP = _uniform(X.shape, 1.0, 0.0, 0.0, p)
+    if across == "y":
+        pP[1] = amp * np.sin(2 * np.pi * Y)
+    else:
+        pP[2] = amp * np.sin(2 * np.pi * X)
+    return {"name": f"shear_wave_{across}_{n}", "cfg": cfg, "phi": phi, "prim_N": pP.copy(),
+            "prim_P": pP}
+
+
+def sound_wave(n=32, mu=0.01, amp=1e-3, p=100.0):
+    """Standing sound wave u = amp c sin(2 pi x) in one viscous gas (1D,
+    periodic, density 1, pressure p): with Stokes' hypothesis and no heat
+    conduction its amplitude decays as exp(-(2/3) nu k^2 t), k = 2 pi."""
+    d = 1.0 / n
+    cfg = config(n, 1, d, d, AIR, AIR, ["periodic"] * 4, dim=1, mu=(mu, mu))
+    X, _ = _centres(cfg)
+    phi = np.ones_like(X)
+    c = math.sqrt(1.4 * p)
+    pP = _uniform(X.shape, 1.0, 0.0, 0.0, p)
+    pP[1] = amp * c * np.sin(2 * np.pi * X)
+    return {"name": f"sound_wave_{n}", "cfg": cfg, "phi": phi, "prim_N": pP.copy(), "prim_P": pP}

@@ -50,7 +50,8 @@ class Config(ctypes.Structure):
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double)]
+                ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("mu", ctypes.c_double * 2)]
 
 
 class Profile(ctypes.Structure):
@@ -150,6 +151,8 @@ def make_config(cfg: dict, stream=None, device=0) -> Config:
     c.device = int(device)
     c.weno_char = int(cfg.get("weno_char", 0))
     c.sigma = float(cfg.get("sigma", 0.0))
+    mu = cfg.get("mu", (0.0, 0.0))
+    c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
     return c
 
 

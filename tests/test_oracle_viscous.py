@@ -1,0 +1,80 @@
+"""Pins of the oracle's viscous fluxes (Eq. 3 and 5: central-difference
+viscous face fluxes times the apertures, each fluid's viscous traction on
+its interface boundary; not part of the compressible method's hot path,
+the survey's NEXT-2 item) against closed forms of the compressible
+Navier-Stokes equations with Stokes' hypothesis and no heat conduction:
+a shear wave decays as exp(-nu k^2 t) (in either orientation: the
+x-face and y-face stresses), a standing sound wave as exp(-(2/3) nu k^2 t)
+(the normal stresses with their 4/3 and 2/3), and the explicit viscous
+time-step limit keeps a strongly viscous wave stable."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_03917_gb300 import inputs
+
+K2 = (2 * math.pi) ** 2
+
+
+def _shear(n, across="y", mu=0.01, T=0.5, amp=0.01):
+    c = inputs.shear_wave(n, mu=mu, amp=amp, across=across)
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    I0 = o.integrals()
+    while o.t < T * (1 - 1e-14):
+        o.step_single_dt(1, T)
+    assert o.status == 0
+    _, qP, _ = o.state()
+    x = (np.arange(n) + 0.5) / n
+    if across == "y":
+        a = 2.0 * ((qP[1] / qP[0]) * np.sin(2 * np.pi * x)[:, None]).mean()
+    else:
+        a = 2.0 * ((qP[2] / qP[0]) * np.sin(2 * np.pi * x)[None, :]).mean()
+    return a / (amp * math.exp(-mu * K2 * T)) - 1.0, I0, o.integrals()
+
+
+@pytest.mark.parametrize("across", ["y", "x"])
+def test_shear_wave_decays_at_the_viscous_rate(across):
+    e32, I0, I1 = _shear(32, across)
+    e64, _, _ = _shear(64, across)
+    assert abs(e32) < 1e-3 and abs(e64) < abs(e32) / 3.0, (e32, e64)
+    # viscous fluxes are conservative: energy (heat gained = kinetic energy
+    # lost) and the zero-mean momentum stay
+    assert abs(I1[1, 3] / I0[1, 3] - 1.0) <= 1e-13
+    assert abs(I1[1, 1]) + abs(I1[1, 2]) <= 1e-15 * I0[1, 0]
+
+
+def test_without_viscosity_the_shear_wave_does_not_decay():
+    e, _, _ = _shear(32, mu=0.0)
+    assert abs(e) < 0.01
+
+
+def test_explicit_viscous_limit_keeps_a_strongly_viscous_wave_stable():
+    # nu = 1 on 32 cells: the acoustic step alone (nu dt / dx^2 = 0.8) would
+    # exceed the explicit diffusion limit and the wave would blow up
+    e, _, _ = _shear(32, mu=1.0, T=0.02)
+    assert abs(e) < 0.02, e
+
+
+def _sound_amplitude(n, mu, periods=4):
+    c = inputs.sound_wave(n, mu=mu)
+    o = O.Oracle(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    T = periods / math.sqrt(1.4 * 100.0)  # whole periods: u returns to its shape
+    while o.t < T * (1 - 1e-14):
+        o.step_single_dt(1, T)
+    assert o.status == 0
+    _, qP, _ = o.state()
+    x = (np.arange(n) + 0.5) / n
+    return 2.0 * ((qP[1][0] / qP[0][0]) * np.sin(2 * np.pi * x)).mean(), T
+
+
+def test_sound_wave_is_damped_by_the_normal_stresses():
+    # the viscous run against the inviscid one isolates the viscous damping
+    mu = 0.02
+    for n in (64,):
+        a_v, T = _sound_amplitude(n, mu)
+        a_0, _ = _sound_amplitude(n, 0.0)
+        ratio = a_v / a_0
+        exact = math.exp(-(2.0 / 3.0) * mu * K2 * T)
+        assert abs(ratio / exact - 1.0) < 2e-3, (ratio, exact)
