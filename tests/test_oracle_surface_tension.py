@@ -1,6 +1,7 @@
-"""Pins of the oracle's surface tension (Eq. 10, Sec. 4.3; not part of the
-compressible method's hot path, the survey's NEXT-2 item): the interface
-Riemann problem with a pressure jump against an independent solver and
+"""Pins of the oracle's surface tension (Eq. 10, Sec. 4.3; part of the
+weakly compressible model of Sec. 2.2, built here on the stiffened-gas
+equations): the interface Riemann problem with a pressure jump against an
+independent solver and
 the static equilibrium it must keep, the level-set curvature against the
 exact curvature of circles and lines, and the Laplace law of a static
 drop, whose pressure jump must be sigma / R."""

@@ -1,8 +1,9 @@
 """Pins of the oracle's viscous fluxes (Eq. 3 and 5: central-difference
 viscous face fluxes times the apertures, each fluid's viscous traction on
-its interface boundary; not part of the compressible method's hot path,
-the survey's NEXT-2 item) against closed forms of the compressible
-Navier-Stokes equations with Stokes' hypothesis and no heat conduction:
+its interface boundary; part of the weakly compressible model of Sec. 2.2,
+built here on the stiffened-gas equations) against closed forms of the
+compressible Navier-Stokes equations with Stokes' hypothesis and no heat
+conduction:
 a shear wave decays as exp(-nu k^2 t) (in either orientation: the
 x-face and y-face stresses), a standing sound wave as exp(-(2/3) nu k^2 t)
 (the normal stresses with their 4/3 and 2/3), and the explicit viscous
