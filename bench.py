@@ -201,9 +201,9 @@ BYTES_PER_UPDATE = 8 * (4 + 2 + 2 + 3 + 4 + 2 + 4)
 # dram__bytes_write.sum of an air launch of the 512 x 128 shock-bubble,
 # 65 536 updates) per finite-volume tile shape; scaled by the updates of a
 # launch for the roofline's traffic (null for a shape not captured)
-MEASURED_DRAM_BYTES_PER_UPDATE = {(32, 8): 6723840 / 65536, (16, 16): 6692096 / 65536,
-                                  (16, 8): 6680064 / 65536, (32, 4): 6727424 / 65536,
-                                  (64, 4): 6726656 / 65536}
+MEASURED_DRAM_BYTES_PER_UPDATE = {(32, 8): 6732544 / 65536, (16, 16): 6677760 / 65536,
+                                  (16, 8): 6679808 / 65536, (32, 4): 6727936 / 65536,
+                                  (64, 4): 6728192 / 65536}
 FALLBACK_HBM_GBS = 6800.0
 
 
