@@ -105,3 +105,23 @@ def test_batch_of_256_instances(tmp_path):
         o.step_multi_dt(ncyc)
         assert o.status == 0
         compare(b.instances[i], o, 1e-12)
+
+
+def test_shock_bubble_1024x256_characteristic(tmp_path):
+    """The characteristic-wise option at the same size and in the same launch
+    configuration (`bench.py --weno characteristic`): graph launches, tile
+    shape from the autotuner, three cycles against the oracle."""
+    sif = _sif()
+    from paper_1905_03917_gb300 import autotune
+    case = inputs.shock_bubble(1024, 256)
+    case["cfg"] = dict(case["cfg"], weno_char=1)
+    s = sif.Solver(case["cfg"]).init_fluids(*_arrays(case))
+    shape, _ = autotune.tune(s, cache=str(tmp_path / "tune.json"), cycles=2)
+    infos = [s.step_multi_dt(1) for _ in range(3)]
+    o = _oracle(case)
+    oinfos = [o.step_multi_dt(1) for _ in range(3)]
+    for a, b in zip(infos, oinfos):
+        assert a["substeps"] == b["substeps"] and a["n_used"] == b["n_used"]
+        assert abs(a["t"] - b["t"]) <= 1e-13 * b["t"]
+    assert o.status == 0
+    print("tile", shape, "relative L1 after 3 cycles:", compare(s, o, 1e-12))
