@@ -20,6 +20,8 @@ struct sif_ctx {
   Grid g;
   cudaStream_t st;
   size_t NP;
+  // xn: exchange flux as applied to fluid N; xm: as applied to fluid P,
+  // negated (equal to xn without surface tension and viscosity)
   double *q[2][4], *w[2][4], *phi, *alpha, *ax, *ay, *sx, *sy, *xn[3], *xm[3], *ul[2];
   double *q0[2][4], *prev[4], *fut[4], *qi[4], *xc[3], *phi0, *phiR;
   double *tmp;       // band-indexed scratch, 8 planes
