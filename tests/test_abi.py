@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_1905_03917_gb300 import build, sif
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -61,6 +63,20 @@ def test_weno_epsilon_below_the_reciprocal_range_is_rejected():
     from paper_1905_03917_gb300 import inputs
     lib = sif.load()
     cfg = dict(inputs.shock_tube_1d(64)["cfg"], weno_eps=1e-30)
+    c = sif.make_config(cfg)
+    h = ctypes.c_void_p()
+    assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("sigma", -1.0), ("sigma", float("nan")),
+                                         ("mu", (-1e-3, 0.0)), ("mu", (0.0, float("inf"))),
+                                         ("weno_char", 2)])
+def test_invalid_physics_options_are_rejected_without_gpu_work(field, value):
+    from paper_1905_03917_gb300 import inputs
+    lib = sif.load()
+    cfg = dict(inputs.shock_tube_1d(64)["cfg"])
+    cfg[field] = value
     c = sif.make_config(cfg)
     h = ctypes.c_void_p()
     assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
