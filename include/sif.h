@@ -305,12 +305,17 @@ int sif_probe_reciprocal(const double *d, double *r, long long n, void *stream);
  * Scratch: a 1 MiB file-scope device array holds the row partial sums, so
  * ny may not exceed 16384 (SIF_EINVAL beyond that, or for nx, ny < 1).
  * Every GPU that loads the library keeps that array until the process
- * exits.  The first call on a device looks up the array's device address
- * with that device current; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (on
- * different streams or devices' peers) race on it and must be ordered by
- * the caller.  Each call overwrites every partial sum it reads, so nothing
- * needs clearing between calls.  Calls no cudaMalloc/cudaFree. */
+ * exits.  The call works on the current device: q_N, q_P and out must
+ * live there.  The first call on a device looks up the array's device
+ * address with that device current and caches it; make that first call
+ * before any stream capture.  The cached address is not valid after a
+ * cudaDeviceReset (which unloads the module); first calls on one device
+ * from several host threads at once are safe (they store the same
+ * address).  Each GPU has its own copy of the array: calls that overlap
+ * on the same GPU (on any streams) race on it and must be ordered by the
+ * caller; calls on different GPUs share nothing.  Each call overwrites
+ * every partial sum it reads, so nothing needs clearing between calls.
+ * Calls no cudaMalloc/cudaFree. */
 int sif_integrals_noalloc(const double *q_N, const double *q_P, int nx, int ny, double dx,
                           double dy, double *out, void *stream);
 

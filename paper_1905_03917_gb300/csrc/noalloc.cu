@@ -8,6 +8,8 @@
 // monitoring hook inside a time-stepping loop where an allocation would
 // synchronise the device.  For them sif_integrals_noalloc works on planes
 // they already own and writes into an output they already own.
+#include <atomic>
+
 #include "sif_internal.cuh"
 
 // Scratch for the per-row partial sums of the 8 planes (8 * max rows
@@ -42,9 +44,11 @@ __global__ void k_noalloc_final(const double *rows, int ny, double dxdy, double 
   out[pl] = s * dxdy;
 }
 
-// device address of the scratch array, looked up once per device
-static void *g_scratch_addr[64];
-static int g_scratch_ready[64];
+// device address of the scratch array, looked up once per device (it is
+// no longer valid after a cudaDeviceReset, which unloads the module).
+// Concurrent first calls on one device store the same value; the atomics
+// keep those stores well defined.
+static std::atomic<void *> g_scratch_addr[64];
 
 extern "C" int sif_integrals_noalloc(const double *q_N, const double *q_P, int nx, int ny,
                                      double dx, double dy, double *out, void *stream) {
@@ -52,18 +56,17 @@ extern "C" int sif_integrals_noalloc(const double *q_N, const double *q_P, int n
   if (ny > NOALLOC_MAX_ROWS) return SIF_EINVAL;  // scratch holds NOALLOC_MAX_ROWS rows
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SIF_ECUDA;
-  if (!g_scratch_ready[dev]) {
+  void *ptr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
     // set-up on the current device: the host-side name of the array is not
     // a device address, so ask the runtime for the address once
-    void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_rows) != cudaSuccess || !ptr) {
       cudaGetLastError();
       return SIF_ECUDA;
     }
-    g_scratch_addr[dev] = ptr;
-    g_scratch_ready[dev] = 1;
+    g_scratch_addr[dev].store(ptr, std::memory_order_release);
   }
-  double *rows = (double *)g_scratch_addr[dev];
+  double *rows = (double *)ptr;
   cudaStream_t st = (cudaStream_t)stream;
   NoallocPlanes planes;
   for (int m = 0; m < 4; m++) {

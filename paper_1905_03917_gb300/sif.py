@@ -197,14 +197,29 @@ def probe_reciprocal(d):
 
 
 def integrals_noalloc(q_N, q_P, dx, dy, out, stream=None):
-    """Totals of device planes (torch CUDA tensors of shape (4, ny, nx))
-    into the device tensor `out` (8 doubles) without any device
-    allocation; see sif_integrals_noalloc in include/sif.h."""
+    """Totals of device planes (contiguous float64 CUDA tensors of shape
+    (4, ny, nx)) into the device tensor `out` (at least 8 doubles) without
+    any device allocation; see sif_integrals_noalloc in include/sif.h.
+    All three tensors must be on one GPU; the call runs with that GPU
+    current, on `stream` (a cudaStream_t handle) or, by default, on torch's
+    current stream of that GPU, so that it is ordered after the work that
+    filled the planes."""
+    import torch
     (a, ka), (b, kb), (o, ko) = _ptr(q_N), _ptr(q_P), _ptr(out)
     if not (ka == kb == ko == DEVICE):
         raise ValueError("integrals_noalloc takes device tensors")
+    if q_N.dim() != 3 or q_N.shape[0] != 4:
+        raise ValueError(f"q_N must have shape (4, ny, nx), got {tuple(q_N.shape)}")
+    if tuple(q_P.shape) != tuple(q_N.shape):
+        raise ValueError(f"q_P has shape {tuple(q_P.shape)}, q_N {tuple(q_N.shape)}")
+    if out.numel() < 8:
+        raise ValueError("out must hold at least 8 doubles")
+    if not (q_N.device == q_P.device == out.device):
+        raise ValueError("q_N, q_P and out must be on the same GPU")
     ny, nx = q_N.shape[-2], q_N.shape[-1]
-    rc = load().sif_integrals_noalloc(a, b, int(nx), int(ny), float(dx), float(dy), o, stream)
+    with torch.cuda.device(q_N.device):
+        st = stream if stream is not None else torch.cuda.current_stream(q_N.device).cuda_stream
+        rc = load().sif_integrals_noalloc(a, b, int(nx), int(ny), float(dx), float(dy), o, st)
     if rc != OK:
         raise SifError(rc, "sif_integrals_noalloc rejected the call")
 

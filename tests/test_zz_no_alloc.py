@@ -32,7 +32,9 @@ def test_noalloc_totals_match_context_totals_twice():
         sif.integrals_noalloc(qN, qP, cfg["dx"], cfg["dy"], out)
         got = out.cpu().numpy().reshape(2, 4)
         assert np.all(np.isfinite(got))
-        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+        # both reductions take one warp per row, the same lane striding and
+        # shuffle tree, the same row order and no FMA contraction: equal bits
+        assert np.array_equal(got, ref), np.abs(got - ref).max()
 
 
 def test_noalloc_rejects_rows_beyond_scratch():
@@ -45,3 +47,20 @@ def test_noalloc_rejects_rows_beyond_scratch():
     with pytest.raises(sif.SifError) as e:
         sif.integrals_noalloc(q, q, 1.0, 1.0, out)
     assert e.value.code == sif.EINVAL
+
+
+def test_noalloc_rejects_malformed_tensors():
+    """Shapes that would make the kernels read or write past a buffer are
+    refused in the binding before any launch."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_03917_gb300 import sif
+    q = torch.zeros((4, 8, 8), dtype=torch.float64, device="cuda")
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        sif.integrals_noalloc(q[0], q[0], 1.0, 1.0, out)      # (ny, nx), not (4, ny, nx)
+    with pytest.raises(ValueError):
+        sif.integrals_noalloc(q, q[:, :4].contiguous(), 1.0, 1.0, out)  # q_P of another shape
+    with pytest.raises(ValueError):
+        sif.integrals_noalloc(q, q, 1.0, 1.0, out[:4])       # out too short
