@@ -5,7 +5,8 @@ the original single-time-step method with --mode single -- over the whole
 two-fluid problem: interaction step, cut-cell finite-volume stages of both
 fluids, level-set advection and reinitialisation, mixing, flux
 correction.  The headline metric is fluid cell-updates per second: (cell,
-fluid) pairs updated by a finite-volume RK stage, per second.
+fluid) pairs with a face open to the fluid, updated by a finite-volume RK
+step (each fluid's stages averaged over its step), per second.
 
 Default workload: the air-helium shock-bubble interaction on a 1024 x 256
 grid (Mach 1.22 shock, helium bubble R = 0.2), synthetic initial data.
@@ -44,6 +45,9 @@ FLOPS_PER_FACE_CHAR = 22 + 28 + 2 * 5 * 4 * 7 + 4 * 142 + 4 * 7 + 4
 FLOPS_PER_UPDATE_CHAR = {2: 2 * 35 + 2 * FLOPS_PER_FACE_CHAR + 4 * 10,
                          1: 35 + FLOPS_PER_FACE_CHAR + 4 * 7}
 METRIC = "fluid cell-updates/s (FP64), % HBM peak; multi-dt vs single-dt speedup at equal err"
+# value's unit: (cell, fluid) pairs with a face open to the fluid, per RK
+# step of that fluid (a step of S stages counts each such cell once)
+UNIT = "fluid cell-updates/s"
 # nominal FP64 rate of a GB300: 152 SMs x 4 flops/clock (2 FMA) x 2.07 GHz
 NOMINAL_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
@@ -133,15 +137,16 @@ def over_ranks(dist, total_ms, updates):
 
 
 def cpu_baseline(case, mode, budget_s=20.0, max_steps=200):
-    """The oracle as it stands, serial, on the first steps of the workload."""
+    """The oracle as it stands, serial, on the first steps of the workload:
+    (steps, seconds, fluid cell-updates the oracle counted itself)."""
     from oracle import oracle as O
     o = O.Oracle(case["cfg"]).init(case["phi"], case["prim_N"], case["prim_P"])
     t0 = time.perf_counter()
-    n = 0
+    n, work = 0, 0.0
     while n < max_steps and time.perf_counter() - t0 < budget_s:
-        (o.step_multi_dt if mode == "multi" else o.step_single_dt)(1)
+        work += (o.step_multi_dt if mode == "multi" else o.step_single_dt)(1)["fluid_cell_updates"]
         n += 1
-    return n, time.perf_counter() - t0
+    return n, time.perf_counter() - t0, work
 
 
 def run_reference(args):
@@ -158,38 +163,22 @@ def run_reference(args):
     for _ in range(args.warmup):
         step(1)
     t0 = time.perf_counter()
+    work = 0.0
     for _ in range(args.steps):
-        step(1)
+        work += step(1)["fluid_cell_updates"]   # counted by the oracle itself
     dt = time.perf_counter() - t0
-    # count the same (cell, fluid) updates the GPU path counts for these steps
-    updates = gpu_updates_for(case, args.mode, args.warmup, args.steps)
-    value = updates / dt if updates else None
+    value = work / dt
     line = {"impl": "reference", "metric": METRIC, "value": value,
-            "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": case["name"], "mode": args.mode, "nx": case["cfg"]["nx"],
                        "ny": case["cfg"]["ny"], "reconstruction": weno},
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed steps after {args.warmup} of {case['name']}"},
-            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def gpu_updates_for(case, mode, skip, count):
-    try:
-        import torch
-        if not torch.cuda.is_available():
-            return None
-        from paper_1905_03917_gb300 import sif
-        s = sif.Solver(case["cfg"]).init_fluids(*(np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")))
-        step = s.step_multi_dt if mode == "multi" else s.step_single_dt
-        if skip:
-            step(skip)
-        return step(count)["cell_updates"]
-    except Exception:
-        return None
 
 
 # Algorithmic DRAM bytes of one (cell, fluid) finite-volume RK stage: the
@@ -247,146 +236,193 @@ def _eq13(n, substeps, m):
     return n / (substeps - (substeps - 1.0) * m)
 
 
-def multi_vs_single(case, fine_case, device, steps_single=600, cfls=(0.6, 0.5, 0.4, 0.3)):
-    """Speedup of the multi-time-step method at equal error (Sec. 4.2).
+def _time_at_error(curve, e):
+    """Time of a method at error e, interpolated log-log between the two
+    neighbouring points of its CFL sweep that bracket e (curve: list of
+    {"err", "ms"} in sweep order); None when no pair brackets e."""
+    for a, b in zip(curve, curve[1:]):
+        ea, eb = a["err"], b["err"]
+        if ea == e:
+            return a["ms"]
+        if (ea - e) * (eb - e) < 0:
+            w = (np.log(e) - np.log(ea)) / (np.log(eb) - np.log(ea))
+            return float(np.exp(np.log(a["ms"]) + w * (np.log(b["ms"]) - np.log(a["ms"]))))
+    if curve and curve[-1]["err"] == e:
+        return curve[-1]["ms"]
+    return None
 
-    T is the time steps_single single-dt steps at CFL 0.6 reach (through
-    the shock-bubble interaction).  The reference is the single-dt method
-    on the twice finer grid, run to T on the GPU and averaged 2 x 2.  The
-    error of a run is the relative L1 of the mixture density (and, for
-    information, of the fluid-P indicator phi > 0) against it.  Multi-dt
-    runs sweep the CFL number; the multi-dt time at the error of single-dt
-    at CFL 0.6 is interpolated log-log between the two CFL numbers that
-    bracket it (multi-dt at CFL 0.6 itself when its error is already no
-    larger).  Also reported: the equivalent-grid rate (nx ny x single-dt
-    steps to T per second of each method) and the speedup Eq. 13 predicts
-    from the measured n, [n] and m."""
+
+def equal_error_speedup(single, multi):
+    """Speedup of the multi- over the single-time-step method at equal
+    error from both methods' CFL sweeps (lists of {"cfl", "err", "ms"}, CFL
+    decreasing).  The headline level is the smaller of the two CFL-0.6
+    errors -- the loosest error both sweeps reach -- where one method sits
+    on its CFL-0.6 point and the other is interpolated on its own curve;
+    the curve gives the speedup at every single-step sweep point whose
+    error the multi-step sweep brackets.  Nothing is extrapolated."""
+    curve = []
+    for pt in single:
+        tm = _time_at_error(multi, pt["err"])
+        curve.append({"single_cfl": pt["cfl"], "err": pt["err"],
+                      "speedup": pt["ms"] / tm if tm else None})
+    if not single or not multi:
+        return None, None, curve
+    e_star = min(single[0]["err"], multi[0]["err"])
+    ts, tm = _time_at_error(single, e_star), _time_at_error(multi, e_star)
+    return (ts / tm if ts and tm else None), e_star, curve
+
+
+def _rel_l1(f, ref):
+    return float(np.abs(f - ref).sum() / np.abs(ref).sum())
+
+
+def _sweep_point(cfg, arrs, device, mode, T, error_of, profiled=False):
+    """One run of a method from the initial data to time T: untimed warm-up
+    steps (graph capture), then a timed run to T on a fresh start; the
+    error of the final state.  profiled: also a step-by-step pass with the
+    library's counters (schedule trace and finite-volume time)."""
     import torch
     from paper_1905_03917_gb300 import sif
-    cfl0 = case["cfg"].get("cfl", 0.6)
-    arrs = _prim_arrays(case)
-    probe = sif.Solver(case["cfg"], device=device).init_fluids(*arrs)
-    probe.step_single_dt(steps_single)
-    T = probe.t
-    probe.close()
-
-    def fields(s):
-        qN, qP, phi = s.state()
-        return qN[0] + qP[0], (phi > 0).astype(np.float64)
-
-    def timed(s, step):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        info = step(10 ** 6, t_end=T)
-        torch.cuda.synchronize()
-        return 1e3 * (time.perf_counter() - t0), info
-
-    def err(f, ref):
-        return float(np.abs(f - ref).sum() / np.abs(ref).sum()) if ref is not None else None
-
-    # reference: single-dt on the finer grid (GPU; parity-tested against the oracle)
-    if fine_case is not None:
-        fine = sif.Solver(fine_case["cfg"], device=device).init_fluids(*_prim_arrays(fine_case))
-        fine.step_single_dt(10 ** 7, t_end=T)
-        assert abs(fine.t - T) <= 1e-12 * T
-        ref_rho, ref_ind = (_coarsen(f) for f in fields(fine))
-        fine.close()
-    else:
-        ref_rho = ref_ind = None
-        cfls = (cfl0,)
-
-    # single-dt at CFL 0.6, first a profiled pass that also builds the graphs
-    s = sif.Solver(case["cfg"], device=device).init_fluids(*arrs)
-    s.profile(True)
-    n_single = 0
-    while s.t < T:
-        s.step_single_dt(1, t_end=T)
-        n_single += 1
-    ps = s.profile_read()
-    s.profile(False)
-    s.init_fluids(*arrs)
-    single_ms, _ = timed(s, s.step_single_dt)
-    rho, ind = fields(s)
-    single = {"ms": single_ms, "steps": n_single, "err_rho": err(rho, ref_rho),
-              "err_indicator": err(ind, ref_ind)}
-    s.close()
-
-    sweep = []
-    for cfl in cfls:
-        cfg = dict(case["cfg"], cfl=cfl)
-        m = sif.Solver(cfg, device=device).init_fluids(*arrs)
-        rec = {"cfl": cfl}
-        if cfl == cfl0:
-            # profiled pass cycle by cycle: the n(t) trace and the updates
-            m.profile(True)
-            trace = []
-            while m.t < T:
-                info = m.step_multi_dt(1, t_end=T)
-                trace.append((info["t"], info["n_raw"], info["substeps"]))
-            pm = m.profile_read()
-            m.profile(False)
-            rec["cycles"] = len(trace)
+    s = sif.Solver(cfg, device=device).init_fluids(*arrs)
+    step = s.step_multi_dt if mode == "multi" else s.step_single_dt
+    rec = {"cfl": cfg.get("cfl", 0.6)}
+    if profiled:
+        s.profile(True)
+        trace = []
+        while s.t < T:
+            info = step(1, t_end=T)
+            trace.append((info["t"], info["n_raw"], info["substeps"]))
+        prof = s.profile_read()
+        s.profile(False)
+        rec["steps"] = len(trace)
+        rec["profile"] = prof
+        if mode == "multi":
             rec["mean_substeps"] = float(np.mean([x[2] for x in trace]))
             rec["mean_n"] = float(np.mean([x[1] for x in trace]))
             stride = max(1, len(trace) // 12)
-            rec["n_trace"] = [[round(x[0], 5), round(x[1], 3), x[2]] for x in trace[::stride]]
-        else:
-            m.step_multi_dt(10 ** 6, t_end=T)   # graphs built for this CFL
-        m.init_fluids(*arrs)
-        rec["ms"], _ = timed(m, m.step_multi_dt)
-        rho, ind = fields(m)
-        rec["err_rho"], rec["err_indicator"] = err(rho, ref_rho), err(ind, ref_ind)
-        m.close()
-        sweep.append(rec)
-
-    # multi-dt time at the error of single-dt at CFL 0.6
-    e_s = single["err_rho"]
-    t_eq = None
-    if e_s is None:
-        pass
-    elif sweep[0]["err_rho"] <= e_s:
-        t_eq = sweep[0]["ms"]
+            rec["n_trace"] = [[round(x[0], 6), round(x[1], 3), x[2]] for x in trace[::stride]]
     else:
-        for a, b in zip(sweep, sweep[1:]):
-            if (a["err_rho"] - e_s) * (b["err_rho"] - e_s) <= 0 and a["err_rho"] != b["err_rho"]:
-                w = (np.log(e_s) - np.log(a["err_rho"])) / (np.log(b["err_rho"]) - np.log(a["err_rho"]))
-                t_eq = float(np.exp(np.log(a["ms"]) + w * (np.log(b["ms"]) - np.log(a["ms"]))))
-                break
+        step(3, t_end=T)
+    s.init_fluids(*arrs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = step(10 ** 7, t_end=T)
+    torch.cuda.synchronize()
+    rec["ms"] = 1e3 * (time.perf_counter() - t0)
+    rec["fluid_cell_updates"] = info["fluid_cell_updates"]
+    assert abs(s.t - T) <= 1e-12 * T, (s.t, T)
+    rec.update(error_of(s))
+    s.close()
+    return rec
 
-    # Eq. 13 from measured quantities: over the run, single-dt does
-    # 2 (u1 + u2) updates a step and a multi-dt cycle 2 (u1 + [n] u2), which
-    # gives fluid 1's share of the updates; m is that share of the finite-
-    # volume time of the single-dt run over its whole time
-    m0 = sweep[0]
+
+def multi_vs_single(case, device, steps_single=600, cfls=(0.6, 0.5, 0.4, 0.3, 0.2),
+                    ref_cfl=0.05, exact=None, T=None):
+    """Speedup of the multi-time-step method at equal error (Sec. 3.1,
+    Eq. 13; the paper's Table 1 compares the two methods' times).
+
+    T is the time steps_single single-time-step steps at CFL 0.6 reach
+    (unless given).
+    Both methods trade time-integration error for speed, so their error is
+    measured against the same method's limit on the same grid: the
+    single-time-step method at a small CFL number (ref_cfl) run to T (both
+    methods converge to the same semi-discrete solution as the step
+    shrinks).  The error of a run is the relative L1 of the mixture density
+    Sum_k (alpha rho)_k (the fluid-P indicator phi >= 0 beside it).  Both
+    methods sweep the CFL number; equal_error_speedup interpolates the time
+    each needs for a common error on its own curve.  exact (optional): a
+    function of a solver returning the error against an exact solution,
+    reported beside (the spatial error dominates it).  Also: the same-CFL
+    speedup, the equivalent-grid rate (nx ny x single steps to T per
+    second of each method) and Eq. 13's prediction from the measured n,
+    [n] and m."""
+    from paper_1905_03917_gb300 import sif
+    cfg0 = dict(case["cfg"], cfl=0.6)
+    arrs = _prim_arrays(case)
+    if T is None:
+        probe = sif.Solver(cfg0, device=device).init_fluids(*arrs)
+        probe.step_single_dt(steps_single)
+        T = probe.t
+        probe.close()
+
+    ref = sif.Solver(dict(cfg0, cfl=ref_cfl), device=device).init_fluids(*arrs)
+    ref.step_single_dt(10 ** 8, t_end=T)
+    assert abs(ref.t - T) <= 1e-12 * T
+    qN, qP, phi = ref.state()
+    ref_rho, ref_ind = qN[0] + qP[0], (phi >= 0).astype(np.float64)
+    ref.close()
+
+    def error_of(s):
+        qN, qP, phi = s.state()
+        out = {"err": _rel_l1(qN[0] + qP[0], ref_rho),
+               "err_indicator": _rel_l1((phi >= 0).astype(np.float64), ref_ind)}
+        if exact is not None:
+            out["err_exact"] = exact(s)
+        return out
+
+    sweeps = {}
+    for mode in ("single", "multi"):
+        sweeps[mode] = [_sweep_point(dict(cfg0, cfl=c), arrs, device, mode, T, error_of,
+                                     profiled=(c == 0.6)) for c in cfls]
+    speedup, e_star, curve = equal_error_speedup(sweeps["single"], sweeps["multi"])
+
+    # Eq. 13 from measured quantities (CFL 0.6 runs): over the run
+    # single-dt does 2 (u1 + u2) open-cell stage updates a step and a
+    # multi-dt cycle 2 (u1 + [n] u2), which gives fluid 1's share of the
+    # updates; m is that share of the finite-volume time of the single-dt
+    # run over its whole time
+    s0, m0 = sweeps["single"][0], sweeps["multi"][0]
+    ps, pm = s0.pop("profile"), m0.pop("profile")
+    for pt in sweeps["single"][1:] + sweeps["multi"][1:]:
+        pt.pop("profile", None)
     s_bar = m0["mean_substeps"]
-    a_s = ps["fv_cell_updates"] / (2.0 * n_single)             # u1 + u2 per step
-    a_m = pm["fv_cell_updates"] / (2.0 * m0["cycles"])        # u1 + [n] u2 per cycle
+    a_s = ps["fv_open_updates"] / (2.0 * s0["steps"])          # u1 + u2 per step
+    a_m = pm["fv_open_updates"] / (2.0 * m0["steps"])          # u1 + [n] u2 per cycle
     u2 = (a_m - a_s) / (s_bar - 1.0) if s_bar > 1.0 else 0.0
     u1 = a_s - u2
-    m_share = (u1 / a_s) * (ps["fv_ms"] / single_ms)
-    n_eff = n_single / m0["cycles"]
+    m_share = (u1 / a_s) * (ps["fv_ms"] / s0["ms"])
+    n_eff = s0["steps"] / m0["steps"]
     cells = case["cfg"]["nx"] * case["cfg"]["ny"]
-    ref = f"single-dt on {fine_case['name']} averaged 2x2 (GPU)" if fine_case else None
-    return {"T": T, "reference": ref,
-            "speedup_at_equal_error": single_ms / t_eq if t_eq else None,
-            "speedup_same_cfl": single_ms / m0["ms"],
-            "single": single, "multi_sweep": sweep,
+    return {"T": T, "reference": f"single-dt at CFL {ref_cfl} on the same grid to T (GPU)",
+            "error": "relative L1 of the mixture density against the reference",
+            "speedup_at_equal_error": speedup, "equal_error_level": e_star,
+            "speedup_curve": curve,
+            "speedup_same_cfl": s0["ms"] / m0["ms"],
+            "single_sweep": sweeps["single"], "multi_sweep": sweeps["multi"],
             "eq13": {"n": n_eff, "substeps": s_bar, "m": m_share,
                      "fluid1_update_share": u1 / a_s,
-                     "fv_share_of_single_step": ps["fv_ms"] / single_ms,
+                     "fv_share_of_single_step": ps["fv_ms"] / s0["ms"],
                      "predicted_speedup": _eq13(n_eff, s_bar, m_share)},
-            "equivalent_grid_updates_per_s": {"single": cells * n_single / (single_ms * 1e-3),
-                                              "multi": cells * n_single / (m0["ms"] * 1e-3)},
-            "timing": "host wall clock around synchronising calls that run to T"}
+            "equivalent_grid_updates_per_s": {"single": cells * s0["steps"] / (s0["ms"] * 1e-3),
+                                              "multi": cells * s0["steps"] / (m0["ms"] * 1e-3)},
+            "timing": "host wall clock around one synchronising call that runs to T"}
 
 
-def adjoint_cost(device, n=512, nsteps=200, every=20):
+def tube_exact_error(T):
+    """L1 error of the 1D water/air tube's mixture density against the
+    cell-averaged exact solution (16 samples a cell) at time T."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import exact_riemann as ER
+    L = (1000.0, 0.0, 1.0e9, 4.4, 6.0e8)
+    R = (1.0, 0.0, 1.0e5, 1.4, 0.0)
+
+    def err(s):
+        qN, qP, _ = s.state()
+        n = s.nx
+        xs = (np.arange(n)[:, None] + (np.arange(16)[None, :] + 0.5) / 16) / n
+        ex, _, _, _ = ER.sample_left_rarefaction_right_shock(L, R, 0.5, T, xs.ravel())
+        ex = np.array(ex).reshape(n, 16).mean(axis=1)
+        return float(np.abs(qN[0, 0] + qP[0, 0] - ex).sum() / n)
+    return err
+
+
+def adjoint_cost(device, n=512, nsteps=200, every=20, centre=(0.7, 0.0)):
     """Gradient of the x = 1 wall pressure after nsteps single-dt steps with
     respect to the initial gas pressure field (gas-water bubble, n x n,
     nondimensional units) through the checkpointed autograd Function."""
     import torch
     from paper_1905_03917_gb300 import adjoint, inputs, sif
-    case = inputs.adjoint_bubble(n, centre=(0.7, 0.0))
+    case = inputs.adjoint_bubble(n, centre=centre)
     cfg = case["cfg"]
     dev = torch.device("cuda", device)
     phi, pN, pP = (torch.tensor(a, dtype=torch.float64, device=dev) for a in _prim_arrays(case))
@@ -416,7 +452,8 @@ def adjoint_cost(device, n=512, nsteps=200, every=20):
     bwd_ms = 1e3 * (time.perf_counter() - t0)
     g = pNg.grad[3]
     s.close()
-    return {"workload": f"adjoint_bubble_{n}x{n} (gas-water, nondimensional, bubble at x=0.7)",
+    return {"workload": f"adjoint_bubble_{n}x{n} (gas-water, nondimensional, bubble at "
+                        f"({centre[0]}, {centre[1]}))",
             "steps": nsteps, "checkpoint_every": every,
             "forward_ms_per_step": plain_ms / nsteps,
             "checkpointed_forward_ms_per_step": fwd_ms / nsteps,
@@ -427,25 +464,44 @@ def adjoint_cost(device, n=512, nsteps=200, every=20):
                       "segment from its checkpoint, recording, then its adjoint steps"}
 
 
-def run_ours(args):
-    import torch
-    rank, ws, local, dist = dist_setup()
-    torch.cuda.set_device(local)
+def _roofline(prof, shape, char, dim, total_ms):
+    """The finite-volume kernel against the FP64 peak: algorithmic flops of
+    the open (cell, fluid) stage updates of an average launch over its
+    average duration (the kernel's own global-timer span per launch)."""
     from paper_1905_03917_gb300 import sif
-    case = workload(args.workload, seed=rank)
-    char = args.weno == "characteristic"
-    if char:
-        case["cfg"]["weno_char"] = 1
-    arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
-    s = sif.Solver(case["cfg"], device=local).init_fluids(*arrs)
-    from paper_1905_03917_gb300 import autotune
-    if args.tile:
-        shape, tune_rec = tuple(int(x) for x in args.tile.split("x")), {}
-        s.set_tile_shape(*shape)
-    else:
-        shape, tune_rec = autotune.tune(s, device=local, cycles=3)
-    step = s.step_multi_dt if args.mode == "multi" else s.step_single_dt
-    for _ in range(args.warmup):
+    flops = (FLOPS_PER_UPDATE_CHAR if char else FLOPS_PER_UPDATE)[dim]
+    launches = max(prof["fv_launches"], 1)
+    fv_avg_ms = prof["fv_ms"] / launches
+    units = prof["fv_open_updates"] / launches
+    tile_units = prof["fv_cell_updates"] / launches
+    achieved = units * flops / (fv_avg_ms * 1e-3) / 1e12 if fv_avg_ms > 0 else None
+    per_update = None if char else MEASURED_DRAM_BYTES_PER_UPDATE.get(tuple(shape))
+    try:
+        probe = sif.measure_fp64_peak()
+    except Exception:
+        probe = None
+    return {"kernel": "k_fv_stage", "bound": "alu", "achieved": achieved,
+            "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / NOMINAL_FP64_TFLOPS if achieved else None,
+            "traffic": tile_units * per_update if per_update is not None else None,
+            "traffic_source": f"ncu DRAM bytes per computed cell of the 512 x 128 capture with "
+                              f"{shape[0]} x {shape[1]} tiles x cells computed per launch",
+            "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
+            "fp64_probe_tflops": probe, "flops_per_update": flops,
+            "units": "open (cell, fluid) stage updates", "avg_launch_ms": fv_avg_ms,
+            "updates_per_launch": units, "computed_cells_per_launch": tile_units,
+            "share_of_step": prof["fv_ms"] / total_ms if total_ms else None,
+            "hbm": _hbm_context(units, fv_avg_ms)}
+
+
+def measure_solver(s, mode, steps, warmup, device, dist=None):
+    """Warm-up, then `steps` steps timed one by one with CUDA events (L2
+    flushed before each), SM clocks sampled meanwhile; returns the timed
+    milliseconds, the work in fluid cell-updates, the schedule and the
+    library's counters over the timed steps."""
+    import torch
+    step = s.step_multi_dt if mode == "multi" else s.step_single_dt
+    for _ in range(warmup):
         step(1)
     # the library works on its private blocking stream, which is ordered
     # with the legacy default stream that torch's events are recorded on
@@ -454,9 +510,9 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     s.profile(True)
-    total_ms, updates, substeps = 0.0, 0, []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    total_ms, work, substeps = 0.0, 0.0, []
+    with ClockSampler(device) as clk:
+        for _ in range(steps):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -464,48 +520,142 @@ def run_ours(args):
             e1.record()
             e1.synchronize()
             total_ms += e0.elapsed_time(e1)
-            updates += info["cell_updates"]
+            work += info["fluid_cell_updates"]
             substeps.append(info["substeps"])
     prof = s.profile_read()
     s.profile(False)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    total_ms_all, updates_all = over_ranks(dist, total_ms, updates)
-    value = updates_all / (total_ms_all / 1e3)
+    del flush
+    return total_ms, work, substeps, prof, clk.summary()
 
-    # end to end through the public API: host state in, one step, host state out
-    n = case["cfg"]["nx"] * case["cfg"]["ny"]
+
+def e2e_rate(s, mode, steps):
+    """The metric through the public API with host buffers: every step the
+    state is copied in from pinned host memory, advanced and copied out."""
+    import torch
+    step = s.step_multi_dt if mode == "multi" else s.step_single_dt
+    n = s.nx * s.ny
     hq = [torch.empty(4 * n, dtype=torch.float64).pin_memory() for _ in range(2)]
     hphi = torch.empty(n, dtype=torch.float64).pin_memory()
     s.state_into(hq[0].numpy(), hq[1].numpy(), hphi.numpy())
     t_now = s.t
-    e2e_ms, e2e_updates = 0.0, 0
-    for _ in range(args.steps):
+    ms, work = 0.0, 0.0
+    for _ in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.set_state(hq[0].numpy(), hq[1].numpy(), hphi.numpy(), t_now)
         info = step(1)
         s.state_into(hq[0].numpy(), hq[1].numpy(), hphi.numpy())
-        e2e_ms += 1e3 * (time.perf_counter() - t0)
-        e2e_updates += info["cell_updates"]
+        ms += 1e3 * (time.perf_counter() - t0)
+        work += info["fluid_cell_updates"]
         t_now = info["t"]
-    e2e_bytes = 9 * n * 8
+    nbytes = 9 * n * 8
+    return {"value": work / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes}
 
+
+def workload_line(name, mode, steps, warmup, device, tile="", weno="componentwise"):
+    """Throughput of one more single-grid workload on this GPU (its own
+    warm-up, timed steps and clock record), for the same JSON line."""
+    from paper_1905_03917_gb300 import autotune, sif
+    case = workload(name)
+    if weno == "characteristic":
+        case["cfg"]["weno_char"] = 1
+    s = sif.Solver(case["cfg"], device=device).init_fluids(*_prim_arrays(case))
+    if tile:
+        shape = tuple(int(x) for x in tile.split("x"))
+        s.set_tile_shape(*shape)
+    else:
+        shape, _ = autotune.tune(s, device=device, cycles=3)
+    total_ms, work, substeps, prof, clocks = measure_solver(s, mode, steps, warmup, device)
+    line = {"workload": case["name"], "mode": mode, "value": work / (total_ms / 1e3),
+            "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
+            "mean_substeps": float(np.mean(substeps)), "tile_shape": list(shape),
+            "roofline": _roofline(prof, shape, weno == "characteristic", case["cfg"]["dim"],
+                                  total_ms),
+            "gpu_launches": prof["kernel_launches"], "clocks": clocks}
+    s.close()
+    return line
+
+
+def batched_line(steps, warmup, device, dist=None, rank=0, ws=1, weno="componentwise"):
+    """Many independent gas-water instances (64^2 .. 512^2), one graph
+    launch per batch cycle, tile shapes from the autotuner.  The instances
+    are independent problems, so with several ranks each rank takes an
+    equal share of them (no exchange)."""
+    import torch
+    from paper_1905_03917_gb300 import autotune, sif
+    cases = workload("batched")
+    mine = partition(len(cases), rank, ws)
+    cases = [cases[i] for i in mine]
+    if weno == "characteristic":
+        for c in cases:
+            c["cfg"]["weno_char"] = 1
+    b = sif.Batch([c["cfg"] for c in cases], device=device)
+    for s_, c in zip(b.instances, cases):
+        s_.init_fluids(*_prim_arrays(c))
+    tuned = autotune.tune_batch(b, device=device, cycles=1)
+    for _ in range(warmup):
+        b.step_multi_dt(1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, work = 0.0, 0.0
+    with ClockSampler(device) as clk:
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.step_multi_dt(1)
+            total_ms += 1e3 * (time.perf_counter() - t0)
+            work += b.last_open_updates / 2.0  # RK2: two stages a step
+    if dist:
+        dist.barrier()
+    cells = sum(c["cfg"]["nx"] * c["cfg"]["ny"] for c in cases)
+    rec = {"workload": f"batched_{len(cases)}_instances", "cells": cells,
+           "instances": [int(i) for i in (mine[0], mine[-1])] if mine else [],
+           "one_graph_per_cycle": b.one_graph,
+           "tile_shapes": {k: list(v) for k, v in tuned.items()}, "clocks": clk.summary()}
+    b.close()
+    return total_ms, work, rec
+
+
+def partition(n, rank, ws):
+    """Contiguous share of n independent instances for one of ws ranks
+    (sizes differ by at most one)."""
+    base, extra = divmod(n, ws)
+    start = rank * base + min(rank, extra)
+    return list(range(start, start + base + (1 if rank < extra else 0)))
+
+
+def run_ours(args):
+    import torch
+    rank, ws, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1905_03917_gb300 import autotune, sif
+    case = workload(args.workload, seed=rank)
+    char = args.weno == "characteristic"
+    if char:
+        case["cfg"]["weno_char"] = 1
+    s = sif.Solver(case["cfg"], device=local).init_fluids(*_prim_arrays(case))
+    if args.tile:
+        shape, tune_rec = tuple(int(x) for x in args.tile.split("x")), {}
+        s.set_tile_shape(*shape)
+    else:
+        shape, tune_rec = autotune.tune(s, device=local, cycles=3)
+    total_ms, work, substeps, prof, clocks = measure_solver(s, args.mode, args.steps,
+                                                            args.warmup, local, dist)
+    if dist:
+        dist.barrier()
+    total_ms_all, work_all = over_ranks(dist, total_ms, work)
+    value = work_all / (total_ms_all / 1e3)
+    e2e = e2e_rate(s, args.mode, args.steps)
+    s.close()
     if rank != 0:
         return
-    dim = case["cfg"]["dim"]
-    flops = (FLOPS_PER_UPDATE_CHAR if char else FLOPS_PER_UPDATE)[dim]
-    traffic_per_update = None if char else MEASURED_DRAM_BYTES_PER_UPDATE.get(tuple(shape))
-    fv_avg_ms = prof["fv_ms"] / max(prof["fv_launches"], 1)
-    fv_units = prof["fv_cell_updates"] / max(prof["fv_launches"], 1)
-    achieved_tf = fv_units * flops / (fv_avg_ms * 1e-3) / 1e12 if fv_avg_ms > 0 else None
-    try:
-        probe = sif.measure_fp64_peak(local)
-    except Exception:
-        probe = None
     line = {
-        "metric": METRIC, "value": value, "unit": "cell-updates/s",
+        "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms_all / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -513,89 +663,73 @@ def run_ours(args):
                    "ny": case["cfg"]["ny"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}", "mean_substeps": float(np.mean(substeps)),
                    "tile_shape": list(shape), "reconstruction": args.weno,
+                   "work_unit": "open (cell, fluid) pairs x RK steps",
                    "autotune_ms_per_cycle": tune_rec.get("ms_per_cycle")},
-        "roofline": {"kernel": "k_fv_stage", "bound": "alu", "achieved": achieved_tf,
-                     "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / NOMINAL_FP64_TFLOPS if achieved_tf else None,
-                     "traffic": (fv_units * traffic_per_update
-                                 if traffic_per_update is not None else None),
-                     "traffic_source": f"ncu DRAM bytes per update of the 512 x 128 capture with "
-                                       f"{shape[0]} x {shape[1]} tiles x updates per launch",
-                     "peak_source": "nominal FP64 (152 SMs x 4 flop/clk x 2.07 GHz)",
-                     "fp64_probe_tflops": probe, "flops_per_update": flops,
-                     "avg_launch_ms": fv_avg_ms, "updates_per_launch": fv_units,
-                     "share_of_step": prof["fv_ms"] / total_ms if total_ms else None,
-                     "hbm": _hbm_context(fv_units, fv_avg_ms)},
+        "roofline": _roofline(prof, shape, char, case["cfg"]["dim"], total_ms),
         "gpu_launches": prof["kernel_launches"],
-        "e2e": {"value": e2e_updates / (e2e_ms / 1e3), "unit": "cell-updates/s",
-                "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
-        "clocks": clk.summary(),
+        "e2e": e2e,
+        "clocks": clocks,
     }
-    if ws == 1 and not args.no_extras and case["name"].startswith("shock_bubble"):
-        from paper_1905_03917_gb300 import inputs
-        fine = inputs.shock_bubble(2 * case["cfg"]["nx"], 2 * case["cfg"]["ny"])
-        line["multi_vs_single"] = multi_vs_single(case, fine, local)
+    extras = ws == 1 and not args.no_extras
+    if extras and case["name"].startswith("shock_bubble"):
+        line["multi_vs_single"] = multi_vs_single(case, local)
+        tube = inputs_tube()
+        T = 2e-4
+        line["tube_multi_vs_single"] = multi_vs_single_tube(tube, local, T)
+        line["underwater_explosion"] = workload_line("underwater_explosion", "multi", args.steps,
+                                                     args.warmup, local, weno=args.weno)
+        ms_b, work_b, rec_b = batched_line(args.batch_cycles, args.warmup, local,
+                                           weno=args.weno)
+        rec_b.update({"value": work_b / (ms_b / 1e3), "unit": UNIT, "steps": args.batch_cycles,
+                      "ms_per_step": ms_b / args.batch_cycles,
+                      "timing": "host wall clock around each synchronising batch call"})
+        line["batched"] = rec_b
         line["adjoint"] = adjoint_cost(local)
-    elif ws == 1 and not args.no_extras and case["name"].startswith("underwater_explosion"):
-        # water, the fast fluid, fills almost the whole domain: the same-grid
-        # comparison over about 500 cycles with the n(t) trace, no finer
-        # reference (4096^2 to the same time would take minutes)
-        line["multi_vs_single"] = multi_vs_single(case, None, local, steps_single=1000)
+        line["adjoint_origin"] = adjoint_cost(local, centre=(0.0, 0.0))
     if ws == 1 and not args.no_cpu_baseline:
-        nsteps, secs = cpu_baseline(case, args.mode, budget_s=args.cpu_budget)
-        upd = gpu_updates_for(case, args.mode, 0, nsteps)
-        line["cpu_baseline"] = {"value": upd / secs if upd else None, "unit": "cell-updates/s",
+        nsteps, secs, work_cpu = cpu_baseline(case, args.mode, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": work_cpu / secs, "unit": UNIT,
                                 "cores": 1, "kind": "oracle",
                                 "sample": f"first {nsteps} {args.mode}-dt steps of {case['name']} "
-                                          f"({secs:.1f} s serial)"}
+                                          f"({secs:.1f} s serial; updates counted by the oracle)"}
     print(json.dumps(line), flush=True)
 
 
+def inputs_tube():
+    from paper_1905_03917_gb300 import inputs
+    return inputs.shock_tube_1d(400, rk_order=2)
+
+
+def multi_vs_single_tube(case, device, T):
+    """The 1D water/air tube (400 cells, TVD-RK2): the same protocol with
+    the run length set by T = 2e-4 s, the error also against the exact
+    solution."""
+    return multi_vs_single(case, device, ref_cfl=0.025, exact=tube_exact_error(T), T=T)
+
+
 def run_batched(args):
-    """Many independent gas-water instances (64^2 .. 512^2), one graph
-    launch per batch cycle, tile shapes from the autotuner."""
+    """The batch of independent instances as the headline workload; with
+    several ranks the instances are split between them."""
     import torch
     rank, ws, local, dist = dist_setup()
     torch.cuda.set_device(local)
-    from paper_1905_03917_gb300 import autotune, sif
-    cases = workload("batched", seed=rank)
-    if args.weno == "characteristic":
-        for c in cases:
-            c["cfg"]["weno_char"] = 1
-    b = sif.Batch([c["cfg"] for c in cases], device=local)
-    for s_, c in zip(b.instances, cases):
-        s_.init_fluids(*(np.ascontiguousarray(c[x]) for x in ("phi", "prim_N", "prim_P")))
-    tuned = autotune.tune_batch(b, device=local, cycles=1)
-    for _ in range(args.warmup):
-        b.step_multi_dt(1)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    total_ms, updates = 0.0, 0
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            updates += b.step_multi_dt(1)
-            total_ms += 1e3 * (time.perf_counter() - t0)
-    if dist:
-        dist.barrier()
-    total_ms, updates = over_ranks(dist, total_ms, updates)
+    total_ms, work, rec = batched_line(args.steps, args.warmup, local, dist, rank, ws,
+                                       weno=args.weno)
+    total_ms, work = over_ranks(dist, total_ms, work)
     if rank != 0:
         return
-    cells = sum(c["cfg"]["nx"] * c["cfg"]["ny"] for c in cases)
-    line = {"metric": METRIC, "value": updates / (total_ms / 1e3),
-            "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": work / (total_ms / 1e3),
+            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batched_{len(cases)}_instances", "cells": cells,
-                       "one_graph_per_cycle": b.one_graph,
-                       "tile_shapes": {k: list(v) for k, v in tuned.items()},
+            "config": {"workload": "batched_256_instances", "cells_rank0": rec["cells"],
+                       "partition": "instances split evenly between ranks, no exchange",
+                       "one_graph_per_cycle": rec["one_graph_per_cycle"],
+                       "tile_shapes": rec["tile_shapes"],
                        "l2": "flushed between timed steps (256 MB write)",
                        "timing": "host wall clock around each synchronising batch call"},
-            "clocks": clk.summary()}
+            "clocks": rec["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -609,13 +743,15 @@ def main():
     ap.add_argument("--mode", default="multi", choices=["multi", "single"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-cycles", type=int, default=200,
+                    help="timed cycles of the 256-instance batch in the default line")
     ap.add_argument("--tile", default="",
                     help="finite-volume tile shape TXxTY instead of the autotuner's choice")
     ap.add_argument("--weno", default="componentwise", choices=["componentwise", "characteristic"],
                     help="finite-volume reconstruction: on conserved components (the paper's "
                          "WENO-LF) or on characteristic fields")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the multi-vs-single and adjoint measurements")
+                    help="skip the multi-vs-single, explosion, batch and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -103,7 +103,14 @@ typedef struct {
   double n_used;     /* ratio after the 0.7 truncation (1 = single step) */
   int role_fluid1;   /* 0 = N, 1 = P, -1 for single-dt steps */
   int substeps;      /* fluid-2 sub-steps in the last cycle */
-  long long cell_updates; /* (cell, fluid) RK stage updates done by the call */
+  long long cell_updates; /* (cell, fluid) RK stage updates computed by the call's
+                             finite-volume stages (every cell of a fluid's active
+                             tiles, see sif_set_tile_shape) */
+  long long open_updates; /* of those, the (cell, fluid) pairs with at least one
+                             face open to the fluid (aperture A_k > 0, Eq. 2): the
+                             cells whose update Eq. 2 computes.  open_updates /
+                             rk_order is the call's work in fluid cell-updates
+                             (RK steps), independent of the tile shape */
 } sif_cycle_info;
 
 /* Create a context on cfg->device; allocates all device memory it needs.
@@ -183,11 +190,13 @@ int sif_batch_create(int n, const sif_config *cfgs, sif_batch **out);
 int sif_batch_instance(sif_batch *b, int i, sif_ctx **out);
 
 /* ncycles accelerated cycles of every instance (each at its own time
- * step and sub-step count).  *cell_updates (nullable) receives the
- * (cell, fluid) stage updates of all instances.  Every instance must have
+ * step and sub-step count).  *cell_updates and *open_updates (nullable)
+ * receive the sums over all instances of sif_cycle_info's counters of the
+ * same names.  Every instance must have
  * been initialised.  Synchronises at the end; the first error of any
  * instance is returned (sif_batch_last_error names the instance). */
-int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates);
+int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates,
+                            long long *open_updates);
 
 const char *sif_batch_last_error(const sif_batch *b);
 
@@ -261,6 +270,7 @@ typedef struct {
   long long fv_launches;      /* cut-cell finite-volume stage launches among them */
   double fv_ms;               /* summed CUDA-event time of those launches */
   long long fv_cell_updates;  /* (cell, fluid) stage updates they performed */
+  long long fv_open_updates;  /* of those, cells with a face open to the fluid */
 } sif_profile;
 
 /* enable != 0 resets the counters and starts recording a pair of CUDA

@@ -54,7 +54,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt1", ctypes.c_double), ("dt2", ctypes.c_double),
                 ("n_raw", ctypes.c_double), ("n_used", ctypes.c_double),
                 ("role_fluid1", ctypes.c_int), ("substeps", ctypes.c_int),
-                ("err", ctypes.c_int)]
+                ("err", ctypes.c_int), ("open_updates", ctypes.c_longlong)]
 
 
 _lib_handle = None
@@ -171,7 +171,9 @@ class Oracle:
     def _info(self, info):
         return {"t": info.t, "dt1": info.dt1, "dt2": info.dt2, "n_raw": info.n_raw,
                 "n_used": info.n_used, "role_fluid1": info.role_fluid1,
-                "substeps": info.substeps, "err": info.err}
+                "substeps": info.substeps, "err": info.err,
+                "open_updates": info.open_updates,
+                "fluid_cell_updates": info.open_updates / self._c.rk_order}
 
     def step_single_dt(self, nsteps=1, t_end=0.0):
         info = _Info()

@@ -75,6 +75,9 @@ struct orc_ctx {
   double lf[2][2];  /* Lax-Friedrichs alpha per fluid and direction */
   double t;
   int err;
+  /* (cell, fluid) pairs whose update had a face open to the fluid, summed
+   * over the finite-volume stages: the work count of the throughput figure */
+  long long open_updates;
   /* scratch */
   double *q0[2][4], *L[2][4], *old[4], *fx[4], *fy[4];
   double *prev[4], *fut[4], *qi[4], *xc[3];
@@ -892,6 +895,16 @@ static void fv_rhs(orc_ctx *o, int k, double *const L[4]) {
   for (int j = 0; j < ny; j++)
     for (int i = 0; i < nx; i++) {
       int c = ID(o, i, j);
+      /* a cell counts as updated if one of its faces is open to fluid k */
+      double Al = k == 1 ? o->ax[c] : 1.0 - o->ax[c];
+      double Ar = k == 1 ? o->ax[ID(o, i + 1, j)] : 1.0 - o->ax[ID(o, i + 1, j)];
+      int open = Al != 0.0 || Ar != 0.0;
+      if (o->c.dim == 2) {
+        double Ab = k == 1 ? o->ay[c] : 1.0 - o->ay[c];
+        double At = k == 1 ? o->ay[ID(o, i, j + 1)] : 1.0 - o->ay[ID(o, i, j + 1)];
+        open = open || Ab != 0.0 || At != 0.0;
+      }
+      o->open_updates += open;
       for (int m = 0; m < 4; m++) {
         double r = (o->fx[m][c] - o->fx[m][ID(o, i + 1, j)]) / o->c.dx;
         if (o->c.dim == 2) r += (o->fy[m][c] - o->fy[m][ID(o, i, j + 1)]) / o->c.dy;
@@ -1118,6 +1131,7 @@ static void single_step_after_eval(orc_ctx *o, double dt, step_record *rec) {
 }
 
 int orc_step_single_dt(orc_ctx *o, int nsteps, double t_end, orc_info *info) {
+  long long open0 = o->open_updates;
   for (int n = 0; n < nsteps; n++) {
     if (t_end > 0.0 && o->t >= t_end) break;
     eval(o, o->q, o->phi);
@@ -1134,7 +1148,10 @@ int orc_step_single_dt(orc_ctx *o, int nsteps, double t_end, orc_info *info) {
       info->substeps = 1;
     }
   }
-  if (info) info->err = o->err;
+  if (info) {
+    info->err = o->err;
+    info->open_updates = o->open_updates - open0;
+  }
   return o->err;
 }
 
@@ -1282,6 +1299,7 @@ static void cycle(orc_ctx *o, double t_end, orc_info *info) {
 }
 
 int orc_step_multi_dt(orc_ctx *o, int ncycles, double t_end, orc_info *info) {
+  long long open0 = o->open_updates;
   if (o->c.rk_order != 2) {
     o->err |= ORC_ERR_INVAL;
     if (info) info->err = o->err;
@@ -1291,7 +1309,10 @@ int orc_step_multi_dt(orc_ctx *o, int ncycles, double t_end, orc_info *info) {
     if (t_end > 0.0 && o->t >= t_end) break;
     cycle(o, t_end, info);
   }
-  if (info) info->err = o->err;
+  if (info) {
+    info->err = o->err;
+    info->open_updates = o->open_updates - open0;
+  }
   return o->err;
 }
 

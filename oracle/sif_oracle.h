@@ -54,6 +54,8 @@ typedef struct {
   int role_fluid1; /* index (0 = N, 1 = P) of the fluid with the larger step */
   int substeps;    /* fluid-2 sub-steps taken in the last cycle */
   int err;
+  long long open_updates; /* (cell, fluid) finite-volume stage updates of the call
+                             in cells with a face open to the fluid */
 } orc_info;
 
 typedef struct orc_ctx orc_ctx;

@@ -41,7 +41,7 @@ struct sif_ctx {
   int debug_sync;    // SIF_DEBUG_SYNC=1: synchronise and check after each phase
   // profiling: device counters (kernel launches, finite-volume launch time)
   int profiling;
-  unsigned long long launches0, updates0;
+  unsigned long long launches0, updates0, open0;
   // work stream: the caller's, or a private blocking stream (ordered with
   // the legacy default stream) when the caller passes none
   cudaStream_t own_stream;
@@ -592,7 +592,12 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
   }
 }
 
-static int finish(sif_ctx *c, sif_cycle_info *info, unsigned long long upd0) {
+// update counters at the start of a call: active-tile and open-cell stage updates
+struct Upd {
+  unsigned long long tile, open;
+};
+
+static int finish(sif_ctx *c, sif_cycle_info *info, Upd upd0) {
   side_join(c);
   int rc = check_launch(c, "step");
   if (rc) return rc;
@@ -601,7 +606,8 @@ static int finish(sif_ctx *c, sif_cycle_info *info, unsigned long long upd0) {
   c->band_work = c->hsc->n_band;
   if (info) {
     info->t = c->hsc->t;
-    info->cell_updates = (long long)(c->hsc->updates - upd0);
+    info->cell_updates = (long long)(c->hsc->updates - upd0.tile);
+    info->open_updates = (long long)(c->hsc->open_updates - upd0.open);
   }
   if (c->hsc->err & DERR_NONPHYS) {
     set_err(c, "non-physical state (rho <= 0 or p + p_inf <= 0) in a real cell");
@@ -614,7 +620,7 @@ static int finish(sif_ctx *c, sif_cycle_info *info, unsigned long long upd0) {
   return SIF_OK;
 }
 
-static int begin_call(sif_ctx *c, double t_end, unsigned long long *upd0) {
+static int begin_call(sif_ctx *c, double t_end, Upd *upd0) {
   if (!c->inited) {
     set_err(c, "state not initialised");
     return SIF_ESTATE;
@@ -623,7 +629,8 @@ static int begin_call(sif_ctx *c, double t_end, unsigned long long *upd0) {
   side_join(c);
   CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  *upd0 = c->hsc->updates;
+  upd0->tile = c->hsc->updates;
+  upd0->open = c->hsc->open_updates;
   // reset the error word; set t_end
   c->hbuf[0] = t_end;
   CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st));
@@ -639,7 +646,7 @@ extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycl
     set_err(c, "adjoint tape full (%d of %d steps recorded)", c->tape_len, c->tape_cap);
     return SIF_EINVAL;
   }
-  unsigned long long upd0;
+  Upd upd0;
   int rc = begin_call(c, t_end, &upd0);
   if (rc) return rc;
   for (int n = 0; n < nsteps; n++) {
@@ -1024,7 +1031,7 @@ extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycl
     set_err(c, "the adjoint tape records single-time-step steps only");
     return SIF_ESTATE;
   }
-  unsigned long long upd0;
+  Upd upd0;
   int rc = begin_call(c, t_end, &upd0);
   if (rc) return rc;
   if (ensure_graphs(c) == SIF_OK) {
@@ -1603,6 +1610,7 @@ extern "C" int sif_profile_enable(sif_ctx *c, int enable) {
     CK(cudaMemcpy((char *)c->sc + offsetof(Scalars, timing), &z, sizeof(z), cudaMemcpyHostToDevice));
     c->launches0 = device_launches();
     c->updates0 = c->hsc->updates;
+    c->open0 = c->hsc->open_updates;
   } else {
     int zero = 0;
     CK(cudaMemcpy(&c->sc->timing, &zero, sizeof(int), cudaMemcpyHostToDevice));
@@ -1620,6 +1628,7 @@ extern "C" int sif_profile_read(sif_ctx *c, sif_profile *out) {
   out->fv_launches = (long long)c->hsc->fv_launches;
   out->fv_ms = (double)c->hsc->fv_ns * 1e-6;
   out->fv_cell_updates = (long long)(c->hsc->updates - c->updates0);
+  out->fv_open_updates = (long long)(c->hsc->open_updates - c->open0);
   return SIF_OK;
 }
 
@@ -1764,9 +1773,10 @@ static int batch_build(sif_batch *b) {
   return SIF_OK;
 }
 
-extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates) {
+extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cell_updates,
+                                       long long *open_updates) {
   if (!b || ncycles < 0) return SIF_EINVAL;
-  std::vector<unsigned long long> upd0(b->n);
+  std::vector<Upd> upd0(b->n);
   bool rebuild = !b->exec;
   for (int i = 0; i < b->n; i++) {
     sif_ctx *c = b->ctx[i];
@@ -1797,17 +1807,19 @@ extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cel
     snprintf(b->err, sizeof(b->err), "batch cycle: %s", cudaGetErrorString(e));
     return SIF_ECUDA;
   }
-  long long total = 0;
+  long long total = 0, total_open = 0;
   int first_rc = SIF_OK;
   for (int i = 0; i < b->n; i++) {
     int rc = finish(b->ctx[i], nullptr, upd0[i]);
-    total += (long long)(b->ctx[i]->hsc->updates - upd0[i]);
+    total += (long long)(b->ctx[i]->hsc->updates - upd0[i].tile);
+    total_open += (long long)(b->ctx[i]->hsc->open_updates - upd0[i].open);
     if (rc != SIF_OK && first_rc == SIF_OK) {
       first_rc = rc;
       snprintf(b->err, sizeof(b->err), "instance %d: %.200s", i, b->ctx[i]->err);
     }
   }
   if (cell_updates) *cell_updates = total;
+  if (open_updates) *open_updates = total_open;
   return first_rc;
 }
 

@@ -200,6 +200,7 @@ struct FvShape {
   // two threads per output cell: a CTA's phases finish in half the time,
   // which matters when a fluid has few tiles (the sub-cycled fluid)
   static constexpr int threads = 2 * TX * TY;
+  static_assert(threads >= TX * TY, "the open-cell count needs a thread per cell");
 };
 
 // the three phases over an SX x SY block of output cells at (i0, j0), with
@@ -397,15 +398,21 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
     __syncthreads();
   }
 
-  // phase 3: update of the block's cells
+  // phase 3: update of the block's cells; count those with an open face of
+  // fluid k (the work unit of the throughput figures)
   const double dt = *A.dtp;
   const double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
   const double sgn = k == 0 ? 1.0 : -1.0;
+  const double closed = k == 0 ? 1.0 : 0.0;  // aperture A_P of a face closed to fluid k
+  int open_cells = 0;
   for (int r = tid; r < SX * SY; r += nth) {
     int li = r % SX, lj = r / SX;
     int i = i0 + li, j = j0 + lj;
     if (i >= g.nx || j >= g.ny) continue;
     int c = gidx(g, i, j);
+    bool open = A.ax[c] != closed || A.ax[c + 1] != closed;
+    if (d2) open = open || A.ay[c] != closed || A.ay[c + g.PX] != closed;
+    open_cells += open ? 1 : 0;
     bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
 #pragma unroll
     for (int m = 0; m < 4; m++) {
@@ -421,6 +428,11 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
       A.dst[m][c] = out;
     }
   }
+  // every thread holds at most one cell here (a CTA has two threads per
+  // cell of its tile, see FvShape), so the count is a barrier count
+  const int nopen = __syncthreads_count(open_cells);
+  if (tid == 0 && nopen > 0)
+    atomicAdd((unsigned long long *)&A.sc->open_updates, (unsigned long long)nopen);
 }
 
 // A fluid with fewer active tiles than the GPU has SMs (the sub-cycled

@@ -57,7 +57,8 @@ struct Scalars {
   int n_cut, n_tiles[2];
   double dtk_raw[2];
   double dt2_first;             // fluid-2 step chosen at the start of the cycle
-  unsigned long long updates;   // (cell, fluid) stage updates issued
+  unsigned long long updates;   // (cell, fluid) stage updates issued (active-tile cells)
+  unsigned long long open_updates;  // of those, cells with an open face of the fluid
   // finite-volume launch timing on the GPU's global timer (graph-safe):
   // each launch keeps its earliest block start and latest block end, the
   // last block to finish adds the span to fv_ns

@@ -56,14 +56,15 @@ class Config(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("fv_launches", ctypes.c_longlong),
-                ("fv_ms", ctypes.c_double), ("fv_cell_updates", ctypes.c_longlong)]
+                ("fv_ms", ctypes.c_double), ("fv_cell_updates", ctypes.c_longlong),
+                ("fv_open_updates", ctypes.c_longlong)]
 
 
 class CycleInfo(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt1", ctypes.c_double), ("dt2", ctypes.c_double),
                 ("n_raw", ctypes.c_double), ("n_used", ctypes.c_double),
                 ("role_fluid1", ctypes.c_int), ("substeps", ctypes.c_int),
-                ("cell_updates", ctypes.c_longlong)]
+                ("cell_updates", ctypes.c_longlong), ("open_updates", ctypes.c_longlong)]
 
 
 _lib = None
@@ -102,7 +103,8 @@ def load(path: str | None = None):
     L.sif_get_tile_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
     L.sif_batch_create.argtypes = [I, ctypes.POINTER(Config), ctypes.POINTER(P)]
     L.sif_batch_instance.argtypes = [P, I, ctypes.POINTER(P)]
-    L.sif_batch_step_multi_dt.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong)]
+    L.sif_batch_step_multi_dt.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_longlong)]
     L.sif_batch_last_error.argtypes = [P]
     L.sif_batch_last_error.restype = ctypes.c_char_p
     L.sif_batch_destroy.argtypes = [P]
@@ -271,7 +273,9 @@ class Solver:
     def _info(self, info):
         return {"t": info.t, "dt1": info.dt1, "dt2": info.dt2, "n_raw": info.n_raw,
                 "n_used": info.n_used, "role_fluid1": info.role_fluid1,
-                "substeps": info.substeps, "cell_updates": info.cell_updates}
+                "substeps": info.substeps, "cell_updates": info.cell_updates,
+                "open_updates": info.open_updates,
+                "fluid_cell_updates": info.open_updates / int(self.cfg.get("rk_order", 2))}
 
     def step_single_dt(self, nsteps=1, t_end=0.0):
         info = CycleInfo()
@@ -327,7 +331,8 @@ class Solver:
         p = Profile()
         self._check(load().sif_profile_read(self._h, ctypes.byref(p)))
         return {"kernel_launches": p.kernel_launches, "fv_launches": p.fv_launches,
-                "fv_ms": p.fv_ms, "fv_cell_updates": p.fv_cell_updates}
+                "fv_ms": p.fv_ms, "fv_cell_updates": p.fv_cell_updates,
+                "fv_open_updates": p.fv_open_updates}
 
     def load_checkpoint(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
@@ -418,10 +423,14 @@ class Batch:
         return self.instances[i]
 
     def step_multi_dt(self, ncycles=1):
-        n = ctypes.c_longlong(0)
-        rc = load().sif_batch_step_multi_dt(self._h, int(ncycles), ctypes.byref(n))
+        """ncycles batch cycles; returns the (cell, fluid) stage updates of
+        all instances (active-tile cells); last_open_updates keeps the
+        open-cell count of the same call."""
+        n, o = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        rc = load().sif_batch_step_multi_dt(self._h, int(ncycles), ctypes.byref(n), ctypes.byref(o))
         if rc != OK:
             raise SifError(rc, load().sif_batch_last_error(self._h).decode())
+        self.last_open_updates = o.value
         return n.value
 
     @property

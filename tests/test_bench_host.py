@@ -26,3 +26,38 @@ def test_eq13_limits_and_the_papers_example():
     assert np.isclose(bench._eq13(2.8, 3, 0.75), 2.8 / 1.5)
     # integer ratio with one sub-step: the original method
     assert bench._eq13(1.0, 1, 0.3) == 1.0
+
+
+def test_time_at_error_interpolates_log_log_and_never_extrapolates():
+    curve = [{"cfl": 0.6, "err": 4e-3, "ms": 100.0}, {"cfl": 0.3, "err": 1e-3, "ms": 200.0}]
+    # halfway in log error is halfway in log time
+    assert np.isclose(bench._time_at_error(curve, 2e-3), 100.0 * np.sqrt(2.0))
+    assert bench._time_at_error(curve, 4e-3) == 100.0
+    assert bench._time_at_error(curve, 1e-3) == 200.0
+    assert bench._time_at_error(curve, 5e-3) is None
+    assert bench._time_at_error(curve, 5e-4) is None
+
+
+def test_equal_error_speedup_takes_the_looser_common_error():
+    single = [{"cfl": 0.6, "err": 2e-3, "ms": 100.0}, {"cfl": 0.3, "err": 5e-4, "ms": 200.0}]
+    # multi-step: larger error at the same CFL number, half the time
+    multi = [{"cfl": 0.6, "err": 4e-3, "ms": 50.0}, {"cfl": 0.3, "err": 1e-3, "ms": 100.0}]
+    sp, e_star, curve = bench.equal_error_speedup(single, multi)
+    assert e_star == 2e-3
+    # multi needs 50 * sqrt(2) ms for 2e-3 (halfway in log error)
+    assert np.isclose(sp, 100.0 / (50.0 * np.sqrt(2.0)))
+    assert np.isclose(curve[0]["speedup"], sp)
+    assert curve[1]["speedup"] is None          # 5e-4 lies outside the multi sweep
+    # the other way round: multi more accurate at CFL 0.6
+    sp2, e2, _ = bench.equal_error_speedup(multi, single)
+    assert e2 == 2e-3 and np.isclose(sp2, 50.0 * np.sqrt(2.0) / 100.0)
+
+
+def test_partition_covers_every_instance_once():
+    for n in (1, 7, 256):
+        for ws in (1, 2, 3, 8):
+            parts = [bench.partition(n, r, ws) for r in range(ws)]
+            flat = [i for p in parts for i in p]
+            assert flat == list(range(n))
+            sizes = [len(p) for p in parts]
+            assert max(sizes) - min(sizes) <= 1

@@ -27,7 +27,17 @@ def _rank_main(rank, world, port, out_dir, what):
     import bench
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
-        if what == "reduce":
+        if what == "batch":
+            # each rank advances its share of 256 independent instances;
+            # the whole job is the sum of the shares' work over the
+            # slowest rank's time
+            r, ws, local, dist = bench.dist_setup()
+            mine = bench.partition(256, r, ws)
+            res = {"rank": r, "mine": mine,
+                   "fig": bench.over_ranks(dist, 10.0 + 5.0 * r, sum(i + 1 for i in mine))}
+            dist.barrier()
+            print(json.dumps(res))
+        elif what == "reduce":
             r, ws, local, dist = bench.dist_setup()
             res = {"rank": r, "ws": ws, "local": local,
                    "fig": bench.over_ranks(dist, 10.0 + 5.0 * r, 100 * (r + 1))}
@@ -77,3 +87,11 @@ def test_oracle_arm_runs_on_rank_zero_only(tmp_path):
 def test_single_rank_needs_no_process_group():
     import bench
     assert bench.over_ranks(None, 7.5, 12) == (7.5, 12.0)
+
+
+def test_two_ranks_split_the_batch_and_merge_its_work(tmp_path):
+    outs = [json.loads(t) for t in _spawn(tmp_path, "batch")]
+    assert outs[0]["mine"] + outs[1]["mine"] == list(range(256))
+    assert len(outs[0]["mine"]) == len(outs[1]["mine"]) == 128
+    for res in outs:
+        assert res["fig"] == [15.0, float(256 * 257 // 2)]

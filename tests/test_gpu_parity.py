@@ -85,10 +85,12 @@ def test_init_matches_oracle():
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_single_step(name):
     g, o = pair(CASES[name]())
-    g.step_single_dt(1)
-    o.step_single_dt(1)
+    gi = g.step_single_dt(1)
+    oi = o.step_single_dt(1)
     compare(g, o, 1e-12)
     assert abs(g.t - o.t) <= 1e-14 * o.t
+    # the work count (cells with a face open to the fluid), integer: exact
+    assert gi["open_updates"] == oi["open_updates"] > 0
 
 
 @pytest.mark.parametrize("name", ["tube_rk3", "bubble_periodic", "shock_bubble", "explosion"])
@@ -108,6 +110,7 @@ def test_one_multi_dt_cycle(name):
     assert gi["substeps"] == oi["substeps"]
     assert gi["role_fluid1"] == oi["role_fluid1"] or oi["substeps"] == 1
     compare(g, o, 1e-12)
+    assert gi["open_updates"] == oi["open_updates"] > 0
 
 
 @pytest.mark.parametrize("name", MULTI)
