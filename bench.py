@@ -401,8 +401,7 @@ def multi_vs_single(case, device, steps_single=600, cfls=(0.6, 0.5, 0.4, 0.3, 0.
 def tube_exact_error(T):
     """L1 error of the 1D water/air tube's mixture density against the
     cell-averaged exact solution (16 samples a cell) at time T."""
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    import exact_riemann as ER
+    from tests import exact_riemann as ER
     L = (1000.0, 0.0, 1.0e9, 4.4, 6.0e8)
     R = (1.0, 0.0, 1.0e5, 1.4, 0.0)
 
