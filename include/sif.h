@@ -173,6 +173,19 @@ int sif_load(sif_ctx *ctx, const void *buf, size_t len);
 int sif_set_tile_shape(sif_ctx *ctx, int tx, int ty);
 int sif_get_tile_shape(const sif_ctx *ctx, int *tx, int *ty);
 
+/* Limits of the two bounded loops of a step (no counterpart in the paper,
+ * whose method has no iteration limits): max_substeps, the fluid-2
+ * sub-steps one accelerated cycle may take (default 4096; Sec. 3.1's
+ * sub-cycle loop), and newton_iters, the Newton iterations of each
+ * interface Riemann problem (default 50).  A cycle that reaches
+ * max_substeps before its last sub-step stops with SIF_ETIMEOUT and leaves
+ * the state undefined (restore a checkpoint); a Riemann problem that has
+ * not converged after newton_iters iterations makes the step return
+ * SIF_ENOCONV.  A value <= 0 keeps that limit; SIF_EINVAL above 1000000
+ * sub-steps or 10000 iterations.  The captured graphs are rebuilt on the
+ * next step.  Synchronises. */
+int sif_set_limits(sif_ctx *ctx, int max_substeps, int newton_iters);
+
 /* ---------------------------------------------------------------------
  * Batches of independent problems (uneven grid sizes) advanced together:
  * every instance's accelerated cycle is one device-driven CUDA graph

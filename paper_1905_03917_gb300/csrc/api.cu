@@ -66,6 +66,7 @@ struct sif_ctx {
   int graph_gen;             // bumped whenever the graphs are rebuilt
   int inited;
   int last_status;
+  int max_substeps;  // fluid-2 sub-steps allowed in one accelerated cycle
   // adjoint: tape of recorded single-time-step steps (own allocation) and
   // the adjoint's scratch planes (allocated on first use)
   int tape_cap, tape_len, tape_alloc;
@@ -84,6 +85,10 @@ struct sif_ctx {
 // the cut cells without a physical state of both stages and fluids
 static const int kTapePlanes = 36;
 static const int kTapeW1 = 19, kTapeW2 = 27, kTapeFlags = 35;
+
+// default limits of the two bounded loops of a step (sif_set_limits)
+static const int kMaxSubsteps = 4096;  // fluid-2 sub-steps in one cycle
+static const int kNewtonMax = 50;      // Newton iterations per interface Riemann problem
 
 // launch counting happens on the device (SIF_TICK); the host-side notes
 // the wrappers make are not used for measurement
@@ -222,6 +227,8 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.mu[1] = f.mu[1];
   g.tx = FV_TX;
   g.ty = FV_TY;
+  g.newton_max = kNewtonMax;
+  c->max_substeps = kMaxSubsteps;
   g.ntx = (f.nx + g.tx - 1) / g.tx;
   g.nty = (f.ny + g.ty - 1) / g.ty;
   c->NP = (size_t)g.PX * g.PY;
@@ -614,8 +621,14 @@ static int finish(sif_ctx *c, sif_cycle_info *info, Upd upd0) {
     return SIF_ENONPHYS;
   }
   if (c->hsc->err & DERR_NOCONV) {
-    set_err(c, "interface Riemann Newton iteration did not converge");
+    set_err(c, "interface Riemann Newton iteration did not converge in %d iterations",
+            c->g.newton_max);
     return SIF_ENOCONV;
+  }
+  if (c->hsc->err & DERR_TIMEOUT) {
+    set_err(c, "the cycle needed more than %d fluid-2 sub-steps (state undefined)",
+            c->max_substeps);
+    return SIF_ETIMEOUT;
   }
   return SIF_OK;
 }
@@ -782,8 +795,9 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
     geometry(c, true);
     mix_one(c, f2, c->q[f2]);
-    if (sub > 100000) {
-      set_err(c, "sub-cycle count exceeded 100000");
+    if (sub >= c->max_substeps) {
+      set_err(c, "the cycle needed more than %d fluid-2 sub-steps (state undefined)",
+              c->max_substeps);
       return SIF_ETIMEOUT;
     }
   }
@@ -798,8 +812,6 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
 // cycle, fluid 1's identity, first and last sub-step) and a WHILE node
 // repeats the fluid-2 sub-step, so no host round trip remains inside a
 // cycle.  The kernels are exactly those of the host-driven path.
-
-static const int kMaxSubsteps = 4096;
 
 static cudaGraph_t capture_graph(sif_ctx *c) {
   cudaStreamCaptureStatus st;
@@ -922,7 +934,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
     geometry(c, true);
     mix_one(c, f2, c->q[f2]);
   });
-  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, kMaxSubsteps, c->st);
+  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, c->max_substeps, c->st);
 }
 
 static void graph_cycle_body(sif_ctx *c, int f1) {
@@ -934,7 +946,7 @@ static void graph_cycle_body(sif_ctx *c, int f1) {
   copy4(c, c->fut, c->q[f1]);
   fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
   cudaGraphConditionalHandle hloop = new_handle(c);
-  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, kMaxSubsteps, c->st);  // last = 0 here
+  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, c->max_substeps, c->st);  // last = 0 here
   cond_node(c, hloop, true, [&] { graph_substep(c, f1, hloop); });
   launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
 }
@@ -1052,10 +1064,6 @@ extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycl
       info->dt1 = h->mode == 0 ? h->dt : h->dt1;
       info->dt2 = h->mode == 0 ? h->dt : h->dt2_first;
       info->substeps = h->mode == 0 ? 1 : h->sub;
-    }
-    if (!rc && c->hsc->mode == 1 && c->hsc->sub >= kMaxSubsteps) {
-      set_err(c, "sub-cycle count reached %d", kMaxSubsteps);
-      return SIF_ETIMEOUT;
     }
     return rc;
   }
@@ -1662,6 +1670,24 @@ extern "C" int sif_get_tile_shape(const sif_ctx *c, int *tx, int *ty) {
   if (!c || !tx || !ty) return SIF_EINVAL;
   *tx = c->g.tx;
   *ty = c->g.ty;
+  return SIF_OK;
+}
+
+// ---------------------------------------------------------------------
+// limits of the bounded loops (both are baked into the captured graphs)
+
+extern "C" int sif_set_limits(sif_ctx *c, int max_substeps, int newton_iters) {
+  if (!c) return SIF_EINVAL;
+  if (max_substeps > 1000000 || newton_iters > 10000) {
+    set_err(c, "limits too large (%d sub-steps, %d Newton iterations)", max_substeps,
+            newton_iters);
+    return SIF_EINVAL;
+  }
+  cudaSetDevice(c->cfg.device);
+  CK(cudaStreamSynchronize(c->st));
+  if (max_substeps > 0) c->max_substeps = max_substeps;
+  if (newton_iters > 0) c->g.newton_max = newton_iters;
+  free_graphs(c);
   return SIF_OK;
 }
 

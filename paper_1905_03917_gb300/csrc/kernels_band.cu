@@ -171,7 +171,7 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
 // star sound speed.
 __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, double un,
                                          double pk, double gk, double pik, double jump,
-                                         double &ps, double &us, double &cs) {
+                                         int maxit, double &ps, double &us, double &cs) {
   double ck = sqrt(gk * (pk + pik) / rho);
   double ro = __shfl_xor_sync(pair, rho, 1), uo = __shfl_xor_sync(pair, un, 1);
   double po = __shfl_xor_sync(pair, pk, 1), pio = __shfl_xor_sync(pair, pik, 1);
@@ -187,7 +187,7 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
   const double own = L ? jump : 0.0;  // this lane's star pressure is p + own
   int it = 0, conv = 0, done = 0;
   double f, df;
-  while (it < 50) {
+  while (it < maxit) {
     it++;
     riemann_side(p + own, rho, pk, gk, pik, ck, f, df);
     double fo = __shfl_xor_sync(pair, f, 1), dfo = __shfl_xor_sync(pair, df, 1);
@@ -274,7 +274,8 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
     // fluid N (Eq. 10; kappa > 0 where fluid N is convex)
     const double jump = g.sigma != 0.0 ? g.sigma * curvature(g, phi, i, j) : 0.0;
     double ps, us, cs;
-    int e = riemann_solve_pair(pair, side, rho, un, pk, g.gamma[side], g.pinf[side], jump, ps,
+    int e = riemann_solve_pair(pair, side, rho, un, pk, g.gamma[side], g.pinf[side], jump,
+                               g.newton_max, ps,
                                us, cs);
     if (e && side == 0) atomicOr(&sc->err, e);
     // each fluid's exchange flux with its own interface pressure: fluid N
@@ -761,7 +762,7 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
 }
 
 // graph conditions from the scheduler's decisions
-__global__ void k_cond(int op, const Scalars *sc, cudaGraphConditionalHandle h0,
+__global__ void k_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0,
                        cudaGraphConditionalHandle h1, cudaGraphConditionalHandle h2, int max_sub) {
   SIF_TICK();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -782,6 +783,8 @@ __global__ void k_cond(int op, const Scalars *sc, cudaGraphConditionalHandle h0,
       // stop after the last sub-step, on a device error, or when the
       // sub-step count or step size has gone wrong
       bool go = !sc->last && sc->err == 0 && sc->sub < max_sub && sc->dt2 > 0.0;
+      // the sub-step limit stops an unfinished cycle: an error, not an end
+      if (!sc->last && sc->err == 0 && sc->sub >= max_sub) sc->err |= DERR_TIMEOUT;
       cudaGraphSetConditional(h0, go ? 1u : 0u);
       break;
     }

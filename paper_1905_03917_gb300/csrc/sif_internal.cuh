@@ -38,6 +38,7 @@ struct Grid {
   double mu[2];   // dynamic viscosities of fluids N and P, 0 = inviscid
   int tx, ty;    // finite-volume tile shape (output cells per CTA)
   int ntx, nty;  // tiles per direction
+  int newton_max;  // Newton iterations allowed per interface Riemann problem
 };
 
 // Scalars that live in device memory so that a whole step can run without

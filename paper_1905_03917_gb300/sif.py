@@ -28,7 +28,7 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif_batch_create", "sif_batch_instance", "sif_batch_step_multi_dt",
            "sif_batch_last_error", "sif_batch_destroy", "sif_batch_one_graph",
            "sif_tape_reset", "sif_tape_length", "sif_replay_step", "sif_adjoint_step",
-           "sif_adjoint_init", "sif_probe_reciprocal"]
+           "sif_adjoint_init", "sif_probe_reciprocal", "sif_set_limits"]
 
 
 class SifError(RuntimeError):
@@ -100,6 +100,8 @@ def load(path: str | None = None):
     L.sif_probe_reciprocal.argtypes = [P, P, ctypes.c_longlong, P]
     L.sif_integrals_noalloc.argtypes = [P, P, I, I, D, D, P, P]
     L.sif_set_tile_shape.argtypes = [P, I, I]
+    L.sif_set_limits.argtypes = [P, I, I]
+    L.sif_set_limits.restype = I
     L.sif_get_tile_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
     L.sif_batch_create.argtypes = [I, ctypes.POINTER(Config), ctypes.POINTER(P)]
     L.sif_batch_instance.argtypes = [P, I, ctypes.POINTER(P)]
@@ -317,6 +319,11 @@ class Solver:
 
     def set_tile_shape(self, tx: int, ty: int):
         self._check(load().sif_set_tile_shape(self._h, int(tx), int(ty)))
+
+    def set_limits(self, max_substeps=0, newton_iters=0):
+        """Sub-steps per accelerated cycle and Newton iterations per
+        interface Riemann problem (0 keeps a limit); see sif_set_limits."""
+        self._check(load().sif_set_limits(self._h, int(max_substeps), int(newton_iters)))
 
     @property
     def tile_shape(self):

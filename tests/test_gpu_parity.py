@@ -34,20 +34,31 @@ def sound_speed_scale(case):
 
 
 def compare(gpu, orc, tol, cref=None):
-    """Relative L1 of every fluid/component and of phi; returns the worst.
-    Momentum is measured against (mass x the largest initial sound speed)
-    when the reference momentum is smaller, so that a component that is
-    zero up to round-off (a fluid at rest) is judged on a physical scale."""
+    """Relative L1 of every fluid/component and of phi, and the largest
+    element-wise difference relative to the component's largest value;
+    returns the worst.  Momentum is measured against (mass x the largest
+    initial sound speed) when the reference momentum is smaller, so that a
+    component that is zero up to round-off (a fluid at rest) is judged on a
+    physical scale: its rounding errors scale with the momentum fluxes,
+    rho c, not with its own (vanishing) size."""
     worst = 0.0
     gs, os_ = gpu.state(), orc.state()
     cref = cref if cref is not None else getattr(orc, "cref", 0.0)
     for k in range(2):
         mass = np.abs(os_[k][0]).sum()
+        rho_max = np.abs(os_[k][0]).max()
         for m in range(4):
             floor = 1e-300 if m in (0, 3) else max(mass * cref, 1e-300)
             e = rel_l1(gs[k][m], os_[k][m], floor)
             worst = max(worst, e)
             assert e <= tol, (k, m, e)
+            scale = np.abs(os_[k][m]).max()
+            if m in (1, 2):
+                scale = max(scale, rho_max * cref)
+            if scale > 0.0:
+                e_max = np.abs(gs[k][m] - os_[k][m]).max() / scale
+                worst = max(worst, e_max)
+                assert e_max <= tol, ("max", k, m, e_max)
     e = rel_l1(gs[2], os_[2], 1e-300)
     assert e <= tol, ("phi", e)
     return max(worst, e)
@@ -121,6 +132,20 @@ def test_fifty_multi_dt_cycles(name):
         subs_g.append(g.step_multi_dt(1)["substeps"])
         subs_o.append(o.step_multi_dt(1)["substeps"])
     assert subs_g == subs_o
+    compare(g, o, 1e-8)
+
+
+@pytest.mark.parametrize("name", ["shock_bubble", "explosion_fast_gas"])
+def test_hundred_multi_dt_cycles(name):
+    """100 accelerated cycles (every one a multi-step cycle with its own
+    sub-step count): the schedule cycle by cycle and the states at 1e-8."""
+    g, o = pair(CASES[name]())
+    subs_g, subs_o = [], []
+    for _ in range(100):
+        subs_g.append(g.step_multi_dt(1)["substeps"])
+        subs_o.append(o.step_multi_dt(1)["substeps"])
+    assert subs_g == subs_o
+    assert min(subs_o) >= 2
     compare(g, o, 1e-8)
 
 
