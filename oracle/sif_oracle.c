@@ -82,6 +82,9 @@ struct orc_ctx {
   double *q0[2][4], *L[2][4], *old[4], *fx[4], *fy[4];
   double *prev[4], *fut[4], *qi[4], *xc[3];
   double *phi0, *lphi, *p0;
+  /* RK3 cycle: the level set at the two sub-step boundaries around fluid
+   * 1's third-stage time and at the end of the cycle */
+  double *phia, *phib, *phie;
   unsigned char *band, *rext;
   /* per fluid: 1 where a small cell's content is not a physical state
    * (set by prim for the current stage) */
@@ -1179,6 +1182,8 @@ static void interpolate(orc_ctx *o, double th) {
       }
 }
 
+static void cycle_rk3(orc_ctx *o, int f1, double dt1, double dt2, orc_info *info);
+
 /* one cycle of the accelerated method (Sec. 3.1, steps 1-5) */
 static void cycle(orc_ctx *o, double t_end, orc_info *info) {
   eval(o, o->q, o->phi);
@@ -1214,6 +1219,10 @@ static void cycle(orc_ctx *o, double t_end, orc_info *info) {
   if (info) {
     info->dt1 = dt1;
     info->n_used = dt1 / dt2;
+  }
+  if (o->c.rk_order == 3) {
+    cycle_rk3(o, f1, dt1, dt2, info);
+    return;
   }
   for (int m = 0; m < 3; m++) memset(o->xc[m], 0, sizeof(double) * o->NP);
   /* step 2: fluid-1 first RK stage with dt1; keep previous and future */
@@ -1298,13 +1307,195 @@ static void cycle(orc_ctx *o, double t_end, orc_info *info) {
   }
 }
 
+/* Eq. 8-9 with the weight b of the evaluation's Runge-Kutta stage: a
+ * fluid-2 evaluation adds b dt2 X_1; one that fluid 1 uses too (shared)
+ * also removes b dt1 X_1; a fluid-1-only evaluation (dt2 = 0, shared)
+ * only removes b dt1 X_1. */
+static void record_b(orc_ctx *o, int f1, int shared, double b, double dt1, double dt2) {
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      for (int m = 0; m < 3; m++) {
+        double x1 = (f1 == 0 ? o->xn : o->xp)[m][c];
+        if (shared) o->xc[m][c] = o->xc[m][c] + (-b * x1) * dt1;
+        if (dt2 > 0.0) o->xc[m][c] = o->xc[m][c] + (b * x1) * dt2;
+      }
+    }
+}
+
+/* linear interpolation in time between two snapshots a (weight 1 - th)
+ * and b (weight th); where they agree the value is kept as it is */
+static void interp2(const orc_ctx *o, double *dst, const double *a, const double *b, double th) {
+  for (int j = 0; j < o->c.ny; j++)
+    for (int i = 0; i < o->c.nx; i++) {
+      int c = ID(o, i, j);
+      dst[c] = a[c] == b[c] ? a[c] : (1.0 - th) * a[c] + th * b[c];
+    }
+}
+
+/* One accelerated cycle with SSP-RK3 (stage weights b = 1/6, 1/6, 2/3 at
+ * the stage times t^n, t^n + dt, t^n + dt/2): the generalisation of Sec.
+ * 3.1 steps 1-5, whose scheme is written for RK2.  Fluid 1 (the larger
+ * step dt1) takes its first stage at t^n, sharing the cycle's first
+ * interaction step with fluid 2's first sub-step; fluid 2 sub-cycles with
+ * dt2, every one of its stage evaluations seeing fluid 1 by Eq. 7 between
+ * its states at t^n and after its first stage; fluid 1's second stage
+ * shares the last sub-step's second evaluation (both at t1 = t^n + dt1);
+ * fluid 1's third stage is evaluated at t^n + dt1/2 on the level set
+ * interpolated linearly between the two sub-step boundaries around that
+ * time (with a single sub-step, dt1 = dt2, it shares fluid 2's third
+ * evaluation instead, which makes that cycle the single-step method).  The
+ * correction quantities collect b dt2 X_1 of every fluid-2 evaluation and
+ * -b dt1 X_1 of every fluid-1 one (Eq. 8-9 with RK3's weights) and are
+ * applied to fluid 1 at the end, before its mixing.  That removes the
+ * exchange flux of fluid 1's own third evaluation from its result exactly
+ * (it enters only that last update), so fluid 2 takes part in it with its
+ * state at t1: its state at t^n + dt1/2 would not change the result. */
+static void cycle_rk3(orc_ctx *o, int f1, double dt1, double dt2, orc_info *info) {
+  const int f2 = 1 - f1;
+  const double b12 = 1.0 / 6.0, b3 = 2.0 / 3.0;
+  const double th = 0.5 * dt1;  /* fluid 1's third-stage time, from t^n */
+  for (int m = 0; m < 3; m++) memset(o->xc[m], 0, sizeof(double) * o->NP);
+  /* fluid-1 first stage with dt1; previous and future states */
+  fv_rhs(o, f1, o->L[f1]);
+  copy_planes(o, o->prev, o->q[f1], 4);
+  for (int m = 0; m < 4; m++)
+    rk_plane(o, 1, o->fut[m], o->prev[m], o->prev[m], o->L[f1][m], dt1, NULL);
+  double t2 = 0.0, ta = 0.0, tb = 0.0;
+  int sub = 0, have_a = 0, have_b = 0;
+  double *qs[2][4];
+  for (;;) {
+    sub++;
+    if (sub > 1) {
+      interpolate(o, t2 / dt1);
+      geometry(o, o->phi);
+      mix(o, f1, o->qi);
+      for (int m = 0; m < 4; m++) {
+        qs[f1][m] = o->qi[m];
+        qs[f2][m] = o->q[f2][m];
+      }
+      eval(o, qs, o->phi);
+      dt2 = dt_of(o, f2);
+    }
+    int last = (dt1 - t2) <= dt2 * (1.0 + 1e-12);
+    if (last) dt2 = dt1 - t2;
+    const int single = sub == 1 && last;  /* dt1 = dt2: all shared */
+    record_b(o, f1, sub == 1, b12, dt1, dt2);
+    /* the sub-step that reaches fluid 1's third-stage time starts here */
+    if (!have_a && (th < t2 + dt2 || last)) {
+      memcpy(o->phia, o->phi, sizeof(double) * o->NP);
+      ta = t2;
+      have_a = 1;
+    }
+    /* stage 1 of fluid 2 and the level set */
+    copy_planes(o, o->q0[f2], o->q[f2], 4);
+    memcpy(o->phi0, o->phi, sizeof(double) * o->NP);
+    make_band(o, o->phi0);
+    fv_rhs(o, f2, o->L[f2]);
+    ls_rhs(o, o->phi, o->lphi);
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 1, o->q[f2][m], o->q0[f2][m], o->q[f2][m], o->L[f2][m], dt2, NULL);
+    rk_plane(o, 1, o->phi, o->phi0, o->phi, o->lphi, dt2, o->band);
+    geometry(o, o->phi);
+    mix(o, f2, o->q[f2]);
+    /* stage 2 at t2 + dt2: fluid 1 by Eq. 7, at t1 its future state */
+    if (last) {
+      mix(o, f1, o->fut);
+      for (int m = 0; m < 4; m++) qs[f1][m] = o->fut[m];
+    } else {
+      interpolate(o, (t2 + dt2) / dt1);
+      mix(o, f1, o->qi);
+      for (int m = 0; m < 4; m++) qs[f1][m] = o->qi[m];
+    }
+    for (int m = 0; m < 4; m++) qs[f2][m] = o->q[f2][m];
+    eval(o, qs, o->phi);
+    record_b(o, f1, last, b12, dt1, dt2);
+    fv_rhs(o, f2, o->L[f2]);
+    ls_rhs(o, o->phi, o->lphi);
+    if (last) fv_rhs(o, f1, o->L[f1]);
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 2, o->q[f2][m], o->q0[f2][m], o->q[f2][m], o->L[f2][m], dt2, NULL);
+    rk_plane(o, 2, o->phi, o->phi0, o->phi, o->lphi, dt2, o->band);
+    if (last)
+      for (int m = 0; m < 4; m++)
+        rk_plane(o, 2, o->q[f1][m], o->prev[m], o->fut[m], o->L[f1][m], dt1, NULL);
+    geometry(o, o->phi);
+    mix(o, f2, o->q[f2]);
+    /* (with more sub-steps fluid 1's second-stage state is mixed with the
+     * geometry of its third stage, after the loop) */
+    if (single) mix(o, f1, o->q[f1]);
+    /* stage 3 at t2 + dt2/2: fluid 1 by Eq. 7 (with one sub-step its own
+     * second-stage state, the evaluation being shared) */
+    if (single) {
+      for (int m = 0; m < 4; m++) qs[f1][m] = o->q[f1][m];
+    } else {
+      interpolate(o, (t2 + 0.5 * dt2) / dt1);
+      mix(o, f1, o->qi);
+      for (int m = 0; m < 4; m++) qs[f1][m] = o->qi[m];
+    }
+    for (int m = 0; m < 4; m++) qs[f2][m] = o->q[f2][m];
+    eval(o, qs, o->phi);
+    record_b(o, f1, single, b3, dt1, dt2);
+    fv_rhs(o, f2, o->L[f2]);
+    ls_rhs(o, o->phi, o->lphi);
+    if (single) fv_rhs(o, f1, o->L[f1]);
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 3, o->q[f2][m], o->q0[f2][m], o->q[f2][m], o->L[f2][m], dt2, NULL);
+    rk_plane(o, 3, o->phi, o->phi0, o->phi, o->lphi, dt2, o->band);
+    if (single)
+      for (int m = 0; m < 4; m++)
+        rk_plane(o, 3, o->q[f1][m], o->prev[m], o->q[f1][m], o->L[f1][m], dt1, NULL);
+    reinit(o, o->phi);
+    geometry(o, o->phi);
+    mix(o, f2, o->q[f2]);
+    /* the sub-step that reached fluid 1's third-stage time ends here */
+    if (have_a && !have_b) {
+      memcpy(o->phib, o->phi, sizeof(double) * o->NP);
+      tb = t2 + dt2;
+      have_b = 1;
+    }
+    if (last) break;
+    t2 += dt2;
+  }
+  if (sub > 1) {
+    /* fluid 1's third stage at t^n + dt1/2 on the level set interpolated
+     * between the bracketing sub-step boundaries (a fluid-1-only
+     * evaluation; fluid 1's second-stage state is mixed with its geometry) */
+    double w = (th - ta) / (tb - ta);
+    memcpy(o->phie, o->phi, sizeof(double) * o->NP);
+    interp2(o, o->phi, o->phia, o->phib, w);
+    geometry(o, o->phi);
+    mix(o, f1, o->q[f1]);
+    for (int m = 0; m < 4; m++) {
+      qs[f1][m] = o->q[f1][m];
+      qs[f2][m] = o->q[f2][m];
+    }
+    eval(o, qs, o->phi);
+    record_b(o, f1, 1, b3, dt1, 0.0);
+    fv_rhs(o, f1, o->L[f1]);
+    for (int m = 0; m < 4; m++)
+      rk_plane(o, 3, o->q[f1][m], o->prev[m], o->q[f1][m], o->L[f1][m], dt1, NULL);
+    memcpy(o->phi, o->phie, sizeof(double) * o->NP);
+    geometry(o, o->phi);
+  }
+  if (o->c.flux_correction) {
+    double dxdy = o->c.dx * o->c.dy;
+    for (int j = 0; j < o->c.ny; j++)
+      for (int i = 0; i < o->c.nx; i++) {
+        int c = ID(o, i, j);
+        for (int m = 0; m < 3; m++) o->q[f1][m + 1][c] += o->xc[m][c] / dxdy;
+      }
+  }
+  mix(o, f1, o->q[f1]);
+  o->t += dt1;
+  if (info) {
+    info->substeps = sub;
+    info->t = o->t;
+  }
+}
+
 int orc_step_multi_dt(orc_ctx *o, int ncycles, double t_end, orc_info *info) {
   long long open0 = o->open_updates;
-  if (o->c.rk_order != 2) {
-    o->err |= ORC_ERR_INVAL;
-    if (info) info->err = o->err;
-    return o->err;
-  }
   for (int n = 0; n < ncycles; n++) {
     if (t_end > 0.0 && o->t >= t_end) break;
     cycle(o, t_end, info);
@@ -1351,6 +1542,9 @@ orc_ctx *orc_create(const orc_config *cfg) {
     o->fut[m] = plane(o);
     o->qi[m] = plane(o);
   }
+  o->phia = plane(o);
+  o->phib = plane(o);
+  o->phie = plane(o);
   for (int m = 0; m < 3; m++) {
     o->xn[m] = plane(o);
     o->xp[m] = plane(o);
@@ -1391,6 +1585,9 @@ void orc_destroy(orc_ctx *o) {
     free(o->fut[m]);
     free(o->qi[m]);
   }
+  free(o->phia);
+  free(o->phib);
+  free(o->phie);
   for (int m = 0; m < 3; m++) {
     free(o->xn[m]);
     free(o->xp[m]);

@@ -35,7 +35,7 @@ typedef struct {
   double gamma[2];    /* stiffened gas: [0] fluid N (phi < 0), [1] fluid P */
   double pinf[2];
   double cfl;         /* 0.6 */
-  int rk_order;       /* 2 (paper) or 3 (single-dt only) */
+  int rk_order;       /* 2 (paper) or 3 (SSP-RK3; its multi-dt cycle is cycle_rk3) */
   double weno_eps;    /* 1e-6 */
   double mix_alpha;   /* small-cell threshold, 0.5 */
   double ratio_threshold; /* n truncation threshold, 0.7 */
