@@ -1333,6 +1333,23 @@ static void interp2(const orc_ctx *o, double *dst, const double *a, const double
     }
 }
 
+/* The evaluation of fluid 1's third RK3 stage inside a cycle: fluid 1's
+ * stencil states on the current geometry (recovered, extended) and its
+ * wave speeds, and no exchange flux -- the correction quantities would
+ * remove that evaluation's exchange from fluid 1's result exactly, so it
+ * is left out (fluid 1 ends with the exchange fluid 2 received, Eq. 8-9).
+ * Fluid 2's stencil states are extended on the same geometry from where
+ * they are, as warm start of the next interaction step. */
+static void eval_third(orc_ctx *o, int f1, double *p) {
+  prim(o, f1, o->q[f1]);
+  for (int k = 0; k < 2; k++) extend(o, k, p);
+  for (int k = 0; k < 2; k++) wave_maxima(o, k, p);
+  for (int m = 0; m < 3; m++) {
+    memset(o->xn[m], 0, sizeof(double) * o->NP);
+    memset(o->xp[m], 0, sizeof(double) * o->NP);
+  }
+}
+
 /* One accelerated cycle with SSP-RK3 (stage weights b = 1/6, 1/6, 2/3 at
  * the stage times t^n, t^n + dt, t^n + dt/2): the generalisation of Sec.
  * 3.1 steps 1-5, whose scheme is written for RK2.  Fluid 1 (the larger
@@ -1347,10 +1364,10 @@ static void interp2(const orc_ctx *o, double *dst, const double *a, const double
  * evaluation instead, which makes that cycle the single-step method).  The
  * correction quantities collect b dt2 X_1 of every fluid-2 evaluation and
  * -b dt1 X_1 of every fluid-1 one (Eq. 8-9 with RK3's weights) and are
- * applied to fluid 1 at the end, before its mixing.  That removes the
- * exchange flux of fluid 1's own third evaluation from its result exactly
- * (it enters only that last update), so fluid 2 takes part in it with its
- * state at t1: its state at t^n + dt1/2 would not change the result. */
+ * applied to fluid 1 at the end, before its mixing.  That would remove
+ * the exchange flux of fluid 1's own third evaluation from its result
+ * exactly (the flux enters only that last update), so that evaluation
+ * carries none (eval_third). */
 static void cycle_rk3(orc_ctx *o, int f1, double dt1, double dt2, orc_info *info) {
   const int f2 = 1 - f1;
   const double b12 = 1.0 / 6.0, b3 = 2.0 / 3.0;
@@ -1466,12 +1483,7 @@ static void cycle_rk3(orc_ctx *o, int f1, double dt1, double dt2, orc_info *info
     interp2(o, o->phi, o->phia, o->phib, w);
     geometry(o, o->phi);
     mix(o, f1, o->q[f1]);
-    for (int m = 0; m < 4; m++) {
-      qs[f1][m] = o->q[f1][m];
-      qs[f2][m] = o->q[f2][m];
-    }
-    eval(o, qs, o->phi);
-    record_b(o, f1, 1, b3, dt1, 0.0);
+    eval_third(o, f1, o->phi);
     fv_rhs(o, f1, o->L[f1]);
     for (int m = 0; m < 4; m++)
       rk_plane(o, 3, o->q[f1][m], o->prev[m], o->q[f1][m], o->L[f1][m], dt1, NULL);
