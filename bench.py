@@ -710,13 +710,13 @@ def run_ours(args):
 
 def inputs_tube():
     from paper_1905_03917_gb300 import inputs
-    return inputs.shock_tube_1d(400, rk_order=2)
+    return inputs.shock_tube_1d(400, rk_order=3)
 
 
 def multi_vs_single_tube(case, device, T):
-    """The 1D water/air tube (400 cells, TVD-RK2): the same protocol with
-    the run length set by T = 2e-4 s, the error also against the exact
-    solution."""
+    """The 1D water/air tube (400 cells, WENO5 + SSP-RK3, both methods): the
+    same protocol with the run length set by T = 2e-4 s, the error also
+    against the exact solution."""
     return multi_vs_single(case, device, ref_cfl=0.025, exact=tube_exact_error(T), T=T)
 
 

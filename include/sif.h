@@ -63,7 +63,8 @@ typedef struct {
   double gamma[2];       /* stiffened gas p = (gamma-1) rho e - gamma p_inf; [0] = N, [1] = P */
   double pinf[2];
   double cfl;            /* CFL number, 0.6 in the paper (Sec. 4) */
-  int rk_order;          /* 2 = TVD-RK2 (the paper, Sec. 3); 3 = SSP-RK3 (single-dt only) */
+  int rk_order;          /* 2 = TVD-RK2 (the paper, Sec. 3); 3 = SSP-RK3 (both methods; the
+                            adjoint calls require 2) */
   double weno_eps;       /* WENO5 epsilon, 1e-6; at least 1e-20 */
   double mix_alpha;      /* small-cell mixing threshold, 0.5 */
   double ratio_threshold;/* time-step-ratio truncation threshold, 0.7 (Sec. 3.1) */
@@ -132,10 +133,15 @@ int sif_init_fluids(sif_ctx *ctx, const double *phi, const double *prim_N,
 int sif_step_single_dt(sif_ctx *ctx, int nsteps, double t_end, sif_cycle_info *info);
 
 /* ncycles cycles of the accelerated method (Sec. 3.1 steps 1-5): the fluid
- * with the larger CFL step (fluid 1) takes one RK2 step of dt1 while the
+ * with the larger CFL step (fluid 1) takes one RK step of dt1 while the
  * other sub-cycles against Eq. 7 interpolated states, with the Eq. 8-9
- * correction applied to fluid 1 at the end of the cycle.  Requires
- * rk_order == 2 (SIF_EINVAL otherwise). */
+ * correction applied to fluid 1 at the end of the cycle.  With rk_order 3
+ * (SSP-RK3, the paper's scheme carried to three stages): fluid 1's second
+ * stage shares the last sub-step's evaluation at t1, its third stage is
+ * evaluated at t^n + dt1/2 on the level set interpolated between the two
+ * sub-step boundaries around that time, and the correction quantities
+ * take RK3's stage weights 1/6, 1/6, 2/3; that third evaluation carries no
+ * exchange flux, which the correction would remove from fluid 1 anyway. */
 int sif_step_multi_dt(sif_ctx *ctx, int ncycles, double t_end, sif_cycle_info *info);
 
 /* out[k*4+m] = sum over cells of (alpha U)_{k,m} dx dy (k = N, P; m = mass,

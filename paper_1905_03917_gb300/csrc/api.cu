@@ -24,6 +24,7 @@ struct sif_ctx {
   // negated (equal to xn without surface tension and viscosity)
   double *q[2][4], *w[2][4], *phi, *alpha, *ax, *ay, *sx, *sy, *xn[3], *xm[3], *ul[2];
   double *q0[2][4], *prev[4], *fut[4], *qi[4], *xc[3], *phi0, *phiR;
+  double *phia, *phib, *phie;  // RK3 cycle: kept level sets (see graph_cycle_body3)
   double *tmp;       // band-indexed scratch, 8 planes
   int *bandmap;      // cell -> position in the interaction band, -1 outside
   ExtPlan *ext_plan; // 3 x ncell
@@ -268,6 +269,9 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     for (int m = 0; m < 3; m++) c->xc[m] = plane();
     c->phi0 = plane();
     c->phiR = plane();
+    c->phia = plane();
+    c->phib = plane();
+    c->phie = plane();
     c->tmp = (double *)take(sizeof(double) * 16 * ncell);
     c->bandmap = (int *)take(sizeof(int) * c->NP);
     c->ext_plan = (ExtPlan *)take(sizeof(ExtPlan) * 3 * ncell);
@@ -522,6 +526,32 @@ static void ul_extend(sif_ctx *c) {
   dbg(c, "ls_extend");
 }
 
+// evaluation of fluid 1's third stage in an RK3 cycle (at t^n + dt1/2, the
+// level set interpolated there): fluid 1's stencil states recovered and
+// extended on the current geometry with its wave speeds, no exchange flux
+// (the correction quantities would remove that evaluation's exchange from
+// fluid 1 exactly); fluid 2's stencil states are re-extended where they are
+static void eval_third(sif_ctx *c, int f1) {
+  side_join(c);
+  launch_sched(SCHED_RESET_MAX, c->sc, 0, 0, 0, c->st);
+  launch_prim2(c->g, c->q[0], c->q[1], c->w[0], c->w[1], c->alpha, c->tiles[0], c->tiles[1],
+               ntile(c), c->nostate, c->sc, -1, nullptr, c->band_ev, &c->sc->n_band, c->st,
+               1 - f1);
+  const bool first = c->g.ext_iters >= 1;
+  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
+                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st, c->w[0], c->w[1],
+                   first ? c->tmp : nullptr);
+  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
+                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
+                    c->sc, c->st, first ? 1 : 0);
+  launch_zero_cut(c->g, c->xn, c->xm, c->cut, &c->sc->n_cut, band_work(c), c->st);
+  dbg(c, "third-stage evaluation");
+}
+
+static void d2d_plane(sif_ctx *c, double *dst, const double *src) {
+  cudaMemcpyAsync(dst, src, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
+}
+
 static void copy_planes(sif_ctx *c, double *const dst[4], double *const src[4], int n) {
   for (int m = 0; m < n; m++)
     cudaMemcpyAsync(dst[m], src[m], sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
@@ -698,6 +728,106 @@ static int read_scalars(sif_ctx *c) {
   return SIF_OK;
 }
 
+static void third_stage(sif_ctx *c, int f1);
+
+// one RK3 cycle with fluid 1 = f1 issued from the host: the kernels of
+// graph_substep3 / graph_cycle_body3 in the same order, the branches
+// taken on the host after reading the scheduler's decisions
+static int cycle3(sif_ctx *c, int f1, sif_cycle_info *info) {
+  const int f2 = 1 - f1;
+  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  const double b12 = 1.0 / 6.0, b3 = 2.0 / 3.0;
+  for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
+  copy_planes(c, c->prev, c->q[f1], 4);
+  copy_planes(c, c->fut, c->q[f1], 4);
+  fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
+  double *qs[2][4];
+  for (int m = 0; m < 4; m++) {
+    qs[f1][m] = c->qi[m];
+    qs[f2][m] = c->q[f2][m];
+  }
+  int sub = 0;
+  for (;;) {
+    sub++;
+    if (sub > 1) {
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                    band_work(c), c->st);
+      mix_one(c, f1, c->qi);
+      eval(c, qs, f1);
+      launch_sched(SCHED_SUBSTEP, c->sc, cfl, thr, 0, c->st);
+    } else {
+      launch_sched(SCHED_FIRST_SUB, c->sc, cfl, thr, 0, c->st);
+    }
+    int rc = read_scalars(c);
+    if (rc) return rc;
+    if (c->hsc->err || !(c->hsc->dt2 > 0.0) || !(c->hsc->dt2 < 1e300)) {
+      if (!c->hsc->err) set_err(c, "fluid-2 time step is not positive and finite");
+      return c->hsc->err ? SIF_OK : SIF_ENONPHYS;
+    }
+    const int last = c->hsc->last, single = c->hsc->single;
+    launch_record(c->g, sub == 1, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1],
+                  c->xc[2], c->sc, c->st, b12, 1);
+    launch_copy_if(&c->sc->snap_a, c->phi, c->phia, c->NP, c->st);
+    copy_planes(c, c->q0[f2], c->q[f2], 4);
+    ls_begin(c);
+    ul_extend(c);
+    fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+    ls_stage(c, 1, &c->sc->dt2);
+    geometry(c, true);
+    if (last) {
+      mix_pair(c, f1, c->fut, c->q[f2]);
+      copy_planes(c, c->qi, c->fut, 4);
+    } else {
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                    band_work(c), c->st);
+      mix_pair(c, f1, c->qi, c->q[f2]);
+    }
+    eval(c, qs, last ? -1 : f1);
+    ul_extend(c);
+    launch_record(c->g, last, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2],
+                  c->sc, c->st, b12, 1);
+    fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+    ls_stage(c, 2, &c->sc->dt2);
+    if (last) fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1);
+    geometry(c, true);
+    if (single) {
+      mix_pair(c, f1, c->q[f1], c->q[f2]);
+      copy_planes(c, c->qi, c->q[f1], 4);
+    } else {
+      mix_one(c, f2, c->q[f2]);
+      launch_sched(SCHED_THETA3, c->sc, 0, 0, 0, c->st);
+      launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                    band_work(c), c->st);
+      mix_one(c, f1, c->qi);
+    }
+    eval(c, qs, single ? -1 : f1);
+    ul_extend(c);
+    launch_record(c->g, single, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2],
+                  c->sc, c->st, b3, 1);
+    fv(c, f2, 3, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+    ls_stage(c, 3, &c->sc->dt2);
+    if (single) fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1);
+    reinit(c);
+    geometry(c, true);
+    mix_one(c, f2, c->q[f2]);
+    launch_sched(SCHED_SNAPB, c->sc, 0, 0, 0, c->st);
+    launch_copy_if(&c->sc->snap_b, c->phi, c->phib, c->NP, c->st);
+    if (last) break;
+    launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st);
+    if (sub >= c->max_substeps) {
+      set_err(c, "the cycle needed more than %d fluid-2 sub-steps (state undefined)",
+              c->max_substeps);
+      return SIF_ETIMEOUT;
+    }
+  }
+  if (sub > 1) third_stage(c, f1);
+  if (c->cfg.flux_correction) launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
+  mix_one(c, f1, c->q[f1]);
+  launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
+  if (info) info->substeps = sub;
+  return SIF_OK;
+}
+
 // one cycle of the accelerated method (Sec. 3.1 steps 1-5)
 static int cycle(sif_ctx *c, sif_cycle_info *info) {
   const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
@@ -725,6 +855,7 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     info->dt2 = c->hsc->dt2;
     info->n_used = c->hsc->n_used;
   }
+  if (c->cfg.rk_order == 3) return cycle3(c, f1, info);
   for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
   // step 2: fluid-1 first RK stage with dt1; previous and future states
   copy_planes(c, c->prev, c->q[f1], 4);
@@ -895,7 +1026,7 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   cudaGraphConditionalHandle hl3 = new_handle(c);
   launch_cond(COND_LAST, c->sc, hl1, hn1, 0, 0, c->st);
   launch_cond(COND_LAST, c->sc, hl2, hn2, 0, 0, c->st);
-  launch_cond(COND_LAST, c->sc, hl3, 0, 0, 0, c->st);
+  launch_cond(COND_LAST_ONLY, c->sc, hl3, 0, 0, 0, c->st);
   launch_record(c->g, -1, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 3: fluid-2 and level-set first RK stage with dt2
@@ -951,6 +1082,130 @@ static void graph_cycle_body(sif_ctx *c, int f1) {
   launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
 }
 
+// one fluid-2 sub-step of an RK3 cycle (SSP-RK3: stage evaluations at t2,
+// t2 + dt2 and t2 + dt2/2, weights 1/6, 1/6, 2/3): fluid 1 by Eq. 7 at each
+// evaluation, except at t1 (its future state, the evaluation shared with
+// its second stage) and, when the cycle has a single sub-step, at the third
+// evaluation (its own second-stage state, shared with its third stage).
+// The level sets at the two sub-step boundaries around t^n + dt1/2 are
+// kept for fluid 1's third stage after the loop.
+static void graph_substep3(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) {
+  const int f2 = 1 - f1;
+  const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
+  const double b12 = 1.0 / 6.0, b3 = 2.0 / 3.0;
+  double *qs[2][4];
+  for (int m = 0; m < 4; m++) {
+    qs[f1][m] = c->qi[m];
+    qs[f2][m] = c->q[f2][m];
+  }
+  cudaGraphConditionalHandle hnf = new_handle(c);
+  launch_cond(COND_NOT_FIRST, c->sc, hnf, 0, 0, 0, c->st);
+  cond_node(c, hnf, false, [&] {
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
+    mix_one(c, f1, c->qi);
+    eval(c, qs, f1);
+    launch_sched(SCHED_DT2, c->sc, cfl, thr, 0, c->st);
+  });
+  launch_sched(SCHED_LAST, c->sc, cfl, thr, 0, c->st);
+  cudaGraphConditionalHandle hl1 = new_handle(c), hn1 = new_handle(c);
+  cudaGraphConditionalHandle hl2 = new_handle(c), hn3 = new_handle(c);
+  cudaGraphConditionalHandle hs1 = new_handle(c), hns1 = new_handle(c);
+  cudaGraphConditionalHandle hs2 = new_handle(c);
+  launch_cond(COND_LAST, c->sc, hl1, hn1, 0, 0, c->st);
+  launch_cond(COND_LAST, c->sc, hl2, hn3, 0, 0, c->st);
+  launch_cond(COND_SINGLE, c->sc, hs1, hns1, 0, 0, c->st);
+  launch_cond(COND_SINGLE_ONLY, c->sc, hs2, 0, 0, 0, c->st);
+  launch_record(c->g, -1, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2], c->sc,
+                c->st, b12, 1);
+  launch_copy_if(&c->sc->snap_a, c->phi, c->phia, c->NP, c->st);
+  // stage 1 of fluid 2 and the level set
+  copy4(c, c->q0[f2], c->q[f2]);
+  ls_begin(c);
+  ul_extend(c);
+  fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+  ls_stage(c, 1, &c->sc->dt2);
+  geometry(c, true);
+  // stage 2 at t2 + dt2 (at t1 on the last sub-step)
+  cond_node(c, hl1, false, [&] {
+    mix_pair(c, f1, c->fut, c->q[f2]);
+    copy4(c, c->qi, c->fut);
+  });
+  cond_node(c, hn1, false, [&] {
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
+    mix_pair(c, f1, c->qi, c->q[f2]);
+  });
+  eval(c, qs, f1, &c->sc->last);
+  ul_extend(c);
+  launch_record(c->g, -2, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2], c->sc,
+                c->st, b12, 1);
+  fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+  ls_stage(c, 2, &c->sc->dt2);
+  cond_node(c, hl2, false, [&] { fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1); });
+  geometry(c, true);
+  // stage 3 at t2 + dt2/2
+  cond_node(c, hs1, false, [&] {
+    mix_pair(c, f1, c->q[f1], c->q[f2]);
+    copy4(c, c->qi, c->q[f1]);
+  });
+  cond_node(c, hns1, false, [&] {
+    mix_one(c, f2, c->q[f2]);
+    launch_sched(SCHED_THETA3, c->sc, 0, 0, 0, c->st);
+    launch_interp(c->g, c->qi, c->prev, c->fut, &c->sc->theta, c->band_ev, &c->sc->n_band,
+                  band_work(c), c->st);
+    mix_one(c, f1, c->qi);
+  });
+  eval(c, qs, f1, &c->sc->single);
+  ul_extend(c);
+  launch_record(c->g, -3, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2], c->sc,
+                c->st, b3, 1);
+  fv(c, f2, 3, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
+  ls_stage(c, 3, &c->sc->dt2);
+  cond_node(c, hs2, false, [&] { fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1); });
+  reinit(c);
+  geometry(c, true);
+  mix_one(c, f2, c->q[f2]);
+  launch_sched(SCHED_SNAPB, c->sc, 0, 0, 0, c->st);
+  launch_copy_if(&c->sc->snap_b, c->phi, c->phib, c->NP, c->st);
+  cond_node(c, hn3, false, [&] { launch_sched(SCHED_ADVANCE, c->sc, cfl, thr, 0, c->st); });
+  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, c->max_substeps, c->st);
+}
+
+// fluid 1's third RK3 stage at t^n + dt1/2 on the level set interpolated
+// between the kept ones (a fluid-1-only evaluation, see eval_third); the
+// level set of the cycle's end is restored afterwards
+static void third_stage(sif_ctx *c, int f1) {
+  d2d_plane(c, c->phie, c->phi);
+  launch_sched(SCHED_W3, c->sc, 0, 0, 0, c->st);
+  launch_phi_interp(c->g, c->phi, c->phia, c->phib, &c->sc->theta, c->st);
+  ghost_phi(c);
+  geometry(c, true);
+  mix_one(c, f1, c->q[f1]);
+  eval_third(c, f1);
+  fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1);
+  d2d_plane(c, c->phi, c->phie);
+  geometry(c, true);
+}
+
+static void graph_cycle_body3(sif_ctx *c, int f1) {
+  for (int m = 0; m < 3; m++) cudaMemsetAsync(c->xc[m], 0, sizeof(double) * c->NP, c->st);
+  copy4(c, c->prev, c->q[f1]);
+  copy4(c, c->fut, c->q[f1]);
+  fv(c, f1, 1, c->fut, c->prev, c->prev, &c->sc->dt1);
+  cudaGraphConditionalHandle hloop = new_handle(c);
+  launch_cond(COND_LOOP, c->sc, hloop, 0, 0, c->max_substeps, c->st);
+  cond_node(c, hloop, true, [&] { graph_substep3(c, f1, hloop); });
+  // more than one sub-step: fluid 1's third stage after the loop
+  cudaGraphConditionalHandle hs = new_handle(c), hns = new_handle(c);
+  launch_cond(COND_SINGLE, c->sc, hs, hns, 0, 0, c->st);
+  cond_node(c, hns, false, [&] { third_stage(c, f1); });
+  if (c->cfg.flux_correction)
+    launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
+  mix_one(c, f1, c->q[f1]);
+  launch_sched(SCHED_T_CYCLE, c->sc, 0, 0, 0, c->st);
+}
+
 // one accelerated cycle, captured onto c->st (which must be capturing)
 static void capture_cycle(sif_ctx *c) {
   const double cfl = c->g.cfl, thr = c->cfg.ratio_threshold;
@@ -962,8 +1217,13 @@ static void capture_cycle(sif_ctx *c) {
     single_step_after_eval(c, &c->sc->dt);
     launch_sched(SCHED_T_SINGLE, c->sc, 0, 0, 0, c->st);
   });
-  cond_node(c, h0, false, [&] { graph_cycle_body(c, 0); });
-  cond_node(c, h1, false, [&] { graph_cycle_body(c, 1); });
+  if (c->cfg.rk_order == 3) {
+    cond_node(c, h0, false, [&] { graph_cycle_body3(c, 0); });
+    cond_node(c, h1, false, [&] { graph_cycle_body3(c, 1); });
+  } else {
+    cond_node(c, h0, false, [&] { graph_cycle_body(c, 0); });
+    cond_node(c, h1, false, [&] { graph_cycle_body(c, 1); });
+  }
 }
 
 static void free_graphs(sif_ctx *c) {
@@ -1035,10 +1295,6 @@ static int ensure_graphs(sif_ctx *c) {
 
 extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycle_info *info) {
   if (!c || ncycles < 0) return SIF_EINVAL;
-  if (c->cfg.rk_order != 2) {
-    set_err(c, "the multi-time-step cycle is defined for rk_order 2");
-    return SIF_EINVAL;
-  }
   if (c->tape_cap > 0) {
     set_err(c, "the adjoint tape records single-time-step steps only");
     return SIF_ESTATE;
@@ -1806,10 +2062,9 @@ extern "C" int sif_batch_step_multi_dt(sif_batch *b, int ncycles, long long *cel
   bool rebuild = !b->exec;
   for (int i = 0; i < b->n; i++) {
     sif_ctx *c = b->ctx[i];
-    if (!c->inited || c->cfg.rk_order != 2) {
-      snprintf(b->err, sizeof(b->err), "instance %d: %s", i,
-               c->inited ? "rk_order must be 2" : "not initialised");
-      return c->inited ? SIF_EINVAL : SIF_ESTATE;
+    if (!c->inited) {
+      snprintf(b->err, sizeof(b->err), "instance %d: not initialised", i);
+      return SIF_ESTATE;
     }
     int rc = begin_call(c, 0.0, &upd0[i]);
     if (rc == SIF_OK) rc = ensure_graphs(c);

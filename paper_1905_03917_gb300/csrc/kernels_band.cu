@@ -57,6 +57,7 @@ struct PrimArgs {
   const int *band_flag;
   const int *band;
   const int *nband;
+  int skip_fluid;  // fluid whose states are not recovered at all (-1: none)
 };
 
 // blockIdx.y = fluid; the cells of the fluid's tiles, or of the band
@@ -64,6 +65,7 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
                        Scalars *sc) {
   SIF_TICK();
   const int k = blockIdx.y;
+  if (k == P.skip_fluid) return;
   const bool band_only = k == P.band_fluid && !(P.band_flag && *P.band_flag);
   bool valid;
   int c = 0;
@@ -136,8 +138,9 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
                   double *const wP[4], const double *alpha, const int *tilesN,
                   const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
                   int band_fluid, const int *band_flag, const int *band, const int *nband,
-                  cudaStream_t st) {
+                  cudaStream_t st, int skip_fluid) {
   PrimArgs P;
+  P.skip_fluid = skip_fluid;
   P.band_fluid = band_fluid;
   P.band_flag = band_flag;
   P.band = band;
@@ -530,7 +533,8 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
 // X_1, the exchange flux as applied to fluid 1 (with fluid 1's own
 // interface pressure): fluid N's planes, or fluid P's negated planes
 // negated back, by the cycle's role
-__global__ void k_record(int shared, const int *__restrict__ cut, const int *ncut,
+__global__ void k_record(int shared, double bw, int fluid2, const int *__restrict__ cut,
+                         const int *ncut,
                          const double *__restrict__ n0, const double *__restrict__ n1,
                          const double *__restrict__ n2, const double *__restrict__ m0,
                          const double *__restrict__ m1, const double *__restrict__ m2,
@@ -543,6 +547,7 @@ __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncu
   double dt1 = sc->dt1, dt2 = sc->dt2;
   if (shared == -1) shared = sc->sub == 1;
   else if (shared == -2) shared = sc->last;
+  else if (shared == -3) shared = sc->sub == 1 && sc->last;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = cut[idx];
     const double *xs[3] = {x0, x1, x2};
@@ -552,8 +557,8 @@ __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncu
     for (int m = 0; m < 3; m++) {
       double xv = __dmul_rn(sgn, xs[m][c]);
       double acc = cs[m][c];
-      if (shared) acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(-0.5, xv), dt1));
-      acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(0.5, xv), dt2));
+      if (shared) acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(-bw, xv), dt1));
+      if (fluid2) acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(bw, xv), dt2));
       cs[m][c] = acc;
     }
   }
@@ -561,10 +566,10 @@ __global__ void k_record(int shared, const int *__restrict__ cut, const int *ncu
 
 void launch_record(const Grid &, int shared, const int *cut, int cut_cap, double *const xn[3],
                    double *const xm[3], double *xc0, double *xc1, double *xc2, Scalars *sc,
-                   cudaStream_t st) {
+                   cudaStream_t st, double bw, int fluid2) {
   int blocks = grid_for(cut_cap, 128, 1216);
-  k_record<<<blocks, 128, 0, st>>>(shared, cut, &sc->n_cut, xn[0], xn[1], xn[2], xm[0], xm[1],
-                                   xm[2], xc0, xc1, xc2, sc);
+  k_record<<<blocks, 128, 0, st>>>(shared, bw, fluid2, cut, &sc->n_cut, xn[0], xn[1], xn[2],
+                                   xm[0], xm[1], xm[2], xc0, xc1, xc2, sc);
   sif_note_launches(1);
 }
 
@@ -626,6 +631,62 @@ void launch_correction(const Grid &g, double *const q[4], const double *xc0, con
 }
 
 // ---------------------------------------------------------------------
+// RK3 cycle: the level set at fluid 1's third-stage time
+
+__global__ void k_copy_if(const int *flag, const double *__restrict__ src, double *dst,
+                          size_t n) {
+  SIF_TICK();
+  if (!*flag) return;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x)
+    dst[t] = src[t];
+}
+
+void launch_copy_if(const int *flag, const double *src, double *dst, size_t n, cudaStream_t st) {
+  k_copy_if<<<grid_for((int)((n + 3) / 4), 256, 152 * 8), 256, 0, st>>>(flag, src, dst, n);
+  sif_note_launches(1);
+}
+
+// linear interpolation in time between two kept level sets; a cell where
+// they agree keeps its value as it is
+__global__ void k_phi_interp(Grid g, double *phi, const double *__restrict__ a,
+                             const double *__restrict__ b, const double *thp) {
+  SIF_TICK();
+  const double th = *thp;
+  int n = g.nx * g.ny;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int c = gidx(g, t % g.nx, t / g.nx);
+    double va = a[c], vb = b[c];
+    phi[c] = va == vb ? va : (1.0 - th) * va + th * vb;
+  }
+}
+
+void launch_phi_interp(const Grid &g, double *phi, const double *a, const double *b,
+                       const double *thp, cudaStream_t st) {
+  int n = g.nx * g.ny;
+  k_phi_interp<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(g, phi, a, b, thp);
+  sif_note_launches(1);
+}
+
+__global__ void k_zero_cut(const int *__restrict__ cut, const int *ncut, double *a0, double *a1,
+                           double *a2, double *b0, double *b1, double *b2) {
+  SIF_TICK();
+  int n = *ncut;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int c = cut[t];
+    a0[c] = a1[c] = a2[c] = 0.0;
+    b0[c] = b1[c] = b2[c] = 0.0;
+  }
+}
+
+void launch_zero_cut(const Grid &, double *const xn[3], double *const xm[3], const int *cut,
+                     const int *ncut, int cut_cap, cudaStream_t st) {
+  k_zero_cut<<<grid_for(cut_cap, 128, 1216), 128, 0, st>>>(cut, ncut, xn[0], xn[1], xn[2], xm[0],
+                                                          xm[1], xm[2]);
+  sif_note_launches(1);
+}
+
+// ---------------------------------------------------------------------
 // conserved totals: fixed-order per-row partial sums, then a fixed-order
 // sum of the partials (deterministic)
 
@@ -668,6 +729,18 @@ void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], d
 
 // ---------------------------------------------------------------------
 // device-side scheduler of the single- and multi-time-step methods
+
+// after a sub-step's length is known: does it reach fluid 1's third-stage
+// time (t^n + dt1/2) of an RK3 cycle?  Then its level set at the start is
+// kept.  Also whether the cycle has a single sub-step.
+__device__ void sched_snap_a(Scalars *sc) {
+  sc->single = sc->sub == 1 && sc->last;
+  sc->snap_a = !sc->have_a && (0.5 * sc->dt1 < sc->t2 + sc->dt2 || sc->last);
+  if (sc->snap_a) {
+    sc->have_a = 1;
+    sc->ta = sc->t2;
+  }
+}
 
 __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1) {
   SIF_TICK();
@@ -719,6 +792,9 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
       sc->t2 = 0.0;
       sc->sub = 0;
       sc->last = 0;
+      sc->single = 0;
+      sc->have_a = sc->have_b = sc->snap_a = sc->snap_b = 0;
+      sc->ta = sc->tb = 0.0;
       sc->dt2_first = sc->dt2;
       break;
     }
@@ -733,6 +809,7 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
       sc->dt2 = dt2;
       sc->last = last;
       sc->theta = last ? 1.0 : (t2 + dt2) / dt1;
+      sched_snap_a(sc);
       break;
     }
     case SCHED_ADVANCE:
@@ -750,8 +827,23 @@ __global__ void k_sched(int op, Scalars *sc, double cfl, double thr, int force1)
       sc->dt2 = dt2;
       sc->last = last;
       sc->theta = last ? 1.0 : (t2 + dt2) / dt1;
+      sched_snap_a(sc);
       break;
     }
+    case SCHED_THETA3:
+      sc->theta = (sc->t2 + 0.5 * sc->dt2) / sc->dt1;
+      break;
+    case SCHED_SNAPB:
+      // the sub-step that reached fluid 1's third-stage time ends here
+      sc->snap_b = sc->have_a && !sc->have_b;
+      if (sc->snap_b) {
+        sc->have_b = 1;
+        sc->tb = sc->t2 + sc->dt2;
+      }
+      break;
+    case SCHED_W3:
+      sc->theta = (0.5 * sc->dt1 - sc->ta) / (sc->tb - sc->ta);
+      break;
     case SCHED_T_SINGLE:
       sc->t = sc->t + sc->dt;
       break;
@@ -778,6 +870,16 @@ __global__ void k_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0,
     case COND_LAST:
       cudaGraphSetConditional(h0, sc->last ? 1u : 0u);
       cudaGraphSetConditional(h1, sc->last ? 0u : 1u);
+      break;
+    case COND_SINGLE:
+      cudaGraphSetConditional(h0, sc->single ? 1u : 0u);
+      cudaGraphSetConditional(h1, sc->single ? 0u : 1u);
+      break;
+    case COND_LAST_ONLY:
+      cudaGraphSetConditional(h0, sc->last ? 1u : 0u);
+      break;
+    case COND_SINGLE_ONLY:
+      cudaGraphSetConditional(h0, sc->single ? 1u : 0u);
       break;
     case COND_LOOP: {
       // stop after the last sub-step, on a device error, or when the

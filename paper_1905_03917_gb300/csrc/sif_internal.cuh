@@ -60,6 +60,10 @@ struct Scalars {
   double dt2_first;             // fluid-2 step chosen at the start of the cycle
   unsigned long long updates;   // (cell, fluid) stage updates issued (active-tile cells)
   unsigned long long open_updates;  // of those, cells with an open face of the fluid
+  // RK3 cycle: the sub-step boundaries around fluid 1's third-stage time
+  // (t^n + dt1/2) whose level sets are kept, and the copy decisions
+  double ta, tb;
+  int have_a, have_b, snap_a, snap_b, single, pad_;  // (pad_ keeps the timer block aligned)
   // finite-volume launch timing on the GPU's global timer (graph-safe):
   // each launch keeps its earliest block start and latest block end, the
   // last block to finish adds the span to fv_ns
@@ -405,7 +409,7 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
                   double *const wP[4], const double *alpha, const int *tilesN,
                   const int *tilesP, int tile_cap, unsigned char *const nostate[2], Scalars *sc,
                   int band_fluid, const int *band_flag, const int *band, const int *nband,
-                  cudaStream_t st);
+                  cudaStream_t st, int skip_fluid = -1);
 // viscous part of a finite-volume stage of fluid k (mu[k] > 0): dst +=
 // b dt div(A Fv) over the cells of fluid k's active tiles
 void launch_viscous(const Grid &g, int k, int s, int rk, double *const dst[4],
@@ -427,11 +431,21 @@ void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *ph
                      int band_cap, double *tmp, const double *dtp, cudaStream_t st);
 void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, const int *nrext,
                    int rext_cap, double *tmp, cudaStream_t st);
-// shared: 1 = Eq. 8, 0 = Eq. 9, -1 = Eq. 8 on the first sub-step (device
-// decides), -2 = Eq. 8 on the last sub-step (device decides)
+// Eq. 8-9 with the RK stage weight bw: shared (fluid 1 used the
+// evaluation: -bw dt1 X_1) is 1 or 0, or decided on the device: -1 on the
+// first sub-step, -2 on the last, -3 when the cycle has one sub-step;
+// fluid2 (fluid 2 used it: +bw dt2 X_1)
 void launch_record(const Grid &g, int shared, const int *cut, int cut_cap, double *const xn[3],
                    double *const xm[3], double *xc0, double *xc1, double *xc2, Scalars *sc,
-                   cudaStream_t st);
+                   cudaStream_t st, double bw = 0.5, int fluid2 = 1);
+// a whole plane (ghosts included) copied when *flag is set
+void launch_copy_if(const int *flag, const double *src, double *dst, size_t n, cudaStream_t st);
+// phi = (1 - th) a + th b over the interior, a where a == b (th on the device)
+void launch_phi_interp(const Grid &g, double *phi, const double *a, const double *b,
+                       const double *thp, cudaStream_t st);
+// zero the exchange flux planes of both fluids in the cells of the cut list
+void launch_zero_cut(const Grid &g, double *const xn[3], double *const xm[3], const int *cut,
+                     const int *ncut, int cut_cap, cudaStream_t st);
 // Eq. 7 interpolation of fluid 1 at theta over the cells of a band list
 void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
                    double *const fut[4], const double *thp, const int *band, const int *nband,
@@ -486,11 +500,19 @@ unsigned long long sif_launches_adj();
 #define SCHED_T_CYCLE 7     // t += dt1
 #define SCHED_DT2 8         // fluid-2 dt from the latest interaction
 #define SCHED_LAST 9        // count the sub-step, last-substep test, theta
+#define SCHED_THETA3 10     // theta of the RK3 third stage, (t2 + dt2/2) / dt1
+#define SCHED_SNAPB 11      // keep the level set at the end of this sub-step?
+#define SCHED_W3 12         // theta of fluid 1's third stage between the kept level sets
 
 // conditions of the device-driven cycle graph (cudaGraphSetConditional)
 #define COND_CYCLE 0        // h0 = single step, h1 = cycle with f1 = 0, h2 = cycle with f1 = 1
 #define COND_NOT_FIRST 1    // h0 = sub-step after the first
 #define COND_LAST 2         // h0 = last sub-step, h1 = not last
 #define COND_LOOP 3         // h0 = keep sub-cycling
+#define COND_SINGLE 4       // h0 = the cycle has a single sub-step, h1 = it has more
+// the same tests setting h0 only: every op sets exactly the handles it
+// names (a handle that was not created for this graph is never set)
+#define COND_LAST_ONLY 5    // h0 = last sub-step
+#define COND_SINGLE_ONLY 6  // h0 = a single sub-step
 void launch_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
                  cudaGraphConditionalHandle h2, int max_sub, cudaStream_t st);
