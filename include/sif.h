@@ -94,6 +94,16 @@ typedef struct {
                             traction on its interface boundary through S; the explicit
                             viscous limit 2 nu (1/dx^2 + 1/dy^2) joins the CFL rate.  The
                             adjoint calls require 0. */
+  int tait[2];           /* 1 = fluid k follows Tait's equation (Eq. 4, the weakly
+                            compressible model's closure, Sec. 2.2): p = tait_B ((rho /
+                            tait_rho0)^gamma - 1) + tait_p0, the pressure a function of
+                            the density alone (the energy component is carried but does
+                            not enter it); the interface Riemann problem takes such a
+                            side's shock from mass and momentum alone.  pinf[k] is then
+                            ignored: the sound speed is c^2 = gamma (p + tait_B - tait_p0)
+                            / rho.  0 = stiffened gas.  Requires weno_char 0; the adjoint
+                            calls require 0. */
+  double tait_B[2], tait_rho0[2], tait_p0[2];  /* > 0, > 0, finite */
 } sif_config;
 
 /* Per-cycle record of the multi-time-step schedule (Sec. 3.1). */

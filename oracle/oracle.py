@@ -47,7 +47,9 @@ class _Config(ctypes.Structure):
                 ("band", ctypes.c_double),
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double),
-                ("mu", ctypes.c_double * 2)]
+                ("mu", ctypes.c_double * 2), ("tait", ctypes.c_int * 2),
+                ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
+                ("tait_p0", ctypes.c_double * 2)]
 
 
 class _Info(ctypes.Structure):
@@ -92,6 +94,7 @@ def lib():
         L.orc_riemann.argtypes = [dp, dp, dp]
         L.orc_char_basis.argtypes = [D, D, D, D, D, D, I, dp, dp]
         L.orc_riemann_jump.argtypes = [dp, dp, D, dp]
+        L.orc_riemann_jump2.argtypes = [dp, dp, D, I, I, dp]
         L.orc_curvature.restype = D
         L.orc_curvature.argtypes = [P, I, I]
         L.orc_step_taped.argtypes = [P, dp, dp, dp, dp]
@@ -143,6 +146,11 @@ def make_config(cfg: dict) -> _Config:
     c.sigma = float(cfg.get("sigma", 0.0))
     mu = cfg.get("mu", (0.0, 0.0))
     c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
+    # Tait's equation per fluid: (B, rho0, p0) or None for a stiffened gas
+    for k, t in enumerate(cfg.get("tait", (None, None))):
+        if t is not None:
+            c.tait[k] = 1
+            c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
     return c
 
 
@@ -345,3 +353,14 @@ def riemann(left, right):
     rc = lib().orc_riemann(_ptr(L), _ptr(R), _ptr(out))
     return {"p": out[0], "u": out[1], "rho_L": out[2], "rho_R": out[3],
             "c_L": out[4], "c_R": out[5], "iters": int(out[6]), "rc": rc}
+
+
+def riemann_baro(left, right, baro_l, baro_r, jump=0.0):
+    """As riemann_jump() with either side barotropic (Tait's equation: the
+    shock branch from mass and momentum alone, the star density on the
+    fluid's curve p + pinf ~ rho^gamma)."""
+    L, R, out = _f64(left), _f64(right), np.empty(8)
+    rc = lib().orc_riemann_jump2(_ptr(L), _ptr(R), float(jump), int(baro_l), int(baro_r),
+                                 _ptr(out))
+    return {"p": out[0], "u": out[1], "rho_L": out[2], "rho_R": out[3],
+            "c_L": out[4], "c_R": out[5], "iters": int(out[6]), "p_L": out[7], "rc": rc}

@@ -384,7 +384,11 @@ static void prim(orc_ctx *o, int k, double *const q[4]) {
       double u = q[1][c] / q[0][c];
       double v = q[2][c] / q[0][c];
       double E = q[3][c] / a;
-      double p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - g * pi;
+      double p;
+      if (o->c.tait[k]) /* Tait's equation (Eq. 4): the density alone */
+        p = o->c.tait_B[k] * (pow(rho / o->c.tait_rho0[k], g) - 1.0) + o->c.tait_p0[k];
+      else
+        p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - g * pi;
       if (!(rho > 0.0) || !(p + pi > 0.0)) {
         if (a < 1.0) {
           o->nostate[k][c] = 1;
@@ -470,9 +474,19 @@ static void wave_maxima(orc_ctx *o, int k, const double *p) {
 /* interface interaction: exact two-material Riemann problem           */
 
 static void side_f(double p, double rho, double pk, double g, double pi,
-                   double ck, double *f, double *df) {
+                   double ck, int baro, double *f, double *df) {
   double P = pk + pi, Pp = p + pi;
-  if (p > pk) {
+  if (p > pk && baro) {
+    /* barotropic shock (Tait): u jump^2 = (p - pk)(1/rho - 1/rho*), rho* =
+     * rho r^(1/g), r = (p + pi)/(pk + pi); 1 - r^(-1/g) without
+     * cancellation for r near 1 */
+    double x = (p - pk) / P;
+    double a = -expm1(-log1p(x) / g);        /* 1 - r^(-1/g) */
+    double gsq = (p - pk) * a / rho;
+    double dg = (a + (p - pk) * pow(1.0 + x, -1.0 / g - 1.0) / (g * P)) / rho;
+    *f = sqrt(gsq);
+    *df = dg / (2.0 * *f);
+  } else if (p > pk) {
     double A = 2.0 / ((g + 1.0) * rho);
     double B = (g - 1.0) / (g + 1.0) * P;
     double qr = sqrt(A / (Pp + B));
@@ -485,9 +499,9 @@ static void side_f(double p, double rho, double pk, double g, double pi,
   }
 }
 
-static double star_density(double p, double rho, double pk, double g, double pi) {
+static double star_density(double p, double rho, double pk, double g, double pi, int baro) {
   double r = (p + pi) / (pk + pi);
-  if (p > pk) {
+  if (p > pk && !baro) {
     double qq = (g - 1.0) / (g + 1.0);
     return rho * (r + qq) / (qq * r + 1.0);
   }
@@ -497,23 +511,28 @@ static double star_density(double p, double rho, double pk, double g, double pi)
 /* The star state satisfies u*_L = u*_R with p*_L = p*_R + jump: Newton on
  * the right star pressure p for f_L(p + jump) + f_R(p) + u_R - u_L = 0,
  * from the acoustic guess, each side's p + p_inf floored. */
-int orc_riemann_jump(const double *L, const double *R, double jump, double *out) {
+int orc_riemann_jump2(const double *L, const double *R, double jump, int bl, int br,
+                      double *out) {
   double rl = L[0], ul = L[1], pl = L[2], gl = L[3], pil = L[4];
   double rr = R[0], ur = R[1], pr = R[2], gr = R[3], pir = R[4];
   double cl = sqrt(gl * (pl + pil) / rl), cr = sqrt(gr * (pr + pir) / rr);
   double pscale = dmin(pl + pil, pr + pir);
   double pfloor = dmax(-pir, -pil - jump) + 1e-12 * pscale;
   double p = 0.5 * ((pl - jump) + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
-  if (p < pfloor) p = pfloor;
+  /* iterates stay above the floor without landing on it (where a
+   * rarefaction's derivative diverges and a tiny step would pass for
+   * convergence): a guess below it starts halfway to the larger pressure,
+   * a step across it halves the distance to it instead */
+  if (p < pfloor) p = pfloor + 0.5 * (dmax(pl - jump, pr) - pfloor);
   int it = 0, conv = 0, done = 0;
   double fl, dfl, fr, dfr;
   while (it < 50) {
     it++;
-    side_f(p + jump, rl, pl, gl, pil, cl, &fl, &dfl);
-    side_f(p, rr, pr, gr, pir, cr, &fr, &dfr);
+    side_f(p + jump, rl, pl, gl, pil, cl, bl, &fl, &dfl);
+    side_f(p, rr, pr, gr, pir, cr, br, &fr, &dfr);
     double F = fl + fr + (ur - ul);
     double pn = p - F / (dfl + dfr);
-    if (pn < pfloor) pn = pfloor;
+    if (pn < pfloor) pn = pfloor + 0.5 * (p - pfloor);
     double dp = fabs(pn - p);
     p = pn;
     if (conv) {
@@ -523,11 +542,11 @@ int orc_riemann_jump(const double *L, const double *R, double jump, double *out)
     if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
   }
   double plst = p + jump;
-  side_f(plst, rl, pl, gl, pil, cl, &fl, &dfl);
-  side_f(p, rr, pr, gr, pir, cr, &fr, &dfr);
+  side_f(plst, rl, pl, gl, pil, cl, bl, &fl, &dfl);
+  side_f(p, rr, pr, gr, pir, cr, br, &fr, &dfr);
   double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
-  double rsl = star_density(plst, rl, pl, gl, pil);
-  double rsr = star_density(p, rr, pr, gr, pir);
+  double rsl = star_density(plst, rl, pl, gl, pil, bl);
+  double rsr = star_density(p, rr, pr, gr, pir, br);
   out[0] = p;
   out[1] = us;
   out[2] = rsl;
@@ -537,6 +556,10 @@ int orc_riemann_jump(const double *L, const double *R, double jump, double *out)
   out[6] = (double)it;
   out[7] = plst;
   return (done || conv) ? 0 : ORC_ERR_NOCONV;
+}
+
+int orc_riemann_jump(const double *L, const double *R, double jump, double *out) {
+  return orc_riemann_jump2(L, R, jump, 0, 0, out);
 }
 
 int orc_riemann(const double *L, const double *R, double *out) {
@@ -594,7 +617,8 @@ static void interface(orc_ctx *o, const double *p) {
                      o->w[1][3][c], o->c.gamma[1], o->c.pinf[1]};
       double out[8];
       double jump = o->c.sigma != 0.0 ? o->c.sigma * curvature(o, p, i, j) : 0.0;
-      if (orc_riemann_jump(L, R, jump, out)) o->err |= ORC_ERR_NOCONV;
+      if (orc_riemann_jump2(L, R, jump, o->c.tait[0], o->c.tait[1], out))
+        o->err |= ORC_ERR_NOCONV;
       double psN = out[7], psP = out[0], us = out[1];
       o->xn[0][c] = -psN * Sx;
       o->xn[1][c] = -psN * Sy;
@@ -1532,8 +1556,17 @@ orc_ctx *orc_create(const orc_config *cfg) {
   if (!(cfg->sigma >= 0.0) || !isfinite(cfg->sigma)) return NULL;
   for (int k = 0; k < 2; k++)
     if (!(cfg->mu[k] >= 0.0) || !isfinite(cfg->mu[k])) return NULL;
+  for (int k = 0; k < 2; k++) {
+    if (cfg->tait[k] != 0 && cfg->tait[k] != 1) return NULL;
+    if (cfg->tait[k] && (!(cfg->tait_B[k] > 0.0) || !(cfg->tait_rho0[k] > 0.0) ||
+                         !isfinite(cfg->tait_p0[k]) || !isfinite(cfg->tait_B[k])))
+      return NULL;
+  }
   orc_ctx *o = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   o->c = *cfg;
+  /* a Tait fluid's sound speed is the stiffened gas's with pinf = B - p0 */
+  for (int k = 0; k < 2; k++)
+    if (o->c.tait[k]) o->c.pinf[k] = o->c.tait_B[k] - o->c.tait_p0[k];
   if (o->c.dim == 1) o->c.bc[2] = o->c.bc[3] = ORC_BC_ZEROGRAD;
   o->PX = cfg->nx + 2 * GH;
   o->PY = cfg->ny + 2 * GH;

@@ -47,6 +47,12 @@ typedef struct {
   int weno_char;         /* 1 = WENO5 on characteristic fields, 0 = component-wise */
   double sigma;          /* surface tension coefficient (Eq. 10); 0 = none */
   double mu[2];          /* dynamic viscosities of fluids N and P (Eq. 3, 5); 0 = inviscid */
+  /* Tait's equation (Eq. 4) for fluid k when tait[k] = 1: p = B ((rho /
+   * rho0)^gamma - 1) + p0, the pressure a function of the density alone
+   * (the energy component is carried but does not enter it); pinf[k] is
+   * then B - p0, which gives the sound speed c^2 = gamma (p + pinf) / rho */
+  int tait[2];
+  double tait_B[2], tait_rho0[2], tait_p0[2];
 } orc_config;
 
 typedef struct {
@@ -86,6 +92,11 @@ int orc_geometry(orc_ctx *o, double *alpha, double *ax, double *ay,
  * speeds, Newton iterations, left star pressure.  Returns ORC_ERR_NOCONV if
  * Newton does not converge in 50 iterations. */
 int orc_riemann_jump(const double *L, const double *R, double jump, double *out);
+/* The same with either side barotropic (baro_l, baro_r = 1: a fluid on the
+ * curve p + pinf proportional to rho^gamma, Tait's equation): its shock
+ * branch from mass and momentum alone, its star density on the curve. */
+int orc_riemann_jump2(const double *L, const double *R, double jump, int baro_l, int baro_r,
+                      double *out);
 /* Curvature div(grad phi / |grad phi|) of the current level set at cell
  * (i, j) by central differences (0 in 1D or where grad phi = 0). */
 double orc_curvature(orc_ctx *o, int i, int j);

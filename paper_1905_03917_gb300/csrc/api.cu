@@ -60,6 +60,8 @@ struct sif_ctx {
   int br_base_has_ed, br_tail_has_ed;
   int side_pending;
   int use_graphs;
+  int no_graph_env;    // SIF_NO_GRAPH=1: cycles issued from the host on purpose
+  int require_graphs;  // SIF_REQUIRE_GRAPHS=1: a failed capture is an error
   int graph_bucket;  // band grid size baked into the graphs
   int num_sms;
   cudaGraphExec_t g_cycle, g_single;
@@ -137,7 +139,15 @@ static int validate(const sif_config *f, char *why, size_t n) {
   if (!(f->dx > 0.0) || !(f->dy > 0.0)) return snprintf(why, n, "dx, dy must be > 0"), SIF_EINVAL;
   for (int k = 0; k < 2; k++) {
     if (!(f->gamma[k] > 1.0)) return snprintf(why, n, "gamma must be > 1"), SIF_EINVAL;
-    if (!(f->pinf[k] >= 0.0)) return snprintf(why, n, "p_inf must be >= 0"), SIF_EINVAL;
+    if (f->tait[k] != 0 && f->tait[k] != 1) return snprintf(why, n, "tait must be 0 or 1"), SIF_EINVAL;
+    if (f->tait[k]) {
+      if (!(f->tait_B[k] > 0.0 && f->tait_B[k] < 1e300) || !(f->tait_rho0[k] > 0.0 && f->tait_rho0[k] < 1e300) ||
+          !(f->tait_p0[k] > -1e300 && f->tait_p0[k] < 1e300))
+        return snprintf(why, n, "Tait parameters: B > 0, rho0 > 0, p0 finite"), SIF_EINVAL;
+      if (f->weno_char) return snprintf(why, n, "weno_char requires stiffened-gas fluids"), SIF_EINVAL;
+    } else if (!(f->pinf[k] >= 0.0)) {
+      return snprintf(why, n, "p_inf must be >= 0"), SIF_EINVAL;
+    }
   }
   for (int s = 0; s < 4; s++)
     if (f->bc[s] < 0 || f->bc[s] > 2) return snprintf(why, n, "bad boundary kind"), SIF_EINVAL;
@@ -200,7 +210,10 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   }
   {
     const char *ng = getenv("SIF_NO_GRAPH");
-    c->use_graphs = !(ng && ng[0] == '1');
+    c->no_graph_env = ng && ng[0] == '1';
+    c->use_graphs = !c->no_graph_env;
+    const char *rq = getenv("SIF_REQUIRE_GRAPHS");
+    c->require_graphs = rq && rq[0] == '1';
   }
   Grid &g = c->g;
   g.dim = f.dim;
@@ -215,6 +228,12 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   for (int k = 0; k < 2; k++) {
     g.gamma[k] = f.gamma[k];
     g.pinf[k] = f.pinf[k];
+    g.tait[k] = f.tait[k];
+    g.tB[k] = f.tait_B[k];
+    g.trho0[k] = f.tait_rho0[k];
+    g.tp0[k] = f.tait_p0[k];
+    // a Tait fluid's sound speed is the stiffened gas's with p_inf = B - p0
+    if (f.tait[k]) g.pinf[k] = f.pinf[k] = f.tait_B[k] - f.tait_p0[k];
   }
   g.cfl = f.cfl;
   g.weno_eps = f.weno_eps;
@@ -703,6 +722,8 @@ extern "C" int sif_step_single_dt(sif_ctx *c, int nsteps, double t_end, sif_cycl
       taped_step(c);  // the same kernels in the same order, recording
     } else if (ensure_graphs(c) == SIF_OK) {
       CK(cudaGraphLaunch(c->g_single, c->st));
+    } else if (c->require_graphs && c->use_graphs == 0 && !c->no_graph_env) {
+      return SIF_ECUDA;
     } else {
       eval(c, c->q);
       launch_sched(SCHED_SINGLE_DT, c->sc, c->g.cfl, 0, 0, c->st);
@@ -1277,6 +1298,8 @@ static int build_graphs(sif_ctx *c) {
   if (gs) cudaGraphDestroy(gs);
   cudaGetLastError();
   if (c->gerr) {
+    set_err(c, "cycle graph capture failed (%s); cycles are issued from the host",
+            cudaGetErrorString((cudaError_t)c->gerr));
     free_graphs(c);
     c->use_graphs = 0;  // fall back to the host-driven sequence
     return SIF_ECUDA;
@@ -1284,6 +1307,9 @@ static int build_graphs(sif_ctx *c) {
   return SIF_OK;
 }
 
+// 0: graphs in use; SIF_ECUDA: the host issues the kernels instead (graphs
+// switched off by SIF_NO_GRAPH=1 or a failed capture, whose reason is in
+// c->err).  With SIF_REQUIRE_GRAPHS=1 a step call returns that failure.
 static int ensure_graphs(sif_ctx *c) {
   if (!c->use_graphs) return SIF_ECUDA;
   // rebuild when the band outgrew the baked grid sizes or shrank far below
@@ -1302,7 +1328,9 @@ extern "C" int sif_step_multi_dt(sif_ctx *c, int ncycles, double t_end, sif_cycl
   Upd upd0;
   int rc = begin_call(c, t_end, &upd0);
   if (rc) return rc;
-  if (ensure_graphs(c) == SIF_OK) {
+  const int graphs = ensure_graphs(c);
+  if (graphs != SIF_OK && c->require_graphs && !c->no_graph_env) return SIF_ECUDA;
+  if (graphs == SIF_OK) {
     for (int n = 0; n < ncycles; n++) {
       if (t_end > 0.0) {
         rc = read_scalars(c);
@@ -1731,9 +1759,11 @@ extern "C" int sif_tape_reset(sif_ctx *c, int capacity) {
     set_err(c, "the adjoint is defined for rk_order 2");
     return SIF_EINVAL;
   }
-  if (c->cfg.weno_char || c->cfg.sigma != 0.0 || c->cfg.mu[0] != 0.0 || c->cfg.mu[1] != 0.0) {
+  if (c->cfg.weno_char || c->cfg.sigma != 0.0 || c->cfg.mu[0] != 0.0 || c->cfg.mu[1] != 0.0 ||
+      c->cfg.tait[0] || c->cfg.tait[1]) {
     set_err(c, "the adjoint is defined for the component-wise reconstruction (weno_char 0) "
-               "of the inviscid model without surface tension (sigma 0, mu 0)");
+               "of the inviscid stiffened-gas model without surface tension (sigma 0, mu 0, "
+               "tait 0)");
     return SIF_EINVAL;
   }
   cudaSetDevice(c->cfg.device);

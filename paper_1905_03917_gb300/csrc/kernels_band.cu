@@ -99,7 +99,9 @@ __global__ void k_prim(Grid g, PrimArgs P, const double *__restrict__ alpha, con
       double u = q1[c] * iq;
       double v = q2[c] * iq;
       double E = a == 1.0 ? q3[c] : q3[c] / a;
-      double p = (gm - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - gm * pi;
+      // Tait's equation (Eq. 4): the pressure of the density alone
+      double p = g.tait[k] ? g.tB[k] * (pow(rho / g.trho0[k], gm) - 1.0) + g.tp0[k]
+                           : (gm - 1.0) * (E - 0.5 * rho * (u * u + v * v)) - gm * pi;
       bool phys = rho > 0.0 && p + pi > 0.0;
       // a cut cell whose content is not a physical state takes an
       // extended state like a sliver; a full cell with such content is an
@@ -174,7 +176,8 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
 // star sound speed.
 __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, double un,
                                          double pk, double gk, double pik, double jump,
-                                         int maxit, double &ps, double &us, double &cs) {
+                                         int maxit, int baro, double &ps, double &us,
+                                         double &cs) {
   double ck = sqrt(gk * (pk + pik) / rho);
   double ro = __shfl_xor_sync(pair, rho, 1), uo = __shfl_xor_sync(pair, un, 1);
   double po = __shfl_xor_sync(pair, pk, 1), pio = __shfl_xor_sync(pair, pik, 1);
@@ -186,18 +189,20 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
   double pscale = fmin(pl + pil, pr + pir);
   double pfloor = fmax(-pir, -pil - jump) + 1e-12 * pscale;
   double p = 0.5 * ((pl - jump) + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
-  if (p < pfloor) p = pfloor;
+  // iterates stay above the floor without landing on it (a rarefaction's
+  // derivative diverges there and a tiny step would pass for convergence)
+  if (p < pfloor) p = pfloor + 0.5 * (fmax(pl - jump, pr) - pfloor);
   const double own = L ? jump : 0.0;  // this lane's star pressure is p + own
   int it = 0, conv = 0, done = 0;
   double f, df;
   while (it < maxit) {
     it++;
-    riemann_side(p + own, rho, pk, gk, pik, ck, f, df);
+    riemann_side(p + own, rho, pk, gk, pik, ck, f, df, baro);
     double fo = __shfl_xor_sync(pair, f, 1), dfo = __shfl_xor_sync(pair, df, 1);
     double fl = L ? f : fo, fr = L ? fo : f, dfl = L ? df : dfo, dfr = L ? dfo : df;
     double F = fl + fr + (ur - ul);
     double pn = p - F / (dfl + dfr);
-    if (pn < pfloor) pn = pfloor;
+    if (pn < pfloor) pn = pfloor + 0.5 * (p - pfloor);
     double dp = fabs(pn - p);
     p = pn;
     if (conv) {
@@ -207,11 +212,11 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
     if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
   }
   ps = p + own;
-  riemann_side(ps, rho, pk, gk, pik, ck, f, df);
+  riemann_side(ps, rho, pk, gk, pik, ck, f, df, baro);
   double fo = __shfl_xor_sync(pair, f, 1);
   double fl = L ? f : fo, fr = L ? fo : f;
   us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
-  double rs = riemann_star_density(ps, rho, pk, gk, pik);
+  double rs = riemann_star_density(ps, rho, pk, gk, pik, baro);
   cs = sqrt(gk * (ps + pik) / rs);
   return (done || conv) ? 0 : DERR_NOCONV;
 }
@@ -278,7 +283,7 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
     const double jump = g.sigma != 0.0 ? g.sigma * curvature(g, phi, i, j) : 0.0;
     double ps, us, cs;
     int e = riemann_solve_pair(pair, side, rho, un, pk, g.gamma[side], g.pinf[side], jump,
-                               g.newton_max, ps,
+                               g.newton_max, g.tait[side], ps,
                                us, cs);
     if (e && side == 0) atomicOr(&sc->err, e);
     // each fluid's exchange flux with its own interface pressure: fluid N

@@ -39,6 +39,10 @@ struct Grid {
   int tx, ty;    // finite-volume tile shape (output cells per CTA)
   int ntx, nty;  // tiles per direction
   int newton_max;  // Newton iterations allowed per interface Riemann problem
+  // Tait's equation (Eq. 4) per fluid: p = tB ((rho/trho0)^gamma - 1) + tp0
+  // (pinf is then tB - tp0)
+  int tait[2];
+  double tB[2], trho0[2], tp0[2];
 };
 
 // Scalars that live in device memory so that a whole step can run without
@@ -296,9 +300,19 @@ __device__ inline double weno5_plain(double v1, double v2, double v3, double v4,
 __device__ inline double pos_pow(double r, double e) { return exp2(e * log2(r)); }
 
 __device__ inline void riemann_side(double p, double rho, double pk, double g, double pi,
-                                    double ck, double &f, double &df) {
+                                    double ck, double &f, double &df, int baro = 0) {
   double P = pk + pi, Pp = p + pi;
-  if (p > pk) {
+  if (p > pk && baro) {
+    // barotropic shock (Tait's equation): u jump^2 = (p - pk)(1/rho -
+    // 1/rho*), rho* = rho r^(1/g), r = (p + pi)/(pk + pi); 1 - r^(-1/g)
+    // taken without cancellation for r near 1
+    double x = (p - pk) / P;
+    double a = -expm1(-log1p(x) / g);
+    double gsq = (p - pk) * a / rho;
+    double dg = (a + (p - pk) * pos_pow(1.0 + x, -1.0 / g - 1.0) / (g * P)) / rho;
+    f = sqrt(gsq);
+    df = dg / (2.0 * f);
+  } else if (p > pk) {
     double A = 2.0 / ((g + 1.0) * rho);
     double B = (g - 1.0) / (g + 1.0) * P;
     double qr = sqrt(A / (Pp + B));
@@ -313,9 +327,10 @@ __device__ inline void riemann_side(double p, double rho, double pk, double g, d
   }
 }
 
-__device__ inline double riemann_star_density(double p, double rho, double pk, double g, double pi) {
+__device__ inline double riemann_star_density(double p, double rho, double pk, double g, double pi,
+                                             int baro = 0) {
   double r = (p + pi) / (pk + pi);
-  if (p > pk) {
+  if (p > pk && !baro) {
     double qq = (g - 1.0) / (g + 1.0);
     return rho * (r + qq) / (qq * r + 1.0);
   }
@@ -330,7 +345,7 @@ __device__ inline int riemann_solve(double rl, double ul, double pl, double gl, 
   double pscale = fmin(pl + pil, pr + pir);
   double pfloor = -fmin(pil, pir) + 1e-12 * pscale;
   double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
-  if (p < pfloor) p = pfloor;
+  if (p < pfloor) p = pfloor + 0.5 * (fmax(pl, pr) - pfloor);
   int it = 0, conv = 0, done = 0;
   double fl, dfl, fr, dfr;
   while (it < 50) {
@@ -339,7 +354,7 @@ __device__ inline int riemann_solve(double rl, double ul, double pl, double gl, 
     riemann_side(p, rr, pr, gr, pir, cr, fr, dfr);
     double F = fl + fr + (ur - ul);
     double pn = p - F / (dfl + dfr);
-    if (pn < pfloor) pn = pfloor;
+    if (pn < pfloor) pn = pfloor + 0.5 * (p - pfloor);
     double dp = fabs(pn - p);
     p = pn;
     if (conv) {

@@ -28,8 +28,16 @@ def config(nx, ny, dx, dy, matN, matP, bc, dim=2, x0=0.0, y0=0.0, **kw):
            "weno_eps": 1e-6, "mix_alpha": 0.5, "ratio_threshold": 0.7,
            "ext_iters": 10, "reinit_iters": 2, "band": 6.0,
            "flux_correction": 1, "force_ratio_one": 0}
+    if "tait" in matN or "tait" in matP:
+        cfg["tait"] = [matN.get("tait"), matP.get("tait")]
     cfg.update(kw)
     return cfg
+
+
+def tait(B, rho0, p0, gamma):
+    """A fluid closed by Tait's equation (Eq. 4), p = B ((rho/rho0)^gamma -
+    1) + p0; its sound speed is the stiffened gas's with p_inf = B - p0."""
+    return {"gamma": gamma, "pinf": B - p0, "tait": (B, rho0, p0)}
 
 
 def _centres(cfg):

@@ -51,7 +51,9 @@ class Config(ctypes.Structure):
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double),
-                ("mu", ctypes.c_double * 2)]
+                ("mu", ctypes.c_double * 2), ("tait", ctypes.c_int * 2),
+                ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
+                ("tait_p0", ctypes.c_double * 2)]
 
 
 class Profile(ctypes.Structure):
@@ -157,6 +159,11 @@ def make_config(cfg: dict, stream=None, device=0) -> Config:
     c.sigma = float(cfg.get("sigma", 0.0))
     mu = cfg.get("mu", (0.0, 0.0))
     c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
+    # Tait's equation per fluid: (B, rho0, p0), or None for a stiffened gas
+    for k, t in enumerate(cfg.get("tait", (None, None))):
+        if t is not None:
+            c.tait[k] = 1
+            c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
     return c
 
 

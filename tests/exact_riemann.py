@@ -102,3 +102,49 @@ def sample_left_rarefaction_right_shock(L, R, x0, t, x):
         else:
             out.append(rr)
     return out, ps, us, x0 + us * t
+
+
+def tait_density(p, B, rho0, p0, g):
+    """Density on Tait's curve p = B ((rho/rho0)^g - 1) + p0."""
+    return rho0 * ((p - p0) / B + 1.0) ** (1.0 / g)
+
+
+def velocity_jump_tait(p, pk, B, rho0, p0, g):
+    """u-change across the wave of a barotropic (Tait) side at star
+    pressure p: a shock carries mass flux m with m^2 = (p - pk)/(1/rho_k -
+    1/rho*) from mass and momentum alone; a rarefaction integrates
+    dp/(rho c) along the curve, c^2 = dp/drho = g B rho^(g-1) / rho0^g."""
+    rk = tait_density(pk, B, rho0, p0, g)
+    if p > pk:
+        rs = tait_density(p, B, rho0, p0, g)
+        m = math.sqrt((p - pk) / (1.0 / rk - 1.0 / rs))
+        return (p - pk) / m
+
+    def integrand(s):
+        r = tait_density(s, B, rho0, p0, g)
+        c = math.sqrt(g * B * r ** (g - 1.0) / rho0 ** g)
+        return 1.0 / (r * c)
+
+    val, _ = quad(integrand, p, pk, epsabs=0.0, epsrel=1e-13, limit=200)
+    return -val
+
+
+def star_state_tait(L, R, pmin):
+    """L, R = (u, p, jump_fn) per side, where jump_fn(p, pk) gives the
+    side's u-change (velocity_jump_tait or velocity_jump bound to the
+    side's parameters); pmin: the smallest pressure both sides admit (a
+    Tait fluid's p0 - B, a stiffened gas's -p_inf); returns p*, u*."""
+    ul, pl, fl = L
+    ur, pr, fr = R
+
+    def F(p):
+        return fl(p, pl) + fr(p, pr) + (ur - ul)
+
+    lo = pmin + 1e-9 * (min(pl, pr) - pmin)
+    hi = max(pl, pr) * 10.0 + 1.0
+    assert F(lo) < 0.0, "no star state above the admissible pressure"
+    while F(hi) < 0.0:
+        hi *= 10.0
+    p = brentq(F, lo, hi, xtol=1e-300, rtol=1e-15, maxiter=500)
+    us = 0.5 * (ul + ur) + 0.5 * (fr(p, pr) - fl(p, pl))
+    return p, us

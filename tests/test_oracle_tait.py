@@ -1,0 +1,83 @@
+"""Pins of Tait's equation of state (Eq. 4, Sec. 2.2: p = B ((rho /
+rho0)^gamma - 1) + p0, the weakly compressible model's closure) in the
+oracle: the interface Riemann problem with barotropic sides against an
+independent solver written from the Tait parameters (Brent on the star
+pressure, the shock from mass and momentum, the rarefaction by quadrature
+of dp/(rho c) along the curve), the pressure recovered from the density
+alone, and the sound speed c^2 = gamma B (rho/rho0)^gamma / rho."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_03917_gb300 import inputs
+from tests import exact_riemann as ER
+
+# the paper's water (Sec. 4.1-4.2, nondimensional) and its weakly
+# compressible liquid and gas (Sec. 4.4)
+WATER = (3310.0, 1.0, 1.0, 7.15)        # B, rho0, p0, gamma
+LIQUID = (5.0e5, 1000.0, 1.0e3, 7.15)
+GAS_T = (100.0, 1.0, 1.0e3, 1.4)
+
+
+def _side(t, rho, u):
+    B, rho0, p0, g = t
+    p = B * ((rho / rho0) ** g - 1.0) + p0
+    return (rho, u, p, g, B - p0), p
+
+
+def _fn(t):
+    B, rho0, p0, g = t
+    return lambda p, pk: ER.velocity_jump_tait(p, pk, B, rho0, p0, g)
+
+
+@pytest.mark.parametrize("tl,rl,ul,tr,rr,ur", [
+    (WATER, 1.02, 0.0, WATER, 0.999, 0.0),      # shock into the low side, rarefaction
+    (WATER, 1.0, 2.0, WATER, 1.0, -2.0),        # two shocks
+    (WATER, 1.0, -1.0, WATER, 1.0, 1.0),        # two rarefactions
+    (LIQUID, 1000.5, 0.3, GAS_T, 1.01, -0.2),   # liquid against gas-like Tait fluid
+    (GAS_T, 1.2, 0.0, LIQUID, 999.9, 0.0),
+])
+def test_tait_riemann_against_independent_solver(tl, rl, ul, tr, rr, ur):
+    L, pl = _side(tl, rl, ul)
+    R, pr = _side(tr, rr, ur)
+    got = O.riemann_baro(L, R, 1, 1)
+    assert got["rc"] == 0
+    pmin = max(tl[2] - tl[0], tr[2] - tr[0])
+    ps, us = ER.star_state_tait((ul, pl, _fn(tl)), (ur, pr, _fn(tr)), pmin)
+    assert abs(got["p"] - ps) <= 1e-10 * (abs(ps) + min(pl + L[4], pr + R[4]))
+    assert abs(got["u"] - us) <= 1e-9 * (abs(us) + 1e-3 * math.sqrt(L[3] * (pl + L[4]) / rl))
+    # the star densities lie on each side's Tait curve
+    assert got["rho_L"] == pytest.approx(ER.tait_density(got["p"], tl[0], tl[1], tl[2], tl[3]),
+                                         rel=1e-13)
+    assert got["rho_R"] == pytest.approx(ER.tait_density(got["p"], tr[0], tr[1], tr[2], tr[3]),
+                                         rel=1e-13)
+
+
+def test_tait_against_ideal_gas_riemann():
+    """A Tait side against a stiffened-gas (ideal) side: the gas keeps its
+    Rankine-Hugoniot shock of the full Euler equations."""
+    L, pl = _side(WATER, 1.001, 0.0)
+    R = (0.001, 0.0, 1.0, 1.4, 0.0)
+    got = O.riemann_baro(L, R, 1, 0)
+    gas = lambda p, pk: ER.velocity_jump(p, 0.001, 1.0, 1.4, 0.0)
+    ps, us = ER.star_state_tait((0.0, pl, _fn(WATER)), (0.0, 1.0, gas), 0.0)
+    assert abs(got["p"] - ps) <= 1e-10 * ps and abs(got["u"] - us) <= 1e-9 * abs(us)
+
+
+def test_tait_pressure_from_density_alone():
+    """A Tait fluid at rest whose energy component disagrees with its
+    density: the recovered pressure (the stencil state) is Tait's of the
+    density, whatever the energy."""
+    n = 16
+    cfg = inputs.config(n, n, 1.0 / n, 1.0 / n, inputs.AIR, inputs.tait(*LIQUID),
+                        ["periodic"] * 4)
+    phi = np.ones((n, n))
+    rho = 1000.0 + np.linspace(0.0, 0.5, n * n).reshape(n, n)
+    B, rho0, p0, g = LIQUID
+    p_tait = B * ((rho / rho0) ** g - 1.0) + p0
+    pP = np.stack([rho, np.zeros_like(rho), np.zeros_like(rho), 3.0 * p_tait])  # energy off
+    o = O.Oracle(cfg).init(phi, pP.copy(), pP)
+    W = o.stencil_states(1)
+    assert np.abs(W[3] - p_tait).max() <= 1e-12 * np.abs(p_tait).max()
