@@ -600,8 +600,19 @@ def batched_line(steps, warmup, device, dist=None, rank=0, ws=1, weno="component
     for s_, c in zip(b.instances, cases):
         s_.init_fluids(*_prim_arrays(c))
     tuned = autotune.tune_batch(b, device=device, cycles=1)
+    cycle = 0
+
+    def step():
+        nonlocal cycle
+        try:
+            b.step_multi_dt(1)
+        except sif.SifError as e:
+            raise RuntimeError(f"{e} (batch cycle {cycle}; tile shapes {tuned}; "
+                               f"{_alone(cases, str(e), cycle + 1, b, device)})") from e
+        cycle += 1
+
     for _ in range(warmup):
-        b.step_multi_dt(1)
+        step()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if dist:
         dist.barrier()
@@ -612,7 +623,7 @@ def batched_line(steps, warmup, device, dist=None, rank=0, ws=1, weno="component
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            b.step_multi_dt(1)
+            step()
             total_ms += 1e3 * (time.perf_counter() - t0)
             work += b.last_open_updates / 2.0  # RK2: two stages a step
     if dist:
@@ -624,6 +635,21 @@ def batched_line(steps, warmup, device, dist=None, rank=0, ws=1, weno="component
            "tile_shapes": {k: list(v) for k, v in tuned.items()}, "clocks": clk.summary()}
     b.close()
     return total_ms, work, rec
+
+
+def _alone(cases, msg, cycles, batch, device):
+    """After a batch instance failed: the same instance advanced alone from
+    its initial data with its tile shape, for the same number of cycles."""
+    from paper_1905_03917_gb300 import sif
+    try:
+        i = int(msg.split("instance ")[1].split(":")[0])
+        s = sif.Solver(cases[i]["cfg"], device=device).init_fluids(*_prim_arrays(cases[i]))
+        s.set_tile_shape(*batch.instances[i].tile_shape)
+        for _ in range(cycles):
+            s.step_multi_dt(1)
+        return f"instance {i} alone: {cycles} cycles without error"
+    except Exception as e:  # noqa: BLE001 -- a diagnostic
+        return f"alone: {e}"
 
 
 def partition(n, rank, ws):

@@ -1217,9 +1217,10 @@ static void graph_cycle_body3(sif_ctx *c, int f1) {
   cudaGraphConditionalHandle hloop = new_handle(c);
   launch_cond(COND_LOOP, c->sc, hloop, 0, 0, c->max_substeps, c->st);
   cond_node(c, hloop, true, [&] { graph_substep3(c, f1, hloop); });
-  // more than one sub-step: fluid 1's third stage after the loop
-  cudaGraphConditionalHandle hs = new_handle(c), hns = new_handle(c);
-  launch_cond(COND_SINGLE, c->sc, hs, hns, 0, 0, c->st);
+  // more than one sub-step: fluid 1's third stage after the loop (every
+  // handle created in a graph gets its conditional node)
+  cudaGraphConditionalHandle hns = new_handle(c);
+  launch_cond(COND_MULTI_ONLY, c->sc, hns, 0, 0, 0, c->st);
   cond_node(c, hns, false, [&] { third_stage(c, f1); });
   if (c->cfg.flux_correction)
     launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);

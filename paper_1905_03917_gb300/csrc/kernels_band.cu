@@ -886,6 +886,9 @@ __global__ void k_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0,
     case COND_SINGLE_ONLY:
       cudaGraphSetConditional(h0, sc->single ? 1u : 0u);
       break;
+    case COND_MULTI_ONLY:
+      cudaGraphSetConditional(h0, sc->single ? 0u : 1u);
+      break;
     case COND_LOOP: {
       // stop after the last sub-step, on a device error, or when the
       // sub-step count or step size has gone wrong

@@ -529,5 +529,6 @@ unsigned long long sif_launches_adj();
 // names (a handle that was not created for this graph is never set)
 #define COND_LAST_ONLY 5    // h0 = last sub-step
 #define COND_SINGLE_ONLY 6  // h0 = a single sub-step
+#define COND_MULTI_ONLY 7   // h0 = more than one sub-step
 void launch_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
                  cudaGraphConditionalHandle h2, int max_sub, cudaStream_t st);

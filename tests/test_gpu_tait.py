@@ -1,0 +1,93 @@
+"""Tait's equation of state (Eq. 4, the weakly compressible model of
+Sec. 2.2) on the GPU: parity with the oracle on the paper's weakly
+compressible cases at small size (surface tension and viscosity included),
+and the two closed forms those cases have, at the paper's resolution: the
+Laplace jump sigma / R = 646.94566 of the square drop recovering its circle
+(Sec. 4.4) and the Rayleigh period of the oscillating drop (Sec. 4.5)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1905_03917_gb300 import inputs
+from tests.test_gpu_parity import _sif, compare, pair
+
+pytestmark = pytest.mark.gpu
+
+
+def _arrays(case):
+    return [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
+
+
+CASES = {
+    "circle_recovery": lambda: inputs.circle_recovery(32),
+    "drop_oscillation": lambda: inputs.drop_oscillation(32),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("multi", [False, True])
+def test_tait_parity(name, multi):
+    g, o = pair(CASES[name]())
+    step_g = g.step_multi_dt if multi else g.step_single_dt
+    step_o = o.step_multi_dt if multi else o.step_single_dt
+    a, b = step_g(1), step_o(1)
+    assert a["substeps"] == b["substeps"]
+    compare(g, o, 1e-12)
+    subs_g = [step_g(1)["substeps"] for _ in range(40)]
+    subs_o = [step_o(1)["substeps"] for _ in range(40)]
+    assert subs_g == subs_o
+    if multi:
+        assert max(subs_o) >= 2
+    compare(g, o, 1e-8)
+
+
+def test_circle_recovery_laplace_jump():
+    """The square liquid drop at 128^2 after t = 2 (accelerated cycles):
+    the pressure inside exceeds the gas pressure outside by sigma / R, R
+    the radius of the circle of the drop's area."""
+    sif = _sif()
+    case = inputs.circle_recovery(128)
+    n = 128
+    s = sif.Solver(case["cfg"]).init_fluids(*_arrays(case))
+    while s.t < 2.0:
+        s.step_multi_dt(200, t_end=2.0)
+    qN, qP, phi = s.state()
+    X, Y = np.meshgrid((np.arange(n) + 0.5) / n, (np.arange(n) + 0.5) / n)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    R = math.sqrt(0.04 / math.pi)
+    inner, outer = (phi < -2.0 / n) & (r < R - 2.0 / n), (phi > 2.0 / n) & (r < 0.45)
+    B, rho0, p0, g = 5.0e5, 1000.0, 1.0e3, 7.15
+    p_in = B * ((qN[0][inner] / rho0) ** g - 1.0) + p0
+    p_out = 100.0 * (qP[0][outer] ** 1.4 - 1.0) + 1.0e3
+    jump = float(p_in.mean() - p_out.mean())
+    area = float((phi < 0).sum()) / n ** 2
+    print(f"Laplace jump {jump:.2f} (sigma/R = {73.0 / R:.5f}), drop area {area:.5f}")
+    assert abs(area - 0.04) <= 0.02 * 0.04
+    assert abs(jump - 73.0 / R) <= 0.10 * 73.0 / R
+
+
+def test_drop_oscillation_period():
+    """The elliptic drop at 128^2: the difference of its second moments
+    (x^2 - y^2 over the liquid) changes sign every half period; the
+    period between the first and third sign changes is the Rayleigh
+    period of mode 2, T = 2 pi / sqrt(6 sigma / ((rho_l + rho_g) R^3))."""
+    sif = _sif()
+    n = 128
+    case = inputs.drop_oscillation(n)
+    s = sif.Solver(case["cfg"]).init_fluids(*_arrays(case))
+    X, Y = np.meshgrid((np.arange(n) + 0.5) / n, (np.arange(n) + 0.5) / n)
+    trace = []
+    while s.t < 0.2:
+        s.step_multi_dt(5, t_end=0.2)
+        qN, _, _ = s.state()
+        m = qN[0] / 100.0   # liquid volume per cell
+        trace.append((s.t, float((m * ((X - 0.5) ** 2 - (Y - 0.5) ** 2)).sum())))
+    t, d = np.array(trace).T
+    z = [t[i] - d[i] * (t[i + 1] - t[i]) / (d[i + 1] - d[i])
+         for i in range(len(d) - 1) if d[i] * d[i + 1] < 0]
+    R = math.sqrt(0.2 * 0.125)
+    T = 2.0 * math.pi / math.sqrt(6.0 * 341.642 / (101.0 * R ** 3))
+    print("sign changes", [round(v, 5) for v in z], "Rayleigh period", T)
+    assert len(z) >= 3
+    assert abs((z[2] - z[0]) - T) <= 0.10 * T

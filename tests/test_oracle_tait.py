@@ -81,3 +81,63 @@ def test_tait_pressure_from_density_alone():
     o = O.Oracle(cfg).init(phi, pP.copy(), pP)
     W = o.stencil_states(1)
     assert np.abs(W[3] - p_tait).max() <= 1e-12 * np.abs(p_tait).max()
+
+
+def _tait_static(n=32, angle=0.0):
+    """A planar interface between the paper's weakly compressible liquid
+    and gas (Sec. 4.4) at rest at the common reference pressure, normal to
+    the reflective walls it meets (an oblique one meets its mirror image
+    in a kink, which is not static)."""
+    d = 1.0 / n
+    cfg = inputs.config(n, n, d, d, inputs.tait(*LIQUID[:3], LIQUID[3]),
+                        inputs.tait(*GAS_T[:3], GAS_T[3]), ["reflect"] * 4)
+    X, Y = inputs._centres(cfg)
+    phi = (X - 0.5) * math.cos(angle) + (Y - 0.5) * math.sin(angle) - 0.013
+    pN = inputs._uniform(X.shape, LIQUID[1], 0.0, 0.0, LIQUID[2])
+    pP = inputs._uniform(X.shape, GAS_T[1], 0.0, 0.0, GAS_T[2])
+    return cfg, phi, pN, pP
+
+
+@pytest.mark.parametrize("multi", [False, True])
+def test_tait_static_interface_stays_static(multi):
+    """Both Tait fluids at their reference density (p = p0 = 1e3 on both
+    sides) across a planar interface: the interface Riemann problem returns
+    p0 and zero velocity and the state stays at rest to round-off."""
+    cfg, phi, pN, pP = _tait_static()
+    o = O.Oracle(cfg).init(phi, pN, pP)
+    for _ in range(60):
+        (o.step_multi_dt if multi else o.step_single_dt)(1)
+    assert o.status == 0
+    qN, qP, _ = o.state()
+    al = o.geometry()["alpha"]
+    for q, a, t in ((qN, 1 - al, LIQUID), (qP, al, GAS_T)):
+        m = a > 1e-6
+        rho = q[0][m] / a[m]
+        assert np.abs(rho - t[1]).max() <= 1e-12 * t[1]
+        assert np.abs(q[1][m]).max() <= 1e-12 * t[1] and np.abs(q[2][m]).max() <= 1e-12 * t[1]
+
+
+def test_tait_bubble_conserves_mass_and_momentum():
+    """A periodic box with a gas-like Tait bubble in the Tait liquid, moving
+    and perturbed, in multi-step cycles with the correction: mass of each
+    fluid and the total momentum are conserved to round-off (the energy
+    component is carried passively)."""
+    n = 40
+    d = 1.0 / n
+    cfg = inputs.config(n, n, d, d, inputs.tait(*LIQUID[:3], LIQUID[3]),
+                        inputs.tait(*GAS_T[:3], GAS_T[3]), ["periodic"] * 4)
+    X, Y = inputs._centres(cfg)
+    phi = -(np.hypot(X - 0.5, Y - 0.5) - 0.2)            # gas (P) inside the bubble
+    rng = np.random.default_rng(2)
+    pN = inputs._uniform(X.shape, LIQUID[1], 0.3, -0.2, LIQUID[2])
+    pP = inputs._uniform(X.shape, GAS_T[1], 0.3, -0.2, GAS_T[2])
+    pN[0] *= 1.0 + 1e-4 * np.sin(2 * np.pi * X + rng.uniform(0, 6))
+    pP[0] *= 1.0 + 1e-2 * np.sin(2 * np.pi * Y + rng.uniform(0, 6))
+    o = O.Oracle(cfg).init(phi, pN, pP)
+    I0 = o.integrals()
+    subs = [o.step_multi_dt(1)["substeps"] for _ in range(40)]
+    assert o.status == 0 and max(subs) >= 2
+    I1 = o.integrals()
+    assert np.abs(I1[:, 0] - I0[:, 0]).max() <= 1e-13 * np.abs(I0[:, 0]).max()
+    mom0, mom1 = I0[:, 1:3].sum(0), I1[:, 1:3].sum(0)
+    assert np.abs(mom1 - mom0).max() <= 1e-13 * I0[:, 0].sum()
