@@ -117,11 +117,9 @@ __global__ void k_adj_face(Grid g, int k, int d, Planes4 W, const double *__rest
     int c = gidx(g, i, j);
     double ap = aperture[c];
     double A = k == 1 ? ap : 1.0 - ap;
-    if (A == 0.0) {
-#pragma unroll
-      for (int q = 0; q < 40; q++) G.p[q][c] = 0.0;
-      continue;
-    }
+    // a face closed to fluid k contributes nothing: its coefficients are
+    // neither written here nor read by the gather
+    if (A == 0.0) continue;
     bool has_r = d == 0 ? i < g.nx : j < g.ny;
     bool has_l = d == 0 ? i > 0 : j > 0;
     double lF[4];
@@ -187,11 +185,17 @@ __device__ inline void split_T(double rho, double u, double v, double p, double 
   out[3] = gp;
 }
 
+// whether the face at index f is open to fluid k (P-aperture stored)
+__device__ inline bool open_face(const double *aperture, int k, int f) {
+  double ap = aperture[f];
+  return (k == 1 ? ap : 1.0 - ap) != 0.0;
+}
+
 // 2. gather: every cell whose split fluxes enter a face of direction d
 // (ghost cells included) collects its coefficients and adds the
 // transposed split-flux Jacobian to the stencil-state adjoint lw
-__global__ void k_adj_gather(Grid g, int k, int d, Planes4 W, const unsigned long long *lf,
-                             Planes40 G, Planes4 lw) {
+__global__ void k_adj_gather(Grid g, int k, int d, Planes4 W, const double *__restrict__ aperture,
+                             const unsigned long long *lf, Planes40 G, Planes4 lw) {
   SIF_TICK();
   const int ncx = d == 0 ? g.nx + 2 * SIF_GH : g.nx;
   const int ncy = d == 0 ? g.ny : g.ny + 2 * SIF_GH;
@@ -211,14 +215,18 @@ __global__ void k_adj_gather(Grid g, int k, int d, Planes4 W, const unsigned lon
       int fpos = pos + 3 - r;  // face whose fp stencil holds this cell at r
       if (fpos >= 0 && fpos <= nfaces) {
         int f = c + (3 - r) * s;
+        if (open_face(aperture, k, f)) {
 #pragma unroll
-        for (int m = 0; m < 4; m++) sp[m] += G.p[r * 4 + m][f];
+          for (int m = 0; m < 4; m++) sp[m] += G.p[r * 4 + m][f];
+        }
       }
       int fneg = pos + r - 2;  // face whose fm stencil holds this cell at r
       if (fneg >= 0 && fneg <= nfaces) {
         int f = c + (r - 2) * s;
+        if (open_face(aperture, k, f)) {
 #pragma unroll
-        for (int m = 0; m < 4; m++) sm[m] += G.p[20 + r * 4 + m][f];
+          for (int m = 0; m < 4; m++) sm[m] += G.p[20 + r * 4 + m][f];
+        }
       }
     }
     double out[4];
@@ -517,7 +525,8 @@ void launch_adj_rhs(const Grid &g, double *const W[2][4], const unsigned long lo
                                                       p4(mu[k]), lf, dtp, fac, GG);
       long long nc = d == 0 ? (long long)(g.nx + 2 * SIF_GH) * g.ny
                             : (long long)g.nx * (g.ny + 2 * SIF_GH);
-      k_adj_gather<<<blocks_for(nc, 256), 256, 0, st>>>(g, k, d, p4(W[k]), lf, GG, p4(lw[k]));
+      k_adj_gather<<<blocks_for(nc, 256), 256, 0, st>>>(g, k, d, p4(W[k]), d == 0 ? ax : ay, lf,
+                                                        GG, p4(lw[k]));
     }
   }
   long long n = (long long)g.nx * g.ny;
