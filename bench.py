@@ -782,7 +782,10 @@ def main():
     ap.add_argument("--mode", default="multi", choices=["multi", "single"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-cycles", type=int, default=200,
+    # instance 121 of the seed-0 batch (436^2, gas at about 3000 times the
+    # water's pressure) reaches a non-physical state in cycle 67, in the
+    # oracle and on the GPU alike: the default line times 60 cycles
+    ap.add_argument("--batch-cycles", type=int, default=60,
                     help="timed cycles of the 256-instance batch in the default line")
     ap.add_argument("--tile", default="",
                     help="finite-volume tile shape TXxTY instead of the autotuner's choice")
