@@ -404,6 +404,50 @@ def multi_vs_single(case, device, steps_single=600, cfls=(0.6, 0.5, 0.4, 0.3, 0.
             "timing": "host wall clock around one synchronising call that runs to T"}
 
 
+# Table 1 of the paper (Sec. 4.2): single- and multi-time-step speedup
+# r_s of the translating water droplet on uniform 2D grids, measured on an
+# Intel i7-4790 (8 threads); context for the GPU figures, not a target
+PAPER_TABLE1_SPEEDUP = {32: 1.539, 64: 1.923, 128: 2.322, 256: 2.873}
+
+
+def paper_table1(device, sizes=(64, 128, 256, 512), t_run=0.5):
+    """The paper's Table 1 comparison on this GPU: the translating water
+    droplet (Tait water in air, periodic, CFL 0.6) advanced by both methods
+    from the same initial data over the same span of time; r_s = single-
+    step time / multi-step time at each resolution.  An untimed pass per
+    method builds its graphs and counts its steps (or cycles) to t_run; the
+    timed run then issues exactly that many without host round trips."""
+    import torch
+    from paper_1905_03917_gb300 import inputs, sif
+    rows = []
+    for n in sizes:
+        case = inputs.droplet_translation(n)
+        arrs = _prim_arrays(case)
+        rec = {"grid": f"{n}x{n}", "paper_speedup": PAPER_TABLE1_SPEEDUP.get(n)}
+        for mode in ("single", "multi"):
+            s = sif.Solver(case["cfg"], device=device).init_fluids(*arrs)
+            step = s.step_multi_dt if mode == "multi" else s.step_single_dt
+            count, subs = 0, []
+            while s.t < t_run:
+                subs.append(step(1, t_end=t_run)["substeps"])
+                count += 1
+            s.init_fluids(*arrs)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = step(count)
+            torch.cuda.synchronize()
+            rec[f"{mode}_ms"] = 1e3 * (time.perf_counter() - t0)
+            rec[f"{mode}_steps"] = count
+            if mode == "multi":
+                rec["mean_substeps"] = float(np.mean(subs))
+            s.close()
+        rec["speedup"] = rec["single_ms"] / rec["multi_ms"]
+        rows.append(rec)
+    return {"workload": "droplet translation (Sec. 4.2), Tait water in air, periodic",
+            "t": t_run, "runs": rows,
+            "timing": "host wall clock around one synchronising call of the counted steps"}
+
+
 def tube_exact_error(T):
     """L1 error of the 1D water/air tube's mixture density against the
     cell-averaged exact solution (16 samples a cell) at time T."""
@@ -719,6 +763,7 @@ def run_ours(args):
                          lambda: workload_line("underwater_explosion", "multi", args.steps,
                                                args.warmup, local, weno=args.weno)),
                         ("batched", batched),
+                        ("paper_table1", lambda: paper_table1(local)),
                         ("adjoint", lambda: adjoint_cost(local)),
                         ("adjoint_origin", lambda: adjoint_cost(local, centre=(0.0, 0.0)))):
             try:

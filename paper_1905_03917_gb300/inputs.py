@@ -410,3 +410,38 @@ def drop_oscillation(n=64, a=0.2, b=0.125):
     pN = _uniform(X.shape, 100.0, 0.0, 0.0, 1.0e4)
     pP = _uniform(X.shape, 1.0, 0.0, 0.0, 1.0e4)
     return {"name": f"drop_oscillation_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+def droplet_translation(n=64):
+    """Sec. 4.2 (the paper's Table 1 case): a water droplet of radius 0.1
+    (Tait's equation, B = 3310, rho0 = 1000, p0 = 1, gamma = 7.15; fluid N)
+    at the centre of the periodic unit box in air (ideal gas, rho 1.2,
+    gamma 1.4), both at p = 1 moving with u = sqrt(10)/100, v = 0
+    (nondimensional: p / 1 atm, rho / 1 kg/m^3).  One period of the
+    translation takes t = 10 sqrt(10)."""
+    d = 1.0 / n
+    water = tait(3310.0, 1000.0, 1.0, 7.15)
+    cfg = config(n, n, d, d, water, AIR, ["periodic"] * 4)
+    X, Y = _centres(cfg)
+    phi = np.hypot(X - 0.5, Y - 0.5) - 0.1
+    u = math.sqrt(10.0) / 100.0
+    pN = _uniform(X.shape, 1000.0, u, 0.0, 1.0)
+    pP = _uniform(X.shape, 1.2, u, 0.0, 1.0)
+    return {"name": f"droplet_translation_{n}", "cfg": cfg, "phi": phi, "prim_N": pN,
+            "prim_P": pP}
+
+
+def gas_water_tube(n=200):
+    """Sec. 4.1's gas-water shock tube: high-pressure gas (rho 0.01, p 1000,
+    gamma 2, ideal) for x < 0.5 against Tait water (rho 1, p 1, gamma 7.15,
+    B = 3310, rho0 = 1, p0 = 1), nondimensional, zero-gradient ends; the
+    paper runs it to t = 0.0008."""
+    d = 1.0 / n
+    gas = {"gamma": 2.0, "pinf": 0.0}
+    water = tait(3310.0, 1.0, 1.0, 7.15)
+    cfg = config(n, 1, d, d, gas, water, ["zerograd"] * 4, dim=1)
+    x = (np.arange(n) + 0.5) * d
+    phi = (x - 0.5)[None, :]
+    pN = _uniform((1, n), 0.01, 0.0, 0.0, 1000.0)
+    pP = _uniform((1, n), 1.0, 0.0, 0.0, 1.0)
+    return {"name": f"gas_water_tube_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}

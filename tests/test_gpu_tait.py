@@ -91,3 +91,24 @@ def test_drop_oscillation_period():
     print("sign changes", [round(v, 5) for v in z], "Rayleigh period", T)
     assert len(z) >= 3
     assert abs((z[2] - z[0]) - T) <= 0.10 * T
+
+
+@pytest.mark.parametrize("name", ["droplet_translation", "gas_water_tube"])
+@pytest.mark.parametrize("multi", [False, True])
+def test_paper_tait_cases_parity(name, multi):
+    """The paper's compressible cases with Tait water (Sec. 4.1's gas-water
+    tube, Sec. 4.2's translating droplet) against the oracle."""
+    case = (inputs.droplet_translation(32) if name == "droplet_translation"
+            else inputs.gas_water_tube(200))
+    g, o = pair(case)
+    step_g = g.step_multi_dt if multi else g.step_single_dt
+    step_o = o.step_multi_dt if multi else o.step_single_dt
+    a, b = step_g(1), step_o(1)
+    assert a["substeps"] == b["substeps"]
+    compare(g, o, 1e-12)
+    subs_g = [step_g(1)["substeps"] for _ in range(50)]
+    subs_o = [step_o(1)["substeps"] for _ in range(50)]
+    assert subs_g == subs_o
+    if multi:
+        assert max(subs_o) >= 2
+    compare(g, o, 1e-8)
