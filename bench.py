@@ -837,6 +837,8 @@ def main():
     ap.add_argument("--weno", default="componentwise", choices=["componentwise", "characteristic"],
                     help="finite-volume reconstruction: on conserved components (the paper's "
                          "WENO-LF) or on characteristic fields")
+    ap.add_argument("--adjoint-size", type=int, default=512,
+                    help="grid of the --workload adjoint measurement (n x n)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-vs-single, explosion, batch and adjoint measurements")
     args = ap.parse_args()
@@ -846,6 +848,13 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "adjoint":
+        # the adjoint measurement alone (gas-water bubble at x = 0.7, n x n,
+        # --steps single-dt steps, a checkpoint every --steps / 2), e.g. for
+        # kernel captures of the backward pass on a small case
+        r = adjoint_cost(0, n=args.adjoint_size, nsteps=args.steps,
+                         every=max(1, args.steps // 2))
+        print(json.dumps({"impl": "ours", "adjoint": r}), flush=True)
     else:
         run_ours(args)
 

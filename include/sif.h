@@ -104,6 +104,14 @@ typedef struct {
                             / rho.  0 = stiffened gas.  Requires weno_char 0; the adjoint
                             calls require 0. */
   double tait_B[2], tait_rho0[2], tait_p0[2];  /* > 0, > 0, finite */
+  int flux;              /* face flux of the finite-volume stage (Eq. 2): 0 = WENO5 on
+                            Lax-Friedrichs split fluxes, per conserved component or field
+                            (the paper's WENO-LF); 1 = HLLC (Toro's contact-restoring
+                            approximate Riemann solver, Davis wave-speed bounds) between
+                            WENO5 reconstructions of the primitive state (rho, u, v, p)
+                            from either side, a reconstruction with rho <= 0 or
+                            p + pinf <= 0 replaced by its cell's state.  1 requires
+                            weno_char 0; the adjoint calls require 0. */
 } sif_config;
 
 /* Per-cycle record of the multi-time-step schedule (Sec. 3.1). */

@@ -34,6 +34,9 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+# face fluxes of the finite-volume stage: WENO5-LF (the paper's), HLLC
+FLUXES = {"lf": 0, "hllc": 1}
+
 class _Config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double),
@@ -49,7 +52,7 @@ class _Config(ctypes.Structure):
                 ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("mu", ctypes.c_double * 2), ("tait", ctypes.c_int * 2),
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
-                ("tait_p0", ctypes.c_double * 2)]
+                ("tait_p0", ctypes.c_double * 2), ("flux", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -93,6 +96,7 @@ def lib():
         L.orc_cell_alpha.argtypes = [D, D, D, D]
         L.orc_riemann.argtypes = [dp, dp, dp]
         L.orc_char_basis.argtypes = [D, D, D, D, D, D, I, dp, dp]
+        L.orc_hllc.argtypes = [dp, dp, D, D, I, dp]
         L.orc_riemann_jump.argtypes = [dp, dp, D, dp]
         L.orc_riemann_jump2.argtypes = [dp, dp, D, I, I, dp]
         L.orc_curvature.restype = D
@@ -147,6 +151,10 @@ def make_config(cfg: dict) -> _Config:
     mu = cfg.get("mu", (0.0, 0.0))
     c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
     # Tait's equation per fluid: (B, rho0, p0) or None for a stiffened gas
+    fl = cfg.get("flux", "lf")
+    if fl not in FLUXES:
+        raise ValueError(f"flux must be one of {sorted(FLUXES)}")
+    c.flux = FLUXES[fl]
     for k, t in enumerate(cfg.get("tait", (None, None))):
         if t is not None:
             c.tait[k] = 1
@@ -345,6 +353,14 @@ def riemann_jump(left, right, jump):
     rc = lib().orc_riemann_jump(_ptr(L), _ptr(R), float(jump), _ptr(out))
     return {"p": out[0], "u": out[1], "rho_L": out[2], "rho_R": out[3],
             "c_L": out[4], "c_R": out[5], "iters": int(out[6]), "p_L": out[7], "rc": rc}
+
+
+def hllc(WL, WR, gamma, pinf, d):
+    """HLLC flux of direction d between primitive states (rho, u, v, p);
+    None for a non-physical state."""
+    L, R, F = _f64(WL), _f64(WR), np.empty(4)
+    rc = lib().orc_hllc(_ptr(L), _ptr(R), float(gamma), float(pinf), int(d), _ptr(F))
+    return None if rc else F
 
 
 def riemann(left, right):

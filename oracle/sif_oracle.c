@@ -787,6 +787,92 @@ int orc_char_basis(double g, double pinf, double rho, double u, double v, double
   return 0;
 }
 
+/* physical flux of direction d and conserved state of a primitive state of
+ * a stiffened gas */
+static void euler_flux(const double *W, double g, double pi, int d, double *F, double *U) {
+  double rho = W[0], u = W[1], v = W[2], p = W[3];
+  double E = (p + g * pi) / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+  double un = d == 0 ? u : v;
+  U[0] = rho;
+  U[1] = rho * u;
+  U[2] = rho * v;
+  U[3] = E;
+  F[0] = rho * un;
+  F[1] = rho * u * un;
+  F[2] = rho * v * un;
+  F[3] = un * (E + p);
+  F[1 + d] += p;
+}
+
+/* HLLC (Toro, Riemann Solvers and Numerical Methods for Fluid Dynamics,
+ * Sec. 10.4): the two outer waves S_L, S_R bound the fan, the contact
+ * moves with S*, and the star states on either side of it are
+ *   U*_K = rho_K (S_K - un_K) / (S_K - S*) (1, S* along d, ut_K across d,
+ *          E_K / rho_K + (S* - un_K) (S* + p_K / (rho_K (S_K - un_K)))).
+ * The flux is F_L, F_L + S_L (U*_L - U_L), F_R + S_R (U*_R - U_R) or F_R
+ * as the face (x/t = 0) lies left of S_L, between S_L and S*, between S*
+ * and S_R, or right of S_R. */
+int orc_hllc(const double *WL, const double *WR, double g, double pi, int d, double *F) {
+  if (!(WL[0] > 0.0) || !(WR[0] > 0.0) || !(WL[3] + pi > 0.0) || !(WR[3] + pi > 0.0) ||
+      !(g > 1.0) || (d != 0 && d != 1))
+    return ORC_ERR_INVAL;
+  double FL[4], UL[4], FR[4], UR[4];
+  euler_flux(WL, g, pi, d, FL, UL);
+  euler_flux(WR, g, pi, d, FR, UR);
+  double rl = WL[0], rr = WR[0], pl = WL[3], pr = WR[3];
+  double ul = d == 0 ? WL[1] : WL[2], ur = d == 0 ? WR[1] : WR[2];
+  double cl = sqrt(g * (pl + pi) / rl), cr = sqrt(g * (pr + pi) / rr);
+  double SL = dmin(ul - cl, ur - cr), SR = dmax(ul + cl, ur + cr);
+  if (SL >= 0.0) {
+    for (int m = 0; m < 4; m++) F[m] = FL[m];
+    return 0;
+  }
+  if (SR <= 0.0) {
+    for (int m = 0; m < 4; m++) F[m] = FR[m];
+    return 0;
+  }
+  double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) /
+              (rl * (SL - ul) - rr * (SR - ur));
+  const double *W = Ss >= 0.0 ? WL : WR;
+  const double *FK = Ss >= 0.0 ? FL : FR;
+  const double *UK = Ss >= 0.0 ? UL : UR;
+  double SK = Ss >= 0.0 ? SL : SR, uK = Ss >= 0.0 ? ul : ur;
+  double fac = W[0] * (SK - uK) / (SK - Ss);
+  double Us[4];
+  Us[0] = fac;
+  Us[1] = fac * (d == 0 ? Ss : W[1]);
+  Us[2] = fac * (d == 0 ? W[2] : Ss);
+  Us[3] = fac * (UK[3] / W[0] + (Ss - uK) * (Ss + W[3] / (W[0] * (SK - uK))));
+  for (int m = 0; m < 4; m++) F[m] = FK[m] + SK * (Us[m] - UK[m]);
+  return 0;
+}
+
+/* HLLC face flux of fluid k between cells c - s and c: each primitive
+ * component reconstructed by WENO5 from the left (cells c-3s .. c+s) and
+ * from the right (cells c+2s .. c-2s); a reconstructed state that is not
+ * physical (density or p + pinf not positive) is replaced by its cell's
+ * own state (first order) */
+static void face_flux_hllc(const orc_ctx *o, int k, int c, int s, int d, double *Fh) {
+  double g = o->c.gamma[k], pi = o->c.pinf[k];
+  double WL[4], WR[4];
+  for (int m = 0; m < 4; m++) {
+    const double *w = o->w[k][m];
+    double vl[5], vr[5];
+    for (int r = 0; r < 5; r++) {
+      vl[r] = w[c + (r - 3) * s];
+      vr[r] = w[c + (2 - r) * s];
+    }
+    WL[m] = orc_weno5(vl, o->c.weno_eps);
+    WR[m] = orc_weno5(vr, o->c.weno_eps);
+  }
+  if (!(WL[0] > 0.0) || !(WL[3] + pi > 0.0))
+    for (int m = 0; m < 4; m++) WL[m] = o->w[k][m][c - s];
+  if (!(WR[0] > 0.0) || !(WR[3] + pi > 0.0))
+    for (int m = 0; m < 4; m++) WR[m] = o->w[k][m][c];
+  if (orc_hllc(WL, WR, g, pi, d, Fh) != 0)
+    for (int m = 0; m < 4; m++) Fh[m] = NAN;  /* a non-physical stencil state */
+}
+
 /* numerical flux through the face between cells c - s and c, where s is
  * the index stride of direction d.  Component-wise: WENO5 of each
  * conserved component of the split fluxes.  Characteristic-wise: the split
@@ -795,6 +881,10 @@ int orc_char_basis(double g, double pinf, double rho, double u, double v, double
  * reconstructed by WENO5, and the fields are mapped back by the right
  * eigenvectors. */
 static void face_flux(const orc_ctx *o, int k, int c, int s, int d, double *Fh) {
+  if (o->c.flux == 1) {
+    face_flux_hllc(o, k, c, s, d, Fh);
+    return;
+  }
   double a = o->lf[k][d];
   double fp[6][4], fm[6][4];
   for (int r = 0; r < 6; r++) split(o, k, c + (r - 3) * s, d, a, fp[r], fm[r]);
@@ -1553,6 +1643,8 @@ orc_ctx *orc_create(const orc_config *cfg) {
     return NULL;
   if (cfg->rk_order != 2 && cfg->rk_order != 3) return NULL;
   if (cfg->weno_char != 0 && cfg->weno_char != 1) return NULL;
+  if (cfg->flux != 0 && cfg->flux != 1) return NULL;
+  if (cfg->flux == 1 && cfg->weno_char) return NULL;
   if (!(cfg->sigma >= 0.0) || !isfinite(cfg->sigma)) return NULL;
   for (int k = 0; k < 2; k++)
     if (!(cfg->mu[k] >= 0.0) || !isfinite(cfg->mu[k])) return NULL;
@@ -2240,8 +2332,8 @@ int orc_adjoint_step(orc_ctx *o, double dt, const double *lf, const double *phi1
                      const double *phi2, const double *lam_in, double *lam_out) {
   /* the adjoint is written for the component-wise reconstruction without
    * surface tension */
-  if (o->c.rk_order != 2 || o->c.weno_char || o->c.sigma != 0.0 || o->c.mu[0] != 0.0 ||
-      o->c.mu[1] != 0.0) {
+  if (o->c.rk_order != 2 || o->c.weno_char || o->c.flux || o->c.sigma != 0.0 ||
+      o->c.mu[0] != 0.0 || o->c.mu[1] != 0.0) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }
@@ -2346,7 +2438,8 @@ int orc_rhs_frozen(orc_ctx *o, const double *lf, double *out) {
 }
 
 int orc_rhs_adjoint(orc_ctx *o, const double *lf, const double *mu_in, double *lq_out) {
-  if (o->c.weno_char || o->c.sigma != 0.0 || o->c.mu[0] != 0.0 || o->c.mu[1] != 0.0) {
+  if (o->c.weno_char || o->c.flux || o->c.sigma != 0.0 || o->c.mu[0] != 0.0 ||
+      o->c.mu[1] != 0.0) {
     o->err |= ORC_ERR_INVAL;
     return o->err;
   }

@@ -53,6 +53,11 @@ typedef struct {
    * then B - p0, which gives the sound speed c^2 = gamma (p + pinf) / rho */
   int tait[2];
   double tait_B[2], tait_rho0[2], tait_p0[2];
+  /* face flux: 0 = WENO5 on Lax-Friedrichs split fluxes (the paper's),
+   * 1 = HLLC (Toro's contact-restoring approximate Riemann solver) between
+   * WENO5 reconstructions of the primitive state from either side
+   * (requires weno_char 0) */
+  int flux;
 } orc_config;
 
 typedef struct {
@@ -79,6 +84,15 @@ int orc_set_state(orc_ctx *o, const double *q_N, const double *q_P, const double
 int orc_integrals(const orc_ctx *o, double *out);
 double orc_time(const orc_ctx *o);
 int orc_status(const orc_ctx *o);
+
+/* HLLC flux through a face of direction d (0 = x, 1 = y) between the
+ * primitive states WL and WR (rho, u, v, p) of one stiffened gas (gamma,
+ * pinf): Davis's wave-speed bounds S_L = min(un_L - c_L, un_R - c_R),
+ * S_R = max(un_L + c_L, un_R + c_R), the contact speed S* from the
+ * momentum balance across the two outer waves, and the flux of the state
+ * region the face lies in.  F = flux of (rho, rho u, rho v, E).  Returns
+ * ORC_ERR_INVAL for a non-physical state. */
+int orc_hllc(const double *WL, const double *WR, double gamma, double pinf, int d, double *F);
 
 /* Geometry of the current level set: alpha_P, x-face and y-face P-apertures
  * (left/bottom face of each cell, nx+1 by ny and nx by ny+1 arrays), and

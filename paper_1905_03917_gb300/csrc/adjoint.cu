@@ -34,10 +34,15 @@ __device__ inline double lf_value(const unsigned long long *lf, int k, int d) {
 // ---------------------------------------------------------------------
 // WENO5-JS and its derivative with respect to the five stencil values
 
+// The divisions are reciprocals (Newton's iteration from the device's
+// approximate reciprocal, within an ulp of IEEE division) times the
+// numerators, and the constant 1/6 a product: the derivative is the same
+// function, rounded differently.
 __device__ inline void weno5_grad(const double v[5], double eps, double g[5]) {
-  const double q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
-  const double q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
-  const double q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+  constexpr double s6 = 1.0 / 6.0;
+  const double q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) * s6;
+  const double q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) * s6;
+  const double q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) * s6;
   // smoothness indicators b_i = 13/12 s_i^2 + 1/4 t_i^2
   const double s0 = v[0] - 2.0 * v[1] + v[2], t0 = v[0] - 4.0 * v[1] + 3.0 * v[2];
   const double s1 = v[1] - 2.0 * v[2] + v[3], t1 = v[1] - v[3];
@@ -45,32 +50,36 @@ __device__ inline void weno5_grad(const double v[5], double eps, double g[5]) {
   const double b0 = 13.0 / 12.0 * s0 * s0 + 0.25 * t0 * t0;
   const double b1 = 13.0 / 12.0 * s1 * s1 + 0.25 * t1 * t1;
   const double b2 = 13.0 / 12.0 * s2 * s2 + 0.25 * t2 * t2;
-  const double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-  const double a0 = 0.1 / (e0 * e0), a1 = 0.6 / (e1 * e1), a2 = 0.3 / (e2 * e2);
-  const double S = a0 + a1 + a2, iS = 1.0 / S;
-  const double r = (a0 * q0 + a1 * q1 + a2 * q2) * iS;
-  // d r = sum_i (a_i dq_i + (q_i - r) da_i) / S with da_i = -2 a_i / e_i db_i
-  const double c0 = -2.0 * a0 / e0 * (q0 - r), c1 = -2.0 * a1 / e1 * (q1 - r),
-               c2 = -2.0 * a2 / e2 * (q2 - r);
+  const double i0 = recip_newton3(eps + b0), i1 = recip_newton3(eps + b1),
+               i2 = recip_newton3(eps + b2);
+  const double a0 = 0.1 * i0 * i0, a1 = 0.6 * i1 * i1, a2 = 0.3 * i2 * i2;
+  const double iS = recip_newton3(a0 + a1 + a2);
+  // normalised weights w_i = a_i / S and the reconstruction r
+  const double w0 = a0 * iS, w1 = a1 * iS, w2 = a2 * iS;
+  const double r = w0 * q0 + w1 * q1 + w2 * q2;
+  // d r = sum_i (w_i dq_i + (q_i - r) da_i / S) with da_i = -2 a_i / e_i db_i
+  const double c0 = -2.0 * w0 * i0 * (q0 - r), c1 = -2.0 * w1 * i1 * (q1 - r),
+               c2 = -2.0 * w2 * i2 * (q2 - r);
   // db_i / dv = 13/6 s_i ds_i + 1/2 t_i dt_i
-  const double u0 = 13.0 / 6.0 * s0, w0 = 0.5 * t0;
-  const double u1 = 13.0 / 6.0 * s1, w1 = 0.5 * t1;
-  const double u2 = 13.0 / 6.0 * s2, w2 = 0.5 * t2;
-  const double d0[5] = {u0 + w0, -2.0 * u0 - 4.0 * w0, u0 + 3.0 * w0, 0.0, 0.0};
-  const double d1[5] = {0.0, u1 + w1, -2.0 * u1, u1 - w1, 0.0};
-  const double d2[5] = {0.0, 0.0, u2 + 3.0 * w2, -2.0 * u2 - 4.0 * w2, u2 + w2};
+  const double u0 = 13.0 / 6.0 * s0, z0 = 0.5 * t0;
+  const double u1 = 13.0 / 6.0 * s1, z1 = 0.5 * t1;
+  const double u2 = 13.0 / 6.0 * s2, z2 = 0.5 * t2;
+  const double d0[5] = {u0 + z0, -2.0 * u0 - 4.0 * z0, u0 + 3.0 * z0, 0.0, 0.0};
+  const double d1[5] = {0.0, u1 + z1, -2.0 * u1, u1 - z1, 0.0};
+  const double d2[5] = {0.0, 0.0, u2 + 3.0 * z2, -2.0 * u2 - 4.0 * z2, u2 + z2};
   const double dq0[5] = {2.0 / 6.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0};
   const double dq1[5] = {0.0, -1.0 / 6.0, 5.0 / 6.0, 2.0 / 6.0, 0.0};
   const double dq2[5] = {0.0, 0.0, 2.0 / 6.0, 5.0 / 6.0, -1.0 / 6.0};
 #pragma unroll
   for (int k = 0; k < 5; k++)
-    g[k] = (a0 * dq0[k] + a1 * dq1[k] + a2 * dq2[k] + c0 * d0[k] + c1 * d1[k] + c2 * d2[k]) * iS;
+    g[k] = w0 * dq0[k] + w1 * dq1[k] + w2 * dq2[k] + c0 * d0[k] + c1 * d1[k] + c2 * d2[k];
 }
 
 // LF split fluxes fp = (F + a U)/2, fm = (F - a U)/2 of one primitive state
+// (ig1 = 1 / (gamma - 1))
 __device__ inline void split_state(double rho, double u, double v, double p, double g, double pi,
-                                   int d, double a, double fp[4], double fm[4]) {
-  double E = (p + g * pi) / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+                                   double ig1, int d, double a, double fp[4], double fm[4]) {
+  double E = (p + g * pi) * ig1 + 0.5 * rho * (u * u + v * v);
   double U[4] = {rho, rho * u, rho * v, E};
   double vn = d == 0 ? u : v;
   double F[4] = {rho * vn, rho * u * vn, rho * v * vn, vn * (E + p)};
@@ -110,7 +119,7 @@ __global__ void k_adj_face(Grid g, int k, int d, Planes4 W, const double *__rest
   const double h = d == 0 ? g.dx : g.dy;
   const double a = lf_value(lf, k, d);
   const double scale = fac * *dtp;
-  const double gm = g.gamma[k], pi = g.pinf[k];
+  const double gm = g.gamma[k], pi = g.pinf[k], ig1 = 1.0 / (gm - 1.0), ih = 1.0 / h;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf;
        t += (long long)gridDim.x * blockDim.x) {
     int i = (int)(t % nfx), j = (int)(t / nfx);
@@ -126,13 +135,14 @@ __global__ void k_adj_face(Grid g, int k, int d, Planes4 W, const double *__rest
 #pragma unroll
     for (int m = 0; m < 4; m++) {
       double r = has_r ? mu.p[m][c] : 0.0, l = has_l ? mu.p[m][c - s] : 0.0;
-      lF[m] = A * scale * (r - l) / h;
+      lF[m] = A * scale * (r - l) * ih;
     }
     double fp[6][4], fm[6][4];
 #pragma unroll
     for (int r = 0; r < 6; r++) {
       int cc = c + (r - 3) * s;
-      split_state(W.p[0][cc], W.p[1][cc], W.p[2][cc], W.p[3][cc], gm, pi, d, a, fp[r], fm[r]);
+      split_state(W.p[0][cc], W.p[1][cc], W.p[2][cc], W.p[3][cc], gm, pi, ig1, d, a, fp[r],
+                  fm[r]);
     }
 #pragma unroll
     for (int m = 0; m < 4; m++) {

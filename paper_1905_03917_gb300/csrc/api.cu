@@ -33,6 +33,7 @@ struct sif_ctx {
   double *partial;   // integrals: 8*ny partial sums + pointer table
   double *integ;     // 8 totals
   int *band_ev, *band_ls, *rext_ls, *cut, *tiles[2];
+  int *etiles;       // band tiles of the blocked extension
   unsigned char *nostate[2];  // per fluid: cut cells holding no physical state
   Scalars *sc;       // device
   Scalars *hsc;      // pinned host mirror
@@ -61,6 +62,8 @@ struct sif_ctx {
   int side_pending;
   int use_graphs;
   int no_graph_env;    // SIF_NO_GRAPH=1: cycles issued from the host on purpose
+  int ext_blocked;     // extension sweeps in shared memory per band tile (else one
+                       // launch per sweep or two; SIF_EXT_SWEEPS=1 asks for those)
   int require_graphs;  // SIF_REQUIRE_GRAPHS=1: a failed capture is an error
   int graph_bucket;  // band grid size baked into the graphs
   int num_sms;
@@ -157,6 +160,9 @@ static int validate(const sif_config *f, char *why, size_t n) {
   if (!(f->cfl > 0.0) || f->cfl > 1.0) return snprintf(why, n, "cfl must be in (0, 1]"), SIF_EINVAL;
   if (f->rk_order != 2 && f->rk_order != 3) return snprintf(why, n, "rk_order must be 2 or 3"), SIF_EINVAL;
   if (f->weno_char != 0 && f->weno_char != 1) return snprintf(why, n, "weno_char must be 0 or 1"), SIF_EINVAL;
+  if (f->flux != 0 && f->flux != 1) return snprintf(why, n, "flux must be 0 or 1"), SIF_EINVAL;
+  if (f->flux == 1 && f->weno_char)
+    return snprintf(why, n, "the HLLC flux reconstructs primitive states (weno_char 0)"), SIF_EINVAL;
   if (!(f->sigma >= 0.0 && f->sigma < 1e300)) return snprintf(why, n, "sigma must be finite and >= 0"), SIF_EINVAL;
   for (int k = 0; k < 2; k++)
     if (!(f->mu[k] >= 0.0 && f->mu[k] < 1e300)) return snprintf(why, n, "mu must be finite and >= 0"), SIF_EINVAL;
@@ -202,6 +208,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   }
   for (int i = 0; i < 4; i++) cudaStreamCreateWithFlags(&c->cap[i], cudaStreamNonBlocking);
   fv_prepare();
+  ext_prepare();
   {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -242,6 +249,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.ext_iters = f.ext_iters;
   g.reinit_iters = f.reinit_iters;
   g.weno_char = f.weno_char;
+  g.flux = f.flux;
   g.sigma = f.sigma;
   g.mu[0] = f.mu[0];
   g.mu[1] = f.mu[1];
@@ -252,6 +260,10 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
   g.ntx = (f.nx + g.tx - 1) / g.tx;
   g.nty = (f.ny + g.ty - 1) / g.ty;
   c->NP = (size_t)g.PX * g.PY;
+  {
+    const char *es = getenv("SIF_EXT_SWEEPS");
+    c->ext_blocked = ext_blocked_ok(g) && !(es && es[0] == '1');
+  }
 
   // one pool carved into 256-byte aligned pieces; a first pass over the
   // same carving (with a null base) measures the exact size
@@ -303,6 +315,7 @@ extern "C" int sif_create(const sif_config *cfg, sif_ctx **out) {
     c->cut = (int *)take(sizeof(int) * ncell);
     c->tiles[0] = (int *)take(sizeof(int) * ntiles);
     c->tiles[1] = (int *)take(sizeof(int) * ntiles);
+    c->etiles = (int *)take(sizeof(int) * ext_tiles(c->g));
     c->nostate[0] = (unsigned char *)take(c->NP);
     c->nostate[1] = (unsigned char *)take(c->NP);
     c->sc = (Scalars *)take(sizeof(Scalars));
@@ -465,7 +478,7 @@ static void geometry(sif_ctx *c, bool after_ls = false) {
   launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st,
                   band ? c->band_ev : nullptr, band ? &c->sc->n_band : nullptr,
                   band ? band_work(c) : 0);
-  launch_band_map(c->g, c->phi, c->band_ev, c->bandmap, &c->sc->n_band, c->st);
+  launch_band_map(c->g, c->phi, c->band_ev, c->bandmap, &c->sc->n_band, c->etiles, c->st);
   launch_tile_lists(c->g, c->phi, c->tiles[0], c->tiles[1], c->sc, c->st);
   dbg(c, "geometry");
 }
@@ -494,6 +507,28 @@ static void mix_pair(sif_ctx *c, int f1, double *const q1[4], double *const q2[4
   mix2(c, 3, f1 == 0 ? q1 : q2, f1 == 0 ? q2 : q1);
 }
 
+// extension plans of the three fields on the current geometry and the
+// extension of both fluids' stencil states (Sec. 2.3) over the band
+static void extend_states(sif_ctx *c) {
+  if (c->ext_blocked) {
+    launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band,
+                     c->bandmap, c->ext_plan, ncell(c), band_work(c), c->nostate, c->st, c->w[0],
+                     c->w[1], c->tmp, 1);
+    launch_ext_blocked(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
+                       c->etiles, &c->sc->n_band, c->bandmap, c->band_ev, band_work(c), c->tmp,
+                       c->alpha, c->nostate, c->sc, c->num_sms, c->st);
+    return;
+  }
+  // the plan kernel also takes the stencil states' first sweep
+  const bool first = c->g.ext_iters >= 1;
+  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
+                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st, c->w[0], c->w[1],
+                   first ? c->tmp : nullptr);
+  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
+                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
+                    c->sc, c->st, first ? 1 : 0);
+}
+
 // interaction step for stage states qs of both fluids and the current phi:
 // stencil states and their extension, interface Riemann problems, exchange
 // flux and the level-set velocity in cut cells (whose extension over the
@@ -514,14 +549,7 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
                ntile(c), c->nostate, c->sc, band_fluid, band_flag, c->band_ev,
                &c->sc->n_band, c->st);
   dbg(c, "prim");
-  // the plan kernel also takes the stencil states' first sweep
-  const bool first = c->g.ext_iters >= 1;
-  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
-                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st, c->w[0], c->w[1],
-                   first ? c->tmp : nullptr);
-  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
-                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
-                    c->sc, c->st, first ? 1 : 0);
+  extend_states(c);
   dbg(c, "extend");
   cudaMemsetAsync(c->ul[0], 0, sizeof(double) * c->NP, c->st);
   cudaMemsetAsync(c->ul[1], 0, sizeof(double) * c->NP, c->st);
@@ -538,9 +566,14 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
 // graph the sweeps are a branch beside that stage.
 static void ul_extend(sif_ctx *c) {
   side_branch(c, [&] {
-    launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
-                      band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
-                      c->sc, c->st);
+    if (c->ext_blocked)
+      launch_ext_blocked(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
+                         c->etiles, &c->sc->n_band, c->bandmap, c->band_ev, band_work(c), c->tmp,
+                         c->alpha, c->nostate, c->sc, c->num_sms, c->st);
+    else
+      launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
+                        band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
+                        c->sc, c->st);
   });
   dbg(c, "ls_extend");
 }
@@ -556,13 +589,7 @@ static void eval_third(sif_ctx *c, int f1) {
   launch_prim2(c->g, c->q[0], c->q[1], c->w[0], c->w[1], c->alpha, c->tiles[0], c->tiles[1],
                ntile(c), c->nostate, c->sc, -1, nullptr, c->band_ev, &c->sc->n_band, c->st,
                1 - f1);
-  const bool first = c->g.ext_iters >= 1;
-  launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
-                   c->ext_plan, ncell(c), band_work(c), c->nostate, c->st, c->w[0], c->w[1],
-                   first ? c->tmp : nullptr);
-  launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 0, 2, c->ext_plan, ncell(c),
-                    band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
-                    c->sc, c->st, first ? 1 : 0);
+  extend_states(c);
   launch_zero_cut(c->g, c->xn, c->xm, c->cut, &c->sc->n_cut, band_work(c), c->st);
   dbg(c, "third-stage evaluation");
 }
@@ -1760,11 +1787,11 @@ extern "C" int sif_tape_reset(sif_ctx *c, int capacity) {
     set_err(c, "the adjoint is defined for rk_order 2");
     return SIF_EINVAL;
   }
-  if (c->cfg.weno_char || c->cfg.sigma != 0.0 || c->cfg.mu[0] != 0.0 || c->cfg.mu[1] != 0.0 ||
-      c->cfg.tait[0] || c->cfg.tait[1]) {
-    set_err(c, "the adjoint is defined for the component-wise reconstruction (weno_char 0) "
-               "of the inviscid stiffened-gas model without surface tension (sigma 0, mu 0, "
-               "tait 0)");
+  if (c->cfg.weno_char || c->cfg.flux || c->cfg.sigma != 0.0 || c->cfg.mu[0] != 0.0 ||
+      c->cfg.mu[1] != 0.0 || c->cfg.tait[0] || c->cfg.tait[1]) {
+    set_err(c, "the adjoint is defined for the component-wise WENO-LF flux (weno_char 0, "
+               "flux 0) of the inviscid stiffened-gas model without surface tension (sigma 0, "
+               "mu 0, tait 0)");
     return SIF_EINVAL;
   }
   cudaSetDevice(c->cfg.device);

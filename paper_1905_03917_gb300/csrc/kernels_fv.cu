@@ -201,7 +201,58 @@ struct FvShape {
   // which matters when a fluid has few tiles (the sub-cycled fluid)
   static constexpr int threads = 2 * TX * TY;
   static_assert(threads >= TX * TY, "the open-cell count needs a thread per cell");
+  // the HLLC form's stencil states and reconstructed face states fit the
+  // split-flux layout's storage
+  static_assert(4 * (HX * TY + TX * HY) + 8 * nfaces <=
+                    4 * (2 * HX * TY + 2 * TX * HY) + 4 * nfaces,
+                "HLLC shared memory");
 };
+
+// phase 3: update of the block's SX x SY cells from the aperture-weighted
+// face fluxes FXo ([4][(SX+1)*SY]) and FYo ([4][SX*(SY+1)]) in shared
+// memory; count the cells with an open face of fluid k (the work unit of
+// the throughput figures)
+template <int SX, int SY>
+__device__ __forceinline__ void fv_update(const FvArgs &A, const double *FXo, const double *FYo,
+                                          int i0, int j0) {
+  const Grid &g = A.g;
+  const int k = A.k;
+  const bool d2 = g.dim == 2;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const double dt = *A.dtp;
+  const double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
+  const double sgn = k == 0 ? 1.0 : -1.0;
+  const double closed = k == 0 ? 1.0 : 0.0;  // aperture A_P of a face closed to fluid k
+  int open_cells = 0;
+  for (int r = tid; r < SX * SY; r += nth) {
+    int li = r % SX, lj = r / SX;
+    int i = i0 + li, j = j0 + lj;
+    if (i >= g.nx || j >= g.ny) continue;
+    int c = gidx(g, i, j);
+    bool open = A.ax[c] != closed || A.ax[c + 1] != closed;
+    if (d2) open = open || A.ay[c] != closed || A.ay[c + g.PX] != closed;
+    open_cells += open ? 1 : 0;
+    bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      const double *fx = FXo + m * (SX + 1) * SY + lj * (SX + 1) + li;
+      double L = (fx[0] - fx[1]) * inv_dx;
+      if (d2) {
+        const double *fy = FYo + m * SX * (SY + 1) + lj * SX + li;
+        L += (fy[0] - fy[SX]) * inv_dy;
+      }
+      if (m > 0 && cut) L += sgn * A.xn[m - 1][c] * inv_dxdy;
+      double cur = A.cur[m][c];
+      double out = A.s == 1 ? cur + dt * L : A.a * A.base[m][c] + A.b * (cur + dt * L);
+      A.dst[m][c] = out;
+    }
+  }
+  // every thread holds at most one cell here (a CTA has two threads per
+  // cell of its tile, see FvShape), so the count is a barrier count
+  const int nopen = __syncthreads_count(open_cells);
+  if (tid == 0 && nopen > 0)
+    atomicAdd((unsigned long long *)&A.sc->open_updates, (unsigned long long)nopen);
+}
 
 // the three phases over an SX x SY block of output cells at (i0, j0), with
 // the CTA's threads (any count)
@@ -398,88 +449,246 @@ __device__ __forceinline__ void fv_cells(const FvArgs &A, double *smem, int i0, 
     __syncthreads();
   }
 
-  // phase 3: update of the block's cells; count those with an open face of
-  // fluid k (the work unit of the throughput figures)
-  const double dt = *A.dtp;
-  const double inv_dx = 1.0 / g.dx, inv_dy = 1.0 / g.dy, inv_dxdy = 1.0 / (g.dx * g.dy);
-  const double sgn = k == 0 ? 1.0 : -1.0;
-  const double closed = k == 0 ? 1.0 : 0.0;  // aperture A_P of a face closed to fluid k
-  int open_cells = 0;
-  for (int r = tid; r < SX * SY; r += nth) {
-    int li = r % SX, lj = r / SX;
-    int i = i0 + li, j = j0 + lj;
-    if (i >= g.nx || j >= g.ny) continue;
-    int c = gidx(g, i, j);
-    bool open = A.ax[c] != closed || A.ax[c + 1] != closed;
-    if (d2) open = open || A.ay[c] != closed || A.ay[c + g.PX] != closed;
-    open_cells += open ? 1 : 0;
-    bool cut = (A.sx[c] != 0.0 || A.sy[c] != 0.0);
-#pragma unroll
-    for (int m = 0; m < 4; m++) {
-      const double *fx = FXo + m * (SX + 1) * SY + lj * (SX + 1) + li;
-      double L = (fx[0] - fx[1]) * inv_dx;
-      if (d2) {
-        const double *fy = FYo + m * SX * (SY + 1) + lj * SX + li;
-        L += (fy[0] - fy[SX]) * inv_dy;
-      }
-      if (m > 0 && cut) L += sgn * A.xn[m - 1][c] * inv_dxdy;
-      double cur = A.cur[m][c];
-      double out = A.s == 1 ? cur + dt * L : A.a * A.base[m][c] + A.b * (cur + dt * L);
-      A.dst[m][c] = out;
-    }
+  fv_update<SX, SY>(A, FXo, FYo, i0, j0);
+}
+
+// ---------------------------------------------------------------------
+// HLLC face flux (option flux = 1; Toro, Riemann Solvers and Numerical
+// Methods for Fluid Dynamics, Sec. 10.4): Davis's bounds S_L, S_R on the
+// outer waves, the contact speed S* from the momentum balance across them,
+// the star states U*_K = rho_K (S_K - un_K) / (S_K - S*) (1, S*, ut_K,
+// E_K / rho_K + (S* - un_K) (S* + p_K / (rho_K (S_K - un_K)))) and the
+// flux of the region holding the face.  W = (rho, u, v, p); F over (rho,
+// rho u, rho v, E) of direction d.
+
+__device__ __forceinline__ void euler_flux_state(const double W[4], double inv_gm1, double e0c,
+                                                 bool yd, double F[4], double U[4]) {
+  const double rho = W[0], u = W[1], v = W[2], p = W[3];
+  const double E = p * inv_gm1 + e0c + 0.5 * rho * (u * u + v * v);
+  const double un = yd ? v : u;
+  const double mn = rho * un;
+  U[0] = rho, U[1] = rho * u, U[2] = rho * v, U[3] = E;
+  F[0] = mn, F[1] = mn * u, F[2] = mn * v, F[3] = un * (E + p);
+  if (yd) F[2] += p;
+  else F[1] += p;
+}
+
+__device__ __forceinline__ void hllc_flux(const double WL[4], const double WR[4], double gm,
+                                          double pi, double inv_gm1, double e0c, bool yd,
+                                          double F[4]) {
+  const double rl = WL[0], rr = WR[0], pl = WL[3], pr = WR[3];
+  const double ul = yd ? WL[2] : WL[1], ur = yd ? WR[2] : WR[1];
+  const double cl = sqrt(gm * (pl + pi) / rl), cr = sqrt(gm * (pr + pi) / rr);
+  const double SL = fmin(ul - cl, ur - cr), SR = fmax(ul + cl, ur + cr);
+  double U[4];
+  if (SL >= 0.0 || SR <= 0.0) {
+    euler_flux_state(SL >= 0.0 ? WL : WR, inv_gm1, e0c, yd, F, U);
+    return;
   }
-  // every thread holds at most one cell here (a CTA has two threads per
-  // cell of its tile, see FvShape), so the count is a barrier count
-  const int nopen = __syncthreads_count(open_cells);
-  if (tid == 0 && nopen > 0)
-    atomicAdd((unsigned long long *)&A.sc->open_updates, (unsigned long long)nopen);
+  const double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) /
+                    (rl * (SL - ul) - rr * (SR - ur));
+  // the side of the contact the face lies on
+  const bool left = Ss >= 0.0;
+  const double *W = left ? WL : WR;
+  const double SK = left ? SL : SR, uK = left ? ul : ur;
+  euler_flux_state(W, inv_gm1, e0c, yd, F, U);
+  const double fac = W[0] * (SK - uK) / (SK - Ss);
+  double Us[4];
+  Us[0] = fac;
+  Us[1] = fac * (yd ? W[1] : Ss);
+  Us[2] = fac * (yd ? Ss : W[2]);
+  Us[3] = fac * (U[3] / W[0] + (Ss - uK) * (Ss + W[3] / (W[0] * (SK - uK))));
+#pragma unroll
+  for (int m = 0; m < 4; m++) F[m] = F[m] + SK * (Us[m] - U[m]);
+}
+
+// a WENO5 reconstruction as one value (the fraction over a reciprocal, a
+// division where the denominator leaves the reciprocal's range)
+__device__ __forceinline__ double weno5_value(double v1, double v2, double v3, double v4,
+                                              double v5, double eps12_13) {
+  double n, d;
+  weno5_frac(v1, v2, v3, v4, v5, eps12_13, n, d);
+  if (d < 0x1p1000 && isfinite(n)) return n * recip_newton3(d);
+  return n / d;
+}
+
+// the HLLC stage over an SX x SY block: (1) the stencil states of the
+// block's rows with x-halo and columns with y-halo, (2) per (face,
+// component) the WENO5 reconstructions from the left and from the right,
+// (3) per face the HLLC flux of the two reconstructed states (a state with
+// rho <= 0 or p + pinf <= 0 replaced by its cell's), times the aperture,
+// into the storage of (1), (4) the update
+template <int SX, int SY>
+__device__ __forceinline__ void fv_cells_hllc(const FvArgs &A, double *smem, int i0, int j0) {
+  constexpr int HX = SX + 6, HY = SY + 6;
+  constexpr int NXF = (SX + 1) * SY, NYF = SX * (SY + 1);
+  const Grid &g = A.g;
+  const int k = A.k;
+  double *wx = smem;                // [4][HX*SY]
+  double *wy = wx + 4 * HX * SY;    // [4][SX*HY]
+  double *WL = wy + 4 * SX * HY;    // [4][NXF + NYF], x faces then y faces
+  double *WR = WL + 4 * (NXF + NYF);
+  double *Fx = wx;                  // [4][NXF] (over wx, free after (2))
+  double *Fy = wy;                  // [4][NYF]
+  const double gm = g.gamma[k], pi = g.pinf[k];
+  const double inv_gm1 = 1.0 / (gm - 1.0), e0c = gm * pi * inv_gm1;
+  const bool d2 = g.dim == 2;
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  for (int r = tid; r < HX * SY; r += nth) {
+    int i = i0 - 3 + r % HX, j = j0 + r / HX;
+    const bool ok = i <= g.nx + 2 && j < g.ny;
+    const int c = ok ? gidx(g, i, j) : 0;
+#pragma unroll
+    for (int m = 0; m < 4; m++) wx[m * HX * SY + r] = ok ? A.w[m][c] : 0.0;
+  }
+  if (d2)
+    for (int r = tid; r < SX * HY; r += nth) {
+      int i = i0 + r % SX, j = j0 - 3 + r / SX;
+      const bool ok = i < g.nx && j <= g.ny + 2;
+      const int c = ok ? gidx(g, i, j) : 0;
+#pragma unroll
+      for (int m = 0; m < 4; m++) wy[m * SX * HY + r] = ok ? A.w[m][c] : 0.0;
+    }
+  __syncthreads();
+
+  const double eps = g.weno_eps * (12.0 / 13.0);  // see weno5_frac
+  constexpr int NXI = 4 * NXF;
+  const int NI = NXI + (d2 ? 4 * NYF : 0);
+  for (int r = tid; r < NI; r += nth) {
+    const double *P;
+    int st, slot;
+    if (r < NXI) {
+      const int m = r / NXF, f = r % NXF;
+      const int fi = f % (SX + 1), fj = f / (SX + 1);
+      // cells i-3..i+2 of face i are at halo columns fi..fi+5
+      P = wx + m * HX * SY + fj * HX + fi;
+      st = 1;
+      slot = m * (NXF + NYF) + f;
+    } else {
+      const int q = r - NXI, m = q / NYF, f = q % NYF;
+      const int fi = f % SX, fj = f / SX;
+      P = wy + m * SX * HY + fj * SX + fi;
+      st = SX;
+      slot = m * (NXF + NYF) + NXF + f;
+    }
+    WL[slot] = weno5_value(P[0], P[st], P[2 * st], P[3 * st], P[4 * st], eps);
+    WR[slot] = weno5_value(P[5 * st], P[4 * st], P[3 * st], P[2 * st], P[st], eps);
+  }
+  __syncthreads();
+
+  const int nfc = NXF + (d2 ? NYF : 0);
+  for (int r = tid; r < nfc; r += nth) {
+    const bool yd = r >= NXF;
+    const int f = yd ? r - NXF : r;
+    const int fi = yd ? f % SX : f % (SX + 1), fj = yd ? f / SX : f / (SX + 1);
+    const int i = i0 + fi, j = j0 + fj;
+    const bool open = yd ? (i < g.nx && j <= g.ny) : (i <= g.nx && j < g.ny);
+    double A_ = 0.0;
+    if (open) A_ = yd ? A.ay[gidx(g, i, j)] : A.ax[gidx(g, i, j)];
+    if (k == 0) A_ = 1.0 - A_;
+    double Fh[4] = {0.0, 0.0, 0.0, 0.0};
+    if (open && A_ != 0.0) {
+      const int cr = gidx(g, i, j), cl = yd ? gidx(g, i, j - 1) : gidx(g, i - 1, j);
+      double wl[4], wr[4];
+#pragma unroll
+      for (int m = 0; m < 4; m++) {
+        wl[m] = WL[m * (NXF + NYF) + r];
+        wr[m] = WR[m * (NXF + NYF) + r];
+      }
+      if (!(wl[0] > 0.0) || !(wl[3] + pi > 0.0))
+#pragma unroll
+        for (int m = 0; m < 4; m++) wl[m] = A.w[m][cl];
+      if (!(wr[0] > 0.0) || !(wr[3] + pi > 0.0))
+#pragma unroll
+        for (int m = 0; m < 4; m++) wr[m] = A.w[m][cr];
+      hllc_flux(wl, wr, gm, pi, inv_gm1, e0c, yd, Fh);
+    }
+    double *out = yd ? Fy + f : Fx + f;
+    const int nf = yd ? NYF : NXF;
+#pragma unroll
+    for (int m = 0; m < 4; m++) out[m * nf] = A_ * Fh[m];
+  }
+  __syncthreads();
+  fv_update<SX, SY>(A, Fx, Fy, i0, j0);
 }
 
 // A fluid with fewer active tiles than the GPU has SMs (the sub-cycled
 // fluid of a small region) has each tile computed by two CTAs, one half of
-// the tile each along its longer side: twice the SMs for the same face
-// fluxes (the halo share grows, the arithmetic per face is the same).
+// the tile each along its longer side, and with at most a quarter as many
+// tiles as SMs by four CTAs, quarters of the tile (along x when the tile is
+// at least four times as wide as high, else two by two): more SMs for the
+// same face fluxes (the halo share grows, the arithmetic per face is the
+// same).  Quarters of more tiles than that would put two CTAs on some SMs
+// and finish later than halves.
 template <int TX, int TY>
 struct FvHalf {
   static constexpr bool along_x = TX >= TY;
   static constexpr int SX = along_x ? TX / 2 : TX, SY = along_x ? TY : TY / 2;
+  __device__ static void origin(int part, int &i0, int &j0) {
+    if (part) {
+      if (along_x) i0 += SX;
+      else j0 += SY;
+    }
+  }
+};
+template <int TX, int TY>
+struct FvQuarter {
+  static constexpr bool along_x = TX >= 4 * TY;
+  static constexpr int SX = along_x ? TX / 4 : TX / 2, SY = along_x ? TY : TY / 2;
+  __device__ static void origin(int part, int &i0, int &j0) {
+    if (along_x) {
+      i0 += part * SX;
+    } else {
+      i0 += (part & 1) * SX;
+      j0 += (part >> 1) * SY;
+    }
+  }
 };
 
-// CH: characteristic-wise reconstruction (more registers a thread: two
-// CTAs per SM instead of three)
-template <int TX, int TY, bool CH>
+// MODE: 0 WENO5-LF per component, 1 WENO5-LF on characteristic fields, 2
+// HLLC (1 and 2 take more registers a thread: two CTAs per SM, not three)
+template <int TX, int TY, int MODE>
 __global__ void __launch_bounds__(FvShape<TX, TY>::threads,
-                                  (CH ? 1024 : 1536) / FvShape<TX, TY>::threads)
+                                  (MODE == 0 ? 1536 : 1024) / FvShape<TX, TY>::threads)
 k_fv_stage(FvArgs A) {
   SIF_TICK();
   const Grid &g = A.g;
   const int ntiles = A.ntiles[A.k];
-  const bool split = ntiles < A.split_below;
-  const int t = split ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  // CTAs per tile (the grid holds at least twice as many CTAs as SMs):
+  // quarters only while every quarter still gets an SM of its own
+  const int parts = 4 * ntiles <= A.split_below ? 4 : (ntiles < A.split_below ? 2 : 1);
+  const int t = (int)blockIdx.x / parts, part = (int)blockIdx.x % parts;
   if (t >= ntiles) return;
   extern __shared__ double smem[];
   const int tile = A.tiles[t];
   int i0 = (tile % g.ntx) * TX, j0 = (tile / g.ntx) * TY;
   using H = FvHalf<TX, TY>;
-  if (split) {
-    if (blockIdx.x & 1) {
-      if (H::along_x) i0 += H::SX;
-      else j0 += H::SY;
-    }
-  }
+  using Q = FvQuarter<TX, TY>;
+  if (parts == 2) H::origin(part, i0, j0);
+  if (parts == 4) Q::origin(part, i0, j0);
   if (threadIdx.x == 0) {
-    int w_ = min(split ? H::SX : TX, g.nx - i0), h_ = min(split ? H::SY : TY, g.ny - j0);
+    const int bw = parts == 4 ? Q::SX : (parts == 2 ? H::SX : TX);
+    const int bh = parts == 4 ? Q::SY : (parts == 2 ? H::SY : TY);
+    int w_ = min(bw, g.nx - i0), h_ = min(bh, g.ny - j0);
     if (w_ > 0 && h_ > 0)
       atomicAdd((unsigned long long *)&A.sc->updates, (unsigned long long)(w_ * h_));
   }
   const bool timed = A.sc->timing;
   if (timed && threadIdx.x == 0) atomicMin((unsigned long long *)&A.sc->fv_t0, globaltimer_ns());
-  if (split) fv_cells<H::SX, H::SY, CH>(A, smem, i0, j0);
-  else fv_cells<TX, TY, CH>(A, smem, i0, j0);
+  if constexpr (MODE == 2) {
+    if (parts == 4) fv_cells_hllc<Q::SX, Q::SY>(A, smem, i0, j0);
+    else if (parts == 2) fv_cells_hllc<H::SX, H::SY>(A, smem, i0, j0);
+    else fv_cells_hllc<TX, TY>(A, smem, i0, j0);
+  } else {
+    constexpr bool CH = MODE == 1;
+    if (parts == 4) fv_cells<Q::SX, Q::SY, CH>(A, smem, i0, j0);
+    else if (parts == 2) fv_cells<H::SX, H::SY, CH>(A, smem, i0, j0);
+    else fv_cells<TX, TY, CH>(A, smem, i0, j0);
+  }
   if (timed) {
     __syncthreads();
-    if (threadIdx.x == 0)
-      fv_timer_block_done(A.sc, (unsigned int)(split ? 2 * ntiles : ntiles));
+    if (threadIdx.x == 0) fv_timer_block_done(A.sc, (unsigned int)(parts * ntiles));
   }
 }
 
@@ -502,11 +711,13 @@ bool fv_shape_supported(int tx, int ty) {
 static int g_fv_priority = 0;
 
 void fv_prepare() {
-#define FV_PREP(a, b)                                                                          \
-  cudaFuncSetAttribute(k_fv_stage<a, b, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                       (int)FvShape<a, b>::smem());                                          \
-  cudaFuncSetAttribute(k_fv_stage<a, b, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                       (int)FvShape<a, b>::smem_char());
+#define FV_PREP(a, b)                                                                      \
+  cudaFuncSetAttribute(k_fv_stage<a, b, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)FvShape<a, b>::smem());                                      \
+  cudaFuncSetAttribute(k_fv_stage<a, b, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)FvShape<a, b>::smem_char());                                 \
+  cudaFuncSetAttribute(k_fv_stage<a, b, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)FvShape<a, b>::smem());
   FV_SHAPES(FV_PREP)
 #undef FV_PREP
   int least = 0, greatest = 0;
@@ -560,10 +771,13 @@ void launch_fv_stage(const Grid &g, int k, int s, int rk, double *const dst[4],
     cfg.blockDim = dim3(FvShape<a, b>::threads);          \
     if (g.weno_char) {                                    \
       cfg.dynamicSmemBytes = FvShape<a, b>::smem_char();  \
-      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, true>, A);  \
+      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, 1>, A);   \
+    } else if (g.flux == 1) {                             \
+      cfg.dynamicSmemBytes = FvShape<a, b>::smem();       \
+      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, 2>, A);   \
     } else {                                              \
       cfg.dynamicSmemBytes = FvShape<a, b>::smem();       \
-      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, false>, A); \
+      cudaLaunchKernelEx(&cfg, k_fv_stage<a, b, 0>, A);   \
     }                                                     \
     return;                                               \
   }

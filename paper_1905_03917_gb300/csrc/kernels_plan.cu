@@ -18,39 +18,49 @@ static int blocks_for(int n, int per) {
 // ---------------------------------------------------------------------
 // interaction band and its map
 
+int ext_tiles(const Grid &g) {
+  return ((g.nx + SIF_ETILE - 1) / SIF_ETILE) * ((g.ny + SIF_ETILE - 1) / SIF_ETILE);
+}
+
+// one CTA per SIF_ETILE x SIF_ETILE tile: its band cells join the band list
+// (warp-aggregated positions) and the map, and a tile holding any of them
+// joins the extension tile list
 __global__ void k_band_mapped(Grid g, const double *__restrict__ p, int *band, int *map,
-                              int *nband) {
+                              int *nband, int *etiles) {
   SIF_TICK();
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = t % g.nx, j = t / g.nx;
+  const int tilesx = (g.nx + SIF_ETILE - 1) / SIF_ETILE;
+  const int i = (blockIdx.x % tilesx) * SIF_ETILE + (threadIdx.x % SIF_ETILE);
+  const int j = (blockIdx.x / tilesx) * SIF_ETILE + (threadIdx.x / SIF_ETILE);
   bool in = false;
   int c = 0;
-  if (j < g.ny) {
+  if (i < g.nx && j < g.ny) {
     c = gidx(g, i, j);
     in = fabs(p[c]) < g.band * g.h;
   }
   unsigned mask = __ballot_sync(0xffffffffu, in);
-  if (!mask) return;
-  int lane = threadIdx.x & 31, lead = __ffs(mask) - 1;
-  int base = 0;
-  if (lane == lead) base = atomicAdd(nband, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, lead);
-  if (in) {
-    int pos = base + __popc(mask & ((1u << lane) - 1u));
-    band[pos] = c;
-    map[c] = pos;
+  if (mask) {
+    int lane = threadIdx.x & 31, lead = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == lead) base = atomicAdd(nband, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (in) {
+      int pos = base + __popc(mask & ((1u << lane) - 1u));
+      band[pos] = c;
+      map[c] = pos;
+    }
   }
+  if (__syncthreads_or(in) && threadIdx.x == 0) etiles[atomicAdd(nband + 1, 1)] = blockIdx.x;
 }
 
 // the whole map is cleared (not only the previous band's entries): a reset
 // of the device scalars (initialisation, checkpoint restore) loses the
 // previous band's count, and the clear must not depend on it
 void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
-                     cudaStream_t st) {
-  int n = g.nx * g.ny;
+                     int *etiles, cudaStream_t st) {
   cudaMemsetAsync(map, 0xff, sizeof(int) * (size_t)g.PX * g.PY, st);
-  cudaMemsetAsync(nband, 0, sizeof(int), st);
-  k_band_mapped<<<(n + 255) / 256, 256, 0, st>>>(g, phi, band, map, nband);
+  cudaMemsetAsync(nband, 0, 2 * sizeof(int), st);
+  k_band_mapped<<<ext_tiles(g), SIF_ETILE * SIF_ETILE, 0, st>>>(g, phi, band, map, nband,
+                                                               etiles);
   sif_note_launches(1);
 }
 
@@ -74,7 +84,8 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
                             const double *__restrict__ sy, const int *__restrict__ band,
                             const int *nband, const int *__restrict__ map, ExtPlan *plan,
                             int cap, const unsigned char *__restrict__ ns0,
-                            const unsigned char *__restrict__ ns1, ExtFields F, double *sweep0) {
+                            const unsigned char *__restrict__ ns1, ExtFields F, double *sweep0,
+                            int copy) {
   SIF_TICK();
   const int f = blockIdx.y;  // field: W_N, W_P, level-set velocity
   int n = *nband;
@@ -120,13 +131,14 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
       }
       plan[(size_t)f * cap + idx] = pl;
       // the first sweep of the stencil states (k_ext_sweep without a
-      // previous sweep), while the plan is at hand
+      // previous sweep), while the plan is at hand; for the blocked
+      // extension the band cells' own values instead
       if (sweep0 && f < 2) {
 #pragma unroll
         for (int m = 0; m < 4; m++) {
           const double *a = F.p[f][m];
           double v;
-          if (pl.cx < 0 && pl.cy < 0) {
+          if (copy || (pl.cx < 0 && pl.cy < 0)) {
             v = a[c];
           } else {
             v = 0.0;
@@ -144,7 +156,7 @@ void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, con
                       const double *sy, const int *band, const int *nband, const int *map,
                       ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
                       cudaStream_t st, double *const wN[4], double *const wP[4],
-                      double *sweep0) {
+                      double *sweep0, int copy) {
   ExtFields F = {};
   if (sweep0)
     for (int m = 0; m < 4; m++) {
@@ -153,7 +165,8 @@ void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, con
     }
   // one block row per field
   k_ext_setup<<<dim3(blocks_for(work, 64), 3), 64, 0, st>>>(
-      g, alpha, phi, sx, sy, band, nband, map, plan, cap, nostate[0], nostate[1], F, sweep0);
+      g, alpha, phi, sx, sy, band, nband, map, plan, cap, nostate[0], nostate[1], F, sweep0,
+      copy);
   sif_note_launches(1);
 }
 
@@ -352,6 +365,228 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
     launched++;
   }
   sif_note_launches(launched);
+}
+
+// ---------------------------------------------------------------------
+// blocked extension: all Jacobi sweeps of a band tile in shared memory.
+// A CTA loads its tile with a halo of g.ext_iters cells (every field value
+// there: band cells at their pre-extension values, others constant), the
+// targets' upwind neighbours and weights, and runs the sweeps in place.  A
+// target on the region's rim whose neighbour lies outside keeps a stale
+// value; staleness moves one cell per sweep, so after g.ext_iters sweeps
+// the tile itself holds the values the band-wide Jacobi iteration gives,
+// each computed by the same operations in the same order.
+//
+// Where the pre-extension band values come from decides where the results
+// may go.  The stencil states' band values are copied to a band-indexed
+// buffer by the plan kernel (k_ext_setup): the CTAs read band cells only
+// there and other cells only from the planes, so each writes its tile's
+// band values straight into the planes (and folds their wave speeds).  The
+// level-set velocity's band values are read from the planes, so its
+// results go to a band-indexed buffer and a second launch writes them back.
+
+constexpr int EXT_THREADS = 512;
+constexpr int EXT_RW_MAX = SIF_ETILE + 2 * SIF_EXT_BLOCKED_MAX;
+// region cells (and targets) a thread holds
+constexpr int EXT_PER = (EXT_RW_MAX * EXT_RW_MAX + EXT_THREADS - 1) / EXT_THREADS;
+
+static size_t ext_blocked_smem(int nc, int H) {
+  const size_t rw = SIF_ETILE + 2 * H, r = rw * rw;
+  // values, then per target: two weights, packed neighbours, region index;
+  // per region cell its band position
+  return r * (sizeof(double) * (nc + 2) + 3 * sizeof(int));
+}
+
+bool ext_blocked_ok(const Grid &g) {
+  return g.ext_iters >= 1 && g.ext_iters <= SIF_EXT_BLOCKED_MAX;
+}
+
+// DIRECT: band values from bandin (4 x cap per field, band-indexed), results
+// into the planes with the wave-speed fold; else band values from the
+// planes, results into out (4 x cap per field)
+template <int NC, bool DIRECT>
+__global__ void __launch_bounds__(EXT_THREADS)
+k_ext_blocked(Grid g, ExtFields F, int f0, const ExtPlan *__restrict__ plan, int cap,
+              const int *__restrict__ etiles, const int *nband, const int *__restrict__ map,
+              const double *__restrict__ bandin, double *out, const double *__restrict__ alpha,
+              const unsigned char *__restrict__ ns0, const unsigned char *__restrict__ ns1,
+              Scalars *sc) {
+  SIF_TICK();
+  extern __shared__ double esm[];
+  __shared__ int s_nt;
+  const int f = f0 + blockIdx.y;
+  const int H = g.ext_iters, RW = SIF_ETILE + 2 * H, R = RW * RW;
+  double *val = esm;              // NC x R
+  double *wxs = val + NC * R;     // per target
+  double *wys = wxs + R;
+  int *nbs = (int *)(wys + R);    // neighbours' region indices + 1 (x low, y high half)
+  int *tls = nbs + R;             // target's region index
+  int *bps = tls + R;             // region cell's band position (-1: none)
+  const ExtPlan *P = plan + (size_t)f * cap;
+  const double *in = DIRECT ? bandin + (size_t)f * 4 * cap : nullptr;
+  double *o = DIRECT ? nullptr : out + (size_t)blockIdx.y * 4 * cap;
+  const unsigned char *ns = f == 0 ? ns0 : ns1;
+  const int tilesx = (g.nx + SIF_ETILE - 1) / SIF_ETILE;
+  const int nt_tiles = nband[1];
+  const int tid = threadIdx.x;
+  double lx = 0.0, ly = 0.0;
+  for (int q = blockIdx.x; q < nt_tiles; q += gridDim.x) {
+    const int et = etiles[q];
+    const int ri0 = (et % tilesx) * SIF_ETILE - H, rj0 = (et / tilesx) * SIF_ETILE - H;
+    if (tid == 0) s_nt = 0;
+    // the region's band positions and plane values, then the band cells'
+    // plans (and buffered values): two dependent load levels in all
+    int cc[EXT_PER], bp[EXT_PER];
+    double v[EXT_PER][NC];
+#pragma unroll
+    for (int l = 0; l < EXT_PER; l++) {
+      const int r = tid + l * EXT_THREADS;
+      const int i = ri0 + r % RW, j = rj0 + r / RW;
+      const bool ok = r < R && i >= 0 && j >= 0 && i < g.nx && j < g.ny;
+      cc[l] = ok ? gidx(g, i, j) : -1;
+      bp[l] = ok ? map[cc[l]] : -1;
+    }
+    ExtPlan pl[EXT_PER];
+#pragma unroll
+    for (int l = 0; l < EXT_PER; l++) {
+      pl[l] = ExtPlan{-1, -1, -1, -1, 0.0, 0.0};
+      if (bp[l] >= 0) pl[l] = P[bp[l]];
+      // band values (the planes' band cells are being written by other
+      // CTAs in the direct form), else the planes
+      const bool buffered = DIRECT && bp[l] >= 0;
+#pragma unroll
+      for (int m = 0; m < NC; m++)
+        v[l][m] = buffered ? in[(size_t)m * cap + bp[l]] : (cc[l] >= 0 ? F.p[f][m][cc[l]] : 0.0);
+    }
+    __syncthreads();  // s_nt is set
+#pragma unroll
+    for (int l = 0; l < EXT_PER; l++) {
+      const int r = tid + l * EXT_THREADS;
+      if (r >= R) continue;
+      bps[r] = bp[l];
+#pragma unroll
+      for (int m = 0; m < NC; m++) val[m * R + r] = v[l][m];
+      if (pl[l].cx < 0 && pl[l].cy < 0) continue;
+      const int li = r % RW, lj = r / RW, c = cc[l];
+      int nx_ = -1, ny_ = -1;
+      bool rim = false;
+      if (pl[l].cx >= 0) {
+        const int d = pl[l].cx - c;  // +-1
+        if (li + d < 0 || li + d >= RW) rim = true;
+        else nx_ = r + d;
+      }
+      if (pl[l].cy >= 0) {
+        const int d = (pl[l].cy - c) / g.PX;  // +-1
+        if (lj + d < 0 || lj + d >= RW) rim = true;
+        else ny_ = r + d * RW;
+      }
+      if (rim) continue;
+      const int k = atomicAdd(&s_nt, 1);
+      tls[k] = r;
+      wxs[k] = pl[l].wx;
+      wys[k] = pl[l].wy;
+      nbs[k] = (nx_ + 1) | ((ny_ + 1) << 16);
+    }
+    __syncthreads();
+    const int nt = s_nt;
+    for (int s = 0; s < H; s++) {
+      double nv[EXT_PER][NC];
+#pragma unroll
+      for (int kk = 0; kk < EXT_PER; kk++) {
+        const int k = tid + kk * EXT_THREADS;
+        if (k < nt) {
+          const int nb = nbs[k], nx_ = (nb & 0xffff) - 1, ny_ = (nb >> 16) - 1;
+          const double wx = wxs[k], wy = wys[k];
+#pragma unroll
+          for (int m = 0; m < NC; m++) {
+            double x = 0.0;
+            if (nx_ >= 0) x += wx * val[m * R + nx_];
+            if (ny_ >= 0) x += wy * val[m * R + ny_];
+            nv[kk][m] = x;
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < EXT_PER; kk++) {
+        const int k = tid + kk * EXT_THREADS;
+        if (k < nt) {
+          const int r = tls[k];
+#pragma unroll
+          for (int m = 0; m < NC; m++) val[m * R + r] = nv[kk][m];
+        }
+      }
+      __syncthreads();
+    }
+    // the tile's band cells
+    for (int r = tid; r < SIF_ETILE * SIF_ETILE; r += EXT_THREADS) {
+      const int li = H + r % SIF_ETILE, lj = H + r / SIF_ETILE;
+      const int i = ri0 + li, j = rj0 + lj;
+      if (i >= g.nx || j >= g.ny) continue;
+      const int rr = lj * RW + li, b = bps[rr];
+      if (b < 0) continue;
+      if (DIRECT) {
+        const int c = gidx(g, i, j);
+#pragma unroll
+        for (int m = 0; m < NC; m++) F.p[f][m][c] = val[m * R + rr];
+        if (!(vol_k(alpha, f, c) > SIF_ALPHA_REAL) || ns[c]) {
+          const double rho = val[rr], u = val[R + rr], vv = val[2 * R + rr],
+                       p = val[3 * R + rr];
+          const double cs = sqrt(fmax(F.gamma[f] * (p + F.pinf[f]) / rho, 0.0));
+          lx = fmax(lx, fabs(u) + cs);
+          ly = fmax(ly, fabs(vv) + cs);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < NC; m++) o[(size_t)m * cap + b] = val[m * R + rr];
+      }
+    }
+    __syncthreads();
+  }
+  if (DIRECT) ext_fold_lf(lx, ly, sc->lf[f]);
+}
+
+void ext_prepare() {
+  cudaFuncSetAttribute(k_ext_blocked<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ext_blocked_smem(4, SIF_EXT_BLOCKED_MAX));
+  cudaFuncSetAttribute(k_ext_blocked<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ext_blocked_smem(2, SIF_EXT_BLOCKED_MAX));
+  cudaGetLastError();
+}
+
+void launch_ext_blocked(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
+                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap,
+                        const int *etiles, const int *nband, const int *map, const int *band,
+                        int work, double *tmp, const double *alpha,
+                        const unsigned char *const nostate[2], Scalars *sc, int num_sms,
+                        cudaStream_t st) {
+  ExtFields F;
+  for (int m = 0; m < 4; m++) {
+    F.p[0][m] = wN[m];
+    F.p[1][m] = wP[m];
+    F.p[2][m] = m == 0 ? ul0 : (m == 1 ? ul1 : nullptr);
+  }
+  F.ncomp[0] = F.ncomp[1] = 4;
+  F.ncomp[2] = 2;
+  for (int k = 0; k < 2; k++) {
+    F.gamma[k] = g.gamma[k];
+    F.pinf[k] = g.pinf[k];
+  }
+  const int nt = ext_tiles(g);
+  dim3 grid(nt < 2 * num_sms ? nt : 2 * num_sms, nf);
+  if (f0 < 2) {
+    // the stencil states' band values are in tmp (k_ext_setup's copy)
+    k_ext_blocked<4, true><<<grid, EXT_THREADS, ext_blocked_smem(4, g.ext_iters), st>>>(
+        g, F, f0, plan, cap, etiles, nband, map, tmp, nullptr, alpha, nostate[0], nostate[1],
+        sc);
+    sif_note_launches(1);
+    return;
+  }
+  k_ext_blocked<2, false><<<grid, EXT_THREADS, ext_blocked_smem(2, g.ext_iters), st>>>(
+      g, F, f0, plan, cap, etiles, nband, map, nullptr, tmp, alpha, nostate[0], nostate[1], sc);
+  k_ext_scatter<<<dim3(blocks_for(work, 64), nf), 64, 0, st>>>(g, F, f0, cap, band, nband, tmp,
+                                                               alpha, nostate[0], nostate[1], sc);
+  sif_note_launches(2);
 }
 
 // ---------------------------------------------------------------------

@@ -34,6 +34,7 @@ struct Grid {
   double cfl, weno_eps, mix_alpha, band;
   int ext_iters, reinit_iters;
   int weno_char;  // finite-volume reconstruction on characteristic fields
+  int flux;       // face flux: 0 WENO5-LF, 1 HLLC on WENO5 primitive states
   double sigma;   // surface tension coefficient (Eq. 10), 0 = none
   double mu[2];   // dynamic viscosities of fluids N and P, 0 = inviscid
   int tx, ty;    // finite-volume tile shape (output cells per CTA)
@@ -57,7 +58,7 @@ struct Scalars {
   double n_raw, n_used;
   int f1, mode, last, sub;
   int err;
-  int n_band, n_band_spare;   // interaction-step band (and unused slot)
+  int n_band, n_etile;        // interaction-step band and its extension tiles
   int n_band_ls, n_rext;      // level-set step band and its face neighbours
   int n_cut, n_tiles[2];
   double dtk_raw[2];
@@ -396,8 +397,27 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
                        cudaStream_t st);
 void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
                        cudaStream_t st);
+// band list and map, and the list of SIF_ETILE^2 tiles holding band cells
+// (count in nband[1]) for the blocked extension
 void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
-                     cudaStream_t st);
+                     int *etiles, cudaStream_t st);
+// edge of the square tiles of the blocked extension
+#define SIF_ETILE 16
+// sweep counts the blocked extension takes (its tile's halo is that wide)
+#define SIF_EXT_BLOCKED_MAX 12
+int ext_tiles(const Grid &g);
+bool ext_blocked_ok(const Grid &g);
+// all g.ext_iters Jacobi sweeps of fields [f0, f0 + nf) (W_N and W_P
+// together, from the band values launch_ext_setup copied to tmp, or the
+// level-set velocity alone) over the band tiles, with the write-back of the
+// band values (and the stencil states' wave speeds)
+void launch_ext_blocked(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
+                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap,
+                        const int *etiles, const int *nband, const int *map, const int *band,
+                        int work, double *tmp, const double *alpha,
+                        const unsigned char *const nostate[2], Scalars *sc, int num_sms,
+                        cudaStream_t st);
+void ext_prepare();
 void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[4],
                  const double *alpha, const double *phi, const int *band, const int *map,
                  const int *nband, MixPlan *plan, int cap, int work, double *tmp,
@@ -405,12 +425,14 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
 // nostate[k]: 1 where a cut cell of fluid k holds no physical state (set by
 // the primitive recovery of the same interaction step)
 // sweep0 != null: also the first Jacobi sweep of both fluids' stencil
-// states wN, wP into the sweep buffer (then launch_ext_sweeps with first_done)
+// states wN, wP into the sweep buffer (then launch_ext_sweeps with
+// first_done), or with copy the band cells' own values (then
+// launch_ext_blocked, which reads them there)
 void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, const double *sx,
                       const double *sy, const int *band, const int *nband, const int *map,
                       ExtPlan *plan, int cap, int work, const unsigned char *const nostate[2],
                       cudaStream_t st, double *const wN[4] = nullptr,
-                      double *const wP[4] = nullptr, double *sweep0 = nullptr);
+                      double *const wP[4] = nullptr, double *sweep0 = nullptr, int copy = 0);
 // f0 = 0, nf = 2: stencil states of both fluids; f0 = 2, nf = 1: level-set velocity
 void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], double *ul0,
                        double *ul1, int f0, int nf, const ExtPlan *plan, int cap, int work,

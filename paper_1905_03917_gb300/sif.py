@@ -37,6 +37,9 @@ class SifError(RuntimeError):
         self.code = code
 
 
+# face fluxes of the finite-volume stage: WENO5-LF (the paper's), HLLC
+FLUXES = {"lf": 0, "hllc": 1}
+
 class Config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double),
@@ -53,7 +56,7 @@ class Config(ctypes.Structure):
                 ("weno_char", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("mu", ctypes.c_double * 2), ("tait", ctypes.c_int * 2),
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
-                ("tait_p0", ctypes.c_double * 2)]
+                ("tait_p0", ctypes.c_double * 2), ("flux", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -160,6 +163,10 @@ def make_config(cfg: dict, stream=None, device=0) -> Config:
     mu = cfg.get("mu", (0.0, 0.0))
     c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
     # Tait's equation per fluid: (B, rho0, p0), or None for a stiffened gas
+    fl = cfg.get("flux", "lf")
+    if fl not in FLUXES:
+        raise ValueError(f"flux must be one of {sorted(FLUXES)}")
+    c.flux = FLUXES[fl]
     for k, t in enumerate(cfg.get("tait", (None, None))):
         if t is not None:
             c.tait[k] = 1

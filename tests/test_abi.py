@@ -81,3 +81,19 @@ def test_invalid_physics_options_are_rejected_without_gpu_work(field, value):
     h = ctypes.c_void_p()
     assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
     assert not h.value
+
+
+def test_invalid_face_flux_options_are_rejected_without_gpu_work():
+    from paper_1905_03917_gb300 import inputs
+    lib = sif.load()
+    cfg = dict(inputs.shock_tube_1d(64)["cfg"], flux="hllc", weno_char=1)
+    c = sif.make_config(cfg)
+    h = ctypes.c_void_p()
+    assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
+    assert not h.value
+    c = sif.make_config(inputs.shock_tube_1d(64)["cfg"])
+    c.flux = 2
+    assert lib.sif_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
+    assert not h.value
+    with pytest.raises(ValueError):
+        sif.make_config(dict(inputs.shock_tube_1d(64)["cfg"], flux="roe"))
