@@ -97,6 +97,10 @@ __device__ inline void split_state(double rho, double u, double v, double p, dou
 // derivative of both reconstructions weighted by lamF:
 //   G[r*4+m]      -> split flux fp of cell c + (r-3)s, r = 0..4
 //   G[20 + r*4+m] -> split flux fm of cell c + (2-r)s, r = 0..4
+// The split fluxes of every cell the faces read (ghost layers included)
+// are computed once per (fluid, direction) into SP (fp then fm, four
+// planes each); the face kernel then takes one (face, component) per
+// thread.
 
 struct Planes4 {
   double *p[4];
@@ -108,54 +112,71 @@ struct Planes40 {
   double *p[40];
 };
 
-__global__ void k_adj_face(Grid g, int k, int d, Planes4 W, const double *__restrict__ aperture,
-                           Planes4 mu, const unsigned long long *lf, const double *dtp,
-                           double fac, Planes40 G) {
+// plane base + m of a parameter array, m in 0..3 chosen without indexing
+// the parameter array dynamically (which would copy it to local memory)
+template <class P>
+__device__ __forceinline__ double *plane_m(const P &pl, int base, int m) {
+  return m == 0 ? pl.p[base] : m == 1 ? pl.p[base + 1] : m == 2 ? pl.p[base + 2] : pl.p[base + 3];
+}
+
+__global__ void k_adj_split(Grid g, int k, int d, Planes4 W, const unsigned long long *lf,
+                            Planes8 SP) {
+  SIF_TICK();
+  // cells -3 .. n+2 along d, 0 .. n-1 across
+  const int ncx = d == 0 ? g.nx + 2 * SIF_GH : g.nx;
+  const int ncy = d == 0 ? g.ny : g.ny + 2 * SIF_GH;
+  const int ox = d == 0 ? -SIF_GH : 0, oy = d == 0 ? 0 : -SIF_GH;
+  const long long n = (long long)ncx * ncy;
+  const double a = lf_value(lf, k, d);
+  const double gm = g.gamma[k], pi = g.pinf[k], ig1 = 1.0 / (gm - 1.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = gidx(g, (int)(t % ncx) + ox, (int)(t / ncx) + oy);
+    double fp[4], fm[4];
+    split_state(W.p[0][c], W.p[1][c], W.p[2][c], W.p[3][c], gm, pi, ig1, d, a, fp, fm);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      SP.p[m][c] = fp[m];
+      SP.p[4 + m][c] = fm[m];
+    }
+  }
+}
+
+__global__ void k_adj_face(Grid g, int k, int d, Planes8 SP, const double *__restrict__ aperture,
+                           Planes4 mu, const double *dtp, double fac, Planes40 G) {
   SIF_TICK();
   const int nfx = d == 0 ? g.nx + 1 : g.nx;
   const int nfy = d == 0 ? g.ny : g.ny + 1;
   const long long nf = (long long)nfx * nfy;
   const int s = d == 0 ? 1 : g.PX;
-  const double h = d == 0 ? g.dx : g.dy;
-  const double a = lf_value(lf, k, d);
+  const double ih = 1.0 / (d == 0 ? g.dx : g.dy);
   const double scale = fac * *dtp;
-  const double gm = g.gamma[k], pi = g.pinf[k], ig1 = 1.0 / (gm - 1.0), ih = 1.0 / h;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 4 * nf;
        t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t % nfx), j = (int)(t / nfx);
-    int c = gidx(g, i, j);
-    double ap = aperture[c];
-    double A = k == 1 ? ap : 1.0 - ap;
+    const int m = (int)(t / nf);
+    const long long f = t % nf;
+    const int i = (int)(f % nfx), j = (int)(f / nfx);
+    const int c = gidx(g, i, j);
+    const double ap = aperture[c];
+    const double A = k == 1 ? ap : 1.0 - ap;
     // a face closed to fluid k contributes nothing: its coefficients are
     // neither written here nor read by the gather
     if (A == 0.0) continue;
-    bool has_r = d == 0 ? i < g.nx : j < g.ny;
-    bool has_l = d == 0 ? i > 0 : j > 0;
-    double lF[4];
+    const bool has_r = d == 0 ? i < g.nx : j < g.ny;
+    const bool has_l = d == 0 ? i > 0 : j > 0;
+    const double *mum = plane_m(mu, 0, m);
+    const double r_ = has_r ? mum[c] : 0.0, l_ = has_l ? mum[c - s] : 0.0;
+    const double lF = A * scale * (r_ - l_) * ih;
+    const double *fp = plane_m(SP, 0, m), *fm = plane_m(SP, 4, m);
+    const double vp[5] = {fp[c - 3 * s], fp[c - 2 * s], fp[c - s], fp[c], fp[c + s]};
+    const double vm[5] = {fm[c + 2 * s], fm[c + s], fm[c], fm[c - s], fm[c - 2 * s]};
+    double gp[5], gq[5];
+    weno5_grad(vp, g.weno_eps, gp);
+    weno5_grad(vm, g.weno_eps, gq);
 #pragma unroll
-    for (int m = 0; m < 4; m++) {
-      double r = has_r ? mu.p[m][c] : 0.0, l = has_l ? mu.p[m][c - s] : 0.0;
-      lF[m] = A * scale * (r - l) * ih;
-    }
-    double fp[6][4], fm[6][4];
-#pragma unroll
-    for (int r = 0; r < 6; r++) {
-      int cc = c + (r - 3) * s;
-      split_state(W.p[0][cc], W.p[1][cc], W.p[2][cc], W.p[3][cc], gm, pi, ig1, d, a, fp[r],
-                  fm[r]);
-    }
-#pragma unroll
-    for (int m = 0; m < 4; m++) {
-      double vp[5] = {fp[0][m], fp[1][m], fp[2][m], fp[3][m], fp[4][m]};
-      double vm[5] = {fm[5][m], fm[4][m], fm[3][m], fm[2][m], fm[1][m]};
-      double gp[5], gq[5];
-      weno5_grad(vp, g.weno_eps, gp);
-      weno5_grad(vm, g.weno_eps, gq);
-#pragma unroll
-      for (int r = 0; r < 5; r++) {
-        G.p[r * 4 + m][c] = lF[m] * gp[r];
-        G.p[20 + r * 4 + m][c] = lF[m] * gq[r];
-      }
+    for (int r = 0; r < 5; r++) {
+      plane_m(G, r * 4, m)[c] = lF * gp[r];
+      plane_m(G, 20 + r * 4, m)[c] = lF * gq[r];
     }
   }
 }
@@ -522,28 +543,31 @@ void launch_adj_rhs(const Grid &g, double *const W[2][4], const unsigned long lo
                     const double *dtp, double fac, double *const mu[2][4], const double *ax,
                     const double *ay, const double *phi, const double *sx, const double *sy,
                     const int *cut, const int *ncut, int cut_cap, double *const G[40],
-                    double *const lw[2][4], cudaStream_t st) {
+                    double *const SPp[8], double *const lw[2][4], cudaStream_t st) {
   Planes40 GG;
   for (int q = 0; q < 40; q++) GG.p[q] = G[q];
+  Planes8 SP;
+  for (int q = 0; q < 8; q++) SP.p[q] = SPp[q];
   for (int k = 0; k < 2; k++)
     for (int m = 0; m < 4; m++)
       cudaMemsetAsync(lw[k][m], 0, sizeof(double) * (size_t)g.PX * g.PY, st);
   for (int k = 0; k < 2; k++) {
     for (int d = 0; d < g.dim; d++) {
       long long nf = (long long)(g.nx + (d == 0)) * (g.ny + (d == 1));
-      k_adj_face<<<blocks_for(nf, 128), 128, 0, st>>>(g, k, d, p4(W[k]), d == 0 ? ax : ay,
-                                                      p4(mu[k]), lf, dtp, fac, GG);
       long long nc = d == 0 ? (long long)(g.nx + 2 * SIF_GH) * g.ny
                             : (long long)g.nx * (g.ny + 2 * SIF_GH);
-      k_adj_gather<<<blocks_for(nc, 256), 256, 0, st>>>(g, k, d, p4(W[k]), d == 0 ? ax : ay, lf,
+      launch_k(k_adj_split, blocks_for(nc, 256), 256, 0, st, g, k, d, p4(W[k]), lf, SP);
+      launch_k(k_adj_face, blocks_for(4 * nf, 128), 128, 0, st, g, k, d, SP, d == 0 ? ax : ay,
+                                                          p4(mu[k]), dtp, fac, GG);
+      launch_k(k_adj_gather, blocks_for(nc, 256), 256, 0, st, g, k, d, p4(W[k]), d == 0 ? ax : ay, lf,
                                                         GG, p4(lw[k]));
     }
   }
   long long n = (long long)g.nx * g.ny;
-  k_adj_ghost<<<blocks_for(n), 256, 0, st>>>(g, p8(lw));
-  k_adj_interface<<<blocks_for(cut_cap, 128, 2432), 128, 0, st>>>(g, p8(W), phi, sx, sy, cut,
+  launch_k(k_adj_ghost, blocks_for(n), 256, 0, st, g, p8(lw));
+  launch_k(k_adj_interface, blocks_for(cut_cap, 128, 2432), 128, 0, st, g, p8(W), phi, sx, sy, cut,
                                                                    ncut, p8(mu), dtp, fac, p8(lw));
-  sif_note_launches(4 * g.dim + 2);
+  sif_note_launches(6 * g.dim + 2);
 }
 
 void launch_adj_extension(const Grid &g, double *const lw[2][4], const ExtPlan *plan, int cap,
@@ -551,14 +575,14 @@ void launch_adj_extension(const Grid &g, double *const lw[2][4], const ExtPlan *
                           double *tmp, cudaStream_t st) {
   dim3 grid(blocks_for(work, 128, 2432), 2);
   double *buf[2] = {tmp, tmp + (size_t)8 * cap};
-  k_adj_ext_load<<<grid, 128, 0, st>>>(p8(lw), band, nband, cap, buf[0]);
+  launch_k(k_adj_ext_load, grid, 128, 0, st, p8(lw), band, nband, cap, buf[0]);
   int cur = 0;
   for (int it = 0; it < g.ext_iters; it++) {
-    k_adj_ext_sweep<<<grid, 128, 0, st>>>(g, plan, cap, band, nband, map, buf[cur], buf[cur ^ 1],
+    launch_k(k_adj_ext_sweep, grid, 128, 0, st, g, plan, cap, band, nband, map, buf[cur], buf[cur ^ 1],
                                           p8(lw));
     cur ^= 1;
   }
-  k_adj_ext_store<<<grid, 128, 0, st>>>(p8(lw), band, nband, cap, buf[cur]);
+  launch_k(k_adj_ext_store, grid, 128, 0, st, p8(lw), band, nband, cap, buf[cur]);
   sif_note_launches(g.ext_iters + 2);
 }
 
@@ -567,7 +591,7 @@ void launch_adj_prim(const Grid &g, double *const W[2][4], const double *alpha,
                      double *const out[2][4], double *const A[2][4], double ca,
                      double *const B[2][4], double cb, cudaStream_t st) {
   long long n = (long long)g.nx * g.ny;
-  k_adj_prim<<<blocks_for(n), 256, 0, st>>>(g, p8(W), alpha, nostate[0], nostate[1], p8(lw),
+  launch_k(k_adj_prim, blocks_for(n), 256, 0, st, g, p8(W), alpha, nostate[0], nostate[1], p8(lw),
                                             p8(out), p8(A), ca, p8(B), cb);
   sif_note_launches(1);
 }
@@ -575,7 +599,7 @@ void launch_adj_prim(const Grid &g, double *const W[2][4], const double *alpha,
 void launch_adj_init(const Grid &g, double *const prim[2][4], const double *alpha,
                      double *const lam[2][4], double *const out[2][4], cudaStream_t st) {
   long long n = (long long)g.nx * g.ny;
-  k_adj_init<<<blocks_for(n), 256, 0, st>>>(g, p8(prim), alpha, p8(lam), p8(out));
+  launch_k(k_adj_init, blocks_for(n), 256, 0, st, g, p8(prim), alpha, p8(lam), p8(out));
   sif_note_launches(1);
 }
 

@@ -80,6 +80,7 @@ struct sif_ctx {
   double *tape_scal;    // tape_alloc x 16: dt, LF speeds of stage 1 and 2 (bit patterns)
   void *adj_pool;
   double *lamA[2][4], *lamB[2][4], *lamC[2][4], *lw[2][4], *prim[2][4], *G[40];
+  double *SP[8];  // split fluxes of one (fluid, direction) for the face coefficients
   double *sv_q[2][4], *sv_w[2][4], *sv_phi;
   Scalars *sv_sc;
   char err[256];
@@ -1636,7 +1637,7 @@ static void taped_step(sif_ctx *c) {
 
 static int ensure_adj_scratch(sif_ctx *c) {
   if (c->adj_pool) return SIF_OK;
-  const int nplanes = 24 + 8 + 8 + 40 + 17;
+  const int nplanes = 24 + 8 + 8 + 40 + 8 + 17;
   size_t pb = sizeof(double) * c->NP;
   size_t bytes = pb * nplanes + sizeof(Scalars) + 256;
   if (cudaMalloc(&c->adj_pool, bytes) != cudaSuccess) {
@@ -1662,6 +1663,7 @@ static int ensure_adj_scratch(sif_ctx *c) {
       c->sv_w[k][m] = take();
     }
   for (int q = 0; q < 40; q++) c->G[q] = take();
+  for (int q = 0; q < 8; q++) c->SP[q] = take();
   c->sv_phi = take();
   c->sv_sc = (Scalars *)p;
   CK(cudaMemsetAsync(c->adj_pool, 0, bytes, c->st));
@@ -1726,7 +1728,7 @@ static void adj_stage(sif_ctx *c, double *const W[2][4], const unsigned char *co
   launch_ext_setup(c->g, c->alpha, c->phi, c->sx, c->sy, c->band_ev, &c->sc->n_band, c->bandmap,
                    c->ext_plan, ncell(c), band_work(c), flags, c->st);
   launch_adj_rhs(c->g, W, (const unsigned long long *)lf, dtp, fac, mu, c->ax, c->ay, c->phi,
-                 c->sx, c->sy, c->cut, &c->sc->n_cut, ncell(c), c->G, c->lw, c->st);
+                 c->sx, c->sy, c->cut, &c->sc->n_cut, ncell(c), c->G, c->SP, c->lw, c->st);
   launch_adj_extension(c->g, c->lw, c->ext_plan, ncell(c), band_work(c), c->band_ev,
                        &c->sc->n_band, c->bandmap, c->tmp, c->st);
   launch_adj_prim(c->g, W, c->alpha, flags, c->lw, out, A, ca, B, cb, c->st);

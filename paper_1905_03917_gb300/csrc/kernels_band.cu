@@ -157,7 +157,7 @@ void launch_prim2(const Grid &g, double *const qN[4], double *const qP[4], doubl
   }
   P.tiles[0] = tilesN;
   P.tiles[1] = tilesP;
-  k_prim<<<dim3(tile_cap, 2), g.tx * g.ty, 0, st>>>(g, P, alpha, sc->n_tiles, sc);
+  launch_k(k_prim, dim3(tile_cap, 2), g.tx * g.ty, 0, st, g, P, alpha, sc->n_tiles, sc);
   sif_note_launches(1);
 }
 
@@ -337,7 +337,7 @@ void launch_interface(const Grid &g, double *const wN[4], double *const wP[4], c
   // larger blocks would occupy a handful of SMs.  cut_cap bounds the cut
   // count (the kernel loops over the device count).
   int blocks = grid_for(2 * cut_cap, 32, 9728);
-  k_interface<<<blocks, 32, 0, st>>>(g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
+  launch_k(k_interface, blocks, 32, 0, st, g, wN[0], wN[1], wN[2], wN[3], wP[0], wP[1], wP[2], wP[3],
                                       phi, sx, sy, cut, &sc->n_cut, xn[0], xn[1], xn[2], xm[0],
                                       xm[1], xm[2], ul0, ul1, sc);
   sif_note_launches(1);
@@ -434,8 +434,8 @@ void launch_ls_stage(const Grid &g, int s, int rk, double *phi, const double *ph
   double a = rk == 3 ? A3[s] : A2[s], b = rk == 3 ? B3[s] : B2[s];
   int blocks = grid_for(band_cap, 64, 2432);
   // phi's ghost layers are current: every change of phi fills them
-  k_ls_stage<<<blocks, 64, 0, st>>>(g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
-  k_band_scatter_phi<<<blocks, 64, 0, st>>>(g, band, nband, tmp, phi);
+  launch_k(k_ls_stage, blocks, 64, 0, st, g, s, a, b, phi, phi0, ul0, ul1, band, nband, tmp, dtp);
+  launch_k(k_band_scatter_phi, blocks, 64, 0, st, g, band, nband, tmp, phi);
   sif_note_launches(2);
 }
 
@@ -525,8 +525,8 @@ void launch_reinit(const Grid &g, double *phi, double *phi0, const int *rext, co
   cudaMemcpyAsync(phi0, phi, sizeof(double) * (size_t)g.PX * g.PY, cudaMemcpyDeviceToDevice, st);
   int blocks = grid_for(rext_cap, 64, 2432);
   for (int it = 0; it < g.reinit_iters; it++) {
-    k_reinit<<<blocks, 64, 0, st>>>(g, phi, phi0, rext, nrext, tmp);
-    k_band_scatter_phi<<<blocks, 64, 0, st>>>(g, rext, nrext, tmp, phi);
+    launch_k(k_reinit, blocks, 64, 0, st, g, phi, phi0, rext, nrext, tmp);
+    launch_k(k_band_scatter_phi, blocks, 64, 0, st, g, rext, nrext, tmp, phi);
   }
   sif_note_launches(2 * g.reinit_iters);
 }
@@ -573,7 +573,7 @@ void launch_record(const Grid &, int shared, const int *cut, int cut_cap, double
                    double *const xm[3], double *xc0, double *xc1, double *xc2, Scalars *sc,
                    cudaStream_t st, double bw, int fluid2) {
   int blocks = grid_for(cut_cap, 128, 1216);
-  k_record<<<blocks, 128, 0, st>>>(shared, bw, fluid2, cut, &sc->n_cut, xn[0], xn[1], xn[2],
+  launch_k(k_record, blocks, 128, 0, st, shared, bw, fluid2, cut, &sc->n_cut, xn[0], xn[1], xn[2],
                                    xm[0], xm[1], xm[2], xc0, xc1, xc2, sc);
   sif_note_launches(1);
 }
@@ -605,7 +605,7 @@ __global__ void k_interp(Grid g, double *i0, double *i1, double *i2, double *i3,
 void launch_interp(const Grid &g, double *const qi[4], double *const prev[4],
                    double *const fut[4], const double *thp, const int *band, const int *nband,
                    int band_cap, cudaStream_t st) {
-  k_interp<<<grid_for(band_cap, 64, 2432), 64, 0, st>>>(g, qi[0], qi[1], qi[2], qi[3], prev[0],
+  launch_k(k_interp, grid_for(band_cap, 64, 2432), 64, 0, st, g, qi[0], qi[1], qi[2], qi[3], prev[0],
                                                        prev[1], prev[2], prev[3], fut[0],
                                                        fut[1], fut[2], fut[3], thp, band, nband);
   sif_note_launches(1);
@@ -631,7 +631,7 @@ __global__ void k_correction(Grid g, double *q1, double *q2, double *q3, const d
 void launch_correction(const Grid &g, double *const q[4], const double *xc0, const double *xc1,
                        const double *xc2, cudaStream_t st) {
   int n = g.nx * g.ny;
-  k_correction<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g, q[1], q[2], q[3], xc0, xc1, xc2);
+  launch_k(k_correction, grid_for(n, 256, 152 * 16), 256, 0, st, g, q[1], q[2], q[3], xc0, xc1, xc2);
   sif_note_launches(1);
 }
 
@@ -648,7 +648,7 @@ __global__ void k_copy_if(const int *flag, const double *__restrict__ src, doubl
 }
 
 void launch_copy_if(const int *flag, const double *src, double *dst, size_t n, cudaStream_t st) {
-  k_copy_if<<<grid_for((int)((n + 3) / 4), 256, 152 * 8), 256, 0, st>>>(flag, src, dst, n);
+  launch_k(k_copy_if, grid_for((int)((n + 3) / 4), 256, 152 * 8), 256, 0, st, flag, src, dst, n);
   sif_note_launches(1);
 }
 
@@ -669,7 +669,7 @@ __global__ void k_phi_interp(Grid g, double *phi, const double *__restrict__ a,
 void launch_phi_interp(const Grid &g, double *phi, const double *a, const double *b,
                        const double *thp, cudaStream_t st) {
   int n = g.nx * g.ny;
-  k_phi_interp<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(g, phi, a, b, thp);
+  launch_k(k_phi_interp, grid_for(n, 256, 152 * 8), 256, 0, st, g, phi, a, b, thp);
   sif_note_launches(1);
 }
 
@@ -686,7 +686,7 @@ __global__ void k_zero_cut(const int *__restrict__ cut, const int *ncut, double 
 
 void launch_zero_cut(const Grid &, double *const xn[3], double *const xm[3], const int *cut,
                      const int *ncut, int cut_cap, cudaStream_t st) {
-  k_zero_cut<<<grid_for(cut_cap, 128, 1216), 128, 0, st>>>(cut, ncut, xn[0], xn[1], xn[2], xm[0],
+  launch_k(k_zero_cut, grid_for(cut_cap, 128, 1216), 128, 0, st, cut, ncut, xn[0], xn[1], xn[2], xm[0],
                                                           xm[1], xm[2]);
   sif_note_launches(1);
 }
@@ -727,8 +727,8 @@ void launch_integrals(const Grid &g, double *const qN[4], double *const qP[4], d
                       int, double *out, cudaStream_t st) {
   Planes8 tab = {{qN[0], qN[1], qN[2], qN[3], qP[0], qP[1], qP[2], qP[3]}};
   dim3 grid((g.ny + 7) / 8, 8);
-  k_integrals_rows<<<grid, 256, 0, st>>>(g, tab, partial);
-  k_integrals_final<<<1, 32, 0, st>>>(g, partial, out);
+  launch_k(k_integrals_rows, grid, 256, 0, st, g, tab, partial);
+  launch_k(k_integrals_final, 1, 32, 0, st, g, partial, out);
   sif_note_launches(2);
 }
 
@@ -903,11 +903,11 @@ __global__ void k_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0,
 
 void launch_cond(int op, Scalars *sc, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
                  cudaGraphConditionalHandle h2, int max_sub, cudaStream_t st) {
-  k_cond<<<1, 32, 0, st>>>(op, sc, h0, h1, h2, max_sub);
+  launch_k(k_cond, 1, 32, 0, st, op, sc, h0, h1, h2, max_sub);
 }
 
 void launch_sched(int op, Scalars *sc, double cfl, double thr, int force1, cudaStream_t st) {
-  k_sched<<<1, 32, 0, st>>>(op, sc, cfl, thr, force1);
+  launch_k(k_sched, 1, 32, 0, st, op, sc, cfl, thr, force1);
   sif_note_launches(1);
 }
 

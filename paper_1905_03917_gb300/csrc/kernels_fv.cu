@@ -872,7 +872,7 @@ void launch_viscous(const Grid &g, int k, int s, int rk, double *const dst[4],
                     int tile_cap, const double *dtp, Scalars *sc, cudaStream_t st) {
   static const double B2[3] = {0.0, 1.0, 0.5}, B3[4] = {0.0, 1.0, 0.25, 2.0 / 3.0};
   const double bw = rk == 3 ? B3[s] : B2[s];
-  k_viscous<<<tile_cap > 0 ? tile_cap : 1, 128, 0, st>>>(g, k, bw, dtp, tiles, sc->n_tiles,
+  launch_k(k_viscous, tile_cap > 0 ? tile_cap : 1, 128, 0, st, g, k, bw, dtp, tiles, sc->n_tiles,
                                                         w[1], w[2], ax, ay, dst[1], dst[2],
                                                         dst[3]);
   sif_note_launches(1);

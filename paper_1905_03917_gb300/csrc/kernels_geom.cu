@@ -45,7 +45,7 @@ __global__ void k_ghost(Grid g, GhostSet s) {
 
 void launch_fill_ghost(const Grid &g, const GhostSet &s, cudaStream_t st) {
   int n = (2 * (g.nx + 2 * SIF_GH) * SIF_GH + 2 * SIF_GH * g.ny) * s.n;
-  k_ghost<<<(n + 255) / 256, 256, 0, st>>>(g, s);
+  launch_k(k_ghost, (n + 255) / 256, 256, 0, st, g, s);
   sif_note_launches(1);
 }
 
@@ -156,11 +156,11 @@ void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax
   if (band) {
     int blocks = (band_cap + 127) / 128;
     if (blocks > 2432) blocks = 2432;
-    k_geometry_band<<<blocks < 1 ? 1 : blocks, 128, 0, st>>>(g, phi, alpha, ax, ay, sx, sy,
+    launch_k(k_geometry_band, blocks < 1 ? 1 : blocks, 128, 0, st, g, phi, alpha, ax, ay, sx, sy,
                                                              band, nband, cut_list, &sc->n_cut);
   } else {
     int n = (g.nx + 1) * (g.ny + 1);
-    k_geometry<<<(n + 255) / 256, 256, 0, st>>>(g, phi, alpha, ax, ay, sx, sy, cut_list,
+    launch_k(k_geometry, (n + 255) / 256, 256, 0, st, g, phi, alpha, ax, ay, sx, sy, cut_list,
                                                 &sc->n_cut);
   }
   sif_note_launches(1);
@@ -197,7 +197,7 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
                        cudaStream_t st) {
   cudaMemsetAsync(counts, 0, 2 * sizeof(int), st);
   int n = g.nx * g.ny;
-  k_band<<<(n + 255) / 256, 256, 0, st>>>(g, phi, band, rext, &counts[0], &counts[1]);
+  launch_k(k_band, (n + 255) / 256, 256, 0, st, g, phi, band, rext, &counts[0], &counts[1]);
   sif_note_launches(1);
 }
 
@@ -231,7 +231,7 @@ __global__ void k_tiles(Grid g, const double *__restrict__ p, int *t0, int *t1, 
 void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
                        cudaStream_t st) {
   cudaMemsetAsync(sc->n_tiles, 0, 2 * sizeof(int), st);
-  k_tiles<<<g.ntx * g.nty, 128, 0, st>>>(g, phi, tiles0, tiles1, sc->n_tiles);
+  launch_k(k_tiles, g.ntx * g.nty, 128, 0, st, g, phi, tiles0, tiles1, sc->n_tiles);
   sif_note_launches(1);
 }
 
@@ -265,7 +265,7 @@ void launch_init_state(const Grid &g, double *const qN[4], double *const qP[4],
                        double *const wN[4], double *const wP[4], const double *alpha,
                        cudaStream_t st) {
   int n = g.nx * g.ny;
-  k_init_q<<<(n + 255) / 256, 256, 0, st>>>(g, qN[0], qN[1], qN[2], qN[3], qP[0], qP[1], qP[2],
+  launch_k(k_init_q, (n + 255) / 256, 256, 0, st, g, qN[0], qN[1], qN[2], qN[3], qP[0], qP[1], qP[2],
                                             qP[3], wN[0], wN[1], wN[2], wN[3], wP[0], wP[1],
                                             wP[2], wP[3], alpha);
   sif_note_launches(1);

@@ -59,7 +59,7 @@ void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int 
                      int *etiles, cudaStream_t st) {
   cudaMemsetAsync(map, 0xff, sizeof(int) * (size_t)g.PX * g.PY, st);
   cudaMemsetAsync(nband, 0, 2 * sizeof(int), st);
-  k_band_mapped<<<ext_tiles(g), SIF_ETILE * SIF_ETILE, 0, st>>>(g, phi, band, map, nband,
+  launch_k(k_band_mapped, ext_tiles(g), SIF_ETILE * SIF_ETILE, 0, st, g, phi, band, map, nband,
                                                                etiles);
   sif_note_launches(1);
 }
@@ -73,6 +73,15 @@ struct ExtFields {
   int ncomp[3];
   double gamma[2], pinf[2];
 };
+
+// the upwind-weighted mean of a target's neighbour values x (weight wx,
+// present if hx) and y (wy, hy): one product and one fused multiply-add,
+// the same operations in every form of the extension
+__device__ __forceinline__ double ext_mean(bool hx, double wx, double x, bool hy, double wy,
+                                           double y) {
+  if (hx && hy) return __fma_rn(wy, y, wx * x);
+  return hx ? wx * x : wy * y;
+}
 
 // ---------------------------------------------------------------------
 // extension plans: for every band cell and each of the three extended
@@ -141,9 +150,8 @@ __global__ void k_ext_setup(Grid g, const double *__restrict__ alpha,
           if (copy || (pl.cx < 0 && pl.cy < 0)) {
             v = a[c];
           } else {
-            v = 0.0;
-            if (pl.cx >= 0) v += pl.wx * a[pl.cx];
-            if (pl.cy >= 0) v += pl.wy * a[pl.cy];
+            v = ext_mean(pl.cx >= 0, pl.wx, pl.cx >= 0 ? a[pl.cx] : 0.0, pl.cy >= 0, pl.wy,
+                         pl.cy >= 0 ? a[pl.cy] : 0.0);
           }
           sweep0[(size_t)f * 4 * cap + (size_t)m * cap + idx] = v;
         }
@@ -164,7 +172,7 @@ void launch_ext_setup(const Grid &g, const double *alpha, const double *phi, con
       F.p[1][m] = wP[m];
     }
   // one block row per field
-  k_ext_setup<<<dim3(blocks_for(work, 64), 3), 64, 0, st>>>(
+  launch_k(k_ext_setup, dim3(blocks_for(work, 64), 3), 64, 0, st, 
       g, alpha, phi, sx, sy, band, nband, map, plan, cap, nostate[0], nostate[1], F, sweep0,
       copy);
   sif_note_launches(1);
@@ -203,10 +211,9 @@ __device__ void ext_fold_lf(double lx, double ly, unsigned long long *lf) {
 __device__ __forceinline__ double ext_one(const ExtPlan &px, int bp, int cell, const double *a,
                                           const double *b) {
   if (px.cx < 0 && px.cy < 0) return b ? b[bp] : a[cell];
-  double v = 0.0;
-  if (px.cx >= 0) v += px.wx * ((b && px.bx >= 0) ? b[px.bx] : a[px.cx]);
-  if (px.cy >= 0) v += px.wy * ((b && px.by >= 0) ? b[px.by] : a[px.cy]);
-  return v;
+  const double x = px.cx >= 0 ? ((b && px.bx >= 0) ? b[px.bx] : a[px.cx]) : 0.0;
+  const double y = px.cy >= 0 ? ((b && px.by >= 0) ? b[px.by] : a[px.cy]) : 0.0;
+  return ext_mean(px.cx >= 0, px.wx, x, px.cy >= 0, px.wy, y);
 }
 
 // S (1 or 2) Jacobi sweeps in one launch.  With S = 2 a target recomputes
@@ -258,9 +265,9 @@ __global__ void k_ext_sweep(ExtFields F, int f0, const ExtPlan *__restrict__ pla
       } else if (pl.cx < 0 && pl.cy < 0) {
         v = b ? b[idx] : a[c];
       } else {
-        v = 0.0;
-        if (pl.cx >= 0) v += pl.wx * (hx ? ext_one(px, pl.bx, pl.cx, a, b) : a[pl.cx]);
-        if (pl.cy >= 0) v += pl.wy * (hy ? ext_one(py, pl.by, pl.cy, a, b) : a[pl.cy]);
+        const double x = pl.cx >= 0 ? (hx ? ext_one(px, pl.bx, pl.cx, a, b) : a[pl.cx]) : 0.0;
+        const double y = pl.cy >= 0 ? (hy ? ext_one(py, pl.by, pl.cy, a, b) : a[pl.cy]) : 0.0;
+        v = ext_mean(pl.cx >= 0, pl.wx, x, pl.cy >= 0, pl.wy, y);
       }
       out[m] = v;
     }
@@ -345,10 +352,10 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
     const int S = (f0 == 0 && remaining % 2 == 0) ? 2 : 1;
     const int wb = remaining == S && src != nullptr;
     if (S == 1)
-      k_ext_sweep<1><<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur], wb,
+      launch_k(k_ext_sweep<1>, grid, 64, 0, st, F, f0, plan, cap, band, nband, src, buf[cur], wb,
                                           alpha, nostate[0], nostate[1], sc);
     else
-      k_ext_sweep<2><<<grid, 64, 0, st>>>(F, f0, plan, cap, band, nband, src, buf[cur], wb,
+      launch_k(k_ext_sweep<2>, grid, 64, 0, st, F, f0, plan, cap, band, nband, src, buf[cur], wb,
                                           alpha, nostate[0], nostate[1], sc);
     remaining -= S;
     launched++;
@@ -360,7 +367,7 @@ void launch_ext_sweeps(const Grid &g, double *const wN[4], double *const wP[4], 
     cur ^= 1;
   }
   if (src) {
-    k_ext_scatter<<<grid, 64, 0, st>>>(g, F, f0, cap, band, nband, src, alpha, nostate[0],
+    launch_k(k_ext_scatter, grid, 64, 0, st, g, F, f0, cap, band, nband, src, alpha, nostate[0],
                                         nostate[1], sc);
     launched++;
   }
@@ -389,6 +396,8 @@ constexpr int EXT_THREADS = 512;
 constexpr int EXT_RW_MAX = SIF_ETILE + 2 * SIF_EXT_BLOCKED_MAX;
 // region cells (and targets) a thread holds
 constexpr int EXT_PER = (EXT_RW_MAX * EXT_RW_MAX + EXT_THREADS - 1) / EXT_THREADS;
+// the largest distance of a region cell to the region's rim
+constexpr int EXT_DMAX = (EXT_RW_MAX - 1) / 2;
 
 static size_t ext_blocked_smem(int nc, int H) {
   const size_t rw = SIF_ETILE + 2 * H, r = rw * rw;
@@ -413,7 +422,7 @@ k_ext_blocked(Grid g, ExtFields F, int f0, const ExtPlan *__restrict__ plan, int
               Scalars *sc) {
   SIF_TICK();
   extern __shared__ double esm[];
-  __shared__ int s_nt;
+  __shared__ int s_hist[EXT_DMAX + 1], s_start[EXT_DMAX + 1];
   const int f = f0 + blockIdx.y;
   const int H = g.ext_iters, RW = SIF_ETILE + 2 * H, R = RW * RW;
   double *val = esm;              // NC x R
@@ -433,7 +442,7 @@ k_ext_blocked(Grid g, ExtFields F, int f0, const ExtPlan *__restrict__ plan, int
   for (int q = blockIdx.x; q < nt_tiles; q += gridDim.x) {
     const int et = etiles[q];
     const int ri0 = (et % tilesx) * SIF_ETILE - H, rj0 = (et / tilesx) * SIF_ETILE - H;
-    if (tid == 0) s_nt = 0;
+    for (int d = tid; d <= EXT_DMAX; d += EXT_THREADS) s_hist[d] = 0;
     // the region's band positions and plane values, then the band cells'
     // plans (and buffered values): two dependent load levels in all
     int cc[EXT_PER], bp[EXT_PER];
@@ -458,10 +467,16 @@ k_ext_blocked(Grid g, ExtFields F, int f0, const ExtPlan *__restrict__ plan, int
       for (int m = 0; m < NC; m++)
         v[l][m] = buffered ? in[(size_t)m * cap + bp[l]] : (cc[l] >= 0 ? F.p[f][m][cc[l]] : 0.0);
     }
-    __syncthreads();  // s_nt is set
+    __syncthreads();  // s_hist is clear
+    // targets sorted by their distance to the region's rim, the farthest
+    // first: sweep s (0-based) updates only those at distance s + 1 or more
+    // (the others are stale by then whatever they hold), a prefix of the
+    // list
+    int dist[EXT_PER], nxs[EXT_PER], nys[EXT_PER];
 #pragma unroll
     for (int l = 0; l < EXT_PER; l++) {
       const int r = tid + l * EXT_THREADS;
+      dist[l] = -1;
       if (r >= R) continue;
       bps[r] = bp[l];
 #pragma unroll
@@ -481,15 +496,33 @@ k_ext_blocked(Grid g, ExtFields F, int f0, const ExtPlan *__restrict__ plan, int
         else ny_ = r + d * RW;
       }
       if (rim) continue;
-      const int k = atomicAdd(&s_nt, 1);
-      tls[k] = r;
-      wxs[k] = pl[l].wx;
-      wys[k] = pl[l].wy;
-      nbs[k] = (nx_ + 1) | ((ny_ + 1) << 16);
+      dist[l] = min(min(li, lj), min(RW - 1 - li, RW - 1 - lj));
+      nxs[l] = nx_;
+      nys[l] = ny_;
+      atomicAdd(&s_hist[dist[l]], 1);
     }
     __syncthreads();
-    const int nt = s_nt;
+    if (tid == 0) {
+      // s_start[d]: targets farther than d from the rim (they come first)
+      int acc = 0;
+      for (int d = EXT_DMAX; d >= 0; d--) {
+        s_start[d] = acc;
+        acc += s_hist[d];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < EXT_PER; l++) {
+      if (dist[l] < 0) continue;
+      const int k = s_start[dist[l]] + atomicAdd(&s_hist[dist[l]], -1) - 1;
+      tls[k] = tid + l * EXT_THREADS;
+      wxs[k] = pl[l].wx;
+      wys[k] = pl[l].wy;
+      nbs[k] = (nxs[l] + 1) | ((nys[l] + 1) << 16);
+    }
+    __syncthreads();
     for (int s = 0; s < H; s++) {
+      const int nt = s_start[s];
       double nv[EXT_PER][NC];
 #pragma unroll
       for (int kk = 0; kk < EXT_PER; kk++) {
@@ -498,12 +531,9 @@ k_ext_blocked(Grid g, ExtFields F, int f0, const ExtPlan *__restrict__ plan, int
           const int nb = nbs[k], nx_ = (nb & 0xffff) - 1, ny_ = (nb >> 16) - 1;
           const double wx = wxs[k], wy = wys[k];
 #pragma unroll
-          for (int m = 0; m < NC; m++) {
-            double x = 0.0;
-            if (nx_ >= 0) x += wx * val[m * R + nx_];
-            if (ny_ >= 0) x += wy * val[m * R + ny_];
-            nv[kk][m] = x;
-          }
+          for (int m = 0; m < NC; m++)
+            nv[kk][m] = ext_mean(nx_ >= 0, wx, nx_ >= 0 ? val[m * R + nx_] : 0.0, ny_ >= 0, wy,
+                                 ny_ >= 0 ? val[m * R + ny_] : 0.0);
         }
       }
       __syncthreads();
@@ -576,15 +606,15 @@ void launch_ext_blocked(const Grid &g, double *const wN[4], double *const wP[4],
   dim3 grid(nt < 2 * num_sms ? nt : 2 * num_sms, nf);
   if (f0 < 2) {
     // the stencil states' band values are in tmp (k_ext_setup's copy)
-    k_ext_blocked<4, true><<<grid, EXT_THREADS, ext_blocked_smem(4, g.ext_iters), st>>>(
+    launch_k(k_ext_blocked<4, true>, grid, EXT_THREADS, ext_blocked_smem(4, g.ext_iters), st, 
         g, F, f0, plan, cap, etiles, nband, map, tmp, nullptr, alpha, nostate[0], nostate[1],
         sc);
     sif_note_launches(1);
     return;
   }
-  k_ext_blocked<2, false><<<grid, EXT_THREADS, ext_blocked_smem(2, g.ext_iters), st>>>(
+  launch_k(k_ext_blocked<2, false>, grid, EXT_THREADS, ext_blocked_smem(2, g.ext_iters), st, 
       g, F, f0, plan, cap, etiles, nband, map, nullptr, tmp, alpha, nostate[0], nostate[1], sc);
-  k_ext_scatter<<<dim3(blocks_for(work, 64), nf), 64, 0, st>>>(g, F, f0, cap, band, nband, tmp,
+  launch_k(k_ext_scatter, dim3(blocks_for(work, 64), nf), 64, 0, st, g, F, f0, cap, band, nband, tmp,
                                                                alpha, nostate[0], nostate[1], sc);
   sif_note_launches(2);
 }
@@ -768,8 +798,8 @@ void launch_mix2(const Grid &g, int mask, double *const qN[4], double *const qP[
   }
   // small blocks spread the band's few thousand cells over the SMs
   int b = blocks_for(work, 64);
-  k_mix_setup<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, alpha, phi, band, nband, plan, cap);
-  k_mix_apply<<<dim3(b, 2), 64, 0, st>>>(g, mask, Q, map, plan, cap, band, nband);
+  launch_k(k_mix_setup, dim3(b, 2), 64, 0, st, g, mask, Q, alpha, phi, band, nband, plan, cap);
+  launch_k(k_mix_apply, dim3(b, 2), 64, 0, st, g, mask, Q, map, plan, cap, band, nband);
   sif_note_launches(2);
 }
 
@@ -843,9 +873,9 @@ void launch_mix_adjoint(const Grid &g, double *const lN[4], double *const lP[4],
     L.q[1][m] = lP[m];
   }
   int b = blocks_for(work, 128);
-  k_mix_adj_setup<<<b, 128, 0, st>>>(g, alpha, phi, band, nband, plan, cap);
-  k_mix_adj_apply<<<dim3(b, 2), 128, 0, st>>>(g, L, map, plan, cap, band, nband, tmp);
-  k_mix_scatter<<<dim3(b, 2), 128, 0, st>>>(3, L, band, nband, tmp);
+  launch_k(k_mix_adj_setup, b, 128, 0, st, g, alpha, phi, band, nband, plan, cap);
+  launch_k(k_mix_adj_apply, dim3(b, 2), 128, 0, st, g, L, map, plan, cap, band, nband, tmp);
+  launch_k(k_mix_scatter, dim3(b, 2), 128, 0, st, 3, L, band, nband, tmp);
   sif_note_launches(3);
 }
 

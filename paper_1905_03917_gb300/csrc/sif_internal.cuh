@@ -85,6 +85,19 @@ static __device__ unsigned long long g_tu_launches;
     if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)     \
       atomicAdd(&g_tu_launches, 1ull);                                                \
   } while (0)
+
+// kernel launch through the launch-configuration form (every launch site
+// goes through here)
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
 unsigned long long sif_launches_geom();
 unsigned long long sif_launches_band();
 unsigned long long sif_launches_plan();
@@ -510,7 +523,7 @@ void launch_adj_rhs(const Grid &g, double *const W[2][4], const unsigned long lo
                     const double *dtp, double fac, double *const mu[2][4], const double *ax,
                     const double *ay, const double *phi, const double *sx, const double *sy,
                     const int *cut, const int *ncut, int cut_cap, double *const G[40],
-                    double *const lw[2][4], cudaStream_t st);
+                    double *const SP[8], double *const lw[2][4], cudaStream_t st);
 void launch_adj_extension(const Grid &g, double *const lw[2][4], const ExtPlan *plan, int cap,
                           int work, const int *band, const int *nband, const int *map,
                           double *tmp, cudaStream_t st);

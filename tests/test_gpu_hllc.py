@@ -43,7 +43,10 @@ def test_hllc_parity(name, multi):
 def test_contact_at_rest_stays_sharp():
     """A density jump at rest inside fluid P of a 1D tube (uniform pressure,
     no velocity): after 200 steps every cell's density is its initial one
-    to round-off."""
+    to round-off (1e-9 of 4: the kernel's WENO5, a fraction over one
+    reciprocal, returns a constant to within an ulp, not exactly, and those
+    ulps of pressure drive acoustic round-off that reached 3.3e-11; the
+    Lax-Friedrichs flux moves the jump by more than 1e-2)."""
     sif = _sif()
     n = 128
     d = 1.0 / n
@@ -57,7 +60,7 @@ def test_contact_at_rest_stays_sharp():
     s = sif.Solver(cfg).init_fluids((x - 0.5)[None, :], pN, pP)
     s.step_single_dt(200)
     qN, qP, _ = s.state()
-    assert np.abs(qN[0, 0] + qP[0, 0] - np.where(x > 0.75, 4.0, 1.0)).max() <= 1e-12
+    assert np.abs(qN[0, 0] + qP[0, 0] - np.where(x > 0.75, 4.0, 1.0)).max() <= 1e-9
 
 
 def test_tile_shape_does_not_change_hllc_results():
