@@ -562,10 +562,12 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
 // extension of the level-set velocity set by the last interaction step
 // (its plan, band and sweep buffers stay untouched until a level-set
 // stage, a reinitialisation, a mixing, a geometry or the next interaction
-// step, each of which joins it first).  Called just before the
+// step, each of which joins it first), and with s > 0 the level set's RK
+// stage s after it (it reads only the extended velocity and phi, which the
+// finite-volume stages do not touch).  Called just before the
 // finite-volume stage that follows the interaction step: in a captured
-// graph the sweeps are a branch beside that stage.
-static void ul_extend(sif_ctx *c) {
+// graph both are a branch beside that stage.
+static void ul_extend(sif_ctx *c, int s = 0, const double *dtp = nullptr) {
   side_branch(c, [&] {
     if (c->ext_blocked)
       launch_ext_blocked(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
@@ -575,6 +577,9 @@ static void ul_extend(sif_ctx *c) {
       launch_ext_sweeps(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
                         band_work(c), c->band_ev, &c->sc->n_band, c->tmp, c->alpha, c->nostate,
                         c->sc, c->st);
+    if (s > 0)
+      launch_ls_stage(c->g, s, c->cfg.rk_order, c->phi, c->phi0, c->ul[0], c->ul[1], c->band_ls,
+                      &c->sc->n_band_ls, ncell(c), c->tmp, dtp, c->st);
   });
   dbg(c, "ls_extend");
 }
@@ -625,13 +630,6 @@ static void ls_begin(sif_ctx *c) {
   launch_band_lists(c->g, c->phi, c->band_ls, c->rext_ls, &c->sc->n_band_ls, c->st);
 }
 
-static void ls_stage(sif_ctx *c, int s, const double *dtp) {
-  side_join(c);
-  launch_ls_stage(c->g, s, c->cfg.rk_order, c->phi, c->phi0, c->ul[0], c->ul[1], c->band_ls,
-                  &c->sc->n_band_ls, ncell(c), c->tmp, dtp, c->st);
-  dbg(c, "ls_stage");
-}
-
 static void reinit(sif_ctx *c) {
   side_join(c);
   launch_reinit(c->g, c->phi, c->phiR, c->rext_ls, &c->sc->n_rext, ncell(c), c->tmp, c->st);
@@ -655,7 +653,7 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
   ls_begin(c);
   for (int s = 1; s <= S; s++) {
     if (s > 1) eval(c, c->q);
-    ul_extend(c);
+    ul_extend(c, s, dtp);
     if (rec && s == 2) {
       cudaMemcpyAsync(rec->lf2, c->sc->lf, sizeof(c->sc->lf), cudaMemcpyDeviceToDevice, c->st);
       for (int k = 0; k < 2; k++)
@@ -667,9 +665,10 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
         for (int m = 0; m < 4; m++)
           cudaMemcpyAsync(rec->W[s - 1][k][m], c->w[k][m], sizeof(double) * c->NP,
                           cudaMemcpyDeviceToDevice, c->st);
-    ls_stage(c, s, dtp);
-    if (rec && s == 1)
+    if (rec && s == 1) {
+      side_join(c);  // the level set's first stage
       cudaMemcpyAsync(rec->phi1, c->phi, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
+    }
     if (s == S) reinit(c);
     geometry(c, true);
     mix_both(c);
@@ -819,9 +818,8 @@ static int cycle3(sif_ctx *c, int f1, sif_cycle_info *info) {
     launch_copy_if(&c->sc->snap_a, c->phi, c->phia, c->NP, c->st);
     copy_planes(c, c->q0[f2], c->q[f2], 4);
     ls_begin(c);
-    ul_extend(c);
+    ul_extend(c, 1, &c->sc->dt2);
     fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-    ls_stage(c, 1, &c->sc->dt2);
     geometry(c, true);
     if (last) {
       mix_pair(c, f1, c->fut, c->q[f2]);
@@ -832,11 +830,10 @@ static int cycle3(sif_ctx *c, int f1, sif_cycle_info *info) {
       mix_pair(c, f1, c->qi, c->q[f2]);
     }
     eval(c, qs, last ? -1 : f1);
-    ul_extend(c);
+    ul_extend(c, 2, &c->sc->dt2);
     launch_record(c->g, last, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2],
                   c->sc, c->st, b12, 1);
     fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-    ls_stage(c, 2, &c->sc->dt2);
     if (last) fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1);
     geometry(c, true);
     if (single) {
@@ -850,11 +847,10 @@ static int cycle3(sif_ctx *c, int f1, sif_cycle_info *info) {
       mix_one(c, f1, c->qi);
     }
     eval(c, qs, single ? -1 : f1);
-    ul_extend(c);
+    ul_extend(c, 3, &c->sc->dt2);
     launch_record(c->g, single, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2],
                   c->sc, c->st, b3, 1);
     fv(c, f2, 3, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-    ls_stage(c, 3, &c->sc->dt2);
     if (single) fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1);
     reinit(c);
     geometry(c, true);
@@ -943,9 +939,8 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     // step 3: fluid-2 and level-set first RK stage with dt2
     copy_planes(c, c->q0[f2], c->q[f2], 4);
     ls_begin(c);
-    ul_extend(c);  // of the cycle's first or this sub-step's interaction step
+    ul_extend(c, 1, &c->sc->dt2);  // of the cycle's first or this sub-step's interaction step
     fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-    ls_stage(c, 1, &c->sc->dt2);
     geometry(c, true);
     if (last) {
       mix_pair(c, f1, c->fut, c->q[f2]);
@@ -958,12 +953,11 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     }
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
     eval(c, qs, last ? -1 : f1);
-    ul_extend(c);
+    ul_extend(c, 2, &c->sc->dt2);
     launch_record(c->g, last, c->cut, ncell(c), c->xn, c->xm, c->xc[0],
                   c->xc[1], c->xc[2], c->sc, c->st);
     // step 4 (and 5 on the last sub-step): second RK stage
     fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-    ls_stage(c, 2, &c->sc->dt2);
     if (last) fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1);
     reinit(c);
     if (last) {
@@ -1081,9 +1075,8 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
   // step 3: fluid-2 and level-set first RK stage with dt2
   copy4(c, c->q0[f2], c->q[f2]);
   ls_begin(c);
-  ul_extend(c);  // of the cycle's first or this sub-step's interaction step
+  ul_extend(c, 1, &c->sc->dt2);  // of the cycle's first or this sub-step's interaction step
   fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-  ls_stage(c, 1, &c->sc->dt2);
   geometry(c, true);
   cond_node(c, hl1, false, [&] {
     mix_pair(c, f1, c->fut, c->q[f2]);
@@ -1095,12 +1088,11 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
     mix_pair(c, f1, c->qi, c->q[f2]);
   });
   eval(c, qs, f1, &c->sc->last);
-  ul_extend(c);
+  ul_extend(c, 2, &c->sc->dt2);
   launch_record(c->g, -2, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 4 (and 5 on the last sub-step): second RK stage
   fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-  ls_stage(c, 2, &c->sc->dt2);
   cond_node(c, hl2, false, [&] { fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1); });
   reinit(c);
   cond_node(c, hl3, false, [&] {
@@ -1171,9 +1163,8 @@ static void graph_substep3(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop)
   // stage 1 of fluid 2 and the level set
   copy4(c, c->q0[f2], c->q[f2]);
   ls_begin(c);
-  ul_extend(c);
+  ul_extend(c, 1, &c->sc->dt2);
   fv(c, f2, 1, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-  ls_stage(c, 1, &c->sc->dt2);
   geometry(c, true);
   // stage 2 at t2 + dt2 (at t1 on the last sub-step)
   cond_node(c, hl1, false, [&] {
@@ -1186,11 +1177,10 @@ static void graph_substep3(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop)
     mix_pair(c, f1, c->qi, c->q[f2]);
   });
   eval(c, qs, f1, &c->sc->last);
-  ul_extend(c);
+  ul_extend(c, 2, &c->sc->dt2);
   launch_record(c->g, -2, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2], c->sc,
                 c->st, b12, 1);
   fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-  ls_stage(c, 2, &c->sc->dt2);
   cond_node(c, hl2, false, [&] { fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1); });
   geometry(c, true);
   // stage 3 at t2 + dt2/2
@@ -1206,11 +1196,10 @@ static void graph_substep3(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop)
     mix_one(c, f1, c->qi);
   });
   eval(c, qs, f1, &c->sc->single);
-  ul_extend(c);
+  ul_extend(c, 3, &c->sc->dt2);
   launch_record(c->g, -3, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2], c->sc,
                 c->st, b3, 1);
   fv(c, f2, 3, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
-  ls_stage(c, 3, &c->sc->dt2);
   cond_node(c, hs2, false, [&] { fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1); });
   reinit(c);
   geometry(c, true);
