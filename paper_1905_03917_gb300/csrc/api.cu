@@ -564,10 +564,12 @@ static void eval(sif_ctx *c, double *const qs[2][4], int band_fluid = -1,
 // stage, a reinitialisation, a mixing, a geometry or the next interaction
 // step, each of which joins it first), and with s > 0 the level set's RK
 // stage s after it (it reads only the extended velocity and phi, which the
-// finite-volume stages do not touch).  Called just before the
+// finite-volume stages do not touch), and with reinit_after the step's
+// reinitialisation after that.  Called just before the
 // finite-volume stage that follows the interaction step: in a captured
 // graph both are a branch beside that stage.
-static void ul_extend(sif_ctx *c, int s = 0, const double *dtp = nullptr) {
+static void ul_extend(sif_ctx *c, int s = 0, const double *dtp = nullptr,
+                      bool reinit_after = false) {
   side_branch(c, [&] {
     if (c->ext_blocked)
       launch_ext_blocked(c->g, c->w[0], c->w[1], c->ul[0], c->ul[1], 2, 1, c->ext_plan, ncell(c),
@@ -580,6 +582,8 @@ static void ul_extend(sif_ctx *c, int s = 0, const double *dtp = nullptr) {
     if (s > 0)
       launch_ls_stage(c->g, s, c->cfg.rk_order, c->phi, c->phi0, c->ul[0], c->ul[1], c->band_ls,
                       &c->sc->n_band_ls, ncell(c), c->tmp, dtp, c->st);
+    if (reinit_after)
+      launch_reinit(c->g, c->phi, c->phiR, c->rext_ls, &c->sc->n_rext, ncell(c), c->tmp, c->st);
   });
   dbg(c, "ls_extend");
 }
@@ -630,12 +634,6 @@ static void ls_begin(sif_ctx *c) {
   launch_band_lists(c->g, c->phi, c->band_ls, c->rext_ls, &c->sc->n_band_ls, c->st);
 }
 
-static void reinit(sif_ctx *c) {
-  side_join(c);
-  launch_reinit(c->g, c->phi, c->phiR, c->rext_ls, &c->sc->n_rext, ncell(c), c->tmp, c->st);
-  dbg(c, "reinit");
-}
-
 // where a recorded step keeps its level set after stage 1 and the
 // Lax-Friedrichs speeds of stage 2
 struct TapeHook {
@@ -653,7 +651,7 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
   ls_begin(c);
   for (int s = 1; s <= S; s++) {
     if (s > 1) eval(c, c->q);
-    ul_extend(c, s, dtp);
+    ul_extend(c, s, dtp, s == S);
     if (rec && s == 2) {
       cudaMemcpyAsync(rec->lf2, c->sc->lf, sizeof(c->sc->lf), cudaMemcpyDeviceToDevice, c->st);
       for (int k = 0; k < 2; k++)
@@ -669,7 +667,6 @@ static void single_step_after_eval(sif_ctx *c, const double *dtp, const TapeHook
       side_join(c);  // the level set's first stage
       cudaMemcpyAsync(rec->phi1, c->phi, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, c->st);
     }
-    if (s == S) reinit(c);
     geometry(c, true);
     mix_both(c);
   }
@@ -847,12 +844,11 @@ static int cycle3(sif_ctx *c, int f1, sif_cycle_info *info) {
       mix_one(c, f1, c->qi);
     }
     eval(c, qs, single ? -1 : f1);
-    ul_extend(c, 3, &c->sc->dt2);
+    ul_extend(c, 3, &c->sc->dt2, true);
     launch_record(c->g, single, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2],
                   c->sc, c->st, b3, 1);
     fv(c, f2, 3, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
     if (single) fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1);
-    reinit(c);
     geometry(c, true);
     mix_one(c, f2, c->q[f2]);
     launch_sched(SCHED_SNAPB, c->sc, 0, 0, 0, c->st);
@@ -953,13 +949,12 @@ static int cycle(sif_ctx *c, sif_cycle_info *info) {
     }
     for (int m = 0; m < 4; m++) qs[f2][m] = c->q[f2][m];
     eval(c, qs, last ? -1 : f1);
-    ul_extend(c, 2, &c->sc->dt2);
+    ul_extend(c, 2, &c->sc->dt2, true);
     launch_record(c->g, last, c->cut, ncell(c), c->xn, c->xm, c->xc[0],
                   c->xc[1], c->xc[2], c->sc, c->st);
     // step 4 (and 5 on the last sub-step): second RK stage
     fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
     if (last) fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1);
-    reinit(c);
     if (last) {
       if (c->cfg.flux_correction) launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
       geometry(c, true);
@@ -1088,13 +1083,12 @@ static void graph_substep(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop) 
     mix_pair(c, f1, c->qi, c->q[f2]);
   });
   eval(c, qs, f1, &c->sc->last);
-  ul_extend(c, 2, &c->sc->dt2);
+  ul_extend(c, 2, &c->sc->dt2, true);
   launch_record(c->g, -2, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1],
                 c->xc[2], c->sc, c->st);
   // step 4 (and 5 on the last sub-step): second RK stage
   fv(c, f2, 2, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
   cond_node(c, hl2, false, [&] { fv(c, f1, 2, c->q[f1], c->prev, c->fut, &c->sc->dt1); });
-  reinit(c);
   cond_node(c, hl3, false, [&] {
     if (c->cfg.flux_correction)
       launch_correction(c->g, c->q[f1], c->xc[0], c->xc[1], c->xc[2], c->st);
@@ -1196,12 +1190,11 @@ static void graph_substep3(sif_ctx *c, int f1, cudaGraphConditionalHandle hloop)
     mix_one(c, f1, c->qi);
   });
   eval(c, qs, f1, &c->sc->single);
-  ul_extend(c, 3, &c->sc->dt2);
+  ul_extend(c, 3, &c->sc->dt2, true);
   launch_record(c->g, -3, c->cut, ncell(c), c->xn, c->xm, c->xc[0], c->xc[1], c->xc[2], c->sc,
                 c->st, b3, 1);
   fv(c, f2, 3, c->q[f2], c->q0[f2], c->q[f2], &c->sc->dt2);
   cond_node(c, hs2, false, [&] { fv(c, f1, 3, c->q[f1], c->prev, c->q[f1], &c->sc->dt1); });
-  reinit(c);
   geometry(c, true);
   mix_one(c, f2, c->q[f2]);
   launch_sched(SCHED_SNAPB, c->sc, 0, 0, 0, c->st);

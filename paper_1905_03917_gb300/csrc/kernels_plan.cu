@@ -602,8 +602,13 @@ void launch_ext_blocked(const Grid &g, double *const wN[4], double *const wP[4],
     F.gamma[k] = g.gamma[k];
     F.pinf[k] = g.pinf[k];
   }
-  const int nt = ext_tiles(g);
-  dim3 grid(nt < 2 * num_sms ? nt : 2 * num_sms, nf);
+  // about one CTA per band tile (the CTAs loop over the device's tile
+  // count): a band tile holds some 32 band cells or more, and a CTA that
+  // finds no tile still takes a whole SM's registers to start
+  int gx = ext_tiles(g);
+  if (gx > work / 32 + 1) gx = work / 32 + 1;
+  if (gx > 2 * num_sms) gx = 2 * num_sms;
+  dim3 grid(gx, nf);
   if (f0 < 2) {
     // the stencil states' band values are in tmp (k_ext_setup's copy)
     launch_k(k_ext_blocked<4, true>, grid, EXT_THREADS, ext_blocked_smem(4, g.ext_iters), st, 

@@ -8,7 +8,9 @@ launches, one call per cycle after warm-up cycles.
   the oracle at the same bar, plus conservation of the totals;
 * the batch of 256 independent gas-water instances (64^2 .. 512^2), one
   graph launch per batch cycle: every instance bitwise equal to the same
-  instance advanced alone, and seeded samples against the oracle."""
+  instance advanced alone, and seeded samples against the oracle;
+* the shock-bubble with the characteristic reconstruction and with the
+  HLLC face flux, three cycles each against the oracle."""
 import numpy as np
 import pytest
 
@@ -123,5 +125,26 @@ def test_shock_bubble_1024x256_characteristic(tmp_path):
     for a, b in zip(infos, oinfos):
         assert a["substeps"] == b["substeps"] and a["n_used"] == b["n_used"]
         assert abs(a["t"] - b["t"]) <= 1e-13 * b["t"]
+    assert o.status == 0
+    print("tile", shape, "relative L1 after 3 cycles:", compare(s, o, 1e-12))
+
+
+def test_shock_bubble_1024x256_hllc(tmp_path):
+    """The HLLC face flux at the same size and in the same launch
+    configuration (`bench.py --flux hllc`): graph launches, tile shape from
+    the autotuner, three cycles against the oracle."""
+    sif = _sif()
+    from paper_1905_03917_gb300 import autotune
+    case = inputs.shock_bubble(1024, 256)
+    case["cfg"] = dict(case["cfg"], flux="hllc")
+    s = sif.Solver(case["cfg"]).init_fluids(*_arrays(case))
+    shape, _ = autotune.tune(s, cache=str(tmp_path / "tune.json"), cycles=2)
+    infos = [s.step_multi_dt(1) for _ in range(3)]
+    o = _oracle(case)
+    oinfos = [o.step_multi_dt(1) for _ in range(3)]
+    for a, b in zip(infos, oinfos):
+        assert a["substeps"] == b["substeps"] and a["n_used"] == b["n_used"]
+        assert abs(a["t"] - b["t"]) <= 1e-13 * b["t"]
+        assert a["open_updates"] == b["open_updates"]
     assert o.status == 0
     print("tile", shape, "relative L1 after 3 cycles:", compare(s, o, 1e-12))
