@@ -63,7 +63,8 @@ struct sif_ctx {
   int use_graphs;
   int no_graph_env;    // SIF_NO_GRAPH=1: cycles issued from the host on purpose
   int ext_blocked;     // extension sweeps in shared memory per band tile (else one
-                       // launch per sweep or two; SIF_EXT_SWEEPS=1 asks for those)
+                       // launch per sweep or two: batch instances, or
+                       // SIF_EXT_SWEEPS=1)
   int require_graphs;  // SIF_REQUIRE_GRAPHS=1: a failed capture is an error
   int graph_bucket;  // band grid size baked into the graphs
   int num_sms;
@@ -2021,6 +2022,11 @@ extern "C" int sif_batch_create(int n, const sif_config *cfgs, sif_batch **out) 
     sif_config f = cfgs[i];
     f.cuda_stream = nullptr;  // every instance gets its own stream
     rc = sif_create(&f, &b->ctx[i]);
+    // the instances' kernels run side by side: the extension sweeps go one
+    // launch per sweep or two (small blocks that share SMs) rather than as
+    // band tiles whose CTAs each take a whole SM's registers (measured on
+    // the 256-instance batch: 244 against 274 ms a cycle)
+    if (rc == SIF_OK) b->ctx[i]->ext_blocked = 0;
   }
   if (rc == SIF_OK && cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess)
     rc = SIF_ECUDA;
