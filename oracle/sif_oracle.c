@@ -42,7 +42,9 @@
  *          identities of the transposed step, and central differences of
  *          a wall-pressure functional over 20 replayed steps.
  * Parity unpinned (checked only against the GPU): the number of extension
- * and reinitialisation sweeps and the band width (the paper gives none).
+ * and reinitialisation sweeps and the band width (the paper gives none),
+ * the larger-neighbour fallback of the mixing targets, and the interface
+ * viscous flux.
  */
 #include "sif_oracle.h"
 

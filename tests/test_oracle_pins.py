@@ -202,3 +202,59 @@ def test_mixing_at_45_degrees_uses_the_three_cells_toward_the_fluid():
     for jj, ii in [(j, i + 1), (j + 1, i), (j + 1, i + 1)]:
         r = d[:, jj, ii] / (U1 - U0)
         assert np.all(r > 0.0) and np.ptp(r) <= 1e-12 * r.max()
+
+
+# a level set (in cell sizes) whose cell (3, 3) is a small cell of fluid P
+# with every neighbour along its normal small too, while the diagonal cell
+# (4, 4), on the far side, is the only large one among its eight
+# neighbours (found by a seeded search over random cell values)
+FALLBACK_PHI = [
+    [0.9552, 0.6392, 0.3317, -0.8522, -0.9501, -0.5694, 0.4804],
+    [0.4172, 0.4063, -0.8709, -0.7265, 0.916, -0.0814, -0.1751],
+    [-0.5485, 0.6076, 0.4587, -0.5417, -0.9063, -0.5847, -0.299],
+    [0.5248, -0.3328, -0.649, 0.608, -0.7226, -0.9753, 0.5237],
+    [0.0857, -0.5202, -0.5325, -0.8012, 0.9313, 0.2032, -0.8916],
+    [-0.214, -0.6107, -0.0544, 0.8527, -0.4416, -0.2559, -0.9489],
+    [-0.1315, -0.3844, -0.4929, 0.301, -0.3898, -0.8517, -0.2369]]
+
+
+def test_mixing_falls_back_to_the_largest_of_the_eight_neighbours():
+    """Reading 8's second rule: a small cell none of whose neighbours along
+    its normal is large mixes with the largest of its eight neighbours when
+    that one is large, even on the far side of the normal.  The source's
+    state after mixing is then its own plus the exchange with that target,
+    M = (q_t a_s - q_s a_t) / (a_s + a_t), both from the pre-mix states."""
+    n = 7
+    phi = np.array(FALLBACK_PHI) / n
+    cfg = inputs.config(n, n, 1.0 / n, 1.0 / n, {"gamma": 1.4, "pinf": 0.0},
+                        {"gamma": 1.4, "pinf": 0.0}, ["reflect"] * 4)
+    o = O.Oracle(cfg)
+    w = inputs._uniform((n, n), 1.0, 0.0, 0.0, 1.0)
+    o.init(phi, w, w)
+    a = o.geometry()["alpha"]
+    i, j = 3, 3
+    # the preconditions, from the oracle's geometry: a small source, its
+    # normal's neighbours (x, y and diagonal, by the central-difference
+    # gradient of phi) all small, and one large neighbour of the eight
+    gx, gy = phi[j, i + 1] - phi[j, i - 1], phi[j + 1, i] - phi[j - 1, i]
+    sx, sy = (1 if gx >= 0 else -1), (1 if gy >= 0 else -1)
+    assert 0.0 < a[j, i] < 0.5
+    for (ii, jj) in ((i + sx, j), (i, j + sy), (i + sx, j + sy)):
+        assert a[jj, ii] < 0.5
+    large = [(ii, jj) for jj in (j - 1, j, j + 1) for ii in (i - 1, i, i + 1)
+             if (ii, jj) != (i, j) and a[jj, ii] >= 0.5]
+    assert large == [(4, 4)] and (sx, sy) == (-1, -1)
+    rng = np.random.default_rng(11)
+    qP = np.stack([a * rng.uniform(0.5, 2.0, size=(n, n)) for _ in range(4)])
+    o.set_state(np.zeros((4, n, n)).ravel(), qP.ravel(), phi.ravel())
+    o.mix_only(1)
+    out = o.state()[1][:, j, i]
+    aS, aT = a[j, i], a[4, 4]
+    expect = qP[:, j, i] + (qP[:, 4, 4] * aS - qP[:, j, i] * aT) / (aS + aT)
+    assert np.abs(out - expect).max() <= 1e-14 * np.abs(expect).max()
+    # what the other rules would have given differs: the normal's small
+    # neighbours larger than the source (third rule), each alone
+    for (ii, jj) in ((i - 1, j), (i - 1, j - 1)):
+        aT = a[jj, ii]
+        other = qP[:, j, i] + (qP[:, jj, ii] * aS - qP[:, j, i] * aT) / (aS + aT)
+        assert np.abs(out - other).max() > 1e-3 * np.abs(expect).max()
