@@ -43,8 +43,7 @@
  *          a wall-pressure functional over 20 replayed steps.
  * Parity unpinned (checked only against the GPU): the number of extension
  * and reinitialisation sweeps and the band width (the paper gives none),
- * the larger-neighbour fallback of the mixing targets, and the interface
- * viscous flux.
+ * and the interface viscous flux.
  */
 #include "sif_oracle.h"
 

@@ -258,3 +258,53 @@ def test_mixing_falls_back_to_the_largest_of_the_eight_neighbours():
         aT = a[jj, ii]
         other = qP[:, j, i] + (qP[:, jj, ii] * aS - qP[:, j, i] * aT) / (aS + aT)
         assert np.abs(out - other).max() > 1e-3 * np.abs(expect).max()
+
+
+# a small cell of fluid P at (3, 3) none of whose eight neighbours is large,
+# two of its three neighbours along the normal larger than itself (found
+# by a seeded search)
+LARGER_PHI = [
+    [0.459, 0.1005, -0.3754, 0.6933, -0.5151, -0.9433, 0.6208],
+    [-0.4813, -0.2628, -0.8927, -0.9472, 0.3934, -0.0881, -0.1716],
+    [0.2845, -0.4022, -0.29, -0.8526, -0.1154, -0.9, -0.9968],
+    [-0.275, -0.8849, -0.2323, -0.3196, 0.7491, -0.4147, -0.6388],
+    [-0.4156, 0.0833, -0.8958, 0.3905, -0.3218, -0.206, -0.4018],
+    [-0.3836, -0.8128, -0.7969, 0.1585, -0.7968, -0.3252, -0.5658],
+    [0.7711, -0.1644, -0.8841, -0.1825, -0.9758, -0.7902, 0.4431]]
+
+
+def test_mixing_falls_back_to_larger_neighbours_along_the_normal():
+    """Reading 8's third rule: with no large cell among the eight, the
+    source mixes with the neighbours along its normal (x, y, diagonal, by
+    the central-difference gradient of phi) that are larger than itself,
+    with weights n_x^2, n_y^2, |n_x n_y| normalised over those kept:
+    M_t = beta_t (q_t a_s - q_s a_t) / (a_s beta_t + a_t)."""
+    n = 7
+    phi = np.array(LARGER_PHI) / n
+    cfg = inputs.config(n, n, 1.0 / n, 1.0 / n, {"gamma": 1.4, "pinf": 0.0},
+                        {"gamma": 1.4, "pinf": 0.0}, ["reflect"] * 4)
+    o = O.Oracle(cfg)
+    w = inputs._uniform((n, n), 1.0, 0.0, 0.0, 1.0)
+    o.init(phi, w, w)
+    a = o.geometry()["alpha"]
+    i, j = 3, 3
+    assert 0.0 < a[j, i] < 0.5
+    assert max(a[j + dj, i + di] for dj in (-1, 0, 1) for di in (-1, 0, 1)
+               if (di, dj) != (0, 0)) < 0.5
+    gx, gy = phi[j, i + 1] - phi[j, i - 1], phi[j + 1, i] - phi[j - 1, i]
+    nx_, ny_ = gx / math.hypot(gx, gy), gy / math.hypot(gx, gy)
+    sx, sy = (1 if nx_ >= 0 else -1), (1 if ny_ >= 0 else -1)
+    cand = [((i + sx, j), nx_ * nx_), ((i, j + sy), ny_ * ny_), ((i + sx, j + sy), abs(nx_ * ny_))]
+    kept = [(c, wt) for c, wt in cand if wt > 0 and a[c[1], c[0]] > a[j, i]]
+    assert [c for c, _ in kept] == [(4, 3), (4, 4)]
+    rng = np.random.default_rng(12)
+    qP = np.stack([a * rng.uniform(0.5, 2.0, size=(n, n)) for _ in range(4)])
+    o.set_state(np.zeros((4, n, n)).ravel(), qP.ravel(), phi.ravel())
+    o.mix_only(1)
+    out = o.state()[1][:, j, i]
+    aS, W = a[j, i], sum(wt for _, wt in kept)
+    expect = qP[:, j, i].copy()
+    for (ti, tj), wt in kept:
+        b, aT = wt / W, a[tj, ti]
+        expect += b * (qP[:, tj, ti] * aS - qP[:, j, i] * aT) / (aS * b + aT)
+    assert np.abs(out - expect).max() <= 1e-14 * np.abs(expect).max()
