@@ -480,8 +480,8 @@ static void geometry(sif_ctx *c, bool after_ls = false) {
   launch_geometry(c->g, c->phi, c->alpha, c->ax, c->ay, c->sx, c->sy, c->cut, c->sc, c->st,
                   band ? c->band_ev : nullptr, band ? &c->sc->n_band : nullptr,
                   band ? band_work(c) : 0);
-  launch_band_map(c->g, c->phi, c->band_ev, c->bandmap, &c->sc->n_band, c->etiles, c->st);
-  launch_tile_lists(c->g, c->phi, c->tiles[0], c->tiles[1], c->sc, c->st);
+  launch_band_tiles(c->g, c->phi, c->band_ev, c->bandmap, c->etiles, c->tiles[0], c->tiles[1],
+                    c->sc, c->st);
   dbg(c, "geometry");
 }
 

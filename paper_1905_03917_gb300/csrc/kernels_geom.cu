@@ -202,39 +202,6 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
 }
 
 // ---------------------------------------------------------------------
-// fv tiles in which fluid k can hold an open face: a cell of the tile or of
-// its one-cell ring (ghosts included) lies on fluid k's side
-
-__global__ void k_tiles(Grid g, const double *__restrict__ p, int *t0, int *t1, int *n) {
-  SIF_TICK();
-  int tile = blockIdx.x;
-  int tx = tile % g.ntx, ty = tile / g.ntx;
-  int i0 = tx * g.tx - 1, j0 = ty * g.ty - 1;
-  int wy = g.dim == 2 ? g.ty + 2 : 1;
-  if (g.dim == 1) j0 = 0;
-  int any_pos = 0, any_neg = 0;
-  for (int r = threadIdx.x; r < (g.tx + 2) * wy; r += blockDim.x) {
-    int i = i0 + r % (g.tx + 2), j = j0 + r / (g.tx + 2);
-    if (i < -1 || i > g.nx || j < -1 || j > g.ny) continue;
-    double v = p[gidx(g, i, j)];
-    if (v >= 0.0) any_pos = 1;
-    else any_neg = 1;
-  }
-  any_pos = __syncthreads_or(any_pos);
-  any_neg = __syncthreads_or(any_neg);
-  if (threadIdx.x == 0) {
-    if (any_neg) t0[atomicAdd(&n[0], 1)] = tile;
-    if (any_pos) t1[atomicAdd(&n[1], 1)] = tile;
-  }
-}
-
-void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
-                       cudaStream_t st) {
-  cudaMemsetAsync(sc->n_tiles, 0, 2 * sizeof(int), st);
-  launch_k(k_tiles, g.ntx * g.nty, 128, 0, st, g, phi, tiles0, tiles1, sc->n_tiles);
-  sif_note_launches(1);
-}
-
 // ---------------------------------------------------------------------
 // initial data: (alpha U)_k = alpha_k U(W_k) from the primitive fields
 

@@ -22,45 +22,74 @@ int ext_tiles(const Grid &g) {
   return ((g.nx + SIF_ETILE - 1) / SIF_ETILE) * ((g.ny + SIF_ETILE - 1) / SIF_ETILE);
 }
 
-// one CTA per SIF_ETILE x SIF_ETILE tile: its band cells join the band list
-// (warp-aggregated positions) and the map, and a tile holding any of them
-// joins the extension tile list
-__global__ void k_band_mapped(Grid g, const double *__restrict__ p, int *band, int *map,
-                              int *nband, int *etiles) {
+// Blocks [0, ext_tiles): one SIF_ETILE x SIF_ETILE tile each, whose band
+// cells join the band list (warp-aggregated positions) and the map, and
+// which joins the extension tile list if it holds any.  Blocks from
+// ext_tiles on: one finite-volume tile each, which joins fluid k's tile
+// list if a cell of the tile or of its one-cell ring (ghosts included) lies
+// on fluid k's side (where fluid k can hold an open face).  Both read only
+// phi.
+__global__ void k_band_tiles(Grid g, const double *__restrict__ p, int *band, int *map,
+                             int *etiles, int *t0, int *t1, Scalars *sc) {
   SIF_TICK();
   const int tilesx = (g.nx + SIF_ETILE - 1) / SIF_ETILE;
-  const int i = (blockIdx.x % tilesx) * SIF_ETILE + (threadIdx.x % SIF_ETILE);
-  const int j = (blockIdx.x / tilesx) * SIF_ETILE + (threadIdx.x / SIF_ETILE);
-  bool in = false;
-  int c = 0;
-  if (i < g.nx && j < g.ny) {
-    c = gidx(g, i, j);
-    in = fabs(p[c]) < g.band * g.h;
-  }
-  unsigned mask = __ballot_sync(0xffffffffu, in);
-  if (mask) {
-    int lane = threadIdx.x & 31, lead = __ffs(mask) - 1;
-    int base = 0;
-    if (lane == lead) base = atomicAdd(nband, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, lead);
-    if (in) {
-      int pos = base + __popc(mask & ((1u << lane) - 1u));
-      band[pos] = c;
-      map[c] = pos;
+  const int nt = tilesx * ((g.ny + SIF_ETILE - 1) / SIF_ETILE);
+  if ((int)blockIdx.x < nt) {
+    const int i = (blockIdx.x % tilesx) * SIF_ETILE + (threadIdx.x % SIF_ETILE);
+    const int j = (blockIdx.x / tilesx) * SIF_ETILE + (threadIdx.x / SIF_ETILE);
+    bool in = false;
+    int c = 0;
+    if (i < g.nx && j < g.ny) {
+      c = gidx(g, i, j);
+      in = fabs(p[c]) < g.band * g.h;
     }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    if (mask) {
+      int lane = threadIdx.x & 31, lead = __ffs(mask) - 1;
+      int base = 0;
+      if (lane == lead) base = atomicAdd(&sc->n_band, __popc(mask));
+      base = __shfl_sync(0xffffffffu, base, lead);
+      if (in) {
+        int pos = base + __popc(mask & ((1u << lane) - 1u));
+        band[pos] = c;
+        map[c] = pos;
+      }
+    }
+    if (__syncthreads_or(in) && threadIdx.x == 0)
+      etiles[atomicAdd(&sc->n_etile, 1)] = blockIdx.x;
+    return;
   }
-  if (__syncthreads_or(in) && threadIdx.x == 0) etiles[atomicAdd(nband + 1, 1)] = blockIdx.x;
+  const int tile = blockIdx.x - nt;
+  const int tx = tile % g.ntx, ty = tile / g.ntx;
+  const int i0 = tx * g.tx - 1, j0 = g.dim == 2 ? ty * g.ty - 1 : 0;
+  const int wy = g.dim == 2 ? g.ty + 2 : 1;
+  int any_pos = 0, any_neg = 0;
+  for (int r = threadIdx.x; r < (g.tx + 2) * wy; r += blockDim.x) {
+    int i = i0 + r % (g.tx + 2), j = j0 + r / (g.tx + 2);
+    if (i < -1 || i > g.nx || j < -1 || j > g.ny) continue;
+    double v = p[gidx(g, i, j)];
+    if (v >= 0.0) any_pos = 1;
+    else any_neg = 1;
+  }
+  any_pos = __syncthreads_or(any_pos);
+  any_neg = __syncthreads_or(any_neg);
+  if (threadIdx.x == 0) {
+    if (any_neg) t0[atomicAdd(&sc->n_tiles[0], 1)] = tile;
+    if (any_pos) t1[atomicAdd(&sc->n_tiles[1], 1)] = tile;
+  }
 }
 
 // the whole map is cleared (not only the previous band's entries): a reset
 // of the device scalars (initialisation, checkpoint restore) loses the
 // previous band's count, and the clear must not depend on it
-void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
-                     int *etiles, cudaStream_t st) {
+void launch_band_tiles(const Grid &g, const double *phi, int *band, int *map, int *etiles,
+                       int *tiles0, int *tiles1, Scalars *sc, cudaStream_t st) {
+  static_assert(offsetof(Scalars, n_tiles) == offsetof(Scalars, n_band) + 2 * sizeof(int),
+                "the band, extension-tile and finite-volume tile counts are cleared together");
   cudaMemsetAsync(map, 0xff, sizeof(int) * (size_t)g.PX * g.PY, st);
-  cudaMemsetAsync(nband, 0, 2 * sizeof(int), st);
-  launch_k(k_band_mapped, ext_tiles(g), SIF_ETILE * SIF_ETILE, 0, st, g, phi, band, map, nband,
-                                                               etiles);
+  cudaMemsetAsync(&sc->n_band, 0, 4 * sizeof(int), st);
+  launch_k(k_band_tiles, ext_tiles(g) + g.ntx * g.nty, SIF_ETILE * SIF_ETILE, 0, st, g, phi,
+           band, map, etiles, tiles0, tiles1, sc);
   sif_note_launches(1);
 }
 

@@ -59,8 +59,9 @@ struct Scalars {
   int f1, mode, last, sub;
   int err;
   int n_band, n_etile;        // interaction-step band and its extension tiles
+  int n_tiles[2];             // finite-volume tiles per fluid (cleared with the two above)
   int n_band_ls, n_rext;      // level-set step band and its face neighbours
-  int n_cut, n_tiles[2];
+  int n_cut, n_pad_;
   double dtk_raw[2];
   double dt2_first;             // fluid-2 step chosen at the start of the cycle
   unsigned long long updates;   // (cell, fluid) stage updates issued (active-tile cells)
@@ -408,12 +409,11 @@ void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax
 // counts[0] = band size, counts[1] = band + face neighbours (if rext)
 void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, int *counts,
                        cudaStream_t st);
-void launch_tile_lists(const Grid &g, const double *phi, int *tiles0, int *tiles1, Scalars *sc,
-                       cudaStream_t st);
-// band list and map, and the list of SIF_ETILE^2 tiles holding band cells
-// (count in nband[1]) for the blocked extension
-void launch_band_map(const Grid &g, const double *phi, int *band, int *map, int *nband,
-                     int *etiles, cudaStream_t st);
+// band list and map, the list of SIF_ETILE^2 tiles holding band cells (for
+// the blocked extension) and the finite-volume tile lists of both fluids,
+// in one launch (counts in sc->n_band, n_etile, n_tiles)
+void launch_band_tiles(const Grid &g, const double *phi, int *band, int *map, int *etiles,
+                       int *tiles0, int *tiles1, Scalars *sc, cudaStream_t st);
 // edge of the square tiles of the blocked extension
 #define SIF_ETILE 16
 // sweep counts the blocked extension takes (its tile's halo is that wide)
