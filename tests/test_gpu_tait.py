@@ -43,26 +43,33 @@ def test_tait_parity(name, multi):
 
 
 def test_circle_recovery_laplace_jump():
-    """The square liquid drop at 128^2 after t = 2 (accelerated cycles):
-    the pressure inside exceeds the gas pressure outside by sigma / R, R
-    the radius of the circle of the drop's area."""
+    """The square liquid drop at 128^2 (accelerated cycles): the pressure
+    inside exceeds the gas pressure outside by sigma / R, R the radius of
+    the circle of the drop's area.  The weakly compressible drop keeps
+    ringing (single snapshots of the jump scatter by about 120 around their
+    mean after t = 1), so the jump is averaged over eleven snapshots from
+    t = 1.5 to the paper's t = 2."""
     sif = _sif()
     case = inputs.circle_recovery(128)
     n = 128
     s = sif.Solver(case["cfg"]).init_fluids(*_arrays(case))
-    while s.t < 2.0:
-        s.step_multi_dt(200, t_end=2.0)
-    qN, qP, phi = s.state()
     X, Y = np.meshgrid((np.arange(n) + 0.5) / n, (np.arange(n) + 0.5) / n)
     r = np.hypot(X - 0.5, Y - 0.5)
     R = math.sqrt(0.04 / math.pi)
-    inner, outer = (phi < -2.0 / n) & (r < R - 2.0 / n), (phi > 2.0 / n) & (r < 0.45)
     B, rho0, p0, g = 5.0e5, 1000.0, 1.0e3, 7.15
-    p_in = B * ((qN[0][inner] / rho0) ** g - 1.0) + p0
-    p_out = 100.0 * (qP[0][outer] ** 1.4 - 1.0) + 1.0e3
-    jump = float(p_in.mean() - p_out.mean())
+    jumps = []
+    for t in np.linspace(1.5, 2.0, 11):
+        while s.t < t - 1e-12:
+            s.step_multi_dt(200, t_end=t)
+        qN, qP, phi = s.state()
+        inner, outer = (phi < -2.0 / n) & (r < R - 2.0 / n), (phi > 2.0 / n) & (r < 0.45)
+        p_in = B * ((qN[0][inner] / rho0) ** g - 1.0) + p0
+        p_out = 100.0 * (qP[0][outer] ** 1.4 - 1.0) + 1.0e3
+        jumps.append(float(p_in.mean() - p_out.mean()))
+    jump = float(np.mean(jumps))
     area = float((phi < 0).sum()) / n ** 2
-    print(f"Laplace jump {jump:.2f} (sigma/R = {73.0 / R:.5f}), drop area {area:.5f}")
+    print(f"Laplace jump {jump:.2f} (sigma/R = {73.0 / R:.5f}; snapshots "
+          f"{[round(j, 1) for j in jumps]}), drop area {area:.5f}")
     assert abs(area - 0.04) <= 0.02 * 0.04
     assert abs(jump - 73.0 / R) <= 0.10 * 73.0 / R
 
