@@ -42,8 +42,7 @@
  *          identities of the transposed step, and central differences of
  *          a wall-pressure functional over 20 replayed steps.
  * Parity unpinned (checked only against the GPU): the number of extension
- * and reinitialisation sweeps and the band width (the paper gives none),
- * and the interface viscous flux.
+ * and reinitialisation sweeps and the band width (the paper gives none).
  */
 #include "sif_oracle.h"
 
@@ -590,6 +589,14 @@ static double curvature(const orc_ctx *o, const double *p, int i, int j) {
 static void visc_stress(double mu, double ux, double uy, double vx, double vy, double *txx,
                         double *txy, double *tyy);
 
+/* velocity component m (1: u, 2: v) at cell (i, j) of the field that is
+ * continuous across the interface: that of the fluid on whose side of the
+ * interface the cell's centre lies (phi < 0: N) */
+static double vel_across(const orc_ctx *o, const double *p, int m, int i, int j) {
+  int c = ID(o, i, j);
+  return o->w[p[c] < 0.0 ? 0 : 1][m][c];
+}
+
 /* X for every cut cell (|S| > 0): fluid N receives momentum -p_I,N S and
  * energy -p_I,N u_I |S|, fluid P momentum p_I,P S and energy p_I,P u_I |S|;
  * no mass crosses.  Without surface tension p_I,N = p_I,P; with it the
@@ -627,28 +634,35 @@ static void interface(orc_ctx *o, const double *p) {
       o->xp[0][c] = psP * Sx;
       o->xp[1][c] = psP * Sy;
       o->xp[2][c] = psP * us * Sm;
-      /* viscous traction of each fluid on its side of the interface: tau_k
-       * from its stencil state's central differences at the cut cell,
-       * applied through its outward interface vector (+S for N, -S for P) */
-      for (int k = 0; k < 2; k++) {
-        if (!(o->c.mu[k] > 0.0)) continue;
-        const double *u = o->w[k][1], *v = o->w[k][2];
-        double ux = (u[ID(o, i + 1, j)] - u[ID(o, i - 1, j)]) / (2.0 * o->c.dx);
-        double vx = (v[ID(o, i + 1, j)] - v[ID(o, i - 1, j)]) / (2.0 * o->c.dx);
+      /* viscous traction across the interface (Eq. 5's interface term):
+       * the stress of the velocity field that is continuous across it (at
+       * every cell the velocity of the fluid on whose side of the
+       * interface its centre lies), by central differences at the cut
+       * cell, with the harmonic mean of the two viscosities; fluid N
+       * receives it through S and fluid P the opposite, each with its work
+       * at that field's velocity in the cut cell (momentum and energy leave
+       * one fluid as they enter the other) */
+      if (o->c.mu[0] > 0.0 && o->c.mu[1] > 0.0) {
+        double muI = 2.0 * o->c.mu[0] * o->c.mu[1] / (o->c.mu[0] + o->c.mu[1]);
+        double ux = (vel_across(o, p, 1, i + 1, j) - vel_across(o, p, 1, i - 1, j)) /
+                    (2.0 * o->c.dx);
+        double vx = (vel_across(o, p, 2, i + 1, j) - vel_across(o, p, 2, i - 1, j)) /
+                    (2.0 * o->c.dx);
         double uy = 0.0, vy = 0.0;
         if (o->c.dim == 2) {
-          uy = (u[ID(o, i, j + 1)] - u[ID(o, i, j - 1)]) / (2.0 * o->c.dy);
-          vy = (v[ID(o, i, j + 1)] - v[ID(o, i, j - 1)]) / (2.0 * o->c.dy);
+          uy = (vel_across(o, p, 1, i, j + 1) - vel_across(o, p, 1, i, j - 1)) / (2.0 * o->c.dy);
+          vy = (vel_across(o, p, 2, i, j + 1) - vel_across(o, p, 2, i, j - 1)) / (2.0 * o->c.dy);
         }
         double txx, txy, tyy;
-        visc_stress(o->c.mu[k], ux, uy, vx, vy, &txx, &txy, &tyy);
-        double sg = k == 0 ? 1.0 : -1.0;
-        double fx = sg * (txx * Sx + txy * Sy), fy = sg * (txy * Sx + tyy * Sy);
-        double e = u[c] * fx + v[c] * fy;
-        double *const *X = k == 0 ? o->xn : o->xp;
-        X[0][c] = X[0][c] + fx;
-        X[1][c] = X[1][c] + fy;
-        X[2][c] = X[2][c] + e;
+        visc_stress(muI, ux, uy, vx, vy, &txx, &txy, &tyy);
+        double fx = txx * Sx + txy * Sy, fy = txy * Sx + tyy * Sy;
+        double e = vel_across(o, p, 1, i, j) * fx + vel_across(o, p, 2, i, j) * fy;
+        o->xn[0][c] = o->xn[0][c] + fx;
+        o->xn[1][c] = o->xn[1][c] + fy;
+        o->xn[2][c] = o->xn[2][c] + e;
+        o->xp[0][c] = o->xp[0][c] - fx;
+        o->xp[1][c] = o->xp[1][c] - fy;
+        o->xp[2][c] = o->xp[2][c] - e;
       }
       o->ul[0][c] = us * nxv;
       o->ul[1][c] = us * nyv;

@@ -302,23 +302,34 @@ __global__ void k_interface(Grid g, const double *__restrict__ n0, const double 
       xm2[c] = -ps * us * Sm;
       sP = fmax(sP, (fabs(us) + cs) * fac);
     }
-    // viscous traction of the lane's fluid on its side of the interface:
-    // its stencil state's stress by central differences at the cut cell,
-    // through its outward interface vector (+S for N, -S for P; fluid P's
-    // planes hold the negated flux)
-    if (g.mu[side] > 0.0) {
-      const double *u = side == 0 ? n1 : p1, *v = side == 0 ? n2 : p2;
-      const double ux = (u[gidx(g, i + 1, j)] - u[gidx(g, i - 1, j)]) / (2.0 * g.dx);
-      const double vx = (v[gidx(g, i + 1, j)] - v[gidx(g, i - 1, j)]) / (2.0 * g.dx);
+    // viscous traction across the interface: the stress of the velocity
+    // field that is continuous across it (at every cell the velocity of
+    // the fluid on whose side its centre lies) by central differences at
+    // the cut cell, with the harmonic mean of the viscosities; fluid N
+    // receives it through S, fluid P the opposite (its planes hold the
+    // negated flux, so both lanes add the same values), each with its work
+    // at that field's velocity in the cut cell
+    if (g.mu[0] > 0.0 && g.mu[1] > 0.0) {
+      const double muI = 2.0 * g.mu[0] * g.mu[1] / (g.mu[0] + g.mu[1]);
+      auto U = [&](int ii, int jj) {
+        const int cc = gidx(g, ii, jj);
+        return phi[cc] < 0.0 ? n1[cc] : p1[cc];
+      };
+      auto V = [&](int ii, int jj) {
+        const int cc = gidx(g, ii, jj);
+        return phi[cc] < 0.0 ? n2[cc] : p2[cc];
+      };
+      const double ux = (U(i + 1, j) - U(i - 1, j)) / (2.0 * g.dx);
+      const double vx = (V(i + 1, j) - V(i - 1, j)) / (2.0 * g.dx);
       double uy = 0.0, vy = 0.0;
       if (g.dim == 2) {
-        uy = (u[gidx(g, i, j + 1)] - u[gidx(g, i, j - 1)]) / (2.0 * g.dy);
-        vy = (v[gidx(g, i, j + 1)] - v[gidx(g, i, j - 1)]) / (2.0 * g.dy);
+        uy = (U(i, j + 1) - U(i, j - 1)) / (2.0 * g.dy);
+        vy = (V(i, j + 1) - V(i, j - 1)) / (2.0 * g.dy);
       }
       double txx, txy, tyy;
-      visc_stress(g.mu[side], ux, uy, vx, vy, txx, txy, tyy);
+      visc_stress(muI, ux, uy, vx, vy, txx, txy, tyy);
       const double fx = txx * Sx + txy * Sy, fy = txy * Sx + tyy * Sy;
-      const double e = u[c] * fx + v[c] * fy;
+      const double e = U(i, j) * fx + V(i, j) * fy;
       double *X0 = side == 0 ? xn0 : xm0, *X1 = side == 0 ? xn1 : xm1, *X2 = side == 0 ? xn2 : xm2;
       X0[c] = X0[c] + fx;
       X1[c] = X1[c] + fy;

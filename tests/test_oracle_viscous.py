@@ -79,3 +79,44 @@ def test_sound_wave_is_damped_by_the_normal_stresses():
         ratio = a_v / a_0
         exact = math.exp(-(2.0 / 3.0) * mu * K2 * T)
         assert abs(ratio / exact - 1.0) < 2e-3, (ratio, exact)
+
+
+def _rayleigh(n, muN, muP, T=0.5, U=0.1, m=4):
+    """Fluid P sliding at U over fluid N at rest, the same gas on both
+    sides, a flat interface 0.3 of a cell above y = 1/2 (reflective walls
+    at y = 0, 1, periodic in x).  Returns fluid N's x momentum per unit
+    length at T against the closed form, and the totals before and after."""
+    d = 1.0 / n
+    cfg = inputs.config(m, n, d, d, inputs.AIR, inputs.AIR,
+                        ["periodic", "periodic", "reflect", "reflect"], mu=(muN, muP))
+    X, Y = inputs._centres(cfg)
+    phi = Y - (0.5 + 0.3 * d)
+    pN = inputs._uniform(X.shape, 1.0, 0.0, 0.0, 100.0)
+    pP = inputs._uniform(X.shape, 1.0, U, 0.0, 100.0)
+    o = O.Oracle(cfg).init(phi, pN, pP)
+    I0 = o.integrals()
+    while o.t < T * (1 - 1e-14):
+        o.step_single_dt(1, T)
+    assert o.status == 0
+    I1 = o.integrals()
+    # two semi-infinite layers of equal density: the interface takes the
+    # velocity U e_P / (e_N + e_P), e_k = sqrt(mu_k), and fluid N's
+    # momentum is that velocity times 2 sqrt(nu_N t / pi)
+    eN, eP = math.sqrt(muN), math.sqrt(muP)
+    exact = U * eP / (eN + eP) * 2.0 * math.sqrt(muN * T / math.pi)
+    return I1[0, 1] / (m * d) / exact - 1.0, I0, I1
+
+
+@pytest.mark.parametrize("mus", [(0.01, 0.01), (0.01, 0.04)])
+def test_interface_transmits_shear(mus):
+    """The viscous traction across the interface couples the two fluids
+    without slip: the momentum fluid N takes from fluid P sliding over it
+    follows the two-layer diffusion solution (first order in the cell
+    size at the interface: 3 % off at 128 cells), while momentum and
+    energy only move between the fluids."""
+    e64, _, _ = _rayleigh(64, *mus)
+    e128, I0, I1 = _rayleigh(128, *mus)
+    assert abs(e128) < 0.05 and abs(e128) < abs(e64) and abs(e64) < 0.1, (e64, e128)
+    tot0, tot1 = I0.sum(axis=0), I1.sum(axis=0)
+    assert abs(tot1[1] - tot0[1]) <= 1e-13 * abs(tot0[3])
+    assert abs(tot1[3] / tot0[3] - 1.0) <= 1e-13
