@@ -193,11 +193,12 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
   // derivative diverges there and a tiny step would pass for convergence)
   if (p < pfloor) p = pfloor + 0.5 * (fmax(pl - jump, pr) - pfloor);
   const double own = L ? jump : 0.0;  // this lane's star pressure is p + own
+  const SideConst sk = side_const(rho, pk, gk, pik, ck, baro);
   int it = 0, conv = 0, done = 0;
   double f, df;
   while (it < maxit) {
     it++;
-    riemann_side(p + own, rho, pk, gk, pik, ck, f, df, baro);
+    riemann_side_k(p + own, sk, f, df);
     double fo = __shfl_xor_sync(pair, f, 1), dfo = __shfl_xor_sync(pair, df, 1);
     double fl = L ? f : fo, fr = L ? fo : f, dfl = L ? df : dfo, dfr = L ? dfo : df;
     double F = fl + fr + (ur - ul);
@@ -212,7 +213,7 @@ __device__ inline int riemann_solve_pair(unsigned pair, int side, double rho, do
     if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
   }
   ps = p + own;
-  riemann_side(ps, rho, pk, gk, pik, ck, f, df, baro);
+  riemann_side_k(ps, sk, f, df);
   double fo = __shfl_xor_sync(pair, f, 1);
   double fl = L ? f : fo, fr = L ? fo : f;
   us = 0.5 * (ul + ur) + 0.5 * (fr - fl);

@@ -734,8 +734,9 @@ struct MixQ {
 };
 
 // plan of every band cell as a source, with the amounts it exchanges with
-// its targets, M = beta (q_t as - q_s at) / (as beta + at), computed from
-// the states before mixing
+// its targets, M = beta (q_t as - q_s at) / (as beta + at) (as the product
+// of the difference and beta / (as beta + at)), computed from the states
+// before mixing
 __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__ alpha,
                             const double *__restrict__ phi, const int *__restrict__ band,
                             const int *nband, MixPlan *plan, int cap) {
@@ -755,9 +756,10 @@ __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__
     double *const *q = Q.q[k];
     for (int t = 0; t < s.nt; t++) {
       int tc = s.tc[t];
-      double den = s.as * s.beta[t] + s.at[t];
-      for (int m = 0; m < 4; m++)
-        s.M[t][m] = s.beta[t] * (q[m][tc] * s.as - q[m][c] * s.at[t]) / den;
+      // one division per target: beta / (as beta + at) times each
+      // component's difference
+      const double bd = s.beta[t] / (s.as * s.beta[t] + s.at[t]);
+      for (int m = 0; m < 4; m++) s.M[t][m] = (q[m][tc] * s.as - q[m][c] * s.at[t]) * bd;
     }
     plan[(size_t)k * cap + idx] = s;
   }

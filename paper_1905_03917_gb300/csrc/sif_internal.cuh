@@ -342,6 +342,49 @@ __device__ inline void riemann_side(double p, double rho, double pk, double g, d
   }
 }
 
+// riemann_side with the quantities that do not depend on p computed once
+// per Riemann problem (the same operations, so the same values)
+struct SideConst {
+  double rho, pk, g, pi, P, A, B, fr, dr, e, eb, gP;
+  int baro;
+};
+
+__device__ inline SideConst side_const(double rho, double pk, double g, double pi, double ck,
+                                       int baro) {
+  SideConst s;
+  s.rho = rho, s.pk = pk, s.g = g, s.pi = pi, s.baro = baro;
+  s.P = pk + pi;
+  s.A = 2.0 / ((g + 1.0) * rho);
+  s.B = (g - 1.0) / (g + 1.0) * s.P;
+  s.fr = 2.0 * ck / (g - 1.0);
+  s.dr = 1.0 / (rho * ck);
+  s.e = (g - 1.0) / (2.0 * g);
+  s.eb = -1.0 / g - 1.0;
+  s.gP = g * s.P;
+  return s;
+}
+
+__device__ inline void riemann_side_k(double p, const SideConst &s, double &f, double &df) {
+  const double Pp = p + s.pi;
+  if (p > s.pk && s.baro) {
+    double x = (p - s.pk) / s.P;
+    double a = -expm1(-log1p(x) / s.g);
+    double gsq = (p - s.pk) * a / s.rho;
+    double dg = (a + (p - s.pk) * pos_pow(1.0 + x, s.eb) / s.gP) / s.rho;
+    f = sqrt(gsq);
+    df = dg / (2.0 * f);
+  } else if (p > s.pk) {
+    double qr = sqrt(s.A / (Pp + s.B));
+    f = (p - s.pk) * qr;
+    df = qr * (1.0 - 0.5 * (p - s.pk) / (Pp + s.B));
+  } else {
+    double r = Pp / s.P;
+    double ra = pos_pow(r, s.e);
+    f = s.fr * (ra - 1.0);
+    df = s.dr * (ra / r);
+  }
+}
+
 __device__ inline double riemann_star_density(double p, double rho, double pk, double g, double pi,
                                              int baro = 0) {
   double r = (p + pi) / (pk + pi);
