@@ -1430,35 +1430,11 @@ extern "C" int sif_get_state(sif_ctx *c, double *qN, double *qP, double *phi, in
   cudaSetDevice(c->cfg.device);
   size_t n = (size_t)ncell(c);
   int rc = SIF_OK;
-  if (mem == SIF_HOST) {
-    // the requested planes packed into the scratch buffer by one kernel,
-    // then one contiguous copy per array
-    side_join(c);
-    double *src[9];
-    int np = 0;
-    if (qN)
-      for (int m = 0; m < 4; m++) src[np++] = c->q[0][m];
-    if (qP)
-      for (int m = 0; m < 4; m++) src[np++] = c->q[1][m];
-    if (phi) src[np++] = c->phi;
-    if (np > 0) launch_pack(c->g, c->tmp, np, src, c->st);
-    double *b = c->tmp;
-    if (qN) {
-      CK(cudaMemcpyAsync(qN, b, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->st));
-      b += 4 * n;
-    }
-    if (qP) {
-      CK(cudaMemcpyAsync(qP, b, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->st));
-      b += 4 * n;
-    }
-    if (phi) CK(cudaMemcpyAsync(phi, b, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
-  } else {
-    for (int m = 0; m < 4 && !rc; m++) {
-      if (qN) rc = get_plane(c, qN + m * n, c->q[0][m], mem);
-      if (qP && !rc) rc = get_plane(c, qP + m * n, c->q[1][m], mem);
-    }
-    if (phi && !rc) rc = get_plane(c, phi, c->phi, mem);
+  for (int m = 0; m < 4 && !rc; m++) {
+    if (qN) rc = get_plane(c, qN + m * n, c->q[0][m], mem);
+    if (qP && !rc) rc = get_plane(c, qP + m * n, c->q[1][m], mem);
   }
+  if (phi && !rc) rc = get_plane(c, phi, c->phi, mem);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->st));
   return SIF_OK;
@@ -1469,22 +1445,9 @@ extern "C" int sif_set_state(sif_ctx *c, const double *qN, const double *qP, con
   if (!c || !qN || !qP || !phi || (mem != SIF_HOST && mem != SIF_DEVICE)) return SIF_EINVAL;
   cudaSetDevice(c->cfg.device);
   size_t n = (size_t)ncell(c);
-  int rc = SIF_OK;
-  if (mem == SIF_HOST) {
-    // three contiguous copies into the scratch buffer (free between calls)
-    // at the link's bandwidth, then one kernel into the padded planes
-    side_join(c);
-    CK(cudaMemcpyAsync(c->tmp, qN, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->tmp + 4 * n, qP, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->tmp + 8 * n, phi, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
-    double *dst[9] = {c->q[0][0], c->q[0][1], c->q[0][2], c->q[0][3], c->q[1][0],
-                      c->q[1][1], c->q[1][2], c->q[1][3], c->phi};
-    launch_unpack(c->g, c->tmp, 9, dst, c->st);
-  } else {
-    rc = put_plane(c, c->phi, phi, mem);
-    for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->q[0][m], qN + m * n, mem);
-    for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->q[1][m], qP + m * n, mem);
-  }
+  int rc = put_plane(c, c->phi, phi, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->q[0][m], qN + m * n, mem);
+  for (int m = 0; m < 4 && !rc; m++) rc = put_plane(c, c->q[1][m], qP + m * n, mem);
   if (rc) return rc;
   geometry(c);
   c->hbuf[0] = t;

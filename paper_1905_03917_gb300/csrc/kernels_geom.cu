@@ -203,56 +203,6 @@ void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, i
 
 // ---------------------------------------------------------------------
 // ---------------------------------------------------------------------
-// host state through a contiguous device copy: nplanes planes of nx*ny
-// values (x fastest) in buf, to or from the padded planes dst/src
-
-struct Planes9 {
-  double *p[9];
-};
-
-__global__ void k_unpack(Grid g, const double *__restrict__ buf, int nplanes, Planes9 dst) {
-  SIF_TICK();
-  const long long n = (long long)g.nx * g.ny;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nplanes * n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(t / n);
-    const int cell = (int)(t % n);
-    dst.p[q][gidx(g, cell % g.nx, cell / g.nx)] = buf[t];
-  }
-}
-
-__global__ void k_pack(Grid g, double *buf, int nplanes, Planes9 src) {
-  SIF_TICK();
-  const long long n = (long long)g.nx * g.ny;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nplanes * n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(t / n);
-    const int cell = (int)(t % n);
-    buf[t] = src.p[q][gidx(g, cell % g.nx, cell / g.nx)];
-  }
-}
-
-static int pack_blocks(const Grid &g, int nplanes) {
-  long long b = ((long long)g.nx * g.ny * nplanes + 255) / 256;
-  return b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : (int)b);
-}
-
-void launch_unpack(const Grid &g, const double *buf, int nplanes, double *const dst[],
-                   cudaStream_t st) {
-  Planes9 P = {};
-  for (int q = 0; q < nplanes; q++) P.p[q] = dst[q];
-  launch_k(k_unpack, pack_blocks(g, nplanes), 256, 0, st, g, buf, nplanes, P);
-  sif_note_launches(1);
-}
-
-void launch_pack(const Grid &g, double *buf, int nplanes, double *const src[], cudaStream_t st) {
-  Planes9 P = {};
-  for (int q = 0; q < nplanes; q++) P.p[q] = src[q];
-  launch_k(k_pack, pack_blocks(g, nplanes), 256, 0, st, g, buf, nplanes, P);
-  sif_note_launches(1);
-}
-
-// ---------------------------------------------------------------------
 // initial data: (alpha U)_k = alpha_k U(W_k) from the primitive fields
 
 __global__ void k_init_q(Grid g, double *qN0, double *qN1, double *qN2, double *qN3,

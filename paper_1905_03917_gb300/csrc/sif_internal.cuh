@@ -452,11 +452,6 @@ void launch_geometry(const Grid &g, const double *phi, double *alpha, double *ax
 // counts[0] = band size, counts[1] = band + face neighbours (if rext)
 void launch_band_lists(const Grid &g, const double *phi, int *band, int *rext, int *counts,
                        cudaStream_t st);
-// nplanes (<= 9) planes of nx*ny values, x fastest, in the contiguous
-// buffer buf to (unpack) or from (pack) the padded planes
-void launch_unpack(const Grid &g, const double *buf, int nplanes, double *const dst[],
-                   cudaStream_t st);
-void launch_pack(const Grid &g, double *buf, int nplanes, double *const src[], cudaStream_t st);
 // band list and map, the list of SIF_ETILE^2 tiles holding band cells (for
 // the blocked extension) and the finite-volume tile lists of both fluids,
 // in one launch (counts in sc->n_band, n_etile, n_tiles)
