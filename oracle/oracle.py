@@ -150,11 +150,12 @@ def make_config(cfg: dict) -> _Config:
     c.sigma = float(cfg.get("sigma", 0.0))
     mu = cfg.get("mu", (0.0, 0.0))
     c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
-    # Tait's equation per fluid: (B, rho0, p0) or None for a stiffened gas
+    # face flux: "lf" (WENO5 on Lax-Friedrichs split fluxes) or "hllc"
     fl = cfg.get("flux", "lf")
     if fl not in FLUXES:
         raise ValueError(f"flux must be one of {sorted(FLUXES)}")
     c.flux = FLUXES[fl]
+    # Tait's equation per fluid: (B, rho0, p0) or None for a stiffened gas
     for k, t in enumerate(cfg.get("tait", (None, None))):
         if t is not None:
             c.tait[k] = 1
