@@ -10,7 +10,9 @@ launches, one call per cycle after warm-up cycles.
   graph launch per batch cycle: every instance bitwise equal to the same
   instance advanced alone, and seeded samples against the oracle;
 * the shock-bubble with the characteristic reconstruction and with the
-  HLLC face flux, three cycles each against the oracle."""
+  HLLC face flux, three cycles each against the oracle;
+* the translating Tait droplet (the paper's Table 1 case) at 256^2, four
+  cycles against the oracle."""
 import numpy as np
 import pytest
 
@@ -148,3 +150,24 @@ def test_shock_bubble_1024x256_hllc(tmp_path):
         assert a["open_updates"] == b["open_updates"]
     assert o.status == 0
     print("tile", shape, "relative L1 after 3 cycles:", compare(s, o, 1e-12))
+
+
+def test_droplet_translation_256_bench_configuration(tmp_path):
+    """The paper's Table 1 case (Tait water in air, periodic) at 256^2 in the
+    launch configuration `bench.py --workload paper_table1` times: graph
+    launches, tile shape from the autotuner, four accelerated cycles of
+    about four water sub-steps against the oracle."""
+    sif = _sif()
+    from paper_1905_03917_gb300 import autotune
+    case = inputs.droplet_translation(256)
+    s = sif.Solver(case["cfg"]).init_fluids(*_arrays(case))
+    shape, _ = autotune.tune(s, cache=str(tmp_path / "tune.json"), cycles=2)
+    infos = [s.step_multi_dt(1) for _ in range(4)]
+    o = _oracle(case)
+    oinfos = [o.step_multi_dt(1) for _ in range(4)]
+    for a, b in zip(infos, oinfos):
+        assert a["substeps"] == b["substeps"] >= 3
+        assert abs(a["t"] - b["t"]) <= 1e-13 * b["t"]
+        assert a["open_updates"] == b["open_updates"]
+    assert o.status == 0
+    print("tile", shape, "relative L1 after 4 cycles:", compare(s, o, 1e-12))
