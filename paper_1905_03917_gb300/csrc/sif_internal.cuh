@@ -87,8 +87,8 @@ static __device__ unsigned long long g_tu_launches;
       atomicAdd(&g_tu_launches, 1ull);                                                \
   } while (0)
 
-// kernel launch through the launch-configuration form (every launch site
-// goes through here)
+// kernel launch through the launch-configuration form (the geometry, band,
+// plan and adjoint kernels; the finite-volume stage sets its priority)
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                      cudaStream_t st, Args &&...args) {
