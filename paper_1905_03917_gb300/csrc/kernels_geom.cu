@@ -37,9 +37,18 @@ __global__ void k_ghost(Grid g, GhostSet s) {
   bool fx, fy;
   int si = ghost_image(i, g.nx, g.bc[0], g.bc[1], fx);
   int sj = ghost_image(j, g.ny, g.bc[2], g.bc[3], fy);
-  double *a = s.p[pl];
+  // the plane and its velocity flag by select (a runtime index into the
+  // parameter block would copy it to local memory)
+  double *a = s.p[0];
+  int vel = s.vel[0];
+#pragma unroll
+  for (int q = 1; q < 8; q++)
+    if (pl == q) {
+      a = s.p[q];
+      vel = s.vel[q];
+    }
   double v = a[gidx(g, si, sj)];
-  bool neg = (s.vel[pl] == 1 && fx) || (s.vel[pl] == 2 && fy);
+  bool neg = (vel == 1 && fx) || (vel == 2 && fy);
   a[gidx(g, i, j)] = neg ? -v : v;
 }
 

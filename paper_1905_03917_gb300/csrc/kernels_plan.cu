@@ -733,6 +733,121 @@ struct MixQ {
   double *q[2][4];
 };
 
+// One source's plan for a state-carrying fluid, written straight to its
+// slot: the decisions and arithmetic of mix_source_plan, with the loads
+// taken in two batches (the 3 x 3 volume fractions, the level set's face
+// neighbours and the cell's state together, then the targets' states) and
+// every array indexed at compile time so that it stays in registers.  Only
+// what k_mix_apply reads is stored: the target count, the targets and the
+// amounts.  Every index lies in the padded planes; inside() decides what
+// is used.
+__device__ void mix_setup_one(const Grid &g, int k, int i, int j, const double *alpha,
+                              const double *phi, double *const q[4], MixPlan *out) {
+  const int c = gidx(g, i, j);
+  double a9[9];
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    const int di = e % 3 - 1, dj = e / 3 - 1;
+    a9[e] = (g.dim == 2 || dj == 0) ? vol_k(alpha, k, gidx(g, i + di, j + dj)) : 0.0;
+  }
+  const double pe = phi[gidx(g, i + 1, j)], pw = phi[gidx(g, i - 1, j)];
+  const double pn = g.dim == 2 ? phi[gidx(g, i, j + 1)] : 0.0;
+  const double ps = g.dim == 2 ? phi[gidx(g, i, j - 1)] : 0.0;
+  double qs[4];
+#pragma unroll
+  for (int m = 0; m < 4; m++) qs[m] = q[m][c];
+  const double as = a9[4];
+  if (as >= g.mix_alpha || (as == 0.0 && qs[0] == 0.0 && qs[1] == 0.0 && qs[2] == 0.0 &&
+                            qs[3] == 0.0)) {
+    out->nt = 0;
+    return;
+  }
+  // unit_normal's arithmetic on the loaded values, turned to point out of
+  // fluid k
+  double nxv = 0.0, nyv = 0.0;
+  {
+    const double gx = (pe - pw) / (2.0 * g.dx);
+    const double gy = g.dim == 2 ? (pn - ps) / (2.0 * g.dy) : 0.0;
+    const double m = sqrt(gx * gx + gy * gy);
+    if (m > 0.0) {
+      nxv = gx / m;
+      nyv = gy / m;
+    }
+  }
+  if (k == 0) {
+    nxv = -nxv;
+    nyv = -nyv;
+  }
+  const int sx = nxv >= 0.0 ? 1 : -1, sy = nyv >= 0.0 ? 1 : -1;
+  // the normal-direction neighbours: across x, across y, the diagonal
+  const int ti[3] = {i + sx, i, i + sx}, tj[3] = {j, j + sy, j + sy};
+  const double at3[3] = {sx > 0 ? a9[5] : a9[3], sy > 0 ? a9[7] : a9[1],
+                         sy > 0 ? (sx > 0 ? a9[8] : a9[6]) : (sx > 0 ? a9[2] : a9[0])};
+  const double wt[3] = {nxv * nxv, nyv * nyv, fabs(nxv * nyv)};
+  const int nt = g.dim == 2 ? 3 : 1;
+  bool keep[3];
+  double sum = 0.0;
+#pragma unroll
+  for (int t = 0; t < 3; t++) {
+    keep[t] = t < nt && inside(g, ti[t], tj[t]) && wt[t] > 0.0 && at3[t] >= g.mix_alpha;
+    if (keep[t]) sum += wt[t];
+  }
+  bool single = false;
+  int best = -1;
+  double ab = 0.0;
+  if (!(sum > 0.0)) {
+    // the largest of the eight neighbours (the first in raster order)
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+      const int di = e % 3 - 1, dj = e / 3 - 1;
+      if (e == 4 || (g.dim == 1 && dj != 0) || !inside(g, i + di, j + dj)) continue;
+      if (a9[e] > ab) {
+        ab = a9[e];
+        best = e;
+      }
+    }
+    if (best >= 0 && ab >= g.mix_alpha) {
+      single = true;
+    } else {
+      // the normal-direction neighbours larger than the source
+#pragma unroll
+      for (int t = 0; t < 3; t++) {
+        keep[t] = t < nt && inside(g, ti[t], tj[t]) && wt[t] > 0.0 && at3[t] > as;
+        if (keep[t]) sum += wt[t];
+      }
+      if (!(sum > 0.0)) {
+        out->nt = 0;
+        return;
+      }
+    }
+  }
+  const int bestc = single ? gidx(g, i + best % 3 - 1, j + best / 3 - 1) : 0;
+  bool use[3];
+  int tcs[3];
+  double bet[3], ats[3], qt[3][4];
+#pragma unroll
+  for (int t = 0; t < 3; t++) {
+    use[t] = single ? t == 0 : keep[t];
+    tcs[t] = single ? bestc : gidx(g, ti[t], tj[t]);
+    bet[t] = single ? 1.0 : wt[t] / sum;
+    ats[t] = single ? ab : at3[t];
+#pragma unroll
+    for (int m = 0; m < 4; m++) qt[t][m] = use[t] ? q[m][tcs[t]] : 0.0;
+  }
+  // M = beta (q_t as - q_s at) / (as beta + at), one division per target
+  int p = 0;
+#pragma unroll
+  for (int t = 0; t < 3; t++) {
+    if (!use[t]) continue;
+    const double bd = bet[t] / (as * bet[t] + ats[t]);
+    out->tc[p] = tcs[t];
+#pragma unroll
+    for (int m = 0; m < 4; m++) out->M[p][m] = (qt[t][m] * as - qs[m] * ats[t]) * bd;
+    p++;
+  }
+  out->nt = p;
+}
+
 // plan of every band cell as a source, with the amounts it exchanges with
 // its targets, M = beta (q_t as - q_s at) / (as beta + at) (as the product
 // of the difference and beta / (as beta + at)), computed from the states
@@ -744,24 +859,15 @@ __global__ void k_mix_setup(Grid g, int mask, MixQ Q, const double *__restrict__
   const int k = blockIdx.y;  // fluid
   if (!(mask & (1 << k))) return;
   int n = *nband;
+  // the fluid's planes chosen by select, not by a runtime index into the
+  // parameter block (which would copy it to local memory)
+  double *q[4];
+#pragma unroll
+  for (int m = 0; m < 4; m++) q[m] = k ? Q.q[1][m] : Q.q[0][m];
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];
     int i = (c % g.PX) - SIF_GH, j = (c / g.PX) - SIF_GH;
-    MixPlan s;
-    if (!mix_source_plan(g, k, i, j, alpha, phi, Q.q[k], s)) {
-      // not a source: the apply kernel reads only the target count
-      plan[(size_t)k * cap + idx].nt = 0;
-      continue;
-    }
-    double *const *q = Q.q[k];
-    for (int t = 0; t < s.nt; t++) {
-      int tc = s.tc[t];
-      // one division per target: beta / (as beta + at) times each
-      // component's difference
-      const double bd = s.beta[t] / (s.as * s.beta[t] + s.at[t]);
-      for (int m = 0; m < 4; m++) s.M[t][m] = (q[m][tc] * s.as - q[m][c] * s.at[t]) * bd;
-    }
-    plan[(size_t)k * cap + idx] = s;
+    mix_setup_one(g, k, i, j, alpha, phi, q, plan + (size_t)k * cap + idx);
   }
 }
 
@@ -776,7 +882,9 @@ __global__ void k_mix_apply(Grid g, int mask, MixQ Q, const int *__restrict__ ma
   int k = blockIdx.y;
   if (!(mask & (1 << k))) return;
   int n = *nband;
-  double *const *q = Q.q[k];
+  double *q[4];
+#pragma unroll
+  for (int m = 0; m < 4; m++) q[m] = k ? Q.q[1][m] : Q.q[0][m];
   const MixPlan *P = plan + (size_t)k * cap;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     int c = band[idx];

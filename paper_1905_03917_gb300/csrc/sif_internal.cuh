@@ -179,28 +179,33 @@ __device__ inline double cell_alpha(double c00, double c10, double c11, double c
     }
     return area;
   }
-  double X[8], Y[8];
-  int m = 0;
+  // the positive part's polygon, its vertices taken in order around the
+  // cell; the shoelace sum gathers each edge's term as its end vertex
+  // comes and closes with the edge back to the first (the same terms in
+  // the same order as over a stored vertex list, in registers)
+  double x0 = 0.0, y0 = 0.0, xl = 0.0, yl = 0.0, a2 = 0.0;
+  bool first = true;
+  auto vertex = [&](double x, double y) {
+    if (first) {
+      x0 = x;
+      y0 = y;
+      first = false;
+    } else {
+      a2 += xl * y - x * yl;
+    }
+    xl = x;
+    yl = y;
+  };
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     int n = (e + 1) & 3;
-    if (v[e] >= 0.0) {
-      X[m] = px[e];
-      Y[m] = py[e];
-      m++;
-    }
+    if (v[e] >= 0.0) vertex(px[e], py[e]);
     if ((v[e] >= 0.0) != (v[n] >= 0.0)) {
       double s = v[e] / (v[e] - v[n]);
-      X[m] = px[e] + s * (px[n] - px[e]);
-      Y[m] = py[e] + s * (py[n] - py[e]);
-      m++;
+      vertex(px[e] + s * (px[n] - px[e]), py[e] + s * (py[n] - py[e]));
     }
   }
-  double a2 = 0.0;
-  for (int k = 0; k < m; k++) {
-    int k1 = (k + 1) % m;
-    a2 += X[k] * Y[k1] - X[k1] * Y[k];
-  }
+  a2 += xl * y0 - x0 * yl;
   return 0.5 * a2;
 }
 
