@@ -1,4 +1,5 @@
-"""ctypes front end of the serial FP64 CPU oracle (``oracle/sif_oracle.c``).
+"""ctypes front end of the serial FP64 CPU oracle (``oracle/sif_oracle.c``
+and its three-dimensional form ``oracle/sif_oracle3d.c``).
 
 TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  Nothing here is
@@ -14,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sif_oracle.c")
+_SRC3 = os.path.join(_HERE, "sif_oracle3d.c")
 _LIB = os.path.join(_HERE, "_build", "liborc.so")
 
 BC = {"reflect": 0, "zerograd": 1, "periodic": 2}
@@ -22,14 +24,14 @@ ERR_NONPHYS, ERR_NOCONV, ERR_INVAL = 1, 2, 4
 
 def build(force: bool = False) -> str:
     """Compile the oracle as a shared library (gcc, no FMA contraction)."""
-    hdr = os.path.join(_HERE, "sif_oracle.h")
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(hdr))
+    deps = [_SRC, _SRC3] + [os.path.join(_HERE, h) for h in ("sif_oracle.h", "sif_oracle3d.h")]
+    newest = max(os.path.getmtime(d) for d in deps)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                           "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +62,22 @@ class _Info(ctypes.Structure):
                 ("n_raw", ctypes.c_double), ("n_used", ctypes.c_double),
                 ("role_fluid1", ctypes.c_int), ("substeps", ctypes.c_int),
                 ("err", ctypes.c_int), ("open_updates", ctypes.c_longlong)]
+
+
+class _Config3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("bc", ctypes.c_int * 6),
+                ("gamma", ctypes.c_double * 2), ("pinf", ctypes.c_double * 2),
+                ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double),
+                ("mix_alpha", ctypes.c_double), ("ratio_threshold", ctypes.c_double),
+                ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
+                ("band", ctypes.c_double),
+                ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
+                ("tait", ctypes.c_int * 2),
+                ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
+                ("tait_p0", ctypes.c_double * 2)]
 
 
 _lib_handle = None
@@ -111,6 +129,21 @@ def lib():
         L.orc_weno5_grad.restype = None
         L.orc_weno5_grad.argtypes = [dp, D, dp]
         L.orc_riemann_grad.argtypes = [dp, dp, D, D, dp, dp]
+        L.orc3_create.restype = P
+        L.orc3_create.argtypes = [ctypes.POINTER(_Config3)]
+        L.orc3_destroy.argtypes = [P]
+        L.orc3_init.argtypes = [P, dp, dp, dp]
+        L.orc3_step_single_dt.argtypes = [P, I, D, ctypes.POINTER(_Info)]
+        L.orc3_step_multi_dt.argtypes = [P, I, D, ctypes.POINTER(_Info)]
+        L.orc3_get_state.argtypes = [P, dp, dp, dp]
+        L.orc3_set_state.argtypes = [P, dp, dp, dp]
+        L.orc3_integrals.argtypes = [P, dp]
+        L.orc3_geometry.argtypes = [P, dp, dp, dp, dp, dp, dp, dp]
+        L.orc3_cell_alpha.restype = D
+        L.orc3_cell_alpha.argtypes = [dp, dp]
+        L.orc3_time.restype = D
+        L.orc3_time.argtypes = [P]
+        L.orc3_status.argtypes = [P]
         _lib_handle = L
     return _lib_handle
 
@@ -307,6 +340,112 @@ class Oracle:
         if rc:
             raise RuntimeError(f"oracle adjoint failed: {rc}")
         return lo.reshape(2, 4, self.ny, self.nx)
+
+
+def make_config3(cfg: dict) -> _Config3:
+    c = _Config3()
+    c.nx, c.ny, c.nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg["nz"])
+    c.x0, c.y0, c.z0 = (float(cfg.get(k, 0.0)) for k in ("x0", "y0", "z0"))
+    c.dx, c.dy, c.dz = float(cfg["dx"]), float(cfg["dy"]), float(cfg["dz"])
+    for i, b in enumerate(cfg["bc"]):
+        c.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    for k in range(2):
+        c.gamma[k] = float(cfg["gamma"][k])
+        c.pinf[k] = float(cfg["pinf"][k])
+    c.cfl = float(cfg.get("cfl", 0.6))
+    c.weno_eps = float(cfg.get("weno_eps", 1e-6))
+    c.mix_alpha = float(cfg.get("mix_alpha", 0.5))
+    c.ratio_threshold = float(cfg.get("ratio_threshold", 0.7))
+    c.ext_iters = int(cfg.get("ext_iters", 10))
+    c.reinit_iters = int(cfg.get("reinit_iters", 2))
+    c.band = float(cfg.get("band", 6.0))
+    c.flux_correction = int(cfg.get("flux_correction", 1))
+    c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
+    for k, t in enumerate(cfg.get("tait", (None, None))):
+        if t is not None:
+            c.tait[k] = 1
+            c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
+    return c
+
+
+class Oracle3:
+    """One two-fluid problem in three dimensions advanced by the serial
+    oracle; arrays are (nz, ny, nx), x fastest, and the primitive fields
+    (rho, u, v, w, p)."""
+
+    def __init__(self, cfg: dict):
+        self.cfg = dict(cfg)
+        self._c = make_config3(cfg)
+        self._h = lib().orc3_create(ctypes.byref(self._c))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration")
+        self.shape = (self._c.nz, self._c.ny, self._c.nx)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc3_destroy(h)
+            self._h = None
+
+    def init(self, phi, prim_N, prim_P):
+        phi, pN, pP = _f64(phi), _f64(prim_N), _f64(prim_P)
+        lib().orc3_init(self._h, _ptr(phi), _ptr(pN), _ptr(pP))
+        return self
+
+    def _info(self, info):
+        return {"t": info.t, "dt1": info.dt1, "dt2": info.dt2, "n_raw": info.n_raw,
+                "n_used": info.n_used, "role_fluid1": info.role_fluid1,
+                "substeps": info.substeps, "err": info.err,
+                "open_updates": info.open_updates,
+                "fluid_cell_updates": info.open_updates / 2}
+
+    def step_single_dt(self, nsteps=1, t_end=0.0):
+        info = _Info()
+        lib().orc3_step_single_dt(self._h, int(nsteps), float(t_end), ctypes.byref(info))
+        return self._info(info)
+
+    def step_multi_dt(self, ncycles=1, t_end=0.0):
+        info = _Info()
+        lib().orc3_step_multi_dt(self._h, int(ncycles), float(t_end), ctypes.byref(info))
+        return self._info(info)
+
+    def state(self):
+        n = int(np.prod(self.shape))
+        qN, qP, phi = np.empty(5 * n), np.empty(5 * n), np.empty(n)
+        lib().orc3_get_state(self._h, _ptr(qN), _ptr(qP), _ptr(phi))
+        return qN.reshape((5,) + self.shape), qP.reshape((5,) + self.shape), phi.reshape(self.shape)
+
+    def set_state(self, qN, qP, phi):
+        qN, qP, phi = _f64(qN), _f64(qP), _f64(phi)
+        lib().orc3_set_state(self._h, _ptr(qN), _ptr(qP), _ptr(phi))
+
+    def integrals(self):
+        out = np.empty(10)
+        lib().orc3_integrals(self._h, _ptr(out))
+        return out.reshape(2, 5)
+
+    def geometry(self):
+        n = int(np.prod(self.shape))
+        arrs = [np.empty(n) for _ in range(7)]
+        lib().orc3_geometry(self._h, *(_ptr(a) for a in arrs))
+        names = ("alpha", "ax", "ay", "az", "sx", "sy", "sz")
+        return {k: a.reshape(self.shape) for k, a in zip(names, arrs)}
+
+    @property
+    def t(self):
+        return lib().orc3_time(self._h)
+
+    @property
+    def status(self):
+        return lib().orc3_status(self._h)
+
+
+def cell_alpha3(corners):
+    """Volume fraction and unit-face interface vector of the unit cube from
+    its corner values c[i + 2 j + 4 k]."""
+    c, s = _f64(corners), np.empty(3)
+    a = lib().orc3_cell_alpha(_ptr(c), _ptr(s))
+    return a, s
 
 
 def weno5(v, eps=1e-6):

@@ -445,3 +445,106 @@ def gas_water_tube(n=200):
     pN = _uniform((1, n), 0.01, 0.0, 0.0, 1000.0)
     pP = _uniform((1, n), 1.0, 0.0, 0.0, 1.0)
     return {"name": f"gas_water_tube_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}
+
+
+# -- three-dimensional cases (Tables 1, 3, 4, "Uniform grid - 3D") -----------
+# Arrays are (nz, ny, nx), x fastest; prim_* holds (rho, u, v, w, p).
+
+def config3(nx, ny, nz, d, matN, matP, bc, **kw):
+    """Configuration of a 3D case on cubic cells of edge d; bc lists the six
+    sides -x, +x, -y, +y, -z, +z."""
+    cfg = {"dim": 3, "nx": nx, "ny": ny, "nz": nz, "x0": 0.0, "y0": 0.0, "z0": 0.0,
+           "dx": d, "dy": d, "dz": d, "bc": list(bc),
+           "gamma": [matN["gamma"], matP["gamma"]], "pinf": [matN["pinf"], matP["pinf"]],
+           "cfl": 0.6, "weno_eps": 1e-6, "mix_alpha": 0.5, "ratio_threshold": 0.7,
+           "ext_iters": 10, "reinit_iters": 2, "band": 6.0, "flux_correction": 1,
+           "force_ratio_one": 0}
+    if "tait" in matN or "tait" in matP:
+        cfg["tait"] = [matN.get("tait"), matP.get("tait")]
+    cfg.update(kw)
+    return cfg
+
+
+def _centres3(cfg):
+    x = cfg["x0"] + (np.arange(cfg["nx"]) + 0.5) * cfg["dx"]
+    y = cfg["y0"] + (np.arange(cfg["ny"]) + 0.5) * cfg["dy"]
+    z = cfg["z0"] + (np.arange(cfg["nz"]) + 0.5) * cfg["dz"]
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def _uniform3(shape, rho, u, v, w, p):
+    out = np.empty((5,) + shape)
+    out[0], out[1], out[2], out[3], out[4] = rho, u, v, w, p
+    return out
+
+
+def droplet_translation_3d(n=128):
+    """Sec. 4.2's 3D case (Table 1, 128^3): the water droplet of
+    droplet_translation() as a sphere, phi = |x - (0.5, 0.5, 0.5)| - 0.1, in
+    the periodic unit cube, both fluids moving with u = sqrt(10)/100, v = w =
+    0 at p = 1."""
+    d = 1.0 / n
+    water = tait(3310.0, 1000.0, 1.0, 7.15)
+    cfg = config3(n, n, n, d, water, AIR, ["periodic"] * 6)
+    X, Y, Z = _centres3(cfg)
+    phi = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) - 0.1
+    u = math.sqrt(10.0) / 100.0
+    pN = _uniform3(X.shape, 1000.0, u, 0.0, 0.0, 1.0)
+    pP = _uniform3(X.shape, 1.2, u, 0.0, 0.0, 1.0)
+    return {"name": f"droplet_translation_3d_{n}", "cfg": cfg, "phi": phi, "prim_N": pN,
+            "prim_P": pP}
+
+
+def shock_bubble_3d(n=32, seed=None, perturb=0.0):
+    """A 3D air-helium shock-bubble on a 2n x n x n box of edge 1/n: a
+    helium sphere of radius 0.25 at (0.75, 0.5, 0.5) (fluid N) hit by a Mach
+    1.22 shock in air moving in +x from x = 0.3; zero-gradient x ends,
+    reflective y and z walls; seeded smooth perturbation of the sphere's
+    radius."""
+    d = 1.0 / n
+    cfg = config3(2 * n, n, n, d, HELIUM, AIR,
+                  ["zerograd", "zerograd", "reflect", "reflect", "reflect", "reflect"])
+    X, Y, Z = _centres3(cfg)
+    r = 0.25
+    if seed is not None and perturb:
+        rng = np.random.default_rng(seed)
+        th = np.arctan2(Z - 0.5, Y - 0.5)
+        r = r * (1.0 + perturb * np.cos(rng.integers(2, 5) * th + rng.uniform(0, 2 * np.pi)))
+    phi = np.sqrt((X - 0.75) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) - r
+    rho2, u2, p2, _ = normal_shock(1.4, 1.0, 1.0, 1.22)
+    pre = X >= 0.3
+    pP = _uniform3(X.shape, 1.0, 0.0, 0.0, 0.0, 1.0)
+    pP[0][~pre], pP[1][~pre], pP[4][~pre] = rho2, u2, p2
+    pN = _uniform3(X.shape, 0.138, 0.0, 0.0, 0.0, 1.0)
+    return {"name": f"shock_bubble_3d_{2 * n}x{n}x{n}", "cfg": cfg, "phi": phi,
+            "prim_N": pN, "prim_P": pP}
+
+
+def extrude(case, nz):
+    """A 2D case repeated along z over nz cells of the x spacing, periodic
+    in z, with w = 0: the 3D method must reproduce the 2D one on it."""
+    c2 = case["cfg"]
+    bc = list(c2["bc"])
+    kw = {k: c2[k] for k in ("cfl", "weno_eps", "mix_alpha", "ratio_threshold", "ext_iters",
+                             "reinit_iters", "band", "flux_correction", "force_ratio_one")
+          if k in c2}
+    mats = [{"gamma": c2["gamma"][k], "pinf": c2["pinf"][k]} for k in range(2)]
+    if "tait" in c2:
+        for k in range(2):
+            if c2["tait"][k] is not None:
+                mats[k]["tait"] = tuple(c2["tait"][k])
+    cfg = config3(c2["nx"], c2["ny"], nz, c2["dx"], mats[0], mats[1],
+                  bc + ["periodic", "periodic"], **kw)
+    cfg["dy"] = c2["dy"]
+
+    def rep(a):
+        return np.repeat(a[..., None, :, :], nz, axis=-3)
+
+    def prim(p2):
+        out = np.zeros((5, nz) + p2.shape[1:])
+        out[0], out[1], out[2], out[4] = rep(p2[0]), rep(p2[1]), rep(p2[2]), rep(p2[3])
+        return out
+
+    return {"name": case["name"] + f"_z{nz}", "cfg": cfg, "phi": rep(case["phi"]),
+            "prim_N": prim(case["prim_N"]), "prim_P": prim(case["prim_P"])}
