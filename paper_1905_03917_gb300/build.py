@@ -27,6 +27,9 @@ SOURCES = {
     "probe.cu": ["--fmad=true"],
     "noalloc.cu": ["--fmad=false"],
     "adjoint.cu": ["--fmad=true"],
+    "kernels3d.cu": ["--fmad=false"],
+    "fv3d.cu": ["--fmad=true"],
+    "api3d.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -40,7 +43,8 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in SOURCES]
-    files += [os.path.join(CSRC, "sif_internal.cuh"), os.path.join(ROOT, "include", "sif.h"),
+    files += [os.path.join(CSRC, "sif_internal.cuh"), os.path.join(CSRC, "sif3d_internal.cuh"),
+              os.path.join(ROOT, "include", "sif.h"), os.path.join(ROOT, "include", "sif3d.h"),
               os.path.abspath(__file__)]
     return files
 

@@ -28,7 +28,11 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif_batch_create", "sif_batch_instance", "sif_batch_step_multi_dt",
            "sif_batch_last_error", "sif_batch_destroy", "sif_batch_one_graph",
            "sif_tape_reset", "sif_tape_length", "sif_replay_step", "sif_adjoint_step",
-           "sif_adjoint_init", "sif_probe_reciprocal", "sif_set_limits"]
+           "sif_adjoint_init", "sif_probe_reciprocal", "sif_set_limits",
+           "sif3_create", "sif3_init_fluids", "sif3_step_single_dt", "sif3_step_multi_dt",
+           "sif3_get_state", "sif3_set_state", "sif3_integrals", "sif3_geometry",
+           "sif3_get_time", "sif3_profile_enable", "sif3_profile_read", "sif3_last_error",
+           "sif3_destroy"]
 
 
 class SifError(RuntimeError):
@@ -57,6 +61,23 @@ class Config(ctypes.Structure):
                 ("mu", ctypes.c_double * 2), ("tait", ctypes.c_int * 2),
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
                 ("tait_p0", ctypes.c_double * 2), ("flux", ctypes.c_int)]
+
+
+class Config3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("bc", ctypes.c_int * 6),
+                ("gamma", ctypes.c_double * 2), ("pinf", ctypes.c_double * 2),
+                ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double),
+                ("mix_alpha", ctypes.c_double), ("ratio_threshold", ctypes.c_double),
+                ("ext_iters", ctypes.c_int), ("reinit_iters", ctypes.c_int),
+                ("band", ctypes.c_double),
+                ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
+                ("tait", ctypes.c_int * 2),
+                ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
+                ("tait_p0", ctypes.c_double * 2),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -123,6 +144,24 @@ def load(path: str | None = None):
     L.sif_replay_step.argtypes = [P, I, P, P, I]
     L.sif_adjoint_step.argtypes = [P, I, P, P, I]
     L.sif_adjoint_init.argtypes = [P, P, P, P, P, P, I]
+    L.sif3_create.argtypes = [ctypes.POINTER(Config3), ctypes.POINTER(P)]
+    L.sif3_init_fluids.argtypes = [P, P, P, P, I]
+    L.sif3_step_single_dt.argtypes = [P, I, D, ctypes.POINTER(CycleInfo)]
+    L.sif3_step_multi_dt.argtypes = [P, I, D, ctypes.POINTER(CycleInfo)]
+    L.sif3_get_state.argtypes = [P, P, P, P, I]
+    L.sif3_set_state.argtypes = [P, P, P, P, I]
+    L.sif3_integrals.argtypes = [P, P]
+    L.sif3_geometry.argtypes = [P, P, P, P, P, P, P, P, I]
+    L.sif3_get_time.argtypes = [P, ctypes.POINTER(D)]
+    L.sif3_profile_enable.argtypes = [P, I]
+    L.sif3_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
+    L.sif3_last_error.argtypes = [P]
+    L.sif3_last_error.restype = ctypes.c_char_p
+    L.sif3_destroy.argtypes = [P]
+    for f in (L.sif3_create, L.sif3_init_fluids, L.sif3_step_single_dt, L.sif3_step_multi_dt,
+              L.sif3_get_state, L.sif3_set_state, L.sif3_integrals, L.sif3_geometry,
+              L.sif3_get_time, L.sif3_profile_enable, L.sif3_profile_read, L.sif3_destroy):
+        f.restype = I
     for f in (L.sif_tape_reset, L.sif_tape_length, L.sif_replay_step, L.sif_adjoint_step,
               L.sif_adjoint_init):
         f.restype = I
@@ -471,3 +510,140 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def make_config3(cfg: dict, stream=None, device=0) -> Config3:
+    c = Config3()
+    c.nx, c.ny, c.nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg["nz"])
+    c.x0, c.y0, c.z0 = (float(cfg.get(k, 0.0)) for k in ("x0", "y0", "z0"))
+    c.dx, c.dy, c.dz = float(cfg["dx"]), float(cfg["dy"]), float(cfg["dz"])
+    if len(cfg["bc"]) != 6:
+        raise ValueError("a 3D configuration lists six boundary kinds")
+    for i, b in enumerate(cfg["bc"]):
+        c.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    for k in range(2):
+        c.gamma[k], c.pinf[k] = float(cfg["gamma"][k]), float(cfg["pinf"][k])
+    c.cfl = float(cfg.get("cfl", 0.6))
+    c.weno_eps = float(cfg.get("weno_eps", 1e-6))
+    c.mix_alpha = float(cfg.get("mix_alpha", 0.5))
+    c.ratio_threshold = float(cfg.get("ratio_threshold", 0.7))
+    c.ext_iters = int(cfg.get("ext_iters", 10))
+    c.reinit_iters = int(cfg.get("reinit_iters", 2))
+    c.band = float(cfg.get("band", 6.0))
+    c.flux_correction = int(cfg.get("flux_correction", 1))
+    c.force_ratio_one = int(cfg.get("force_ratio_one", 0))
+    for k, t in enumerate(cfg.get("tait", (None, None))):
+        if t is not None:
+            c.tait[k] = 1
+            c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
+    c.cuda_stream = stream
+    c.device = int(device)
+    return c
+
+
+class Solver3:
+    """One two-fluid problem in three dimensions held on the GPU by libsif
+    (include/sif3d.h).  Arrays are (nz, ny, nx), x fastest; the primitive
+    fields are (rho, u, v, w, p) and the state (alpha U) has five
+    components (mass, x-, y-, z-momentum, energy) per fluid."""
+
+    def __init__(self, cfg: dict, stream=None, device=0):
+        self.cfg = dict(cfg)
+        self.shape = (int(cfg["nz"]), int(cfg["ny"]), int(cfg["nx"]))
+        L = load()
+        h = ctypes.c_void_p()
+        c = make_config3(cfg, stream, device)
+        rc = L.sif3_create(ctypes.byref(c), ctypes.byref(h))
+        if rc != OK:
+            raise SifError(rc, "sif3_create rejected the configuration or failed to allocate")
+        self._h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SifError(rc, load().sif3_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sif3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fluids(self, phi, prim_N, prim_P):
+        (p0, k0), (p1, k1), (p2, k2) = _ptr(phi), _ptr(prim_N), _ptr(prim_P)
+        if not (k0 == k1 == k2):
+            raise ValueError("all inputs must be in the same memory")
+        n = int(np.prod(self.shape))
+        for a, m in ((phi, 1), (prim_N, 5), (prim_P, 5)):
+            size = a.size if isinstance(a, np.ndarray) else a.numel()
+            if size != m * n:
+                raise ValueError(f"expected {m} planes of {self.shape}")
+        self._check(load().sif3_init_fluids(self._h, p0, p1, p2, k0))
+        return self
+
+    def _info(self, info):
+        return {"t": info.t, "dt1": info.dt1, "dt2": info.dt2, "n_raw": info.n_raw,
+                "n_used": info.n_used, "role_fluid1": info.role_fluid1,
+                "substeps": info.substeps, "cell_updates": info.cell_updates,
+                "open_updates": info.open_updates,
+                "fluid_cell_updates": info.open_updates / 2}
+
+    def step_single_dt(self, nsteps=1, t_end=0.0):
+        info = CycleInfo()
+        self._check(load().sif3_step_single_dt(self._h, int(nsteps), float(t_end),
+                                               ctypes.byref(info)))
+        return self._info(info)
+
+    def step_multi_dt(self, ncycles=1, t_end=0.0):
+        info = CycleInfo()
+        self._check(load().sif3_step_multi_dt(self._h, int(ncycles), float(t_end),
+                                              ctypes.byref(info)))
+        return self._info(info)
+
+    def state(self):
+        n = int(np.prod(self.shape))
+        qN, qP, phi = np.empty(5 * n), np.empty(5 * n), np.empty(n)
+        self._check(load().sif3_get_state(self._h, qN.ctypes.data, qP.ctypes.data,
+                                          phi.ctypes.data, HOST))
+        sh = (5,) + self.shape
+        return qN.reshape(sh), qP.reshape(sh), phi.reshape(self.shape)
+
+    def state_into(self, qN, qP, phi):
+        (a, ka), (b, kb), (c, kc) = _ptr(qN), _ptr(qP), _ptr(phi)
+        self._check(load().sif3_get_state(self._h, a, b, c, ka))
+
+    def set_state(self, qN, qP, phi):
+        (a, ka), (b, kb), (c, kc) = _ptr(qN), _ptr(qP), _ptr(phi)
+        self._check(load().sif3_set_state(self._h, a, b, c, ka))
+
+    def integrals(self):
+        out = np.empty(10)
+        self._check(load().sif3_integrals(self._h, out.ctypes.data))
+        return out.reshape(2, 5)
+
+    def geometry(self):
+        n = int(np.prod(self.shape))
+        arrs = [np.empty(n) for _ in range(7)]
+        self._check(load().sif3_geometry(self._h, *(a.ctypes.data for a in arrs), HOST))
+        names = ("alpha", "ax", "ay", "az", "sx", "sy", "sz")
+        return {k: a.reshape(self.shape) for k, a in zip(names, arrs)}
+
+    @property
+    def t(self):
+        v = ctypes.c_double()
+        self._check(load().sif3_get_time(self._h, ctypes.byref(v)))
+        return v.value
+
+    def profile_enable(self, on=True):
+        self._check(load().sif3_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self):
+        p = Profile()
+        self._check(load().sif3_profile_read(self._h, ctypes.byref(p)))
+        return {"kernel_launches": p.kernel_launches, "fv_launches": p.fv_launches,
+                "fv_ms": p.fv_ms, "fv_cell_updates": p.fv_cell_updates,
+                "fv_open_updates": p.fv_open_updates}

@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads and exports every entry point that
-include/sif.h declares (no GPU needed: no compute call is made)."""
+include/*.h declares (no GPU needed: no compute call is made)."""
 import ctypes
 import os
 import re
@@ -12,10 +12,16 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_entry_points():
-    with open(os.path.join(ROOT, "include", "sif.h")) as f:
-        txt = f.read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(sif_[a-z_0-9]+)\s*\(", txt)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if not h.endswith(".h"):
+            continue
+        with open(os.path.join(inc, h)) as f:
+            txt = f.read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(sif3?_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_entry_point():
@@ -28,11 +34,11 @@ def test_library_exports_every_declared_entry_point():
     assert set(names) == set(sif.EXPORTS)
 
 
-def test_config_struct_matches_header_field_order():
-    with open(os.path.join(ROOT, "include", "sif.h")) as f:
+def _fields(header, start, end):
+    with open(os.path.join(ROOT, "include", header)) as f:
         txt = f.read()
-    body = txt[txt.index("typedef struct {\n  int dim;"):]
-    body = body[:body.index("} sif_config;")]
+    body = txt[txt.index(start):]
+    body = body[:body.index(end)]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = []
     for decl in body.split(";"):
@@ -44,7 +50,27 @@ def test_config_struct_matches_header_field_order():
         for part in decl.split(","):
             name = re.sub(r"\[.*\]", "", part.strip().split()[-1]).lstrip("*")
             fields.append(name)
+    return fields
+
+
+def test_config_struct_matches_header_field_order():
+    fields = _fields("sif.h", "typedef struct {\n  int dim;", "} sif_config;")
     assert fields == [f[0] for f in sif.Config._fields_]
+
+
+def test_config3_struct_matches_header_field_order():
+    fields = _fields("sif3d.h", "typedef struct {\n  int nx, ny, nz;", "} sif3_config;")
+    assert fields == [f[0] for f in sif.Config3._fields_]
+
+
+def test_invalid_3d_configuration_is_rejected_without_gpu_work():
+    lib = sif.load()
+    c = sif.Config3()
+    c.nx = c.ny = c.nz = 2  # below the WENO5 stencil's reach
+    h = ctypes.c_void_p()
+    assert lib.sif3_create(ctypes.byref(c), ctypes.byref(h)) == sif.EINVAL
+    assert not h.value
+    assert lib.sif3_last_error(None) == b"null context"
 
 
 def test_invalid_configuration_is_rejected_without_gpu_work():
