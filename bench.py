@@ -466,6 +466,70 @@ def paper_table1(device, sizes=(64, 128, 256, 512, 1024)):
             "timing": "host wall clock around one synchronising call of the counted steps"}
 
 
+# Table 1's 3D row (Sec. 4.2: the droplet as a sphere on a uniform 128^3
+# grid), on the same i7-4790: r_s = 1001450.6 s / 349911.1 s
+PAPER_TABLE1_3D_SPEEDUP = {128: 2.862}
+TABLE1_3D_T_RUN = {64: 0.05, 128: 0.02}
+# algorithmic FP64 flops of one (cell, fluid) stage update of the 3D
+# finite-volume kernel: split fluxes 3 x 54, one face per direction
+# 3 x (5 x 2 x 66 + 10), divergence, exchange and RK stage 5 x 14
+FLOPS_PER_UPDATE_3D = 2240
+
+
+def paper_table1_3d(device, sizes=(64, 128)):
+    """The 3D row of Table 1 on this GPU: the translating water sphere
+    (Tait water in air, periodic unit cube) advanced by both methods over
+    the same span of time, r_s = single-step time / accelerated time; each
+    timed run also reports the 3D finite-volume kernel's share of it and
+    its FP64 throughput (CUDA events around every launch)."""
+    import torch
+    from paper_1905_03917_gb300 import inputs, sif
+    peak = NOMINAL_FP64_TFLOPS
+    rows = []
+    for n in sizes:
+        case = inputs.droplet_translation_3d(n)
+        arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
+        t_run = TABLE1_3D_T_RUN.get(n, 0.02)
+        rec = {"grid": f"{n}x{n}x{n}", "t": t_run,
+               "paper_speedup": PAPER_TABLE1_3D_SPEEDUP.get(n)}
+        for mode in ("single", "multi"):
+            s = sif.Solver3(case["cfg"], device=device).init_fluids(*arrs)
+            step = s.step_multi_dt if mode == "multi" else s.step_single_dt
+            count, subs = 0, []
+            while s.t < t_run:
+                subs.append(step(1, t_end=t_run)["substeps"])
+                count += 1
+            s.init_fluids(*arrs)
+            s.profile_enable(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = step(count, t_end=t_run)
+            torch.cuda.synchronize()
+            ms = 1e3 * (time.perf_counter() - t0)
+            prof = s.profile_read()
+            s.profile_enable(False)
+            rec[f"{mode}_ms"] = ms
+            rec[f"{mode}_steps"] = count
+            rec[f"{mode}_fluid_cell_updates_per_s"] = info["fluid_cell_updates"] / (ms / 1e3)
+            achieved = prof["fv_open_updates"] * FLOPS_PER_UPDATE_3D / (prof["fv_ms"] / 1e3) / 1e12
+            rec[f"{mode}_fv"] = {"share_of_run": prof["fv_ms"] / ms,
+                                 "launches": prof["fv_launches"],
+                                 "avg_launch_ms": prof["fv_ms"] / max(prof["fv_launches"], 1),
+                                 "achieved_tflops": achieved, "peak_tflops": peak,
+                                 "frac": achieved / peak,
+                                 "flops_per_update": FLOPS_PER_UPDATE_3D}
+            rec[f"{mode}_kernel_launches"] = prof["kernel_launches"]
+            if mode == "multi":
+                rec["mean_substeps"] = float(np.mean(subs))
+            s.close()
+        rec["speedup"] = rec["single_ms"] / rec["multi_ms"]
+        rows.append(rec)
+    return {"workload": "droplet translation in 3D (Sec. 4.2, Table 1 3D row), Tait water "
+                        "sphere in air, periodic unit cube",
+            "runs": rows,
+            "timing": "host wall clock around one synchronising call of the counted steps"}
+
+
 def tube_exact_error(T):
     """L1 error of the 1D water/air tube's mixture density against the
     cell-averaged exact solution (16 samples a cell) at time T."""
@@ -802,6 +866,7 @@ def run_ours(args):
                                                args.warmup, local, weno=args.weno)),
                         ("batched", batched),
                         ("paper_table1", lambda: paper_table1(local)),
+                        ("paper_table1_3d", lambda: paper_table1_3d(local)),
                         ("adjoint", lambda: adjoint_cost(local)),
                         ("adjoint_origin", lambda: adjoint_cost(local, centre=(0.0, 0.0)))):
             try:
@@ -878,6 +943,8 @@ def main():
     ap.add_argument("--flux", default="lf", choices=["lf", "hllc"],
                     help="face flux: WENO5 on Lax-Friedrichs split fluxes (the paper's) or "
                          "HLLC between WENO5-reconstructed primitive states (main line only)")
+    ap.add_argument("--size3d", type=int, default=0,
+                    help="grid edge of the 3D droplet alone (--workload paper_table1_3d)")
     ap.add_argument("--adjoint-size", type=int, default=512,
                     help="grid of the --workload adjoint measurement (n x n)")
     ap.add_argument("--no-extras", action="store_true",
@@ -892,6 +959,11 @@ def main():
     elif args.workload == "paper_table1":
         # the droplet-translation speedups beside the paper's Table 1 alone
         print(json.dumps({"impl": "ours", "paper_table1": paper_table1(0)}), flush=True)
+    elif args.workload == "paper_table1_3d":
+        # the 3D droplet (Table 1's 3D row) alone; --size picks one grid
+        sizes = (args.size3d,) if args.size3d else (64, 128)
+        print(json.dumps({"impl": "ours", "paper_table1_3d": paper_table1_3d(0, sizes)}),
+              flush=True)
     elif args.workload == "adjoint":
         # the adjoint measurement alone (gas-water bubble at x = 0.7, n x n,
         # --steps single-dt steps, a checkpoint every --steps / 2), e.g. for

@@ -44,6 +44,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, f) for f in SOURCES]
     files += [os.path.join(CSRC, "sif_internal.cuh"), os.path.join(CSRC, "sif3d_internal.cuh"),
+              os.path.join(CSRC, "weno_frac.cuh"),
               os.path.join(ROOT, "include", "sif.h"), os.path.join(ROOT, "include", "sif3d.h"),
               os.path.abspath(__file__)]
     return files

@@ -25,12 +25,14 @@ struct sif3_ctx {
   double *q[2][S3_NC], *w[2][S3_NC], *q0[2][S3_NC];
   double *prev[S3_NC], *fut[S3_NC], *qi[S3_NC];
   double *xc[4], *xn[4], *xp[4], *ul[3];
-  double *phi, *phi0, *lphi, *p0, *old, *alpha, *ax, *ay, *az, *sx, *sy, *sz;
+  double *phi, *phi0, *lphi, *p0, *old, *alpha, *ax, *ay, *az, *sx, *sy, *sz, *corner;
   double *dense;     // nx*ny*nz*5 staging (caller layout)
   double *partial;   // integrals: 10 x nz
   double *extA, *extB;
-  unsigned char *band, *rext, *nostate, *touched;
-  int *extmap, *srcmap, *counts;
+  unsigned char *bandmask, *rext, *nostate, *touched;
+  int *extmap, *srcmap, *counts, *blist;
+  Region band{nullptr, 0};  // the band list of the last interaction step
+  const Region whole{nullptr, 0};
   Ext3 *ext;
   Mix3 *mix;
   int ext_cap = 0, mix_cap = 0, nbricks = 0;
@@ -103,20 +105,21 @@ static void carve(sif3_ctx *c, Carver &cv) {
     c->xp[m] = cv.take<double>(NP);
   }
   for (int d = 0; d < 3; d++) c->ul[d] = cv.take<double>(NP);
-  double **one[] = {&c->phi, &c->phi0, &c->lphi, &c->p0, &c->old, &c->alpha,
-                    &c->ax,  &c->ay,   &c->az,   &c->sx, &c->sy,  &c->sz};
+  double **one[] = {&c->phi, &c->phi0, &c->lphi, &c->p0, &c->old, &c->alpha, &c->ax,
+                    &c->ay,  &c->az,   &c->sx,   &c->sy, &c->sz,  &c->corner};
   for (double **p : one) *p = cv.take<double>(NP);
   c->dense = cv.take<double>(n * S3_NC);
   c->partial = cv.take<double>((size_t)2 * S3_NC * c->g.nz);
   c->extA = cv.take<double>((size_t)3 * S3_NC * c->ext_cap);
   c->extB = cv.take<double>((size_t)3 * S3_NC * c->ext_cap);
-  c->band = cv.take<unsigned char>(NP);
+  c->bandmask = cv.take<unsigned char>(NP);
   c->rext = cv.take<unsigned char>(NP);
   c->nostate = cv.take<unsigned char>(2 * NP);
   c->touched = cv.take<unsigned char>((size_t)2 * c->nbricks);
   c->extmap = cv.take<int>(3 * NP);
   c->srcmap = cv.take<int>(NP);
   c->counts = cv.take<int>(8);
+  c->blist = cv.take<int>((size_t)c->nbricks);
   c->ext = cv.take<Ext3>((size_t)3 * c->ext_cap);
   c->mix = cv.take<Mix3>((size_t)c->mix_cap);
   c->sc = cv.take<Scal3>(1);
@@ -196,6 +199,9 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
   Carver real{c->pool};
   carve(c, real);
   cudaMemsetAsync(c->pool, 0, c->pool_bytes, c->st);
+  // the extension and mixing maps hold -1 between plans
+  cudaMemsetAsync(c->extmap, 0xff, sizeof(int) * 3 * (size_t)c->g.NP, c->st);
+  cudaMemsetAsync(c->srcmap, 0xff, sizeof(int) * (size_t)c->g.NP, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) {
     cudaFree(c->pool);
     if (c->own_stream) cudaStreamDestroy(c->st);
@@ -239,9 +245,22 @@ static void ghost_w(sif3_ctx *c, int k) {
   k3_launch_ghost(c->g, s, c->st);
 }
 
-static void geometry(sif3_ctx *c, double *phi) {
+// geometry of phi over the band list (the level set changed only there
+// since the list was built), or over the whole grid
+static void geometry(sif3_ctx *c, double *phi, bool all = false) {
   ghost1(c, phi);
-  k3_launch_geometry(c->g, phi, c->alpha, c->ax, c->ay, c->az, c->sx, c->sy, c->sz, c->st);
+  k3_launch_geometry(c->g, all ? c->whole : c->band, phi, c->corner, c->alpha, c->ax, c->ay,
+                     c->az, c->sx, c->sy, c->sz, c->st);
+}
+
+// the band list from the current level set, its size read back
+static int rebuild_band(sif3_ctx *c) {
+  k3_launch_band_bricks(c->g, c->nbricks, c->phi, c->blist, c->sc, c->st);
+  int n = 0;
+  cudaMemcpyAsync(&n, &c->sc->nband, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  int rc = cuda_check(c, cudaStreamSynchronize(c->st), "band list");
+  c->band = Region{c->blist, n};
+  return rc;
 }
 
 static void copy_planes(sif3_ctx *c, double *const dst[], double *const src[], int n) {
@@ -249,9 +268,10 @@ static void copy_planes(sif3_ctx *c, double *const dst[], double *const src[], i
     cudaMemcpyAsync(dst[m], src[m], sizeof(double) * c->g.NP, cudaMemcpyDeviceToDevice, c->st);
 }
 
+// small cells lie near the interface: mixing works over the band list
 static void mix(sif3_ctx *c, int k, double *const q[S3_NC]) {
-  k3_launch_mix(c->g, k, q, c->alpha, c->phi, c->srcmap, c->mix, c->counts + 3, c->mix_cap,
-                &c->sc->err, c->st);
+  k3_launch_mix(c->g, c->band, k, q, c->alpha, c->phi, c->srcmap, c->mix, c->counts + 3,
+                c->mix_cap, &c->sc->err, c->st);
 }
 
 // reads the device maxima and error bits after an interaction step
@@ -263,6 +283,7 @@ static int read_scalars(sif3_ctx *c) {
     for (int d = 0; d < 3; d++) c->lf[k][d] = bits_d(c->hs.lf[k][d]);
     c->smax[k] = bits_d(c->hs.smax[k]);
   }
+  c->band = Region{c->blist, c->hs.nband};
   if (c->hs.err & S3_ERR_CAP)
     return fail(c, SIF_EINVAL, "a band list outgrew its capacity (interface too large for "
                                "the grid's band lists)");
@@ -275,25 +296,36 @@ static int read_scalars(sif3_ctx *c) {
 
 // the interaction step for stage states qs and the level set (Sec. 2.1,
 // 2.3): geometry, stencil states with extension, wave maxima, the
-// interface Riemann problems, the level-set velocity
-static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi) {
+// interface Riemann problems, the level-set velocity; then the band list
+// for the next stage.  band_only = f marks an evaluation inside the
+// accelerated cycle whose fluid-1 states (f) are read only near the
+// interface (its stencil states elsewhere, its time step and its
+// Lax-Friedrichs speeds are not used before they are evaluated again over
+// the whole grid); -1 evaluates both fluids everywhere
+static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_only = -1) {
   const Grid3 &g = c->g;
   geometry(c, phi);
   cudaMemsetAsync(c->sc, 0, offsetof(Scal3, err), c->st);  // maxima restart, errors stick
-  k3_launch_prim(g, qs, c->w, c->alpha, c->nostate, c->sc, c->st);
-  k3_ext_plan(g, 0, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
+  for (int k = 0; k < 2; k++)
+    k3_launch_prim(g, k == band_only ? c->band : c->whole, k, qs[k], c->w[k], c->alpha,
+                   c->nostate, c->sc, c->st);
+  k3_ext_plan(g, c->band, 0, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
               c->counts, c->ext_cap, &c->sc->err, c->st);
   double *wp[2 * S3_NC];
   for (int k = 0; k < 2; k++)
     for (int m = 0; m < S3_NC; m++) wp[k * S3_NC + m] = c->w[k][m];
   k3_launch_ext_sweeps(g, 0, c->cfg.ext_iters, c->ext, c->counts, c->ext_cap, wp, S3_NC,
-                       c->extA, c->extB, c->st);
-  k3_launch_wave_maxima(g, c->w, c->alpha, c->nostate, phi, c->sc, c->st);
-  k3_launch_interface(g, c->w, phi, c->sx, c->sy, c->sz, c->xn, c->xp, c->ul, c->sc, c->st);
-  k3_ext_plan(g, 2, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
+                       c->extA, c->extB, c->extmap, c->st);
+  for (int k = 0; k < 2; k++)
+    if (k != band_only)
+      k3_launch_wave_maxima(g, c->whole, k, c->w[k], c->alpha, c->nostate, phi, c->sc, c->st);
+  k3_launch_interface(g, c->band, c->w, phi, c->sx, c->sy, c->sz, c->xn, c->xp, c->ul, c->sc,
+                      c->st);
+  k3_ext_plan(g, c->band, 2, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
               c->counts, c->ext_cap, &c->sc->err, c->st);
   k3_launch_ext_sweeps(g, 2, c->cfg.ext_iters, c->ext, c->counts, c->ext_cap, c->ul, 3,
-                       c->extA, c->extB, c->st);
+                       c->extA, c->extB, c->extmap, c->st);
+  k3_launch_band_bricks(g, c->nbricks, phi, c->blist, c->sc, c->st);
   return read_scalars(c);
 }
 
@@ -337,8 +369,8 @@ static void fv(sif3_ctx *c, int k, int stage, double dt, double *const dst[S3_NC
 // level-set RK stage over the band of phi0
 static void ls_stage(sif3_ctx *c, int stage, double dt) {
   ghost1(c, c->phi);
-  k3_launch_ls_rhs(c->g, c->phi, c->ul, c->band, c->lphi, c->st);
-  k3_launch_rk(c->g, stage, c->phi, c->phi0, c->lphi, dt, c->band, c->st);
+  k3_launch_ls_rhs(c->g, c->band, c->phi, c->ul, c->bandmask, c->lphi, c->st);
+  k3_launch_rk(c->g, c->band, stage, c->phi, c->phi0, c->lphi, dt, c->bandmask, c->st);
 }
 
 static void reinit(sif3_ctx *c) {
@@ -347,13 +379,13 @@ static void reinit(sif3_ctx *c) {
   for (int it = 0; it < c->cfg.reinit_iters; it++) {
     ghost1(c, c->phi);
     cudaMemcpyAsync(c->old, c->phi, sizeof(double) * c->g.NP, cudaMemcpyDeviceToDevice, c->st);
-    k3_launch_reinit(c->g, c->phi, c->old, c->p0, c->rext, c->st);
+    k3_launch_reinit(c->g, c->band, c->phi, c->old, c->p0, c->rext, c->st);
   }
 }
 
 static void start_level_set_step(sif3_ctx *c) {
   cudaMemcpyAsync(c->phi0, c->phi, sizeof(double) * c->g.NP, cudaMemcpyDeviceToDevice, c->st);
-  k3_launch_band(c->g, c->phi0, c->band, c->rext, c->st);
+  k3_launch_band(c->g, c->phi0, c->bandmask, c->rext, c->st);
 }
 
 // one RK2 step of both fluids and the level set with a common dt, the
@@ -427,20 +459,20 @@ static int cycle(sif3_ctx *c, double t_end, sif_cycle_info *info) {
     sub++;
     if (sub > 4096) return fail(c, SIF_ETIMEOUT, "sub-cycle loop exceeded 4096 sub-steps");
     if (sub > 1) {
-      k3_launch_interp(c->g, c->qi, c->prev, c->fut, t2 / dt1, c->st);
+      k3_launch_interp(c->g, c->band, c->qi, c->prev, c->fut, t2 / dt1, c->st);
       geometry(c, c->phi);
       mix(c, f1, c->qi);
       for (int m = 0; m < S3_NC; m++) {
         qs[f1][m] = c->qi[m];
         qs[f2][m] = c->q[f2][m];
       }
-      rc = eval(c, qs, c->phi);
+      rc = eval(c, qs, c->phi, f1);
       if (rc) return rc;
       dt2 = dt_of(c, f2);
     }
     bool last = (dt1 - t2) <= dt2 * (1.0 + 1e-12);
     if (last) dt2 = dt1 - t2;
-    k3_launch_record(c->g, sub == 1, x1, c->xc, dt1, dt2, c->st);
+    k3_launch_record(c->g, c->band, sub == 1, x1, c->xc, dt1, dt2, c->st);
     // step 3: fluid 2 and the level set, first stage with dt2
     copy_planes(c, c->q0[f2], c->q[f2], S3_NC);
     start_level_set_step(c);
@@ -452,14 +484,14 @@ static int cycle(sif3_ctx *c, double t_end, sif_cycle_info *info) {
       mix(c, f1, c->fut);
       for (int m = 0; m < S3_NC; m++) qs[f1][m] = c->fut[m];
     } else {
-      k3_launch_interp(c->g, c->qi, c->prev, c->fut, (t2 + dt2) / dt1, c->st);
+      k3_launch_interp(c->g, c->band, c->qi, c->prev, c->fut, (t2 + dt2) / dt1, c->st);
       mix(c, f1, c->qi);
       for (int m = 0; m < S3_NC; m++) qs[f1][m] = c->qi[m];
     }
     for (int m = 0; m < S3_NC; m++) qs[f2][m] = c->q[f2][m];
-    rc = eval(c, qs, c->phi);
+    rc = eval(c, qs, c->phi, last ? -1 : f1);
     if (rc) return rc;
-    k3_launch_record(c->g, last, x1, c->xc, dt1, dt2, c->st);
+    k3_launch_record(c->g, c->band, last, x1, c->xc, dt1, dt2, c->st);
     // step 4 (and 5 on the last sub-step): second stage
     fv(c, f2, 2, dt2, c->q[f2], c->q[f2], c->q0[f2]);
     ls_stage(c, 2, dt2);
@@ -588,7 +620,9 @@ int sif3_init_fluids(sif3_ctx *c, const double *phi, const double *pN, const dou
   double *one[1] = {c->phi};
   int rc = planes_in(c, phi, 1, one, mem_kind);
   if (rc) return rc;
-  geometry(c, c->phi);
+  geometry(c, c->phi, true);
+  rc = rebuild_band(c);
+  if (rc) return rc;
   size_t n = ncell(c);
   for (int k = 0; k < 2; k++) {
     const double *src = k ? pP : pN;
@@ -632,7 +666,9 @@ int sif3_set_state(sif3_ctx *c, const double *qN, const double *qP, const double
   double *one[1] = {c->phi};
   if (!rc && phi) rc = planes_in(c, phi, 1, one, mem_kind);
   if (rc) return rc;
-  geometry(c, c->phi);
+  geometry(c, c->phi, true);
+  rc = rebuild_band(c);
+  if (rc) return rc;
   c->inited = true;
   return cuda_check(c, cudaStreamSynchronize(c->st), "set state");
 }
@@ -659,7 +695,7 @@ int sif3_geometry(sif3_ctx *c, double *alpha, double *ax, double *ay, double *az
   if (!c) return SIF_EINVAL;
   if (!kind_ok(mem_kind)) return fail(c, SIF_EINVAL, "bad mem_kind");
   cudaSetDevice(c->cfg.device);
-  geometry(c, c->phi);
+  geometry(c, c->phi, true);
   double *outs[7] = {alpha, ax, ay, az, sx, sy, sz};
   double *srcs[7] = {c->alpha, c->ax, c->ay, c->az, c->sx, c->sy, c->sz};
   for (int q = 0; q < 7; q++) {

@@ -1,97 +1,67 @@
 // fv3d.cu -- the three-dimensional cut-cell finite-volume stage (Eq. 2
-// with six faces): one CTA per brick of 8 x 8 x 4 cells.
+// with six faces): one CTA of 256 threads per brick of 8 x 8 x 4 cells,
+// one thread per cell.
 //
 // The CTA first checks whether any face of its cells is open to the fluid;
-// a closed brick has L = 0 and is left as it is.  Otherwise each face of
-// the brick (the cells' lower faces and the brick's upper boundary faces:
-// 9 x 8 x 4 + 8 x 9 x 4 + 8 x 8 x 5 = 896) is computed once: the stencil
-// states of its six cells along the normal give the Lax-Friedrichs split
-// fluxes f+- = (F_d +- a_d U)/2 (a_d the fluid's global speed, Sec. 4's
-// WENO-LF), each conserved component is reconstructed by WENO5-JS from
-// both sides, and the face value times the aperture A_k goes to shared
-// memory (36 KB).  Each thread then forms its cell's divergence plus the
-// interface exchange X / V and applies the RK stage in registers.
+// a closed brick has L = 0 (see Fv3Args for what the RK stage then does).
+// Otherwise the three directions are taken in turn, each in three phases
+// separated by barriers: (1) the Lax-Friedrichs split fluxes f+- = (F_d +-
+// a_d U)/2 (a_d the fluid's global speed, Sec. 4's WENO-LF) of every cell
+// of the brick and of the three cells beyond it on either side along d go
+// to shared memory, each computed once; (2) each (face, component) of the
+// brick's faces along d -- its cells' lower faces and the brick's upper
+// boundary -- is reconstructed by WENO5-JS from both sides and multiplied
+// by the aperture A_k (the two reconstructions as fractions over one
+// reciprocal, weno_frac.cuh), into shared memory; (3) each thread adds its cell's
+// difference of the two faces over h_d to its right-hand side in
+// registers.  The interface exchange X / V and the RK stage follow in
+// registers.  64 KB of shared memory and 82 registers: three CTAs per SM.
 #include <atomic>
 
 #include "sif3d_internal.cuh"
+#include "weno_frac.cuh"
 
 static std::atomic<unsigned long long> g_fv_launches{0};
 unsigned long long k3_fv_launches() { return g_fv_launches.load(); }
-
-#define NFX (S3_BX + 1) * S3_BY * S3_BZ
-#define NFY S3_BX * (S3_BY + 1) * S3_BZ
-#define NFZ S3_BX * S3_BY * (S3_BZ + 1)
-
-__device__ inline double sqf(double a) { return a * a; }
-
-__device__ inline double weno5_fv(double v1, double v2, double v3, double v4, double v5,
-                                  double eps) {
-  double q0 = (2.0 * v1 - 7.0 * v2 + 11.0 * v3) / 6.0;
-  double q1 = (-v2 + 5.0 * v3 + 2.0 * v4) / 6.0;
-  double q2 = (2.0 * v3 + 5.0 * v4 - v5) / 6.0;
-  double b0 = 13.0 / 12.0 * sqf(v1 - 2.0 * v2 + v3) + 0.25 * sqf(v1 - 4.0 * v2 + 3.0 * v3);
-  double b1 = 13.0 / 12.0 * sqf(v2 - 2.0 * v3 + v4) + 0.25 * sqf(v2 - v4);
-  double b2 = 13.0 / 12.0 * sqf(v3 - 2.0 * v4 + v5) + 0.25 * sqf(3.0 * v3 - 4.0 * v4 + v5);
-  double a0 = 0.1 / sqf(eps + b0);
-  double a1 = 0.6 / sqf(eps + b1);
-  double a2 = 0.3 / sqf(eps + b2);
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
-}
-
-// WENO5-LF flux of every component at the lower d-face of cell c
-__device__ inline void face_flux3(const Grid3 &g, const Fv3Args &a, int c, int s, int d,
-                                  double *Fh) {
-  const double gm = g.gamma[a.k], pi = g.pinf[a.k], ad = a.lf[d];
-  double U[6][S3_NC], F[6][S3_NC];
-#pragma unroll
-  for (int r = 0; r < 6; r++) {
-    int cc = c + (r - 3) * s;
-    double rho = a.w[0][cc], u = a.w[1][cc], v = a.w[2][cc], w = a.w[3][cc], p = a.w[4][cc];
-    double E = (p + gm * pi) / (gm - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
-    double un = d == 0 ? u : d == 1 ? v : w;
-    U[r][0] = rho;
-    U[r][1] = rho * u;
-    U[r][2] = rho * v;
-    U[r][3] = rho * w;
-    U[r][4] = E;
-    F[r][0] = rho * un;
-    F[r][1] = rho * u * un + (d == 0 ? p : 0.0);
-    F[r][2] = rho * v * un + (d == 1 ? p : 0.0);
-    F[r][3] = rho * w * un + (d == 2 ? p : 0.0);
-    F[r][4] = un * (E + p);
-  }
-#pragma unroll
-  for (int m = 0; m < S3_NC; m++) {
-    double fp[6], fm[6];
-#pragma unroll
-    for (int r = 0; r < 6; r++) {
-      fp[r] = 0.5 * (F[r][m] + ad * U[r][m]);
-      fm[r] = 0.5 * (F[r][m] - ad * U[r][m]);
-    }
-    Fh[m] = weno5_fv(fp[0], fp[1], fp[2], fp[3], fp[4], g.eps) +
-            weno5_fv(fm[5], fm[4], fm[3], fm[2], fm[1], g.eps);
-  }
-}
 
 __device__ inline double ap3(const double *A, int k, int c) {
   return k == 1 ? A[c] : 1.0 - A[c];
 }
 
-__global__ void __launch_bounds__(256) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
-  __shared__ double fx[S3_NC][NFX];
-  __shared__ double fy[S3_NC][NFY];
-  __shared__ double fz[S3_NC][NFZ];
+// extents of the direction-d pass: the brick plus three cells on either
+// side along d (the split fluxes a face's stencil reads), and its faces
+__host__ __device__ constexpr int reg_len(int d) {
+  return d == 0 ? S3_BX + 6 : d == 1 ? S3_BY + 6 : S3_BZ + 6;
+}
+__host__ __device__ constexpr int brick_len(int d) {
+  return d == 0 ? S3_BX : d == 1 ? S3_BY : S3_BZ;
+}
+#define S3_REG_MAX ((S3_BZ + 6) * S3_BX * S3_BY)  // the z pass is the largest
+#define S3_FACE_MAX (S3_BX * S3_BY * (S3_BZ + 1))
+#define S3_FV_SMEM (sizeof(double) * S3_NC * (2 * S3_REG_MAX + S3_FACE_MAX))
+
+__global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
+  extern __shared__ double smem[];
+  double *sp = smem;                              // f+ [m][cell of the pass]
+  double *sm = sp + S3_NC * S3_REG_MAX;           // f- [m][cell of the pass]
+  double *sf = sm + S3_NC * S3_REG_MAX;           // A_k F [m][face of the pass]
   const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
   const int tid = threadIdx.x;
   const int li = tid % S3_BX, lj = (tid / S3_BX) % S3_BY, lk = tid / (S3_BX * S3_BY);
   const int i = bx * S3_BX + li, j = by * S3_BY + lj, kk = bz * S3_BZ + lk;
   const bool valid = i < g.nx && j < g.ny && kk < g.nz;
-  const int k = a.k, sx = 1, sy = g.PX, sz = g.PX * g.PY;
+  const int k = a.k;
+  const int st[3] = {1, g.PX, g.PX * g.PY};
+  const int nn[3] = {g.nx, g.ny, g.nz};
+  const int b0[3] = {bx * S3_BX, by * S3_BY, bz * S3_BZ};
+  const double *Ad[3] = {a.ax, a.ay, a.az};
+  // reciprocals of the cell sizes and volume, one division each per thread
+  const double ih[3] = {1.0 / g.dx, 1.0 / g.dy, 1.0 / g.dz};
   int c = valid ? g3(g, i, j, kk) : 0;
   int open = 0;
   if (valid)
-    open = ap3(a.ax, k, c) != 0.0 || ap3(a.ax, k, c + sx) != 0.0 || ap3(a.ay, k, c) != 0.0 ||
-           ap3(a.ay, k, c + sy) != 0.0 || ap3(a.az, k, c) != 0.0 || ap3(a.az, k, c + sz) != 0.0;
+    for (int d = 0; d < 3; d++)
+      open |= ap3(Ad[d], k, c) != 0.0 || ap3(Ad[d], k, c + st[d]) != 0.0;
   int nopen = __syncthreads_count(open);
   const int brick = bx + gridDim.x * (by + gridDim.y * bz);
   if (nopen == 0) {
@@ -104,75 +74,107 @@ __global__ void __launch_bounds__(256) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
       a.dst[m][c] = 0.5 * a.base[m][c] + 0.5 * (a.cur[m][c] + a.dt * 0.0);
     return;
   }
-  if (tid == 0 && a.stage == 1) a.touched[brick] = 1;
   if (tid == 0) {
-    int ncell = min(S3_BX, g.nx - bx * S3_BX) * min(S3_BY, g.ny - by * S3_BY) *
-                min(S3_BZ, g.nz - bz * S3_BZ);
+    if (a.stage == 1) a.touched[brick] = 1;
+    int ncell = min(S3_BX, g.nx - b0[0]) * min(S3_BY, g.ny - b0[1]) * min(S3_BZ, g.nz - b0[2]);
     atomicAdd(&sc->cells, (unsigned long long)ncell);
     atomicAdd(&sc->open, (unsigned long long)nopen);
   }
-  // faces: x-faces (ii in 0..8) then y-faces (jj in 0..8) then z-faces
-  for (int f = tid; f < NFX + NFY + NFZ; f += blockDim.x) {
-    int d, fi, fj, fk, slot;
-    if (f < NFX) {
-      d = 0;
-      slot = f;
-      fi = f % (S3_BX + 1);
-      fj = (f / (S3_BX + 1)) % S3_BY;
-      fk = f / ((S3_BX + 1) * S3_BY);
-    } else if (f < NFX + NFY) {
-      d = 1;
-      slot = f - NFX;
-      fi = slot % S3_BX;
-      fj = (slot / S3_BX) % (S3_BY + 1);
-      fk = slot / (S3_BX * (S3_BY + 1));
-    } else {
-      d = 2;
-      slot = f - NFX - NFY;
-      fi = slot % S3_BX;
-      fj = (slot / S3_BX) % S3_BY;
-      fk = slot / (S3_BX * S3_BY);
-    }
-    int gi = bx * S3_BX + fi, gj = by * S3_BY + fj, gk = bz * S3_BZ + fk;
-    // a face belongs to the domain if its cell (the one above it) is
-    // inside along the other two axes and at most n along its own
-    bool ok = d == 0 ? (gi <= g.nx && gj < g.ny && gk < g.nz)
-                     : d == 1 ? (gi < g.nx && gj <= g.ny && gk < g.nz)
-                              : (gi < g.nx && gj < g.ny && gk <= g.nz);
-    double Fh[S3_NC] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (ok) {
-      int cf = g3(g, gi, gj, gk);
-      const double *A = d == 0 ? a.ax : d == 1 ? a.ay : a.az;
-      double Ak = ap3(A, k, cf);
-      if (Ak != 0.0) {
-        face_flux3(g, a, cf, d == 0 ? sx : d == 1 ? sy : sz, d, Fh);
-        for (int m = 0; m < S3_NC; m++) Fh[m] = Ak * Fh[m];
+  const double gm = g.gamma[k], pi = g.pinf[k];
+  const double eps = g.eps * (12.0 / 13.0);  // see weno5_frac
+  double r[S3_NC] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    // pass layout: position along d fastest, then the two other axes in
+    // (x, y, z) order
+    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+    const int L = reg_len(d), n1 = brick_len(e1), n2 = brick_len(e2);
+    const int ncells = L * n1 * n2, nfaces = (brick_len(d) + 1) * n1 * n2;
+    const double ad = a.lf[d];
+    // split fluxes of every cell of the pass
+    for (int t = tid; t < ncells; t += blockDim.x) {
+      int p = t % L, q1 = (t / L) % n1, q2 = t / (L * n1);
+      int x[3];
+      x[d] = b0[d] - 3 + p;
+      x[e1] = b0[e1] + q1;
+      x[e2] = b0[e2] + q2;
+      bool in = x[d] >= -3 && x[d] < nn[d] + 3 && x[e1] < nn[e1] && x[e2] < nn[e2];
+      double fp[S3_NC] = {0.0, 0.0, 0.0, 0.0, 0.0}, fm[S3_NC] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      if (in) {
+        int cc = g3(g, x[0], x[1], x[2]);
+        double rho = a.w[0][cc], u = a.w[1][cc], v = a.w[2][cc], w = a.w[3][cc];
+        double pr = a.w[4][cc];
+        double E = (pr + gm * pi) / (gm - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+        double un = d == 0 ? u : d == 1 ? v : w;
+        double U[S3_NC] = {rho, rho * u, rho * v, rho * w, E};
+        double F[S3_NC] = {rho * un, rho * u * un + (d == 0 ? pr : 0.0),
+                           rho * v * un + (d == 1 ? pr : 0.0),
+                           rho * w * un + (d == 2 ? pr : 0.0), un * (E + pr)};
+#pragma unroll
+        for (int m = 0; m < S3_NC; m++) {
+          fp[m] = 0.5 * (F[m] + ad * U[m]);
+          fm[m] = 0.5 * (F[m] - ad * U[m]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < S3_NC; m++) {
+        sp[m * S3_REG_MAX + t] = fp[m];
+        sm[m * S3_REG_MAX + t] = fm[m];
       }
     }
-    double *dst = d == 0 ? &fx[0][0] : d == 1 ? &fy[0][0] : &fz[0][0];
-    int stride = d == 0 ? NFX : d == 1 ? NFY : NFZ;
-    for (int m = 0; m < S3_NC; m++) dst[m * stride + slot] = Fh[m];
+    __syncthreads();
+    // (face, component) items: WENO5 from both sides times the aperture
+    for (int t = tid; t < nfaces * S3_NC; t += blockDim.x) {
+      int f = t % nfaces, m = t / nfaces;
+      int p = f % (brick_len(d) + 1), q = f / (brick_len(d) + 1);
+      int q1 = q % n1, q2 = q / n1;
+      int x[3];
+      x[d] = b0[d] + p;
+      x[e1] = b0[e1] + q1;
+      x[e2] = b0[e2] + q2;
+      double Fh = 0.0;
+      if (x[d] <= nn[d] && x[e1] < nn[e1] && x[e2] < nn[e2]) {
+        double Ak = ap3(Ad[d], k, g3(g, x[0], x[1], x[2]));
+        if (Ak != 0.0) {
+          // the face between pass cells p + 2 and p + 3
+          const double *P = sp + m * S3_REG_MAX + q * L + p;
+          const double *M = sm + m * S3_REG_MAX + q * L + p;
+          double nl, dl, nr, dr;
+          weno5_frac(P[0], P[1], P[2], P[3], P[4], eps, nl, dl);
+          weno5_frac(M[5], M[4], M[3], M[2], M[1], eps, nr, dr);
+          Fh = face_value(Ak, nl, dl, nr, dr);
+        }
+      }
+      sf[m * S3_FACE_MAX + f] = Fh;
+    }
+    __syncthreads();
+    if (valid) {
+      int x[3] = {li, lj, lk};
+      int lo = x[d] + (brick_len(d) + 1) * (x[e1] + n1 * x[e2]);
+#pragma unroll
+      for (int m = 0; m < S3_NC; m++)
+        r[m] += (sf[m * S3_FACE_MAX + lo] - sf[m * S3_FACE_MAX + lo + 1]) * ih[d];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (!valid) return;
-  const int ix = li + (S3_BX + 1) * (lj + S3_BY * lk);
-  const int iy = li + S3_BX * (lj + (S3_BY + 1) * lk);
-  const int iz = li + S3_BX * (lj + S3_BY * lk);
-  const double dv = g.dx * g.dy * g.dz;
+  const double idv = 1.0 / (g.dx * g.dy * g.dz);
+#pragma unroll
   for (int m = 0; m < S3_NC; m++) {
-    double r = 0.0;
-    r += (fx[m][ix] - fx[m][ix + 1]) / g.dx;
-    r += (fy[m][iy] - fy[m][iy + S3_BX]) / g.dy;
-    r += (fz[m][iz] - fz[m][iz + S3_BX * S3_BY]) / g.dz;
-    if (m > 0) r += a.x[m - 1][c] / dv;
+    double rr = r[m];
+    if (m > 0) rr += a.x[m - 1][c] * idv;
     double cur = a.cur[m][c];
-    double v = a.stage == 1 ? cur + a.dt * r : 0.5 * a.base[m][c] + 0.5 * (cur + a.dt * r);
-    a.dst[m][c] = v;
+    a.dst[m][c] = a.stage == 1 ? cur + a.dt * rr : 0.5 * a.base[m][c] + 0.5 * (cur + a.dt * rr);
   }
 }
 
 void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k3_fv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3_FV_SMEM);
+    attr = true;
+  }
   dim3 grid((g.nx + S3_BX - 1) / S3_BX, (g.ny + S3_BY - 1) / S3_BY, (g.nz + S3_BZ - 1) / S3_BZ);
-  k3_fv<<<grid, S3_BX * S3_BY * S3_BZ, 0, st>>>(g, a, sc);
+  k3_fv<<<grid, S3_BX * S3_BY * S3_BZ, S3_FV_SMEM, st>>>(g, a, sc);
   g_fv_launches++;
 }

@@ -7,10 +7,12 @@
 // Compiled without FMA contraction: these kernels take the method's
 // branch decisions (signs, thresholds, target choices), which therefore
 // round like a plain serial evaluation of the same formulas.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
 #include "sif3d_internal.cuh"
+#include "sif_internal.cuh"
 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long k3_launches() { return g_launches.load(); }
@@ -75,7 +77,9 @@ __global__ void k3_ghost(Grid3 g, Planes3 s, int d) {
     ci = a, cj = b, ck = src, di = a, dj = b, dk = dst;
   }
   int cs = g3(g, ci, cj, ck), cd = g3(g, di, dj, dk);
-  for (int q = 0; q < s.n; q++) {
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    if (q >= s.n) break;
     double v = s.p[q][cs];
     s.p[q][cd] = (s.vel[q] == d + 1 && bc == 0) ? -v : v;
   }
@@ -149,18 +153,64 @@ __device__ inline double corner3(const Grid3 &g, const double *p, int i, int j, 
   return 0.125 * (a + b);
 }
 
+// positions of the extended range (indices 0..n along each axis): the
+// whole range, or per listed brick its cells and the layer above them (9
+// x 9 x 5 positions in 512 threads; neighbouring bricks share a layer and
+// write the same values there)
+#define S3_EXT_SLOTS 512
+__device__ inline bool region_ext(const Grid3 &g, const Region &R, long long t, int &i, int &j,
+                                  int &k) {
+  int ex = g.nx + 1, ey = g.ny + 1;
+  if (!R.list) {
+    if (t >= (long long)ex * ey * (g.nz + 1)) return false;
+    i = (int)(t % ex);
+    j = (int)((t / ex) % ey);
+    k = (int)(t / ((long long)ex * ey));
+    return true;
+  }
+  long long b = t / S3_EXT_SLOTS;
+  int l = (int)(t % S3_EXT_SLOTS);
+  if (b >= R.count || l >= (S3_BX + 1) * (S3_BY + 1) * (S3_BZ + 1)) return false;
+  int bi = R.list[b];
+  int nbx = (g.nx + S3_BX - 1) / S3_BX, nby = (g.ny + S3_BY - 1) / S3_BY;
+  i = (bi % nbx) * S3_BX + l % (S3_BX + 1);
+  j = ((bi / nbx) % nby) * S3_BY + (l / (S3_BX + 1)) % (S3_BY + 1);
+  k = (bi / (nbx * nby)) * S3_BZ + l / ((S3_BX + 1) * (S3_BY + 1));
+  return i <= g.nx && j <= g.ny && k <= g.nz;
+}
+
+inline long long region_ext_threads(const Grid3 &g, const Region &R) {
+  return R.list ? (long long)R.count * S3_EXT_SLOTS
+                : (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+}
+
+// corner values of the lower corners (indices 0..n), each from the eight
+// cells around it.  Over the band list: a changed level-set value changes
+// only the corners of its own cell and the cell above along each axis,
+// both inside its brick's range
+__global__ void k3_corners(Grid3 g, Region R, const double *phi, double *corner) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!region_ext(g, R, t, i, j, k)) return;
+  corner[g3(g, i, j, k)] = corner3(g, phi, i, j, k);
+}
+
 // one thread per cell of the (nx+1)(ny+1)(nz+1) extended range: the
 // apertures of the cell's three lower faces and, for interior cells,
 // alpha_P and S from the divergence theorem over the P region
-__global__ void k3_geometry(Grid3 g, const double *phi, double *alpha, double *ax, double *ay,
-                            double *az, double *sxo, double *syo, double *szo) {
-  int ex = g.nx + 1, ey = g.ny + 1;
-  long long total = (long long)ex * ey * (g.nz + 1);
+__global__ void k3_geometry(Grid3 g, Region R, const double *corner, double *alpha, double *ax,
+                            double *ay, double *az, double *sxo, double *syo, double *szo) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+  int i, j, k;
+  if (!region_ext(g, R, t, i, j, k)) return;
+  // corners beyond the upper ends (index n + 1) exist only for the faces
+  // a thread of the extended range does not write; they read zeros
   double C[8];
-  for (int v = 0; v < 8; v++) C[v] = corner3(g, phi, i + (v & 1), j + ((v >> 1) & 1), k + (v >> 2));
+#pragma unroll
+  for (int v = 0; v < 8; v++) {
+    int ci = i + (v & 1), cj = j + ((v >> 1) & 1), ck = k + (v >> 2);
+    C[v] = (ci <= g.nx && cj <= g.ny && ck <= g.nz) ? corner[g3(g, ci, cj, ck)] : 0.0;
+  }
   // faces in their own (a, b) axes counter-clockwise: x-face (y, z),
   // y-face (x, z), z-face (x, y); C index = di + 2 dj + 4 dk
   double axm = sq_fraction(C[0], C[2], C[6], C[4]);
@@ -190,9 +240,12 @@ __global__ void k3_geometry(Grid3 g, const double *phi, double *alpha, double *a
     // order of the other two coordinates ((d+1) mod 3, (d+2) mod 3)
     double m0 = 0.0, m1 = 0.0, m2 = 0.0;
     int nc = 0;
+#pragma unroll
     for (int d = 0; d < 3; d++) {
       int e1 = d == 2 ? 0 : d + 1, e2 = d == 0 ? 2 : d - 1;
+#pragma unroll
       for (int a = 0; a < 2; a++)
+#pragma unroll
         for (int b = 0; b < 2; b++) {
           int lo = (a << e1) | (b << e2);  // corner index bit per axis
           int hi = lo | (1 << d);
@@ -220,11 +273,32 @@ __global__ void k3_geometry(Grid3 g, const double *phi, double *alpha, double *a
   alpha[c] = al;
 }
 
-void k3_launch_geometry(const Grid3 &g, const double *phi, double *alpha, double *ax,
-                        double *ay, double *az, double *sx, double *sy, double *sz,
-                        cudaStream_t st) {
-  long long total = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-  k3_geometry<<<nblk(total, 128), 128, 0, st>>>(g, phi, alpha, ax, ay, az, sx, sy, sz);
+void k3_launch_geometry(const Grid3 &g, const Region &R, const double *phi, double *corner,
+                        double *alpha, double *ax, double *ay, double *az, double *sx,
+                        double *sy, double *sz, cudaStream_t st) {
+  long long total = region_ext_threads(g, R);
+  if (total == 0) return;
+  k3_corners<<<nblk(total, 256), 256, 0, st>>>(g, R, phi, corner);
+  k3_geometry<<<nblk(total, 128), 128, 0, st>>>(g, R, corner, alpha, ax, ay, az, sx, sy, sz);
+  tick(2);
+}
+
+// the band list: every brick with a cell closer to the interface than
+// thr (|phi| < thr), one CTA per brick; the count lands in sc->nband
+__global__ void k3_band_bricks(Grid3 g, const double *phi, double thr, int *list, Scal3 *sc) {
+  const int bi = blockIdx.x, tid = threadIdx.x;
+  int nbx = (g.nx + S3_BX - 1) / S3_BX, nby = (g.ny + S3_BY - 1) / S3_BY;
+  int i = (bi % nbx) * S3_BX + tid % S3_BX;
+  int j = ((bi / nbx) % nby) * S3_BY + (tid / S3_BX) % S3_BY;
+  int k = (bi / (nbx * nby)) * S3_BZ + tid / (S3_BX * S3_BY);
+  int near = i < g.nx && j < g.ny && k < g.nz && fabs(phi[g3(g, i, j, k)]) < thr;
+  if (__syncthreads_or(near) && tid == 0) list[atomicAdd(&sc->nband, 1)] = bi;
+}
+
+void k3_launch_band_bricks(const Grid3 &g, int nbricks, const double *phi, int *list, Scal3 *sc,
+                           cudaStream_t st) {
+  cudaMemsetAsync(&sc->nband, 0, sizeof(int), st);
+  k3_band_bricks<<<nbricks, S3_BX * S3_BY * S3_BZ, 0, st>>>(g, phi, g.bw + 3.0 * g.h, list, sc);
   tick();
 }
 
@@ -296,17 +370,12 @@ void k3_launch_init_state(const Grid3 &g, const double *alpha, const double *pri
 // hold fluid k; a cut cell whose content is not a physical state is marked
 // and treated as empty by the stencils; a full one is an error
 
-__global__ void k3_prim(Grid3 g, Planes3 q0, Planes3 q1, Planes3 w0, Planes3 w1,
-                        const double *alpha, unsigned char *nostate, Scal3 *sc) {
-  long long n = (long long)g.nx * g.ny * g.nz;
+__global__ void k3_prim(Grid3 g, Region R, int k, Planes3 q, Planes3 w, const double *alpha,
+                        unsigned char *nostate, Scal3 *sc) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int k = blockIdx.y;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
-  const Planes3 &q = k ? q1 : q0;
-  const Planes3 &w = k ? w1 : w0;
   unsigned char *ns = nostate + (size_t)k * g.NP;
   double a = volk(alpha, k, c);
   ns[c] = 0;
@@ -335,17 +404,17 @@ __global__ void k3_prim(Grid3 g, Planes3 q0, Planes3 q1, Planes3 w0, Planes3 w1,
   w.p[4][c] = p;
 }
 
-void k3_launch_prim(const Grid3 &g, double *const q[2][S3_NC], double *const w[2][S3_NC],
-                    const double *alpha, unsigned char *nostate, Scal3 *sc, cudaStream_t st) {
-  Planes3 P[4] = {};
+void k3_launch_prim(const Grid3 &g, const Region &R, int k, double *const q[S3_NC],
+                    double *const w[S3_NC], const double *alpha, unsigned char *nostate,
+                    Scal3 *sc, cudaStream_t st) {
+  Planes3 Q{}, W{};
   for (int m = 0; m < S3_NC; m++) {
-    P[0].p[m] = q[0][m];
-    P[1].p[m] = q[1][m];
-    P[2].p[m] = w[0][m];
-    P[3].p[m] = w[1][m];
+    Q.p[m] = q[m];
+    W.p[m] = w[m];
   }
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_prim<<<dim3(nblk(n, 256), 2), 256, 0, st>>>(g, P[0], P[1], P[2], P[3], alpha, nostate, sc);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_prim<<<nblk(n, 256), 256, 0, st>>>(g, R, k, Q, W, alpha, nostate, sc);
   tick();
 }
 
@@ -371,16 +440,14 @@ __device__ inline void normal3(const Grid3 &g, const double *p, int c, double n[
 // interaction step; the sweeps then read the neighbours' previous values
 // from the slot buffer (targets) or the plane (everything else).
 
-__global__ void k3_ext_mark(Grid3 g, int group, const double *phi, const double *alpha,
+__global__ void k3_ext_mark(Grid3 g, Region R, int group, const double *phi, const double *alpha,
                             const unsigned char *nostate, const double *sx, const double *sy,
                             const double *sz, int *map, Ext3 *plan, int *count, int cap,
                             int *err) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int grp = group < 2 ? blockIdx.y : 2;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   if (!(fabs(phi[c]) < g.bw)) return;
   if (grp < 2) {
@@ -429,17 +496,19 @@ __global__ void k3_ext_setup(Grid3 g, int group, const double *phi, const int *m
     e.slot[d] = e.w[d] > 0.0 ? map[(size_t)grp * g.NP + e.nb[d]] : -1;
 }
 
-int k3_ext_plan(const Grid3 &g, int group, const double *phi, const double *alpha,
-                const unsigned char *nostate, const double *sx, const double *sy,
-                const double *sz, int *map, Ext3 *plan, int *count, int cap, int *err,
-                cudaStream_t st) {
+int k3_ext_plan(const Grid3 &g, const Region &R, int group, const double *phi,
+                const double *alpha, const unsigned char *nostate, const double *sx,
+                const double *sy, const double *sz, int *map, Ext3 *plan, int *count, int cap,
+                int *err, cudaStream_t st) {
+  // map holds -1 everywhere between plans (set at creation, restored by
+  // the last sweep for the cells it marked)
   int groups = group < 2 ? 2 : 1, g0 = group < 2 ? 0 : 2;
-  cudaMemsetAsync(map + (size_t)g0 * g.NP, 0xff, sizeof(int) * (size_t)g.NP * groups, st);
   cudaMemsetAsync(count + g0, 0, sizeof(int) * groups, st);
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_ext_mark<<<dim3(nblk(n, 256), groups), 256, 0, st>>>(g, group, phi, alpha, nostate, sx,
-                                                          sy, sz, map, plan, count, cap,
-                                                          err);
+  long long n = region_threads(g, R);
+  if (n > 0)
+    k3_ext_mark<<<dim3(nblk(n, 256), groups), 256, 0, st>>>(g, R, group, phi, alpha, nostate,
+                                                            sx, sy, sz, map, plan, count, cap,
+                                                            err);
   k3_ext_setup<<<dim3(nblk(cap, 128), groups), 128, 0, st>>>(g, group, phi, map, plan, count,
                                                               cap);
   tick(2);
@@ -455,7 +524,8 @@ struct ExtBufs {
 // first sweep (first = 1) takes the targets' own start values from the
 // planes, the last one (last = 1) writes the results into the planes
 __global__ void k3_ext_sweep(Grid3 g, int group, int nf, ExtBufs B, const Ext3 *plan,
-                             const int *count, int cap, int first, int last, int iters) {
+                             const int *count, int cap, int first, int last, int iters,
+                             int *map) {
   int grp = group < 2 ? blockIdx.y : 2;
   int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= min(count[grp], cap)) return;
@@ -482,11 +552,12 @@ __global__ void k3_ext_sweep(Grid3 g, int group, int nf, ExtBufs B, const Ext3 *
     else
       wr[(size_t)m * cap + slot] = val;
   }
+  if (last) map[(size_t)grp * g.NP + e.cell] = -1;
 }
 
 void k3_launch_ext_sweeps(const Grid3 &g, int group, int iters, const Ext3 *plan,
                           const int *count, int cap, double *const planes[], int nf,
-                          double *bufA, double *bufB, cudaStream_t st) {
+                          double *bufA, double *bufB, int *map, cudaStream_t st) {
   // planes: for group < 2, 2 * S3_NC pointers (fluid N then P); else nf
   ExtBufs B{};
   int groups = group < 2 ? 2 : 1;
@@ -503,17 +574,19 @@ void k3_launch_ext_sweeps(const Grid3 &g, int group, int iters, const Ext3 *plan
     B.a = a;
     B.b = b;
     k3_ext_sweep<<<grid, 128, 0, st>>>(g, group, nf, B, plan, count, cap, s == 0,
-                                       iters > 1 && s == iters - 1, iters);
+                                       iters > 1 && s == iters - 1, iters, map);
     double *t = a;
     a = b;
     b = t;
   }
-  if (iters == 1) {
+  if (iters <= 1) {
+    // no sweep left to write the planes (and restore the maps): a copy pass
     B.a = a;
     B.b = b;
-    k3_ext_sweep<<<grid, 128, 0, st>>>(g, group, nf, B, plan, count, cap, 0, 1, 0);
+    k3_ext_sweep<<<grid, 128, 0, st>>>(g, group, nf, B, plan, count, cap, iters == 0, 1, 0,
+                                       map);
   }
-  tick(iters + (iters == 1));
+  tick(iters + (iters <= 1));
 }
 
 // ---------------------------------------------------------------------
@@ -526,49 +599,69 @@ __device__ inline double warp_max3(double v) {
   return v;
 }
 
-__global__ void k3_wave_maxima(Grid3 g, Planes3 w0, Planes3 w1, const double *alpha,
-                               const unsigned char *nostate, const double *phi, Scal3 *sc) {
-  long long n = (long long)g.nx * g.ny * g.nz;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int k = blockIdx.y;
-  double l[3] = {0.0, 0.0, 0.0}, s = 0.0;
-  if (t < n) {
-    int i, j, kk;
-    cell_ijk(g, (int)t, i, j, kk);
-    int c = g3(g, i, j, kk);
-    const Planes3 &w = k ? w1 : w0;
-    bool real = volk(alpha, k, c) > S3_ALPHA_REAL && !nostate[(size_t)k * g.NP + c];
-    if (real || fabs(phi[c]) < g.bw) {
-      double rho = w.p[0][c], pr = w.p[4][c];
-      double cs = sqrt(fmax(g.gamma[k] * (pr + g.pinf[k]) / rho, 0.0));
-      double r = 0.0;
-      const double hd[3] = {g.dx, g.dy, g.dz};
-      for (int d = 0; d < 3; d++) {
-        double a = fabs(w.p[1 + d][c]) + cs;
-        l[d] = a;
-        r += a / hd[d];
-      }
-      if (real) s = r;
-    }
+// maxima of n values over the block (warp shuffles, then shared memory),
+// one atomic per value and block: the maxima of a whole-grid launch would
+// otherwise serialise on a few addresses
+template <int N>
+__device__ inline void block_max_atomic(double (&v)[N], unsigned long long *const (&dst)[N]) {
+  __shared__ double part[N][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < N; q++) {
+    double x = warp_max3(v[q]);
+    if (lane == 0) part[q][wid] = x;
   }
-  for (int d = 0; d < 3; d++) l[d] = warp_max3(l[d]);
-  s = warp_max3(s);
-  if ((threadIdx.x & 31) == 0) {
-    for (int d = 0; d < 3; d++) atomic_max_d(&sc->lf[k][d], l[d]);
-    atomic_max_d(&sc->smax[k], s);
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < N; q++) {
+      double x = lane < nw ? part[q][lane] : 0.0;
+      x = warp_max3(x);
+      if (lane == 0) atomic_max_d(dst[q], x);
+    }
   }
 }
 
-void k3_launch_wave_maxima(const Grid3 &g, double *const w[2][S3_NC], const double *alpha,
-                           const unsigned char *nostate, const double *phi, Scal3 *sc,
-                           cudaStream_t st) {
-  Planes3 P[2] = {};
-  for (int m = 0; m < S3_NC; m++) {
-    P[0].p[m] = w[0][m];
-    P[1].p[m] = w[1][m];
+// grid-stride: a few blocks per SM, each thread keeping its maxima over
+// many cells, so that few atomics reach the four addresses
+__global__ void k3_wave_maxima(Grid3 g, Region R, int k, Planes3 w, const double *alpha,
+                               const unsigned char *nostate, const double *phi, Scal3 *sc,
+                               long long nthreads) {
+  double l[3] = {0.0, 0.0, 0.0}, s = 0.0;
+  const double hd[3] = {g.dx, g.dy, g.dz};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nthreads;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i, j, kk;
+    if (!region_cell(g, R, t, i, j, kk)) continue;
+    int c = g3(g, i, j, kk);
+    bool real = volk(alpha, k, c) > S3_ALPHA_REAL && !nostate[(size_t)k * g.NP + c];
+    if (!(real || fabs(phi[c]) < g.bw)) continue;
+    double rho = w.p[0][c], pr = w.p[4][c];
+    double cs = sqrt(fmax(g.gamma[k] * (pr + g.pinf[k]) / rho, 0.0));
+    double r = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      double a = fabs(w.p[1 + d][c]) + cs;
+      l[d] = fmax(l[d], a);
+      r += a / hd[d];
+    }
+    if (real) s = fmax(s, r);
   }
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_wave_maxima<<<dim3(nblk(n, 256), 2), 256, 0, st>>>(g, P[0], P[1], alpha, nostate, phi, sc);
+  double v[4] = {l[0], l[1], l[2], s};
+  unsigned long long *const dst[4] = {&sc->lf[k][0], &sc->lf[k][1], &sc->lf[k][2],
+                                      &sc->smax[k]};
+  block_max_atomic<4>(v, dst);
+}
+
+void k3_launch_wave_maxima(const Grid3 &g, const Region &R, int k, double *const w[S3_NC],
+                           const double *alpha, const unsigned char *nostate, const double *phi,
+                           Scal3 *sc, cudaStream_t st) {
+  Planes3 W{};
+  for (int m = 0; m < S3_NC; m++) W.p[m] = w[m];
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  int blocks = std::min(nblk(n, 256), 152 * 8);
+  k3_wave_maxima<<<blocks, 256, 0, st>>>(g, R, k, W, alpha, nostate, phi, sc, n);
   tick();
 }
 
@@ -578,48 +671,18 @@ void k3_launch_wave_maxima(const Grid3 &g, double *const w[2][S3_NC], const doub
 // guess with the pressure floor kept at a distance; either side may be a
 // Tait fluid (barotropic shock branch)
 
-__device__ inline void side3(double p, double rho, double pk, double g, double pi, double ck,
-                             int baro, double &f, double &df) {
-  double P = pk + pi, Pp = p + pi;
-  if (p > pk && baro) {
-    double x = (p - pk) / P;
-    double a = -expm1(-log1p(x) / g);
-    double gsq = (p - pk) * a / rho;
-    double dg = (a + (p - pk) * pow(1.0 + x, -1.0 / g - 1.0) / (g * P)) / rho;
-    f = sqrt(gsq);
-    df = dg / (2.0 * f);
-  } else if (p > pk) {
-    double A = 2.0 / ((g + 1.0) * rho);
-    double B = (g - 1.0) / (g + 1.0) * P;
-    double qr = sqrt(A / (Pp + B));
-    f = (p - pk) * qr;
-    df = qr * (1.0 - 0.5 * (p - pk) / (Pp + B));
-  } else {
-    double r = Pp / P;
-    f = 2.0 * ck / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
-    df = 1.0 / (rho * ck) * pow(r, -(g + 1.0) / (2.0 * g));
-  }
-}
+// each side's wave function and derivative: the library's form with the
+// quantities that do not depend on p taken once per problem and powers of
+// the positive pressure ratio as exp2(e log2 r), one per side and iteration
+// (sif_internal.cuh: side_const, riemann_side_k, riemann_star_density)
 
-__device__ inline double star_rho3(double p, double rho, double pk, double g, double pi,
-                                   int baro) {
-  double r = (p + pi) / (pk + pi);
-  if (p > pk && !baro) {
-    double qq = (g - 1.0) / (g + 1.0);
-    return rho * (r + qq) / (qq * r + 1.0);
-  }
-  return rho * pow(r, 1.0 / g);
-}
-
-__global__ void k3_interface(Grid3 g, Planes3 w0, Planes3 w1, const double *phi,
+__global__ void k3_interface(Grid3 g, Region R, Planes3 w0, Planes3 w1, const double *phi,
                              const double *sx, const double *sy, const double *sz, Planes3 xn,
                              Planes3 xp, Planes3 ul, Scal3 *sc) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double s0 = 0.0, s1 = 0.0;
-  if (t < n) {
-    int i, j, kk;
-    cell_ijk(g, (int)t, i, j, kk);
+  int i, j, kk;
+  if (region_cell(g, R, t, i, j, kk)) {
     int c = g3(g, i, j, kk);
     double S[3] = {sx[c], sy[c], sz[c]};
     bool cut = S[0] != 0.0 || S[1] != 0.0 || S[2] != 0.0;
@@ -646,10 +709,12 @@ __global__ void k3_interface(Grid3 g, Planes3 w0, Planes3 w1, const double *phi,
       if (p < pfloor) p = pfloor + 0.5 * (fmax(pl - 0.0, pr) - pfloor);
       int it = 0, conv = 0, done = 0;
       double fl, dfl, fr, dfr;
+      const SideConst sl = side_const(rl, pl, gl, pil, cl, bl);
+      const SideConst sr = side_const(rr, pr, gr, pir, cr, br);
       while (it < 50) {
         it++;
-        side3(p + 0.0, rl, pl, gl, pil, cl, bl, fl, dfl);
-        side3(p, rr, pr, gr, pir, cr, br, fr, dfr);
+        riemann_side_k(p, sl, fl, dfl);
+        riemann_side_k(p, sr, fr, dfr);
         double F = fl + fr + (ur_ - ul_);
         double pn = p - F / (dfl + dfr);
         if (pn < pfloor) pn = pfloor + 0.5 * (p - pfloor);
@@ -662,11 +727,11 @@ __global__ void k3_interface(Grid3 g, Planes3 w0, Planes3 w1, const double *phi,
         if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
       }
       if (!(done || conv)) atomicOr(&sc->err, S3_ERR_NOCONV);
-      side3(p, rl, pl, gl, pil, cl, bl, fl, dfl);
-      side3(p, rr, pr, gr, pir, cr, br, fr, dfr);
+      riemann_side_k(p, sl, fl, dfl);
+      riemann_side_k(p, sr, fr, dfr);
       double us = 0.5 * (ul_ + ur_) + 0.5 * (fr - fl);
-      double rsl = star_rho3(p, rl, pl, gl, pil, bl);
-      double rsr = star_rho3(p, rr, pr, gr, pir, br);
+      double rsl = riemann_star_density(p, rl, pl, gl, pil, bl);
+      double rsr = riemann_star_density(p, rr, pr, gr, pir, br);
       double csl = sqrt(gl * (p + pil) / rsl), csr = sqrt(gr * (p + pir) / rsr);
       for (int d = 0; d < 3; d++) {
         xn.p[d][c] = -p * S[d];
@@ -680,15 +745,13 @@ __global__ void k3_interface(Grid3 g, Planes3 w0, Planes3 w1, const double *phi,
       s1 = (fabs(us) + csr) * fac;
     }
   }
-  s0 = warp_max3(s0);
-  s1 = warp_max3(s1);
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_d(&sc->smax[0], s0);
-    atomic_max_d(&sc->smax[1], s1);
-  }
+  double v[2] = {s0, s1};
+  unsigned long long *const dst[2] = {&sc->smax[0], &sc->smax[1]};
+  block_max_atomic<2>(v, dst);
 }
 
-void k3_launch_interface(const Grid3 &g, double *const w[2][S3_NC], const double *phi,
+void k3_launch_interface(const Grid3 &g, const Region &R, double *const w[2][S3_NC],
+                         const double *phi,
                          const double *sx, const double *sy, const double *sz,
                          double *const xn[4], double *const xp[4], double *const ul[3],
                          Scal3 *sc, cudaStream_t st) {
@@ -702,8 +765,9 @@ void k3_launch_interface(const Grid3 &g, double *const w[2][S3_NC], const double
     XP.p[m] = xp[m];
   }
   for (int d = 0; d < 3; d++) UL.p[d] = ul[d];
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_interface<<<nblk(n, 128), 128, 0, st>>>(g, W0, W1, phi, sx, sy, sz, XN, XP, UL, sc);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_interface<<<nblk(n, 128), 128, 0, st>>>(g, R, W0, W1, phi, sx, sy, sz, XN, XP, UL, sc);
   tick();
 }
 
@@ -714,13 +778,11 @@ void k3_launch_interface(const Grid3 &g, double *const w[2][S3_NC], const double
 // them), what its neighbourhood's sources move in and out -- the serial
 // in-place order, so the sums round alike
 
-__global__ void k3_mix_plan(Grid3 g, int k, Planes3 q, const double *alpha, const double *phi,
+__global__ void k3_mix_plan(Grid3 g, Region R, int k, Planes3 q, const double *alpha, const double *phi,
                             int *srcmap, Mix3 *plan, int *count, int cap, int *err) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   double as = volk(alpha, k, c);
   if (as >= g.mix_alpha) return;
@@ -805,15 +867,20 @@ __global__ void k3_mix_plan(Grid3 g, int k, Planes3 q, const double *alpha, cons
     for (int m = 0; m < S3_NC; m++)
       P.M[q7][m] = beta * (q.p[m][tc] * as - q.p[m][c] * at) / den;
   }
+  P.cell = c;
   srcmap[c] = slot;
 }
 
-__global__ void k3_mix_apply(Grid3 g, Planes3 q, const int *srcmap, const Mix3 *plan) {
-  long long n = (long long)g.nx * g.ny * g.nz;
+// restores srcmap to -1 at the sources the plan marked
+__global__ void k3_mix_unmark(int *srcmap, const Mix3 *plan, const int *count, int cap) {
+  int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot < min(*count, cap)) srcmap[plan[slot].cell] = -1;
+}
+
+__global__ void k3_mix_apply(Grid3 g, Region R, Planes3 q, const int *srcmap, const Mix3 *plan) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   int sz = g.PX * g.PY;
   bool any = false;
@@ -845,18 +912,21 @@ __global__ void k3_mix_apply(Grid3 g, Planes3 q, const int *srcmap, const Mix3 *
   for (int m = 0; m < S3_NC; m++) q.p[m][c] = v[m];
 }
 
-void k3_launch_mix(const Grid3 &g, int k, double *const q[S3_NC], const double *alpha,
-                   const double *phi, int *srcmap, Mix3 *plan, int *count, int cap, int *err,
-                   cudaStream_t st) {
+void k3_launch_mix(const Grid3 &g, const Region &R, int k, double *const q[S3_NC],
+                   const double *alpha, const double *phi, int *srcmap, Mix3 *plan, int *count,
+                   int cap, int *err, cudaStream_t st) {
+  // srcmap holds -1 everywhere between calls (set at creation, restored
+  // by k3_mix_unmark)
   Planes3 Q{};
   for (int m = 0; m < S3_NC; m++) Q.p[m] = q[m];
-  cudaMemsetAsync(srcmap, 0xff, sizeof(int) * (size_t)g.NP, st);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
   cudaMemsetAsync(count, 0, sizeof(int), st);
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_mix_plan<<<nblk(n, 128), 128, 0, st>>>(g, k, Q, alpha, phi, srcmap, plan, count, cap,
+  k3_mix_plan<<<nblk(n, 128), 128, 0, st>>>(g, R, k, Q, alpha, phi, srcmap, plan, count, cap,
                                             err);
-  k3_mix_apply<<<nblk(n, 256), 256, 0, st>>>(g, Q, srcmap, plan);
-  tick(2);
+  k3_mix_apply<<<nblk(n, 256), 256, 0, st>>>(g, R, Q, srcmap, plan);
+  k3_mix_unmark<<<nblk(cap, 256), 256, 0, st>>>(srcmap, plan, count, cap);
+  tick(3);
 }
 
 // ---------------------------------------------------------------------
@@ -929,13 +999,11 @@ __device__ inline double hj3(const double *p, int c, int s, double h, bool bw, d
   return weno5_3(v[0], v[1], v[2], v[3], v[4], eps);
 }
 
-__global__ void k3_ls_rhs(Grid3 g, const double *phi, Planes3 ul, const unsigned char *band,
+__global__ void k3_ls_rhs(Grid3 g, Region R, const double *phi, Planes3 ul, const unsigned char *band,
                           double *L) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   if (!band[c]) {
     L[c] = 0.0;
@@ -951,23 +1019,22 @@ __global__ void k3_ls_rhs(Grid3 g, const double *phi, Planes3 ul, const unsigned
   L[c] = -r;
 }
 
-void k3_launch_ls_rhs(const Grid3 &g, const double *phi, double *const ul[3],
+void k3_launch_ls_rhs(const Grid3 &g, const Region &R, const double *phi, double *const ul[3],
                       const unsigned char *band, double *lphi, cudaStream_t st) {
   Planes3 U{};
   for (int d = 0; d < 3; d++) U.p[d] = ul[d];
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_ls_rhs<<<nblk(n, 128), 128, 0, st>>>(g, phi, U, band, lphi);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_ls_rhs<<<nblk(n, 128), 128, 0, st>>>(g, R, phi, U, band, lphi);
   tick();
 }
 
 // dst = dst + dt L (stage 1) or base/2 + (dst + dt L)/2 (stage 2) where mask
-__global__ void k3_rk(Grid3 g, int stage, double *dst, const double *base, const double *L,
+__global__ void k3_rk(Grid3 g, Region R, int stage, double *dst, const double *base, const double *L,
                       double dt, const unsigned char *mask) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   if (mask && !mask[c]) return;
   if (stage == 1)
@@ -976,10 +1043,11 @@ __global__ void k3_rk(Grid3 g, int stage, double *dst, const double *base, const
     dst[c] = 0.5 * base[c] + 0.5 * (dst[c] + dt * L[c]);
 }
 
-void k3_launch_rk(const Grid3 &g, int stage, double *dst, const double *base,
+void k3_launch_rk(const Grid3 &g, const Region &R, int stage, double *dst, const double *base,
                   const double *L, double dt, const unsigned char *mask, cudaStream_t st) {
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_rk<<<nblk(n, 256), 256, 0, st>>>(g, stage, dst, base, L, dt, mask);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_rk<<<nblk(n, 256), 256, 0, st>>>(g, R, stage, dst, base, L, dt, mask);
   tick();
 }
 
@@ -992,13 +1060,11 @@ __device__ inline double grad_est3(const double *p, int c, int s, double h) {
 // one reinitialisation sweep over the band and its face neighbours: the
 // subcell fix where phi0 changes sign across a face, Godunov's Hamiltonian
 // with one-sided HJ-WENO5 derivatives elsewhere, no new extremum
-__global__ void k3_reinit(Grid3 g, double *phi, const double *q, const double *z,
+__global__ void k3_reinit(Grid3 g, Region R, double *phi, const double *q, const double *z,
                           const unsigned char *rext) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   if (!rext[c]) return;
   const int st[3] = {1, g.PX, g.PX * g.PY};
@@ -1062,10 +1128,11 @@ __global__ void k3_reinit(Grid3 g, double *phi, const double *q, const double *z
   }
 }
 
-void k3_launch_reinit(const Grid3 &g, double *phi, const double *old, const double *p0,
-                      const unsigned char *rext, cudaStream_t st) {
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_reinit<<<nblk(n, 128), 128, 0, st>>>(g, phi, old, p0, rext);
+void k3_launch_reinit(const Grid3 &g, const Region &R, double *phi, const double *old,
+                      const double *p0, const unsigned char *rext, cudaStream_t st) {
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_reinit<<<nblk(n, 128), 128, 0, st>>>(g, R, phi, old, p0, rext);
   tick();
 }
 
@@ -1073,13 +1140,11 @@ void k3_launch_reinit(const Grid3 &g, double *phi, const double *old, const doub
 // the accelerated cycle's pieces: Eq. 8-9 records, Eq. 7 interpolation,
 // the final correction, and the volume integrals
 
-__global__ void k3_record(Grid3 g, int shared, Planes3 x1, Planes3 xc, double dt1,
+__global__ void k3_record(Grid3 g, Region R, int shared, Planes3 x1, Planes3 xc, double dt1,
                           double dt2) {
-  long long n = (long long)g.nx * g.ny * g.nz;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   for (int m = 0; m < 4; m++) {
     double x = x1.p[m][c];
@@ -1089,38 +1154,39 @@ __global__ void k3_record(Grid3 g, int shared, Planes3 x1, Planes3 xc, double dt
   }
 }
 
-void k3_launch_record(const Grid3 &g, int shared, double *const x1[4], double *const xc[4],
-                      double dt1, double dt2, cudaStream_t st) {
+void k3_launch_record(const Grid3 &g, const Region &R, int shared, double *const x1[4],
+                      double *const xc[4], double dt1, double dt2, cudaStream_t st) {
   Planes3 X{}, C{};
   for (int m = 0; m < 4; m++) {
     X.p[m] = x1[m];
     C.p[m] = xc[m];
   }
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_record<<<nblk(n, 256), 256, 0, st>>>(g, shared, X, C, dt1, dt2);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_record<<<nblk(n, 256), 256, 0, st>>>(g, R, shared, X, C, dt1, dt2);
   tick();
 }
 
-__global__ void k3_interp(Grid3 g, Planes3 qi, Planes3 prev, Planes3 fut, double th) {
-  long long n = (long long)g.nx * g.ny * g.nz;
+__global__ void k3_interp(Grid3 g, Region R, Planes3 qi, Planes3 prev, Planes3 fut, double th) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
   int i, j, kk;
-  cell_ijk(g, (int)t, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
   int c = g3(g, i, j, kk);
   for (int m = 0; m < S3_NC; m++) qi.p[m][c] = (1.0 - th) * prev.p[m][c] + th * fut.p[m][c];
 }
 
-void k3_launch_interp(const Grid3 &g, double *const qi[S3_NC], double *const prev[S3_NC],
-                      double *const fut[S3_NC], double th, cudaStream_t st) {
+void k3_launch_interp(const Grid3 &g, const Region &R, double *const qi[S3_NC],
+                      double *const prev[S3_NC], double *const fut[S3_NC], double th,
+                      cudaStream_t st) {
   Planes3 A{}, B{}, C{};
   for (int m = 0; m < S3_NC; m++) {
     A.p[m] = qi[m];
     B.p[m] = prev[m];
     C.p[m] = fut[m];
   }
-  long long n = (long long)g.nx * g.ny * g.nz;
-  k3_interp<<<nblk(n, 256), 256, 0, st>>>(g, A, B, C, th);
+  long long n = region_threads(g, R);
+  if (n == 0) return;
+  k3_interp<<<nblk(n, 256), 256, 0, st>>>(g, R, A, B, C, th);
   tick();
 }
 

@@ -38,7 +38,7 @@ struct Scal3 {
   unsigned long long lf[2][3];
   unsigned long long smax[2];
   int err;
-  int pad;
+  int nband;  // bricks in the band list
   unsigned long long cells, open;  // finite-volume stage updates
   unsigned long long launches;
 };
@@ -46,6 +46,43 @@ struct Scal3 {
 #define S3_ERR_NONPHYS 1
 #define S3_ERR_NOCONV 2
 #define S3_ERR_CAP 4  // a band list outgrew its capacity
+
+// where a kernel works: the whole grid (list == nullptr; one thread per
+// cell) or the cells of the listed bricks (count bricks of S3_BX x S3_BY x
+// S3_BZ cells, 256 threads each).  The band list holds every brick with a
+// cell within band + 3 cells of the interface, rebuilt after each
+// interaction step: everything the next stage changes near the interface
+// (level set, geometry, exchange fluxes, extension targets, small cells)
+// lies in it, and outside it those fields keep their values.
+struct Region {
+  const int *list;
+  int count;
+};
+
+__device__ inline bool region_cell(const Grid3 &g, const Region &R, long long t, int &i, int &j,
+                                   int &k) {
+  if (!R.list) {
+    if (t >= (long long)g.nx * g.ny * g.nz) return false;
+    int tt = (int)t;
+    i = tt % g.nx;
+    int r = tt / g.nx;
+    j = r % g.ny;
+    k = r / g.ny;
+    return true;
+  }
+  long long b = t >> 8;
+  if (b >= R.count) return false;
+  int bi = R.list[b], l = (int)(t & 255);
+  int nbx = (g.nx + S3_BX - 1) / S3_BX, nby = (g.ny + S3_BY - 1) / S3_BY;
+  i = (bi % nbx) * S3_BX + l % S3_BX;
+  j = ((bi / nbx) % nby) * S3_BY + (l / S3_BX) % S3_BY;
+  k = (bi / (nbx * nby)) * S3_BZ + l / (S3_BX * S3_BY);
+  return i < g.nx && j < g.ny && k < g.nz;
+}
+
+inline long long region_threads(const Grid3 &g, const Region &R) {
+  return R.list ? (long long)R.count * 256 : (long long)g.nx * g.ny * g.nz;
+}
 
 // an extension target: its upwind neighbours (cells), their target slots
 // (-1: not a target, value read from the plane) and weights; den = 0 marks
@@ -58,6 +95,7 @@ struct Ext3 {
 
 // a small-cell mixing source: its targets and the amounts moved from each
 struct Mix3 {
+  int cell;
   int nt;
   int tc[7];
   double M[7][S3_NC];
@@ -91,45 +129,50 @@ struct Fv3Args {
   const double *x[4];  // exchange flux as applied to fluid k
 };
 
-// host launch wrappers (each launch adds to the context's counter)
+// host launch wrappers (each launch adds to the launch counter); R is the
+// region a kernel works on
 void k3_launch_ghost(const Grid3 &g, const Planes3 &s, cudaStream_t st);
-void k3_launch_geometry(const Grid3 &g, const double *phi, double *alpha, double *ax,
-                        double *ay, double *az, double *sx, double *sy, double *sz,
-                        cudaStream_t st);
+void k3_launch_geometry(const Grid3 &g, const Region &R, const double *phi, double *corner,
+                        double *alpha, double *ax, double *ay, double *az, double *sx,
+                        double *sy, double *sz, cudaStream_t st);
+void k3_launch_band_bricks(const Grid3 &g, int nbricks, const double *phi, int *list, Scal3 *sc,
+                           cudaStream_t st);
 void k3_launch_init_state(const Grid3 &g, const double *alpha, const double *prim_dense,
                           double *const q[S3_NC], double *const w[S3_NC], int k,
                           cudaStream_t st);
-void k3_launch_prim(const Grid3 &g, double *const q[2][S3_NC], double *const w[2][S3_NC],
-                    const double *alpha, unsigned char *nostate, Scal3 *sc, cudaStream_t st);
-int k3_ext_plan(const Grid3 &g, int fields, const double *phi, const double *alpha,
-                const unsigned char *nostate, const double *sx, const double *sy,
-                const double *sz, int *map, Ext3 *plan, int *count, int cap, int *err,
-                cudaStream_t st);
+void k3_launch_prim(const Grid3 &g, const Region &R, int k, double *const q[S3_NC],
+                    double *const w[S3_NC], const double *alpha, unsigned char *nostate,
+                    Scal3 *sc, cudaStream_t st);
+int k3_ext_plan(const Grid3 &g, const Region &R, int group, const double *phi,
+                const double *alpha, const unsigned char *nostate, const double *sx,
+                const double *sy, const double *sz, int *map, Ext3 *plan, int *count, int cap,
+                int *err, cudaStream_t st);
 void k3_launch_ext_sweeps(const Grid3 &g, int group, int iters, const Ext3 *plan,
                           const int *count, int cap, double *const planes[], int nf,
-                          double *bufA, double *bufB, cudaStream_t st);
-void k3_launch_wave_maxima(const Grid3 &g, double *const w[2][S3_NC], const double *alpha,
-                           const unsigned char *nostate, const double *phi, Scal3 *sc,
-                           cudaStream_t st);
-void k3_launch_interface(const Grid3 &g, double *const w[2][S3_NC], const double *phi,
-                         const double *sx, const double *sy, const double *sz,
-                         double *const xn[4], double *const xp[4], double *const ul[3],
-                         Scal3 *sc, cudaStream_t st);
-void k3_launch_mix(const Grid3 &g, int k, double *const q[S3_NC], const double *alpha,
-                   const double *phi, int *srcmap, Mix3 *plan, int *count, int cap, int *err,
-                   cudaStream_t st);
+                          double *bufA, double *bufB, int *map, cudaStream_t st);
+void k3_launch_wave_maxima(const Grid3 &g, const Region &R, int k, double *const w[S3_NC],
+                           const double *alpha, const unsigned char *nostate, const double *phi,
+                           Scal3 *sc, cudaStream_t st);
+void k3_launch_interface(const Grid3 &g, const Region &R, double *const w[2][S3_NC],
+                         const double *phi, const double *sx, const double *sy,
+                         const double *sz, double *const xn[4], double *const xp[4],
+                         double *const ul[3], Scal3 *sc, cudaStream_t st);
+void k3_launch_mix(const Grid3 &g, const Region &R, int k, double *const q[S3_NC],
+                   const double *alpha, const double *phi, int *srcmap, Mix3 *plan, int *count,
+                   int cap, int *err, cudaStream_t st);
 void k3_launch_band(const Grid3 &g, const double *phi, unsigned char *band,
                     unsigned char *rext, cudaStream_t st);
-void k3_launch_ls_rhs(const Grid3 &g, const double *phi, double *const ul[3],
+void k3_launch_ls_rhs(const Grid3 &g, const Region &R, const double *phi, double *const ul[3],
                       const unsigned char *band, double *lphi, cudaStream_t st);
-void k3_launch_rk(const Grid3 &g, int stage, double *dst, const double *base,
+void k3_launch_rk(const Grid3 &g, const Region &R, int stage, double *dst, const double *base,
                   const double *L, double dt, const unsigned char *mask, cudaStream_t st);
-void k3_launch_reinit(const Grid3 &g, double *phi, const double *old, const double *p0,
-                      const unsigned char *rext, cudaStream_t st);
-void k3_launch_record(const Grid3 &g, int shared, double *const x1[4], double *const xc[4],
-                      double dt1, double dt2, cudaStream_t st);
-void k3_launch_interp(const Grid3 &g, double *const qi[S3_NC], double *const prev[S3_NC],
-                      double *const fut[S3_NC], double th, cudaStream_t st);
+void k3_launch_reinit(const Grid3 &g, const Region &R, double *phi, const double *old,
+                      const double *p0, const unsigned char *rext, cudaStream_t st);
+void k3_launch_record(const Grid3 &g, const Region &R, int shared, double *const x1[4],
+                      double *const xc[4], double dt1, double dt2, cudaStream_t st);
+void k3_launch_interp(const Grid3 &g, const Region &R, double *const qi[S3_NC],
+                      double *const prev[S3_NC], double *const fut[S3_NC], double th,
+                      cudaStream_t st);
 void k3_launch_correction(const Grid3 &g, double *const q[S3_NC], double *const xc[4],
                           double dv, cudaStream_t st);
 void k3_launch_integrals(const Grid3 &g, double *const q[2][S3_NC], double *partial,
