@@ -30,7 +30,7 @@ struct sif3_ctx {
   double *partial;   // integrals: 10 x nz
   double *extA, *extB;
   unsigned char *bandmask, *rext, *nostate, *touched;
-  int *extmap, *srcmap, *counts, *blist;
+  int *extmap, *srcmap, *counts, *blist, *cutlist;
   Region band{nullptr, 0};  // the band list of the last interaction step
   const Region whole{nullptr, 0};
   Ext3 *ext;
@@ -120,6 +120,7 @@ static void carve(sif3_ctx *c, Carver &cv) {
   c->srcmap = cv.take<int>(NP);
   c->counts = cv.take<int>(8);
   c->blist = cv.take<int>((size_t)c->nbricks);
+  c->cutlist = cv.take<int>((size_t)c->ext_cap);
   c->ext = cv.take<Ext3>((size_t)3 * c->ext_cap);
   c->mix = cv.take<Mix3>((size_t)c->mix_cap);
   c->sc = cv.take<Scal3>(1);
@@ -319,8 +320,8 @@ static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_o
   for (int k = 0; k < 2; k++)
     if (k != band_only)
       k3_launch_wave_maxima(g, c->whole, k, c->w[k], c->alpha, c->nostate, phi, c->sc, c->st);
-  k3_launch_interface(g, c->band, c->w, phi, c->sx, c->sy, c->sz, c->xn, c->xp, c->ul, c->sc,
-                      c->st);
+  k3_launch_interface(g, c->band, c->w, phi, c->sx, c->sy, c->sz, c->xn, c->xp, c->ul,
+                      c->cutlist, c->counts + 4, c->ext_cap, c->sc, c->st);
   k3_ext_plan(g, c->band, 2, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
               c->counts, c->ext_cap, &c->sc->err, c->st);
   k3_launch_ext_sweeps(g, 2, c->cfg.ext_iters, c->ext, c->counts, c->ext_cap, c->ul, 3,

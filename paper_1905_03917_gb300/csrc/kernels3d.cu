@@ -465,11 +465,8 @@ __global__ void k3_ext_mark(Grid3 g, Region R, int group, const double *phi, con
   plan[(size_t)grp * cap + slot].cell = c;
 }
 
-__global__ void k3_ext_setup(Grid3 g, int group, const double *phi, const int *map,
-                             Ext3 *plan, const int *count, int cap) {
-  int grp = group < 2 ? blockIdx.y : 2;
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= min(count[grp], cap)) return;
+__device__ inline void ext_setup_one(const Grid3 &g, int grp, const double *phi,
+                                     const int *map, Ext3 *plan, int cap, int slot) {
   Ext3 &e = plan[(size_t)grp * cap + slot];
   int c = e.cell;
   int r = c, i = r % g.PX - S3_GH;
@@ -496,6 +493,19 @@ __global__ void k3_ext_setup(Grid3 g, int group, const double *phi, const int *m
     e.slot[d] = e.w[d] > 0.0 ? map[(size_t)grp * g.NP + e.nb[d]] : -1;
 }
 
+// the list kernels run a bounded grid over the slots (the lists' lengths
+// are known on the device only)
+#define S3_LIST_BLOCKS (152 * 4)
+
+__global__ void k3_ext_setup(Grid3 g, int group, const double *phi, const int *map,
+                             Ext3 *plan, const int *count, int cap) {
+  int grp = group < 2 ? blockIdx.y : 2;
+  int n = min(count[grp], cap);
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += gridDim.x * blockDim.x)
+    ext_setup_one(g, grp, phi, map, plan, cap, slot);
+}
+
 int k3_ext_plan(const Grid3 &g, const Region &R, int group, const double *phi,
                 const double *alpha, const unsigned char *nostate, const double *sx,
                 const double *sy, const double *sz, int *map, Ext3 *plan, int *count, int cap,
@@ -509,7 +519,8 @@ int k3_ext_plan(const Grid3 &g, const Region &R, int group, const double *phi,
     k3_ext_mark<<<dim3(nblk(n, 256), groups), 256, 0, st>>>(g, R, group, phi, alpha, nostate,
                                                             sx, sy, sz, map, plan, count, cap,
                                                             err);
-  k3_ext_setup<<<dim3(nblk(cap, 128), groups), 128, 0, st>>>(g, group, phi, map, plan, count,
+  k3_ext_setup<<<dim3(std::min(nblk(cap, 128), S3_LIST_BLOCKS), groups), 128, 0, st>>>(
+      g, group, phi, map, plan, count,
                                                               cap);
   tick(2);
   return 0;
@@ -527,8 +538,9 @@ __global__ void k3_ext_sweep(Grid3 g, int group, int nf, ExtBufs B, const Ext3 *
                              const int *count, int cap, int first, int last, int iters,
                              int *map) {
   int grp = group < 2 ? blockIdx.y : 2;
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= min(count[grp], cap)) return;
+  int n = min(count[grp], cap);
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += gridDim.x * blockDim.x) {
   const Ext3 &e = plan[(size_t)grp * cap + slot];
   const double *rd = B.a + (size_t)grp * S3_NC * cap;
   double *wr = B.b + (size_t)grp * S3_NC * cap;
@@ -553,6 +565,7 @@ __global__ void k3_ext_sweep(Grid3 g, int group, int nf, ExtBufs B, const Ext3 *
       wr[(size_t)m * cap + slot] = val;
   }
   if (last) map[(size_t)grp * g.NP + e.cell] = -1;
+  }
 }
 
 void k3_launch_ext_sweeps(const Grid3 &g, int group, int iters, const Ext3 *plan,
@@ -563,7 +576,7 @@ void k3_launch_ext_sweeps(const Grid3 &g, int group, int iters, const Ext3 *plan
   int groups = group < 2 ? 2 : 1;
   for (int gr = 0; gr < groups; gr++)
     for (int m = 0; m < nf; m++) B.src[group < 2 ? gr : 2][m] = planes[gr * S3_NC + m];
-  dim3 grid(nblk(cap, 128), groups);
+  dim3 grid(std::min(nblk(cap, 128), S3_LIST_BLOCKS), groups);
   // sweep s reads the previous sweep's values (A) and writes B; the first
   // reads the planes, the last writes the planes (no sweep reads the planes'
   // targets after they changed: the last sweep's reads come from A)
@@ -676,22 +689,41 @@ void k3_launch_wave_maxima(const Grid3 &g, const Region &R, int k, double *const
 // the positive pressure ratio as exp2(e log2 r), one per side and iteration
 // (sif_internal.cuh: side_const, riemann_side_k, riemann_star_density)
 
-__global__ void k3_interface(Grid3 g, Region R, Planes3 w0, Planes3 w1, const double *phi,
-                             const double *sx, const double *sy, const double *sz, Planes3 xn,
-                             Planes3 xp, Planes3 ul, Scal3 *sc) {
+// the cut cells (S != 0) of the region into a dense list, the exchange
+// flux and interface velocity cleared everywhere in it: the Riemann
+// problems then run on full warps (FP64 issue is the cost of a warp
+// instruction, however few of its lanes hold a cut cell)
+__global__ void k3_cut_list(Grid3 g, Region R, const double *sx, const double *sy,
+                            const double *sz, Planes3 xn, Planes3 xp, Planes3 ul, int *list,
+                            int *count, int cap, int *err) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
   int i, j, kk;
-  if (region_cell(g, R, t, i, j, kk)) {
-    int c = g3(g, i, j, kk);
+  if (!region_cell(g, R, t, i, j, kk)) return;
+  int c = g3(g, i, j, kk);
+  for (int m = 0; m < 4; m++) {
+    xn.p[m][c] = 0.0;
+    xp.p[m][c] = 0.0;
+  }
+  for (int d = 0; d < 3; d++) ul.p[d][c] = 0.0;
+  if (sx[c] == 0.0 && sy[c] == 0.0 && sz[c] == 0.0) return;
+  int slot = atomicAdd(count, 1);
+  if (slot >= cap) {
+    atomicOr(err, S3_ERR_CAP);
+    return;
+  }
+  list[slot] = c;
+}
+
+__global__ void k3_interface(Grid3 g, const int *list, const int *count, int cap, Planes3 w0,
+                             Planes3 w1, const double *phi, const double *sx, const double *sy,
+                             const double *sz, Planes3 xn, Planes3 xp, Planes3 ul, Scal3 *sc) {
+  double s0 = 0.0, s1 = 0.0;
+  const int ncut = min(*count, cap);
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < ncut;
+       slot += gridDim.x * blockDim.x) {
+    int c = list[slot];
     double S[3] = {sx[c], sy[c], sz[c]};
-    bool cut = S[0] != 0.0 || S[1] != 0.0 || S[2] != 0.0;
-    for (int m = 0; m < 4; m++) {
-      xn.p[m][c] = 0.0;
-      xp.p[m][c] = 0.0;
-    }
-    for (int d = 0; d < 3; d++) ul.p[d][c] = 0.0;
-    if (cut) {
+    {
       double Sm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
       double nv[3];
       normal3(g, phi, c, nv);
@@ -741,8 +773,8 @@ __global__ void k3_interface(Grid3 g, Region R, Planes3 w0, Planes3 w1, const do
       xn.p[3][c] = -p * us * Sm;
       xp.p[3][c] = p * us * Sm;
       double fac = 1.0 / g.dx + 1.0 / g.dy + 1.0 / g.dz;
-      s0 = (fabs(us) + csl) * fac;
-      s1 = (fabs(us) + csr) * fac;
+      s0 = fmax(s0, (fabs(us) + csl) * fac);
+      s1 = fmax(s1, (fabs(us) + csr) * fac);
     }
   }
   double v[2] = {s0, s1};
@@ -751,10 +783,10 @@ __global__ void k3_interface(Grid3 g, Region R, Planes3 w0, Planes3 w1, const do
 }
 
 void k3_launch_interface(const Grid3 &g, const Region &R, double *const w[2][S3_NC],
-                         const double *phi,
-                         const double *sx, const double *sy, const double *sz,
-                         double *const xn[4], double *const xp[4], double *const ul[3],
-                         Scal3 *sc, cudaStream_t st) {
+                         const double *phi, const double *sx, const double *sy,
+                         const double *sz, double *const xn[4], double *const xp[4],
+                         double *const ul[3], int *cutlist, int *cutcount, int cap, Scal3 *sc,
+                         cudaStream_t st) {
   Planes3 W0{}, W1{}, XN{}, XP{}, UL{};
   for (int m = 0; m < S3_NC; m++) {
     W0.p[m] = w[0][m];
@@ -767,8 +799,14 @@ void k3_launch_interface(const Grid3 &g, const Region &R, double *const w[2][S3_
   for (int d = 0; d < 3; d++) UL.p[d] = ul[d];
   long long n = region_threads(g, R);
   if (n == 0) return;
-  k3_interface<<<nblk(n, 128), 128, 0, st>>>(g, R, W0, W1, phi, sx, sy, sz, XN, XP, UL, sc);
-  tick();
+  cudaMemsetAsync(cutcount, 0, sizeof(int), st);
+  k3_cut_list<<<nblk(n, 256), 256, 0, st>>>(g, R, sx, sy, sz, XN, XP, UL, cutlist, cutcount, cap,
+                                            &sc->err);
+  // one warp per block: consecutive cut cells fill a warp, warps spread
+  // over the SMs
+  k3_interface<<<std::min(nblk(cap, 32), 4 * S3_LIST_BLOCKS), 32, 0, st>>>(
+      g, cutlist, cutcount, cap, W0, W1, phi, sx, sy, sz, XN, XP, UL, sc);
+  tick(2);
 }
 
 // ---------------------------------------------------------------------
@@ -873,8 +911,10 @@ __global__ void k3_mix_plan(Grid3 g, Region R, int k, Planes3 q, const double *a
 
 // restores srcmap to -1 at the sources the plan marked
 __global__ void k3_mix_unmark(int *srcmap, const Mix3 *plan, const int *count, int cap) {
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot < min(*count, cap)) srcmap[plan[slot].cell] = -1;
+  int n = min(*count, cap);
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += gridDim.x * blockDim.x)
+    srcmap[plan[slot].cell] = -1;
 }
 
 __global__ void k3_mix_apply(Grid3 g, Region R, Planes3 q, const int *srcmap, const Mix3 *plan) {
@@ -925,7 +965,8 @@ void k3_launch_mix(const Grid3 &g, const Region &R, int k, double *const q[S3_NC
   k3_mix_plan<<<nblk(n, 128), 128, 0, st>>>(g, R, k, Q, alpha, phi, srcmap, plan, count, cap,
                                             err);
   k3_mix_apply<<<nblk(n, 256), 256, 0, st>>>(g, R, Q, srcmap, plan);
-  k3_mix_unmark<<<nblk(cap, 256), 256, 0, st>>>(srcmap, plan, count, cap);
+  k3_mix_unmark<<<std::min(nblk(cap, 256), S3_LIST_BLOCKS), 256, 0, st>>>(srcmap, plan, count,
+                                                                           cap);
   tick(3);
 }
 
@@ -1197,6 +1238,9 @@ __global__ void k3_correction(Grid3 g, Planes3 q, Planes3 xc, double dv) {
   int i, j, kk;
   cell_ijk(g, (int)t, i, j, kk);
   int c = g3(g, i, j, kk);
+  // cells with nothing recorded (all but those an evaluation found cut)
+  // would add 0 / dv
+  if (xc.p[0][c] == 0.0 && xc.p[1][c] == 0.0 && xc.p[2][c] == 0.0 && xc.p[3][c] == 0.0) return;
   for (int m = 0; m < 4; m++) q.p[m + 1][c] += xc.p[m][c] / dv;
 }
 

@@ -156,7 +156,8 @@ void k3_launch_wave_maxima(const Grid3 &g, const Region &R, int k, double *const
 void k3_launch_interface(const Grid3 &g, const Region &R, double *const w[2][S3_NC],
                          const double *phi, const double *sx, const double *sy,
                          const double *sz, double *const xn[4], double *const xp[4],
-                         double *const ul[3], Scal3 *sc, cudaStream_t st);
+                         double *const ul[3], int *cutlist, int *cutcount, int cap, Scal3 *sc,
+                         cudaStream_t st);
 void k3_launch_mix(const Grid3 &g, const Region &R, int k, double *const q[S3_NC],
                    const double *alpha, const double *phi, int *srcmap, Mix3 *plan, int *count,
                    int cap, int *err, cudaStream_t st);
