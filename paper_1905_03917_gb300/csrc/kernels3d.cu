@@ -120,27 +120,37 @@ __device__ inline double sq_fraction(double c0, double c1, double c2, double c3)
     }
     return area;
   }
-  double X[8], Y[8];
+  // shoelace over the polygon's vertices in order, streamed (first and
+  // previous vertex kept) instead of stored: the same terms summed in the
+  // same order, the closing edge last
+  double fx = 0.0, fy = 0.0, qx = 0.0, qy = 0.0, a2 = 0.0;
   int m = 0;
   for (int e = 0; e < 4; e++) {
     int nx = (e + 1) & 3;
-    if (v[e] >= 0.0) {
-      X[m] = px[e];
-      Y[m] = py[e];
-      m++;
-    }
-    if ((v[e] >= 0.0) != (v[nx] >= 0.0)) {
-      double s = v[e] / (v[e] - v[nx]);
-      X[m] = px[e] + s * (px[nx] - px[e]);
-      Y[m] = py[e] + s * (py[nx] - py[e]);
+    for (int part = 0; part < 2; part++) {
+      double x, y;
+      if (part == 0) {
+        if (!(v[e] >= 0.0)) continue;
+        x = px[e];
+        y = py[e];
+      } else {
+        if ((v[e] >= 0.0) == (v[nx] >= 0.0)) continue;
+        double s = v[e] / (v[e] - v[nx]);
+        x = px[e] + s * (px[nx] - px[e]);
+        y = py[e] + s * (py[nx] - py[e]);
+      }
+      if (m == 0) {
+        fx = x;
+        fy = y;
+      } else {
+        a2 += qx * y - x * qy;
+      }
+      qx = x;
+      qy = y;
       m++;
     }
   }
-  double a2 = 0.0;
-  for (int q = 0; q < m; q++) {
-    int q1 = q + 1 == m ? 0 : q + 1;
-    a2 += X[q] * Y[q1] - X[q1] * Y[q];
-  }
+  a2 += qx * fy - fx * qy;
   return 0.5 * a2;
 }
 
@@ -816,8 +826,10 @@ void k3_launch_interface(const Grid3 &g, const Region &R, double *const w[2][S3_
 // them), what its neighbourhood's sources move in and out -- the serial
 // in-place order, so the sums round alike
 
-__global__ void k3_mix_plan(Grid3 g, Region R, int k, Planes3 q, const double *alpha, const double *phi,
-                            int *srcmap, Mix3 *plan, int *count, int cap, int *err) {
+// the sources of the region into a dense list (the plan's slots), so that
+// the plan's FP64 work runs on full warps
+__global__ void k3_mix_sources(Grid3 g, Region R, int k, Planes3 q, const double *alpha,
+                               Mix3 *plan, int *count, int cap, int *err) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int i, j, kk;
   if (!region_cell(g, R, t, i, j, kk)) return;
@@ -827,6 +839,22 @@ __global__ void k3_mix_plan(Grid3 g, Region R, int k, Planes3 q, const double *a
   bool empty = as == 0.0;
   for (int m = 0; m < S3_NC; m++) empty = empty && q.p[m][c] == 0.0;
   if (empty) return;
+  int slot = atomicAdd(count, 1);
+  if (slot >= cap) {
+    atomicOr(err, S3_ERR_CAP);
+    return;
+  }
+  plan[slot].cell = c;
+}
+
+__device__ void mix_plan_one(const Grid3 &g, int k, const Planes3 &q, const double *alpha,
+                             const double *phi, int *srcmap, Mix3 *plan, int slot) {
+  Mix3 &P = plan[slot];
+  const int c = P.cell;
+  int r = c, i = r % g.PX - S3_GH;
+  r /= g.PX;
+  int j = r % g.PY - S3_GH, kk = r / g.PY - S3_GH;
+  double as = volk(alpha, k, c);
   double nv[3];
   normal3(g, phi, c, nv);
   if (k == 0)
@@ -877,13 +905,10 @@ __global__ void k3_mix_plan(Grid3 g, Region R, int k, Planes3 q, const double *a
       }
     }
   }
-  if (single < 0 && !(sum > 0.0)) return;
-  int slot = atomicAdd(count, 1);
-  if (slot >= cap) {
-    atomicOr(err, S3_ERR_CAP);
+  if (single < 0 && !(sum > 0.0)) {
+    P.nt = 0;  // no target: nothing moves
     return;
   }
-  Mix3 &P = plan[slot];
   int nt = 0;
   for (int q7 = 0; q7 < 7 && single < 0; q7++) {
     if (!(keep >> q7 & 1)) continue;
@@ -905,8 +930,15 @@ __global__ void k3_mix_plan(Grid3 g, Region R, int k, Planes3 q, const double *a
     for (int m = 0; m < S3_NC; m++)
       P.M[q7][m] = beta * (q.p[m][tc] * as - q.p[m][c] * at) / den;
   }
-  P.cell = c;
   srcmap[c] = slot;
+}
+
+__global__ void k3_mix_plan(Grid3 g, int k, Planes3 q, const double *alpha, const double *phi,
+                            int *srcmap, Mix3 *plan, const int *count, int cap) {
+  int n = min(*count, cap);
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += gridDim.x * blockDim.x)
+    mix_plan_one(g, k, q, alpha, phi, srcmap, plan, slot);
 }
 
 // restores srcmap to -1 at the sources the plan marked
@@ -962,12 +994,15 @@ void k3_launch_mix(const Grid3 &g, const Region &R, int k, double *const q[S3_NC
   long long n = region_threads(g, R);
   if (n == 0) return;
   cudaMemsetAsync(count, 0, sizeof(int), st);
-  k3_mix_plan<<<nblk(n, 128), 128, 0, st>>>(g, R, k, Q, alpha, phi, srcmap, plan, count, cap,
-                                            err);
+  k3_mix_sources<<<nblk(n, 256), 256, 0, st>>>(g, R, k, Q, alpha, plan, count, cap, err);
+  // one warp per block, as for the interface problems
+  k3_mix_plan<<<std::min(nblk(cap, 32), 4 * S3_LIST_BLOCKS), 32, 0, st>>>(g, k, Q, alpha, phi,
+                                                                          srcmap, plan, count,
+                                                                          cap);
   k3_mix_apply<<<nblk(n, 256), 256, 0, st>>>(g, R, Q, srcmap, plan);
   k3_mix_unmark<<<std::min(nblk(cap, 256), S3_LIST_BLOCKS), 256, 0, st>>>(srcmap, plan, count,
                                                                            cap);
-  tick(3);
+  tick(4);
 }
 
 // ---------------------------------------------------------------------
