@@ -77,7 +77,7 @@ class _Config3(ctypes.Structure):
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("tait", ctypes.c_int * 2),
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
-                ("tait_p0", ctypes.c_double * 2)]
+                ("tait_p0", ctypes.c_double * 2), ("sigma", ctypes.c_double)]
 
 
 _lib_handle = None
@@ -141,6 +141,8 @@ def lib():
         L.orc3_geometry.argtypes = [P, dp, dp, dp, dp, dp, dp, dp]
         L.orc3_cell_alpha.restype = D
         L.orc3_cell_alpha.argtypes = [dp, dp]
+        L.orc3_curvature.restype = D
+        L.orc3_curvature.argtypes = [P, I, I, I]
         L.orc3_time.restype = D
         L.orc3_time.argtypes = [P]
         L.orc3_status.argtypes = [P]
@@ -365,6 +367,7 @@ def make_config3(cfg: dict) -> _Config3:
         if t is not None:
             c.tait[k] = 1
             c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
+    c.sigma = float(cfg.get("sigma", 0.0))
     return c
 
 
@@ -430,6 +433,9 @@ class Oracle3:
         lib().orc3_geometry(self._h, *(_ptr(a) for a in arrs))
         names = ("alpha", "ax", "ay", "az", "sx", "sy", "sz")
         return {k: a.reshape(self.shape) for k, a in zip(names, arrs)}
+
+    def curvature(self, i, j, k):
+        return lib().orc3_curvature(self._h, int(i), int(j), int(k))
 
     @property
     def t(self):

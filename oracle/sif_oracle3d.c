@@ -20,6 +20,9 @@
  *       patch taken as planar through the mean xi_m of its edge crossings
  *       (exact for a planar interface, equal to the 2D polygon area for a
  *       level set that does not vary along z);
+ *   surface tension -- Eq. 10's jump sigma kappa with kappa the mean
+ *       curvature div(grad phi / |grad phi|) by central differences, as in
+ *       2D with the third axis's terms;
  *   mixing targets -- the seven neighbours toward the fluid along n_k (x, y,
  *       z, the three face diagonals and the cube diagonal) with weights
  *       n_x^2, n_y^2, n_z^2, |n_x n_y|, |n_x n_z|, |n_y n_z|, |n_x n_y
@@ -441,10 +444,39 @@ static void wave_maxima(orc3_ctx *o, int kf, const double *p) {
 /* ------------------------------------------------------------------ */
 /* interface interaction: the two-material Riemann problem along n      */
 
-/* For every cut cell (S != 0): fluid N receives momentum -p_I S and energy
- * -p_I u_I |S|, fluid P the opposite, no mass; the level-set velocity of
- * the cell is u_I n; the star states' speeds enter each fluid's CFL rate as
- * (|u_I| + c*_k)(1/dx + 1/dy + 1/dz). */
+/* mean curvature of the level set, kappa = div(grad phi / |grad phi|), by
+ * second-order central differences: (sum over the axes a of phi_aa times
+ * the squared gradient across a, minus twice the sum over axis pairs of
+ * phi_a phi_b phi_ab) / |grad phi|^3; 2 / r for phi = r - R */
+static double curvature3(const orc3_ctx *o, const double *p, int i, int j, int k) {
+  const double h[3] = {o->c.dx, o->c.dy, o->c.dz};
+  const int st[3] = {1, o->PX, o->PX * o->PY};
+  int c = ID(o, i, j, k);
+  double g[3], gg[3][3];
+  for (int a = 0; a < 3; a++) {
+    g[a] = (p[c + st[a]] - p[c - st[a]]) / (2.0 * h[a]);
+    gg[a][a] = (p[c + st[a]] - 2.0 * p[c] + p[c - st[a]]) / (h[a] * h[a]);
+  }
+  for (int a = 0; a < 3; a++)
+    for (int b = a + 1; b < 3; b++) {
+      int sa = st[a], sb = st[b];
+      gg[a][b] = (p[c + sa + sb] - p[c + sa - sb] - p[c - sa + sb] + p[c - sa - sb]) /
+                 (4.0 * h[a] * h[b]);
+    }
+  double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  if (!(g2 > 0.0)) return 0.0;
+  double num = gg[0][0] * (g[1] * g[1] + g[2] * g[2]) + gg[1][1] * (g[0] * g[0] + g[2] * g[2]) +
+               gg[2][2] * (g[0] * g[0] + g[1] * g[1]) -
+               2.0 * (g[0] * g[1] * gg[0][1] + g[0] * g[2] * gg[0][2] + g[1] * g[2] * gg[1][2]);
+  return num / (g2 * sqrt(g2));
+}
+
+/* For every cut cell (S != 0): fluid N receives momentum -p_I,N S and
+ * energy -p_I,N u_I |S|, fluid P momentum p_I,P S and energy p_I,P u_I |S|,
+ * no mass; with surface tension the pressure jumps by sigma kappa from
+ * fluid P into fluid N (Eq. 10), kappa > 0 where fluid N is convex; the
+ * level-set velocity of the cell is u_I n; the star states' speeds enter
+ * each fluid's CFL rate as (|u_I| + c*_k)(1/dx + 1/dy + 1/dz). */
 static void interface(orc3_ctx *o, const double *p) {
   for (int m = 0; m < 4; m++) memset(o->xn[m], 0, sizeof(double) * o->NP);
   for (int m = 0; m < 4; m++) memset(o->xp[m], 0, sizeof(double) * o->NP);
@@ -467,7 +499,8 @@ static void interface(orc3_ctx *o, const double *p) {
         double L[5] = {o->w[0][0][c], un[0], o->w[0][4][c], o->c.gamma[0], o->c.pinf[0]};
         double R[5] = {o->w[1][0][c], un[1], o->w[1][4][c], o->c.gamma[1], o->c.pinf[1]};
         double out[8];
-        if (orc_riemann_jump2(L, R, 0.0, o->c.tait[0], o->c.tait[1], out))
+        double jump = o->c.sigma != 0.0 ? o->c.sigma * curvature3(o, p, i, j, k) : 0.0;
+        if (orc_riemann_jump2(L, R, jump, o->c.tait[0], o->c.tait[1], out))
           o->err |= ORC_ERR_NOCONV;
         double psN = out[7], psP = out[0], us = out[1];
         for (int d = 0; d < 3; d++) {
@@ -993,6 +1026,7 @@ static double *plane(orc3_ctx *o) { return (double *)calloc((size_t)o->NP, sizeo
 orc3_ctx *orc3_create(const orc3_config *cfg) {
   if (cfg->nx < GH || cfg->ny < GH || cfg->nz < GH) return NULL;
   if (!(cfg->dx > 0.0) || !(cfg->dy > 0.0) || !(cfg->dz > 0.0)) return NULL;
+  if (!(cfg->sigma >= 0.0) || !isfinite(cfg->sigma)) return NULL;
   for (int k = 0; k < 2; k++) {
     if (cfg->tait[k] != 0 && cfg->tait[k] != 1) return NULL;
     if (cfg->tait[k] && (!(cfg->tait_B[k] > 0.0) || !(cfg->tait_rho0[k] > 0.0) ||
@@ -1123,6 +1157,11 @@ int orc3_geometry(orc3_ctx *o, double *alpha, double *ax, double *ay, double *az
   if (sy) copy_out(o, o->sy, sy);
   if (sz) copy_out(o, o->sz, sz);
   return 0;
+}
+
+double orc3_curvature(orc3_ctx *o, int i, int j, int k) {
+  fill_ghost(o, o->phi, 0);
+  return curvature3(o, o->phi, i, j, k);
 }
 
 double orc3_time(const orc3_ctx *o) { return o->t; }

@@ -8,9 +8,10 @@
  * the two-dimensional oracle's pointwise routines (WENO5, the two-material
  * Riemann problem, the square's area fraction), which are pinned there.
  *
- * Scope: inviscid stiffened-gas or Tait fluids (Eq. 1, 4), component-wise
- * WENO5 on Lax-Friedrichs split fluxes, TVD-RK2, the single-time-step step
- * and the accelerated cycle of Sec. 3.1 (Eq. 7-9).
+ * Scope: inviscid stiffened-gas or Tait fluids (Eq. 1, 4) with or without
+ * surface tension (Eq. 10), component-wise WENO5 on Lax-Friedrichs split
+ * fluxes, TVD-RK2, the single-time-step step and the accelerated cycle of
+ * Sec. 3.1 (Eq. 7-9).
  */
 #ifndef SIF_ORACLE3D_H
 #define SIF_ORACLE3D_H
@@ -38,6 +39,7 @@ typedef struct {
   int force_ratio_one;
   int tait[2];        /* Tait's equation for fluid k (Eq. 4) */
   double tait_B[2], tait_rho0[2], tait_p0[2];
+  double sigma;       /* surface tension coefficient (Eq. 10); 0 = none */
 } orc3_config;
 
 typedef struct orc3_ctx orc3_ctx;
@@ -63,6 +65,9 @@ int orc3_geometry(orc3_ctx *o, double *alpha, double *ax, double *ay, double *az
  * corner values c[i + 2 j + 4 k] (i, j, k in {0, 1} along x, y, z);
  * s[3] in unit-face areas; returns alpha_P */
 double orc3_cell_alpha(const double *c, double *s);
+/* curvature div(grad phi / |grad phi|) of the current level set at cell
+ * (i, j, k), second-order central differences */
+double orc3_curvature(orc3_ctx *o, int i, int j, int k);
 double orc3_time(const orc3_ctx *o);
 int orc3_status(const orc3_ctx *o);
 

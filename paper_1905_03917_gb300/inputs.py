@@ -548,3 +548,22 @@ def extrude(case, nz):
 
     return {"name": case["name"] + f"_z{nz}", "cfg": cfg, "phi": rep(case["phi"]),
             "prim_N": prim(case["prim_N"]), "prim_P": prim(case["prim_P"])}
+
+
+def static_drop_3d(n=24, sigma=36.0, radius=0.25, equilibrium=True):
+    """Sec. 4.3's static drop as a sphere: a gas drop (gamma 1.4, rho 10;
+    fluid N) of radius 0.25 at the centre of the unit cube in air (gamma
+    1.4, rho 1), both at rest at p0 = 1e3, surface tension sigma, so that
+    the pressure jump tends to 2 sigma / R (Laplace's law for a sphere);
+    equilibrium=True starts the drop at p0 + 2 sigma / R.  Reflective
+    walls."""
+    d = 1.0 / n
+    p0 = 1.0e3
+    gas = {"gamma": 1.4, "pinf": 0.0}
+    cfg = config3(n, n, n, d, gas, AIR, ["reflect"] * 6, sigma=sigma)
+    X, Y, Z = _centres3(cfg)
+    phi = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) - radius
+    pN = _uniform3(X.shape, 10.0, 0.0, 0.0, 0.0,
+                   p0 + (2.0 * sigma / radius if equilibrium else 0.0))
+    pP = _uniform3(X.shape, 1.0, 0.0, 0.0, 0.0, p0)
+    return {"name": f"static_drop_3d_{n}", "cfg": cfg, "phi": phi, "prim_N": pN, "prim_P": pP}

@@ -297,3 +297,86 @@ def test_uniform_flow_keeps_each_fluids_mean_velocity():
     for f in range(2):
         assert abs(it[f, 1] / it[f, 0] / u0 - 1.0) < 1e-4
         assert np.abs(it[f, 2:4]).max() <= 1e-14 * abs(it[f, 1])
+
+
+# -- surface tension (Eq. 10) in 3D: Laplace's law for a sphere ---------------
+
+def _sphere_curvature_error(n):
+    c = I.static_drop_3d(n)
+    o = O.Oracle3(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    g = o.geometry()
+    X, Y, Z = I._centres3(c["cfg"])
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    cut = (g["sx"] != 0) | (g["sy"] != 0) | (g["sz"] != 0)
+    err = max(abs(o.curvature(i, j, k) - 2.0 / r[k, j, i]) for k, j, i in zip(*np.nonzero(cut)))
+    return err * 0.25 / 2.0  # relative to 2 / R
+
+
+def test_curvature_of_spheres_converges_second_order():
+    # phi = r - R: every level set is a sphere, of mean curvature 2 / r
+    e16, e32 = _sphere_curvature_error(16), _sphere_curvature_error(32)
+    assert e32 < 5e-3 and np.log2(e16 / e32) >= 1.8, (e16, e32)
+
+
+def test_curvature_of_a_cylinder_is_the_2d_curvature():
+    c2 = I.static_drop(32, liquid=False)
+    c3 = I.extrude(c2, 4)
+    c3["cfg"]["sigma"] = c2["cfg"]["sigma"]
+    o2 = O.Oracle(c2["cfg"]).init(c2["phi"], c2["prim_N"], c2["prim_P"])
+    o3 = O.Oracle3(c3["cfg"]).init(c3["phi"], c3["prim_N"], c3["prim_P"])
+    for i, j in ((12, 16), (16, 12), (13, 13), (19, 20)):
+        assert o3.curvature(i, j, 2) == pytest.approx(o2.curvature(i, j), rel=1e-12, abs=1e-12)
+
+
+def test_curvature_of_a_plane_is_zero():
+    cfg = I.config3(12, 12, 12, 1.0 / 12, I.AIR, I.HELIUM, ["reflect"] * 6, sigma=1.0)
+    X, Y, Z = I._centres3(cfg)
+    phi = 0.3 * X - 0.5 * Y + 0.81 * Z - 0.4
+    prim = I._uniform3(phi.shape, 1.0, 0.0, 0.0, 0.0, 1.0)
+    o = O.Oracle3(cfg).init(phi, prim, prim)
+    assert max(abs(o.curvature(i, j, k)) for i in range(1, 11) for j in range(1, 11)
+               for k in range(1, 11)) <= 1e-9
+
+
+def _laplace_jump_3d(n, steps, sigma=36.0, equilibrium=True, multi=False):
+    c = I.static_drop_3d(n, sigma=sigma, equilibrium=equilibrium)
+    o = O.Oracle3(c["cfg"]).init(c["phi"], c["prim_N"], c["prim_P"])
+    X, Y, Z = I._centres3(c["cfg"])
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    d = 1.0 / n
+    I0 = o.integrals()
+    hist = []
+    for s in range(steps):
+        (o.step_multi_dt if multi else o.step_single_dt)(1)
+        if s % 10 == 9:
+            qN, qP, _ = o.state()
+            a = o.geometry()["alpha"]
+            inn, out = (r < 0.25 - 2 * d) & (a < 1e-3), (r > 0.25 + 2 * d) & (a > 0.999)
+
+            def pres(q, al, m):
+                rho = q[0][m] / al[m]
+                u, v, w = (q[x][m] / q[0][m] for x in (1, 2, 3))
+                return (0.4 * (q[4][m] / al[m] - 0.5 * rho * (u * u + v * v + w * w))).mean()
+            hist.append(pres(qN, 1 - a, inn) - pres(qP, a, out))
+    assert o.status == 0
+    return np.array(hist), I0, o
+
+
+def test_static_sphere_keeps_the_laplace_jump():
+    """A gas sphere started in Laplace equilibrium (p inside = p outside +
+    2 sigma / R = 288 above it) keeps the jump: within 2 % over 60 steps on
+    24^3 (6 cells a radius), closer than on 16^3."""
+    h16, _, _ = _laplace_jump_3d(16, 60)
+    h24, _, _ = _laplace_jump_3d(24, 60)
+    e16, e24 = np.abs(h16 / 288.0 - 1.0).max(), np.abs(h24 / 288.0 - 1.0).max()
+    assert e24 <= 0.02 and e24 < e16, (e16, e24)
+
+
+def test_no_jump_without_surface_tension_and_masses_kept():
+    h, _, _ = _laplace_jump_3d(16, 30, sigma=0.0, equilibrium=False)
+    assert np.abs(h).max() <= 0.05 * 288.0, h
+    # the accelerated cycle with surface tension keeps each fluid's mass
+    _, I0, o = _laplace_jump_3d(16, 10, multi=True)
+    I1 = o.integrals()
+    for k in range(2):
+        assert abs(I1[k, 0] - I0[k, 0]) <= 1e-13 * I0[k, 0]
