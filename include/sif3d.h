@@ -18,10 +18,10 @@
  * fluid (x, y, z, the face and cube diagonals) weighted n_x^2, n_y^2,
  * n_z^2, |n_x n_y|, |n_x n_z|, |n_y n_z|, |n_x n_y n_z|^(2/3).
  *
- * Scope: stiffened-gas or Tait fluids (Eq. 1, 4), component-wise WENO5 on
- * Lax-Friedrichs split fluxes, TVD-RK2.  The options of the 2D solver
- * (characteristic WENO5, HLLC, surface tension, viscosity, RK3, adjoint)
- * are not available in 3D.
+ * Scope: stiffened-gas or Tait fluids (Eq. 1, 4) with or without surface
+ * tension (Eq. 10), component-wise WENO5 on Lax-Friedrichs split fluxes,
+ * TVD-RK2.  The other options of the 2D solver (characteristic WENO5,
+ * HLLC, viscosity, RK3, adjoint) are not available in 3D.
  *
  * Conventions are those of sif.h: 0 or a negative SIF_E* code, the reason
  * from sif3_last_error(); arrays are caller-owned and copied; mem_kind is
@@ -62,6 +62,11 @@ typedef struct {
   double tait_B[2], tait_rho0[2], tait_p0[2];
   void *cuda_stream;     /* cudaStream_t for all work; NULL = a private blocking stream */
   int device;            /* CUDA device ordinal */
+  double sigma;          /* surface tension coefficient (Eq. 10), >= 0; 0 = none.  The
+                            interface Riemann problem carries the jump p_N - p_P =
+                            sigma kappa, kappa = div(grad phi / |grad phi|) by central
+                            differences (2 / r for a sphere), and each fluid receives
+                            the exchange flux of its own interface pressure */
 } sif3_config;
 
 /* Create a context; allocates its device memory (about 110 planes of

@@ -140,6 +140,7 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
     return SIF_EINVAL;
   if (f.ext_iters < 0 || f.reinit_iters < 0 || !(f.band > 0) || !(f.mix_alpha > 0))
     return SIF_EINVAL;
+  if (!(f.sigma >= 0.0) || !std::isfinite(f.sigma)) return SIF_EINVAL;
   for (int s = 0; s < 6; s++)
     if (!bc_ok(f.bc[s])) return SIF_EINVAL;
   for (int d = 0; d < 3; d++)
@@ -169,6 +170,7 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
   }
   g.eps = f.weno_eps;
   g.mix_alpha = f.mix_alpha;
+  g.sigma = f.sigma;
   int n = f.nx * f.ny * f.nz;
   c->ext_cap = std::min(n, std::max(1 << 18, n / 4));
   c->mix_cap = std::min(n, std::max(1 << 16, n / 16));

@@ -699,6 +699,36 @@ void k3_launch_wave_maxima(const Grid3 &g, const Region &R, int k, double *const
 // the positive pressure ratio as exp2(e log2 r), one per side and iteration
 // (sif_internal.cuh: side_const, riemann_side_k, riemann_star_density)
 
+// mean curvature div(grad phi / |grad phi|) by second-order central
+// differences: (sum over axes a of phi_aa times the squared gradient across
+// a, minus twice the sum over axis pairs of phi_a phi_b phi_ab) / |grad
+// phi|^3 (2 / r for a sphere, positive where fluid N is convex)
+__device__ inline double curvature3(const Grid3 &g, const double *p, int c) {
+  const double h[3] = {g.dx, g.dy, g.dz};
+  const int st[3] = {1, g.PX, g.PX * g.PY};
+  double gd[3], gg[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    gd[a] = (p[c + st[a]] - p[c - st[a]]) / (2.0 * h[a]);
+    gg[a][a] = (p[c + st[a]] - 2.0 * p[c] + p[c - st[a]]) / (h[a] * h[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = a + 1; b < 3; b++) {
+      int sa = st[a], sb = st[b];
+      gg[a][b] = (p[c + sa + sb] - p[c + sa - sb] - p[c - sa + sb] + p[c - sa - sb]) /
+                 (4.0 * h[a] * h[b]);
+    }
+  double g2 = gd[0] * gd[0] + gd[1] * gd[1] + gd[2] * gd[2];
+  if (!(g2 > 0.0)) return 0.0;
+  double num = gg[0][0] * (gd[1] * gd[1] + gd[2] * gd[2]) +
+               gg[1][1] * (gd[0] * gd[0] + gd[2] * gd[2]) +
+               gg[2][2] * (gd[0] * gd[0] + gd[1] * gd[1]) -
+               2.0 * (gd[0] * gd[1] * gg[0][1] + gd[0] * gd[2] * gg[0][2] + gd[1] * gd[2] * gg[1][2]);
+  return num / (g2 * sqrt(g2));
+}
+
 // the cut cells (S != 0) of the region into a dense list, the exchange
 // flux and interface velocity cleared everywhere in it: the Riemann
 // problems then run on full warps (FP64 issue is the cost of a warp
@@ -744,18 +774,20 @@ __global__ void k3_interface(Grid3 g, const int *list, const int *count, int cap
       double ul_ = w0.p[1][c] * nv[0] + w0.p[2][c] * nv[1] + w0.p[3][c] * nv[2];
       double ur_ = w1.p[1][c] * nv[0] + w1.p[2][c] * nv[1] + w1.p[3][c] * nv[2];
       int bl = g.tait[0], br = g.tait[1];
+      // Eq. 10: the N-side pressure exceeds the P side's by sigma kappa
+      const double jump = g.sigma != 0.0 ? g.sigma * curvature3(g, phi, c) : 0.0;
       double cl = sqrt(gl * (pl + pil) / rl), cr = sqrt(gr * (pr + pir) / rr);
       double pscale = fmin(pl + pil, pr + pir);
-      double pfloor = fmax(-pir, -pil - 0.0) + 1e-12 * pscale;
-      double p = 0.5 * ((pl - 0.0) + pr) - 0.125 * (ur_ - ul_) * (rl + rr) * (cl + cr);
-      if (p < pfloor) p = pfloor + 0.5 * (fmax(pl - 0.0, pr) - pfloor);
+      double pfloor = fmax(-pir, -pil - jump) + 1e-12 * pscale;
+      double p = 0.5 * ((pl - jump) + pr) - 0.125 * (ur_ - ul_) * (rl + rr) * (cl + cr);
+      if (p < pfloor) p = pfloor + 0.5 * (fmax(pl - jump, pr) - pfloor);
       int it = 0, conv = 0, done = 0;
       double fl, dfl, fr, dfr;
       const SideConst sl = side_const(rl, pl, gl, pil, cl, bl);
       const SideConst sr = side_const(rr, pr, gr, pir, cr, br);
       while (it < 50) {
         it++;
-        riemann_side_k(p, sl, fl, dfl);
+        riemann_side_k(p + jump, sl, fl, dfl);
         riemann_side_k(p, sr, fr, dfr);
         double F = fl + fr + (ur_ - ul_);
         double pn = p - F / (dfl + dfr);
@@ -769,18 +801,20 @@ __global__ void k3_interface(Grid3 g, const int *list, const int *count, int cap
         if (dp <= 1e-10 * (fabs(p) + pscale)) conv = 1;
       }
       if (!(done || conv)) atomicOr(&sc->err, S3_ERR_NOCONV);
-      riemann_side_k(p, sl, fl, dfl);
+      const double plst = p + jump;
+      riemann_side_k(plst, sl, fl, dfl);
       riemann_side_k(p, sr, fr, dfr);
       double us = 0.5 * (ul_ + ur_) + 0.5 * (fr - fl);
-      double rsl = riemann_star_density(p, rl, pl, gl, pil, bl);
+      double rsl = riemann_star_density(plst, rl, pl, gl, pil, bl);
       double rsr = riemann_star_density(p, rr, pr, gr, pir, br);
-      double csl = sqrt(gl * (p + pil) / rsl), csr = sqrt(gr * (p + pir) / rsr);
+      double csl = sqrt(gl * (plst + pil) / rsl), csr = sqrt(gr * (p + pir) / rsr);
+      // each fluid receives the exchange flux of its own interface pressure
       for (int d = 0; d < 3; d++) {
-        xn.p[d][c] = -p * S[d];
+        xn.p[d][c] = -plst * S[d];
         xp.p[d][c] = p * S[d];
         ul.p[d][c] = us * nv[d];
       }
-      xn.p[3][c] = -p * us * Sm;
+      xn.p[3][c] = -plst * us * Sm;
       xp.p[3][c] = p * us * Sm;
       double fac = 1.0 / g.dx + 1.0 / g.dy + 1.0 / g.dz;
       s0 = fmax(s0, (fabs(us) + csl) * fac);

@@ -25,6 +25,7 @@ struct Grid3 {
   int tait[2];
   double tB[2], tr0[2], tp0[2];
   double eps, mix_alpha;
+  double sigma;  // surface tension coefficient (Eq. 10), 0 = none
 };
 
 __host__ __device__ inline int g3(const Grid3 &g, int i, int j, int k) {

@@ -77,7 +77,8 @@ class Config3(ctypes.Structure):
                 ("tait", ctypes.c_int * 2),
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
                 ("tait_p0", ctypes.c_double * 2),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("sigma", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -538,6 +539,7 @@ def make_config3(cfg: dict, stream=None, device=0) -> Config3:
             c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
     c.cuda_stream = stream
     c.device = int(device)
+    c.sigma = float(cfg.get("sigma", 0.0))
     return c
 
 
