@@ -77,7 +77,8 @@ class _Config3(ctypes.Structure):
                 ("flux_correction", ctypes.c_int), ("force_ratio_one", ctypes.c_int),
                 ("tait", ctypes.c_int * 2),
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
-                ("tait_p0", ctypes.c_double * 2), ("sigma", ctypes.c_double)]
+                ("tait_p0", ctypes.c_double * 2), ("sigma", ctypes.c_double),
+                ("mu", ctypes.c_double * 2)]
 
 
 _lib_handle = None
@@ -368,6 +369,8 @@ def make_config3(cfg: dict) -> _Config3:
             c.tait[k] = 1
             c.tait_B[k], c.tait_rho0[k], c.tait_p0[k] = (float(x) for x in t)
     c.sigma = float(cfg.get("sigma", 0.0))
+    mu = cfg.get("mu", (0.0, 0.0))
+    c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
     return c
 
 

@@ -23,6 +23,8 @@
  *   surface tension -- Eq. 10's jump sigma kappa with kappa the mean
  *       curvature div(grad phi / |grad phi|) by central differences, as in
  *       2D with the third axis's terms;
+ *   viscosity -- the 2D oracle's face fluxes, interface traction and time
+ *       step limit with the third velocity component and direction;
  *   mixing targets -- the seven neighbours toward the fluid along n_k (x, y,
  *       z, the three face diagonals and the cube diagonal) with weights
  *       n_x^2, n_y^2, n_z^2, |n_x n_y|, |n_x n_z|, |n_y n_z|, |n_x n_y
@@ -435,6 +437,10 @@ static void wave_maxima(orc3_ctx *o, int kf, const double *p) {
           l[d] = dmax(l[d], a);
           s += a / hd[d];
         }
+        /* explicit viscous limit 2 nu (1/dx^2 + 1/dy^2 + 1/dz^2) */
+        if (real && o->c.mu[kf] > 0.0)
+          s += 2.0 * o->c.mu[kf] / rho *
+               (1.0 / (hd[0] * hd[0]) + 1.0 / (hd[1] * hd[1]) + 1.0 / (hd[2] * hd[2]));
         if (real) sm = dmax(sm, s);
       }
   for (int d = 0; d < 3; d++) o->lf[kf][d] = l[d];
@@ -471,6 +477,25 @@ static double curvature3(const orc3_ctx *o, const double *p, int i, int j, int k
   return num / (g2 * sqrt(g2));
 }
 
+/* Viscous stress (Stokes' hypothesis, no heat conduction) from the
+ * velocity gradient G[a][b] = d u_b / d x_a: tau_aa = mu (4/3 G_aa - 2/3
+ * (the other two diagonal terms)), tau_ab = mu (G_ab + G_ba). */
+static void visc_stress3(double mu, const double G[3][3], double tau[3][3]) {
+  tau[0][0] = mu * (4.0 / 3.0 * G[0][0] - 2.0 / 3.0 * G[1][1] - 2.0 / 3.0 * G[2][2]);
+  tau[1][1] = mu * (4.0 / 3.0 * G[1][1] - 2.0 / 3.0 * G[0][0] - 2.0 / 3.0 * G[2][2]);
+  tau[2][2] = mu * (4.0 / 3.0 * G[2][2] - 2.0 / 3.0 * G[0][0] - 2.0 / 3.0 * G[1][1]);
+  tau[0][1] = tau[1][0] = mu * (G[1][0] + G[0][1]);
+  tau[0][2] = tau[2][0] = mu * (G[2][0] + G[0][2]);
+  tau[1][2] = tau[2][1] = mu * (G[2][1] + G[1][2]);
+}
+
+/* velocity component b (0..2) at cell c of the field that is continuous
+ * across the interface: that of the fluid on whose side of the interface
+ * the cell's centre lies (phi < 0: N) */
+static double vel_across(const orc3_ctx *o, const double *p, int b, int c) {
+  return o->w[p[c] < 0.0 ? 0 : 1][1 + b][c];
+}
+
 /* For every cut cell (S != 0): fluid N receives momentum -p_I,N S and
  * energy -p_I,N u_I |S|, fluid P momentum p_I,P S and energy p_I,P u_I |S|,
  * no mass; with surface tension the pressure jumps by sigma kappa from
@@ -482,6 +507,12 @@ static void interface(orc3_ctx *o, const double *p) {
   for (int m = 0; m < 4; m++) memset(o->xp[m], 0, sizeof(double) * o->NP);
   for (int m = 0; m < 3; m++) memset(o->ul[m], 0, sizeof(double) * o->NP);
   double fac = 1.0 / o->c.dx + 1.0 / o->c.dy + 1.0 / o->c.dz;
+  /* the traction's central differences reach the ghost layers: the
+   * velocities of both fluids' stencil states get the boundary conditions'
+   * ghost values first */
+  if (o->c.mu[0] > 0.0 && o->c.mu[1] > 0.0)
+    for (int kf = 0; kf < 2; kf++)
+      for (int b = 0; b < 3; b++) fill_ghost(o, o->w[kf][1 + b], 1 + b);
   for (int k = 0; k < o->c.nz; k++)
     for (int j = 0; j < o->c.ny; j++)
       for (int i = 0; i < o->c.nx; i++) {
@@ -510,6 +541,31 @@ static void interface(orc3_ctx *o, const double *p) {
         }
         o->xn[3][c] = -psN * us * Sm;
         o->xp[3][c] = psP * us * Sm;
+        /* viscous traction across the interface (Eq. 5's interface term):
+         * the stress of the velocity field that is continuous across it,
+         * central differences at the cut cell, the harmonic mean of the two
+         * viscosities; fluid N receives tau S and fluid P the opposite,
+         * each with its work at that field's velocity in the cut cell */
+        if (o->c.mu[0] > 0.0 && o->c.mu[1] > 0.0) {
+          double muI = 2.0 * o->c.mu[0] * o->c.mu[1] / (o->c.mu[0] + o->c.mu[1]);
+          const int st[3] = {1, o->PX, o->PX * o->PY};
+          const double hd[3] = {o->c.dx, o->c.dy, o->c.dz};
+          double G[3][3], tau[3][3];
+          for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+              G[a][b] = (vel_across(o, p, b, c + st[a]) - vel_across(o, p, b, c - st[a])) /
+                        (2.0 * hd[a]);
+          visc_stress3(muI, G, tau);
+          double f[3], e = 0.0;
+          for (int a = 0; a < 3; a++) f[a] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
+          for (int a = 0; a < 3; a++) e += vel_across(o, p, a, c) * f[a];
+          for (int a = 0; a < 3; a++) {
+            o->xn[a][c] = o->xn[a][c] + f[a];
+            o->xp[a][c] = o->xp[a][c] - f[a];
+          }
+          o->xn[3][c] = o->xn[3][c] + e;
+          o->xp[3][c] = o->xp[3][c] - e;
+        }
         o->smax[0] = dmax(o->smax[0], (fabs(us) + out[4]) * fac);
         o->smax[1] = dmax(o->smax[1], (fabs(us) + out[5]) * fac);
       }
@@ -582,6 +638,35 @@ static void face_flux(const orc3_ctx *o, int kf, int c, int s, int d, double *Fh
   }
 }
 
+/* viscous flux through the lower d-face of cell c (stride s) from the
+ * stencil states by central differences: the normal derivatives across the
+ * face, the tangential ones the mean of the two cells' central differences */
+static void viscous_face(const orc3_ctx *o, int kf, int c, int s, int d, double *Fv) {
+  const double hd[3] = {o->c.dx, o->c.dy, o->c.dz};
+  const int st[3] = {1, o->PX, o->PX * o->PY};
+  int cl = c - s;
+  double G[3][3], tau[3][3];
+  for (int b = 0; b < 3; b++) {
+    const double *u = o->w[kf][1 + b];
+    for (int a = 0; a < 3; a++) {
+      if (a == d)
+        G[a][b] = (u[c] - u[cl]) / hd[a];
+      else
+        G[a][b] = ((u[c + st[a]] - u[c - st[a]]) + (u[cl + st[a]] - u[cl - st[a]])) /
+                  (4.0 * hd[a]);
+    }
+  }
+  visc_stress3(o->c.mu[kf], G, tau);
+  Fv[0] = 0.0;
+  double e = 0.0;
+  for (int b = 0; b < 3; b++) {
+    double uf = 0.5 * (o->w[kf][1 + b][cl] + o->w[kf][1 + b][c]);
+    Fv[1 + b] = tau[d][b];
+    e += uf * tau[d][b];
+  }
+  Fv[4] = e;
+}
+
 static double aperture(const orc3_ctx *o, int kf, int d, int c) {
   const double *A = d == 0 ? o->ax : d == 1 ? o->ay : o->az;
   return kf == 1 ? A[c] : 1.0 - A[c];
@@ -605,6 +690,11 @@ static void fv_rhs(orc3_ctx *o, int kf, double *const L[NC]) {
           if (A == 0.0) continue;
           double Fh[NC];
           face_flux(o, kf, c, st[d], d, Fh);
+          if (o->c.mu[kf] > 0.0) {
+            double Fv[NC];
+            viscous_face(o, kf, c, st[d], d, Fv);
+            for (int m = 0; m < NC; m++) Fh[m] = Fh[m] - Fv[m];
+          }
           for (int m = 0; m < NC; m++) o->fl[d][m][c] = A * Fh[m];
         }
   }
@@ -1027,6 +1117,8 @@ orc3_ctx *orc3_create(const orc3_config *cfg) {
   if (cfg->nx < GH || cfg->ny < GH || cfg->nz < GH) return NULL;
   if (!(cfg->dx > 0.0) || !(cfg->dy > 0.0) || !(cfg->dz > 0.0)) return NULL;
   if (!(cfg->sigma >= 0.0) || !isfinite(cfg->sigma)) return NULL;
+  for (int k = 0; k < 2; k++)
+    if (!(cfg->mu[k] >= 0.0) || !isfinite(cfg->mu[k])) return NULL;
   for (int k = 0; k < 2; k++) {
     if (cfg->tait[k] != 0 && cfg->tait[k] != 1) return NULL;
     if (cfg->tait[k] && (!(cfg->tait_B[k] > 0.0) || !(cfg->tait_rho0[k] > 0.0) ||

@@ -8,9 +8,9 @@
  * the two-dimensional oracle's pointwise routines (WENO5, the two-material
  * Riemann problem, the square's area fraction), which are pinned there.
  *
- * Scope: inviscid stiffened-gas or Tait fluids (Eq. 1, 4) with or without
- * surface tension (Eq. 10), component-wise WENO5 on Lax-Friedrichs split
- * fluxes, TVD-RK2, the single-time-step step and the accelerated cycle of
+ * Scope: stiffened-gas or Tait fluids (Eq. 1, 4) with or without surface
+ * tension (Eq. 10) and viscosity (Eq. 3, 5), component-wise WENO5 on
+ * Lax-Friedrichs split fluxes, TVD-RK2, the single-time-step step and the accelerated cycle of
  * Sec. 3.1 (Eq. 7-9).
  */
 #ifndef SIF_ORACLE3D_H
@@ -40,6 +40,7 @@ typedef struct {
   int tait[2];        /* Tait's equation for fluid k (Eq. 4) */
   double tait_B[2], tait_rho0[2], tait_p0[2];
   double sigma;       /* surface tension coefficient (Eq. 10); 0 = none */
+  double mu[2];       /* dynamic viscosities of fluids N and P (Eq. 3, 5); 0 = inviscid */
 } orc3_config;
 
 typedef struct orc3_ctx orc3_ctx;
