@@ -19,9 +19,9 @@
  * n_z^2, |n_x n_y|, |n_x n_z|, |n_y n_z|, |n_x n_y n_z|^(2/3).
  *
  * Scope: stiffened-gas or Tait fluids (Eq. 1, 4) with or without surface
- * tension (Eq. 10), component-wise WENO5 on Lax-Friedrichs split fluxes,
- * TVD-RK2.  The other options of the 2D solver (characteristic WENO5,
- * HLLC, viscosity, RK3, adjoint) are not available in 3D.
+ * tension (Eq. 10) and viscosity (Eq. 3, 5), component-wise WENO5 on
+ * Lax-Friedrichs split fluxes, TVD-RK2.  The other options of the 2D solver
+ * (characteristic WENO5, HLLC, RK3, adjoint) are not available in 3D.
  *
  * Conventions are those of sif.h: 0 or a negative SIF_E* code, the reason
  * from sif3_last_error(); arrays are caller-owned and copied; mem_kind is
@@ -67,6 +67,13 @@ typedef struct {
                             sigma kappa, kappa = div(grad phi / |grad phi|) by central
                             differences (2 / r for a sphere), and each fluid receives
                             the exchange flux of its own interface pressure */
+  double mu[2];          /* dynamic viscosities of fluids N and P (Eq. 3, 5), >= 0; 0 =
+                            inviscid.  Face viscous fluxes by central differences of the
+                            stencil states times the apertures; with both fluids viscous
+                            the traction of the velocity field that is continuous across
+                            the interface (harmonic-mean viscosity) joins the exchange
+                            flux; the explicit limit 2 nu (1/dx^2 + 1/dy^2 + 1/dz^2) joins
+                            the CFL rate */
 } sif3_config;
 
 /* Create a context; allocates its device memory (about 110 planes of

@@ -141,6 +141,8 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
   if (f.ext_iters < 0 || f.reinit_iters < 0 || !(f.band > 0) || !(f.mix_alpha > 0))
     return SIF_EINVAL;
   if (!(f.sigma >= 0.0) || !std::isfinite(f.sigma)) return SIF_EINVAL;
+  for (int k = 0; k < 2; k++)
+    if (!(f.mu[k] >= 0.0) || !std::isfinite(f.mu[k])) return SIF_EINVAL;
   for (int s = 0; s < 6; s++)
     if (!bc_ok(f.bc[s])) return SIF_EINVAL;
   for (int d = 0; d < 3; d++)
@@ -171,6 +173,8 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
   g.eps = f.weno_eps;
   g.mix_alpha = f.mix_alpha;
   g.sigma = f.sigma;
+  g.mu[0] = f.mu[0];
+  g.mu[1] = f.mu[1];
   int n = f.nx * f.ny * f.nz;
   c->ext_cap = std::min(n, std::max(1 << 18, n / 4));
   c->mix_cap = std::min(n, std::max(1 << 16, n / 16));
@@ -322,6 +326,17 @@ static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_o
   for (int k = 0; k < 2; k++)
     if (k != band_only)
       k3_launch_wave_maxima(g, c->whole, k, c->w[k], c->alpha, c->nostate, phi, c->sc, c->st);
+  if (g.mu[0] > 0.0 && g.mu[1] > 0.0) {
+    // the traction's central differences reach the ghost layers
+    Planes3 v{};
+    for (int k = 0; k < 2; k++)
+      for (int b = 0; b < 3; b++) {
+        v.p[3 * k + b] = c->w[k][1 + b];
+        v.vel[3 * k + b] = 1 + b;
+      }
+    v.n = 6;
+    k3_launch_ghost(g, v, c->st);
+  }
   k3_launch_interface(g, c->band, c->w, phi, c->sx, c->sy, c->sz, c->xn, c->xp, c->ul,
                       c->cutlist, c->counts + 4, c->ext_cap, c->sc, c->st);
   k3_ext_plan(g, c->band, 2, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
@@ -363,6 +378,7 @@ static void fv(sif3_ctx *c, int k, int stage, double dt, double *const dst[S3_NC
     cudaEventRecord(e0, c->st);
   }
   k3_launch_fv(c->g, a, c->sc, c->st);
+  if (c->g.mu[k] > 0.0) k3_launch_viscous(c->g, a, c->st);
   if (c->prof) {
     cudaEventRecord(e1, c->st);
     c->prof_launches++;

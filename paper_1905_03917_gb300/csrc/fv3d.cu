@@ -168,6 +168,94 @@ __global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
   }
 }
 
+// ---------------------------------------------------------------------
+// viscous face fluxes (Eq. 3, 5): through the lower d-face of cell cf
+// (between cf - s and cf) from the stencil states by central differences,
+// the normal derivatives across the face and the tangential ones as the
+// mean of the two cells' central differences; Stokes' stress
+
+__device__ inline void viscous_face3(const Grid3 &g, const Fv3Args &a, int cf, int d,
+                                     double mu, double Fv[4]) {
+  const int st[3] = {1, g.PX, g.PX * g.PY};
+  const double hd[3] = {g.dx, g.dy, g.dz};
+  const int cl = cf - st[d];
+  double G[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; b++) {
+    const double *u = a.w[1 + b];
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      if (e == d)
+        G[e][b] = (u[cf] - u[cl]) / hd[e];
+      else
+        G[e][b] = ((u[cf + st[e]] - u[cf - st[e]]) + (u[cl + st[e]] - u[cl - st[e]])) /
+                  (4.0 * hd[e]);
+    }
+  }
+  // the row d of the stress tensor
+  double t[3];
+#pragma unroll
+  for (int b = 0; b < 3; b++) {
+    // the other two diagonal terms in axis order, as in the stress tensor
+    const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+    if (b == d)
+      t[b] = mu * (4.0 / 3.0 * G[d][d] - 2.0 / 3.0 * G[o1][o1] - 2.0 / 3.0 * G[o2][o2]);
+    else
+      t[b] = mu * (G[b][d] + G[d][b]);
+  }
+  double e = 0.0;
+#pragma unroll
+  for (int b = 0; b < 3; b++) {
+    Fv[b] = t[b];
+    e += 0.5 * (a.w[1 + b][cl] + a.w[1 + b][cf]) * t[b];
+  }
+  Fv[3] = e;
+}
+
+// one thread per cell of a brick with a face open to the fluid: the
+// viscous part of Eq. 2, -sum_d (A Fv)_lower - (A Fv)_upper over h_d, b dt
+// times it added to the stage result (b = 1 at stage 1, 1/2 at stage 2)
+__global__ void __launch_bounds__(256) k3_viscous(Grid3 g, Fv3Args a) {
+  const int tid = threadIdx.x;
+  const int li = tid % S3_BX, lj = (tid / S3_BX) % S3_BY, lk = tid / (S3_BX * S3_BY);
+  const int i = blockIdx.x * S3_BX + li, j = blockIdx.y * S3_BY + lj,
+            kk = blockIdx.z * S3_BZ + lk;
+  const bool valid = i < g.nx && j < g.ny && kk < g.nz;
+  const int k = a.k, st[3] = {1, g.PX, g.PX * g.PY};
+  const double *Ad[3] = {a.ax, a.ay, a.az};
+  const double hd[3] = {g.dx, g.dy, g.dz};
+  int c = valid ? g3(g, i, j, kk) : 0;
+  int open = 0;
+  if (valid)
+    for (int d = 0; d < 3; d++)
+      open |= ap3(Ad[d], k, c) != 0.0 || ap3(Ad[d], k, c + st[d]) != 0.0;
+  if (!__syncthreads_or(open) || !valid) return;
+  const double mu = g.mu[k];
+  double r[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    double lo[4] = {0.0, 0.0, 0.0, 0.0}, hi[4] = {0.0, 0.0, 0.0, 0.0};
+    double Al = ap3(Ad[d], k, c), Ah = ap3(Ad[d], k, c + st[d]);
+    if (Al != 0.0) {
+      viscous_face3(g, a, c, d, mu, lo);
+      for (int m = 0; m < 4; m++) lo[m] = Al * lo[m];
+    }
+    if (Ah != 0.0) {
+      viscous_face3(g, a, c + st[d], d, mu, hi);
+      for (int m = 0; m < 4; m++) hi[m] = Ah * hi[m];
+    }
+    for (int m = 0; m < 4; m++) r[m] += (hi[m] - lo[m]) / hd[d];
+  }
+  const double b = a.stage == 1 ? 1.0 : 0.5;
+  for (int m = 0; m < 4; m++) a.dst[1 + m][c] += b * a.dt * r[m];
+}
+
+void k3_launch_viscous(const Grid3 &g, const Fv3Args &a, cudaStream_t st) {
+  dim3 grid((g.nx + S3_BX - 1) / S3_BX, (g.ny + S3_BY - 1) / S3_BY, (g.nz + S3_BZ - 1) / S3_BZ);
+  k3_viscous<<<grid, S3_BX * S3_BY * S3_BZ, 0, st>>>(g, a);
+  g_fv_launches++;
+}
+
 void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {

@@ -668,6 +668,10 @@ __global__ void k3_wave_maxima(Grid3 g, Region R, int k, Planes3 w, const double
       l[d] = fmax(l[d], a);
       r += a / hd[d];
     }
+    // explicit viscous limit 2 nu (1/dx^2 + 1/dy^2 + 1/dz^2)
+    if (real && g.mu[k] > 0.0)
+      r += 2.0 * g.mu[k] / rho *
+           (1.0 / (hd[0] * hd[0]) + 1.0 / (hd[1] * hd[1]) + 1.0 / (hd[2] * hd[2]));
     if (real) s = fmax(s, r);
   }
   double v[4] = {l[0], l[1], l[2], s};
@@ -816,6 +820,44 @@ __global__ void k3_interface(Grid3 g, const int *list, const int *count, int cap
       }
       xn.p[3][c] = -plst * us * Sm;
       xp.p[3][c] = p * us * Sm;
+      if (g.mu[0] > 0.0 && g.mu[1] > 0.0) {
+        // viscous traction across the interface (Eq. 5's interface term):
+        // the stress of the velocity field that is continuous across it
+        // (each cell's velocity from the fluid on its centre's side), by
+        // central differences, with the harmonic-mean viscosity; fluid N
+        // receives tau S and its work, fluid P the opposite
+        const double muI = 2.0 * g.mu[0] * g.mu[1] / (g.mu[0] + g.mu[1]);
+        const int st[3] = {1, g.PX, g.PX * g.PY};
+        const double hd[3] = {g.dx, g.dy, g.dz};
+        double G[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const int cp = c + st[a], cm = c - st[a];
+          const Planes3 &wp = phi[cp] < 0.0 ? w0 : w1, &wm = phi[cm] < 0.0 ? w0 : w1;
+#pragma unroll
+          for (int b = 0; b < 3; b++) G[a][b] = (wp.p[1 + b][cp] - wm.p[1 + b][cm]) / (2.0 * hd[a]);
+        }
+        double tau[3][3];
+        tau[0][0] = muI * (4.0 / 3.0 * G[0][0] - 2.0 / 3.0 * G[1][1] - 2.0 / 3.0 * G[2][2]);
+        tau[1][1] = muI * (4.0 / 3.0 * G[1][1] - 2.0 / 3.0 * G[0][0] - 2.0 / 3.0 * G[2][2]);
+        tau[2][2] = muI * (4.0 / 3.0 * G[2][2] - 2.0 / 3.0 * G[0][0] - 2.0 / 3.0 * G[1][1]);
+        tau[0][1] = tau[1][0] = muI * (G[1][0] + G[0][1]);
+        tau[0][2] = tau[2][0] = muI * (G[2][0] + G[0][2]);
+        tau[1][2] = tau[2][1] = muI * (G[2][1] + G[1][2]);
+        const Planes3 &wc = phi[c] < 0.0 ? w0 : w1;
+        double f[3], e = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) f[a] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
+#pragma unroll
+        for (int a = 0; a < 3; a++) e += wc.p[1 + a][c] * f[a];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          xn.p[a][c] = xn.p[a][c] + f[a];
+          xp.p[a][c] = xp.p[a][c] - f[a];
+        }
+        xn.p[3][c] = xn.p[3][c] + e;
+        xp.p[3][c] = xp.p[3][c] - e;
+      }
       double fac = 1.0 / g.dx + 1.0 / g.dy + 1.0 / g.dz;
       s0 = fmax(s0, (fabs(us) + csl) * fac);
       s1 = fmax(s1, (fabs(us) + csr) * fac);

@@ -26,6 +26,7 @@ struct Grid3 {
   double tB[2], tr0[2], tp0[2];
   double eps, mix_alpha;
   double sigma;  // surface tension coefficient (Eq. 10), 0 = none
+  double mu[2];  // dynamic viscosities (Eq. 3, 5), 0 = inviscid
 };
 
 __host__ __device__ inline int g3(const Grid3 &g, int i, int j, int k) {
@@ -182,4 +183,7 @@ void k3_launch_integrals(const Grid3 &g, double *const q[2][S3_NC], double *part
 void k3_launch_pack(const Grid3 &g, const double *padded, double *dense, int unpack,
                     cudaStream_t st);
 void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st);
+// with viscosity: the aperture-weighted divergence of the viscous face
+// fluxes of fluid k (Eq. 5), b dt times it added to the stage result dst
+void k3_launch_viscous(const Grid3 &g, const Fv3Args &a, cudaStream_t st);
 unsigned long long k3_launches();

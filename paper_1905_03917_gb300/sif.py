@@ -78,7 +78,7 @@ class Config3(ctypes.Structure):
                 ("tait_B", ctypes.c_double * 2), ("tait_rho0", ctypes.c_double * 2),
                 ("tait_p0", ctypes.c_double * 2),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("sigma", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("mu", ctypes.c_double * 2)]
 
 
 class Profile(ctypes.Structure):
@@ -540,6 +540,8 @@ def make_config3(cfg: dict, stream=None, device=0) -> Config3:
     c.cuda_stream = stream
     c.device = int(device)
     c.sigma = float(cfg.get("sigma", 0.0))
+    mu = cfg.get("mu", (0.0, 0.0))
+    c.mu[0], c.mu[1] = float(mu[0]), float(mu[1])
     return c
 
 

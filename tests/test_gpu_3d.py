@@ -237,3 +237,49 @@ def test_static_sphere_keeps_the_laplace_jump_on_gpu():
             return (0.4 * (q[4][m] / al[m] - 0.5 * rho * (u * u + v * v + w * w))).mean()
         jump = pres(qN, 1 - a, inn) - pres(qP, a, out)
         assert abs(jump / 288.0 - 1.0) <= 0.02, jump
+
+
+# -- viscosity (Eq. 3, 5) -------------------------------------------------------
+
+def viscous_bubble(n=16):
+    """The shock-bubble with both fluids viscous and a shear flow through
+    the box: face viscous fluxes in all three directions, the interface
+    traction, the viscous time-step limit."""
+    c = I.shock_bubble_3d(n // 2)
+    c["cfg"]["mu"] = [0.01, 0.005]
+    X, Y, Z = I._centres3(c["cfg"])
+    for key in ("prim_N", "prim_P"):
+        c[key][3] = 0.3 * np.sin(2.0 * np.pi * Y) * np.cos(2.0 * np.pi * X)
+    return c
+
+
+def test_viscosity_matches_oracle():
+    c = viscous_bubble(16)
+    g, o = pair(c)
+    cref = sound_scale(c)
+    for _ in range(2):
+        gi, oi = g.step_single_dt(1), o.step_single_dt(1)
+        assert gi["t"] == pytest.approx(oi["t"], rel=1e-12)
+        compare3(g.state(), o.state(), 1e-12, cref)
+    gi, oi = g.step_multi_dt(1), o.step_multi_dt(1)
+    assert gi["substeps"] == oi["substeps"]
+    compare3(g.state(), o.state(), 1e-12, cref)
+
+
+def test_shear_wave_along_z_decays_at_the_viscous_rate_on_gpu():
+    """u = a sin(2 pi z) decays as exp(-nu (2 pi)^2 t) in the CUDA path
+    (closed form)."""
+    import math
+    n, mu, amp = 32, 0.01, 0.01
+    cfg = I.config3(4, 4, n, 1.0 / n, I.AIR, I.AIR, ["periodic"] * 6, mu=[mu, mu])
+    X, Y, Z = I._centres3(cfg)
+    phi = np.ones_like(X)
+    prim = I._uniform3(X.shape, 1.0, 0.0, 0.0, 0.0, 100.0)
+    prim[1] = amp * np.sin(2.0 * math.pi * Z)
+    s = _sif().Solver3(cfg).init_fluids(phi, prim, prim.copy())
+    T = 0.5
+    s.step_single_dt(100000, t_end=T)
+    qP = s.state()[1]
+    u = qP[1] / qP[0]
+    a = 2.0 * (u[:, 0, 0] * np.sin(2.0 * math.pi * Z[:, 0, 0])).mean()
+    assert a == pytest.approx(amp * math.exp(-mu * (2.0 * math.pi) ** 2 * T), rel=2e-3)
