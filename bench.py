@@ -476,34 +476,33 @@ TABLE1_3D_T_RUN = {64: 0.05, 128: 0.02}
 FLOPS_PER_UPDATE_3D = 2240
 
 
-def paper_table1_3d(device, sizes=(64, 128)):
-    """The 3D row of Table 1 on this GPU: the translating water sphere
-    (Tait water in air, periodic unit cube) advanced by both methods over
-    the same span of time, r_s = single-step time / accelerated time; each
+def _table_3d(device, build, sizes, t_run, paper, workload):
+    """Both methods over the same span of time from the same initial data
+    on a 3D case, r_s = single-step time / accelerated time per grid; each
     timed run also reports the 3D finite-volume kernel's share of it and
     its FP64 throughput (CUDA events around every launch)."""
     import torch
-    from paper_1905_03917_gb300 import inputs, sif
+    from paper_1905_03917_gb300 import sif
     peak = NOMINAL_FP64_TFLOPS
     rows = []
     for n in sizes:
-        case = inputs.droplet_translation_3d(n)
+        case = build(n)
         arrs = [np.ascontiguousarray(case[x]) for x in ("phi", "prim_N", "prim_P")]
-        t_run = TABLE1_3D_T_RUN.get(n, 0.02)
-        rec = {"grid": f"{n}x{n}x{n}", "t": t_run,
-               "paper_speedup": PAPER_TABLE1_3D_SPEEDUP.get(n)}
+        t_end = t_run[n]
+        rec = {"grid": "x".join(str(case["cfg"][k]) for k in ("nx", "ny", "nz")), "t": t_end,
+               "paper_speedup": paper.get(n)}
         for mode in ("single", "multi"):
             s = sif.Solver3(case["cfg"], device=device).init_fluids(*arrs)
             step = s.step_multi_dt if mode == "multi" else s.step_single_dt
             count, subs = 0, []
-            while s.t < t_run:
-                subs.append(step(1, t_end=t_run)["substeps"])
+            while s.t < t_end:
+                subs.append(step(1, t_end=t_end)["substeps"])
                 count += 1
             s.init_fluids(*arrs)
             s.profile_enable(True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = step(count, t_end=t_run)
+            info = step(count, t_end=t_end)
             torch.cuda.synchronize()
             ms = 1e3 * (time.perf_counter() - t0)
             prof = s.profile_read()
@@ -524,10 +523,35 @@ def paper_table1_3d(device, sizes=(64, 128)):
             s.close()
         rec["speedup"] = rec["single_ms"] / rec["multi_ms"]
         rows.append(rec)
-    return {"workload": "droplet translation in 3D (Sec. 4.2, Table 1 3D row), Tait water "
-                        "sphere in air, periodic unit cube",
-            "runs": rows,
+    return {"workload": workload, "runs": rows,
             "timing": "host wall clock around one synchronising call of the counted steps"}
+
+
+def paper_table1_3d(device, sizes=(64, 128)):
+    """The 3D row of Table 1 on this GPU: the translating water sphere
+    (Tait water in air, periodic unit cube)."""
+    from paper_1905_03917_gb300 import inputs
+    return _table_3d(device, inputs.droplet_translation_3d, sizes, TABLE1_3D_T_RUN,
+                     PAPER_TABLE1_3D_SPEEDUP,
+                     "droplet translation in 3D (Sec. 4.2, Table 1 3D row), Tait water "
+                     "sphere in air, periodic unit cube")
+
+
+# Table 3's 3D row (Sec. 4.4: the square drop as a cube relaxing to a
+# sphere, 128^3), same i7-4790: r_s = 946140.3 s / 328314.1 s
+PAPER_TABLE3_3D_SPEEDUP = {128: 2.882}
+TABLE3_3D_T_RUN = {64: 0.004, 128: 0.002}
+
+
+def paper_table3_3d(device, sizes=(128,)):
+    """The 3D row of Table 3 on this GPU: the cubic Tait-liquid drop with
+    surface tension and viscosity relaxing toward a sphere, over a short
+    span of the relaxation."""
+    from paper_1905_03917_gb300 import inputs
+    return _table_3d(device, inputs.circle_recovery_3d, sizes, TABLE3_3D_T_RUN,
+                     PAPER_TABLE3_3D_SPEEDUP,
+                     "circle recovery in 3D (Sec. 4.4, Table 3 3D row), Tait liquid cube in a "
+                     "Tait gas-like fluid, surface tension and viscosity")
 
 
 def tube_exact_error(T):
@@ -867,6 +891,7 @@ def run_ours(args):
                         ("batched", batched),
                         ("paper_table1", lambda: paper_table1(local)),
                         ("paper_table1_3d", lambda: paper_table1_3d(local)),
+                        ("paper_table3_3d", lambda: paper_table3_3d(local)),
                         ("adjoint", lambda: adjoint_cost(local)),
                         ("adjoint_origin", lambda: adjoint_cost(local, centre=(0.0, 0.0)))):
             try:
@@ -962,8 +987,8 @@ def main():
     elif args.workload == "paper_table1_3d":
         # the 3D droplet (Table 1's 3D row) alone; --size picks one grid
         sizes = (args.size3d,) if args.size3d else (64, 128)
-        print(json.dumps({"impl": "ours", "paper_table1_3d": paper_table1_3d(0, sizes)}),
-              flush=True)
+        print(json.dumps({"impl": "ours", "paper_table1_3d": paper_table1_3d(0, sizes),
+                          "paper_table3_3d": paper_table3_3d(0)}), flush=True)
     elif args.workload == "adjoint":
         # the adjoint measurement alone (gas-water bubble at x = 0.7, n x n,
         # --steps single-dt steps, a checkpoint every --steps / 2), e.g. for

@@ -283,3 +283,18 @@ def test_shear_wave_along_z_decays_at_the_viscous_rate_on_gpu():
     u = qP[1] / qP[0]
     a = 2.0 * (u[:, 0, 0] * np.sin(2.0 * math.pi * Z[:, 0, 0])).mean()
     assert a == pytest.approx(amp * math.exp(-mu * (2.0 * math.pi) ** 2 * T), rel=2e-3)
+
+
+def test_circle_recovery_3d_matches_oracle():
+    """Table 3's 3D case (Tait fluids, surface tension, viscosity) at 32^3:
+    two single steps and one accelerated cycle against the oracle."""
+    c = I.circle_recovery_3d(32)
+    g, o = pair(c)
+    cref = sound_scale(c)
+    for _ in range(2):
+        g.step_single_dt(1)
+        o.step_single_dt(1)
+    compare3(g.state(), o.state(), 1e-12, cref)
+    gi, oi = g.step_multi_dt(1), o.step_multi_dt(1)
+    assert gi["substeps"] == oi["substeps"] and gi["role_fluid1"] == oi["role_fluid1"]
+    compare3(g.state(), o.state(), 1e-12, cref)
