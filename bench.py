@@ -543,6 +543,22 @@ PAPER_TABLE3_3D_SPEEDUP = {128: 2.882}
 TABLE3_3D_T_RUN = {64: 0.004, 128: 0.002}
 
 
+# Table 4's 3D row (Sec. 4.6: the contracting liquid filament, 64 x 64 x
+# 128 in one eighth of the domain), same i7-4790: r_s = 668940.1 / 275521.6
+PAPER_TABLE4_3D_SPEEDUP = {64: 2.428}
+TABLE4_3D_T_RUN = {32: 3.0e-6, 64: 1.5e-6}
+
+
+def paper_table4_3d(device, sizes=(64,)):
+    """The 3D row of Table 4 on this GPU: the liquid filament with surface
+    tension and viscosity at the start of its contraction."""
+    from paper_1905_03917_gb300 import inputs
+    return _table_3d(device, inputs.filament_3d, sizes, TABLE4_3D_T_RUN,
+                     PAPER_TABLE4_3D_SPEEDUP,
+                     "liquid filament contraction in 3D (Sec. 4.6, Table 4 3D row), Tait "
+                     "liquid in Tait air, surface tension and viscosity, SI units")
+
+
 def paper_table3_3d(device, sizes=(128,)):
     """The 3D row of Table 3 on this GPU: the cubic Tait-liquid drop with
     surface tension and viscosity relaxing toward a sphere, over a short
@@ -892,6 +908,7 @@ def run_ours(args):
                         ("paper_table1", lambda: paper_table1(local)),
                         ("paper_table1_3d", lambda: paper_table1_3d(local)),
                         ("paper_table3_3d", lambda: paper_table3_3d(local)),
+                        ("paper_table4_3d", lambda: paper_table4_3d(local)),
                         ("adjoint", lambda: adjoint_cost(local)),
                         ("adjoint_origin", lambda: adjoint_cost(local, centre=(0.0, 0.0)))):
             try:
@@ -988,7 +1005,8 @@ def main():
         # the 3D droplet (Table 1's 3D row) alone; --size picks one grid
         sizes = (args.size3d,) if args.size3d else (64, 128)
         print(json.dumps({"impl": "ours", "paper_table1_3d": paper_table1_3d(0, sizes),
-                          "paper_table3_3d": paper_table3_3d(0)}), flush=True)
+                          "paper_table3_3d": paper_table3_3d(0),
+                          "paper_table4_3d": paper_table4_3d(0)}), flush=True)
     elif args.workload == "adjoint":
         # the adjoint measurement alone (gas-water bubble at x = 0.7, n x n,
         # --steps single-dt steps, a checkpoint every --steps / 2), e.g. for

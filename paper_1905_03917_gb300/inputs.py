@@ -587,3 +587,26 @@ def circle_recovery_3d(n=128):
     pP = _uniform3(X.shape, 1.0, 0.0, 0.0, 0.0, 1.0e3)
     return {"name": f"circle_recovery_3d_{n}", "cfg": cfg, "phi": phi, "prim_N": pN,
             "prim_P": pP}
+
+
+def filament_3d(n=64):
+    """Sec. 4.6's 3D case (Table 4, 64 x 64 x 128): a liquid filament of
+    radius R = 0.19 mm with a hemispherical cap, its half-length to the
+    cap's centre 1.52 mm, in one eighth of the physical domain (1 x 1 x 2
+    mm; reflective symmetry planes at x = y = z = 0 and walls opposite), SI
+    units.  Tait liquid (rho0 = 1000, p0 = 1e4, B = 3e6, gamma = 7.15, mu =
+    1e-3; fluid N) in Tait air (rho0 = 1, p0 = 1e4, B = 500, gamma = 1.4, mu
+    = 1.6e-5), surface tension 0.072, both at rest."""
+    mm = 1.0e-3
+    d = mm / n
+    liq, gas = tait(3.0e6, 1000.0, 1.0e4, 7.15), tait(500.0, 1.0, 1.0e4, 1.4)
+    cfg = config3(n, n, 2 * n, d, liq, gas, ["reflect"] * 6, sigma=0.072,
+                  mu=(1.0e-3, 1.6e-5))
+    X, Y, Z = _centres3(cfg)
+    zc = 1.52 * mm
+    phi = np.where(Z < zc, np.sqrt(X ** 2 + Y ** 2),
+                   np.sqrt(X ** 2 + Y ** 2 + (Z - zc) ** 2)) - 0.19 * mm
+    pN = _uniform3(X.shape, 1000.0, 0.0, 0.0, 0.0, 1.0e4)
+    pP = _uniform3(X.shape, 1.0, 0.0, 0.0, 0.0, 1.0e4)
+    return {"name": f"filament_3d_{n}x{n}x{2 * n}", "cfg": cfg, "phi": phi, "prim_N": pN,
+            "prim_P": pP}

@@ -298,3 +298,18 @@ def test_circle_recovery_3d_matches_oracle():
     gi, oi = g.step_multi_dt(1), o.step_multi_dt(1)
     assert gi["substeps"] == oi["substeps"] and gi["role_fluid1"] == oi["role_fluid1"]
     compare3(g.state(), o.state(), 1e-12, cref)
+
+
+def test_filament_3d_matches_oracle():
+    """Table 4's 3D case (Tait fluids, surface tension, viscosity, SI
+    units, symmetry planes) at 16 x 16 x 32."""
+    c = I.filament_3d(16)
+    g, o = pair(c)
+    cref = sound_scale(c)
+    for _ in range(2):
+        g.step_single_dt(1)
+        o.step_single_dt(1)
+    compare3(g.state(), o.state(), 1e-12, cref)
+    gi, oi = g.step_multi_dt(1), o.step_multi_dt(1)
+    assert gi["substeps"] == oi["substeps"] and gi["role_fluid1"] == oi["role_fluid1"]
+    compare3(g.state(), o.state(), 1e-12, cref)
