@@ -144,6 +144,18 @@ def test_twenty_cycles_match_oracle():
     compare3(g.state(), o.state(), 1e-8, cref)
 
 
+def test_hundred_cycles_match_oracle():
+    """The long-run bar: 100 accelerated cycles (about 350 water sub-steps)
+    of the droplet with its pressure pulse to 1e-8."""
+    c = pulse_droplet(16)
+    g, o = pair(c)
+    for _ in range(100):
+        gi, oi = g.step_multi_dt(1), o.step_multi_dt(1)
+        assert gi["substeps"] == oi["substeps"]
+    assert g.t == pytest.approx(o.t, rel=1e-10)
+    compare3(g.state(), o.state(), 1e-8, sound_scale(c))
+
+
 def test_conservation_with_correction_on_gpu():
     c = pulse_droplet(16)
     g, _ = pair(c)
