@@ -102,7 +102,8 @@ int sif3_step_multi_dt(sif3_ctx *ctx, int ncycles, double t_end, sif_cycle_info 
 
 /* State out / in: q_N, q_P five planes of alpha U each (mass, x-, y-,
  * z-momentum, energy), phi one plane; any may be NULL.  set_state
- * recomputes the geometry from phi. */
+ * recomputes the geometry from phi and clears the error bits a failed step
+ * left. */
 int sif3_get_state(sif3_ctx *ctx, double *qN, double *qP, double *phi, int mem_kind);
 int sif3_set_state(sif3_ctx *ctx, const double *qN, const double *qP, const double *phi,
                    int mem_kind);
@@ -118,6 +119,17 @@ int sif3_geometry(sif3_ctx *ctx, double *alpha, double *ax, double *ay, double *
                   double *sx, double *sy, double *sz, int mem_kind);
 
 int sif3_get_time(const sif3_ctx *ctx, double *t);
+
+/* Limits of the two bounded loops of a step, as sif_set_limits (no
+ * counterpart in the paper): max_substeps, the fluid-2 sub-steps one
+ * accelerated cycle may take (default 4096), and newton_iters, the Newton
+ * iterations of each interface Riemann problem (default 50).  A cycle that
+ * reaches max_substeps before its last sub-step stops with SIF_ETIMEOUT and
+ * leaves the state undefined (restore it with sif3_set_state); a Riemann
+ * problem not converged after newton_iters iterations makes the step return
+ * SIF_ENOCONV.  A value <= 0 keeps that limit; SIF_EINVAL above 1000000
+ * sub-steps or 10000 iterations. */
+int sif3_set_limits(sif3_ctx *ctx, int max_substeps, int newton_iters);
 
 /* Kernel timing of the finite-volume stages (the dominant kernel): while
  * enabled every launch is bracketed by events on the context's stream and

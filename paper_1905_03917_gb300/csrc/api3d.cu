@@ -36,6 +36,7 @@ struct sif3_ctx {
   Ext3 *ext;
   Mix3 *mix;
   int ext_cap = 0, mix_cap = 0, nbricks = 0;
+  int max_substeps = 4096;
   Scal3 *sc = nullptr;
   Scal3 hs;
   double lf[2][3], smax[2];
@@ -175,6 +176,7 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
   g.sigma = f.sigma;
   g.mu[0] = f.mu[0];
   g.mu[1] = f.mu[1];
+  g.newton_iters = 50;
   int n = f.nx * f.ny * f.nz;
   c->ext_cap = std::min(n, std::max(1 << 18, n / 4));
   c->mix_cap = std::min(n, std::max(1 << 16, n / 16));
@@ -476,7 +478,9 @@ static int cycle(sif3_ctx *c, double t_end, sif_cycle_info *info) {
   double *qs[2][S3_NC];
   for (;;) {
     sub++;
-    if (sub > 4096) return fail(c, SIF_ETIMEOUT, "sub-cycle loop exceeded 4096 sub-steps");
+    if (sub > c->max_substeps)
+      return fail(c, SIF_ETIMEOUT, "sub-cycle loop reached its limit of " +
+                                       std::to_string(c->max_substeps) + " sub-steps");
     if (sub > 1) {
       k3_launch_interp(c->g, c->band, c->qi, c->prev, c->fut, t2 / dt1, c->st);
       geometry(c, c->phi);
@@ -685,6 +689,8 @@ int sif3_set_state(sif3_ctx *c, const double *qN, const double *qP, const double
   double *one[1] = {c->phi};
   if (!rc && phi) rc = planes_in(c, phi, 1, one, mem_kind);
   if (rc) return rc;
+  // a state set from outside starts without the error bits of the last step
+  cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st);
   geometry(c, c->phi, true);
   rc = rebuild_band(c);
   if (rc) return rc;
@@ -722,6 +728,15 @@ int sif3_geometry(sif3_ctx *c, double *alpha, double *ax, double *ay, double *az
     int rc = planes_out(c, outs[q], 1, &srcs[q], mem_kind);
     if (rc) return rc;
   }
+  return SIF_OK;
+}
+
+int sif3_set_limits(sif3_ctx *c, int max_substeps, int newton_iters) {
+  if (!c) return SIF_EINVAL;
+  if (max_substeps > 1000000 || newton_iters > 10000)
+    return fail(c, SIF_EINVAL, "limits above 1000000 sub-steps or 10000 iterations");
+  if (max_substeps > 0) c->max_substeps = max_substeps;
+  if (newton_iters > 0) c->g.newton_iters = newton_iters;
   return SIF_OK;
 }
 

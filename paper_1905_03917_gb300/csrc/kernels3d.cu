@@ -789,7 +789,7 @@ __global__ void k3_interface(Grid3 g, const int *list, const int *count, int cap
       double fl, dfl, fr, dfr;
       const SideConst sl = side_const(rl, pl, gl, pil, cl, bl);
       const SideConst sr = side_const(rr, pr, gr, pir, cr, br);
-      while (it < 50) {
+      while (it < g.newton_iters) {
         it++;
         riemann_side_k(p + jump, sl, fl, dfl);
         riemann_side_k(p, sr, fr, dfr);

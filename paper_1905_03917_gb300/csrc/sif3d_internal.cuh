@@ -27,6 +27,7 @@ struct Grid3 {
   double eps, mix_alpha;
   double sigma;  // surface tension coefficient (Eq. 10), 0 = none
   double mu[2];  // dynamic viscosities (Eq. 3, 5), 0 = inviscid
+  int newton_iters;  // limit of each interface Newton iteration
 };
 
 __host__ __device__ inline int g3(const Grid3 &g, int i, int j, int k) {

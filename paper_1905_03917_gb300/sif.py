@@ -32,7 +32,7 @@ EXPORTS = ["sif_create", "sif_init_fluids", "sif_step_single_dt", "sif_step_mult
            "sif3_create", "sif3_init_fluids", "sif3_step_single_dt", "sif3_step_multi_dt",
            "sif3_get_state", "sif3_set_state", "sif3_integrals", "sif3_geometry",
            "sif3_get_time", "sif3_profile_enable", "sif3_profile_read", "sif3_last_error",
-           "sif3_destroy"]
+           "sif3_destroy", "sif3_set_limits"]
 
 
 class SifError(RuntimeError):
@@ -159,6 +159,8 @@ def load(path: str | None = None):
     L.sif3_last_error.argtypes = [P]
     L.sif3_last_error.restype = ctypes.c_char_p
     L.sif3_destroy.argtypes = [P]
+    L.sif3_set_limits.argtypes = [P, I, I]
+    L.sif3_set_limits.restype = I
     for f in (L.sif3_create, L.sif3_init_fluids, L.sif3_step_single_dt, L.sif3_step_multi_dt,
               L.sif3_get_state, L.sif3_set_state, L.sif3_integrals, L.sif3_geometry,
               L.sif3_get_time, L.sif3_profile_enable, L.sif3_profile_read, L.sif3_destroy):
@@ -641,6 +643,11 @@ class Solver3:
         v = ctypes.c_double()
         self._check(load().sif3_get_time(self._h, ctypes.byref(v)))
         return v.value
+
+    def set_limits(self, max_substeps=0, newton_iters=0):
+        """Limits of the sub-cycle loop and the interface Newton iteration
+        (<= 0 keeps a limit); see sif3_set_limits."""
+        self._check(load().sif3_set_limits(self._h, int(max_substeps), int(newton_iters)))
 
     def profile_enable(self, on=True):
         self._check(load().sif3_profile_enable(self._h, int(bool(on))))

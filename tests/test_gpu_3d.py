@@ -325,3 +325,35 @@ def test_filament_3d_matches_oracle():
     gi, oi = g.step_multi_dt(1), o.step_multi_dt(1)
     assert gi["substeps"] == oi["substeps"] and gi["role_fluid1"] == oi["role_fluid1"]
     compare3(g.state(), o.state(), 1e-12, cref)
+
+
+# -- error paths of the bounded loops (no fault: host-set limits) -------------
+
+def test_substep_limit_gives_timeout_and_the_context_recovers():
+    sif = _sif()
+    c = pulse_droplet(16)
+    s = sif.Solver3(c["cfg"]).init_fluids(*(np.ascontiguousarray(c[x])
+                                            for x in ("phi", "prim_N", "prim_P")))
+    saved = s.state()
+    s.set_limits(max_substeps=2)
+    with pytest.raises(sif.SifError) as e:
+        s.step_multi_dt(1)
+    assert e.value.code == sif.ETIMEOUT
+    s.set_limits(max_substeps=4096)
+    s.set_state(*saved)
+    assert s.step_multi_dt(1)["substeps"] >= 3
+
+
+def test_newton_limit_gives_noconv_and_the_context_recovers():
+    sif = _sif()
+    c = gas_bubble(16)
+    s = sif.Solver3(c["cfg"]).init_fluids(*(np.ascontiguousarray(c[x])
+                                            for x in ("phi", "prim_N", "prim_P")))
+    saved = s.state()
+    s.set_limits(newton_iters=1)
+    with pytest.raises(sif.SifError) as e:
+        s.step_single_dt(1)
+    assert e.value.code == sif.ENOCONV
+    s.set_limits(newton_iters=50)
+    s.set_state(*saved)
+    s.step_single_dt(1)
