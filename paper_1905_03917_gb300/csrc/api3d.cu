@@ -30,8 +30,9 @@ struct sif3_ctx {
   double *partial;   // integrals: 10 x nz
   double *extA, *extB;
   unsigned char *bandmask, *rext, *nostate, *touched;
-  int *extmap, *srcmap, *counts, *blist, *cutlist;
+  int *extmap, *srcmap, *counts, *blist, *cutlist, *flist[2];
   Region band{nullptr, 0};  // the band list of the last interaction step
+  Region fluid[2] = {{nullptr, 0}, {nullptr, 0}};  // each fluid's brick list
   const Region whole{nullptr, 0};
   Ext3 *ext;
   Mix3 *mix;
@@ -121,6 +122,8 @@ static void carve(sif3_ctx *c, Carver &cv) {
   c->srcmap = cv.take<int>(NP);
   c->counts = cv.take<int>(8);
   c->blist = cv.take<int>((size_t)c->nbricks);
+  c->flist[0] = cv.take<int>((size_t)c->nbricks);
+  c->flist[1] = cv.take<int>((size_t)c->nbricks);
   c->cutlist = cv.take<int>((size_t)c->ext_cap);
   c->ext = cv.take<Ext3>((size_t)3 * c->ext_cap);
   c->mix = cv.take<Mix3>((size_t)c->mix_cap);
@@ -264,11 +267,14 @@ static void geometry(sif3_ctx *c, double *phi, bool all = false) {
 
 // the band list from the current level set, its size read back
 static int rebuild_band(sif3_ctx *c) {
-  k3_launch_band_bricks(c->g, c->nbricks, c->phi, c->blist, c->sc, c->st);
-  int n = 0;
-  cudaMemcpyAsync(&n, &c->sc->nband, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  k3_launch_band_bricks(c->g, c->nbricks, c->phi, c->alpha, c->blist, c->flist[0],
+                        c->flist[1], c->sc, c->st);
+  int n[3] = {0, 0, 0};
+  cudaMemcpyAsync(n, &c->sc->nband, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st);
   int rc = cuda_check(c, cudaStreamSynchronize(c->st), "band list");
-  c->band = Region{c->blist, n};
+  c->band = Region{c->blist, n[0]};
+  c->fluid[0] = Region{c->flist[0], n[1]};
+  c->fluid[1] = Region{c->flist[1], n[2]};
   return rc;
 }
 
@@ -293,6 +299,8 @@ static int read_scalars(sif3_ctx *c) {
     c->smax[k] = bits_d(c->hs.smax[k]);
   }
   c->band = Region{c->blist, c->hs.nband};
+  c->fluid[0] = Region{c->flist[0], c->hs.nfluid[0]};
+  c->fluid[1] = Region{c->flist[1], c->hs.nfluid[1]};
   if (c->hs.err & S3_ERR_CAP)
     return fail(c, SIF_EINVAL, "a band list outgrew its capacity (interface too large for "
                                "the grid's band lists)");
@@ -315,8 +323,10 @@ static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_o
   const Grid3 &g = c->g;
   geometry(c, phi);
   cudaMemsetAsync(c->sc, 0, offsetof(Scal3, err), c->st);  // maxima restart, errors stick
+  // each fluid's cells lie in its brick list (built with the band list
+  // at the previous interaction step)
   for (int k = 0; k < 2; k++)
-    k3_launch_prim(g, k == band_only ? c->band : c->whole, k, qs[k], c->w[k], c->alpha,
+    k3_launch_prim(g, k == band_only ? c->band : c->fluid[k], k, qs[k], c->w[k], c->alpha,
                    c->nostate, c->sc, c->st);
   k3_ext_plan(g, c->band, 0, phi, c->alpha, c->nostate, c->sx, c->sy, c->sz, c->extmap, c->ext,
               c->counts, c->ext_cap, &c->sc->err, c->st);
@@ -327,7 +337,8 @@ static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_o
                        c->extA, c->extB, c->extmap, c->st);
   for (int k = 0; k < 2; k++)
     if (k != band_only)
-      k3_launch_wave_maxima(g, c->whole, k, c->w[k], c->alpha, c->nostate, phi, c->sc, c->st);
+      k3_launch_wave_maxima(g, c->fluid[k], k, c->w[k], c->alpha, c->nostate, phi, c->sc,
+                            c->st);
   if (g.mu[0] > 0.0 && g.mu[1] > 0.0) {
     // the traction's central differences reach the ghost layers
     Planes3 v{};
@@ -345,7 +356,8 @@ static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_o
               c->counts, c->ext_cap, &c->sc->err, c->st);
   k3_launch_ext_sweeps(g, 2, c->cfg.ext_iters, c->ext, c->counts, c->ext_cap, c->ul, 3,
                        c->extA, c->extB, c->extmap, c->st);
-  k3_launch_band_bricks(g, c->nbricks, phi, c->blist, c->sc, c->st);
+  k3_launch_band_bricks(g, c->nbricks, phi, c->alpha, c->blist, c->flist[0], c->flist[1], c->sc,
+                        c->st);
   return read_scalars(c);
 }
 

@@ -294,21 +294,36 @@ void k3_launch_geometry(const Grid3 &g, const Region &R, const double *phi, doub
 }
 
 // the band list: every brick with a cell closer to the interface than
-// thr (|phi| < thr), one CTA per brick; the count lands in sc->nband
-__global__ void k3_band_bricks(Grid3 g, const double *phi, double thr, int *list, Scal3 *sc) {
+// thr (|phi| < thr); and per fluid k the band bricks and those holding
+// fluid k (alpha_k > the sliver threshold): until the next list, fluid k
+// can appear only inside the band, so its real and extended cells lie in
+// its list.  One CTA per brick; the counts land in sc->nband, sc->nfluid
+__global__ void k3_band_bricks(Grid3 g, const double *phi, const double *alpha, double thr,
+                               int *list, int *fl0, int *fl1, Scal3 *sc) {
   const int bi = blockIdx.x, tid = threadIdx.x;
   int nbx = (g.nx + S3_BX - 1) / S3_BX, nby = (g.ny + S3_BY - 1) / S3_BY;
   int i = (bi % nbx) * S3_BX + tid % S3_BX;
   int j = ((bi / nbx) % nby) * S3_BY + (tid / S3_BX) % S3_BY;
   int k = (bi / (nbx * nby)) * S3_BZ + tid / (S3_BX * S3_BY);
-  int near = i < g.nx && j < g.ny && k < g.nz && fabs(phi[g3(g, i, j, k)]) < thr;
-  if (__syncthreads_or(near) && tid == 0) list[atomicAdd(&sc->nband, 1)] = bi;
+  bool valid = i < g.nx && j < g.ny && k < g.nz;
+  int c = valid ? g3(g, i, j, k) : 0;
+  int near = valid && fabs(phi[c]) < thr;
+  int hasN = valid && 1.0 - alpha[c] > S3_ALPHA_REAL;
+  int hasP = valid && alpha[c] > S3_ALPHA_REAL;
+  int b = __syncthreads_or(near);
+  int bN = __syncthreads_or(hasN), bP = __syncthreads_or(hasP);
+  if (tid == 0) {
+    if (b) list[atomicAdd(&sc->nband, 1)] = bi;
+    if (b || bN) fl0[atomicAdd(&sc->nfluid[0], 1)] = bi;
+    if (b || bP) fl1[atomicAdd(&sc->nfluid[1], 1)] = bi;
+  }
 }
 
-void k3_launch_band_bricks(const Grid3 &g, int nbricks, const double *phi, int *list, Scal3 *sc,
-                           cudaStream_t st) {
-  cudaMemsetAsync(&sc->nband, 0, sizeof(int), st);
-  k3_band_bricks<<<nbricks, S3_BX * S3_BY * S3_BZ, 0, st>>>(g, phi, g.bw + 3.0 * g.h, list, sc);
+void k3_launch_band_bricks(const Grid3 &g, int nbricks, const double *phi, const double *alpha,
+                           int *list, int *fl0, int *fl1, Scal3 *sc, cudaStream_t st) {
+  cudaMemsetAsync(&sc->nband, 0, 3 * sizeof(int), st);  // nband, nfluid[2]
+  k3_band_bricks<<<nbricks, S3_BX * S3_BY * S3_BZ, 0, st>>>(g, phi, alpha, g.bw + 3.0 * g.h,
+                                                            list, fl0, fl1, sc);
   tick();
 }
 

@@ -41,7 +41,9 @@ struct Scal3 {
   unsigned long long lf[2][3];
   unsigned long long smax[2];
   int err;
-  int nband;  // bricks in the band list
+  int nband;      // bricks in the band list
+  int nfluid[2];  // bricks in each fluid's list (band and the fluid's cells)
+  int pad;
   unsigned long long cells, open;  // finite-volume stage updates
   unsigned long long launches;
 };
@@ -138,8 +140,8 @@ void k3_launch_ghost(const Grid3 &g, const Planes3 &s, cudaStream_t st);
 void k3_launch_geometry(const Grid3 &g, const Region &R, const double *phi, double *corner,
                         double *alpha, double *ax, double *ay, double *az, double *sx,
                         double *sy, double *sz, cudaStream_t st);
-void k3_launch_band_bricks(const Grid3 &g, int nbricks, const double *phi, int *list, Scal3 *sc,
-                           cudaStream_t st);
+void k3_launch_band_bricks(const Grid3 &g, int nbricks, const double *phi, const double *alpha,
+                           int *list, int *fl0, int *fl1, Scal3 *sc, cudaStream_t st);
 void k3_launch_init_state(const Grid3 &g, const double *alpha, const double *prim_dense,
                           double *const q[S3_NC], double *const w[S3_NC], int k,
                           cudaStream_t st);
