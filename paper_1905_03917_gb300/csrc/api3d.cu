@@ -318,7 +318,7 @@ static int read_scalars(sif3_ctx *c) {
 // accelerated cycle whose fluid-1 states (f) are read only near the
 // interface (its stencil states elsewhere, its time step and its
 // Lax-Friedrichs speeds are not used before they are evaluated again over
-// the whole grid); -1 evaluates both fluids everywhere
+// its brick list); -1 evaluates each fluid over its brick list
 static int eval(sif3_ctx *c, double *const qs[2][S3_NC], double *phi, int band_only = -1) {
   const Grid3 &g = c->g;
   geometry(c, phi);

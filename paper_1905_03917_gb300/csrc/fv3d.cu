@@ -12,10 +12,10 @@
 // brick's faces along d -- its cells' lower faces and the brick's upper
 // boundary -- is reconstructed by WENO5-JS from both sides and multiplied
 // by the aperture A_k (the two reconstructions as fractions over one
-// reciprocal, weno_frac.cuh), into shared memory; (3) each thread adds its cell's
-// difference of the two faces over h_d to its right-hand side in
+// reciprocal, weno_frac.cuh), into shared memory; (3) each thread adds its
+// cell's difference of the two faces times 1/h_d to its right-hand side in
 // registers.  The interface exchange X / V and the RK stage follow in
-// registers.  64 KB of shared memory and 82 registers: three CTAs per SM.
+// registers.  64 KB of shared memory and 70 registers: three CTAs per SM.
 #include <atomic>
 
 #include "sif3d_internal.cuh"
