@@ -507,10 +507,14 @@ __device__ inline void ext_setup_one(const Grid3 &g, int grp, const double *phi,
   if (!in3(g, i + s0, j, kk)) wx = 0.0;
   if (!in3(g, i, j + s1, kk)) wy = 0.0;
   if (!in3(g, i, j, kk + s2)) wz = 0.0;
+  // the upwind-weighted mean sum_d w_d v_d / sum_d w_d with the weights
+  // normalised once per interaction step: each sweep then takes one
+  // product and two FMAs per field instead of a division
   e.den = wx + wy + wz;
-  e.w[0] = wx;
-  e.w[1] = wy;
-  e.w[2] = wz;
+  const double iden = e.den > 0.0 ? 1.0 / e.den : 0.0;
+  e.w[0] = wx * iden;
+  e.w[1] = wy * iden;
+  e.w[2] = wz * iden;
   e.nb[0] = c + s0;
   e.nb[1] = c + s1 * g.PX;
   e.nb[2] = c + s2 * g.PX * g.PY;
@@ -582,7 +586,7 @@ __global__ void k3_ext_sweep(Grid3 g, int group, int nf, ExtBufs B, const Ext3 *
         double v = (s >= 0 && !first) ? rd[(size_t)m * cap + s] : P[e.nb[d]];
         num += e.w[d] * v;
       }
-      val = num / e.den;
+      val = num;
     }
     if (last)
       P[e.cell] = val;
