@@ -37,6 +37,9 @@ struct sif3_ctx {
   Ext3 *ext;
   Mix3 *mix;
   int ext_cap = 0, mix_cap = 0, nbricks = 0;
+  int ntouched = 0;          // touched flags per fluid (the larger brick count)
+  int fv_small[2] = {0, 0};  // brick shape of each fluid's current RK step
+  int sms = 152;
   int max_substeps = 4096;
   Scal3 *sc = nullptr;
   Scal3 hs;
@@ -117,7 +120,7 @@ static void carve(sif3_ctx *c, Carver &cv) {
   c->bandmask = cv.take<unsigned char>(NP);
   c->rext = cv.take<unsigned char>(NP);
   c->nostate = cv.take<unsigned char>(2 * NP);
-  c->touched = cv.take<unsigned char>((size_t)2 * c->nbricks);
+  c->touched = cv.take<unsigned char>((size_t)2 * c->ntouched);
   c->extmap = cv.take<int>(3 * NP);
   c->srcmap = cv.take<int>(NP);
   c->counts = cv.take<int>(8);
@@ -190,6 +193,8 @@ int sif3_create(const sif3_config *cfg, sif3_ctx **out) {
     delete c;
     return rc;
   }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, f.device);
+  c->ntouched = std::max(c->nbricks, k3_fv_bricks(g, 1));
   if (f.cuda_stream) {
     c->st = (cudaStream_t)f.cuda_stream;
   } else {
@@ -365,7 +370,12 @@ static void fv(sif3_ctx *c, int k, int stage, double dt, double *const dst[S3_NC
                double *const cur[S3_NC], double *const base[S3_NC]) {
   ghost_w(c, k);
   Fv3Args a{};
-  a.touched = c->touched + (size_t)k * c->nbricks;
+  // a fluid on fewer bricks than one wave of the stage's CTAs (three per
+  // SM) runs on 4 x 4 x 4 bricks: its launch lasts about one CTA's
+  // lifetime, which the smaller bricks shorten; the shape is kept from
+  // stage 1 to stage 2 (the touched flags are per brick)
+  if (stage == 1) c->fv_small[k] = c->fluid[k].count < 3 * c->sms ? 1 : 0;
+  a.touched = c->touched + (size_t)k * c->ntouched;
   a.k = k;
   a.stage = stage;
   a.dt = dt;
@@ -391,7 +401,7 @@ static void fv(sif3_ctx *c, int k, int stage, double dt, double *const dst[S3_NC
     e1 = c->ev[c->ev_used++];
     cudaEventRecord(e0, c->st);
   }
-  k3_launch_fv(c->g, a, c->sc, c->st);
+  k3_launch_fv(c->g, a, c->sc, c->st, c->fv_small[k]);
   if (c->g.mu[k] > 0.0) k3_launch_viscous(c->g, a, c->st);
   if (c->prof) {
     cudaEventRecord(e1, c->st);

@@ -15,7 +15,9 @@
 // reciprocal, weno_frac.cuh), into shared memory; (3) each thread adds its
 // cell's difference of the two faces times 1/h_d to its right-hand side in
 // registers.  The interface exchange X / V and the RK stage follow in
-// registers.  64 KB of shared memory and 70 registers: three CTAs per SM.
+// registers.  Two shapes are instantiated: 8 x 8 x 4 (256 threads, 64 KB of
+// shared memory, three CTAs per SM) and 4 x 4 x 4 (64 threads, 16 KB) for a
+// fluid on few bricks, whose launch lasts about one CTA lifetime.
 #include <atomic>
 
 #include "sif3d_internal.cuh"
@@ -28,32 +30,44 @@ __device__ inline double ap3(const double *A, int k, int c) {
   return k == 1 ? A[c] : 1.0 - A[c];
 }
 
-// extents of the direction-d pass: the brick plus three cells on either
+// a brick shape of the stage: BX x BY x BZ cells, one thread each.
+// Extents of the direction-d pass: the brick plus three cells on either
 // side along d (the split fluxes a face's stencil reads), and its faces
-__host__ __device__ constexpr int reg_len(int d) {
-  return d == 0 ? S3_BX + 6 : d == 1 ? S3_BY + 6 : S3_BZ + 6;
-}
-__host__ __device__ constexpr int brick_len(int d) {
-  return d == 0 ? S3_BX : d == 1 ? S3_BY : S3_BZ;
-}
-#define S3_REG_MAX ((S3_BZ + 6) * S3_BX * S3_BY)  // the z pass is the largest
-#define S3_FACE_MAX (S3_BX * S3_BY * (S3_BZ + 1))
-#define S3_FV_SMEM (sizeof(double) * S3_NC * (2 * S3_REG_MAX + S3_FACE_MAX))
+template <int BX, int BY, int BZ>
+struct FvBrick {
+  static constexpr int threads = BX * BY * BZ;
+  __host__ __device__ static constexpr int len(int d) { return d == 0 ? BX : d == 1 ? BY : BZ; }
+  __host__ __device__ static constexpr int reg(int d) { return len(d) + 6; }
+  static constexpr int reg_max = (BZ + 6) * BX * BY > (BX + 6) * BY * BZ
+                                     ? ((BZ + 6) * BX * BY > (BY + 6) * BX * BZ
+                                            ? (BZ + 6) * BX * BY
+                                            : (BY + 6) * BX * BZ)
+                                     : ((BX + 6) * BY * BZ > (BY + 6) * BX * BZ
+                                            ? (BX + 6) * BY * BZ
+                                            : (BY + 6) * BX * BZ);
+  static constexpr int face_max = BX * BY * BZ + (BX * BY > BY * BZ
+                                                      ? (BX * BY > BX * BZ ? BX * BY : BX * BZ)
+                                                      : (BY * BZ > BX * BZ ? BY * BZ : BX * BZ));
+  static constexpr size_t smem = sizeof(double) * S3_NC * (2 * reg_max + face_max);
+};
 
-__global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
+template <int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
+  using B = FvBrick<BX, BY, BZ>;
+  constexpr int S3_REG_MAX = B::reg_max, S3_FACE_MAX = B::face_max;
   extern __shared__ double smem[];
   double *sp = smem;                              // f+ [m][cell of the pass]
   double *sm = sp + S3_NC * S3_REG_MAX;           // f- [m][cell of the pass]
   double *sf = sm + S3_NC * S3_REG_MAX;           // A_k F [m][face of the pass]
   const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
   const int tid = threadIdx.x;
-  const int li = tid % S3_BX, lj = (tid / S3_BX) % S3_BY, lk = tid / (S3_BX * S3_BY);
-  const int i = bx * S3_BX + li, j = by * S3_BY + lj, kk = bz * S3_BZ + lk;
+  const int li = tid % BX, lj = (tid / BX) % BY, lk = tid / (BX * BY);
+  const int i = bx * BX + li, j = by * BY + lj, kk = bz * BZ + lk;
   const bool valid = i < g.nx && j < g.ny && kk < g.nz;
   const int k = a.k;
   const int st[3] = {1, g.PX, g.PX * g.PY};
   const int nn[3] = {g.nx, g.ny, g.nz};
-  const int b0[3] = {bx * S3_BX, by * S3_BY, bz * S3_BZ};
+  const int b0[3] = {bx * BX, by * BY, bz * BZ};
   const double *Ad[3] = {a.ax, a.ay, a.az};
   // reciprocals of the cell sizes and volume, one division each per thread
   const double ih[3] = {1.0 / g.dx, 1.0 / g.dy, 1.0 / g.dz};
@@ -76,7 +90,7 @@ __global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
   }
   if (tid == 0) {
     if (a.stage == 1) a.touched[brick] = 1;
-    int ncell = min(S3_BX, g.nx - b0[0]) * min(S3_BY, g.ny - b0[1]) * min(S3_BZ, g.nz - b0[2]);
+    int ncell = min(BX, g.nx - b0[0]) * min(BY, g.ny - b0[1]) * min(BZ, g.nz - b0[2]);
     atomicAdd(&sc->cells, (unsigned long long)ncell);
     atomicAdd(&sc->open, (unsigned long long)nopen);
   }
@@ -88,8 +102,8 @@ __global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
     // pass layout: position along d fastest, then the two other axes in
     // (x, y, z) order
     const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
-    const int L = reg_len(d), n1 = brick_len(e1), n2 = brick_len(e2);
-    const int ncells = L * n1 * n2, nfaces = (brick_len(d) + 1) * n1 * n2;
+    const int L = B::reg(d), n1 = B::len(e1), n2 = B::len(e2);
+    const int ncells = L * n1 * n2, nfaces = (B::len(d) + 1) * n1 * n2;
     const double ad = a.lf[d];
     // split fluxes of every cell of the pass
     for (int t = tid; t < ncells; t += blockDim.x) {
@@ -126,7 +140,7 @@ __global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
     // (face, component) items: WENO5 from both sides times the aperture
     for (int t = tid; t < nfaces * S3_NC; t += blockDim.x) {
       int f = t % nfaces, m = t / nfaces;
-      int p = f % (brick_len(d) + 1), q = f / (brick_len(d) + 1);
+      int p = f % (B::len(d) + 1), q = f / (B::len(d) + 1);
       int q1 = q % n1, q2 = q / n1;
       int x[3];
       x[d] = b0[d] + p;
@@ -150,7 +164,7 @@ __global__ void __launch_bounds__(256, 2) k3_fv(Grid3 g, Fv3Args a, Scal3 *sc) {
     __syncthreads();
     if (valid) {
       int x[3] = {li, lj, lk};
-      int lo = x[d] + (brick_len(d) + 1) * (x[e1] + n1 * x[e2]);
+      int lo = x[d] + (B::len(d) + 1) * (x[e1] + n1 * x[e2]);
 #pragma unroll
       for (int m = 0; m < S3_NC; m++)
         r[m] += (sf[m * S3_FACE_MAX + lo] - sf[m * S3_FACE_MAX + lo + 1]) * ih[d];
@@ -256,13 +270,29 @@ void k3_launch_viscous(const Grid3 &g, const Fv3Args &a, cudaStream_t st) {
   g_fv_launches++;
 }
 
-void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st) {
+template <int BX, int BY, int BZ>
+static void launch_fv_shape(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st) {
+  using B = FvBrick<BX, BY, BZ>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k3_fv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3_FV_SMEM);
+    cudaFuncSetAttribute(k3_fv<BX, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)B::smem);
     attr = true;
   }
-  dim3 grid((g.nx + S3_BX - 1) / S3_BX, (g.ny + S3_BY - 1) / S3_BY, (g.nz + S3_BZ - 1) / S3_BZ);
-  k3_fv<<<grid, S3_BX * S3_BY * S3_BZ, S3_FV_SMEM, st>>>(g, a, sc);
+  dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + BZ - 1) / BZ);
+  k3_fv<BX, BY, BZ><<<grid, B::threads, B::smem, st>>>(g, a, sc);
+}
+
+int k3_fv_bricks(const Grid3 &g, int small) {
+  return small ? ((g.nx + 3) / 4) * ((g.ny + 3) / 4) * ((g.nz + 3) / 4)
+               : ((g.nx + S3_BX - 1) / S3_BX) * ((g.ny + S3_BY - 1) / S3_BY) *
+                     ((g.nz + S3_BZ - 1) / S3_BZ);
+}
+
+void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st, int small) {
+  if (small)
+    launch_fv_shape<4, 4, 4>(g, a, sc, st);
+  else
+    launch_fv_shape<S3_BX, S3_BY, S3_BZ>(g, a, sc, st);
   g_fv_launches++;
 }

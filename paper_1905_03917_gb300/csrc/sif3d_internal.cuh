@@ -185,7 +185,11 @@ void k3_launch_integrals(const Grid3 &g, double *const q[2][S3_NC], double *part
                          cudaStream_t st);
 void k3_launch_pack(const Grid3 &g, const double *padded, double *dense, int unpack,
                     cudaStream_t st);
-void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st);
+// small = 1 runs the stage on bricks of 4 x 4 x 4 cells (for a fluid on few
+// bricks: many short CTAs instead of a few long ones); the touched flags
+// are per brick of the shape used, which stage 1 and stage 2 must share
+void k3_launch_fv(const Grid3 &g, const Fv3Args &a, Scal3 *sc, cudaStream_t st, int small);
+int k3_fv_bricks(const Grid3 &g, int small);
 // with viscosity: the aperture-weighted divergence of the viscous face
 // fluxes of fluid k (Eq. 5), b dt times it added to the stage result dst
 void k3_launch_viscous(const Grid3 &g, const Fv3Args &a, cudaStream_t st);
