@@ -165,9 +165,9 @@ __device__ inline double corner3(const Grid3 &g, const double *p, int i, int j, 
 
 // positions of the extended range (indices 0..n along each axis): the
 // whole range, or per listed brick its cells and the layer above them (9
-// x 9 x 5 positions in 512 threads; neighbouring bricks share a layer and
-// write the same values there)
-#define S3_EXT_SLOTS 512
+// x 9 x 5 positions, one thread each, packed with no idle slots;
+// neighbouring bricks share a layer and write the same values there)
+#define S3_EXT_SLOTS ((S3_BX + 1) * (S3_BY + 1) * (S3_BZ + 1))
 __device__ inline bool region_ext(const Grid3 &g, const Region &R, long long t, int &i, int &j,
                                   int &k) {
   int ex = g.nx + 1, ey = g.ny + 1;
@@ -180,7 +180,7 @@ __device__ inline bool region_ext(const Grid3 &g, const Region &R, long long t, 
   }
   long long b = t / S3_EXT_SLOTS;
   int l = (int)(t % S3_EXT_SLOTS);
-  if (b >= R.count || l >= (S3_BX + 1) * (S3_BY + 1) * (S3_BZ + 1)) return false;
+  if (b >= R.count) return false;
   int bi = R.list[b];
   int nbx = (g.nx + S3_BX - 1) / S3_BX, nby = (g.ny + S3_BY - 1) / S3_BY;
   i = (bi % nbx) * S3_BX + l % (S3_BX + 1);
